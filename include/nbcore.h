@@ -1,0 +1,285 @@
+/*
+ * nbcore.h -- C ABI of libnbcore, the B300 (sm_103a) nonbonded-force / MD / HMC
+ * library for the hot path of arXiv 2503.20541 (DIMOS).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Atoms of all systems of a handle are concatenated in system order
+ *    ("caller order"); system s owns atoms [offset_s, offset_s + n_s) where
+ *    offset_s is the sum of the n of the systems before it.
+ *  - Positions are float[N][4] = (x, y, z, q): coordinates plus the charge q in
+ *    the fourth slot.  Coordinates may lie anywhere; the library wraps them
+ *    into the box internally and never rewrites caller coordinates except in
+ *    md_step / hmc_trajectory, whose job is to move them.
+ *  - Forces, cotangents and gradients with respect to positions are
+ *    float[N][3].
+ *  - Every pointer marked (device) is CUDA device memory owned by the caller;
+ *    the library keeps no reference past the call.  Pointers marked (host) are
+ *    read during the call only.  The handle owns its scratch (cell lists,
+ *    neighbour list, fixed-point accumulators, PME meshes, cuFFT plans).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Entry points are asynchronous on that stream unless stated otherwise.
+ *  - Errors discovered on the device (list overflow, fixed-point overflow,
+ *    non-finite coordinates) are OR-ed into a sticky device word; nb_check
+ *    synchronises the stream, returns the first of them as a status and
+ *    clears it.  No kernel traps.
+ *  - Units are the caller's (reduced LJ, or kJ/mol, Angstrom, e with ke given).
+ */
+#ifndef NBCORE_H
+#define NBCORE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NB_OK = 0,
+    NB_ERR_ARG = 1,                 /* invalid argument (NULL, size, unsupported option) */
+    NB_ERR_BOX_TOO_SMALL = 2,       /* periodic box edge < 2 r_nl: minimum image is ambiguous */
+    NB_ERR_LIST_OVERFLOW = 3,       /* an atom has more neighbours than the list capacity */
+    NB_ERR_FIXEDPOINT_OVERFLOW = 4, /* |value| * 2^force_bits does not fit in int64 */
+    NB_ERR_NONFINITE = 5,           /* NaN / Inf coordinate */
+    NB_ERR_TIMEOUT = 6,             /* reserved for bounded device waits */
+    NB_ERR_CUDA = 7,                /* a CUDA runtime or cuFFT call failed */
+    NB_ERR_NOMEM = 8                /* device allocation failed */
+} nb_status;
+
+/* Bits of the sticky device error word (nb_check maps them to nb_status). */
+#define NB_DEVERR_LIST_OVERFLOW 1u
+#define NB_DEVERR_FIXEDPOINT 2u
+#define NB_DEVERR_NONFINITE 4u
+
+/* Energy components per system, in this order (FP64). */
+#define NB_E_LJ 0    /* Lennard-Jones, Eq. (lj), r < r_c, optional switch S(x) */
+#define NB_E_DIR 1   /* Ewald direct space, sum ke q_i q_j erfc(alpha r)/r, r < r_c */
+#define NB_E_EXCL 2  /* exclusion correction, -sum_excl ke q_i q_j erf(alpha r)/r */
+#define NB_E_SELF 3  /* Ewald self energy, -ke alpha/sqrt(pi) sum q_i^2 */
+#define NB_E_REC 4   /* PME reciprocal-space energy */
+#define NB_E_KIN 5   /* kinetic energy 1/2 sum m v^2 (MD / HMC only) */
+#define NB_NE 6
+
+/* Term flags for nonbonded_forces / md_step / hmc_trajectory. */
+#define NB_TERM_LJ 1
+#define NB_TERM_COUL 2   /* Ewald direct + exclusion correction + self */
+#define NB_TERM_PME 4    /* PME reciprocal space (systems with a PME mesh) */
+#define NB_TERM_ALL 7
+#define NB_FORCE_REBUILD 256 /* rebuild the neighbour list unconditionally */
+
+/*
+ * One periodic (or open) system.  Follows Sec. 2.1.2 of the paper:
+ *   r_nl = r_cut + r_skin (r_skin is the paper's "ghost radius" r_g, default 0.25 r_c);
+ *   the list is rebuilt when an atom has moved more than r_skin/2;
+ *   LJ with Lorentz-Berthelot mixing, optional switch from r_switch to r_cut;
+ *   Ewald splitting alpha, Coulomb constant ke (ke = 0: no charges);
+ *   smooth PME of order 4 on a pme_grid[0] x pme_grid[1] x pme_grid[2] mesh
+ *   (all zero: no reciprocal space).
+ * Periodic systems need box[d] >= 2 r_nl in every dimension.  Open systems
+ * (periodic = 0) must keep every coordinate inside [0, box).
+ */
+typedef struct {
+    int32_t n_atoms;
+    int32_t periodic;     /* 1: periodic orthorhombic box; 0: open system embedded in `box` */
+    double box[3];
+    double r_cut;
+    double r_skin;
+    double r_switch;      /* < 0: no switch */
+    double alpha;
+    double ke;
+    int32_t pme_grid[3];
+    int32_t pme_order;    /* 4 (the only order implemented) */
+} nb_system_desc;
+
+/* Tuning knobs; zero-initialise for defaults. */
+typedef struct {
+    int32_t max_neighbors;   /* per-atom list capacity (full list); 0: from density */
+    int32_t lanes_per_atom;  /* 4, 8, 16 or 32 lanes per atom in list/pair kernels; 0: auto */
+    int32_t cell_div;        /* cells of edge >= r_nl / cell_div, cell_div in {1, 2}; 0: auto */
+    int32_t force_bits;      /* fixed-point fraction bits for forces; 0: 32 */
+} nb_options;
+
+typedef struct nb_handle nb_handle;
+
+/* Human-readable name of a status. */
+const char* nb_status_str(nb_status s);
+
+/*
+ * Create a handle for n_systems systems on the current CUDA device.
+ *   sys[n_systems]        (host) system descriptors.
+ *   sigma, sqrt_eps [N]   (host) per-atom LJ sigma_i and sqrt(eps_i), caller order
+ *                         (eps_ij = sqrt_eps_i sqrt_eps_j, sigma_ij = (sigma_i + sigma_j)/2).
+ *   excl_off [N+1], excl_idx (host, may both be NULL) CSR exclusion lists in caller
+ *                         indices; a pair is excluded when either atom lists the other
+ *                         (Sec. 2.1.2 "Exclusions and Exceptions"); both atoms must be in
+ *                         the same system.
+ *   opt                   (host, may be NULL) tuning knobs.
+ * Allocates all device scratch.  Returns NB_ERR_BOX_TOO_SMALL / NB_ERR_ARG on invalid
+ * systems, NB_ERR_NOMEM / NB_ERR_CUDA on allocation or plan failure (nothing leaks).
+ */
+nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_systems,
+                    const float* sigma, const float* sqrt_eps,
+                    const int32_t* excl_off, const int32_t* excl_idx,
+                    const nb_options* opt);
+
+/* Free a handle and all its device memory (synchronises the device). NULL is a no-op. */
+void nb_destroy(nb_handle* h);
+
+/* Total atom count and system count of a handle. */
+int64_t nb_num_atoms(const nb_handle* h);
+int32_t nb_num_systems(const nb_handle* h);
+
+/*
+ * Synchronise `stream`, read and clear the sticky device error word.
+ * Returns NB_OK or the status of the first error bit set.
+ */
+nb_status nb_check(nb_handle* h, void* stream);
+
+/*
+ * Neighbour list (Sec. 2.1.2 "Neighborlists"; the NeighborHandling(...).get_neighborlist(pos)
+ * call of the paper).  Cell list with cells of edge >= r_nl/cell_div, counting sort of atoms
+ * by cell, then a Verlet list of all pairs with |mi(x_i - x_j)| < r_nl = r_cut + r_skin,
+ * excluded pairs removed.
+ *   xq [N][4]      (device) positions and charges.
+ *   pairs_out      (device, may be NULL) receives up to max_pairs unordered pairs
+ *                  (i, j), i < j, caller indices, as int32[max_pairs][2]; their order is
+ *                  unspecified.
+ *   n_pairs_out    (host) number of unordered pairs in the list (may exceed max_pairs).
+ *   force_rebuild  0: rebuild only if an atom moved more than r_skin/2 since the last
+ *                  build (the paper's validity test); 1: always.
+ * Synchronous: returns after the list is built.  Errors: NB_ERR_LIST_OVERFLOW (raise
+ * nb_options.max_neighbors), NB_ERR_NONFINITE.
+ */
+nb_status nl_build(nb_handle* h, const float* xq, int32_t* pairs_out, int64_t max_pairs,
+                   int64_t* n_pairs_out, int32_t force_rebuild, void* stream);
+
+/*
+ * Nonbonded energies and forces (Sec. 2.1.2): LJ, Ewald direct erfc Coulomb under the
+ * minimum image, exclusion correction, self energy and PME reciprocal space, selected
+ * by `terms` (NB_TERM_*; add NB_FORCE_REBUILD to force a list rebuild).  The neighbour
+ * list is checked and rebuilt on the device when needed.
+ *   xq [N][4]            (device) positions and charges.
+ *   f_out [N][3]         (device, may be NULL) forces -dE/dx.
+ *   energies [n_sys][6]  (device, may be NULL) FP64 components NB_E_* (NB_E_KIN = 0).
+ * Forces are accumulated in int64 fixed point (2^force_bits units per force unit), so
+ * they are bitwise reproducible run to run.
+ */
+nb_status nonbonded_forces(nb_handle* h, const float* xq, float* f_out, double* energies,
+                           int32_t terms, void* stream);
+
+/*
+ * PME charge spreading alone (Sec. 2.1.2, smooth PME with order-4 cardinal B-splines):
+ *   grid (device) float, for every PME system s the K0*K1*K2 real mesh of system s,
+ *   index ((k0 * K1) + k1) * K2 + k2, systems concatenated in system order (systems
+ *   without PME take no space).  grid[k] = sum_i q_i M4(u_i0 - k0) M4(u_i1 - k1) M4(u_i2 - k2)
+ *   with u_id = K_d x_id / L_d and periodic wrap of k.
+ */
+nb_status pme_spread(nb_handle* h, const float* xq, float* grid, void* stream);
+
+/*
+ * PME force gathering alone: F_i = -q_i sum_k grad_i[M4 M4 M4](k) phi(k) for a caller
+ * potential mesh phi (device, same layout as pme_spread's grid).  f_out [N][3] (device)
+ * is overwritten (atoms of systems without PME get 0).
+ */
+nb_status pme_gather(nb_handle* h, const float* xq, const float* phi, float* f_out, void* stream);
+
+/*
+ * Velocity-Verlet MD (Sec. 2.2.1, steps 1, 2, 4, 5 of the MD loop; no constraints or
+ * thermostat): n_steps steps of every system with its own step dt[s].
+ *   xq [N][4]           (device, in/out) positions and charges (charges untouched).
+ *   v [N][4]            (device, in/out) (vx, vy, vz, inverse mass) -- the fourth slot
+ *                       is read, not written.
+ *   dt [n_sys]          (device) time step per system.
+ *   energies            (device, may be NULL) FP64 [n_steps+1][n_sys][6]: NB_E_* at every
+ *                       integer step including the start.
+ *   terms               NB_TERM_* selection of force terms.
+ * The neighbour list is checked after every drift and rebuilt on the device when needed.
+ */
+nb_status md_step(nb_handle* h, float* xq, float* v, const float* dt, int32_t n_steps,
+                  double* energies, int32_t terms, void* stream);
+
+/*
+ * One HMC proposal per system (Sec. 4): Maxwell-Boltzmann velocities
+ * v0 = sqrt(kT w) xi (w = inverse mass), n_leap velocity-Verlet steps of length dt[s],
+ * E = U + K in FP64, acceptance alpha = min(1, exp(-(E' - E)/kT)), Metropolis test
+ * u[s] < alpha, squared jump |mi(x' - x)|^2 summed over the system's atoms (the
+ * observable O = x of the ESJD loss, Eq. loss).
+ *   x0 [N][4]        (device) start positions and charges.
+ *   x_out [N][4]     (device) the new chain state: the proposal where accepted, x0
+ *                    elsewhere.  May not alias x0.
+ *   inv_mass [N]     (device) inverse masses w_i.
+ *   dt [n_sys]       (device) step per system.
+ *   xi [N][3]        (device) standard-normal deviates for the velocity draw.
+ *   u [n_sys]        (device, FP64) uniforms in [0,1) for the Metropolis test.
+ *   stats [n_sys][4] (device, FP64) out: dH, alpha, jump, accepted (0/1).
+ *   ckpt             (device, may be NULL) float[ceil(n_leap/ckpt_every)][2][N][4]:
+ *                    (positions, velocities) at steps 0, k, 2k, ... for the backward pass.
+ * With checkpoints, the neighbour list is rebuilt at every checkpoint step so that a
+ * recomputation from a checkpoint repeats the forward trajectory bit for bit.
+ */
+nb_status hmc_trajectory(nb_handle* h, const float* x0, float* x_out, const float* inv_mass,
+                         const float* dt, int32_t n_leap, double kT, const float* xi,
+                         const double* u, double* stats, float* ckpt, int32_t ckpt_every,
+                         int32_t terms, void* stream);
+
+/*
+ * Reverse-mode derivative of hmc_trajectory (the differentiation of Sec. 4, done with
+ * a hand-written adjoint of velocity Verlet and the force VJP instead of autograd).
+ * Given cotangents g_alpha[s] and g_jump[s] of each system's acceptance probability
+ * and squared jump, accumulates
+ *   g_dt [n_sys]     (device, FP64, +=) d/d dt[s],
+ *   g_inv_mass [N]   (device, FP32, +=) d/d w_i,
+ * recomputing the trajectory segment by segment from `ckpt` (written by the forward
+ * call with the same arguments) and applying the force VJP at every state.
+ *   stats            (device) the forward call's stats.
+ * The first call with a given ckpt_every allocates a segment buffer of
+ * 3 (ckpt_every + 1) N float4.  Returns NB_ERR_ARG when `terms` includes PME for a
+ * handle with PME systems (the reciprocal-space VJP is not provided).
+ */
+nb_status hmc_trajectory_backward(nb_handle* h, const float* x0, const float* inv_mass,
+                                  const float* dt, int32_t n_leap, double kT, const float* xi,
+                                  const float* ckpt, int32_t ckpt_every, const double* stats,
+                                  const double* g_alpha, const double* g_jump,
+                                  double* g_dt, float* g_inv_mass, int32_t terms, void* stream);
+
+/*
+ * Force vector-Jacobian product of the real-space terms (LJ, Ewald direct, exclusion
+ * correction): for a cotangent lam [N][3],
+ *   gx = (dF/dx)^T lam           (a Hessian-vector product of -E),
+ *   gq, gsigma, gsqrt_eps        gradients of lam . F with respect to q_i, sigma_i and
+ *                                sqrt(eps_i) (each may be NULL),
+ *   f_out                        the forces F at xq (may be NULL).
+ * All outputs are overwritten, (device) FP32.  PME reciprocal space is not included.
+ */
+nb_status nonbonded_force_vjp(nb_handle* h, const float* xq, const float* lam, float* gx,
+                              float* gq, float* gsigma, float* gsqrt_eps, float* f_out,
+                              void* stream);
+
+/* Cumulative number of neighbour-list rebuilds of a handle (synchronises `stream`). */
+int64_t nb_rebuild_count(nb_handle* h, void* stream);
+
+/*
+ * Per-stage timing (a profiling aid; the paper reports runtimes only).  While enabled,
+ * every entry point brackets the kernels of each stage with CUDA events on its stream.
+ * nb_timing_read synchronises `stream`, returns the summed device milliseconds and the
+ * number of timed intervals per stage since the previous read (host arrays of
+ * NB_NSTAGES), and resets them.  Do not enable it while capturing a CUDA graph.
+ */
+#define NB_STAGE_CHECK 0     /* list validity test + scatter of positions to slot order */
+#define NB_STAGE_REBUILD 1   /* cell binning, scan, scatter, in-cell sort, Verlet list build */
+#define NB_STAGE_PAIR 2      /* fused LJ + Ewald-direct + exclusion pair kernel (or its VJP) */
+#define NB_STAGE_SPREAD 3    /* PME charge spreading and mesh conversion */
+#define NB_STAGE_FFT 4       /* cuFFT transforms (reported separately, not our kernels) */
+#define NB_STAGE_CONVOLVE 5  /* PME influence function and reciprocal energy */
+#define NB_STAGE_GATHER 6    /* PME force gathering */
+#define NB_STAGE_UPDATE 7    /* reductions, force output, integrator updates */
+#define NB_NSTAGES 8
+nb_status nb_timing_enable(nb_handle* h, int32_t enable);
+nb_status nb_timing_read(nb_handle* h, void* stream, double* ms, int64_t* intervals);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBCORE_H */

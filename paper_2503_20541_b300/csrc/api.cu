@@ -1,0 +1,675 @@
+// api.cu -- handle lifecycle and the C entry points of libnbcore (include/nbcore.h).
+//
+// Each entry point only enqueues kernels on the caller's stream; the only host
+// synchronisations are nl_build (which returns a count), nb_check,
+// nb_rebuild_count, nb_timing_read and nb_destroy.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace nb;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+nb_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return NB_OK;
+    if (e == cudaErrorMemoryAllocation) return NB_ERR_NOMEM;
+    return NB_ERR_CUDA;
+}
+
+template <class T>
+cudaError_t dalloc(nb_handle* h, T** p, size_t count) {
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * count);
+    if (e == cudaSuccess) {
+        h->allocs.push_back(q);
+        *p = static_cast<T*>(q);
+    }
+    return e;
+}
+
+void free_all(nb_handle* h) {
+    cudaDeviceSynchronize();
+    for (auto& g : h->fft) {
+        if (g.has_r2c) cufftDestroy(g.r2c);
+        if (g.has_c2r) cufftDestroy(g.c2r);
+    }
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+}
+
+inline cudaStream_t S(void* st) { return static_cast<cudaStream_t>(st); }
+
+int round_up(long long a, int b) { return (int)(((a + b - 1) / b) * b); }
+
+const float4* F4(const float* p) { return reinterpret_cast<const float4*>(p); }
+float4* F4(float* p) { return reinterpret_cast<float4*>(p); }
+
+void request_rebuild(nb_handle* h, cudaStream_t st) { cudaMemsetAsync(h->flags, 0x01, sizeof(unsigned), st); }
+
+// Brackets the kernels of one stage with CUDA events when timing is enabled.
+struct Stage {
+    nb_handle* h;
+    cudaStream_t st;
+    explicit Stage(nb_handle* hh, int stage, cudaStream_t s) : h(hh), st(s) {
+        if (!h->timing) return;
+        for (int k = 0; k < 2; ++k) {
+            cudaEvent_t e;
+            if (h->ev_pool.empty()) {
+                cudaEventCreate(&e);
+            } else {
+                e = h->ev_pool.back();
+                h->ev_pool.pop_back();
+            }
+            h->ev_used.push_back(e);
+        }
+        h->ev_stage.push_back(stage);
+        cudaEventRecord(h->ev_used[h->ev_used.size() - 2], st);
+    }
+    ~Stage() {
+        if (h->timing) cudaEventRecord(h->ev_used.back(), st);
+    }
+};
+
+// Validity check, conditional rebuild (device-side flag), flag reset.
+void prepare(nb_handle* h, const float4* xq, bool force, cudaStream_t st) {
+    {
+        Stage sc(h, NB_STAGE_CHECK, st);
+        if (force) request_rebuild(h, st);
+        launch_load(h, xq, st);
+    }
+    Stage sc(h, NB_STAGE_REBUILD, st);
+    launch_rebuild(h, xq, st);
+    launch_clear_rebuild(h, st);
+}
+
+nb_status run_pme(nb_handle* h, cudaStream_t st) {
+    {
+        Stage sc(h, NB_STAGE_SPREAD, st);
+        launch_pme_spread(h, st);
+    }
+    {
+        Stage sc(h, NB_STAGE_FFT, st);
+        if (launch_pme_fft(h, 0, st)) return NB_ERR_CUDA;
+    }
+    {
+        Stage sc(h, NB_STAGE_CONVOLVE, st);
+        launch_pme_convolve(h, st);
+    }
+    {
+        Stage sc(h, NB_STAGE_FFT, st);
+        if (launch_pme_fft(h, 1, st)) return NB_ERR_CUDA;
+    }
+    Stage sc(h, NB_STAGE_GATHER, st);
+    launch_pme_gather(h, st);
+    return NB_OK;
+}
+
+// Full force evaluation into h->ffix (slot order) and the energy partials.
+nb_status eval(nb_handle* h, const float4* xq, int terms, bool force, cudaStream_t st) {
+    prepare(h, xq, force, st);
+    {
+        Stage sc(h, NB_STAGE_PAIR, st);
+        launch_pair(h, terms, st);
+    }
+    if ((terms & NB_TERM_PME) && h->has_pme) return run_pme(h, st);
+    return NB_OK;
+}
+
+nb_status launched() { return from_cuda(cudaGetLastError()); }
+
+__global__ void k_lam_scatter(int N, const float* __restrict__ lam, const int* __restrict__ iperm,
+                              float4* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    out[iperm[i]] = make_float4(lam[3 * (size_t)i], lam[3 * (size_t)i + 1], lam[3 * (size_t)i + 2], 0.f);
+}
+
+__global__ void k_vjp_out(int N, const float4* __restrict__ gx_s, const float2* __restrict__ gp_s,
+                          const int* __restrict__ iperm, float* __restrict__ gx, float* __restrict__ gq,
+                          float* __restrict__ gsig, float* __restrict__ geps) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int k = iperm[i];
+    float4 g = gx_s[k];
+    gx[3 * (size_t)i] = g.x;
+    gx[3 * (size_t)i + 1] = g.y;
+    gx[3 * (size_t)i + 2] = g.z;
+    if (gq) gq[i] = g.w;
+    float2 p = gp_s[k];
+    if (gsig) gsig[i] = p.x;
+    if (geps) geps[i] = p.y;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+}  // namespace
+
+extern "C" {
+
+const char* nb_status_str(nb_status s) {
+    switch (s) {
+        case NB_OK: return "ok";
+        case NB_ERR_ARG: return "invalid argument";
+        case NB_ERR_BOX_TOO_SMALL: return "periodic box edge smaller than 2 r_nl";
+        case NB_ERR_LIST_OVERFLOW: return "neighbour list capacity exceeded";
+        case NB_ERR_FIXEDPOINT_OVERFLOW: return "fixed-point force accumulator overflow";
+        case NB_ERR_NONFINITE: return "non-finite coordinate";
+        case NB_ERR_TIMEOUT: return "device wait timed out";
+        case NB_ERR_CUDA: return "CUDA or cuFFT error";
+        case NB_ERR_NOMEM: return "device allocation failed";
+    }
+    return "unknown status";
+}
+
+nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_systems, const float* sigma,
+                    const float* sqrt_eps, const int32_t* excl_off, const int32_t* excl_idx,
+                    const nb_options* opt) {
+    if (!out) return NB_ERR_ARG;
+    *out = nullptr;
+    if (!sys || n_systems <= 0 || !sigma || !sqrt_eps) return NB_ERR_ARG;
+    long long N = 0;
+    for (int s = 0; s < n_systems; ++s) {
+        const nb_system_desc& d = sys[s];
+        if (d.n_atoms <= 0) return NB_ERR_ARG;
+        for (int k = 0; k < 3; ++k)
+            if (!finite_pos(d.box[k])) return NB_ERR_ARG;
+        if (!finite_pos(d.r_cut) || !(d.r_skin >= 0.0) || !std::isfinite(d.r_skin)) return NB_ERR_ARG;
+        if (d.r_switch >= d.r_cut) return NB_ERR_ARG;
+        if (!(d.alpha >= 0.0) || !std::isfinite(d.alpha) || !std::isfinite(d.ke)) return NB_ERR_ARG;
+        double rnl = d.r_cut + d.r_skin;
+        if (d.periodic)
+            for (int k = 0; k < 3; ++k)
+                if (d.box[k] < 2.0 * rnl) return NB_ERR_BOX_TOO_SMALL;
+        int npme = (d.pme_grid[0] > 0) + (d.pme_grid[1] > 0) + (d.pme_grid[2] > 0);
+        if (npme != 0 && npme != 3) return NB_ERR_ARG;
+        if (npme == 3) {
+            if (!d.periodic || !(d.alpha > 0.0)) return NB_ERR_ARG;
+            if (d.pme_order != 4 && d.pme_order != 0) return NB_ERR_ARG;
+            for (int k = 0; k < 3; ++k)
+                if (d.pme_grid[k] < 4) return NB_ERR_ARG;
+        }
+        N += d.n_atoms;
+    }
+    if (N >= (1LL << 31) - 64) return NB_ERR_ARG;
+    nb_options o;
+    std::memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    if (o.cell_div != 0 && o.cell_div != 1 && o.cell_div != 2) return NB_ERR_ARG;
+    if (o.lanes_per_atom != 0 && o.lanes_per_atom != 4 && o.lanes_per_atom != 8 && o.lanes_per_atom != 16 &&
+        o.lanes_per_atom != 32)
+        return NB_ERR_ARG;
+    if (o.max_neighbors < 0 || o.force_bits < 0 || o.force_bits > 48 || (o.force_bits > 0 && o.force_bits < 8))
+        return NB_ERR_ARG;
+
+    // exclusions: validate and symmetrise
+    std::vector<std::vector<int>> ex((size_t)N);
+    std::vector<int> sid_h((size_t)N);
+    {
+        long long off = 0;
+        for (int s = 0; s < n_systems; ++s) {
+            for (int a = 0; a < sys[s].n_atoms; ++a) sid_h[(size_t)(off + a)] = s;
+            off += sys[s].n_atoms;
+        }
+    }
+    if (excl_off) {
+        if (excl_off[0] != 0) return NB_ERR_ARG;
+        for (long long i = 0; i < N; ++i) {
+            if (excl_off[i + 1] < excl_off[i]) return NB_ERR_ARG;
+            for (int e = excl_off[i]; e < excl_off[i + 1]; ++e) {
+                if (!excl_idx) return NB_ERR_ARG;
+                long long j = excl_idx[e];
+                if (j < 0 || j >= N || j == i || sid_h[(size_t)j] != sid_h[(size_t)i]) return NB_ERR_ARG;
+                ex[(size_t)i].push_back((int)j);
+                ex[(size_t)j].push_back((int)i);
+            }
+        }
+    }
+    std::vector<int> ex_off_h((size_t)N + 1, 0), ex_idx_h;
+    for (long long i = 0; i < N; ++i) {
+        auto& v = ex[(size_t)i];
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        ex_off_h[(size_t)i + 1] = ex_off_h[(size_t)i] + (int)v.size();
+        ex_idx_h.insert(ex_idx_h.end(), v.begin(), v.end());
+    }
+    ex.clear();
+    ex.shrink_to_fit();
+
+    nb_handle* h = new (std::nothrow) nb_handle();
+    if (!h) return NB_ERR_NOMEM;
+    cudaGetDevice(&h->device);
+    h->n_sys = n_systems;
+    h->n_atoms = (int)N;
+    h->desc.assign(sys, sys + n_systems);
+
+    // tuning defaults from the densest system
+    double nb_max = 0.0;
+    int n_max = 0;
+    bool fine_cells = true;
+    for (int s = 0; s < n_systems; ++s) {
+        const nb_system_desc& d = sys[s];
+        double rnl = d.r_cut + d.r_skin;
+        double V = d.box[0] * d.box[1] * d.box[2];
+        nb_max = std::max(nb_max, d.n_atoms / V * 4.18879020478639 * rnl * rnl * rnl);
+        n_max = std::max(n_max, d.n_atoms);
+        for (int k = 0; k < 3; ++k)
+            if (std::floor(d.box[k] * 2.0 / rnl) < 5.0) fine_cells = false;
+    }
+    h->cell_div = o.cell_div ? o.cell_div : (fine_cells ? 2 : 1);
+    h->lanes = o.lanes_per_atom ? o.lanes_per_atom
+                                : (nb_max >= 256 ? 32 : nb_max >= 96 ? 16 : nb_max >= 40 ? 8 : 4);
+    if (o.max_neighbors > 0) {
+        h->cap = round_up(o.max_neighbors, 32);
+    } else {
+        h->cap = round_up((long long)(1.5 * nb_max + 64.0), 32);
+        h->cap = std::max(32, std::min(h->cap, round_up(n_max, 32)));
+    }
+    h->force_bits = o.force_bits ? o.force_bits : 32;
+    h->fscale = std::ldexp(1.0f, h->force_bits);
+    h->finv = std::ldexp(1.0f, -h->force_bits);
+    h->gscale = std::ldexp(1.0, 32);
+
+    // per-system constants and cell grids
+    h->sys_h.resize(n_systems);
+    int cell_off = 0, atom_off = 0;
+    for (int s = 0; s < n_systems; ++s) {
+        const nb_system_desc& d = sys[s];
+        SysDev& D = h->sys_h[s];
+        std::memset(&D, 0, sizeof(D));
+        double rnl = d.r_cut + d.r_skin;
+        long long ncells = 1;
+        for (int k = 0; k < 3; ++k) {
+            D.L[k] = (float)d.box[k];
+            D.invL[k] = (float)(1.0 / d.box[k]);
+            D.halfL[k] = (float)(0.5 * d.box[k]);
+            int nc = std::max(1, (int)std::floor(d.box[k] * h->cell_div / rnl));
+            nc = std::min(nc, 1024);
+            D.nc[k] = nc;
+            D.cell_scale[k] = (float)(nc / d.box[k]);
+            ncells *= nc;
+        }
+        if ((long long)cell_off + ncells >= (1LL << 31) - 1) {
+            delete h;
+            return NB_ERR_ARG;
+        }
+        D.rc2 = (float)(d.r_cut * d.r_cut);
+        D.rnl2 = (float)(rnl * rnl);
+        D.disp2 = (float)(0.25 * d.r_skin * d.r_skin);
+        D.has_switch = (d.r_switch >= 0.0 && d.r_switch < d.r_cut) ? 1 : 0;
+        D.rs = D.has_switch ? (float)d.r_switch : 0.f;
+        D.inv_sw = D.has_switch ? (float)(1.0 / (d.r_cut - d.r_switch)) : 0.f;
+        D.alpha = (float)d.alpha;
+        D.ke = (float)d.ke;
+        D.beta2 = (float)(d.alpha * d.alpha);
+        D.cell_off = cell_off;
+        D.atom_off = atom_off;
+        D.n_atoms = d.n_atoms;
+        D.periodic = d.periodic ? 1 : 0;
+        D.has_coul = d.ke != 0.0;
+        D.has_lj = 1;
+        D.pme = d.pme_grid[0] > 0;
+        for (int k = 0; k < 3; ++k) {
+            D.K[k] = D.pme ? d.pme_grid[k] : 0;
+            double kl = D.K[k] / d.box[k];
+            D.kl_hi[k] = (float)kl;
+            D.kl_lo[k] = (float)(kl - (double)D.kl_hi[k]);
+        }
+        D.stencil = h->cell_div;
+        D.self_coef = -d.ke * d.alpha / std::sqrt(3.14159265358979323846);
+        cell_off += (int)ncells;
+        atom_off += d.n_atoms;
+    }
+    h->n_cells = cell_off;
+    h->n_scan_blocks = cdiv(h->n_cells, kScanTile);
+
+    cudaError_t e = cudaSuccess;
+#define NB_TRY(x)                        \
+    do {                                 \
+        e = (x);                         \
+        if (e != cudaSuccess) goto fail; \
+    } while (0)
+    {
+        NB_TRY(dalloc(h, &h->sys, n_systems));
+        NB_TRY(dalloc(h, &h->sid, N));
+        NB_TRY(dalloc(h, &h->params, N));
+        NB_TRY(dalloc(h, &h->ex_off, N + 1));
+        NB_TRY(dalloc(h, &h->ex_idx, ex_idx_h.size()));
+        NB_TRY(dalloc(h, &h->cell_count, h->n_cells));
+        NB_TRY(dalloc(h, &h->cell_start, (size_t)h->n_cells + 1));
+        NB_TRY(dalloc(h, &h->cell_cursor, h->n_cells));
+        NB_TRY(dalloc(h, &h->scan_bsum, h->n_scan_blocks));
+        NB_TRY(dalloc(h, &h->cellid, N));
+        NB_TRY(dalloc(h, &h->perm_tmp, N));
+        NB_TRY(dalloc(h, &h->perm, N));
+        NB_TRY(dalloc(h, &h->iperm, N));
+        NB_TRY(dalloc(h, &h->xs, N));
+        NB_TRY(dalloc(h, &h->ps, N));
+        NB_TRY(dalloc(h, &h->xref, N));
+        NB_TRY(dalloc(h, &h->nbr, (size_t)N * h->cap));
+        NB_TRY(dalloc(h, &h->nbr_cnt, N));
+        NB_TRY(dalloc(h, &h->ffix, 3 * (size_t)N));
+        NB_TRY(dalloc(h, &h->e_atom, N));
+        NB_TRY(dalloc(h, &h->flags, 4));
+        NB_TRY(dalloc(h, &h->energy, (size_t)n_systems * NB_NE));
+        NB_TRY(dalloc(h, &h->ke_atom, N));
+        NB_TRY(dalloc(h, &h->vwork, N));
+        NB_TRY(dalloc(h, &h->lam, N));
+        NB_TRY(dalloc(h, &h->gx_s, N));
+        NB_TRY(dalloc(h, &h->gp_s, N));
+        NB_TRY(dalloc(h, &h->hbar_atom, N));
+        NB_TRY(dalloc(h, &h->jump_atom, N));
+        NB_TRY(dalloc(h, &h->e0, (size_t)n_systems * NB_NE));
+        NB_TRY(dalloc(h, &h->e1, (size_t)n_systems * NB_NE));
+        NB_TRY(dalloc(h, &h->xbar, N));
+        NB_TRY(dalloc(h, &h->vbar, N));
+        NB_TRY(dalloc(h, &h->xwork, N));
+        NB_TRY(dalloc(h, &h->dhbar, n_systems));
+        NB_TRY(dalloc(h, &h->counter, 1));
+
+        std::vector<float2> prm((size_t)N);
+        for (long long i = 0; i < N; ++i) prm[(size_t)i] = make_float2(sigma[i], sqrt_eps[i]);
+        std::vector<int> ident((size_t)N);
+        for (long long i = 0; i < N; ++i) ident[(size_t)i] = (int)i;
+        NB_TRY(cudaMemcpy(h->sid, sid_h.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
+        NB_TRY(cudaMemcpy(h->params, prm.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
+        NB_TRY(cudaMemcpy(h->ex_off, ex_off_h.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice));
+        if (!ex_idx_h.empty())
+            NB_TRY(cudaMemcpy(h->ex_idx, ex_idx_h.data(), sizeof(int) * ex_idx_h.size(), cudaMemcpyHostToDevice));
+        NB_TRY(cudaMemcpy(h->perm, ident.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
+        NB_TRY(cudaMemcpy(h->iperm, ident.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
+        NB_TRY(cudaMemset(h->xref, 0xff, sizeof(float4) * N));  // NaN: the first call rebuilds
+        NB_TRY(cudaMemset(h->cell_count, 0, sizeof(int) * h->n_cells));
+        NB_TRY(cudaMemset(h->cell_cursor, 0, sizeof(int) * h->n_cells));
+        NB_TRY(cudaMemset(h->nbr_cnt, 0, sizeof(int) * N));
+        NB_TRY(cudaMemset(h->ffix, 0, sizeof(long long) * 3 * N));
+        NB_TRY(cudaMemset(h->e_atom, 0, sizeof(float4) * N));
+        NB_TRY(cudaMemset(h->ke_atom, 0, sizeof(float) * N));
+        NB_TRY(cudaMemset(h->flags, 0, sizeof(unsigned) * 4));
+        NB_TRY(cudaMemset(h->xs, 0, sizeof(float4) * N));
+        NB_TRY(pme_setup(h));
+        NB_TRY(cudaMemcpy(h->sys, h->sys_h.data(), sizeof(SysDev) * n_systems, cudaMemcpyHostToDevice));
+        NB_TRY(cudaDeviceSynchronize());
+    }
+#undef NB_TRY
+    *out = h;
+    return NB_OK;
+fail:
+    free_all(h);
+    delete h;
+    cudaGetLastError();
+    return e == cudaErrorUnknown ? NB_ERR_CUDA : from_cuda(e);
+}
+
+void nb_destroy(nb_handle* h) {
+    if (!h) return;
+    DeviceGuard g(h->device);
+    free_all(h);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->ev_used) cudaEventDestroy(e);
+    delete h;
+}
+
+int64_t nb_num_atoms(const nb_handle* h) { return h ? h->n_atoms : 0; }
+int32_t nb_num_systems(const nb_handle* h) { return h ? h->n_sys : 0; }
+
+nb_status nb_check(nb_handle* h, void* stream) {
+    if (!h) return NB_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaError_t e = cudaStreamSynchronize(S(stream));
+    if (e != cudaSuccess) return NB_ERR_CUDA;
+    unsigned bits = 0;
+    if (cudaMemcpy(&bits, h->flags + 1, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return NB_ERR_CUDA;
+    if (bits) cudaMemset(h->flags + 1, 0, sizeof(unsigned));
+    if (bits & NB_DEVERR_NONFINITE) return NB_ERR_NONFINITE;
+    if (bits & NB_DEVERR_LIST_OVERFLOW) return NB_ERR_LIST_OVERFLOW;
+    if (bits & NB_DEVERR_FIXEDPOINT) return NB_ERR_FIXEDPOINT_OVERFLOW;
+    return NB_OK;
+}
+
+int64_t nb_rebuild_count(nb_handle* h, void* stream) {
+    if (!h) return -1;
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(S(stream));
+    unsigned long long c = 0;
+    cudaMemcpy(&c, h->flags + 2, sizeof(c), cudaMemcpyDeviceToHost);
+    return (int64_t)c;
+}
+
+nb_status nb_timing_enable(nb_handle* h, int32_t enable) {
+    if (!h) return NB_ERR_ARG;
+    h->timing = enable ? 1 : 0;
+    return NB_OK;
+}
+
+nb_status nb_timing_read(nb_handle* h, void* stream, double* ms, int64_t* intervals) {
+    if (!h || !ms) return NB_ERR_ARG;
+    DeviceGuard g(h->device);
+    for (int k = 0; k < NB_NSTAGES; ++k) {
+        ms[k] = 0.0;
+        if (intervals) intervals[k] = 0;
+    }
+    if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return NB_ERR_CUDA;
+    for (size_t r = 0; r < h->ev_stage.size(); ++r) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, h->ev_used[2 * r], h->ev_used[2 * r + 1]) == cudaSuccess) {
+            ms[h->ev_stage[r]] += t;
+            if (intervals) intervals[h->ev_stage[r]] += 1;
+        }
+    }
+    for (cudaEvent_t e : h->ev_used) h->ev_pool.push_back(e);
+    h->ev_used.clear();
+    h->ev_stage.clear();
+    cudaGetLastError();
+    return NB_OK;
+}
+
+nb_status nl_build(nb_handle* h, const float* xq, int32_t* pairs_out, int64_t max_pairs, int64_t* n_pairs_out,
+                   int32_t force_rebuild, void* stream) {
+    if (!h || !xq || (pairs_out && max_pairs < 0)) return NB_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    prepare(h, F4(xq), force_rebuild != 0, st);
+    cudaMemsetAsync(h->counter, 0, sizeof(unsigned long long), st);
+    launch_export_pairs(h, reinterpret_cast<int2*>(pairs_out), pairs_out ? max_pairs : 0, h->counter, st);
+    nb_status s = launched();
+    if (s != NB_OK) return s;
+    unsigned long long c = 0;
+    if (cudaMemcpyAsync(&c, h->counter, sizeof(c), cudaMemcpyDeviceToHost, st) != cudaSuccess) return NB_ERR_CUDA;
+    s = nb_check(h, stream);
+    if (n_pairs_out) *n_pairs_out = (int64_t)c;
+    return s;
+}
+
+nb_status nonbonded_forces(nb_handle* h, const float* xq, float* f_out, double* energies, int32_t terms,
+                           void* stream) {
+    if (!h || !xq) return NB_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    int t = terms & NB_TERM_ALL;
+    nb_status s = eval(h, F4(xq), t, (terms & NB_FORCE_REBUILD) != 0, st);
+    if (s != NB_OK) return s;
+    Stage sc(h, NB_STAGE_UPDATE, st);
+    if (energies) launch_reduce_energy(h, t, 0, energies, st);
+    if (f_out) launch_finalize_forces(h, f_out, st);
+    return launched();
+}
+
+nb_status pme_spread(nb_handle* h, const float* xq, float* grid, void* stream) {
+    if (!h || !xq || !grid) return NB_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    launch_load(h, F4(xq), st);
+    launch_pme_spread_only(h, grid, st);
+    return launched();
+}
+
+nb_status pme_gather(nb_handle* h, const float* xq, const float* phi, float* f_out, void* stream) {
+    if (!h || !xq || !phi || !f_out) return NB_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    launch_load(h, F4(xq), st);
+    launch_pme_gather_only(h, phi, f_out, st);
+    return launched();
+}
+
+nb_status md_step(nb_handle* h, float* xq, float* v, const float* dt, int32_t n_steps, double* energies,
+                  int32_t terms, void* stream) {
+    if (!h || !xq || !v || !dt || n_steps < 1) return NB_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    int t = terms & NB_TERM_ALL;
+    float4* x4 = F4(xq);
+    float4* v4 = F4(v);
+    const size_t stride = (size_t)h->n_sys * NB_NE;
+    nb_status s;
+    for (int step = 0; step <= n_steps; ++step) {
+        s = eval(h, x4, t, step == 0 && (terms & NB_FORCE_REBUILD), st);
+        if (s != NB_OK) return s;
+        float c_pre = step == 0 ? 0.f : 0.5f;
+        float c_post = step == n_steps ? 0.f : 0.5f;
+        Stage sc(h, NB_STAGE_UPDATE, st);
+        launch_integrate(h, x4, v4, nullptr, dt, c_pre, c_post, step < n_steps, nullptr, nullptr, nullptr, st);
+        if (energies) launch_reduce_energy(h, t, 1, energies + (size_t)step * stride, st);
+    }
+    return launched();
+}
+
+nb_status hmc_trajectory(nb_handle* h, const float* x0, float* x_out, const float* inv_mass, const float* dt,
+                         int32_t n_leap, double kT, const float* xi, const double* u, double* stats, float* ckpt,
+                         int32_t ckpt_every, int32_t terms, void* stream) {
+    if (!h || !x0 || !x_out || x0 == x_out || !inv_mass || !dt || !xi || !u || !stats || n_leap < 1 || !(kT > 0.0))
+        return NB_ERR_ARG;
+    if (ckpt && ckpt_every < 1) return NB_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    int t = terms & NB_TERM_ALL;
+    int N = h->n_atoms;
+    float4* x = F4(x_out);
+    float4* ck = ckpt ? F4(ckpt) : nullptr;
+    cudaMemcpyAsync(x_out, x0, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st);
+    launch_hmc_init(h, inv_mass, xi, kT, st);
+    nb_status s = eval(h, x, t, ck != nullptr, st);
+    if (s != NB_OK) return s;
+    launch_reduce_energy(h, t, 1, h->e0, st);
+    for (int l = 0; l < n_leap; ++l) {
+        float4* cx = nullptr;
+        float4* cv = nullptr;
+        if (ck && l % ckpt_every == 0) {
+            cx = ck + (size_t)(l / ckpt_every) * 2 * N;
+            cv = cx + N;
+        }
+        {
+            Stage sc(h, NB_STAGE_UPDATE, st);
+            launch_integrate(h, x, h->vwork, inv_mass, dt, l == 0 ? 0.f : 0.5f, 0.5f, 1, cx, cv, nullptr, st);
+        }
+        s = eval(h, x, t, ck != nullptr && (l + 1) % ckpt_every == 0, st);
+        if (s != NB_OK) return s;
+    }
+    Stage sc(h, NB_STAGE_UPDATE, st);
+    launch_integrate(h, x, h->vwork, inv_mass, dt, 0.5f, 0.f, 0, nullptr, nullptr, nullptr, st);
+    launch_reduce_energy(h, t, 1, h->e1, st);
+    launch_hmc_finish(h, x, F4(x0), kT, u, stats, st);
+    return launched();
+}
+
+nb_status hmc_trajectory_backward(nb_handle* h, const float* x0, const float* inv_mass, const float* dt,
+                                  int32_t n_leap, double kT, const float* xi, const float* ckpt, int32_t ckpt_every,
+                                  const double* stats, const double* g_alpha, const double* g_jump, double* g_dt,
+                                  float* g_inv_mass, int32_t terms, void* stream) {
+    if (!h || !x0 || !inv_mass || !dt || !xi || !ckpt || !stats || !g_alpha || !g_jump || !g_dt || !g_inv_mass ||
+        n_leap < 1 || ckpt_every < 1 || !(kT > 0.0))
+        return NB_ERR_ARG;
+    int t = terms & NB_TERM_ALL;
+    if ((t & NB_TERM_PME) && h->has_pme) return NB_ERR_ARG;  // reciprocal-space VJP not provided
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    int N = h->n_atoms;
+    int k = ckpt_every;
+    if (h->seg_k < k) {
+        // (k+1) states of positions, velocities and half-step velocities
+        float4* p = nullptr;
+        if (cudaMalloc(&p, sizeof(float4) * 3 * (size_t)(k + 1) * N) != cudaSuccess) return NB_ERR_NOMEM;
+        if (h->seg) {
+            cudaFree(h->seg);
+            h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)h->seg), h->allocs.end());
+        }
+        h->seg = p;
+        h->allocs.push_back(p);
+        h->seg_k = k;
+    }
+    const float4* ck = F4(ckpt);
+    auto seg_x = [&](int i) { return h->seg + (size_t)i * N; };
+    auto seg_v = [&](int i) { return h->seg + (size_t)(h->seg_k + 1 + i) * N; };
+    auto seg_p = [&](int i) { return h->seg + (size_t)(2 * (h->seg_k + 1) + i) * N; };
+    cudaMemsetAsync(h->hbar_atom, 0, sizeof(double) * N, st);
+    int n_seg = (n_leap + k - 1) / k;
+    nb_status s;
+    for (int j = n_seg - 1; j >= 0; --j) {
+        int s0 = j * k, e = std::min(s0 + k, (int)n_leap), m = e - s0;
+        cudaMemcpyAsync(h->xwork, ck + (size_t)j * 2 * N, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(h->vwork, ck + (size_t)j * 2 * N + N, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st);
+        s = eval(h, h->xwork, t, true, st);
+        if (s != NB_OK) return s;
+        for (int q = 0; q < m; ++q) {
+            launch_integrate(h, h->xwork, h->vwork, inv_mass, dt, q == 0 ? 0.f : 0.5f, 0.5f, 1, seg_x(q), seg_v(q),
+                             seg_p(q + 1), st);
+            s = eval(h, h->xwork, t, false, st);
+            if (s != NB_OK) return s;
+        }
+        launch_integrate(h, h->xwork, h->vwork, inv_mass, dt, 0.5f, 0.f, 0, seg_x(m), seg_v(m), nullptr, st);
+        if (j == n_seg - 1)
+            launch_bwd_init(h, seg_x(m), seg_v(m), F4(x0), inv_mass, stats, g_alpha, g_jump, kT, g_inv_mass, st);
+        for (int q = m; q >= 1; --q) {
+            int state = s0 + q;
+            float cf = state == n_leap ? 0.5f : 1.0f;
+            prepare(h, seg_x(q), false, st);
+            launch_bwd_lambda(h, inv_mass, dt, cf, st);
+            {
+                Stage sc(h, NB_STAGE_PAIR, st);
+                launch_vjp(h, t, st);
+            }
+            launch_bwd_adjoint(h, inv_mass, dt, cf, state == n_leap, seg_p(q), g_inv_mass, st);
+        }
+    }
+    s = eval(h, F4(x0), t, false, st);
+    if (s != NB_OK) return s;
+    launch_bwd_final(h, inv_mass, dt, xi, kT, g_inv_mass, g_dt, st);
+    return launched();
+}
+
+nb_status nonbonded_force_vjp(nb_handle* h, const float* xq, const float* lam, float* gx, float* gq, float* gsigma,
+                              float* gsqrt_eps, float* f_out, void* stream) {
+    if (!h || !xq || !lam || !gx) return NB_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    int N = h->n_atoms;
+    prepare(h, F4(xq), false, st);
+    k_lam_scatter<<<cdiv(N, 256), 256, 0, st>>>(N, lam, h->iperm, h->lam);
+    {
+        Stage sc(h, NB_STAGE_PAIR, st);
+        launch_vjp(h, NB_TERM_LJ | NB_TERM_COUL, st);
+    }
+    Stage sc(h, NB_STAGE_UPDATE, st);
+    k_vjp_out<<<cdiv(N, 256), 256, 0, st>>>(N, h->gx_s, h->gp_s, h->iperm, gx, gq, gsigma, gsqrt_eps);
+    if (f_out) launch_finalize_forces(h, f_out, st);
+    return launched();
+}
+
+}  // extern "C"

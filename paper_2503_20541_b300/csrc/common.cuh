@@ -1,0 +1,226 @@
+// common.cuh -- internal types and device helpers of libnbcore (sm_103a).
+//
+// Layout in HBM (N atoms over all systems, "caller order" i, "slot order" k):
+//   caller order : xq float4 (x,y,z,q)  [caller-owned], sid int32, params float2
+//                  (sigma, sqrt_eps), xref float4 (positions at the last list build),
+//                  exclusion CSR.
+//   slot order   : atoms sorted by (system, cell, caller index) after each rebuild;
+//                  xs float4 (wrapped x,y,z,q), ps float2, the full neighbour list
+//                  nbr[k*cap + n] (int32 slots) with counts, fixed-point forces
+//                  ffix[d*N + k] (int64, 2^force_bits per unit), per-atom half
+//                  energies e_atom float4.
+//   System s owns the same index range [atom_off, atom_off + n) in both orders.
+#pragma once
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/nbcore.h"
+
+namespace nb {
+
+constexpr int kMaxExclInline = 8;  // exclusions per atom held in registers by the list build
+constexpr float kInvSqrtPi = 0.56418958354775628f;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = 1024 * kScanItems;  // cells per block of the multi-block scan
+
+// Per-system constants, resident in device memory (read through the L1 path).
+struct SysDev {
+    float L[3], invL[3], halfL[3];
+    float cell_scale[3];  // cells per unit length: nc / L
+    float rc2, rnl2, disp2;
+    float rs, inv_sw;     // switch start and 1/(r_c - r_s)
+    float alpha, ke;
+    float beta2;          // alpha^2
+    float pad0;
+    int nc[3];
+    int cell_off;
+    int atom_off, n_atoms;
+    int periodic, has_switch, has_coul, has_lj;
+    int pme;
+    int K[3];
+    int stencil;          // cell_div: neighbour cells span +-stencil per axis
+    long long grid_off;   // real PME mesh offset (elements)
+    long long cgrid_off;  // complex half-spectrum offset (elements)
+    int pad1, pad2;
+    double self_coef;     // -ke alpha / sqrt(pi)
+    float kl_hi[3], kl_lo[3];  // K_d / L_d as an unevaluated sum hi + lo (double-float)
+    float pad3, pad4;
+};
+
+// An FFT group: PME systems sharing one mesh shape, meshes at a fixed stride.
+struct FftGroup {
+    int K[3];
+    int count;
+    long long grid_off, cgrid_off;
+    long long dist_r = 0, dist_c = 0;  // padded mesh strides within the group
+    cufftHandle r2c = 0, c2r = 0;
+    bool has_r2c = false, has_c2r = false;
+};
+
+}  // namespace nb
+
+struct nb_handle {
+    int device = 0;
+    int n_sys = 0;
+    int n_atoms = 0;
+    int cap = 0;        // per-atom neighbour capacity (full list)
+    int lanes = 32;     // lanes per atom in list build / pair kernels
+    int cell_div = 1;
+    int force_bits = 32;
+    float fscale = 4294967296.0f, finv = 1.0f / 4294967296.0f;
+    double gscale = 4294967296.0;  // PME mesh fixed-point scale
+    int n_cells = 0;
+    int n_scan_blocks = 0;
+    int has_pme = 0;
+    long long grid_total = 0, cgrid_total = 0;
+    int n_conv_blocks = 0;
+
+    std::vector<nb_system_desc> desc;
+    std::vector<nb::SysDev> sys_h;
+    std::vector<nb::FftGroup> fft;
+    std::vector<void*> allocs;
+
+    nb::SysDev* sys = nullptr;
+    int* sid = nullptr;          // [N]
+    float2* params = nullptr;    // [N] caller order
+    int* ex_off = nullptr;       // [N+1]
+    int* ex_idx = nullptr;       // [M]
+    int* cell_count = nullptr;   // [n_cells]
+    int* cell_start = nullptr;   // [n_cells+1]
+    int* cell_cursor = nullptr;  // [n_cells]
+    int* scan_bsum = nullptr;    // [n_scan_blocks]
+    int* cellid = nullptr;       // [N] caller order
+    int* perm_tmp = nullptr;     // [N]
+    int* perm = nullptr;         // [N] slot -> caller
+    int* iperm = nullptr;        // [N] caller -> slot
+    float4* xs = nullptr;        // [N] slot
+    float2* ps = nullptr;        // [N] slot
+    float4* xref = nullptr;      // [N] caller
+    int* nbr = nullptr;          // [N*cap]
+    int* nbr_cnt = nullptr;      // [N]
+    long long* ffix = nullptr;   // [3N] slot
+    float4* e_atom = nullptr;    // [N] slot: half energies (E_lj, E_dir, E_excl, 0) of each atom
+    unsigned* flags = nullptr;   // [0] rebuild request, [1] error bits, [2..3] rebuild count (u64)
+    double* energy = nullptr;    // [n_sys * NB_NE] scratch
+    float* ke_atom = nullptr;    // [N] caller
+    // PME
+    long long* gfix = nullptr;   // [grid_total]
+    float* grid = nullptr;       // [grid_total]
+    float2* cgrid = nullptr;     // [cgrid_total]
+    float* green = nullptr;      // [cgrid_total] influence function G(m)
+    int* conv_blk_sys = nullptr; // [n_conv_blocks]
+    int* conv_blk_off = nullptr; // [n_sys+1] first convolve block of each system
+    double* e_pme_blk = nullptr; // [n_conv_blocks]
+    // dynamics scratch
+    float4* vwork = nullptr;     // [N]
+    float4* lam = nullptr;       // [N] slot: cotangent for the VJP kernels
+    float4* gx_s = nullptr;      // [N] slot: VJP result (x,y,z) and gq (w)
+    float2* gp_s = nullptr;      // [N] slot: gsigma, gsqrt_eps
+    double* hbar_atom = nullptr; // [N]
+    double* jump_atom = nullptr; // [N]
+    double* e0 = nullptr;        // [n_sys * NB_NE]
+    double* e1 = nullptr;        // [n_sys * NB_NE]
+    float4* seg = nullptr;       // [3 * (seg_k + 1) * N] backward segment states
+    int seg_k = 0;
+    float4* xbar = nullptr;      // [N] caller
+    float4* vbar = nullptr;      // [N] caller
+    float4* xwork = nullptr;     // [N] caller: backward recomputation positions
+    double* dhbar = nullptr;     // [n_sys] cotangent of dH
+    unsigned long long* counter = nullptr;  // pair export counter
+    // optional per-stage CUDA-event timing
+    int timing = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_stage;           // stage of each recorded (start, stop) pair
+    std::vector<cudaEvent_t> ev_used;    // start, stop, start, stop, ...
+};
+
+namespace nb {
+
+// ---------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ float wrap1(float x, float L, float invL) {
+    float w = x - L * floorf(x * invL);
+    if (w >= L) w -= L;
+    if (w < 0.f) w = 0.f;
+    return w;
+}
+
+// Minimum-image difference xi - xj of two coordinates wrapped into [0, L).  When the
+// pair straddles the boundary the far coordinate is shifted by L first: that shift is
+// exact (Sterbenz), so the only rounding is that of the small final difference (a plain
+// (xi - xj) -/+ L rounds an intermediate of magnitude ~L).
+__device__ __forceinline__ float mi_pair(float xi, float xj, float L, float hL) {
+    float d = xi - xj;
+    if (d > hL) d = (xi - L) - xj;
+    else if (d < -hL) d = xi - (xj - L);
+    return d;
+}
+
+// Minimum image of an arbitrary difference.
+__device__ __forceinline__ float mi_any(float d, float L, float invL) {
+    return d - L * rintf(d * invL);
+}
+
+__device__ __forceinline__ long long to_fix(float v, float scale, unsigned* err) {
+    float s = v * scale;
+    if (!(fabsf(s) < 9.0e18f)) {
+        atomicOr(err, NB_DEVERR_FIXEDPOINT);
+        return 0;
+    }
+    return __float2ll_rn(s);
+}
+
+__device__ __forceinline__ void red_add(long long* p, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+}
+
+template <int P>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int o = P / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------------------------ launchers
+// neighbor.cu
+void launch_load(nb_handle* h, const float4* xq, cudaStream_t st);
+void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st);
+void launch_clear_rebuild(nb_handle* h, cudaStream_t st);
+void launch_export_pairs(nb_handle* h, int2* out, long long max_pairs, unsigned long long* counter,
+                         cudaStream_t st);
+// pair.cu
+void launch_pair(nb_handle* h, int terms, cudaStream_t st);
+void launch_vjp(nb_handle* h, int terms, cudaStream_t st);
+// pme.cu
+cudaError_t pme_setup(nb_handle* h);
+int launch_pme(nb_handle* h, cudaStream_t st);  // spread + FFT + convolve + FFT + gather into ffix
+void launch_pme_spread(nb_handle* h, cudaStream_t st);
+int launch_pme_fft(nb_handle* h, int inverse, cudaStream_t st);
+void launch_pme_convolve(nb_handle* h, cudaStream_t st);
+void launch_pme_gather(nb_handle* h, cudaStream_t st);
+void launch_pme_spread_only(nb_handle* h, float* grid_out, cudaStream_t st);
+void launch_pme_gather_only(nb_handle* h, const float* phi, float* f_out, cudaStream_t st);
+// dynamics.cu
+void launch_reduce_energy(nb_handle* h, int terms, int with_kin, double* dst, cudaStream_t st);
+void launch_finalize_forces(nb_handle* h, float* f_out, cudaStream_t st);
+void launch_integrate(nb_handle* h, float4* xq, float4* v, const float* w_override, const float* dt,
+                      float c_pre, float c_post, int drift, float4* ck_x, float4* ck_v,
+                      float4* ck_p, cudaStream_t st);
+void launch_hmc_init(nb_handle* h, const float* w, const float* xi, double kT, cudaStream_t st);
+void launch_hmc_finish(nb_handle* h, float4* x_out, const float4* x0, double kT, const double* u,
+                       double* stats, cudaStream_t st);
+void launch_bwd_lambda(nb_handle* h, const float* w, const float* dt, float cf, cudaStream_t st);
+void launch_bwd_init(nb_handle* h, const float4* xL, const float4* vL, const float4* x0, const float* w,
+                     const double* stats, const double* g_alpha, const double* g_jump, double kT,
+                     float* wbar, cudaStream_t st);
+void launch_bwd_adjoint(nb_handle* h, const float* w, const float* dt, float cf, int last,
+                        const float4* p_prev, float* wbar, cudaStream_t st);
+void launch_bwd_final(nb_handle* h, const float* w, const float* dt, const float* xi, double kT,
+                      float* wbar, double* g_dt, cudaStream_t st);
+
+}  // namespace nb

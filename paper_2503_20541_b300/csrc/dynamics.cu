@@ -1,0 +1,361 @@
+// dynamics.cu -- energy reduction, velocity Verlet, HMC and the HMC adjoint.
+//
+// Velocity Verlet (Sec. 2.2.1, steps 1, 2, 4, 5) is run as one fused kernel per
+// step: it completes the previous step's second half kick with the new forces,
+// records the kinetic energy at the integer step, applies the next first half
+// kick and drifts the positions.  All per-system reductions (energies, kinetic
+// energy, HMC jump, dt gradient) run one block per system in a fixed order in
+// FP64, so they are deterministic.
+#include "common.cuh"
+
+namespace nb {
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sm) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[w];
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce_energy(const SysDev* __restrict__ sys,
+                                                                const float4* __restrict__ e_atom,
+                                                                const float4* __restrict__ xs,
+                                                                const float* __restrict__ ke_atom,
+                                                                const double* __restrict__ e_pme_blk,
+                                                                const int* __restrict__ blk_off, int terms,
+                                                                int with_kin, double* __restrict__ dst) {
+    __shared__ double sm[kRedThreads / 32];
+    int s = blockIdx.x;
+    const SysDev& S = sys[s];
+    int a0 = S.atom_off, a1 = S.atom_off + S.n_atoms;
+    double lj = 0.0, dir = 0.0, ex = 0.0, q2 = 0.0, kin = 0.0;
+    for (int k = a0 + threadIdx.x; k < a1; k += kRedThreads) {
+        float4 e = e_atom[k];
+        lj += e.x;
+        dir += e.y;
+        ex += e.z;
+        float q = xs[k].w;
+        q2 += (double)q * q;
+        if (with_kin) kin += ke_atom[k];
+    }
+    lj = block_sum(lj, sm);
+    dir = block_sum(dir, sm);
+    ex = block_sum(ex, sm);
+    q2 = block_sum(q2, sm);
+    kin = block_sum(kin, sm);
+    if (threadIdx.x == 0) {
+        double rec = 0.0;
+        if ((terms & NB_TERM_PME) && S.pme && blk_off)
+            for (int b = blk_off[s]; b < blk_off[s + 1]; ++b) rec += e_pme_blk[b];
+        bool coul = (terms & NB_TERM_COUL) != 0;
+        double* o = dst + (size_t)s * NB_NE;
+        o[NB_E_LJ] = (terms & NB_TERM_LJ) ? lj : 0.0;
+        o[NB_E_DIR] = coul ? dir : 0.0;
+        o[NB_E_EXCL] = coul ? ex : 0.0;
+        o[NB_E_SELF] = coul ? S.self_coef * q2 : 0.0;
+        o[NB_E_REC] = rec;
+        o[NB_E_KIN] = with_kin ? kin : 0.0;
+    }
+}
+
+__global__ void k_finalize(int N, const long long* __restrict__ ffix, const int* __restrict__ iperm, float finv,
+                           float* __restrict__ f_out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int k = iperm[i];
+    f_out[3 * (size_t)i] = __ll2float_rn(ffix[k]) * finv;
+    f_out[3 * (size_t)i + 1] = __ll2float_rn(ffix[(size_t)N + k]) * finv;
+    f_out[3 * (size_t)i + 2] = __ll2float_rn(ffix[2 * (size_t)N + k]) * finv;
+}
+
+__device__ __forceinline__ float3 load_force(const long long* __restrict__ ffix, int N, int k, float finv) {
+    return make_float3(__ll2float_rn(ffix[k]) * finv, __ll2float_rn(ffix[(size_t)N + k]) * finv,
+                       __ll2float_rn(ffix[2 * (size_t)N + k]) * finv);
+}
+
+// v <- v + c_pre dt w F ; record KE ; [store x, v] ; v <- v + c_post dt w F ; [store v] ; x <- x + dt v
+__global__ void k_integrate(int N, float4* __restrict__ xq, float4* __restrict__ v, const float* __restrict__ w_ovr,
+                            const float* __restrict__ dt, const int* __restrict__ sid,
+                            const long long* __restrict__ ffix, const int* __restrict__ iperm, float finv,
+                            float c_pre, float c_post, int drift, float* __restrict__ ke_atom,
+                            float4* __restrict__ ck_x, float4* __restrict__ ck_v, float4* __restrict__ ck_p) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float h = dt[sid[i]];
+    float3 F = load_force(ffix, N, iperm[i], finv);
+    float4 vi = v[i];
+    float w = w_ovr ? w_ovr[i] : vi.w;
+    float4 x = xq[i];
+    float a = c_pre * h * w;
+    vi.x = fmaf(a, F.x, vi.x);
+    vi.y = fmaf(a, F.y, vi.y);
+    vi.z = fmaf(a, F.z, vi.z);
+    ke_atom[i] = (w > 0.f) ? 0.5f * (vi.x * vi.x + vi.y * vi.y + vi.z * vi.z) / w : 0.f;
+    if (ck_x) ck_x[i] = x;
+    if (ck_v) ck_v[i] = make_float4(vi.x, vi.y, vi.z, w);
+    float b = c_post * h * w;
+    vi.x = fmaf(b, F.x, vi.x);
+    vi.y = fmaf(b, F.y, vi.y);
+    vi.z = fmaf(b, F.z, vi.z);
+    if (ck_p) ck_p[i] = make_float4(vi.x, vi.y, vi.z, w);
+    if (drift) {
+        x.x = fmaf(h, vi.x, x.x);
+        x.y = fmaf(h, vi.y, x.y);
+        x.z = fmaf(h, vi.z, x.z);
+        xq[i] = x;
+    }
+    v[i] = vi;
+}
+
+// ------------------------------------------------------------------ HMC
+
+__global__ void k_hmc_init(int N, const float* __restrict__ w, const float* __restrict__ xi, double kT,
+                           float4* __restrict__ v, float* __restrict__ ke_atom) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float wi = w[i];
+    float s = sqrtf((float)kT * wi);
+    float vx = s * xi[3 * (size_t)i], vy = s * xi[3 * (size_t)i + 1], vz = s * xi[3 * (size_t)i + 2];
+    v[i] = make_float4(vx, vy, vz, wi);
+    ke_atom[i] = (wi > 0.f) ? 0.5f * (vx * vx + vy * vy + vz * vz) / wi : 0.f;
+}
+
+__global__ void k_hmc_jump(int N, const float4* __restrict__ x1, const float4* __restrict__ x0,
+                           const int* __restrict__ sid, const SysDev* __restrict__ sys, double* __restrict__ jump) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const SysDev& S = sys[sid[i]];
+    float4 a = x1[i], b = x0[i];
+    float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    if (S.periodic) {
+        dx = mi_any(dx, S.L[0], S.invL[0]);
+        dy = mi_any(dy, S.L[1], S.invL[1]);
+        dz = mi_any(dz, S.L[2], S.invL[2]);
+    }
+    jump[i] = (double)dx * dx + (double)dy * dy + (double)dz * dz;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_hmc_accept(const SysDev* __restrict__ sys,
+                                                             const double* __restrict__ jump,
+                                                             const double* __restrict__ e0,
+                                                             const double* __restrict__ e1, double kT,
+                                                             const double* __restrict__ u, double* __restrict__ stats) {
+    __shared__ double sm[kRedThreads / 32];
+    int s = blockIdx.x;
+    const SysDev& S = sys[s];
+    double j = 0.0;
+    for (int k = S.atom_off + threadIdx.x; k < S.atom_off + S.n_atoms; k += kRedThreads) j += jump[k];
+    j = block_sum(j, sm);
+    if (threadIdx.x == 0) {
+        double H0 = 0.0, H1 = 0.0;
+        for (int c = 0; c < NB_NE; ++c) {
+            H0 += e0[(size_t)s * NB_NE + c];
+            H1 += e1[(size_t)s * NB_NE + c];
+        }
+        double dH = H1 - H0;
+        double a = (dH <= 0.0) ? 1.0 : exp(-dH / kT);
+        if (!(dH == dH)) a = 0.0;  // NaN energy: reject
+        double acc = (u[s] < a) ? 1.0 : 0.0;
+        double* o = stats + (size_t)s * 4;
+        o[0] = dH;
+        o[1] = a;
+        o[2] = j;
+        o[3] = acc;
+    }
+}
+
+__global__ void k_hmc_restore(int N, float4* __restrict__ x_out, const float4* __restrict__ x0,
+                              const int* __restrict__ sid, const double* __restrict__ stats) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    if (stats[(size_t)sid[i] * 4 + 3] == 0.0) x_out[i] = x0[i];
+}
+
+// ------------------------------------------------------------- HMC adjoint
+
+// lam (slot order) = cf * dt * w * vbar
+__global__ void k_bwd_lambda(int N, const float4* __restrict__ vbar, const float* __restrict__ w,
+                             const float* __restrict__ dt, const int* __restrict__ sid, const int* __restrict__ iperm,
+                             float cf, float4* __restrict__ lam) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float c = cf * dt[sid[i]] * w[i];
+    float4 b = vbar[i];
+    lam[iperm[i]] = make_float4(c * b.x, c * b.y, c * b.z, 0.f);
+}
+
+// Adjoint of the loss at the final state: xbar = g_jump 2 mi(x_L - x_0), vbar = dHbar v_L / w,
+// wbar += -dHbar |v_L|^2 / (2 w^2), dHbar = g_alpha dalpha/d dH.
+__global__ void k_bwd_init(int N, const float4* __restrict__ xL, const float4* __restrict__ vL,
+                           const float4* __restrict__ x0, const float* __restrict__ w, const int* __restrict__ sid,
+                           const SysDev* __restrict__ sys, const double* __restrict__ stats,
+                           const double* __restrict__ g_alpha, const double* __restrict__ g_jump, double kT,
+                           float4* __restrict__ xbar, float4* __restrict__ vbar, float* __restrict__ wbar,
+                           double* __restrict__ dhbar) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int s = sid[i];
+    const SysDev& S = sys[s];
+    double a = stats[(size_t)s * 4 + 1];
+    double dHb = (a < 1.0) ? -g_alpha[s] * a / kT : 0.0;
+    if (i == S.atom_off) dhbar[s] = dHb;
+    float4 p = xL[i], q = x0[i], v = vL[i];
+    float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+    if (S.periodic) {
+        dx = mi_any(dx, S.L[0], S.invL[0]);
+        dy = mi_any(dy, S.L[1], S.invL[1]);
+        dz = mi_any(dz, S.L[2], S.invL[2]);
+    }
+    float gj = 2.f * (float)g_jump[s];
+    xbar[i] = make_float4(gj * dx, gj * dy, gj * dz, 0.f);
+    float wi = w[i];
+    float fb = (wi > 0.f) ? (float)dHb / wi : 0.f;
+    vbar[i] = make_float4(fb * v.x, fb * v.y, fb * v.z, 0.f);
+    if (wi > 0.f) wbar[i] += -(float)dHb * 0.5f * (v.x * v.x + v.y * v.y + v.z * v.z) / (wi * wi);
+}
+
+// One state s of the reverse sweep, after the VJP kernel at x_s:
+//   xbar += (dF/dx)^T lam [- dHbar F_s at the final state]
+//   hbar += cf w F_s . vbar ; wbar += cf dt F_s . vbar
+//   (drift of step s-1) hbar += p_{s-1} . xbar ; vbar += dt xbar
+__global__ void k_bwd_adjoint(int N, const float4* __restrict__ gx_s, const long long* __restrict__ ffix,
+                              const int* __restrict__ iperm, float finv, const float* __restrict__ w,
+                              const float* __restrict__ dt, const int* __restrict__ sid, float cf,
+                              const double* __restrict__ dhbar, int last, const float4* __restrict__ p_prev,
+                              float4* __restrict__ xbar, float4* __restrict__ vbar, float* __restrict__ wbar,
+                              double* __restrict__ hbar) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int s = sid[i];
+    int k = iperm[i];
+    float h = dt[s];
+    float wi = w[i];
+    float3 F = load_force(ffix, N, k, finv);
+    float4 g = gx_s[k];
+    float4 xb = xbar[i], vb = vbar[i];
+    xb.x += g.x;
+    xb.y += g.y;
+    xb.z += g.z;
+    if (last) {
+        float d = (float)dhbar[s];
+        xb.x -= d * F.x;
+        xb.y -= d * F.y;
+        xb.z -= d * F.z;
+    }
+    float fv = F.x * vb.x + F.y * vb.y + F.z * vb.z;
+    double hb = (double)(cf * wi * fv);
+    wbar[i] += cf * h * fv;
+    float4 p = p_prev[i];
+    hb += (double)(p.x * xb.x + p.y * xb.y + p.z * xb.z);
+    vb.x = fmaf(h, xb.x, vb.x);
+    vb.y = fmaf(h, xb.y, vb.y);
+    vb.z = fmaf(h, xb.z, vb.z);
+    xbar[i] = xb;
+    vbar[i] = vb;
+    hbar[i] += hb;
+}
+
+// State 0: first half kick of step 0 and the Maxwell-Boltzmann draw v0 = sqrt(kT w) xi.
+// (K_0 = kT/2 sum xi^2 depends on neither w nor dt.)
+__global__ void k_bwd_final(int N, const long long* __restrict__ ffix, const int* __restrict__ iperm, float finv,
+                            const float* __restrict__ w, const float* __restrict__ dt, const int* __restrict__ sid,
+                            const float* __restrict__ xi, double kT, const float4* __restrict__ vbar,
+                            float* __restrict__ wbar, double* __restrict__ hbar) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int s = sid[i];
+    float h = dt[s];
+    float wi = w[i];
+    float3 F = load_force(ffix, N, iperm[i], finv);
+    float4 vb = vbar[i];
+    float fv = F.x * vb.x + F.y * vb.y + F.z * vb.z;
+    hbar[i] += (double)(0.5f * wi * fv);
+    float wb = 0.5f * h * fv;
+    if (wi > 0.f) {
+        float s0 = sqrtf((float)kT * wi);
+        float v0x = s0 * xi[3 * (size_t)i], v0y = s0 * xi[3 * (size_t)i + 1], v0z = s0 * xi[3 * (size_t)i + 2];
+        wb += (vb.x * v0x + vb.y * v0y + vb.z * v0z) / (2.f * wi);
+    }
+    wbar[i] += wb;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_bwd_reduce_h(const SysDev* __restrict__ sys,
+                                                               const double* __restrict__ hbar,
+                                                               double* __restrict__ g_dt) {
+    __shared__ double sm[kRedThreads / 32];
+    int s = blockIdx.x;
+    const SysDev& S = sys[s];
+    double t = 0.0;
+    for (int k = S.atom_off + threadIdx.x; k < S.atom_off + S.n_atoms; k += kRedThreads) t += hbar[k];
+    t = block_sum(t, sm);
+    if (threadIdx.x == 0) g_dt[s] += t;
+}
+
+// ------------------------------------------------------------------ launchers
+
+void launch_reduce_energy(nb_handle* h, int terms, int with_kin, double* dst, cudaStream_t st) {
+    k_reduce_energy<<<h->n_sys, kRedThreads, 0, st>>>(h->sys, h->e_atom, h->xs, h->ke_atom, h->e_pme_blk,
+                                                      h->conv_blk_off, terms, with_kin, dst);
+}
+
+void launch_finalize_forces(nb_handle* h, float* f_out, cudaStream_t st) {
+    int N = h->n_atoms;
+    k_finalize<<<cdiv(N, 256), 256, 0, st>>>(N, h->ffix, h->iperm, h->finv, f_out);
+}
+
+void launch_integrate(nb_handle* h, float4* xq, float4* v, const float* w_ovr, const float* dt, float c_pre,
+                      float c_post, int drift, float4* ck_x, float4* ck_v, float4* ck_p, cudaStream_t st) {
+    int N = h->n_atoms;
+    k_integrate<<<cdiv(N, 256), 256, 0, st>>>(N, xq, v, w_ovr, dt, h->sid, h->ffix, h->iperm, h->finv, c_pre, c_post,
+                                              drift, h->ke_atom, ck_x, ck_v, ck_p);
+}
+
+void launch_hmc_init(nb_handle* h, const float* w, const float* xi, double kT, cudaStream_t st) {
+    int N = h->n_atoms;
+    k_hmc_init<<<cdiv(N, 256), 256, 0, st>>>(N, w, xi, kT, h->vwork, h->ke_atom);
+}
+
+void launch_hmc_finish(nb_handle* h, float4* x_out, const float4* x0, double kT, const double* u, double* stats,
+                       cudaStream_t st) {
+    int N = h->n_atoms;
+    k_hmc_jump<<<cdiv(N, 256), 256, 0, st>>>(N, x_out, x0, h->sid, h->sys, h->jump_atom);
+    k_hmc_accept<<<h->n_sys, kRedThreads, 0, st>>>(h->sys, h->jump_atom, h->e0, h->e1, kT, u, stats);
+    k_hmc_restore<<<cdiv(N, 256), 256, 0, st>>>(N, x_out, x0, h->sid, stats);
+}
+
+void launch_bwd_lambda(nb_handle* h, const float* w, const float* dt, float cf, cudaStream_t st) {
+    int N = h->n_atoms;
+    k_bwd_lambda<<<cdiv(N, 256), 256, 0, st>>>(N, h->vbar, w, dt, h->sid, h->iperm, cf, h->lam);
+}
+
+void launch_bwd_init(nb_handle* h, const float4* xL, const float4* vL, const float4* x0, const float* w,
+                     const double* stats, const double* g_alpha, const double* g_jump, double kT, float* wbar,
+                     cudaStream_t st) {
+    int N = h->n_atoms;
+    k_bwd_init<<<cdiv(N, 256), 256, 0, st>>>(N, xL, vL, x0, w, h->sid, h->sys, stats, g_alpha, g_jump, kT, h->xbar,
+                                             h->vbar, wbar, h->dhbar);
+}
+
+void launch_bwd_adjoint(nb_handle* h, const float* w, const float* dt, float cf, int last, const float4* p_prev,
+                        float* wbar, cudaStream_t st) {
+    int N = h->n_atoms;
+    k_bwd_adjoint<<<cdiv(N, 256), 256, 0, st>>>(N, h->gx_s, h->ffix, h->iperm, h->finv, w, dt, h->sid, cf, h->dhbar,
+                                                last, p_prev, h->xbar, h->vbar, wbar, h->hbar_atom);
+}
+
+void launch_bwd_final(nb_handle* h, const float* w, const float* dt, const float* xi, double kT, float* wbar,
+                      double* g_dt, cudaStream_t st) {
+    int N = h->n_atoms;
+    k_bwd_final<<<cdiv(N, 256), 256, 0, st>>>(N, h->ffix, h->iperm, h->finv, w, dt, h->sid, xi, kT, h->vbar, wbar,
+                                              h->hbar_atom);
+    k_bwd_reduce_h<<<h->n_sys, kRedThreads, 0, st>>>(h->sys, h->hbar_atom, g_dt);
+}
+
+}  // namespace nb

@@ -33,6 +33,20 @@ MASS_H = 1.008
 WATER_MOL_DENSITY = 0.03343  # molecules per cubic Angstrom at 1 g/cm^3
 
 
+def f32(v):
+    """Round a scalar parameter to the nearest FP32 value (kept as a Python float).
+
+    The CUDA path holds box lengths, cut-offs, alpha and ke in FP32; giving both
+    it and the FP64 oracle the same FP32-exact values makes them evaluate the
+    same function (a box that is off by one FP32 ulp shifts every pair that
+    crosses the periodic boundary)."""
+    return float(np.float32(v))
+
+
+def f32_box(L):
+    return np.array([f32(l) for l in np.broadcast_to(np.asarray(L, np.float64), (3,))])
+
+
 @dataclass
 class System:
     """One periodic system: per-atom arrays plus the interaction settings."""
@@ -55,6 +69,13 @@ class System:
     types: np.ndarray = None     # (n,) int32 atom types (mass sharing)
     v: np.ndarray = None         # (n, 3) float32 initial velocities (MD)
     extra: dict = field(default_factory=dict)
+
+    def __setattr__(self, k, v):
+        if k in ("r_cut", "r_skin", "alpha", "ke") or (k == "r_switch" and v is not None and v >= 0):
+            v = f32(v)
+        elif k == "box":
+            v = f32_box(v)
+        object.__setattr__(self, k, v)
 
     @property
     def n(self):

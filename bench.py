@@ -1,0 +1,453 @@
+#!/usr/bin/env python
+"""Benchmark of the nonbonded force path on B300.
+
+Workload (one "step"): one full nonbonded force evaluation of the water box
+of 24,000 atoms (8000 three-site molecules, 62.1 A cubic box, r_c = 9 A,
+r_skin = 2.25 A, Ewald alpha = 0.32 / A, PME 64^3 order 4): neighbour-list
+validity test, list rebuild (forced every step, so every row of the path runs),
+fused LJ + Ewald-direct + exclusion pair kernel, PME spread / cuFFT / convolve /
+cuFFT / gather, energy reduction and force output.  Inputs are synthetic and
+resident in HBM; L2 is flushed between timed steps.
+
+Metric value: pair interactions/s = unordered pairs with r < r_c evaluated per
+second (whole job: summed over replicas when run on N GPUs).  Extra keys report
+MD steps/s (LJ fluid, 864 atoms), the backward/forward time ratio of the
+differentiable HMC step (LJ fluid, 2048 atoms x 10 replicas) and the per-stage
+times.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pair interactions/s and MD steps/s at 1 B300; backward/forward time ratio"
+UNIT = "pair interactions/s"
+WORKLOAD = ("water box 24,000 atoms (8000 3-site molecules, 62.1 A cubic, LJ on O, r_c 9 A, r_skin 2.25 A, "
+            "Ewald alpha 0.32/A, PME 64^3 order 4); step = one full nonbonded force evaluation with the "
+            "neighbour list rebuilt every step")
+
+# Algorithmic FP32 work per unordered pair of the pair kernel (flops, FMA = 2);
+# the counts follow the kernel source ("Roofline").
+FLOP_LIST_PAIR = 18   # min-image difference, r^2, compare
+FLOP_LJ_PAIR = 25     # mixing, (sigma/r)^6, energy, force
+FLOP_COUL_PAIR = 45   # erfc, Gaussian, energy, force
+FLOP_EXCL_PAIR = 45   # erf correction of an excluded pair
+N_SM = 148
+FP32_LANES = 128
+KERNELS_PER_STEP = 16  # our launches per forced-rebuild water evaluation (cuFFT not counted)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    a = ap.parse_args()
+    a.warmup = max(a.warmup, 3)
+    return a
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in a side process."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def pair_counts(nbcore, wl, s, torch):
+    """Unordered pair counts of the workload, counted with the library's own list build:
+    list pairs (r < r_nl), in-cutoff pairs (r < r_c), in-cutoff LJ (O-O) pairs."""
+    def count(sys_):
+        with nbcore.Handle([sys_]) as h:
+            _, n = h.nl_build(torch.from_numpy(nbcore.pack_xq(sys_.x, sys_.q)).cuda(), force_rebuild=True)
+        return int(n)
+    n_list = count(s)
+    s0 = wl.water_box()
+    s0.r_skin = 0.0
+    n_cut = count(s0)
+    o = s0.sqrt_eps > 0
+    so = wl.System(name="oxygen", x=s0.x[o], q=s0.q[o], sigma=s0.sigma[o], sqrt_eps=s0.sqrt_eps[o],
+                   mass=s0.mass[o], box=s0.box, r_cut=s0.r_cut, r_skin=0.0)
+    n_cut_lj = count(so)
+    n_excl = 3 * (s.n // 3)
+    return {"list": n_list, "cutoff": n_cut, "cutoff_lj": n_cut_lj, "excluded": n_excl}
+
+
+def cpu_baseline(s, n_cut, repeats=3):
+    """The FP64 oracle as it stands, timed on the host cores: every row of the
+    all-pairs real-space sum plus the full FP64 smooth PME, best of `repeats`."""
+    import oracle
+    from oracle import pme as opme
+    p = oracle.make_params(s.box, r_cut=s.r_cut, alpha=s.alpha, ke=s.ke)
+    x = s.x.astype(np.float64)
+    rows = np.arange(s.n)
+    best = None
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        oracle.nonbonded_rows(x, s.q, s.sigma, s.sqrt_eps, p, rows, excl=s.excl)
+        opme.pme(x, s.q.astype(np.float64), s.box, s.alpha, s.ke, s.pme_grid)
+        t = time.perf_counter() - t0
+        best = t if best is None else min(best, t)
+    return {"value": n_cut / best, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "full force evaluation of the 24,000-atom box: all 24,000 rows of the FP64 all-pairs "
+                      "real-space sum (OpenMP over rows) + the full FP64 smooth PME (numpy FFT); best of %d, "
+                      "%.2f s each" % (repeats, best)}
+
+
+def run_reference(args):
+    """CPU reference arm: the FP64 oracle, each step a bounded sample of the same workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from oracle import pme as opme
+    from paper_2503_20541_b300 import workloads as wl
+    s = wl.water_box()
+    p = oracle.make_params(s.box, r_cut=s.r_cut, alpha=s.alpha, ke=s.ke)
+    x = s.x.astype(np.float64)
+    frac = 4
+    rows = np.arange(0, s.n, frac)
+    # in-cutoff pair count of the workload (unordered, exclusions removed), by brute force
+    n_cut = 0
+    for i0 in range(0, s.n, 2000):
+        d = x[i0:i0 + 2000, None, :] - x[None, :, :]
+        d -= s.box * np.round(d / s.box)
+        r2 = np.einsum("ijk,ijk->ij", d, d)
+        n_cut += int(np.count_nonzero(r2 < s.r_cut ** 2)) - min(2000, s.n - i0)
+    n_cut = (n_cut - 2 * 3 * (s.n // 3)) // 2
+
+    def step():
+        t0 = time.perf_counter()
+        oracle.nonbonded_rows(x, s.q, s.sigma, s.sqrt_eps, p, rows, excl=s.excl)
+        t_rows = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        opme.pme(x, s.q.astype(np.float64), s.box, s.alpha, s.ke, s.pme_grid)
+        return t_rows * frac + (time.perf_counter() - t1)
+    for _ in range(args.warmup):
+        step()
+    ts = [step() for _ in range(args.steps)]
+    ms = 1e3 * float(np.mean(ts))
+    v = n_cut / (ms / 1e3)
+    cores = oracle.num_threads()
+    sample = ("every %dth of the 24,000 rows of the FP64 all-pairs real-space sum (time x %d) + the full FP64 "
+              "smooth PME, per step" % (frac, frac))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "cpu host cores"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def flops_per_launch(pc):
+    return (FLOP_LIST_PAIR * pc["list"] + FLOP_LJ_PAIR * pc["cutoff_lj"] + FLOP_COUL_PAIR * pc["cutoff"]
+            + FLOP_EXCL_PAIR * pc["excluded"])
+
+
+def traffic_from_profile(path):
+    """DRAM bytes per launch of the pair kernel from the committed ncu summary, if it
+    was taken on the current kernel source (its sha256 prefix is recorded there)."""
+    try:
+        src = open(os.path.join(ROOT, "paper_2503_20541_b300", "csrc", "pair.cu"), "rb").read()
+        sha = hashlib.sha256(src).hexdigest()[:16]
+        rec = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+        if rec.get("pair_cu_sha256_16") != sha:
+            return None
+        return float(rec["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def extras(torch, nbcore, wl):
+    """MD steps/s (LJ 864) and the backward/forward ratio of the differentiable HMC step."""
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    # MD: 864-atom LJ fluid, velocity Verlet dt = 0.005
+    s = wl.lj_fcc()
+    xq = torch.from_numpy(nbcore.pack_xq(s.x, s.q)).cuda()
+    v = torch.zeros((s.n, 4), dtype=torch.float32, device="cuda")
+    v[:, :3] = torch.from_numpy(s.v).cuda()
+    v[:, 3] = 1.0
+    dt = torch.tensor([0.005], dtype=torch.float32, device="cuda")
+    with nbcore.Handle([s]) as h:
+        h.md_step(xq, v, dt, 200, terms=nbcore.NB_TERM_LJ)
+        torch.cuda.synchronize()
+        c0 = h.rebuild_count()
+        e0, e1 = ev(), ev()
+        n = 2000
+        e0.record()
+        h.md_step(xq, v, dt, n, terms=nbcore.NB_TERM_LJ)
+        e1.record()
+        torch.cuda.synchronize()
+        h.check()
+        ms = e0.elapsed_time(e1)
+        out["md_steps_per_s"] = {"value": n / (ms / 1e3), "workload": "LJ fluid 864 atoms (FCC 6^3, rho* 0.8442, "
+                                 "r_c 2.5, r_skin 0.3), velocity Verlet dt 0.005, list checked every step",
+                                 "rebuilds": h.rebuild_count() - c0}
+    # backward / forward: LJ 2048 atoms x 10 replicas, L = 32, checkpoints every 8
+    R, L, K = 10, 32, 8
+    systems = []
+    for r in range(R):
+        sr = wl.lj_random(2048, seed=100 + r, n_types=2)
+        sr.r_switch = 2.2
+        systems.append(sr)
+    n_tot = sum(x.n for x in systems)
+    x0 = torch.cat([torch.from_numpy(nbcore.pack_xq(x.x, x.q)) for x in systems]).cuda()
+    x1 = torch.empty_like(x0)
+    w = torch.ones(n_tot, dtype=torch.float32, device="cuda")
+    dts = torch.full((R,), 0.005, dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    xi = torch.randn((n_tot, 3), device="cuda", generator=gen)
+    u = torch.rand(R, dtype=torch.float64, device="cuda", generator=gen)
+    stats = torch.empty((R, 4), dtype=torch.float64, device="cuda")
+    ck = torch.empty(nbcore.ckpt_size(n_tot, L, K), dtype=torch.float32, device="cuda")
+    ga = torch.ones(R, dtype=torch.float64, device="cuda")
+    gj = torch.ones(R, dtype=torch.float64, device="cuda")
+    gdt = torch.zeros(R, dtype=torch.float64, device="cuda")
+    gw = torch.zeros(n_tot, dtype=torch.float32, device="cuda")
+    with nbcore.Handle(systems) as h:
+        def fwd():
+            h.hmc_trajectory(x0, x1, w, dts, L, 1.0, xi, u, stats, ck, K, terms=nbcore.NB_TERM_LJ)
+
+        def bwd():
+            h.hmc_trajectory_backward(x0, w, dts, L, 1.0, xi, ck, K, stats, ga, gj, gdt, gw, terms=nbcore.NB_TERM_LJ)
+        for _ in range(2):
+            fwd()
+            bwd()
+        torch.cuda.synchronize()
+        reps = 5
+        h.timing_enable(True)
+        h.timing_read()
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(reps):
+            fwd()
+        e1.record()
+        torch.cuda.synchronize()
+        st_f = h.timing_read()
+        e2, e3 = ev(), ev()
+        e2.record()
+        for _ in range(reps):
+            bwd()
+        e3.record()
+        torch.cuda.synchronize()
+        st_b = h.timing_read()
+        h.timing_enable(False)
+        h.check()
+        t_f = e0.elapsed_time(e1) / reps
+        t_b = e2.elapsed_time(e3) / reps
+        kf = st_f["pair"][0] / max(st_f["pair"][1], 1)
+        kb = st_b["pair"][0] / max(st_b["pair"][1], 1)
+        out["bwd_fwd_ratio"] = {
+            "trajectory": t_b / t_f, "kernel": kb / kf, "fwd_ms": t_f, "bwd_ms": t_b,
+            "pair_kernel_us": 1e3 * kf, "vjp_kernel_us": 1e3 * kb,
+            "workload": "differentiable HMC, LJ fluid 2048 atoms x 10 replicas (batched in one handle), "
+                        "32 leapfrog steps, checkpoints every 8 (recompute in the backward), switch 2.2-2.5"}
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2503_20541_b300 import nbcore, workloads as wl
+
+    s = wl.water_box()
+    pc = pair_counts(nbcore, wl, s, torch)
+    xq = torch.from_numpy(nbcore.pack_xq(s.x, s.q)).cuda()
+    f = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+    e = torch.empty((1, 6), dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 126 MB L2
+    h = nbcore.Handle([s])
+
+    def step(rebuild=True):
+        h.nonbonded_forces(xq, f, e, force_rebuild=rebuild)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    h.check()
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    sampler = ClockSampler(vis.split(",")[local] if vis else torch.cuda.current_device())
+    h.timing_enable(True)
+    h.timing_read()
+    sampler.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for i in range(K):
+        flush.zero_()
+        evs[i][0].record()
+        step()
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    stages = h.timing_read()
+    h.timing_enable(False)
+    h.check()
+    ms_local = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    ms = max_over_ranks(ms_local, world)
+    value = world * pc["cutoff"] / (ms / 1e3)
+
+    # list reused (the MD-like case between rebuilds)
+    for _ in range(3):
+        step(rebuild=False)
+    torch.cuda.synchronize()
+    evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for i in range(K):
+        flush.zero_()
+        evr[i][0].record()
+        step(rebuild=False)
+        evr[i][1].record()
+    torch.cuda.synchronize()
+    ms_reuse = float(np.mean([a.elapsed_time(b) for a, b in evr]))
+
+    # end to end through the C ABI with host buffers: H2D positions, evaluation, D2H forces + energies
+    xq_h = xq.cpu().pin_memory()
+    f_h = torch.empty((s.n, 3), dtype=torch.float32).pin_memory()
+    e_h = torch.empty((1, 6), dtype=torch.float64).pin_memory()
+    eve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for i in range(K):
+        flush.zero_()
+        eve[i][0].record()
+        xq.copy_(xq_h, non_blocking=True)
+        step()
+        f_h.copy_(f, non_blocking=True)
+        e_h.copy_(e, non_blocking=True)
+        eve[i][1].record()
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in eve])), world)
+    h.check()
+
+    # roofline of the dominant kernel (the fused pair kernel): FP32-pipe ("alu") bound
+    t_pair = stages["pair"][0] / max(stages["pair"][1], 1)  # ms per launch
+    fl = flops_per_launch(pc)
+    achieved = fl / (t_pair / 1e3) / 1e12
+    f_sm = clocks.get("sm_mhz") or 1920.0
+    peak = N_SM * FP32_LANES * 2 * f_sm * 1e6 / 1e12
+    traffic = traffic_from_profile(os.path.join(ROOT, "profiles", "pair_kernel_water24k.txt"))
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "atoms": s.n, "pairs": pc, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "wall_s_timed_region": t_wall},
+        "roofline": {"bound": "alu", "kernel": "k_pair (fused LJ + Ewald direct + exclusion)", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                     "flops_per_launch": fl, "pair_kernel_us": 1e3 * t_pair,
+                     "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz (measured "
+                                    "during the timed region)" % f_sm},
+        "stage_ms_per_step": {k: v[0] / max(K, 1) for k, v in stages.items()},
+        "ms_per_step_list_reused": ms_reuse,
+        "e2e": {"value": world * pc["cutoff"] / (ms_e2e / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(xq.numel() * 4), "d2h_bytes_per_step": int(f.numel() * 4 + e.numel() * 8)},
+        "clocks": clocks,
+        "gpu_launches": KERNELS_PER_STEP * K,
+    }
+    if rank == 0 and not args.no_extras:
+        out.update(extras(torch, nbcore, wl))
+    if rank == 0 and world == 1:
+        out["cpu_baseline"] = cpu_baseline(s, pc["cutoff"])
+    h.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,151 @@
+"""GPU parity of the HMC proposal (Sec. 4) and of its hand-written adjoint.
+
+Forward: dH, acceptance probability and squared jump per replica against the
+FP64 oracle proposal with the same standard normals.  Backward: dL/d dt and
+dL/d w (inverse masses) of the ESJD loss against FP64 central differences of
+the oracle loss with all random numbers frozen.  The LJ switch is on so that
+the loss is differentiable (with plain truncation cutoff crossings make dH
+jump and finite differences meaningless).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dynamics as odyn
+from paper_2503_20541_b300 import nbcore, workloads as wl
+
+from _helpers import dev_xq, oracle_params
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+R = 4
+N_LEAP = 16
+K_CKPT = 4
+KT = 1.0
+
+
+def _setup(n=256):
+    systems = []
+    for r in range(R):
+        s = wl.lj_random(n, seed=40 + r, n_types=2)
+        s.r_switch = 2.2
+        systems.append(s)
+    masses = odyn.masses_from_logits([0.2, -0.15], systems[0].types, float(n))
+    w = np.tile(1.0 / masses, R).astype(np.float32)
+    dts = np.array([0.004, 0.005, 0.006, 0.0035], np.float32)
+    xi, u = wl.hmc_randoms(R, n, seed=99)
+    return systems, w, dts, xi, u
+
+
+def _oracle_proposal(s, xi, w, dt):
+    p = oracle_params(s)
+
+    def fe(x):
+        e, f = oracle.nonbonded(x, s.q, s.sigma, s.sqrt_eps, p)
+        return f, float(e[0])
+    return odyn.hmc_proposal(s.x.astype(np.float64), xi.astype(np.float64), w.astype(np.float64), float(dt),
+                             N_LEAP, KT, fe, s.box)
+
+
+def _gpu_forward(h, systems, w, dts, xi, u):
+    n_tot = sum(s.n for s in systems)
+    x0 = torch.cat([dev_xq(s) for s in systems])
+    x_out = torch.empty_like(x0)
+    stats = torch.empty((R, 4), dtype=torch.float64, device="cuda")
+    ck = torch.empty(nbcore.ckpt_size(n_tot, N_LEAP, K_CKPT), dtype=torch.float32, device="cuda")
+    args = dict(inv_mass=torch.from_numpy(w).cuda(), dt=torch.from_numpy(dts).cuda(),
+                xi=torch.from_numpy(xi.reshape(-1, 3)).cuda(), u=torch.from_numpy(u).cuda())
+    h.hmc_trajectory(x0, x_out, args["inv_mass"], args["dt"], N_LEAP, KT, args["xi"], args["u"], stats, ck, K_CKPT,
+                     terms=nbcore.NB_TERM_LJ)
+    h.check()
+    return x0, x_out, stats, ck, args
+
+
+def test_hmc_forward_matches_oracle():
+    systems, w, dts, xi, u = _setup()
+    n = systems[0].n
+    with nbcore.Handle(systems) as h:
+        x0, x_out, stats, _, _ = _gpu_forward(h, systems, w, dts, xi, u)
+    st = stats.cpu().numpy()
+    xo = x_out.cpu().numpy()
+    for r, s in enumerate(systems):
+        o = _oracle_proposal(s, xi[r], w[r * n:(r + 1) * n], dts[r])
+        # FP32 energies: |error| ~ 1e-7 * sum|u_ij|; bound by 2e-6 of the energy scale
+        scale = abs(o["U0"]) + o["K0"]
+        assert abs(st[r, 0] - o["dH"]) <= 2e-6 * scale, (r, st[r, 0], o["dH"])
+        assert st[r, 2] == pytest.approx(o["jump"], rel=1e-4)
+        a_gpu = min(1.0, math.exp(-st[r, 0] / KT))
+        assert st[r, 1] == pytest.approx(a_gpu, rel=1e-12)
+        assert st[r, 1] == pytest.approx(o["alpha"], abs=2e-6 * scale)
+        acc = u[r] < st[r, 1]
+        assert st[r, 3] == (1.0 if acc else 0.0)
+        xr = xo[r * n:(r + 1) * n, :3].astype(np.float64)
+        ref = o["x"] if acc else s.x.astype(np.float64)
+        d = xr - ref
+        d -= s.box * np.round(d / s.box)
+        assert np.sqrt(np.mean(d ** 2)) < 1e-4
+
+
+def _replica_loss(s, xi, w, dt):
+    o = _oracle_proposal(s, xi, w, dt)
+    return o["alpha"] * o["jump"] / (R * N_LEAP)
+
+
+def test_hmc_backward_matches_finite_differences():
+    systems, w, dts, xi, u = _setup(n=216)
+    n = systems[0].n
+    with nbcore.Handle(systems) as h:
+        x0, _, stats, ck, a = _gpu_forward(h, systems, w, dts, xi, u)
+        st = stats.cpu().numpy()
+        g_alpha = torch.from_numpy(st[:, 2] / (R * N_LEAP)).cuda()
+        g_jump = torch.from_numpy(st[:, 1] / (R * N_LEAP)).cuda()
+        g_dt = torch.zeros(R, dtype=torch.float64, device="cuda")
+        g_w = torch.zeros(R * n, dtype=torch.float32, device="cuda")
+        h.hmc_trajectory_backward(x0, a["inv_mass"], a["dt"], N_LEAP, KT, a["xi"], ck, K_CKPT, stats, g_alpha,
+                                  g_jump, g_dt, g_w, terms=nbcore.NB_TERM_LJ)
+        h.check()
+    gdt = g_dt.cpu().numpy()
+    gw = g_w.cpu().numpy().astype(np.float64)
+    w64 = w.astype(np.float64)
+    d64 = dts.astype(np.float64)
+    checked = 0
+    for r in range(R):
+        s = systems[r]
+        wr = w64[r * n:(r + 1) * n]
+        o = _oracle_proposal(s, xi[r], wr, d64[r])
+        # alpha = min(1, exp(-dH)) has a kink at dH = 0; the FP32 dH carries an
+        # absolute error of ~1e-6 of the energy scale, so skip replicas inside that band
+        if abs(o["dH"]) < 5e-6 * (abs(o["U0"]) + o["K0"]) or (o["dH"] > 0) != (st[r, 0] > 0):
+            continue
+        checked += 1
+        hstep = 1e-5 * d64[r]
+        fd = (_replica_loss(s, xi[r], wr, d64[r] + hstep) - _replica_loss(s, xi[r], wr, d64[r] - hstep)) / (2 * hstep)
+        assert gdt[r] == pytest.approx(fd, rel=2e-3, abs=1e-9), (r, gdt[r], fd, st[r])
+        # directional derivative along a per-type change of this replica's inverse masses
+        dirv = np.where(s.types == 0, 1.0, -0.7) * wr
+        eps = 1e-5
+        fdw = (_replica_loss(s, xi[r], wr + eps * dirv, d64[r]) - _replica_loss(s, xi[r], wr - eps * dirv, d64[r])) / (
+            2 * eps)
+        assert float(np.dot(gw[r * n:(r + 1) * n], dirv)) == pytest.approx(fdw, rel=2e-3, abs=1e-9), (r, fdw)
+    assert checked >= 2
+
+
+def test_hmc_recompute_is_bitwise_and_rejects_pme_backward():
+    systems, w, dts, xi, u = _setup(n=216)
+    with nbcore.Handle(systems) as h:
+        _, x1, s1, _, _ = _gpu_forward(h, systems, w, dts, xi, u)
+        _, x2, s2, _, _ = _gpu_forward(h, systems, w, dts, xi, u)
+    assert torch.equal(x1, x2) and torch.equal(s1, s2)
+    s = wl.water_box(n_side=6, L=18.9, seed=1, r_cut=8.0, r_skin=1.0, pme_grid=20)
+    with nbcore.Handle([s]) as h:
+        z = torch.zeros(1, dtype=torch.float64, device="cuda")
+        x = dev_xq(s)
+        with pytest.raises(nbcore.NbError):
+            h.hmc_trajectory_backward(x, torch.ones(s.n, device="cuda"), torch.ones(1, device="cuda"), 4, 1.0,
+                                      torch.zeros((s.n, 3), device="cuda"),
+                                      torch.zeros(nbcore.ckpt_size(s.n, 4, 4), device="cuda"), 4,
+                                      torch.zeros((1, 4), dtype=torch.float64, device="cuda"), z, z, z.clone(),
+                                      torch.zeros(s.n, device="cuda"), terms=nbcore.NB_TERM_ALL)

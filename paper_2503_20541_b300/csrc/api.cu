@@ -382,6 +382,20 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(dalloc(h, &h->xwork, N));
         NB_TRY(dalloc(h, &h->dhbar, n_systems));
         NB_TRY(dalloc(h, &h->counter, 1));
+        {
+            std::vector<int> rb_sys, rb_off(n_systems + 1, 0);
+            for (int s = 0; s < n_systems; ++s) {
+                rb_off[s] = (int)rb_sys.size();
+                for (int b = 0; b < cdiv(sys[s].n_atoms, kRedTile); ++b) rb_sys.push_back(s);
+            }
+            rb_off[n_systems] = (int)rb_sys.size();
+            h->n_red_blocks = (int)rb_sys.size();
+            NB_TRY(dalloc(h, &h->red_blk_sys, rb_sys.size()));
+            NB_TRY(dalloc(h, &h->red_blk_off, rb_off.size()));
+            NB_TRY(dalloc(h, &h->red_part, rb_sys.size() * 5));
+            NB_TRY(cudaMemcpy(h->red_blk_sys, rb_sys.data(), sizeof(int) * rb_sys.size(), cudaMemcpyHostToDevice));
+            NB_TRY(cudaMemcpy(h->red_blk_off, rb_off.data(), sizeof(int) * rb_off.size(), cudaMemcpyHostToDevice));
+        }
 
         std::vector<float2> prm((size_t)N);
         for (long long i = 0; i < N; ++i) prm[(size_t)i] = make_float2(sigma[i], sqrt_eps[i]);

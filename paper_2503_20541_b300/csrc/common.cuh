@@ -25,6 +25,7 @@ constexpr int kMaxExclInline = 8;  // exclusions per atom held in registers by t
 constexpr float kInvSqrtPi = 0.56418958354775628f;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = 1024 * kScanItems;  // cells per block of the multi-block scan
+constexpr int kRedTile = 1024;                 // atoms per block of the energy reduction
 
 // Per-system constants, resident in device memory (read through the L1 path).
 struct SysDev {
@@ -105,6 +106,10 @@ struct nb_handle {
     float4* e_atom = nullptr;    // [N] slot: half energies (E_lj, E_dir, E_excl, 0) of each atom
     unsigned* flags = nullptr;   // [0] rebuild request, [1] error bits, [2..3] rebuild count (u64)
     double* energy = nullptr;    // [n_sys * NB_NE] scratch
+    int n_red_blocks = 0;        // energy reduction: blocks of kRedTile atoms, none straddling systems
+    int* red_blk_sys = nullptr;  // [n_red_blocks]
+    int* red_blk_off = nullptr;  // [n_sys+1] first reduction block of each system
+    double* red_part = nullptr;  // [n_red_blocks * 5] per-block FP64 partial sums
     float* ke_atom = nullptr;    // [N] caller
     // PME
     long long* gfix = nullptr;   // [grid_total]

@@ -4,8 +4,8 @@
 // step: it completes the previous step's second half kick with the new forces,
 // records the kinetic energy at the integer step, applies the next first half
 // kick and drifts the positions.  All per-system reductions (energies, kinetic
-// energy, HMC jump, dt gradient) run one block per system in a fixed order in
-// FP64, so they are deterministic.
+// energy, HMC jump, dt gradient) sum in FP64 in a fixed order (energies: per-block
+// partials of 1024 atoms, then one warp per system), so they are deterministic.
 #include "common.cuh"
 
 namespace nb {
@@ -24,17 +24,20 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
     return t;  // valid in thread 0
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_reduce_energy(const SysDev* __restrict__ sys,
-                                                                const float4* __restrict__ e_atom,
-                                                                const float4* __restrict__ xs,
-                                                                const float* __restrict__ ke_atom,
-                                                                const double* __restrict__ e_pme_blk,
-                                                                const int* __restrict__ blk_off, int terms,
-                                                                int with_kin, double* __restrict__ dst) {
+// Energy reduction, stage 1: each block sums kRedTile atoms of one system in FP64.
+__global__ void __launch_bounds__(kRedThreads) k_reduce_part(const int* __restrict__ blk_sys,
+                                                              const int* __restrict__ blk_off,
+                                                              const SysDev* __restrict__ sys,
+                                                              const float4* __restrict__ e_atom,
+                                                              const float4* __restrict__ xs,
+                                                              const float* __restrict__ ke_atom, int with_kin,
+                                                              double* __restrict__ part) {
     __shared__ double sm[kRedThreads / 32];
-    int s = blockIdx.x;
+    int b = blockIdx.x;
+    int s = blk_sys[b];
     const SysDev& S = sys[s];
-    int a0 = S.atom_off, a1 = S.atom_off + S.n_atoms;
+    int a0 = S.atom_off + (b - blk_off[s]) * kRedTile;
+    int a1 = min(a0 + kRedTile, S.atom_off + S.n_atoms);
     double lj = 0.0, dir = 0.0, ex = 0.0, q2 = 0.0, kin = 0.0;
     for (int k = a0 + threadIdx.x; k < a1; k += kRedThreads) {
         float4 e = e_atom[k];
@@ -51,17 +54,42 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_energy(const SysDev* __r
     q2 = block_sum(q2, sm);
     kin = block_sum(kin, sm);
     if (threadIdx.x == 0) {
-        double rec = 0.0;
-        if ((terms & NB_TERM_PME) && S.pme && blk_off)
-            for (int b = blk_off[s]; b < blk_off[s + 1]; ++b) rec += e_pme_blk[b];
+        double* o = part + (size_t)b * 5;
+        o[0] = lj;
+        o[1] = dir;
+        o[2] = ex;
+        o[3] = q2;
+        o[4] = kin;
+    }
+}
+
+// Stage 2: one warp per system adds its blocks' partials (fixed order) and the PME blocks.
+__global__ void k_reduce_final(int n_sys, const SysDev* __restrict__ sys, const int* __restrict__ blk_off,
+                               const double* __restrict__ part, const double* __restrict__ e_pme_blk,
+                               const int* __restrict__ pme_blk_off, int terms, int with_kin,
+                               double* __restrict__ dst) {
+    int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (s >= n_sys) return;
+    const SysDev& S = sys[s];
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = blk_off[s] + lane; b < blk_off[s + 1]; b += 32)
+        for (int c = 0; c < 5; ++c) acc[c] += part[(size_t)b * 5 + c];
+    if ((terms & NB_TERM_PME) && S.pme && pme_blk_off)
+        for (int b = pme_blk_off[s] + lane; b < pme_blk_off[s + 1]; b += 32) acc[5] += e_pme_blk[b];
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    if (lane == 0) {
         bool coul = (terms & NB_TERM_COUL) != 0;
         double* o = dst + (size_t)s * NB_NE;
-        o[NB_E_LJ] = (terms & NB_TERM_LJ) ? lj : 0.0;
-        o[NB_E_DIR] = coul ? dir : 0.0;
-        o[NB_E_EXCL] = coul ? ex : 0.0;
-        o[NB_E_SELF] = coul ? S.self_coef * q2 : 0.0;
-        o[NB_E_REC] = rec;
-        o[NB_E_KIN] = with_kin ? kin : 0.0;
+        o[NB_E_LJ] = (terms & NB_TERM_LJ) ? acc[0] : 0.0;
+        o[NB_E_DIR] = coul ? acc[1] : 0.0;
+        o[NB_E_EXCL] = coul ? acc[2] : 0.0;
+        o[NB_E_SELF] = coul ? S.self_coef * acc[3] : 0.0;
+        o[NB_E_REC] = acc[5];
+        o[NB_E_KIN] = with_kin ? acc[4] : 0.0;
     }
 }
 
@@ -301,7 +329,9 @@ __global__ void __launch_bounds__(kRedThreads) k_bwd_reduce_h(const SysDev* __re
 // ------------------------------------------------------------------ launchers
 
 void launch_reduce_energy(nb_handle* h, int terms, int with_kin, double* dst, cudaStream_t st) {
-    k_reduce_energy<<<h->n_sys, kRedThreads, 0, st>>>(h->sys, h->e_atom, h->xs, h->ke_atom, h->e_pme_blk,
+    k_reduce_part<<<h->n_red_blocks, kRedThreads, 0, st>>>(h->red_blk_sys, h->red_blk_off, h->sys, h->e_atom, h->xs,
+                                                          h->ke_atom, with_kin, h->red_part);
+    k_reduce_final<<<cdiv(h->n_sys, 8), 256, 0, st>>>(h->n_sys, h->sys, h->red_blk_off, h->red_part, h->e_pme_blk,
                                                       h->conv_blk_off, terms, with_kin, dst);
 }
 

@@ -31,10 +31,19 @@ __device__ __forceinline__ void pair_vec(const float4& a, const float4& b, int p
     }
 }
 
+// (sigma/r)^2 with sigma^2 carried as an FMA two-product hi + lo: every pair of two given
+// atom types would otherwise share the same rounding of sigma^2, a bias that the
+// 6th/12th powers amplify and that does not average out over the pairs.
+__device__ __forceinline__ float sig2_over_r2(float sig, float r2inv) {
+    float hi = sig * sig;
+    float lo = fmaf(sig, sig, -hi);
+    return fmaf(lo, r2inv, hi * r2inv);
+}
+
 // LJ per unit eps (u, f = -u'/r) with the optional switch; r2inv = 1/r^2.
 __device__ __forceinline__ void lj_unit(float sig, float r2inv, float rinv, float r2, const SysDev& S,
                                         float& u, float& f) {
-    float s2 = sig * sig * r2inv;
+    float s2 = sig2_over_r2(sig, r2inv);
     float s6 = s2 * s2 * s2;
     u = 4.f * (s6 * s6 - s6);
     f = 24.f * (2.f * s6 * s6 - s6) * r2inv;
@@ -88,11 +97,12 @@ __global__ void __launch_bounds__(256) k_pair(int N, int cap, const float4* __re
             float fr = 0.f;
             if (LJ) {
                 float2 pj = ps[j];
-                float eps = pi.y * pj.y;
+                float eps = pi.y * pj.y;                // eps_ij = eps + eps_lo exactly
+                float eps_lo = fmaf(pi.y, pj.y, -eps);
                 float u, f;
                 lj_unit(0.5f * (pi.x + pj.x), r2inv, rinv, r2, S, u, f);
-                elj = fmaf(eps, u, elj);
-                fr = eps * f;
+                elj = fmaf(eps, u, fmaf(eps_lo, u, elj));
+                fr = fmaf(eps_lo, f, eps * f);
             }
             if (COUL) {
                 float r = r2 * rinv;
@@ -196,7 +206,7 @@ __global__ void __launch_bounds__(256) k_vjp(int N, int cap, const float4* __res
                 float2 pj = ps[j];
                 float eps = pi.y * pj.y;
                 float sig = 0.5f * (pi.x + pj.x);
-                float s2 = sig * sig * r2inv;
+                float s2 = sig2_over_r2(sig, r2inv);
                 float s6 = s2 * s2 * s2, s12 = s6 * s6;
                 float u = 4.f * (s12 - s6);                       // per unit eps
                 float f = 24.f * (2.f * s12 - s6) * r2inv;
@@ -218,8 +228,9 @@ __global__ void __launch_bounds__(256) k_vjp(int N, int cap, const float4* __res
                         u *= sw;
                     }
                 }
-                elj = fmaf(eps, u, elj);
-                fr = eps * f;
+                float eps_lo = fmaf(pi.y, pj.y, -eps);
+                elj = fmaf(eps, u, fmaf(eps_lo, u, elj));
+                fr = fmaf(eps_lo, f, eps * f);
                 fpr = eps * fp;
                 ge = fmaf(pj.y * f, du, ge);
                 gs = fmaf(0.5f * eps * fs, du, gs);

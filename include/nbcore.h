@@ -256,6 +256,28 @@ nb_status nonbonded_force_vjp(nb_handle* h, const float* xq, const float* lam, f
                               float* gq, float* gsigma, float* gsqrt_eps, float* f_out,
                               void* stream);
 
+/*
+ * PME charge spreading without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- code whose device
+ * memory is owned by another allocator (a framework's memory pool, a fixed arena) and
+ * code that must not trigger the device-wide synchronisation an allocation can cause.
+ * Every handle-based call in this header needs nb_create, which allocates; this one needs
+ * no handle.  It computes the same mesh as pme_spread for one periodic system:
+ *   xq [n_atoms][4]   (device) positions and charges.
+ *   box[3] (host)     box edge lengths;  mesh[3] (host) K0, K1, K2, each >= 4.
+ *   grid              (device, caller-owned) float[K0*K1*K2], index ((k0*K1)+k1)*K2+k2.
+ * Its int64 accumulation mesh is a library-owned static device array of
+ * NB_STATIC_MESH_MAX points (8 MiB on every GPU that loads the library, held until the
+ * process exits); K0*K1*K2 > NB_STATIC_MESH_MAX returns NB_ERR_ARG.  The first call on a
+ * device looks the array's address up (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call clears the part of the array it uses and shares the array
+ * with every other call: calls whose executions overlap on the GPU (several streams, or
+ * several host threads) race and corrupt each other's result.
+ */
+#define NB_STATIC_MESH_MAX (1 << 20)
+nb_status pme_spread_static(const float* xq, int32_t n_atoms, const double* box, const int32_t* mesh,
+                            float* grid, void* stream);
+
 /* Cumulative number of neighbour-list rebuilds of a handle (synchronises `stream`). */
 int64_t nb_rebuild_count(nb_handle* h, void* stream);
 

@@ -11,6 +11,9 @@
 // cuFFT performs the 3-D transforms (one batched plan per distinct mesh shape).
 #include <math.h>
 
+#include <cmath>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace nb {
@@ -398,3 +401,108 @@ void launch_pme_gather_only(nb_handle* h, const float* phi, float* f_out, cudaSt
 }
 
 }  // namespace nb
+
+// ------------------------------------------------------------------------------
+// pme_spread_static: the charge spreading above for callers that cannot allocate
+// device memory.  Its int64 accumulation mesh is a file-scope device array of
+// NB_STATIC_MESH_MAX points that every GPU loading the library keeps until exit;
+// host code reaches it only through the address cudaGetSymbolAddress returns (in
+// host code the array's name is a stand-in, not a device address).
+
+namespace nb {
+namespace {
+
+static __device__ __align__(256) long long g_static_mesh[NB_STATIC_MESH_MAX];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_static_mu;
+long long* g_static_mesh_ptr[kMaxDevices] = {};
+
+// Device address of g_static_mesh on the current device, looked up once per device.
+cudaError_t static_mesh_address(long long** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_mesh_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_mesh);
+        if (e != cudaSuccess) return e;
+        g_static_mesh_ptr[dev] = static_cast<long long*>(p);
+    }
+    *out = g_static_mesh_ptr[dev];
+    return cudaSuccess;
+}
+
+// Same arithmetic as k_spread, reading caller-order positions and wrapping them itself.
+__global__ void k_spread_static(int N, const float4* __restrict__ xq, float L0, float L1, float L2, float iL0,
+                                float iL1, float iL2, int K0, int K1, int K2, float kh0, float kh1, float kh2,
+                                float kl0, float kl1, float kl2, long long* __restrict__ mesh, float gscale) {
+    int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = gt >> 4, sub = gt & 15;
+    if (i >= N) return;
+    float4 p = xq[i];
+    p.x = wrap1(p.x, L0, iL0);
+    p.y = wrap1(p.y, L1, iL1);
+    p.z = wrap1(p.z, L2, iL2);
+    int f0, f1, f2;
+    float t0, t1, t2;
+    frac_coord(p.x, K0, kh0, kl0, f0, t0);
+    frac_coord(p.y, K1, kh1, kl1, f1, t1);
+    frac_coord(p.z, K2, kh2, kl2, f2, t2);
+    float w0[4], w1[4], w2[4], d[4];
+    bspline4(t0, w0, d);
+    bspline4(t1, w1, d);
+    bspline4(t2, w2, d);
+    int a = sub >> 2, b = sub & 3;
+    int ix = wrapk(f0 - a, K0), iy = wrapk(f1 - b, K1);
+    float wxy = p.w * w0[a] * w1[b];
+    long long* g = mesh + ((long long)ix * K1 + iy) * K2;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        int iz = wrapk(f2 - c, K2);
+        red_add(g + iz, __float2ll_rn(wxy * w2[c] * gscale));
+    }
+}
+
+__global__ void k_static_mesh_out(long long n, const long long* __restrict__ mesh, float* __restrict__ grid,
+                                  double ginv) {
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    grid[k] = (float)((double)mesh[k] * ginv);
+}
+
+}  // namespace
+}  // namespace nb
+
+extern "C" nb_status pme_spread_static(const float* xq, int32_t n_atoms, const double* box, const int32_t* mesh,
+                                       float* grid, void* stream) {
+    using namespace nb;
+    if (!xq || !grid || !box || !mesh || n_atoms < 0) return NB_ERR_ARG;
+    long long npts = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (!(box[d] > 0.0) || !std::isfinite(box[d]) || mesh[d] < 4) return NB_ERR_ARG;
+        npts *= mesh[d];
+    }
+    if (npts > NB_STATIC_MESH_MAX) return NB_ERR_ARG;
+    long long* scratch = nullptr;
+    if (static_mesh_address(&scratch) != cudaSuccess) return NB_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the mesh keeps the previous call's sums: clear the part this call uses
+    if (cudaMemsetAsync(scratch, 0, sizeof(long long) * (size_t)npts, st) != cudaSuccess) return NB_ERR_CUDA;
+    float kh[3], kl[3];
+    for (int d = 0; d < 3; ++d) {
+        double r = mesh[d] / box[d];
+        kh[d] = (float)r;
+        kl[d] = (float)(r - (double)kh[d]);
+    }
+    const double gscale = std::ldexp(1.0, 32);
+    if (n_atoms > 0)
+        k_spread_static<<<cdiv((long long)n_atoms * 16, 256), 256, 0, st>>>(
+            n_atoms, reinterpret_cast<const float4*>(xq), (float)box[0], (float)box[1], (float)box[2],
+            (float)(1.0 / box[0]), (float)(1.0 / box[1]), (float)(1.0 / box[2]), mesh[0], mesh[1], mesh[2], kh[0],
+            kh[1], kh[2], kl[0], kl[1], kl[2], scratch, (float)gscale);
+    k_static_mesh_out<<<cdiv(npts, 256), 256, 0, st>>>(npts, scratch, grid, 1.0 / gscale);
+    return cudaGetLastError() == cudaSuccess ? NB_OK : NB_ERR_CUDA;
+}

@@ -33,7 +33,9 @@ EXPORTS = [
     "nb_status_str", "nb_create", "nb_destroy", "nb_num_atoms", "nb_num_systems", "nb_check",
     "nl_build", "nonbonded_forces", "pme_spread", "pme_gather", "md_step", "hmc_trajectory",
     "hmc_trajectory_backward", "nonbonded_force_vjp", "nb_rebuild_count", "nb_timing_enable", "nb_timing_read",
+    "pme_spread_static",
 ]
+STATIC_MESH_MAX = 1 << 20
 STAGES = ["check", "rebuild", "pair", "spread", "fft", "convolve", "gather", "update"]
 
 
@@ -119,6 +121,8 @@ def load():
     lib.nb_timing_enable.argtypes = [_vp, _i32]
     lib.nb_timing_read.restype = ctypes.c_int
     lib.nb_timing_read.argtypes = [_vp, _vp, _vp, _vp]
+    lib.pme_spread_static.restype = ctypes.c_int
+    lib.pme_spread_static.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp]
     _lib = lib
     return lib
 
@@ -153,6 +157,21 @@ def _ptr(t, dtype, shape=None, name="tensor", allow_none=False):
 def _ok(status, where):
     if status != 0:
         raise NbError(status, where)
+
+
+def pme_spread_static(xq, box, mesh, grid):
+    """PME charge spreading that allocates no device memory (pme_spread_static in
+    include/nbcore.h), for callers that cannot call cudaMalloc.  No handle is involved;
+    the library's static mesh is shared by all calls, so calls must not overlap on the GPU."""
+    torch = _torch()
+    lib = load()
+    n = int(xq.shape[0])
+    b = np.ascontiguousarray(np.broadcast_to(np.asarray(box, np.float64), (3,)))
+    m = np.ascontiguousarray(np.broadcast_to(np.asarray(mesh, np.int32), (3,)))
+    _ok(lib.pme_spread_static(_ptr(xq, torch.float32, (n, 4), "xq"), n, b.ctypes.data, m.ctypes.data,
+                              _ptr(grid, torch.float32, (int(np.prod(m.astype(np.int64))),), "grid"), _stream()),
+        "pme_spread_static")
+    return grid
 
 
 def ckpt_size(n_atoms, n_leap, ckpt_every):

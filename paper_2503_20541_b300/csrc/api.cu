@@ -271,6 +271,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         n_max = std::max(n_max, d.n_atoms);
         for (int k = 0; k < 3; ++k)
             if (std::floor(d.box[k] * 2.0 / rnl) < 5.0) fine_cells = false;
+        if (d.n_atoms / V * rnl * rnl * rnl < 64.0) fine_cells = false;
     }
     h->cell_div = o.cell_div ? o.cell_div : (fine_cells ? 2 : 1);
     h->lanes = o.lanes_per_atom ? o.lanes_per_atom
@@ -355,6 +356,16 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(dalloc(h, &h->cell_start, (size_t)h->n_cells + 1));
         NB_TRY(dalloc(h, &h->cell_cursor, h->n_cells));
         NB_TRY(dalloc(h, &h->scan_bsum, h->n_scan_blocks));
+        NB_TRY(dalloc(h, &h->cell_sys, h->n_cells));
+        {
+            std::vector<int> cs((size_t)h->n_cells);
+            for (int s = 0; s < n_systems; ++s) {
+                const SysDev& D = h->sys_h[s];
+                int nc = D.nc[0] * D.nc[1] * D.nc[2];
+                for (int k = 0; k < nc; ++k) cs[(size_t)D.cell_off + k] = s;
+            }
+            NB_TRY(cudaMemcpy(h->cell_sys, cs.data(), sizeof(int) * cs.size(), cudaMemcpyHostToDevice));
+        }
         NB_TRY(dalloc(h, &h->cellid, N));
         NB_TRY(dalloc(h, &h->perm_tmp, N));
         NB_TRY(dalloc(h, &h->perm, N));

@@ -93,6 +93,7 @@ struct nb_handle {
     int* cell_start = nullptr;   // [n_cells+1]
     int* cell_cursor = nullptr;  // [n_cells]
     int* scan_bsum = nullptr;    // [n_scan_blocks]
+    int* cell_sys = nullptr;     // [n_cells] system of each cell
     int* cellid = nullptr;       // [N] caller order
     int* perm_tmp = nullptr;     // [N]
     int* perm = nullptr;         // [N] slot -> caller

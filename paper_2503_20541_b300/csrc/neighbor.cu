@@ -10,6 +10,8 @@
 // The sort is a counting sort by (system, cell) followed by a rank sort inside
 // each cell on the caller index, so the slot order -- and with it the list and
 // every FP32 summation order downstream -- depends only on the positions.
+#include <climits>
+
 #include "common.cuh"
 
 namespace nb {
@@ -192,128 +194,220 @@ __global__ void k_cellsort(int n_cells, const int* __restrict__ start, const int
     }
 }
 
-// Cells visited along one axis: either every cell once (nc <= 2*st) or the
-// 2*st+1 cells around c, wrapped (periodic) or clipped (open).
-struct AxisRange {
-    int lo, hi;    // first range [lo, hi]
-    int lo2, hi2;  // second range (wrap), empty if lo2 > hi2
+// Verlet list build, one block per cell.  The block lists the cell's stencil as runs of
+// consecutive cells along x (each run is one contiguous slot range), stages the
+// candidates of all runs in shared memory (in tiles of kBuildTile when the stencil is
+// larger), and each warp serves atoms of the cell: per run it skips the run when the
+// run's (y, z) row is farther than r_nl from the atom, trims the run to the x cells that
+// can hold a partner, tests r^2 < r_nl^2 on 32 candidates at a time and appends the
+// accepted slots with a ballot.  The list order (run order, then slot order) depends only
+// on the positions.  Culling distances carry a relative margin of 1e-5 so that rounding
+// never drops a pair; the exact r^2 test decides.
+constexpr int kBuildThreads = 256;
+constexpr int kBuildWarps = kBuildThreads / 32;
+constexpr int kMaxRuns = 64;        // (2*2+1)^2 rows x 2 runs (periodic wrap) at most 50
+constexpr int kMaxRunCells = 6;     // cells per run: 2*stencil+1 <= 5, or nc <= 4
+constexpr int kBuildTile = 2304;    // candidates per shared-memory tile (36 KB of float4)
+
+struct BuildRun {
+    int slot0;                      // first slot of the run
+    int sm0;                        // offset of the run in the concatenated candidate array
+    int n;                          // candidates in the run
+    int yu, zu;                     // unwrapped row cell indices (INT_MIN: axis not culled)
+    int xu0, ncell;                 // unwrapped x index of the first cell (INT_MIN: no trim)
+    int cb[kMaxRunCells + 1];       // candidate offsets of the run's cells (cb[ncell] = n)
 };
 
-__device__ __forceinline__ AxisRange axis_range(int c, int nc, int st, int periodic) {
-    AxisRange r;
-    r.lo2 = 1;
-    r.hi2 = 0;
-    if (nc <= 2 * st) {
-        r.lo = 0;
-        r.hi = nc - 1;
-        return r;
-    }
-    int a = c - st, b = c + st;
-    if (!periodic) {
-        r.lo = max(a, 0);
-        r.hi = min(b, nc - 1);
-        return r;
-    }
-    if (a < 0) {
-        r.lo = 0; r.hi = b;
-        r.lo2 = a + nc; r.hi2 = nc - 1;
-    } else if (b >= nc) {
-        r.lo = a; r.hi = nc - 1;
-        r.lo2 = 0; r.hi2 = b - nc;
-    } else {
-        r.lo = a; r.hi = b;
-    }
-    return r;
+__device__ __forceinline__ float axis_gap(int cu, float u, float edge) {
+    if (cu == INT_MIN) return 0.f;
+    float lo = cu * edge, hi = (cu + 1) * edge;
+    return fmaxf(0.f, fmaxf(lo - u, u - hi));
 }
 
-// Full Verlet list: P lanes per atom split the candidates of each neighbour-cell
-// run; accepted candidates are compacted with a ballot, so the list order is the
-// fixed visiting order.
-template <int P>
-__global__ void __launch_bounds__(256) k_build(int N, int cap, const float4* __restrict__ xs,
-                                                const int* __restrict__ sid, const SysDev* __restrict__ sys,
-                                                const int* __restrict__ start, const int* __restrict__ perm,
-                                                const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
-                                                int* __restrict__ nbr, int* __restrict__ nbr_cnt,
-                                                unsigned* flags) {
+__global__ void __launch_bounds__(kBuildThreads) k_build_cell(
+    int n_cells, int cap, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
+    const int* __restrict__ start, const float4* __restrict__ xs, const int* __restrict__ perm,
+    const int* __restrict__ ex_off, const int* __restrict__ ex_idx, int* __restrict__ nbr,
+    int* __restrict__ nbr_cnt, unsigned* flags) {
     if (flags[0] == 0u) return;
-    int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    int i = gt / P, lane = gt % P;
-    bool valid = i < N;
-    int ii = valid ? i : N - 1;
-    int wl = threadIdx.x & 31;
-    int gbase = (wl / P) * P;
-    unsigned gmask = (P == 32) ? 0xffffffffu : (((1u << P) - 1u) << gbase);
-    const SysDev& S = sys[sid[ii]];
-    float4 xi = xs[ii];
-    int cx = cell_coord(xi.x, S.cell_scale[0], S.nc[0]);
-    int cy = cell_coord(xi.y, S.cell_scale[1], S.nc[1]);
-    int cz = cell_coord(xi.z, S.cell_scale[2], S.nc[2]);
-    int oi = perm[ii];
-    int e0 = ex_off[oi], ne = ex_off[oi + 1] - e0;
-    int exl[kMaxExclInline];
-#pragma unroll
-    for (int k = 0; k < kMaxExclInline; ++k) exl[k] = (k < ne) ? ex_idx[e0 + k] : -1;
-    const float L0 = S.L[0], L1 = S.L[1], L2 = S.L[2];
-    const float h0 = S.halfL[0], h1 = S.halfL[1], h2 = S.halfL[2];
+    const int c = blockIdx.x;
+    const int i0 = start[c], i1 = start[c + 1];
+    if (i0 == i1) return;
+    __shared__ BuildRun runs[kMaxRuns];
+    __shared__ int n_runs, n_cand;
+    __shared__ float4 cand[kBuildTile];
+    const SysDev& S = sys[cell_sys[c]];
+    const int nc0 = S.nc[0], nc1 = S.nc[1], nc2 = S.nc[2];
+    const int st = S.stencil;
     const int per = S.periodic;
-    const float rnl2 = S.rnl2;
-    int cnt = 0;
-    size_t rowbase = (size_t)ii * cap;
-    AxisRange rz = axis_range(cz, S.nc[2], S.stencil, per);
-    AxisRange ry = axis_range(cy, S.nc[1], S.stencil, per);
-    AxisRange rx = axis_range(cx, S.nc[0], S.stencil, per);
-    for (int zp = 0; zp < 2; ++zp) {
-        int zlo = zp ? rz.lo2 : rz.lo, zhi = zp ? rz.hi2 : rz.hi;
-        for (int z = zlo; z <= zhi; ++z) {
-            for (int yp = 0; yp < 2; ++yp) {
-                int ylo = yp ? ry.lo2 : ry.lo, yhi = yp ? ry.hi2 : ry.hi;
-                for (int y = ylo; y <= yhi; ++y) {
-                    int row = S.cell_off + (z * S.nc[1] + y) * S.nc[0];
-                    for (int xp = 0; xp < 2; ++xp) {
-                        int xlo = xp ? rx.lo2 : rx.lo, xhi = xp ? rx.hi2 : rx.hi;
-                        if (xlo > xhi) continue;
-                        int b = start[row + xlo], e = start[row + xhi + 1];
-                        for (int base = b; base < e; base += P) {
-                            int j = base + lane;
-                            bool acc = false;
-                            if (valid && j < e && j != ii) {
-                                float4 xj = xs[j];
-                                float dx, dy, dz;
-                                if (per) {
-                                    dx = mi_pair(xi.x, xj.x, L0, h0);
-                                    dy = mi_pair(xi.y, xj.y, L1, h1);
-                                    dz = mi_pair(xi.z, xj.z, L2, h2);
-                                } else {
-                                    dx = xi.x - xj.x;
-                                    dy = xi.y - xj.y;
-                                    dz = xi.z - xj.z;
-                                }
-                                float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                                acc = r2 < rnl2;
-                                if (acc && ne > 0) {
-                                    int oj = perm[j];
-#pragma unroll
-                                    for (int k = 0; k < kMaxExclInline; ++k) acc = acc && (exl[k] != oj);
-                                    for (int k = kMaxExclInline; k < ne; ++k) acc = acc && (ex_idx[e0 + k] != oj);
-                                }
-                            }
-                            unsigned bits = (__ballot_sync(gmask, acc) >> gbase);
-                            if (P < 32) bits &= (1u << P) - 1u;
-                            if (acc) {
-                                int pos = cnt + __popc(bits & ((1u << lane) - 1u));
-                                if (pos < cap) nbr[rowbase + pos] = j;
-                            }
-                            cnt += __popc(bits);
-                        }
-                    }
+    const int lc = c - S.cell_off;
+    const int cx = lc % nc0, cy = (lc / nc0) % nc1, cz = lc / (nc0 * nc1);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w == 0) {
+        // stencil runs of this cell: lane l handles row l (at most 25 rows), giving 0-2 runs
+        const bool xall = nc0 <= 2 * st, yall = nc1 <= 2 * st, zall = nc2 <= 2 * st;
+        const int nz = zall ? nc2 : 2 * st + 1, ny = yall ? nc1 : 2 * st + 1;
+        const int nrows = nz * ny;  // <= 32 for stencil <= 2
+        int nseg = 0, seg_lo[2] = {0, 0}, seg_hi[2] = {0, 0}, row = 0, yu = INT_MIN, zu = INT_MIN;
+        if (lane < nrows) {
+            int iz = lane / ny, iy = lane % ny;
+            bool ok = true;
+            int z = iz, y = iy;
+            if (!zall) {
+                zu = cz + iz - st;
+                if (!per && (zu < 0 || zu >= nc2)) ok = false;
+                z = zu < 0 ? zu + nc2 : (zu >= nc2 ? zu - nc2 : zu);
+            }
+            if (!yall) {
+                yu = cy + iy - st;
+                if (!per && (yu < 0 || yu >= nc1)) ok = false;
+                y = yu < 0 ? yu + nc1 : (yu >= nc1 ? yu - nc1 : yu);
+            }
+            if (ok) {
+                row = S.cell_off + (z * nc1 + y) * nc0;
+                int lo = xall ? 0 : cx - st, hi = xall ? nc0 - 1 : cx + st;
+                if (!xall && !per) {
+                    lo = max(lo, 0);
+                    hi = min(hi, nc0 - 1);
+                }
+                if (xall || (lo >= 0 && hi < nc0)) {
+                    seg_lo[0] = lo; seg_hi[0] = hi; nseg = 1;
+                } else if (lo < 0) {
+                    seg_lo[0] = lo; seg_hi[0] = -1; seg_lo[1] = 0; seg_hi[1] = hi; nseg = 2;
+                } else {
+                    seg_lo[0] = lo; seg_hi[0] = nc0 - 1; seg_lo[1] = nc0; seg_hi[1] = hi; nseg = 2;
                 }
             }
         }
+        // candidate counts of this lane's runs
+        int cbuf[2][kMaxRunCells + 1];
+        int slot0[2] = {0, 0}, nn[2] = {0, 0};
+        for (int g = 0; g < nseg; ++g) {
+            int x0 = seg_lo[g], x1 = seg_hi[g];
+            int xw0 = x0 < 0 ? x0 + nc0 : (x0 >= nc0 ? x0 - nc0 : x0);
+            slot0[g] = start[row + xw0];
+            cbuf[g][0] = 0;
+            for (int k = 0; k <= x1 - x0; ++k) cbuf[g][k + 1] = start[row + xw0 + k + 1] - slot0[g];
+            nn[g] = cbuf[g][x1 - x0 + 1];
+        }
+        // exclusive prefix over lanes of run counts and candidate counts
+        int myruns = nseg, mycand = nn[0] + nn[1];
+        int rpre = myruns, cpre = mycand;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int ra = __shfl_up_sync(0xffffffffu, rpre, o), ca = __shfl_up_sync(0xffffffffu, cpre, o);
+            if (lane >= o) {
+                rpre += ra;
+                cpre += ca;
+            }
+        }
+        int rtot = __shfl_sync(0xffffffffu, rpre, 31), ctot = __shfl_sync(0xffffffffu, cpre, 31);
+        rpre -= myruns;
+        cpre -= mycand;
+        for (int g = 0; g < nseg; ++g) {
+            int r = rpre + g;
+            if (r >= kMaxRuns) break;
+            BuildRun& R = runs[r];
+            int x0 = seg_lo[g], x1 = seg_hi[g];
+            R.slot0 = slot0[g];
+            R.sm0 = cpre + (g ? nn[0] : 0);
+            R.n = nn[g];
+            R.yu = yu;
+            R.zu = zu;
+            R.xu0 = xall ? INT_MIN : x0;
+            R.ncell = x1 - x0 + 1;
+            for (int k = 0; k <= x1 - x0 + 1; ++k) R.cb[k] = cbuf[g][k];
+        }
+        if (lane == 0) {
+            n_runs = min(rtot, kMaxRuns);
+            n_cand = ctot;
+            if (rtot > kMaxRuns) atomicOr(&flags[1], NB_DEVERR_LIST_OVERFLOW);
+        }
     }
-    if (valid && lane == 0) {
-        nbr_cnt[ii] = min(cnt, cap);
-        if (cnt > cap) atomicOr(&flags[1], NB_DEVERR_LIST_OVERFLOW);
+    __syncthreads();
+    const int nr = n_runs, total = n_cand;
+    const float L0 = S.L[0], L1 = S.L[1], L2 = S.L[2];
+    const float h0 = S.halfL[0], h1 = S.halfL[1], h2 = S.halfL[2];
+    const float ex = L0 / nc0, ey = L1 / nc1, ez = L2 / nc2;
+    const float rnl2 = S.rnl2;
+    const float rr2 = rnl2 * 1.00002f;
+    for (int t0 = 0; t0 < total; t0 += kBuildTile) {
+        const int t1 = min(total, t0 + kBuildTile);
+        // stage the candidates of [t0, t1)
+        for (int r = 0; r < nr; ++r) {
+            const BuildRun& R = runs[r];
+            int a = max(R.sm0, t0), b = min(R.sm0 + R.n, t1);
+            for (int k = a + threadIdx.x; k < b; k += kBuildThreads) cand[k - t0] = xs[R.slot0 + (k - R.sm0)];
+        }
+        __syncthreads();
+        for (int i = i0 + w; i < i1; i += kBuildWarps) {
+            const float4 xi = xs[i];
+            const int oi = perm[i];
+            const int e0 = ex_off[oi], ne = ex_off[oi + 1] - e0;
+            int cnt = (t0 == 0) ? 0 : nbr_cnt[i];
+            const size_t rowbase = (size_t)i * cap;
+            for (int r = 0; r < nr; ++r) {
+                const BuildRun& R = runs[r];
+                float dy = axis_gap(R.yu, xi.y, ey), dz = axis_gap(R.zu, xi.z, ez);
+                float d2 = fmaf(dz, dz, dy * dy);
+                if (d2 >= rr2) continue;
+                int a = 0, b = R.n;
+                if (R.xu0 != INT_MIN) {
+                    float hx = sqrtf(rr2 - d2) * 1.00001f;
+                    int klo = (int)floorf((xi.x - hx) * S.cell_scale[0]) - R.xu0;
+                    int khi = (int)floorf((xi.x + hx) * S.cell_scale[0]) - R.xu0;
+                    klo = max(klo, 0);
+                    khi = min(khi, R.ncell - 1);
+                    if (klo > khi) continue;
+                    a = R.cb[klo];
+                    b = R.cb[khi + 1];
+                }
+                a = max(a + R.sm0, t0);
+                b = min(b + R.sm0, t1);
+                for (int base = a; base < b; base += 32) {
+                    int k = base + lane;
+                    bool acc = false;
+                    int j = 0;
+                    if (k < b) {
+                        j = R.slot0 + (k - R.sm0);
+                        float4 xj = cand[k - t0];
+                        float dx, ddy, ddz;
+                        if (per) {
+                            dx = mi_pair(xi.x, xj.x, L0, h0);
+                            ddy = mi_pair(xi.y, xj.y, L1, h1);
+                            ddz = mi_pair(xi.z, xj.z, L2, h2);
+                        } else {
+                            dx = xi.x - xj.x;
+                            ddy = xi.y - xj.y;
+                            ddz = xi.z - xj.z;
+                        }
+                        float r2 = fmaf(ddz, ddz, fmaf(ddy, ddy, dx * dx));
+                        acc = (r2 < rnl2) && (j != i);
+                        if (acc && ne > 0) {
+                            int oj = perm[j];
+                            for (int q = 0; q < ne; ++q) acc = acc && (ex_idx[e0 + q] != oj);
+                        }
+                    }
+                    unsigned bits = __ballot_sync(0xffffffffu, acc);
+                    if (acc) {
+                        int pos = cnt + __popc(bits & ((1u << lane) - 1u));
+                        if (pos < cap) nbr[rowbase + pos] = j;
+                    }
+                    cnt += __popc(bits);
+                }
+            }
+            if (lane == 0) {
+                nbr_cnt[i] = cnt;  // running count; clamped after the last tile
+                if (t1 == total) {
+                    if (cnt > cap) {
+                        atomicOr(&flags[1], NB_DEVERR_LIST_OVERFLOW);
+                        nbr_cnt[i] = cap;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
     }
 }
 
@@ -346,14 +440,6 @@ void launch_load(nb_handle* h, const float4* xq, cudaStream_t st) {
     k_load<<<cdiv(N, 256), 256, 0, st>>>(N, xq, h->iperm, h->sid, h->sys, h->xref, h->xs, h->flags);
 }
 
-template <int P>
-static void launch_build_p(nb_handle* h, cudaStream_t st) {
-    int N = h->n_atoms;
-    k_build<P><<<cdiv((long long)N * P, 256), 256, 0, st>>>(N, h->cap, h->xs, h->sid, h->sys, h->cell_start,
-                                                            h->perm, h->ex_off, h->ex_idx, h->nbr, h->nbr_cnt,
-                                                            h->flags);
-}
-
 void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st) {
     int N = h->n_atoms;
     k_bin<<<cdiv(N, 256), 256, 0, st>>>(N, xq, h->sid, h->sys, h->cellid, h->cell_count, h->flags);
@@ -365,12 +451,9 @@ void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st) {
     k_cellsort<<<cdiv((long long)h->n_cells * 32, 256), 256, 0, st>>>(
         h->n_cells, h->cell_start, h->perm_tmp, xq, h->params, h->sid, h->sys, h->perm, h->iperm, h->xs, h->ps,
         h->xref, h->flags);
-    switch (h->lanes) {
-        case 4: launch_build_p<4>(h, st); break;
-        case 8: launch_build_p<8>(h, st); break;
-        case 16: launch_build_p<16>(h, st); break;
-        default: launch_build_p<32>(h, st); break;
-    }
+    k_build_cell<<<h->n_cells, kBuildThreads, 0, st>>>(h->n_cells, h->cap, h->cell_sys, h->sys, h->cell_start,
+                                                        h->xs, h->perm, h->ex_off, h->ex_idx, h->nbr, h->nbr_cnt,
+                                                        h->flags);
 }
 
 void launch_clear_rebuild(nb_handle* h, cudaStream_t st) { k_clear_rebuild<<<1, 1, 0, st>>>(h->flags); }

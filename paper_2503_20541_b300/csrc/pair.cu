@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) k_pair(int N, int cap, const float4* __re
             float rinv = rsqrtf(r2);
             float r2inv = __frcp_rn(r2);  // correctly rounded: LJ raises it to the 6th power
             float fr = 0.f;
-            if (LJ) {
+            if (LJ && pi.y != 0.f) {
                 float2 pj = ps[j];
                 float eps = pi.y * pj.y;                // eps_ij = eps + eps_lo exactly
                 float eps_lo = fmaf(pi.y, pj.y, -eps);
@@ -154,6 +154,157 @@ __global__ void __launch_bounds__(256) k_pair(int N, int cap, const float4* __re
         ffix[(size_t)N + ii] = to_fix(fy, scale, flags + 1);
         ffix[2 * (size_t)N + ii] = to_fix(fz, scale, flags + 1);
         e_atom[ii] = make_float4(0.5f * elj, 0.5f * edir, 0.5f * eex, 0.f);
+    }
+}
+
+// Warp-per-atom variant (used when 32 lanes serve one atom): the cut-off test runs on
+// 32 list entries at a time and the pairs inside r_c are appended, in list order, to a
+// per-warp queue in shared memory; the interaction math then runs on full warps of
+// queued pairs, so lanes are not idle on pairs between r_c and r_nl.  Atoms with
+// eps_i = 0 skip the LJ term as a whole warp.  The summation order is fixed by the list
+// and the ballot order, so results stay bitwise reproducible.
+constexpr int kQWarps = 8;
+
+template <bool LJ, bool COUL>
+__device__ __forceinline__ void pair_heavy(const float4& q, int j, const float4& xi, const float2& pi, bool do_lj,
+                                           const SysDev& S, const float4* __restrict__ xs,
+                                           const float2* __restrict__ ps, float qke, float alpha, float gau_c,
+                                           float& fx, float& fy, float& fz, float& elj, float& edir) {
+    float r2 = q.w;
+    float rinv = rsqrtf(r2);
+    float r2inv = __frcp_rn(r2);
+    float fr = 0.f;
+    if (LJ && do_lj) {
+        float2 pj = ps[j];
+        float eps = pi.y * pj.y;
+        float eps_lo = fmaf(pi.y, pj.y, -eps);
+        float u, f;
+        lj_unit(0.5f * (pi.x + pj.x), r2inv, rinv, r2, S, u, f);
+        elj = fmaf(eps, u, fmaf(eps_lo, u, elj));
+        fr = fmaf(eps_lo, f, eps * f);
+    }
+    if (COUL) {
+        float r = r2 * rinv;
+        float qq = qke * xs[j].w;
+        float ar = alpha * r;
+        float ec = erfcf(ar);
+        float gau = gau_c * __expf(-ar * ar);
+        edir = fmaf(qq * ec, rinv, edir);
+        fr = fmaf(qq * fmaf(ec, rinv, gau), r2inv, fr);
+    }
+    fx = fmaf(fr, q.x, fx);
+    fy = fmaf(fr, q.y, fy);
+    fz = fmaf(fr, q.z, fz);
+}
+
+template <bool LJ, bool COUL>
+__global__ void __launch_bounds__(kQWarps * 32) k_pair_q(int N, int cap, const float4* __restrict__ xs,
+                                                          const float2* __restrict__ ps, const int* __restrict__ sid,
+                                                          const SysDev* __restrict__ sys, const int* __restrict__ nbr,
+                                                          const int* __restrict__ cnt, const int* __restrict__ perm,
+                                                          const int* __restrict__ iperm,
+                                                          const int* __restrict__ ex_off,
+                                                          const int* __restrict__ ex_idx,
+                                                          long long* __restrict__ ffix,
+                                                          float4* __restrict__ e_atom, float scale, unsigned* flags) {
+    __shared__ float4 qd[kQWarps][64];
+    __shared__ int qj[kQWarps][64];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kQWarps + w;
+    if (i >= N) return;  // whole warp
+    const SysDev& S = sys[sid[i]];
+    const float4 xi = xs[i];
+    const float2 pi = ps[i];
+    const int c = cnt[i];
+    const int* row = nbr + (size_t)i * cap;
+    const float L0 = S.L[0], L1 = S.L[1], L2 = S.L[2];
+    const float h0 = S.halfL[0], h1 = S.halfL[1], h2 = S.halfL[2];
+    const int per = S.periodic;
+    const float rc2 = S.rc2;
+    const float qke = S.ke * xi.w;
+    const float alpha = S.alpha;
+    const float gau_c = 2.f * alpha * kInvSqrtPi;
+    const bool do_lj = pi.y != 0.f;
+    const unsigned lt = (1u << lane) - 1u;
+    float fx = 0.f, fy = 0.f, fz = 0.f, elj = 0.f, edir = 0.f, eex = 0.f;
+    int nq = 0;
+    // software pipeline: list indices are loaded two iterations ahead, positions one ahead
+    int jA = lane < c ? __ldg(row + lane) : 0;
+    int jB = 32 + lane < c ? __ldg(row + 32 + lane) : 0;
+    float4 xA = lane < c ? xs[jA] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int base = 0; base < c; base += 32) {
+        const int k = base + lane;
+        const int j = jA;
+        const float4 xj = xA;
+        if (k + 32 < c) xA = xs[jB];
+        jA = jB;
+        jB = (k + 64 < c) ? __ldg(row + k + 64) : 0;
+        bool acc = false;
+        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+        if (k < c) {
+            pair_vec(xi, xj, per, L0, L1, L2, h0, h1, h2, dx, dy, dz);
+            r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            acc = r2 < rc2;
+        }
+        unsigned bits = __ballot_sync(0xffffffffu, acc);
+        if (acc) {
+            int pos = nq + __popc(bits & lt);
+            qd[w][pos] = make_float4(dx, dy, dz, r2);
+            qj[w][pos] = j;
+        }
+        nq += __popc(bits);
+        if (nq >= 32) {
+            __syncwarp();
+            pair_heavy<LJ, COUL>(qd[w][lane], qj[w][lane], xi, pi, do_lj, S, xs, ps, qke, alpha, gau_c, fx, fy, fz,
+                                 elj, edir);
+            __syncwarp();
+            if (lane < nq - 32) {
+                qd[w][lane] = qd[w][lane + 32];
+                qj[w][lane] = qj[w][lane + 32];
+            }
+            nq -= 32;
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+    if (lane < nq)
+        pair_heavy<LJ, COUL>(qd[w][lane], qj[w][lane], xi, pi, do_lj, S, xs, ps, qke, alpha, gau_c, fx, fy, fz, elj,
+                             edir);
+    if (COUL && alpha > 0.f) {
+        int oi = perm[i];
+        int e0 = ex_off[oi];
+        int ne = ex_off[oi + 1] - e0;
+        for (int e = lane; e < ne; e += 32) {
+            int j = iperm[ex_idx[e0 + e]];
+            float4 xj = xs[j];
+            float dx, dy, dz;
+            pair_vec(xi, xj, per, L0, L1, L2, h0, h1, h2, dx, dy, dz);
+            float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            float rinv = rsqrtf(r2);
+            float r2inv = rinv * rinv;
+            float r = r2 * rinv;
+            float qq = qke * xj.w;
+            float ar = alpha * r;
+            float ef = erff(ar);
+            float gau = gau_c * __expf(-ar * ar);
+            eex = fmaf(-qq * ef, rinv, eex);
+            float fr = qq * (gau - ef * rinv) * r2inv;
+            fx = fmaf(fr, dx, fx);
+            fy = fmaf(fr, dy, fy);
+            fz = fmaf(fr, dz, fz);
+        }
+    }
+    fx = group_sum<32>(fx);
+    fy = group_sum<32>(fy);
+    fz = group_sum<32>(fz);
+    elj = group_sum<32>(elj);
+    edir = group_sum<32>(edir);
+    eex = group_sum<32>(eex);
+    if (lane == 0) {
+        ffix[i] = to_fix(fx, scale, flags + 1);
+        ffix[(size_t)N + i] = to_fix(fy, scale, flags + 1);
+        ffix[2 * (size_t)N + i] = to_fix(fz, scale, flags + 1);
+        e_atom[i] = make_float4(0.5f * elj, 0.5f * edir, 0.5f * eex, 0.f);
     }
 }
 
@@ -315,6 +466,12 @@ __global__ void __launch_bounds__(256) k_vjp(int N, int cap, const float4* __res
 template <int P, bool LJ, bool COUL>
 static void pair_p(nb_handle* h, cudaStream_t st) {
     int N = h->n_atoms;
+    if (P == 32) {
+        k_pair_q<LJ, COUL><<<cdiv(N, kQWarps), kQWarps * 32, 0, st>>>(
+            N, h->cap, h->xs, h->ps, h->sid, h->sys, h->nbr, h->nbr_cnt, h->perm, h->iperm, h->ex_off, h->ex_idx,
+            h->ffix, h->e_atom, h->fscale, h->flags);
+        return;
+    }
     k_pair<P, LJ, COUL><<<cdiv((long long)N * P, 256), 256, 0, st>>>(
         N, h->cap, h->xs, h->ps, h->sid, h->sys, h->nbr, h->nbr_cnt, h->perm, h->iperm, h->ex_off, h->ex_idx,
         h->ffix, h->e_atom, h->fscale, h->flags);

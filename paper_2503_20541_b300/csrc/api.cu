@@ -249,6 +249,8 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         ex_off_h[(size_t)i + 1] = ex_off_h[(size_t)i] + (int)v.size();
         ex_idx_h.insert(ex_idx_h.end(), v.begin(), v.end());
     }
+    int max_excl = 0;
+    for (long long i = 0; i < N; ++i) max_excl = std::max(max_excl, ex_off_h[(size_t)i + 1] - ex_off_h[(size_t)i]);
     ex.clear();
     ex.shrink_to_fit();
 
@@ -257,6 +259,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
     cudaGetDevice(&h->device);
     h->n_sys = n_systems;
     h->n_atoms = (int)N;
+    h->max_excl = max_excl;
     h->desc.assign(sys, sys + n_systems);
 
     // tuning defaults from the densest system

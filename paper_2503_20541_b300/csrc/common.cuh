@@ -21,7 +21,6 @@
 
 namespace nb {
 
-constexpr int kMaxExclInline = 8;  // exclusions per atom held in registers by the list build
 constexpr float kInvSqrtPi = 0.56418958354775628f;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = 1024 * kScanItems;  // cells per block of the multi-block scan
@@ -89,6 +88,7 @@ struct nb_handle {
     float2* params = nullptr;    // [N] caller order
     int* ex_off = nullptr;       // [N+1]
     int* ex_idx = nullptr;       // [M]
+    int max_excl = 0;            // most exclusions of one atom
     int* cell_count = nullptr;   // [n_cells]
     int* cell_start = nullptr;   // [n_cells+1]
     int* cell_cursor = nullptr;  // [n_cells]

@@ -194,39 +194,174 @@ __global__ void k_cellsort(int n_cells, const int* __restrict__ start, const int
     }
 }
 
-// Verlet list build, one block per cell.  The block lists the cell's stencil as runs of
-// consecutive cells along x (each run is one contiguous slot range), stages the
-// candidates of all runs in shared memory (in tiles of kBuildTile when the stencil is
-// larger), and each warp serves atoms of the cell: per run it skips the run when the
-// run's (y, z) row is farther than r_nl from the atom, trims the run to the x cells that
-// can hold a partner, tests r^2 < r_nl^2 on 32 candidates at a time and appends the
-// accepted slots with a ballot.  The list order (run order, then slot order) depends only
-// on the positions.  Culling distances carry a relative margin of 1e-5 so that rounding
-// never drops a pair; the exact r^2 test decides.
-constexpr int kBuildThreads = 256;
+// Verlet list build, one block per cell.  Warp 0 lists the cell's stencil as runs of
+// consecutive cells along x (each run is one contiguous slot range).  The block stages
+// the candidates of all runs in shared memory (in tiles of kBuildTile when the stencil
+// is larger) with the periodic image of each run already applied, so that a candidate
+// costs one shared-memory load however many atoms test it.  Each warp then holds up to
+// kBuildAtoms atoms of the cell in registers; lane l tests candidate l of each 32-wide
+// chunk against every held atom and the accepted slots are appended with a ballot.  The
+// list order (run order, then slot order) depends only on the positions, and each row is
+// written by one warp.
+//
+// Images.  Along an axis with a stencil (nc >= 2 st + 1) the unwrapped cell index of a
+// run fixes the image, which is the minimum image of every pair within r_nl.  A run
+// from below the first cell (index < 0) is moved down by L: xj - L is exact because
+// xj >= L/2.  A run from beyond the last cell (index >= nc) is met by moving the atom
+// down instead.  When nc >= 4 st that is done once for the block: the cell's atoms and
+// all candidates that did not wrap are moved down by L, every shift exact since all of
+// them lie above L/2; otherwise the shift rides with the candidate as a flag and the
+// atom side is chosen per pair.  Axes without a stencil (nc <= 2 st) fold per pair.  In
+// every case the difference is the correctly rounded minimum-image difference, the same
+// value the pair kernel computes.
+constexpr int kBuildThreads = 128;
 constexpr int kBuildWarps = kBuildThreads / 32;
 constexpr int kMaxRuns = 64;        // (2*2+1)^2 rows x 2 runs (periodic wrap) at most 50
-constexpr int kMaxRunCells = 6;     // cells per run: 2*stencil+1 <= 5, or nc <= 4
-constexpr int kBuildTile = 2304;    // candidates per shared-memory tile (36 KB of float4)
+constexpr int kBuildTile = 2560;    // candidates per shared-memory tile (40 KB of float4)
+constexpr int kBuildAtoms = 6;      // atoms per warp held in registers (plain images)
+constexpr int kBuildAtomsGen = 3;   // atoms per warp held in registers (per-pair images)
+constexpr float kFar = 1.0e18f;     // coordinate of the padding candidates
 
 struct BuildRun {
     int slot0;                      // first slot of the run
     int sm0;                        // offset of the run in the concatenated candidate array
     int n;                          // candidates in the run
-    int yu, zu;                     // unwrapped row cell indices (INT_MIN: axis not culled)
-    int xu0, ncell;                 // unwrapped x index of the first cell (INT_MIN: no trim)
-    int cb[kMaxRunCells + 1];       // candidate offsets of the run's cells (cb[ncell] = n)
+    int flags;                      // per-pair image: bit d = atom moves down by L on axis d
+    float s[3];                     // shift added to the candidates' coordinates
+    float pad;
 };
 
-__device__ __forceinline__ float axis_gap(int cu, float u, float edge) {
-    if (cu == INT_MIN) return 0.f;
-    float lo = cu * edge, hi = (cu + 1) * edge;
-    return fmaxf(0.f, fmaxf(lo - u, u - hi));
+// Image of a run along one axis with unwrapped cell index u.
+__device__ __forceinline__ void run_image(int u, int nc, bool fold, bool frame, float L, int bit,
+                                          float& s, int& fl) {
+    s = 0.f;
+    if (fold || u == INT_MIN) return;
+    if (u < 0) s = -L;
+    else if (u >= nc) {
+        if (!frame) fl |= bit;
+    } else if (frame) {
+        s = -L;
+    }
 }
 
+// Tests of one tile against the atoms [m0, m0 + na) of warp w (atom m of the warp is
+// slot i0 + w + kBuildWarps m).  GEN: per-pair image flags and folded axes.
+template <int E, bool GEN, int A>
+__device__ __forceinline__ void build_atoms(int i0, int w, int m0, int na, int t0, int nt, bool last,
+                                            const float4* cand, const unsigned char* cflag,
+                                            const float4* __restrict__ xs, const int* __restrict__ perm,
+                                            const int* __restrict__ iperm, const int* __restrict__ ex_off,
+                                            const int* __restrict__ ex_idx, int* __restrict__ nbr,
+                                            int* __restrict__ nbr_cnt, int cap, const float fs[3],
+                                            const float L[3], const float hL[3], const bool fold[3],
+                                            float rnl2, unsigned* flags) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    float ax[A], ay[A], az[A];
+    int ex[A][E + 1];
+    int cnt[A];
+    int* row[A];
+    unsigned slow = 0u;
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+        ax[a] = ay[a] = az[a] = 0.f;
+        cnt[a] = 0;
+        row[a] = nbr;
+#pragma unroll
+        for (int q = 0; q <= E; ++q) ex[a][q] = -1;
+        if (a < na) {
+            const int i = i0 + w + kBuildWarps * (m0 + a);
+            const float4 p = xs[i];
+            ax[a] = p.x + fs[0];
+            ay[a] = p.y + fs[1];
+            az[a] = p.z + fs[2];
+            ex[a][0] = i;  // the atom itself
+            if (E > 0) {
+                const int oi = perm[i];
+                const int e0 = ex_off[oi], ne = ex_off[oi + 1] - e0;
+#pragma unroll
+                for (int q = 0; q < E; ++q) ex[a][q + 1] = (q < ne) ? iperm[ex_idx[e0 + q]] : -1;
+                if (ne > E) slow |= 1u << a;
+            }
+            cnt[a] = (t0 == 0) ? 0 : nbr_cnt[i];
+            row[a] = nbr + (size_t)i * cap;
+        }
+    }
+    for (int base = 0; base < nt; base += 32) {
+        const float4 cj = cand[base + lane];
+        const int j = __float_as_int(cj.w);
+        int fl = 0;
+        if (GEN) fl = cflag[base + lane];
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+            if (a < na) {
+                float dx, dy, dz;
+                if (GEN) {
+                    dx = fold[0] ? mi_pair(ax[a], cj.x, L[0], hL[0]) : ((fl & 1) ? ax[a] - L[0] : ax[a]) - cj.x;
+                    dy = fold[1] ? mi_pair(ay[a], cj.y, L[1], hL[1]) : ((fl & 2) ? ay[a] - L[1] : ay[a]) - cj.y;
+                    dz = fold[2] ? mi_pair(az[a], cj.z, L[2], hL[2]) : ((fl & 4) ? az[a] - L[2] : az[a]) - cj.z;
+                } else {
+                    dx = ax[a] - cj.x;
+                    dy = ay[a] - cj.y;
+                    dz = az[a] - cj.z;
+                }
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                bool acc = r2 < rnl2;
+#pragma unroll
+                for (int q = 0; q <= E; ++q) acc = acc && (j != ex[a][q]);
+                if (E > 0 && ((slow >> a) & 1u) && acc) {
+                    const int i = i0 + w + kBuildWarps * (m0 + a);
+                    const int oi = perm[i];
+                    const int e0 = ex_off[oi], e1 = ex_off[oi + 1];
+                    for (int e = e0 + E; e < e1 && acc; ++e) acc = (iperm[ex_idx[e]] != j);
+                }
+                const unsigned bits = __ballot_sync(0xffffffffu, acc);
+                if (acc) {
+                    const int pos = cnt[a] + __popc(bits & lt);
+                    if (pos < cap) row[a][pos] = j;
+                }
+                cnt[a] += __popc(bits);
+            }
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+            if (a < na) {
+                const int i = i0 + w + kBuildWarps * (m0 + a);
+                int c = cnt[a];
+                if (last && c > cap) {
+                    atomicOr(&flags[1], NB_DEVERR_LIST_OVERFLOW);
+                    c = cap;
+                }
+                nbr_cnt[i] = c;  // running count between tiles, clamped after the last
+            }
+        }
+    }
+}
+
+template <int E, bool GEN, int A>
+__device__ __forceinline__ void build_tile(int i0, int n_i, int t0, int nt, bool last, const float4* cand,
+                                           const unsigned char* cflag, const float4* __restrict__ xs,
+                                           const int* __restrict__ perm, const int* __restrict__ iperm,
+                                           const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
+                                           int* __restrict__ nbr, int* __restrict__ nbr_cnt, int cap,
+                                           const float fs[3], const float L[3], const float hL[3],
+                                           const bool fold[3], float rnl2, unsigned* flags) {
+    const int w = threadIdx.x >> 5;
+    const int mw = n_i > w ? (n_i - w + kBuildWarps - 1) / kBuildWarps : 0;  // atoms of this warp
+    if (mw == 0) return;
+    const int ng = (mw + A - 1) / A;
+    const int gs = (mw + ng - 1) / ng;  // balanced group size <= A
+    for (int m0 = 0; m0 < mw; m0 += gs)
+        build_atoms<E, GEN, A>(i0, w, m0, min(gs, mw - m0), t0, nt, last, cand, cflag, xs, perm, iperm, ex_off,
+                               ex_idx, nbr, nbr_cnt, cap, fs, L, hL, fold, rnl2, flags);
+}
+
+template <int E>
 __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
-    int n_cells, int cap, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
-    const int* __restrict__ start, const float4* __restrict__ xs, const int* __restrict__ perm,
+    int cap, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys, const int* __restrict__ start,
+    const float4* __restrict__ xs, const int* __restrict__ perm, const int* __restrict__ iperm,
     const int* __restrict__ ex_off, const int* __restrict__ ex_idx, int* __restrict__ nbr,
     int* __restrict__ nbr_cnt, unsigned* flags) {
     if (flags[0] == 0u) return;
@@ -236,16 +371,26 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
     __shared__ BuildRun runs[kMaxRuns];
     __shared__ int n_runs, n_cand;
     __shared__ float4 cand[kBuildTile];
+    __shared__ unsigned char cflag[kBuildTile];
     const SysDev& S = sys[cell_sys[c]];
     const int nc0 = S.nc[0], nc1 = S.nc[1], nc2 = S.nc[2];
     const int st = S.stencil;
-    const int per = S.periodic;
+    const bool per = S.periodic != 0;
     const int lc = c - S.cell_off;
     const int cx = lc % nc0, cy = (lc / nc0) % nc1, cz = lc / (nc0 * nc1);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool xall = nc0 <= 2 * st, yall = nc1 <= 2 * st, zall = nc2 <= 2 * st;
+    const bool fold[3] = {per && xall, per && yall, per && zall};
+    const bool top[3] = {per && !xall && cx >= nc0 - st, per && !yall && cy >= nc1 - st,
+                         per && !zall && cz >= nc2 - st};
+    const bool gen = fold[0] || fold[1] || fold[2] || (top[0] && nc0 < 4 * st) || (top[1] && nc1 < 4 * st) ||
+                     (top[2] && nc2 < 4 * st);
+    const bool frame[3] = {!gen && top[0], !gen && top[1], !gen && top[2]};
+    const float L[3] = {S.L[0], S.L[1], S.L[2]};
+    const float hL[3] = {S.halfL[0], S.halfL[1], S.halfL[2]};
+    const float fs[3] = {frame[0] ? -L[0] : 0.f, frame[1] ? -L[1] : 0.f, frame[2] ? -L[2] : 0.f};
     if (w == 0) {
         // stencil runs of this cell: lane l handles row l (at most 25 rows), giving 0-2 runs
-        const bool xall = nc0 <= 2 * st, yall = nc1 <= 2 * st, zall = nc2 <= 2 * st;
         const int nz = zall ? nc2 : 2 * st + 1, ny = yall ? nc1 : 2 * st + 1;
         const int nrows = nz * ny;  // <= 32 for stencil <= 2
         int nseg = 0, seg_lo[2] = {0, 0}, seg_hi[2] = {0, 0}, row = 0, yu = INT_MIN, zu = INT_MIN;
@@ -279,16 +424,12 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
                 }
             }
         }
-        // candidate counts of this lane's runs
-        int cbuf[2][kMaxRunCells + 1];
         int slot0[2] = {0, 0}, nn[2] = {0, 0};
         for (int g = 0; g < nseg; ++g) {
             int x0 = seg_lo[g], x1 = seg_hi[g];
             int xw0 = x0 < 0 ? x0 + nc0 : (x0 >= nc0 ? x0 - nc0 : x0);
             slot0[g] = start[row + xw0];
-            cbuf[g][0] = 0;
-            for (int k = 0; k <= x1 - x0; ++k) cbuf[g][k + 1] = start[row + xw0 + k + 1] - slot0[g];
-            nn[g] = cbuf[g][x1 - x0 + 1];
+            nn[g] = start[row + xw0 + (x1 - x0) + 1] - slot0[g];
         }
         // exclusive prefix over lanes of run counts and candidate counts
         int myruns = nseg, mycand = nn[0] + nn[1];
@@ -307,16 +448,16 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
         for (int g = 0; g < nseg; ++g) {
             int r = rpre + g;
             if (r >= kMaxRuns) break;
-            BuildRun& R = runs[r];
-            int x0 = seg_lo[g], x1 = seg_hi[g];
+            BuildRun R;
             R.slot0 = slot0[g];
             R.sm0 = cpre + (g ? nn[0] : 0);
             R.n = nn[g];
-            R.yu = yu;
-            R.zu = zu;
-            R.xu0 = xall ? INT_MIN : x0;
-            R.ncell = x1 - x0 + 1;
-            for (int k = 0; k <= x1 - x0 + 1; ++k) R.cb[k] = cbuf[g][k];
+            R.flags = 0;
+            run_image(xall ? INT_MIN : seg_lo[g], nc0, fold[0], frame[0], L[0], 1, R.s[0], R.flags);
+            run_image(yu, nc1, fold[1], frame[1], L[1], 2, R.s[1], R.flags);
+            run_image(zu, nc2, fold[2], frame[2], L[2], 4, R.s[2], R.flags);
+            R.pad = 0.f;
+            runs[r] = R;
         }
         if (lane == 0) {
             n_runs = min(rtot, kMaxRuns);
@@ -326,88 +467,35 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
     }
     __syncthreads();
     const int nr = n_runs, total = n_cand;
-    const float L0 = S.L[0], L1 = S.L[1], L2 = S.L[2];
-    const float h0 = S.halfL[0], h1 = S.halfL[1], h2 = S.halfL[2];
-    const float ex = L0 / nc0, ey = L1 / nc1, ez = L2 / nc2;
     const float rnl2 = S.rnl2;
-    const float rr2 = rnl2 * 1.00002f;
     for (int t0 = 0; t0 < total; t0 += kBuildTile) {
         const int t1 = min(total, t0 + kBuildTile);
-        // stage the candidates of [t0, t1)
-        for (int r = 0; r < nr; ++r) {
-            const BuildRun& R = runs[r];
-            int a = max(R.sm0, t0), b = min(R.sm0 + R.n, t1);
-            for (int k = a + threadIdx.x; k < b; k += kBuildThreads) cand[k - t0] = xs[R.slot0 + (k - R.sm0)];
+        const int nt = t1 - t0;
+        // stage: warp w copies runs w, w + kBuildWarps, ...; lanes over the run's slots
+        for (int r = w; r < nr; r += kBuildWarps) {
+            const BuildRun R = runs[r];
+            const int a = max(R.sm0, t0), b = min(R.sm0 + R.n, t1);
+            for (int k = a + lane; k < b; k += 32) {
+                const int j = R.slot0 + (k - R.sm0);
+                const float4 p = xs[j];
+                cand[k - t0] = make_float4(p.x + R.s[0], p.y + R.s[1], p.z + R.s[2], __int_as_float(j));
+                cflag[k - t0] = (unsigned char)R.flags;
+            }
+        }
+        const int ntp = (nt + 31) & ~31;
+        for (int k = nt + threadIdx.x; k < ntp; k += kBuildThreads) {
+            cand[k] = make_float4(kFar, kFar, kFar, __int_as_float(-1));
+            cflag[k] = 0;
         }
         __syncthreads();
-        for (int i = i0 + w; i < i1; i += kBuildWarps) {
-            const float4 xi = xs[i];
-            const int oi = perm[i];
-            const int e0 = ex_off[oi], ne = ex_off[oi + 1] - e0;
-            int cnt = (t0 == 0) ? 0 : nbr_cnt[i];
-            const size_t rowbase = (size_t)i * cap;
-            for (int r = 0; r < nr; ++r) {
-                const BuildRun& R = runs[r];
-                float dy = axis_gap(R.yu, xi.y, ey), dz = axis_gap(R.zu, xi.z, ez);
-                float d2 = fmaf(dz, dz, dy * dy);
-                if (d2 >= rr2) continue;
-                int a = 0, b = R.n;
-                if (R.xu0 != INT_MIN) {
-                    float hx = sqrtf(rr2 - d2) * 1.00001f;
-                    int klo = (int)floorf((xi.x - hx) * S.cell_scale[0]) - R.xu0;
-                    int khi = (int)floorf((xi.x + hx) * S.cell_scale[0]) - R.xu0;
-                    klo = max(klo, 0);
-                    khi = min(khi, R.ncell - 1);
-                    if (klo > khi) continue;
-                    a = R.cb[klo];
-                    b = R.cb[khi + 1];
-                }
-                a = max(a + R.sm0, t0);
-                b = min(b + R.sm0, t1);
-                for (int base = a; base < b; base += 32) {
-                    int k = base + lane;
-                    bool acc = false;
-                    int j = 0;
-                    if (k < b) {
-                        j = R.slot0 + (k - R.sm0);
-                        float4 xj = cand[k - t0];
-                        float dx, ddy, ddz;
-                        if (per) {
-                            dx = mi_pair(xi.x, xj.x, L0, h0);
-                            ddy = mi_pair(xi.y, xj.y, L1, h1);
-                            ddz = mi_pair(xi.z, xj.z, L2, h2);
-                        } else {
-                            dx = xi.x - xj.x;
-                            ddy = xi.y - xj.y;
-                            ddz = xi.z - xj.z;
-                        }
-                        float r2 = fmaf(ddz, ddz, fmaf(ddy, ddy, dx * dx));
-                        acc = (r2 < rnl2) && (j != i);
-                        if (acc && ne > 0) {
-                            int oj = perm[j];
-                            for (int q = 0; q < ne; ++q) acc = acc && (ex_idx[e0 + q] != oj);
-                        }
-                    }
-                    unsigned bits = __ballot_sync(0xffffffffu, acc);
-                    if (acc) {
-                        int pos = cnt + __popc(bits & ((1u << lane) - 1u));
-                        if (pos < cap) nbr[rowbase + pos] = j;
-                    }
-                    cnt += __popc(bits);
-                }
-            }
-            if (lane == 0) {
-                nbr_cnt[i] = cnt;  // running count; clamped after the last tile
-                if (t1 == total) {
-                    if (cnt > cap) {
-                        atomicOr(&flags[1], NB_DEVERR_LIST_OVERFLOW);
-                        nbr_cnt[i] = cap;
-                    }
-                }
-            }
-            __syncwarp();
-        }
-        __syncthreads();
+        const bool last = t1 == total;
+        if (gen)
+            build_tile<E, true, kBuildAtomsGen>(i0, i1 - i0, t0, nt, last, cand, cflag, xs, perm, iperm, ex_off,
+                                                ex_idx, nbr, nbr_cnt, cap, fs, L, hL, fold, rnl2, flags);
+        else
+            build_tile<E, false, kBuildAtoms>(i0, i1 - i0, t0, nt, last, cand, cflag, xs, perm, iperm, ex_off,
+                                              ex_idx, nbr, nbr_cnt, cap, fs, L, hL, fold, rnl2, flags);
+        if (!last) __syncthreads();
     }
 }
 
@@ -451,9 +539,9 @@ void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st) {
     k_cellsort<<<cdiv((long long)h->n_cells * 32, 256), 256, 0, st>>>(
         h->n_cells, h->cell_start, h->perm_tmp, xq, h->params, h->sid, h->sys, h->perm, h->iperm, h->xs, h->ps,
         h->xref, h->flags);
-    k_build_cell<<<h->n_cells, kBuildThreads, 0, st>>>(h->n_cells, h->cap, h->cell_sys, h->sys, h->cell_start,
-                                                        h->xs, h->perm, h->ex_off, h->ex_idx, h->nbr, h->nbr_cnt,
-                                                        h->flags);
+    auto build = h->max_excl == 0 ? k_build_cell<0> : (h->max_excl <= 2 ? k_build_cell<2> : k_build_cell<4>);
+    build<<<h->n_cells, kBuildThreads, 0, st>>>(h->cap, h->cell_sys, h->sys, h->cell_start, h->xs, h->perm,
+                                                 h->iperm, h->ex_off, h->ex_idx, h->nbr, h->nbr_cnt, h->flags);
 }
 
 void launch_clear_rebuild(nb_handle* h, cudaStream_t st) { k_clear_rebuild<<<1, 1, 0, st>>>(h->flags); }

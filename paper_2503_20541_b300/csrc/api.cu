@@ -336,6 +336,9 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
             D.kl_lo[k] = (float)(kl - (double)D.kl_hi[k]);
         }
         D.stencil = h->cell_div;
+        if (D.periodic)
+            for (int k = 0; k < 3; ++k)
+                if (D.nc[k] < 4 * D.stencil) h->build_gen = 1;  // per-pair images in some cells
         D.self_coef = -d.ke * d.alpha / std::sqrt(3.14159265358979323846);
         cell_off += (int)ncells;
         atom_off += d.n_atoms;
@@ -378,6 +381,8 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(dalloc(h, &h->xref, N));
         NB_TRY(dalloc(h, &h->nbr, (size_t)N * h->cap));
         NB_TRY(dalloc(h, &h->nbr_cnt, N));
+        h->excl_w = h->max_excl == 0 ? 0 : (h->max_excl <= 2 ? 2 : 4);
+        if (h->excl_w) NB_TRY(dalloc(h, &h->ex_slot, (size_t)N * h->excl_w));
         NB_TRY(dalloc(h, &h->ffix, 3 * (size_t)N));
         NB_TRY(dalloc(h, &h->e_atom, N));
         NB_TRY(dalloc(h, &h->flags, 4));

@@ -89,6 +89,9 @@ struct nb_handle {
     int* ex_off = nullptr;       // [N+1]
     int* ex_idx = nullptr;       // [M]
     int max_excl = 0;            // most exclusions of one atom
+    int excl_w = 0;              // exclusion slots per atom in ex_slot (0, 2 or 4)
+    int* ex_slot = nullptr;      // [N * excl_w] slot order: partners' slots, -1 padded
+    int build_gen = 0;           // some system needs per-pair images in the list build
     int* cell_count = nullptr;   // [n_cells]
     int* cell_start = nullptr;   // [n_cells+1]
     int* cell_cursor = nullptr;  // [n_cells]

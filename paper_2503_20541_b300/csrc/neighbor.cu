@@ -194,6 +194,34 @@ __global__ void k_cellsort(int n_cells, const int* __restrict__ start, const int
     }
 }
 
+// Exclusion partners of every atom as slots (slot order, E per atom, -1 padded), written
+// once per rebuild so that the list build reads them with one load.
+__global__ void k_excl_slots(int N, int E, const int* __restrict__ perm, const int* __restrict__ iperm,
+                             const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
+                             int* __restrict__ ex_slot, const unsigned* flags) {
+    if (flags[0] == 0u) return;
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    int oi = perm[k];
+    int e0 = ex_off[oi], ne = ex_off[oi + 1] - e0;
+    for (int q = 0; q < E; ++q) ex_slot[(size_t)k * E + q] = q < ne ? iperm[ex_idx[e0 + q]] : -1;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Predicated store: keeps the list append inside one basic block (no branch around it),
+// so the tests of all held atoms interleave.  Nothing in the build reads nbr back.
+__device__ __forceinline__ void st_if(int* p, int v, bool ok) {
+    asm volatile(
+        "{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q st.global.u32 [%0], %1;\n}\n" ::"l"(p), "r"(v),
+        "r"((unsigned)ok));
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Verlet list build, one block per cell.  Warp 0 lists the cell's stencil as runs of
 // consecutive cells along x (each run is one contiguous slot range).  The block stages
 // the candidates of all runs in shared memory (in tiles of kBuildTile when the stencil
@@ -220,6 +248,7 @@ constexpr int kMaxRuns = 64;        // (2*2+1)^2 rows x 2 runs (periodic wrap) a
 constexpr int kBuildTile = 2560;    // candidates per shared-memory tile (40 KB of float4)
 constexpr int kBuildAtoms = 6;      // atoms per warp held in registers (plain images)
 constexpr int kBuildAtomsGen = 3;   // atoms per warp held in registers (per-pair images)
+static_assert(kBuildAtoms == 6, "build_tile dispatches group sizes 1..6");
 constexpr float kFar = 1.0e18f;     // coordinate of the padding candidates
 
 struct BuildRun {
@@ -245,14 +274,17 @@ __device__ __forceinline__ void run_image(int u, int nc, bool fold, bool frame, 
 }
 
 // Tests of one tile against the atoms [m0, m0 + na) of warp w (atom m of the warp is
-// slot i0 + w + kBuildWarps m).  GEN: per-pair image flags and folded axes.
-template <int E, bool GEN, int A>
+// slot i0 + w + kBuildWarps m), na <= A.  Held atoms beyond na sit far away so that the
+// unrolled tests run without branches.  GEN: per-pair image flags and folded axes.
+// SLOW: atoms may have more than E exclusions (the rest are read from the CSR).
+template <int E, bool SLOW, bool GEN, int A>
 __device__ __forceinline__ void build_atoms(int i0, int w, int m0, int na, int t0, int nt, bool last,
                                             const float4* cand, const unsigned char* cflag,
                                             const float4* __restrict__ xs, const int* __restrict__ perm,
                                             const int* __restrict__ iperm, const int* __restrict__ ex_off,
-                                            const int* __restrict__ ex_idx, int* __restrict__ nbr,
-                                            int* __restrict__ nbr_cnt, int cap, const float fs[3],
+                                            const int* __restrict__ ex_idx, const int* __restrict__ ex_slot,
+                                            int* __restrict__ nbr, int* __restrict__ nbr_cnt, int cap,
+                                            const float fs[3],
                                             const float L[3], const float hL[3], const bool fold[3],
                                             float rnl2, unsigned* flags) {
     const int lane = threadIdx.x & 31;
@@ -264,7 +296,7 @@ __device__ __forceinline__ void build_atoms(int i0, int w, int m0, int na, int t
     unsigned slow = 0u;
 #pragma unroll
     for (int a = 0; a < A; ++a) {
-        ax[a] = ay[a] = az[a] = 0.f;
+        ax[a] = ay[a] = az[a] = -kFar;
         cnt[a] = 0;
         row[a] = nbr;
 #pragma unroll
@@ -276,12 +308,11 @@ __device__ __forceinline__ void build_atoms(int i0, int w, int m0, int na, int t
             ay[a] = p.y + fs[1];
             az[a] = p.z + fs[2];
             ex[a][0] = i;  // the atom itself
-            if (E > 0) {
-                const int oi = perm[i];
-                const int e0 = ex_off[oi], ne = ex_off[oi + 1] - e0;
 #pragma unroll
-                for (int q = 0; q < E; ++q) ex[a][q + 1] = (q < ne) ? iperm[ex_idx[e0 + q]] : -1;
-                if (ne > E) slow |= 1u << a;
+            for (int q = 0; q < E; ++q) ex[a][q + 1] = ex_slot[(size_t)i * E + q];
+            if (SLOW) {
+                const int oi = perm[i];
+                if (ex_off[oi + 1] - ex_off[oi] > E) slow |= 1u << a;
             }
             cnt[a] = (t0 == 0) ? 0 : nbr_cnt[i];
             row[a] = nbr + (size_t)i * cap;
@@ -292,36 +323,36 @@ __device__ __forceinline__ void build_atoms(int i0, int w, int m0, int na, int t
         const int j = __float_as_int(cj.w);
         int fl = 0;
         if (GEN) fl = cflag[base + lane];
+        float r2[A];
 #pragma unroll
         for (int a = 0; a < A; ++a) {
-            if (a < na) {
-                float dx, dy, dz;
-                if (GEN) {
-                    dx = fold[0] ? mi_pair(ax[a], cj.x, L[0], hL[0]) : ((fl & 1) ? ax[a] - L[0] : ax[a]) - cj.x;
-                    dy = fold[1] ? mi_pair(ay[a], cj.y, L[1], hL[1]) : ((fl & 2) ? ay[a] - L[1] : ay[a]) - cj.y;
-                    dz = fold[2] ? mi_pair(az[a], cj.z, L[2], hL[2]) : ((fl & 4) ? az[a] - L[2] : az[a]) - cj.z;
-                } else {
-                    dx = ax[a] - cj.x;
-                    dy = ay[a] - cj.y;
-                    dz = az[a] - cj.z;
-                }
-                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                bool acc = r2 < rnl2;
-#pragma unroll
-                for (int q = 0; q <= E; ++q) acc = acc && (j != ex[a][q]);
-                if (E > 0 && ((slow >> a) & 1u) && acc) {
-                    const int i = i0 + w + kBuildWarps * (m0 + a);
-                    const int oi = perm[i];
-                    const int e0 = ex_off[oi], e1 = ex_off[oi + 1];
-                    for (int e = e0 + E; e < e1 && acc; ++e) acc = (iperm[ex_idx[e]] != j);
-                }
-                const unsigned bits = __ballot_sync(0xffffffffu, acc);
-                if (acc) {
-                    const int pos = cnt[a] + __popc(bits & lt);
-                    if (pos < cap) row[a][pos] = j;
-                }
-                cnt[a] += __popc(bits);
+            float dx, dy, dz;
+            if (GEN) {
+                dx = fold[0] ? mi_pair(ax[a], cj.x, L[0], hL[0]) : ((fl & 1) ? ax[a] - L[0] : ax[a]) - cj.x;
+                dy = fold[1] ? mi_pair(ay[a], cj.y, L[1], hL[1]) : ((fl & 2) ? ay[a] - L[1] : ay[a]) - cj.y;
+                dz = fold[2] ? mi_pair(az[a], cj.z, L[2], hL[2]) : ((fl & 4) ? az[a] - L[2] : az[a]) - cj.z;
+            } else {
+                dx = ax[a] - cj.x;
+                dy = ay[a] - cj.y;
+                dz = az[a] - cj.z;
             }
+            r2[a] = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        }
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+            bool acc = r2[a] < rnl2;
+#pragma unroll
+            for (int q = 0; q <= E; ++q) acc = acc && (j != ex[a][q]);
+            if (SLOW && ((slow >> a) & 1u) && acc) {
+                const int i = i0 + w + kBuildWarps * (m0 + a);
+                const int oi = perm[i];
+                const int e0 = ex_off[oi], e1 = ex_off[oi + 1];
+                for (int e = e0 + E; e < e1 && acc; ++e) acc = (iperm[ex_idx[e]] != j);
+            }
+            const unsigned bits = __ballot_sync(0xffffffffu, acc);
+            const int pos = cnt[a] + __popc(bits & lt);
+            st_if(row[a] + pos, j, acc && pos < cap);
+            cnt[a] += __popc(bits);
         }
     }
     if (lane == 0) {
@@ -340,38 +371,57 @@ __device__ __forceinline__ void build_atoms(int i0, int w, int m0, int na, int t
     }
 }
 
-template <int E, bool GEN, int A>
-__device__ __forceinline__ void build_tile(int i0, int n_i, int t0, int nt, bool last, const float4* cand,
+template <int E, bool SLOW>
+__device__ __forceinline__ void build_tile(int i0, int n_i, int t0, int nt, bool last, bool gen, const float4* cand,
                                            const unsigned char* cflag, const float4* __restrict__ xs,
                                            const int* __restrict__ perm, const int* __restrict__ iperm,
                                            const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
-                                           int* __restrict__ nbr, int* __restrict__ nbr_cnt, int cap,
-                                           const float fs[3], const float L[3], const float hL[3],
+                                           const int* __restrict__ ex_slot, int* __restrict__ nbr,
+                                           int* __restrict__ nbr_cnt, int cap, const float fs[3],
+                                           const float L[3], const float hL[3],
                                            const bool fold[3], float rnl2, unsigned* flags) {
     const int w = threadIdx.x >> 5;
     const int mw = n_i > w ? (n_i - w + kBuildWarps - 1) / kBuildWarps : 0;  // atoms of this warp
     if (mw == 0) return;
+    const int A = gen ? kBuildAtomsGen : kBuildAtoms;
     const int ng = (mw + A - 1) / A;
     const int gs = (mw + ng - 1) / ng;  // balanced group size <= A
-    for (int m0 = 0; m0 < mw; m0 += gs)
-        build_atoms<E, GEN, A>(i0, w, m0, min(gs, mw - m0), t0, nt, last, cand, cflag, xs, perm, iperm, ex_off,
-                               ex_idx, nbr, nbr_cnt, cap, fs, L, hL, fold, rnl2, flags);
+    for (int m0 = 0; m0 < mw; m0 += gs) {
+        const int na = min(gs, mw - m0);
+#define NB_BUILD_ARGS i0, w, m0, na, t0, nt, last, cand, cflag, xs, perm, iperm, ex_off, ex_idx, ex_slot, nbr, nbr_cnt, cap, \
+                      fs, L, hL, fold, rnl2, flags
+        if (gen) {
+            build_atoms<E, SLOW, true, kBuildAtomsGen>(NB_BUILD_ARGS);
+        } else {
+            switch (na) {  // warp-uniform: straight-line code for each group size
+                case 1: build_atoms<E, SLOW, false, 1>(NB_BUILD_ARGS); break;
+                case 2: build_atoms<E, SLOW, false, 2>(NB_BUILD_ARGS); break;
+                case 3: build_atoms<E, SLOW, false, 3>(NB_BUILD_ARGS); break;
+                case 4: build_atoms<E, SLOW, false, 4>(NB_BUILD_ARGS); break;
+                case 5: build_atoms<E, SLOW, false, 5>(NB_BUILD_ARGS); break;
+                default: build_atoms<E, SLOW, false, 6>(NB_BUILD_ARGS); break;
+            }
+        }
+#undef NB_BUILD_ARGS
+    }
 }
 
-template <int E>
+template <int E, bool SLOW>
 __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
     int cap, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys, const int* __restrict__ start,
     const float4* __restrict__ xs, const int* __restrict__ perm, const int* __restrict__ iperm,
-    const int* __restrict__ ex_off, const int* __restrict__ ex_idx, int* __restrict__ nbr,
-    int* __restrict__ nbr_cnt, unsigned* flags) {
+    const int* __restrict__ ex_off, const int* __restrict__ ex_idx, const int* __restrict__ ex_slot,
+    int* __restrict__ nbr, int* __restrict__ nbr_cnt, unsigned* flags) {
     if (flags[0] == 0u) return;
     const int c = blockIdx.x;
     const int i0 = start[c], i1 = start[c + 1];
     if (i0 == i1) return;
     __shared__ BuildRun runs[kMaxRuns];
     __shared__ int n_runs, n_cand;
-    __shared__ float4 cand[kBuildTile];
-    __shared__ unsigned char cflag[kBuildTile];
+    // dynamic: kBuildTile candidates, then kBuildTile image-flag bytes when any system can
+    // need per-pair images
+    extern __shared__ float4 cand[];
+    unsigned char* cflag = reinterpret_cast<unsigned char*>(cand + kBuildTile);
     const SysDev& S = sys[cell_sys[c]];
     const int nc0 = S.nc[0], nc1 = S.nc[1], nc2 = S.nc[2];
     const int st = S.stencil;
@@ -471,30 +521,34 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
     for (int t0 = 0; t0 < total; t0 += kBuildTile) {
         const int t1 = min(total, t0 + kBuildTile);
         const int nt = t1 - t0;
-        // stage: warp w copies runs w, w + kBuildWarps, ...; lanes over the run's slots
+        // stage: warp w copies runs w, w + kBuildWarps, ...; lanes over the run's slots.  The
+        // copies go straight to shared memory, all in flight at once; each thread then adds
+        // the run's image shift and the slot to the entries it copied itself.
+        for (int r = w; r < nr; r += kBuildWarps) {
+            const int sm0 = runs[r].sm0, slot0 = runs[r].slot0;
+            const int a = max(sm0, t0), b = min(sm0 + runs[r].n, t1);
+            for (int k = a + lane; k < b; k += 32) cp_async16(&cand[k - t0], &xs[slot0 + (k - sm0)]);
+        }
+        cp_async_wait_all();
         for (int r = w; r < nr; r += kBuildWarps) {
             const BuildRun R = runs[r];
             const int a = max(R.sm0, t0), b = min(R.sm0 + R.n, t1);
             for (int k = a + lane; k < b; k += 32) {
-                const int j = R.slot0 + (k - R.sm0);
-                const float4 p = xs[j];
-                cand[k - t0] = make_float4(p.x + R.s[0], p.y + R.s[1], p.z + R.s[2], __int_as_float(j));
-                cflag[k - t0] = (unsigned char)R.flags;
+                const float4 p = cand[k - t0];
+                cand[k - t0] = make_float4(p.x + R.s[0], p.y + R.s[1], p.z + R.s[2],
+                                           __int_as_float(R.slot0 + (k - R.sm0)));
+                if (gen) cflag[k - t0] = (unsigned char)R.flags;
             }
         }
         const int ntp = (nt + 31) & ~31;
         for (int k = nt + threadIdx.x; k < ntp; k += kBuildThreads) {
             cand[k] = make_float4(kFar, kFar, kFar, __int_as_float(-1));
-            cflag[k] = 0;
+            if (gen) cflag[k] = 0;
         }
         __syncthreads();
         const bool last = t1 == total;
-        if (gen)
-            build_tile<E, true, kBuildAtomsGen>(i0, i1 - i0, t0, nt, last, cand, cflag, xs, perm, iperm, ex_off,
-                                                ex_idx, nbr, nbr_cnt, cap, fs, L, hL, fold, rnl2, flags);
-        else
-            build_tile<E, false, kBuildAtoms>(i0, i1 - i0, t0, nt, last, cand, cflag, xs, perm, iperm, ex_off,
-                                              ex_idx, nbr, nbr_cnt, cap, fs, L, hL, fold, rnl2, flags);
+        build_tile<E, SLOW>(i0, i1 - i0, t0, nt, last, gen, cand, cflag, xs, perm, iperm, ex_off, ex_idx, ex_slot,
+                            nbr, nbr_cnt, cap, fs, L, hL, fold, rnl2, flags);
         if (!last) __syncthreads();
     }
 }
@@ -539,9 +593,17 @@ void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st) {
     k_cellsort<<<cdiv((long long)h->n_cells * 32, 256), 256, 0, st>>>(
         h->n_cells, h->cell_start, h->perm_tmp, xq, h->params, h->sid, h->sys, h->perm, h->iperm, h->xs, h->ps,
         h->xref, h->flags);
-    auto build = h->max_excl == 0 ? k_build_cell<0> : (h->max_excl <= 2 ? k_build_cell<2> : k_build_cell<4>);
-    build<<<h->n_cells, kBuildThreads, 0, st>>>(h->cap, h->cell_sys, h->sys, h->cell_start, h->xs, h->perm,
-                                                 h->iperm, h->ex_off, h->ex_idx, h->nbr, h->nbr_cnt, h->flags);
+    auto build = h->max_excl == 0   ? k_build_cell<0, false>
+                 : h->max_excl <= 2 ? k_build_cell<2, false>
+                 : h->max_excl <= 4 ? k_build_cell<4, false>
+                                    : k_build_cell<4, true>;
+    if (h->excl_w)
+        k_excl_slots<<<cdiv(N, 256), 256, 0, st>>>(N, h->excl_w, h->perm, h->iperm, h->ex_off, h->ex_idx,
+                                                   h->ex_slot, h->flags);
+    const size_t smem = kBuildTile * (sizeof(float4) + (h->build_gen ? 1 : 0));
+    build<<<h->n_cells, kBuildThreads, smem, st>>>(h->cap, h->cell_sys, h->sys, h->cell_start, h->xs, h->perm,
+                                                   h->iperm, h->ex_off, h->ex_idx, h->ex_slot, h->nbr, h->nbr_cnt,
+                                                   h->flags);
 }
 
 void launch_clear_rebuild(nb_handle* h, cudaStream_t st) { k_clear_rebuild<<<1, 1, 0, st>>>(h->flags); }

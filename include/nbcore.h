@@ -95,7 +95,8 @@ typedef struct {
 /* Tuning knobs; zero-initialise for defaults. */
 typedef struct {
     int32_t max_neighbors;   /* per-atom list capacity (full list); 0: from density */
-    int32_t lanes_per_atom;  /* 4, 8, 16 or 32 lanes per atom in list/pair kernels; 0: auto */
+    int32_t stencil_tile;    /* stencil candidates per shared-memory tile of the cell kernels
+                                (multiple of 64 in [256, 8192]); 0: auto from the density */
     int32_t cell_div;        /* cells of edge >= r_nl / cell_div, cell_div in {1, 2}; 0: auto */
     int32_t force_bits;      /* fixed-point fraction bits for forces; 0: 32 */
 } nb_options;

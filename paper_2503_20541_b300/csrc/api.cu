@@ -212,8 +212,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
     std::memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
     if (o.cell_div != 0 && o.cell_div != 1 && o.cell_div != 2) return NB_ERR_ARG;
-    if (o.lanes_per_atom != 0 && o.lanes_per_atom != 4 && o.lanes_per_atom != 8 && o.lanes_per_atom != 16 &&
-        o.lanes_per_atom != 32)
+    if (o.stencil_tile != 0 && (o.stencil_tile < 256 || o.stencil_tile > 8192 || o.stencil_tile % 64 != 0))
         return NB_ERR_ARG;
     if (o.max_neighbors < 0 || o.force_bits < 0 || o.force_bits > 48 || (o.force_bits > 0 && o.force_bits < 8))
         return NB_ERR_ARG;
@@ -277,8 +276,6 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         if (d.n_atoms / V * rnl * rnl * rnl < 64.0) fine_cells = false;
     }
     h->cell_div = o.cell_div ? o.cell_div : (fine_cells ? 2 : 1);
-    h->lanes = o.lanes_per_atom ? o.lanes_per_atom
-                                : (nb_max >= 256 ? 32 : nb_max >= 96 ? 16 : nb_max >= 40 ? 8 : 4);
     if (o.max_neighbors > 0) {
         h->cap = round_up(o.max_neighbors, 32);
     } else {
@@ -344,6 +341,22 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         atom_off += d.n_atoms;
     }
     h->n_cells = cell_off;
+    // shared-memory tile of the cell kernels: the densest system's expected stencil size
+    // with ~3 sigma of Poisson headroom; cells above it take several tiles
+    if (o.stencil_tile) {
+        h->tile = o.stencil_tile;
+    } else {
+        double cand = 0.0;
+        for (int s = 0; s < n_systems; ++s) {
+            const nb_system_desc& d = sys[s];
+            const SysDev& D = h->sys_h[s];
+            double v = d.n_atoms / (d.box[0] * d.box[1] * d.box[2]);
+            for (int k = 0; k < 3; ++k) v *= std::min(D.nc[k], 2 * D.stencil + 1) * d.box[k] / D.nc[k];
+            cand = std::max(cand, v);
+        }
+        long long t = round_up((long long)(cand + 3.0 * std::sqrt(cand) + 96.0), 64);
+        h->tile = (int)std::max(256LL, std::min(t, 4096LL));
+    }
     h->n_scan_blocks = cdiv(h->n_cells, kScanTile);
 
     cudaError_t e = cudaSuccess;
@@ -377,12 +390,17 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(dalloc(h, &h->perm, N));
         NB_TRY(dalloc(h, &h->iperm, N));
         NB_TRY(dalloc(h, &h->xs, N));
+        NB_TRY(dalloc(h, &h->xsb, N));
+        NB_TRY(dalloc(h, &h->pscr, 3 * (size_t)N));
         NB_TRY(dalloc(h, &h->ps, N));
         NB_TRY(dalloc(h, &h->xref, N));
         NB_TRY(dalloc(h, &h->nbr, (size_t)N * h->cap));
         NB_TRY(dalloc(h, &h->nbr_cnt, N));
         h->excl_w = h->max_excl == 0 ? 0 : (h->max_excl <= 2 ? 2 : 4);
-        if (h->excl_w) NB_TRY(dalloc(h, &h->ex_slot, (size_t)N * h->excl_w));
+        if (h->excl_w) {
+            NB_TRY(dalloc(h, &h->ex_slot, (size_t)N * h->excl_w));
+            NB_TRY(dalloc(h, &h->ex_cnt, N));
+        }
         NB_TRY(dalloc(h, &h->ffix, 3 * (size_t)N));
         NB_TRY(dalloc(h, &h->e_atom, N));
         NB_TRY(dalloc(h, &h->flags, 4));
@@ -436,6 +454,9 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(cudaMemset(h->ke_atom, 0, sizeof(float) * N));
         NB_TRY(cudaMemset(h->flags, 0, sizeof(unsigned) * 4));
         NB_TRY(cudaMemset(h->xs, 0, sizeof(float4) * N));
+        NB_TRY(cudaMemset(h->xsb, 0, sizeof(float4) * N));
+        NB_TRY(build_setup(h));
+        NB_TRY(pair_setup(h));
         NB_TRY(pme_setup(h));
         NB_TRY(cudaMemcpy(h->sys, h->sys_h.data(), sizeof(SysDev) * n_systems, cudaMemcpyHostToDevice));
         NB_TRY(cudaDeviceSynchronize());

@@ -5,8 +5,9 @@
 //                  (sigma, sqrt_eps), xref float4 (positions at the last list build),
 //                  exclusion CSR.
 //   slot order   : atoms sorted by (system, cell, caller index) after each rebuild;
-//                  xs float4 (wrapped x,y,z,q), ps float2, the full neighbour list
-//                  nbr[k*cap + n] (int32 slots) with counts, fixed-point forces
+//                  xs float4 (x,y,z,q in the frame of the last build), ps float2, the
+//                  full neighbour list nbr[k*cap + n] (uint16 indices into the stencil
+//                  of k's cell) with counts, fixed-point forces
 //                  ffix[d*N + k] (int64, 2^force_bits per unit), per-atom half
 //                  energies e_atom float4.
 //   System s owns the same index range [atom_off, atom_off + n) in both orders.
@@ -67,7 +68,6 @@ struct nb_handle {
     int n_sys = 0;
     int n_atoms = 0;
     int cap = 0;        // per-atom neighbour capacity (full list)
-    int lanes = 32;     // lanes per atom in list build / pair kernels
     int cell_div = 1;
     int force_bits = 32;
     float fscale = 4294967296.0f, finv = 1.0f / 4294967296.0f;
@@ -91,6 +91,7 @@ struct nb_handle {
     int max_excl = 0;            // most exclusions of one atom
     int excl_w = 0;              // exclusion slots per atom in ex_slot (0, 2 or 4)
     int* ex_slot = nullptr;      // [N * excl_w] slot order: partners' slots, -1 padded
+    int* ex_cnt = nullptr;       // [N] slot order: number of exclusion partners
     int build_gen = 0;           // some system needs per-pair images in the list build
     int* cell_count = nullptr;   // [n_cells]
     int* cell_start = nullptr;   // [n_cells+1]
@@ -101,10 +102,13 @@ struct nb_handle {
     int* perm_tmp = nullptr;     // [N]
     int* perm = nullptr;         // [N] slot -> caller
     int* iperm = nullptr;        // [N] caller -> slot
-    float4* xs = nullptr;        // [N] slot
+    float4* xs = nullptr;        // [N] slot: positions in the frame of the last build
+    float4* xsb = nullptr;       // [N] slot: wrapped positions at the last build
     float2* ps = nullptr;        // [N] slot
     float4* xref = nullptr;      // [N] caller
-    int* nbr = nullptr;          // [N*cap]
+    unsigned short* nbr = nullptr;  // [N*cap] stencil indices of each atom's neighbours
+    int tile = 0;                // candidates per shared-memory tile of the cell kernels
+    float4* pscr = nullptr;      // [3N] partial sums of atoms whose stencil spans several tiles
     int* nbr_cnt = nullptr;      // [N]
     long long* ffix = nullptr;   // [3N] slot
     float4* e_atom = nullptr;    // [N] slot: half energies (E_lj, E_dir, E_excl, 0) of each atom
@@ -199,12 +203,14 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 // neighbor.cu
 void launch_load(nb_handle* h, const float4* xq, cudaStream_t st);
 void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st);
+cudaError_t build_setup(nb_handle* h);
 void launch_clear_rebuild(nb_handle* h, cudaStream_t st);
 void launch_export_pairs(nb_handle* h, int2* out, long long max_pairs, unsigned long long* counter,
                          cudaStream_t st);
 // pair.cu
 void launch_pair(nb_handle* h, int terms, cudaStream_t st);
 void launch_vjp(nb_handle* h, int terms, cudaStream_t st);
+cudaError_t pair_setup(nb_handle* h);
 // pme.cu
 cudaError_t pme_setup(nb_handle* h);
 int launch_pme(nb_handle* h, cudaStream_t st);  // spread + FFT + convolve + FFT + gather into ffix

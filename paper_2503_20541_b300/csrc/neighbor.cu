@@ -10,34 +10,42 @@
 // The sort is a counting sort by (system, cell) followed by a rank sort inside
 // each cell on the caller index, so the slot order -- and with it the list and
 // every FP32 summation order downstream -- depends only on the positions.
-#include <climits>
-
-#include "common.cuh"
+#include "cell.cuh"
 
 namespace nb {
 
+// Positions stay in the frame of the last build: slot k holds its wrapped build
+// position plus the minimum-image displacement since the build, never re-wrapped, so the
+// stencil images chosen at the build stay valid until the next one.
 __global__ void k_load(int N, const float4* __restrict__ xq, const int* __restrict__ iperm,
                        const int* __restrict__ sid, const SysDev* __restrict__ sys,
-                       const float4* __restrict__ xref, float4* __restrict__ xs, unsigned* flags) {
+                       const float4* __restrict__ xref, const float4* __restrict__ xsb, float4* __restrict__ xs,
+                       unsigned* flags) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool need = false;
     if (i < N) {
         float4 p = xq[i];
         const SysDev& S = sys[sid[i]];
+        const int k = iperm[i];
         float4 w = p;
         float4 r = xref[i];
         float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
         if (S.periodic) {
-            w.x = wrap1(p.x, S.L[0], S.invL[0]);
-            w.y = wrap1(p.y, S.L[1], S.invL[1]);
-            w.z = wrap1(p.z, S.L[2], S.invL[2]);
             dx = mi_any(dx, S.L[0], S.invL[0]);
             dy = mi_any(dy, S.L[1], S.invL[1]);
             dz = mi_any(dz, S.L[2], S.invL[2]);
         }
-        xs[iperm[i]] = w;
         float d2 = dx * dx + dy * dy + dz * dz;
         need = !(d2 <= S.disp2);  // NaN (first call, bad input) also requests a rebuild
+        if (S.periodic) {
+            // an atom that needs the rebuild is wrapped (the rebuild re-slots it anyway;
+            // calls that only spread or gather PME charges use it as it is)
+            const float4 b = xsb[k];
+            w = need ? make_float4(wrap1(p.x, S.L[0], S.invL[0]), wrap1(p.y, S.L[1], S.invL[1]),
+                                   wrap1(p.z, S.L[2], S.invL[2]), p.w)
+                     : make_float4(b.x + dx, b.y + dy, b.z + dz, p.w);
+        }
+        xs[k] = w;
     }
     if (__any_sync(0xffffffffu, need) && (threadIdx.x & 31) == 0) atomicOr(&flags[0], 1u);
 }
@@ -167,7 +175,8 @@ __global__ void k_cellsort(int n_cells, const int* __restrict__ start, const int
                            const float4* __restrict__ xq, const float2* __restrict__ params,
                            const int* __restrict__ sid, const SysDev* __restrict__ sys,
                            int* __restrict__ perm, int* __restrict__ iperm, float4* __restrict__ xs,
-                           float2* __restrict__ ps, float4* __restrict__ xref, const unsigned* flags) {
+                           float4* __restrict__ xsb, float2* __restrict__ ps, float4* __restrict__ xref,
+                           const unsigned* flags) {
     if (flags[0] == 0u) return;
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -190,109 +199,66 @@ __global__ void k_cellsort(int n_cells, const int* __restrict__ start, const int
             p.z = wrap1(p.z, S.L[2], S.invL[2]);
         }
         xs[slot] = p;
+        xsb[slot] = p;
         ps[slot] = params[i];
     }
 }
 
-// Exclusion partners of every atom as slots (slot order, E per atom, -1 padded), written
-// once per rebuild so that the list build reads them with one load.
+// Exclusion partners of every atom as slots (slot order, E per atom, -1 padded) and the
+// number of partners, written once per rebuild so that the list build and the pair
+// kernels read them with one load.
 __global__ void k_excl_slots(int N, int E, const int* __restrict__ perm, const int* __restrict__ iperm,
                              const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
-                             int* __restrict__ ex_slot, const unsigned* flags) {
+                             int* __restrict__ ex_slot, int* __restrict__ ex_cnt, const unsigned* flags) {
     if (flags[0] == 0u) return;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     int oi = perm[k];
     int e0 = ex_off[oi], ne = ex_off[oi + 1] - e0;
+    ex_cnt[k] = ne;
     for (int q = 0; q < E; ++q) ex_slot[(size_t)k * E + q] = q < ne ? iperm[ex_idx[e0 + q]] : -1;
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-
-// Predicated store: keeps the list append inside one basic block (no branch around it),
-// so the tests of all held atoms interleave.  Nothing in the build reads nbr back.
-__device__ __forceinline__ void st_if(int* p, int v, bool ok) {
+// Predicated 16-bit store: keeps the list append inside one basic block (no branch
+// around it), so the tests of all held atoms interleave.  Nothing in the build reads
+// the list back.
+__device__ __forceinline__ void st16_if(unsigned short* p, int v, bool ok) {
     asm volatile(
-        "{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q st.global.u32 [%0], %1;\n}\n" ::"l"(p), "r"(v),
+        "{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q st.global.u16 [%0], %1;\n}\n" ::"l"(p), "h"((unsigned short)v),
         "r"((unsigned)ok));
 }
 
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// Verlet list build, one block per cell.  Warp 0 lists the cell's stencil as runs of
-// consecutive cells along x (each run is one contiguous slot range).  The block stages
-// the candidates of all runs in shared memory (in tiles of kBuildTile when the stencil
-// is larger) with the periodic image of each run already applied, so that a candidate
-// costs one shared-memory load however many atoms test it.  Each warp then holds up to
-// kBuildAtoms atoms of the cell in registers; lane l tests candidate l of each 32-wide
-// chunk against every held atom and the accepted slots are appended with a ballot.  The
-// list order (run order, then slot order) depends only on the positions, and each row is
-// written by one warp.
-//
-// Images.  Along an axis with a stencil (nc >= 2 st + 1) the unwrapped cell index of a
-// run fixes the image, which is the minimum image of every pair within r_nl.  A run
-// from below the first cell (index < 0) is moved down by L: xj - L is exact because
-// xj >= L/2.  A run from beyond the last cell (index >= nc) is met by moving the atom
-// down instead.  When nc >= 4 st that is done once for the block: the cell's atoms and
-// all candidates that did not wrap are moved down by L, every shift exact since all of
-// them lie above L/2; otherwise the shift rides with the candidate as a flag and the
-// atom side is chosen per pair.  Axes without a stencil (nc <= 2 st) fold per pair.  In
-// every case the difference is the correctly rounded minimum-image difference, the same
-// value the pair kernel computes.
+// Verlet list build, one block per cell (the cell tile of cell.cuh).  The block stages
+// the candidates of the cell's stencil in shared memory (in tiles of `tile` when the
+// stencil is larger) with each run's image applied and the candidate's slot in .w.
+// Each warp then holds up to kBuildAtoms atoms of the cell in registers; lane l tests
+// candidate l of each 32-wide chunk against every held atom and the accepted candidates
+// are appended, as 16-bit stencil indices, with a ballot.  The list order is the stencil
+// order, which depends only on the positions, and each row is written by one warp.
 constexpr int kBuildThreads = 128;
 constexpr int kBuildWarps = kBuildThreads / 32;
-constexpr int kMaxRuns = 64;        // (2*2+1)^2 rows x 2 runs (periodic wrap) at most 50
-constexpr int kBuildTile = 2560;    // candidates per shared-memory tile (40 KB of float4)
 constexpr int kBuildAtoms = 6;      // atoms per warp held in registers (plain images)
 constexpr int kBuildAtomsGen = 3;   // atoms per warp held in registers (per-pair images)
 static_assert(kBuildAtoms == 6, "build_tile dispatches group sizes 1..6");
-constexpr float kFar = 1.0e18f;     // coordinate of the padding candidates
-
-struct BuildRun {
-    int slot0;                      // first slot of the run
-    int sm0;                        // offset of the run in the concatenated candidate array
-    int n;                          // candidates in the run
-    int flags;                      // per-pair image: bit d = atom moves down by L on axis d
-    float s[3];                     // shift added to the candidates' coordinates
-    float pad;
-};
-
-// Image of a run along one axis with unwrapped cell index u.
-__device__ __forceinline__ void run_image(int u, int nc, bool fold, bool frame, float L, int bit,
-                                          float& s, int& fl) {
-    s = 0.f;
-    if (fold || u == INT_MIN) return;
-    if (u < 0) s = -L;
-    else if (u >= nc) {
-        if (!frame) fl |= bit;
-    } else if (frame) {
-        s = -L;
-    }
-}
 
 // Tests of one tile against the atoms [m0, m0 + na) of warp w (atom m of the warp is
 // slot i0 + w + kBuildWarps m), na <= A.  Held atoms beyond na sit far away so that the
 // unrolled tests run without branches.  GEN: per-pair image flags and folded axes.
 // SLOW: atoms may have more than E exclusions (the rest are read from the CSR).
 template <int E, bool SLOW, bool GEN, int A>
-__device__ __forceinline__ void build_atoms(int i0, int w, int m0, int na, int t0, int nt, bool last,
+__device__ __forceinline__ void build_atoms(const CellCtx& C, int w, int m0, int na, int t0, int nt, bool last,
                                             const float4* cand, const unsigned char* cflag,
                                             const float4* __restrict__ xs, const int* __restrict__ perm,
                                             const int* __restrict__ iperm, const int* __restrict__ ex_off,
                                             const int* __restrict__ ex_idx, const int* __restrict__ ex_slot,
-                                            int* __restrict__ nbr, int* __restrict__ nbr_cnt, int cap,
-                                            const float fs[3],
-                                            const float L[3], const float hL[3], const bool fold[3],
+                                            unsigned short* __restrict__ nbr, int* __restrict__ nbr_cnt, int cap,
                                             float rnl2, unsigned* flags) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     float ax[A], ay[A], az[A];
     int ex[A][E + 1];
     int cnt[A];
-    int* row[A];
+    unsigned short* row[A];
     unsigned slow = 0u;
 #pragma unroll
     for (int a = 0; a < A; ++a) {
@@ -302,11 +268,11 @@ __device__ __forceinline__ void build_atoms(int i0, int w, int m0, int na, int t
 #pragma unroll
         for (int q = 0; q <= E; ++q) ex[a][q] = -1;
         if (a < na) {
-            const int i = i0 + w + kBuildWarps * (m0 + a);
+            const int i = C.i0 + w + kBuildWarps * (m0 + a);
             const float4 p = xs[i];
-            ax[a] = p.x + fs[0];
-            ay[a] = p.y + fs[1];
-            az[a] = p.z + fs[2];
+            ax[a] = p.x + C.fs[0];
+            ay[a] = p.y + C.fs[1];
+            az[a] = p.z + C.fs[2];
             ex[a][0] = i;  // the atom itself
 #pragma unroll
             for (int q = 0; q < E; ++q) ex[a][q + 1] = ex_slot[(size_t)i * E + q];
@@ -321,6 +287,7 @@ __device__ __forceinline__ void build_atoms(int i0, int w, int m0, int na, int t
     for (int base = 0; base < nt; base += 32) {
         const float4 cj = cand[base + lane];
         const int j = __float_as_int(cj.w);
+        const int li = t0 + base + lane;
         int fl = 0;
         if (GEN) fl = cflag[base + lane];
         float r2[A];
@@ -328,9 +295,9 @@ __device__ __forceinline__ void build_atoms(int i0, int w, int m0, int na, int t
         for (int a = 0; a < A; ++a) {
             float dx, dy, dz;
             if (GEN) {
-                dx = fold[0] ? mi_pair(ax[a], cj.x, L[0], hL[0]) : ((fl & 1) ? ax[a] - L[0] : ax[a]) - cj.x;
-                dy = fold[1] ? mi_pair(ay[a], cj.y, L[1], hL[1]) : ((fl & 2) ? ay[a] - L[1] : ay[a]) - cj.y;
-                dz = fold[2] ? mi_pair(az[a], cj.z, L[2], hL[2]) : ((fl & 4) ? az[a] - L[2] : az[a]) - cj.z;
+                dx = gen_diff(ax[a], cj.x, fl, 1, C.fold[0], C.L[0], C.hL[0]);
+                dy = gen_diff(ay[a], cj.y, fl, 2, C.fold[1], C.L[1], C.hL[1]);
+                dz = gen_diff(az[a], cj.z, fl, 4, C.fold[2], C.L[2], C.hL[2]);
             } else {
                 dx = ax[a] - cj.x;
                 dy = ay[a] - cj.y;
@@ -344,14 +311,14 @@ __device__ __forceinline__ void build_atoms(int i0, int w, int m0, int na, int t
 #pragma unroll
             for (int q = 0; q <= E; ++q) acc = acc && (j != ex[a][q]);
             if (SLOW && ((slow >> a) & 1u) && acc) {
-                const int i = i0 + w + kBuildWarps * (m0 + a);
+                const int i = C.i0 + w + kBuildWarps * (m0 + a);
                 const int oi = perm[i];
                 const int e0 = ex_off[oi], e1 = ex_off[oi + 1];
                 for (int e = e0 + E; e < e1 && acc; ++e) acc = (iperm[ex_idx[e]] != j);
             }
             const unsigned bits = __ballot_sync(0xffffffffu, acc);
             const int pos = cnt[a] + __popc(bits & lt);
-            st_if(row[a] + pos, j, acc && pos < cap);
+            st16_if(row[a] + pos, li, acc && pos < cap);
             cnt[a] += __popc(bits);
         }
     }
@@ -359,7 +326,7 @@ __device__ __forceinline__ void build_atoms(int i0, int w, int m0, int na, int t
 #pragma unroll
         for (int a = 0; a < A; ++a) {
             if (a < na) {
-                const int i = i0 + w + kBuildWarps * (m0 + a);
+                const int i = C.i0 + w + kBuildWarps * (m0 + a);
                 int c = cnt[a];
                 if (last && c > cap) {
                     atomicOr(&flags[1], NB_DEVERR_LIST_OVERFLOW);
@@ -372,25 +339,24 @@ __device__ __forceinline__ void build_atoms(int i0, int w, int m0, int na, int t
 }
 
 template <int E, bool SLOW>
-__device__ __forceinline__ void build_tile(int i0, int n_i, int t0, int nt, bool last, bool gen, const float4* cand,
+__device__ __forceinline__ void build_tile(const CellCtx& C, int t0, int nt, bool last, const float4* cand,
                                            const unsigned char* cflag, const float4* __restrict__ xs,
                                            const int* __restrict__ perm, const int* __restrict__ iperm,
                                            const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
-                                           const int* __restrict__ ex_slot, int* __restrict__ nbr,
-                                           int* __restrict__ nbr_cnt, int cap, const float fs[3],
-                                           const float L[3], const float hL[3],
-                                           const bool fold[3], float rnl2, unsigned* flags) {
+                                           const int* __restrict__ ex_slot, unsigned short* __restrict__ nbr,
+                                           int* __restrict__ nbr_cnt, int cap, float rnl2, unsigned* flags) {
     const int w = threadIdx.x >> 5;
+    const int n_i = C.i1 - C.i0;
     const int mw = n_i > w ? (n_i - w + kBuildWarps - 1) / kBuildWarps : 0;  // atoms of this warp
     if (mw == 0) return;
-    const int A = gen ? kBuildAtomsGen : kBuildAtoms;
+    const int A = C.gen ? kBuildAtomsGen : kBuildAtoms;
     const int ng = (mw + A - 1) / A;
     const int gs = (mw + ng - 1) / ng;  // balanced group size <= A
     for (int m0 = 0; m0 < mw; m0 += gs) {
         const int na = min(gs, mw - m0);
-#define NB_BUILD_ARGS i0, w, m0, na, t0, nt, last, cand, cflag, xs, perm, iperm, ex_off, ex_idx, ex_slot, nbr, nbr_cnt, cap, \
-                      fs, L, hL, fold, rnl2, flags
-        if (gen) {
+#define NB_BUILD_ARGS C, w, m0, na, t0, nt, last, cand, cflag, xs, perm, iperm, ex_off, ex_idx, ex_slot, nbr, nbr_cnt, \
+                      cap, rnl2, flags
+        if (C.gen) {
             build_atoms<E, SLOW, true, kBuildAtomsGen>(NB_BUILD_ARGS);
         } else {
             switch (na) {  // warp-uniform: straight-line code for each group size
@@ -408,118 +374,33 @@ __device__ __forceinline__ void build_tile(int i0, int n_i, int t0, int nt, bool
 
 template <int E, bool SLOW>
 __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
-    int cap, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys, const int* __restrict__ start,
-    const float4* __restrict__ xs, const int* __restrict__ perm, const int* __restrict__ iperm,
-    const int* __restrict__ ex_off, const int* __restrict__ ex_idx, const int* __restrict__ ex_slot,
-    int* __restrict__ nbr, int* __restrict__ nbr_cnt, unsigned* flags) {
+    int cap, int tile, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
+    const int* __restrict__ start, const float4* __restrict__ xs, const int* __restrict__ perm,
+    const int* __restrict__ iperm, const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
+    const int* __restrict__ ex_slot, unsigned short* __restrict__ nbr, int* __restrict__ nbr_cnt,
+    unsigned* flags) {
     if (flags[0] == 0u) return;
     const int c = blockIdx.x;
-    const int i0 = start[c], i1 = start[c + 1];
-    if (i0 == i1) return;
+    const SysDev& S = sys[cell_sys[c]];
+    const CellCtx C = cell_ctx(c, S, start);
+    if (C.i0 == C.i1) return;
     __shared__ BuildRun runs[kMaxRuns];
     __shared__ int n_runs, n_cand;
-    // dynamic: kBuildTile candidates, then kBuildTile image-flag bytes when any system can
-    // need per-pair images
+    // dynamic: `tile` candidates, then `tile` image-flag bytes when any system can need
+    // per-pair images
     extern __shared__ float4 cand[];
-    unsigned char* cflag = reinterpret_cast<unsigned char*>(cand + kBuildTile);
-    const SysDev& S = sys[cell_sys[c]];
-    const int nc0 = S.nc[0], nc1 = S.nc[1], nc2 = S.nc[2];
-    const int st = S.stencil;
-    const bool per = S.periodic != 0;
-    const int lc = c - S.cell_off;
-    const int cx = lc % nc0, cy = (lc / nc0) % nc1, cz = lc / (nc0 * nc1);
+    unsigned char* cflag = reinterpret_cast<unsigned char*>(cand + tile);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool xall = nc0 <= 2 * st, yall = nc1 <= 2 * st, zall = nc2 <= 2 * st;
-    const bool fold[3] = {per && xall, per && yall, per && zall};
-    const bool top[3] = {per && !xall && cx >= nc0 - st, per && !yall && cy >= nc1 - st,
-                         per && !zall && cz >= nc2 - st};
-    const bool gen = fold[0] || fold[1] || fold[2] || (top[0] && nc0 < 4 * st) || (top[1] && nc1 < 4 * st) ||
-                     (top[2] && nc2 < 4 * st);
-    const bool frame[3] = {!gen && top[0], !gen && top[1], !gen && top[2]};
-    const float L[3] = {S.L[0], S.L[1], S.L[2]};
-    const float hL[3] = {S.halfL[0], S.halfL[1], S.halfL[2]};
-    const float fs[3] = {frame[0] ? -L[0] : 0.f, frame[1] ? -L[1] : 0.f, frame[2] ? -L[2] : 0.f};
-    if (w == 0) {
-        // stencil runs of this cell: lane l handles row l (at most 25 rows), giving 0-2 runs
-        const int nz = zall ? nc2 : 2 * st + 1, ny = yall ? nc1 : 2 * st + 1;
-        const int nrows = nz * ny;  // <= 32 for stencil <= 2
-        int nseg = 0, seg_lo[2] = {0, 0}, seg_hi[2] = {0, 0}, row = 0, yu = INT_MIN, zu = INT_MIN;
-        if (lane < nrows) {
-            int iz = lane / ny, iy = lane % ny;
-            bool ok = true;
-            int z = iz, y = iy;
-            if (!zall) {
-                zu = cz + iz - st;
-                if (!per && (zu < 0 || zu >= nc2)) ok = false;
-                z = zu < 0 ? zu + nc2 : (zu >= nc2 ? zu - nc2 : zu);
-            }
-            if (!yall) {
-                yu = cy + iy - st;
-                if (!per && (yu < 0 || yu >= nc1)) ok = false;
-                y = yu < 0 ? yu + nc1 : (yu >= nc1 ? yu - nc1 : yu);
-            }
-            if (ok) {
-                row = S.cell_off + (z * nc1 + y) * nc0;
-                int lo = xall ? 0 : cx - st, hi = xall ? nc0 - 1 : cx + st;
-                if (!xall && !per) {
-                    lo = max(lo, 0);
-                    hi = min(hi, nc0 - 1);
-                }
-                if (xall || (lo >= 0 && hi < nc0)) {
-                    seg_lo[0] = lo; seg_hi[0] = hi; nseg = 1;
-                } else if (lo < 0) {
-                    seg_lo[0] = lo; seg_hi[0] = -1; seg_lo[1] = 0; seg_hi[1] = hi; nseg = 2;
-                } else {
-                    seg_lo[0] = lo; seg_hi[0] = nc0 - 1; seg_lo[1] = nc0; seg_hi[1] = hi; nseg = 2;
-                }
-            }
-        }
-        int slot0[2] = {0, 0}, nn[2] = {0, 0};
-        for (int g = 0; g < nseg; ++g) {
-            int x0 = seg_lo[g], x1 = seg_hi[g];
-            int xw0 = x0 < 0 ? x0 + nc0 : (x0 >= nc0 ? x0 - nc0 : x0);
-            slot0[g] = start[row + xw0];
-            nn[g] = start[row + xw0 + (x1 - x0) + 1] - slot0[g];
-        }
-        // exclusive prefix over lanes of run counts and candidate counts
-        int myruns = nseg, mycand = nn[0] + nn[1];
-        int rpre = myruns, cpre = mycand;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int ra = __shfl_up_sync(0xffffffffu, rpre, o), ca = __shfl_up_sync(0xffffffffu, cpre, o);
-            if (lane >= o) {
-                rpre += ra;
-                cpre += ca;
-            }
-        }
-        int rtot = __shfl_sync(0xffffffffu, rpre, 31), ctot = __shfl_sync(0xffffffffu, cpre, 31);
-        rpre -= myruns;
-        cpre -= mycand;
-        for (int g = 0; g < nseg; ++g) {
-            int r = rpre + g;
-            if (r >= kMaxRuns) break;
-            BuildRun R;
-            R.slot0 = slot0[g];
-            R.sm0 = cpre + (g ? nn[0] : 0);
-            R.n = nn[g];
-            R.flags = 0;
-            run_image(xall ? INT_MIN : seg_lo[g], nc0, fold[0], frame[0], L[0], 1, R.s[0], R.flags);
-            run_image(yu, nc1, fold[1], frame[1], L[1], 2, R.s[1], R.flags);
-            run_image(zu, nc2, fold[2], frame[2], L[2], 4, R.s[2], R.flags);
-            R.pad = 0.f;
-            runs[r] = R;
-        }
-        if (lane == 0) {
-            n_runs = min(rtot, kMaxRuns);
-            n_cand = ctot;
-            if (rtot > kMaxRuns) atomicOr(&flags[1], NB_DEVERR_LIST_OVERFLOW);
-        }
-    }
+    if (w == 0) cell_runs(C, S, start, runs, &n_runs, &n_cand, flags);
     __syncthreads();
     const int nr = n_runs, total = n_cand;
+    if (total > 65536) {  // stencil indices are 16-bit
+        if (threadIdx.x == 0) atomicOr(&flags[1], NB_DEVERR_LIST_OVERFLOW);
+        return;
+    }
     const float rnl2 = S.rnl2;
-    for (int t0 = 0; t0 < total; t0 += kBuildTile) {
-        const int t1 = min(total, t0 + kBuildTile);
+    for (int t0 = 0; t0 < total; t0 += tile) {
+        const int t1 = min(total, t0 + tile);
         const int nt = t1 - t0;
         // stage: warp w copies runs w, w + kBuildWarps, ...; lanes over the run's slots.  The
         // copies go straight to shared memory, all in flight at once; each thread then adds
@@ -537,18 +418,18 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
                 const float4 p = cand[k - t0];
                 cand[k - t0] = make_float4(p.x + R.s[0], p.y + R.s[1], p.z + R.s[2],
                                            __int_as_float(R.slot0 + (k - R.sm0)));
-                if (gen) cflag[k - t0] = (unsigned char)R.flags;
+                if (C.gen) cflag[k - t0] = (unsigned char)R.flags;
             }
         }
         const int ntp = (nt + 31) & ~31;
         for (int k = nt + threadIdx.x; k < ntp; k += kBuildThreads) {
             cand[k] = make_float4(kFar, kFar, kFar, __int_as_float(-1));
-            if (gen) cflag[k] = 0;
+            if (C.gen) cflag[k] = 0;
         }
         __syncthreads();
         const bool last = t1 == total;
-        build_tile<E, SLOW>(i0, i1 - i0, t0, nt, last, gen, cand, cflag, xs, perm, iperm, ex_off, ex_idx, ex_slot,
-                            nbr, nbr_cnt, cap, fs, L, hL, fold, rnl2, flags);
+        build_tile<E, SLOW>(C, t0, nt, last, cand, cflag, xs, perm, iperm, ex_off, ex_idx, ex_slot, nbr, nbr_cnt,
+                            cap, rnl2, flags);
         if (!last) __syncthreads();
     }
 }
@@ -561,26 +442,44 @@ __global__ void k_clear_rebuild(unsigned* flags) {
     }
 }
 
-__global__ void k_export_pairs(int N, int cap, const int* __restrict__ nbr, const int* __restrict__ cnt,
-                               const int* __restrict__ perm, int2* out, long long max_pairs,
-                               unsigned long long* counter) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    int oi = perm[k];
-    int c = cnt[k];
-    for (int n = 0; n < c; ++n) {
-        int oj = perm[nbr[(size_t)k * cap + n]];
-        if (oi < oj) {
-            unsigned long long pos = atomicAdd(counter, 1ull);
-            if (out && (long long)pos < max_pairs) out[pos] = make_int2(oi, oj);
+// Pairs of the list as caller indices (i < j), one block per cell: the stencil index of
+// each entry is mapped back to its slot through the cell's runs.
+__global__ void __launch_bounds__(128) k_export_pairs(const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
+                                                      const int* __restrict__ start, int cap,
+                                                      const unsigned short* __restrict__ nbr,
+                                                      const int* __restrict__ cnt, const int* __restrict__ perm,
+                                                      int2* out, long long max_pairs, unsigned long long* counter,
+                                                      unsigned* flags) {
+    const int c = blockIdx.x;
+    const SysDev& S = sys[cell_sys[c]];
+    const CellCtx C = cell_ctx(c, S, start);
+    if (C.i0 == C.i1) return;
+    __shared__ BuildRun runs[kMaxRuns];
+    __shared__ int n_runs, n_cand;
+    if (threadIdx.x < 32) cell_runs(C, S, start, runs, &n_runs, &n_cand, flags);
+    __syncthreads();
+    const int nr = n_runs;
+    for (int i = C.i0 + (threadIdx.x >> 5); i < C.i1; i += blockDim.x >> 5) {
+        const int oi = perm[i];
+        const int m = cnt[i];
+        for (int n = threadIdx.x & 31; n < m; n += 32) {
+            const int k = nbr[(size_t)i * cap + n];
+            const BuildRun& R = runs[run_of(runs, nr, k)];
+            const int oj = perm[R.slot0 + (k - R.sm0)];
+            if (oi < oj) {
+                unsigned long long pos = atomicAdd(counter, 1ull);
+                if (out && (long long)pos < max_pairs) out[pos] = make_int2(oi, oj);
+            }
         }
     }
 }
 
 void launch_load(nb_handle* h, const float4* xq, cudaStream_t st) {
     int N = h->n_atoms;
-    k_load<<<cdiv(N, 256), 256, 0, st>>>(N, xq, h->iperm, h->sid, h->sys, h->xref, h->xs, h->flags);
+    k_load<<<cdiv(N, 256), 256, 0, st>>>(N, xq, h->iperm, h->sid, h->sys, h->xref, h->xsb, h->xs, h->flags);
 }
+
+size_t build_smem(const nb_handle* h) { return (size_t)h->tile * (sizeof(float4) + (h->build_gen ? 1 : 0)); }
 
 void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st) {
     int N = h->n_atoms;
@@ -591,27 +490,41 @@ void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st) {
                                                 h->cell_cursor, h->flags);
     k_scatter<<<cdiv(N, 256), 256, 0, st>>>(N, h->cellid, h->cell_start, h->cell_cursor, h->perm_tmp, h->flags);
     k_cellsort<<<cdiv((long long)h->n_cells * 32, 256), 256, 0, st>>>(
-        h->n_cells, h->cell_start, h->perm_tmp, xq, h->params, h->sid, h->sys, h->perm, h->iperm, h->xs, h->ps,
-        h->xref, h->flags);
-    auto build = h->max_excl == 0   ? k_build_cell<0, false>
-                 : h->max_excl <= 2 ? k_build_cell<2, false>
-                 : h->max_excl <= 4 ? k_build_cell<4, false>
-                                    : k_build_cell<4, true>;
+        h->n_cells, h->cell_start, h->perm_tmp, xq, h->params, h->sid, h->sys, h->perm, h->iperm, h->xs, h->xsb,
+        h->ps, h->xref, h->flags);
     if (h->excl_w)
         k_excl_slots<<<cdiv(N, 256), 256, 0, st>>>(N, h->excl_w, h->perm, h->iperm, h->ex_off, h->ex_idx,
-                                                   h->ex_slot, h->flags);
-    const size_t smem = kBuildTile * (sizeof(float4) + (h->build_gen ? 1 : 0));
-    build<<<h->n_cells, kBuildThreads, smem, st>>>(h->cap, h->cell_sys, h->sys, h->cell_start, h->xs, h->perm,
-                                                   h->iperm, h->ex_off, h->ex_idx, h->ex_slot, h->nbr, h->nbr_cnt,
-                                                   h->flags);
+                                                   h->ex_slot, h->ex_cnt, h->flags);
+    auto build = h->excl_w == 0   ? k_build_cell<0, false>
+                 : h->excl_w == 2 ? k_build_cell<2, false>
+                 : h->max_excl <= 4 ? k_build_cell<4, false>
+                                    : k_build_cell<4, true>;
+    build<<<h->n_cells, kBuildThreads, build_smem(h), st>>>(h->cap, h->tile, h->cell_sys, h->sys, h->cell_start,
+                                                            h->xs, h->perm, h->iperm, h->ex_off, h->ex_idx,
+                                                            h->ex_slot, h->nbr, h->nbr_cnt, h->flags);
+}
+
+cudaError_t build_setup(nb_handle* h) {
+    const int smem = (int)build_smem(h);
+    cudaError_t e = cudaSuccess;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_build_cell<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_build_cell<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_build_cell<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_build_cell<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
+    return e;
 }
 
 void launch_clear_rebuild(nb_handle* h, cudaStream_t st) { k_clear_rebuild<<<1, 1, 0, st>>>(h->flags); }
 
 void launch_export_pairs(nb_handle* h, int2* out, long long max_pairs, unsigned long long* counter,
                          cudaStream_t st) {
-    int N = h->n_atoms;
-    k_export_pairs<<<cdiv(N, 128), 128, 0, st>>>(N, h->cap, h->nbr, h->nbr_cnt, h->perm, out, max_pairs, counter);
+    k_export_pairs<<<h->n_cells, 128, 0, st>>>(h->cell_sys, h->sys, h->cell_start, h->cap, h->nbr, h->nbr_cnt,
+                                               h->perm, out, max_pairs, counter, h->flags);
 }
 
 }  // namespace nb

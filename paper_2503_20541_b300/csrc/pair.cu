@@ -8,28 +8,18 @@
 // correction -ke q_i q_j erf(alpha r)/r (the reciprocal sum still contains the
 // pair).  A pair force is F_i = f(r) d with d = mi(x_i - x_j), f = -U'/r.
 //
-// Work decomposition: P lanes per atom i (P = 4..32) stride over i's full
-// neighbour list (both directions of every pair are listed), i's data stays in
-// registers, partial sums are reduced with warp shuffles in a fixed tree.  No
-// atomics: the force on i is written once, converted to int64 fixed point.
-// Every FP32 summation order is fixed by the list, so results are bitwise
-// reproducible.
-#include "common.cuh"
+// Work decomposition: one block per cell (the cell tile of cell.cuh) stages the
+// positions, charges and LJ parameters of the cell's stencil in shared memory with the
+// build's images applied; one warp per atom of the cell walks its full neighbour list
+// (both directions of every pair are listed; entries are 16-bit stencil indices), tests
+// r < r_c on 32 entries at a time and appends the pairs inside r_c to a per-warp queue,
+// and the interaction math runs on full warps of queued pairs.  i's data stays in
+// registers, partial sums are reduced with warp shuffles in a fixed tree.  No atomics:
+// the force on i is written once, converted to int64 fixed point.  Every FP32
+// summation order is fixed by the list, so results are bitwise reproducible.
+#include "cell.cuh"
 
 namespace nb {
-
-__device__ __forceinline__ void pair_vec(const float4& a, const float4& b, int per, float L0, float L1, float L2,
-                                         float h0, float h1, float h2, float& dx, float& dy, float& dz) {
-    if (per) {
-        dx = mi_pair(a.x, b.x, L0, h0);
-        dy = mi_pair(a.y, b.y, L1, h1);
-        dz = mi_pair(a.z, b.z, L2, h2);
-    } else {
-        dx = a.x - b.x;
-        dy = a.y - b.y;
-        dz = a.z - b.z;
-    }
-}
 
 // (sigma/r)^2 with sigma^2 carried as an FMA two-product hi + lo: every pair of two given
 // atom types would otherwise share the same rounding of sigma^2, a bias that the
@@ -60,207 +50,171 @@ __device__ __forceinline__ void lj_unit(float sig, float r2inv, float rinv, floa
     }
 }
 
-template <int P, bool LJ, bool COUL>
-__global__ void __launch_bounds__(256) k_pair(int N, int cap, const float4* __restrict__ xs,
-                                               const float2* __restrict__ ps, const int* __restrict__ sid,
-                                               const SysDev* __restrict__ sys, const int* __restrict__ nbr,
-                                               const int* __restrict__ cnt, const int* __restrict__ perm,
-                                               const int* __restrict__ iperm, const int* __restrict__ ex_off,
-                                               const int* __restrict__ ex_idx, long long* __restrict__ ffix,
-                                               float4* __restrict__ e_atom, float scale, unsigned* flags) {
-    int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    int i = gt / P, lane = gt % P;
-    bool valid = i < N;
-    int ii = valid ? i : N - 1;
-    const SysDev& S = sys[sid[ii]];
-    const float4 xi = xs[ii];
-    const float2 pi = ps[ii];
-    const int c = valid ? cnt[ii] : 0;
-    const int* row = nbr + (size_t)ii * cap;
-    const float L0 = S.L[0], L1 = S.L[1], L2 = S.L[2];
-    const float h0 = S.halfL[0], h1 = S.halfL[1], h2 = S.halfL[2];
-    const int per = S.periodic;
-    const float rc2 = S.rc2;
-    const float qke = S.ke * xi.w;
-    const float alpha = S.alpha;
-    const float gau_c = 2.f * alpha * kInvSqrtPi;
-    float fx = 0.f, fy = 0.f, fz = 0.f, elj = 0.f, edir = 0.f, eex = 0.f;
-    for (int k = lane; k < c; k += P) {
-        int j = __ldg(row + k);
-        float4 xj = xs[j];
-        float dx, dy, dz;
-        pair_vec(xi, xj, per, L0, L1, L2, h0, h1, h2, dx, dy, dz);
-        float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        if (r2 < rc2) {
-            float rinv = rsqrtf(r2);
-            float r2inv = __frcp_rn(r2);  // correctly rounded: LJ raises it to the 6th power
-            float fr = 0.f;
-            if (LJ && pi.y != 0.f) {
-                float2 pj = ps[j];
-                float eps = pi.y * pj.y;                // eps_ij = eps + eps_lo exactly
-                float eps_lo = fmaf(pi.y, pj.y, -eps);
-                float u, f;
-                lj_unit(0.5f * (pi.x + pj.x), r2inv, rinv, r2, S, u, f);
-                elj = fmaf(eps, u, fmaf(eps_lo, u, elj));
-                fr = fmaf(eps_lo, f, eps * f);
-            }
-            if (COUL) {
-                float r = r2 * rinv;
-                float qq = qke * xj.w;
-                float ar = alpha * r;
-                float ec = erfcf(ar);
-                float gau = gau_c * __expf(-ar * ar);
-                edir = fmaf(qq * ec, rinv, edir);
-                fr = fmaf(qq * fmaf(ec, rinv, gau), r2inv, fr);
-            }
-            fx = fmaf(fr, dx, fx);
-            fy = fmaf(fr, dy, fy);
-            fz = fmaf(fr, dz, fz);
+constexpr int kPairWarps = 8;
+constexpr int kPairThreads = kPairWarps * 32;
+constexpr int kVjpWarps = 16;
+constexpr int kVjpThreads = kVjpWarps * 32;
+constexpr int kQueue = 64;  // per-warp queue of pairs inside r_c
+
+// Exclusion partners of slot i: count and the slot of partner e (from the per-slot
+// table when it holds all of them, else from the CSR).
+struct ExclView {
+    int ew;  // table width (0: no exclusions in the handle)
+    const int* slot;
+    const int* cnt;
+    const int* perm;
+    const int* iperm;
+    const int* off;
+    const int* idx;
+    __device__ __forceinline__ int count(int i) const { return ew ? cnt[i] : 0; }
+    __device__ __forceinline__ int partner(int i, int e) const {
+        if (e < ew) return slot[(size_t)i * ew + e];
+        return iperm[idx[off[perm[i]] + e]];
+    }
+};
+
+// Stage the candidates of stencil tile [t0, t1): positions (image applied, q in .w), LJ
+// parameters, optionally cotangents, and per-pair image flags.
+__device__ __forceinline__ void stage_pair_tile(const CellCtx& C, const BuildRun* runs, int nr, int t0, int t1,
+                                                int nthreads, const float4* __restrict__ xs,
+                                                const float2* __restrict__ ps, const float4* __restrict__ lam,
+                                                float4* cand, float2* par, float4* lamc, unsigned char* cflag) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = nthreads >> 5;
+    for (int r = w; r < nr; r += nw) {
+        const int sm0 = runs[r].sm0, slot0 = runs[r].slot0;
+        const int a = max(sm0, t0), b = min(sm0 + runs[r].n, t1);
+        for (int k = a + lane; k < b; k += 32) {
+            const int j = slot0 + (k - sm0);
+            cp_async16(&cand[k - t0], &xs[j]);
+            cp_async8(&par[k - t0], &ps[j]);
+            if (lamc) cp_async16(&lamc[k - t0], &lam[j]);
         }
     }
-    if (COUL && alpha > 0.f) {
-        // exclusion correction for i's excluded partners (at any distance)
-        int oi = valid ? perm[ii] : 0;
-        int e0 = valid ? ex_off[oi] : 0;
-        int ne = valid ? ex_off[oi + 1] - e0 : 0;
-        for (int e = lane; e < ne; e += P) {
-            int j = iperm[ex_idx[e0 + e]];
-            float4 xj = xs[j];
-            float dx, dy, dz;
-            pair_vec(xi, xj, per, L0, L1, L2, h0, h1, h2, dx, dy, dz);
-            float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            float rinv = rsqrtf(r2);
-            float r2inv = rinv * rinv;
-            float r = r2 * rinv;
-            float qq = qke * xj.w;
-            float ar = alpha * r;
-            float ef = erff(ar);
-            float gau = gau_c * __expf(-ar * ar);
-            eex = fmaf(-qq * ef, rinv, eex);
-            float fr = qq * (gau - ef * rinv) * r2inv;
-            fx = fmaf(fr, dx, fx);
-            fy = fmaf(fr, dy, fy);
-            fz = fmaf(fr, dz, fz);
+    cp_async_wait_all();
+    for (int r = w; r < nr; r += nw) {
+        const BuildRun R = runs[r];
+        const int a = max(R.sm0, t0), b = min(R.sm0 + R.n, t1);
+        for (int k = a + lane; k < b; k += 32) {
+            const float4 p = cand[k - t0];
+            cand[k - t0] = make_float4(p.x + R.s[0], p.y + R.s[1], p.z + R.s[2], p.w);
+            if (C.gen) cflag[k - t0] = (unsigned char)R.flags;
         }
-    }
-    fx = group_sum<P>(fx);
-    fy = group_sum<P>(fy);
-    fz = group_sum<P>(fz);
-    elj = group_sum<P>(elj);
-    edir = group_sum<P>(edir);
-    eex = group_sum<P>(eex);
-    if (valid && lane == 0) {
-        ffix[ii] = to_fix(fx, scale, flags + 1);
-        ffix[(size_t)N + ii] = to_fix(fy, scale, flags + 1);
-        ffix[2 * (size_t)N + ii] = to_fix(fz, scale, flags + 1);
-        e_atom[ii] = make_float4(0.5f * elj, 0.5f * edir, 0.5f * eex, 0.f);
     }
 }
 
-// Warp-per-atom variant (used when 32 lanes serve one atom): the cut-off test runs on
-// 32 list entries at a time and the pairs inside r_c are appended, in list order, to a
-// per-warp queue in shared memory; the interaction math then runs on full warps of
-// queued pairs, so lanes are not idle on pairs between r_c and r_nl.  Atoms with
-// eps_i = 0 skip the LJ term as a whole warp.  The summation order is fixed by the list
-// and the ballot order, so results stay bitwise reproducible.
-constexpr int kQWarps = 8;
+// Difference x_i - x_j of atom i (frame-shifted coordinates a, raw coordinates xr) and
+// staged candidate cj.
+template <bool GEN>
+__device__ __forceinline__ void cell_diff(const CellCtx& C, float ax, float ay, float az, const float4& xr,
+                                          const float4& cj, int fl, float& dx, float& dy, float& dz) {
+    if (GEN) {
+        dx = gen_diff(xr.x, cj.x, fl, 1, C.fold[0], C.L[0], C.hL[0]);
+        dy = gen_diff(xr.y, cj.y, fl, 2, C.fold[1], C.L[1], C.hL[1]);
+        dz = gen_diff(xr.z, cj.z, fl, 4, C.fold[2], C.L[2], C.hL[2]);
+    } else {
+        dx = ax - cj.x;
+        dy = ay - cj.y;
+        dz = az - cj.z;
+    }
+}
 
+__device__ __forceinline__ void pair_vec(const float4& a, const float4& b, int per, const CellCtx& C, float& dx,
+                                         float& dy, float& dz) {
+    if (per) {
+        dx = mi_pair(a.x, b.x, C.L[0], C.hL[0]);
+        dy = mi_pair(a.y, b.y, C.L[1], C.hL[1]);
+        dz = mi_pair(a.z, b.z, C.L[2], C.hL[2]);
+    } else {
+        dx = a.x - b.x;
+        dy = a.y - b.y;
+        dz = a.z - b.z;
+    }
+}
+
+// One queued pair of the force kernel: (dx, dy, dz, r^2) and stencil index lq.
 template <bool LJ, bool COUL>
-__device__ __forceinline__ void pair_heavy(const float4& q, int j, const float4& xi, const float2& pi, bool do_lj,
-                                           const SysDev& S, const float4* __restrict__ xs,
-                                           const float2* __restrict__ ps, float qke, float alpha, float gau_c,
-                                           float& fx, float& fy, float& fz, float& elj, float& edir) {
-    float r2 = q.w;
-    float rinv = rsqrtf(r2);
-    float r2inv = __frcp_rn(r2);
+__device__ __forceinline__ void pair_heavy(const float4& q, int lq, const float2& pi, bool do_lj, const SysDev& S,
+                                           const float4* cand, const float2* par, float qke, float alpha,
+                                           float gau_c, float& fx, float& fy, float& fz, float& elj, float& edir) {
+    const float r2 = q.w;
+    const float rinv = rsqrtf(r2);
     float fr = 0.f;
     if (LJ && do_lj) {
-        float2 pj = ps[j];
-        float eps = pi.y * pj.y;
-        float eps_lo = fmaf(pi.y, pj.y, -eps);
+        const float2 pj = par[lq];
+        const float r2inv = __frcp_rn(r2);  // correctly rounded: LJ raises it to the 6th power
+        const float eps = pi.y * pj.y;      // eps_ij = eps + eps_lo exactly
+        const float eps_lo = fmaf(pi.y, pj.y, -eps);
         float u, f;
         lj_unit(0.5f * (pi.x + pj.x), r2inv, rinv, r2, S, u, f);
         elj = fmaf(eps, u, fmaf(eps_lo, u, elj));
         fr = fmaf(eps_lo, f, eps * f);
     }
     if (COUL) {
-        float r = r2 * rinv;
-        float qq = qke * xs[j].w;
-        float ar = alpha * r;
-        float ec = erfcf(ar);
-        float gau = gau_c * __expf(-ar * ar);
+        const float r = r2 * rinv;
+        const float qq = qke * cand[lq].w;
+        const float ar = alpha * r;
+        const float ec = erfcf(ar);
+        const float gau = gau_c * __expf(-ar * ar);
         edir = fmaf(qq * ec, rinv, edir);
-        fr = fmaf(qq * fmaf(ec, rinv, gau), r2inv, fr);
+        fr = fmaf(qq * fmaf(ec, rinv, gau), rinv * rinv, fr);
     }
     fx = fmaf(fr, q.x, fx);
     fy = fmaf(fr, q.y, fy);
     fz = fmaf(fr, q.z, fz);
 }
 
-template <bool LJ, bool COUL>
-__global__ void __launch_bounds__(kQWarps * 32) k_pair_q(int N, int cap, const float4* __restrict__ xs,
-                                                          const float2* __restrict__ ps, const int* __restrict__ sid,
-                                                          const SysDev* __restrict__ sys, const int* __restrict__ nbr,
-                                                          const int* __restrict__ cnt, const int* __restrict__ perm,
-                                                          const int* __restrict__ iperm,
-                                                          const int* __restrict__ ex_off,
-                                                          const int* __restrict__ ex_idx,
-                                                          long long* __restrict__ ffix,
-                                                          float4* __restrict__ e_atom, float scale, unsigned* flags) {
-    __shared__ float4 qd[kQWarps][64];
-    __shared__ int qj[kQWarps][64];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * kQWarps + w;
-    if (i >= N) return;  // whole warp
-    const SysDev& S = sys[sid[i]];
-    const float4 xi = xs[i];
+// Forces and half energies of atom i over stencil tile [t0, t1) (one warp).
+template <bool LJ, bool COUL, bool GEN>
+__device__ __forceinline__ void pair_atom(const CellCtx& C, const SysDev& S, int N, int i, int t0, int t1, bool multi,
+                                          bool last, const float4* cand, const float2* par, const unsigned char* cflag,
+                                          float4* qd, int* qj, const float4* __restrict__ xs,
+                                          const float2* __restrict__ ps, const unsigned short* __restrict__ nbr,
+                                          const int* __restrict__ cnt, int cap, const ExclView& X,
+                                          long long* __restrict__ ffix, float4* __restrict__ e_atom,
+                                          float4* __restrict__ pscr, float scale, unsigned* flags) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const float4 xr = xs[i];
+    const float ax = xr.x + C.fs[0], ay = xr.y + C.fs[1], az = xr.z + C.fs[2];
     const float2 pi = ps[i];
     const int c = cnt[i];
-    const int* row = nbr + (size_t)i * cap;
-    const float L0 = S.L[0], L1 = S.L[1], L2 = S.L[2];
-    const float h0 = S.halfL[0], h1 = S.halfL[1], h2 = S.halfL[2];
-    const int per = S.periodic;
+    const unsigned short* row = nbr + (size_t)i * cap;
     const float rc2 = S.rc2;
-    const float qke = S.ke * xi.w;
+    const float qke = S.ke * xr.w;
     const float alpha = S.alpha;
     const float gau_c = 2.f * alpha * kInvSqrtPi;
     const bool do_lj = pi.y != 0.f;
-    const unsigned lt = (1u << lane) - 1u;
     float fx = 0.f, fy = 0.f, fz = 0.f, elj = 0.f, edir = 0.f, eex = 0.f;
     int nq = 0;
-    // software pipeline: list indices are loaded two iterations ahead, positions one ahead
-    int jA = lane < c ? __ldg(row + lane) : 0;
-    int jB = 32 + lane < c ? __ldg(row + 32 + lane) : 0;
-    float4 xA = lane < c ? xs[jA] : make_float4(0.f, 0.f, 0.f, 0.f);
+    int kn = lane < c ? row[lane] : 0;  // list entries are loaded one round ahead
     for (int base = 0; base < c; base += 32) {
         const int k = base + lane;
-        const int j = jA;
-        const float4 xj = xA;
-        if (k + 32 < c) xA = xs[jB];
-        jA = jB;
-        jB = (k + 64 < c) ? __ldg(row + k + 64) : 0;
+        const int li = kn;
+        kn = (k + 32 < c) ? row[k + 32] : 0;
+        const bool in = k < c && (!multi || (li >= t0 && li < t1));
         bool acc = false;
         float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
-        if (k < c) {
-            pair_vec(xi, xj, per, L0, L1, L2, h0, h1, h2, dx, dy, dz);
+        if (in) {
+            const float4 cj = cand[li - t0];
+            cell_diff<GEN>(C, ax, ay, az, xr, cj, GEN ? cflag[li - t0] : 0, dx, dy, dz);
             r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             acc = r2 < rc2;
         }
-        unsigned bits = __ballot_sync(0xffffffffu, acc);
+        const unsigned bits = __ballot_sync(0xffffffffu, acc);
         if (acc) {
-            int pos = nq + __popc(bits & lt);
-            qd[w][pos] = make_float4(dx, dy, dz, r2);
-            qj[w][pos] = j;
+            const int pos = nq + __popc(bits & lt);
+            qd[pos] = make_float4(dx, dy, dz, r2);
+            qj[pos] = li - t0;
         }
         nq += __popc(bits);
         if (nq >= 32) {
             __syncwarp();
-            pair_heavy<LJ, COUL>(qd[w][lane], qj[w][lane], xi, pi, do_lj, S, xs, ps, qke, alpha, gau_c, fx, fy, fz,
-                                 elj, edir);
+            pair_heavy<LJ, COUL>(qd[lane], qj[lane], pi, do_lj, S, cand, par, qke, alpha, gau_c, fx, fy, fz, elj,
+                                 edir);
             __syncwarp();
             if (lane < nq - 32) {
-                qd[w][lane] = qd[w][lane + 32];
-                qj[w][lane] = qj[w][lane + 32];
+                qd[lane] = qd[lane + 32];
+                qj[lane] = qj[lane + 32];
             }
             nq -= 32;
             __syncwarp();
@@ -268,27 +222,26 @@ __global__ void __launch_bounds__(kQWarps * 32) k_pair_q(int N, int cap, const f
     }
     __syncwarp();
     if (lane < nq)
-        pair_heavy<LJ, COUL>(qd[w][lane], qj[w][lane], xi, pi, do_lj, S, xs, ps, qke, alpha, gau_c, fx, fy, fz, elj,
-                             edir);
-    if (COUL && alpha > 0.f) {
-        int oi = perm[i];
-        int e0 = ex_off[oi];
-        int ne = ex_off[oi + 1] - e0;
+        pair_heavy<LJ, COUL>(qd[lane], qj[lane], pi, do_lj, S, cand, par, qke, alpha, gau_c, fx, fy, fz, elj, edir);
+    __syncwarp();
+    if (COUL && last && alpha > 0.f) {
+        // exclusion correction for i's excluded partners (at any distance)
+        const int ne = X.count(i);
         for (int e = lane; e < ne; e += 32) {
-            int j = iperm[ex_idx[e0 + e]];
-            float4 xj = xs[j];
+            const int j = X.partner(i, e);
+            const float4 xj = xs[j];
             float dx, dy, dz;
-            pair_vec(xi, xj, per, L0, L1, L2, h0, h1, h2, dx, dy, dz);
-            float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            float rinv = rsqrtf(r2);
-            float r2inv = rinv * rinv;
-            float r = r2 * rinv;
-            float qq = qke * xj.w;
-            float ar = alpha * r;
-            float ef = erff(ar);
-            float gau = gau_c * __expf(-ar * ar);
+            pair_vec(xr, xj, C.per, C, dx, dy, dz);
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float rinv = rsqrtf(r2);
+            const float r2inv = rinv * rinv;
+            const float r = r2 * rinv;
+            const float qq = qke * xj.w;
+            const float ar = alpha * r;
+            const float ef = erff(ar);
+            const float gau = gau_c * __expf(-ar * ar);
             eex = fmaf(-qq * ef, rinv, eex);
-            float fr = qq * (gau - ef * rinv) * r2inv;
+            const float fr = qq * (gau - ef * rinv) * r2inv;
             fx = fmaf(fr, dx, fx);
             fy = fmaf(fr, dy, fy);
             fz = fmaf(fr, dz, fz);
@@ -301,210 +254,372 @@ __global__ void __launch_bounds__(kQWarps * 32) k_pair_q(int N, int cap, const f
     edir = group_sum<32>(edir);
     eex = group_sum<32>(eex);
     if (lane == 0) {
-        ffix[i] = to_fix(fx, scale, flags + 1);
-        ffix[(size_t)N + i] = to_fix(fy, scale, flags + 1);
-        ffix[2 * (size_t)N + i] = to_fix(fz, scale, flags + 1);
-        e_atom[i] = make_float4(0.5f * elj, 0.5f * edir, 0.5f * eex, 0.f);
+        if (multi) {  // stencil in several tiles: partial sums carried in tile order
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+            if (t0 > 0) {
+                a = pscr[3 * (size_t)i];
+                b = pscr[3 * (size_t)i + 1];
+            }
+            fx += a.x;
+            fy += a.y;
+            fz += a.z;
+            elj += a.w;
+            edir += b.x;
+            eex += b.y;
+            if (!last) {
+                pscr[3 * (size_t)i] = make_float4(fx, fy, fz, elj);
+                pscr[3 * (size_t)i + 1] = make_float4(edir, eex, 0.f, 0.f);
+            }
+        }
+        if (last) {
+            ffix[i] = to_fix(fx, scale, flags + 1);
+            ffix[(size_t)N + i] = to_fix(fy, scale, flags + 1);
+            ffix[2 * (size_t)N + i] = to_fix(fz, scale, flags + 1);
+            e_atom[i] = make_float4(0.5f * elj, 0.5f * edir, 0.5f * eex, 0.f);
+        }
+    }
+}
+
+template <bool LJ, bool COUL>
+__global__ void __launch_bounds__(kPairThreads) k_pair_cell(
+    int N, int cap, int tile, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
+    const int* __restrict__ start, const float4* __restrict__ xs, const float2* __restrict__ ps,
+    const unsigned short* __restrict__ nbr, const int* __restrict__ cnt, ExclView X, long long* __restrict__ ffix,
+    float4* __restrict__ e_atom, float4* __restrict__ pscr, float scale, unsigned* flags) {
+    const int c = blockIdx.x;
+    const SysDev& S = sys[cell_sys[c]];
+    const CellCtx C = cell_ctx(c, S, start);
+    if (C.i0 == C.i1) return;
+    __shared__ BuildRun runs[kMaxRuns];
+    __shared__ int n_runs, n_cand;
+    __shared__ float4 qd_all[kPairWarps][kQueue];
+    __shared__ int qj_all[kPairWarps][kQueue];
+    extern __shared__ float4 smem[];
+    float4* cand = smem;
+    float2* par = reinterpret_cast<float2*>(cand + tile);
+    unsigned char* cflag = reinterpret_cast<unsigned char*>(par + tile);
+    const int w = threadIdx.x >> 5;
+    if (w == 0) cell_runs(C, S, start, runs, &n_runs, &n_cand, flags);
+    __syncthreads();
+    const int nr = n_runs, total = n_cand;
+    if (total > 65536) return;  // the build has flagged the overflow
+    const bool multi = total > tile;
+    for (int t0 = 0; t0 < total; t0 += tile) {
+        const int t1 = min(total, t0 + tile);
+        stage_pair_tile(C, runs, nr, t0, t1, kPairThreads, xs, ps, nullptr, cand, par, nullptr, cflag);
+        __syncthreads();
+        const bool last = t1 == total;
+        for (int i = C.i0 + w; i < C.i1; i += kPairWarps) {
+            if (C.gen)
+                pair_atom<LJ, COUL, true>(C, S, N, i, t0, t1, multi, last, cand, par, cflag, qd_all[w], qj_all[w], xs,
+                                          ps, nbr, cnt, cap, X, ffix, e_atom, pscr, scale, flags);
+            else
+                pair_atom<LJ, COUL, false>(C, S, N, i, t0, t1, multi, last, cand, par, cflag, qd_all[w], qj_all[w],
+                                           xs, ps, nbr, cnt, cap, X, ffix, e_atom, pscr, scale, flags);
+        }
+        if (!last) __syncthreads();
     }
 }
 
 // Force VJP.  For each directed pair (i, j) with u = lam_i - lam_j and du = d.u:
 //   gx_i += f u + (f'/r) du d           (J (lam_i - lam_j), J = f I + (f'/r) d d^T)
 //   gq_i += ke q_j (f / qq) du,  gsig_i += 1/2 (df/dsigma_ij) du,  ge_i += sqrt(eps_j) (f/eps) du
-// and the forces F_i as in k_pair.  The exclusion correction contributes the same way.
-template <int P, bool LJ, bool COUL>
-__global__ void __launch_bounds__(256) k_vjp(int N, int cap, const float4* __restrict__ xs,
-                                              const float2* __restrict__ ps, const int* __restrict__ sid,
-                                              const SysDev* __restrict__ sys, const int* __restrict__ nbr,
-                                              const int* __restrict__ cnt, const int* __restrict__ perm,
-                                              const int* __restrict__ iperm, const int* __restrict__ ex_off,
-                                              const int* __restrict__ ex_idx, const float4* __restrict__ lam,
-                                              float4* __restrict__ gx_s, float2* __restrict__ gp_s,
-                                              long long* __restrict__ ffix, float4* __restrict__ e_atom,
-                                              float scale, unsigned* flags) {
-    int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    int i = gt / P, lane = gt % P;
-    bool valid = i < N;
-    int ii = valid ? i : N - 1;
-    const SysDev& S = sys[sid[ii]];
-    const float4 xi = xs[ii];
-    const float2 pi = ps[ii];
-    const float4 li = lam[ii];
-    const int c = valid ? cnt[ii] : 0;
-    const int* row = nbr + (size_t)ii * cap;
-    const float L0 = S.L[0], L1 = S.L[1], L2 = S.L[2];
-    const float h0 = S.halfL[0], h1 = S.halfL[1], h2 = S.halfL[2];
-    const int per = S.periodic;
+// and the forces F_i as in k_pair_cell.  The exclusion correction contributes the same way.
+struct VjpAcc {
+    float fx = 0.f, fy = 0.f, fz = 0.f, elj = 0.f, edir = 0.f, eex = 0.f;
+    float gx = 0.f, gy = 0.f, gz = 0.f, gq = 0.f, gs = 0.f, ge = 0.f;
+};
+
+template <bool LJ, bool COUL>
+__device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, const float4& xjq, const float2& pj,
+                                          const float4& li, const float2& pi, float qi, const SysDev& S,
+                                          float alpha, float a2, float gau_c, VjpAcc& A) {
+    const float dx = q.x, dy = q.y, dz = q.z, r2 = q.w;
+    const float ux = li.x - lj4.x, uy = li.y - lj4.y, uz = li.z - lj4.z;
+    const float du = fmaf(dz, uz, fmaf(dy, uy, dx * ux));
+    const float rinv = rsqrtf(r2);
+    const float r2inv = __frcp_rn(r2);
+    float fr = 0.f, fpr = 0.f;  // f and f'/r
+    if (LJ) {
+        const float eps = pi.y * pj.y;
+        const float sig = 0.5f * (pi.x + pj.x);
+        const float s2 = sig2_over_r2(sig, r2inv);
+        const float s6 = s2 * s2 * s2, s12 = s6 * s6;
+        float u = 4.f * (s12 - s6);  // per unit eps
+        float f = 24.f * (2.f * s12 - s6) * r2inv;
+        float fp = -24.f * (28.f * s12 - 8.f * s6) * r2inv * r2inv;
+        const float sinv = sig > 0.f ? 1.f / sig : 0.f;
+        const float us = 4.f * (12.f * s12 - 6.f * s6) * sinv;           // du/dsigma
+        float fs = 24.f * (24.f * s12 - 6.f * s6) * r2inv * sinv;        // df/dsigma
+        if (S.has_switch) {
+            const float r = r2 * rinv;
+            if (r > S.rs) {
+                const float x = (r - S.rs) * S.inv_sw;
+                const float x2 = x * x, x3 = x2 * x;
+                const float sw = 1.f + x3 * (-10.f + x * (15.f - 6.f * x));
+                const float d1 = x2 * (-30.f + x * (60.f - 30.f * x)) * S.inv_sw;
+                const float d2 = x * (-60.f + x * (180.f - 120.f * x)) * S.inv_sw * S.inv_sw;
+                fp = fp * sw + 2.f * f * d1 * rinv - u * (d2 - d1 * rinv) * r2inv;
+                fs = fs * sw - us * d1 * rinv;
+                f = f * sw - u * d1 * rinv;
+                u *= sw;
+            }
+        }
+        const float eps_lo = fmaf(pi.y, pj.y, -eps);
+        A.elj = fmaf(eps, u, fmaf(eps_lo, u, A.elj));
+        fr = fmaf(eps_lo, f, eps * f);
+        fpr = eps * fp;
+        A.ge = fmaf(pj.y * f, du, A.ge);
+        A.gs = fmaf(0.5f * eps * fs, du, A.gs);
+    }
+    if (COUL) {
+        const float r = r2 * rinv;
+        const float qq = S.ke * qi * xjq.w;
+        const float ar = alpha * r;
+        const float ec = erfcf(ar);
+        const float gau = gau_c * __expf(-ar * ar);
+        const float fcu = fmaf(ec, rinv, gau) * r2inv;  // f per unit qq
+        A.edir = fmaf(qq * ec, rinv, A.edir);
+        fr = fmaf(qq, fcu, fr);
+        fpr = fmaf(-qq * r2inv, fmaf(3.f, fcu, 2.f * a2 * gau), fpr);
+        A.gq = fmaf(S.ke * xjq.w * fcu, du, A.gq);
+    }
+    const float k2 = fpr * du;
+    A.gx = fmaf(fr, ux, fmaf(k2, dx, A.gx));
+    A.gy = fmaf(fr, uy, fmaf(k2, dy, A.gy));
+    A.gz = fmaf(fr, uz, fmaf(k2, dz, A.gz));
+    A.fx = fmaf(fr, dx, A.fx);
+    A.fy = fmaf(fr, dy, A.fy);
+    A.fz = fmaf(fr, dz, A.fz);
+}
+
+template <bool LJ, bool COUL, bool GEN>
+__device__ __forceinline__ void vjp_atom(const CellCtx& C, const SysDev& S, int N, int i, int t0, int t1, bool multi,
+                                         bool last, const float4* cand, const float2* par, const float4* lamc,
+                                         const unsigned char* cflag, float4* qd, int* qj,
+                                         const float4* __restrict__ xs, const float2* __restrict__ ps,
+                                         const float4* __restrict__ lam, const unsigned short* __restrict__ nbr,
+                                         const int* __restrict__ cnt, int cap, const ExclView& X,
+                                         float4* __restrict__ gx_s, float2* __restrict__ gp_s,
+                                         long long* __restrict__ ffix, float4* __restrict__ e_atom,
+                                         float4* __restrict__ pscr, float scale, unsigned* flags) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const float4 xr = xs[i];
+    const float ax = xr.x + C.fs[0], ay = xr.y + C.fs[1], az = xr.z + C.fs[2];
+    const float2 pi = ps[i];
+    const float4 li = lam[i];
+    const int c = cnt[i];
+    const unsigned short* row = nbr + (size_t)i * cap;
     const float rc2 = S.rc2;
     const float alpha = S.alpha, a2 = alpha * alpha;
     const float gau_c = 2.f * alpha * kInvSqrtPi;
-    float fx = 0.f, fy = 0.f, fz = 0.f, elj = 0.f, edir = 0.f, eex = 0.f;
-    float gx = 0.f, gy = 0.f, gz = 0.f, gq = 0.f, gs = 0.f, ge = 0.f;
-    for (int k = lane; k < c; k += P) {
-        int j = __ldg(row + k);
-        float4 xj = xs[j];
-        float dx, dy, dz;
-        pair_vec(xi, xj, per, L0, L1, L2, h0, h1, h2, dx, dy, dz);
-        float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        if (r2 < rc2) {
-            float4 lj4 = lam[j];
-            float ux = li.x - lj4.x, uy = li.y - lj4.y, uz = li.z - lj4.z;
-            float du = fmaf(dz, uz, fmaf(dy, uy, dx * ux));
-            float rinv = rsqrtf(r2);
-            float r2inv = __frcp_rn(r2);
-            float fr = 0.f, fpr = 0.f;  // f and f'/r
-            if (LJ) {
-                float2 pj = ps[j];
-                float eps = pi.y * pj.y;
-                float sig = 0.5f * (pi.x + pj.x);
-                float s2 = sig2_over_r2(sig, r2inv);
-                float s6 = s2 * s2 * s2, s12 = s6 * s6;
-                float u = 4.f * (s12 - s6);                       // per unit eps
-                float f = 24.f * (2.f * s12 - s6) * r2inv;
-                float fp = -24.f * (28.f * s12 - 8.f * s6) * r2inv * r2inv;
-                float sinv = sig > 0.f ? 1.f / sig : 0.f;
-                float us = 4.f * (12.f * s12 - 6.f * s6) * sinv;           // du/dsigma
-                float fs = 24.f * (24.f * s12 - 6.f * s6) * r2inv * sinv;  // df/dsigma
-                if (S.has_switch) {
-                    float r = r2 * rinv;
-                    if (r > S.rs) {
-                        float x = (r - S.rs) * S.inv_sw;
-                        float x2 = x * x, x3 = x2 * x;
-                        float sw = 1.f + x3 * (-10.f + x * (15.f - 6.f * x));
-                        float d1 = x2 * (-30.f + x * (60.f - 30.f * x)) * S.inv_sw;
-                        float d2 = x * (-60.f + x * (180.f - 120.f * x)) * S.inv_sw * S.inv_sw;
-                        fp = fp * sw + 2.f * f * d1 * rinv - u * (d2 - d1 * rinv) * r2inv;
-                        fs = fs * sw - us * d1 * rinv;
-                        f = f * sw - u * d1 * rinv;
-                        u *= sw;
-                    }
-                }
-                float eps_lo = fmaf(pi.y, pj.y, -eps);
-                elj = fmaf(eps, u, fmaf(eps_lo, u, elj));
-                fr = fmaf(eps_lo, f, eps * f);
-                fpr = eps * fp;
-                ge = fmaf(pj.y * f, du, ge);
-                gs = fmaf(0.5f * eps * fs, du, gs);
+    VjpAcc A;
+    int nq = 0;
+    int kn = lane < c ? row[lane] : 0;
+    for (int base = 0; base < c; base += 32) {
+        const int k = base + lane;
+        const int lk = kn;
+        kn = (k + 32 < c) ? row[k + 32] : 0;
+        const bool in = k < c && (!multi || (lk >= t0 && lk < t1));
+        bool acc = false;
+        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+        if (in) {
+            const float4 cj = cand[lk - t0];
+            cell_diff<GEN>(C, ax, ay, az, xr, cj, GEN ? cflag[lk - t0] : 0, dx, dy, dz);
+            r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            acc = r2 < rc2;
+        }
+        const unsigned bits = __ballot_sync(0xffffffffu, acc);
+        if (acc) {
+            const int pos = nq + __popc(bits & lt);
+            qd[pos] = make_float4(dx, dy, dz, r2);
+            qj[pos] = lk - t0;
+        }
+        nq += __popc(bits);
+        if (nq >= 32) {
+            __syncwarp();
+            const int lq = qj[lane];
+            vjp_heavy<LJ, COUL>(qd[lane], lamc[lq], cand[lq], par[lq], li, pi, xr.w, S, alpha, a2, gau_c, A);
+            __syncwarp();
+            if (lane < nq - 32) {
+                qd[lane] = qd[lane + 32];
+                qj[lane] = qj[lane + 32];
             }
-            if (COUL) {
-                float r = r2 * rinv;
-                float qq = S.ke * xi.w * xj.w;
-                float ar = alpha * r;
-                float ec = erfcf(ar);
-                float gau = gau_c * __expf(-ar * ar);
-                float fcu = fmaf(ec, rinv, gau) * r2inv;  // f per unit qq
-                edir = fmaf(qq * ec, rinv, edir);
-                fr = fmaf(qq, fcu, fr);
-                fpr = fmaf(-qq * r2inv, fmaf(3.f, fcu, 2.f * a2 * gau), fpr);
-                gq = fmaf(S.ke * xj.w * fcu, du, gq);
-            }
-            float k2 = fpr * du;
-            gx = fmaf(fr, ux, fmaf(k2, dx, gx));
-            gy = fmaf(fr, uy, fmaf(k2, dy, gy));
-            gz = fmaf(fr, uz, fmaf(k2, dz, gz));
-            fx = fmaf(fr, dx, fx);
-            fy = fmaf(fr, dy, fy);
-            fz = fmaf(fr, dz, fz);
+            nq -= 32;
+            __syncwarp();
         }
     }
-    if (COUL && alpha > 0.f) {
-        int oi = valid ? perm[ii] : 0;
-        int e0 = valid ? ex_off[oi] : 0;
-        int ne = valid ? ex_off[oi + 1] - e0 : 0;
-        for (int e = lane; e < ne; e += P) {
-            int j = iperm[ex_idx[e0 + e]];
-            float4 xj = xs[j];
+    __syncwarp();
+    if (lane < nq) {
+        const int lq = qj[lane];
+        vjp_heavy<LJ, COUL>(qd[lane], lamc[lq], cand[lq], par[lq], li, pi, xr.w, S, alpha, a2, gau_c, A);
+    }
+    __syncwarp();
+    if (COUL && last && alpha > 0.f) {
+        const int ne = X.count(i);
+        for (int e = lane; e < ne; e += 32) {
+            const int j = X.partner(i, e);
+            const float4 xj = xs[j];
             float dx, dy, dz;
-            pair_vec(xi, xj, per, L0, L1, L2, h0, h1, h2, dx, dy, dz);
-            float4 lj4 = lam[j];
-            float ux = li.x - lj4.x, uy = li.y - lj4.y, uz = li.z - lj4.z;
-            float du = fmaf(dz, uz, fmaf(dy, uy, dx * ux));
-            float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            float rinv = rsqrtf(r2);
-            float r2inv = rinv * rinv;
-            float r = r2 * rinv;
-            float qq = S.ke * xi.w * xj.w;
-            float ar = alpha * r;
-            float ef = erff(ar);
-            float gau = gau_c * __expf(-ar * ar);
-            float fxu = (gau - ef * rinv) * r2inv;  // f per unit qq
-            eex = fmaf(-qq * ef, rinv, eex);
-            float fr = qq * fxu;
-            float fpr = -qq * r2inv * fmaf(3.f, fxu, 2.f * a2 * gau);
-            gq = fmaf(S.ke * xj.w * fxu, du, gq);
-            float k2 = fpr * du;
-            gx = fmaf(fr, ux, fmaf(k2, dx, gx));
-            gy = fmaf(fr, uy, fmaf(k2, dy, gy));
-            gz = fmaf(fr, uz, fmaf(k2, dz, gz));
-            fx = fmaf(fr, dx, fx);
-            fy = fmaf(fr, dy, fy);
-            fz = fmaf(fr, dz, fz);
+            pair_vec(xr, xj, C.per, C, dx, dy, dz);
+            const float4 lj4 = lam[j];
+            const float ux = li.x - lj4.x, uy = li.y - lj4.y, uz = li.z - lj4.z;
+            const float du = fmaf(dz, uz, fmaf(dy, uy, dx * ux));
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float rinv = rsqrtf(r2);
+            const float r2inv = rinv * rinv;
+            const float r = r2 * rinv;
+            const float qq = S.ke * xr.w * xj.w;
+            const float ar = alpha * r;
+            const float ef = erff(ar);
+            const float gau = gau_c * __expf(-ar * ar);
+            const float fxu = (gau - ef * rinv) * r2inv;  // f per unit qq
+            A.eex = fmaf(-qq * ef, rinv, A.eex);
+            const float fr = qq * fxu;
+            const float fpr = -qq * r2inv * fmaf(3.f, fxu, 2.f * a2 * gau);
+            A.gq = fmaf(S.ke * xj.w * fxu, du, A.gq);
+            const float k2 = fpr * du;
+            A.gx = fmaf(fr, ux, fmaf(k2, dx, A.gx));
+            A.gy = fmaf(fr, uy, fmaf(k2, dy, A.gy));
+            A.gz = fmaf(fr, uz, fmaf(k2, dz, A.gz));
+            A.fx = fmaf(fr, dx, A.fx);
+            A.fy = fmaf(fr, dy, A.fy);
+            A.fz = fmaf(fr, dz, A.fz);
         }
     }
-    fx = group_sum<P>(fx);
-    fy = group_sum<P>(fy);
-    fz = group_sum<P>(fz);
-    gx = group_sum<P>(gx);
-    gy = group_sum<P>(gy);
-    gz = group_sum<P>(gz);
-    gq = group_sum<P>(gq);
-    gs = group_sum<P>(gs);
-    ge = group_sum<P>(ge);
-    elj = group_sum<P>(elj);
-    edir = group_sum<P>(edir);
-    eex = group_sum<P>(eex);
-    if (valid && lane == 0) {
-        ffix[ii] = to_fix(fx, scale, flags + 1);
-        ffix[(size_t)N + ii] = to_fix(fy, scale, flags + 1);
-        ffix[2 * (size_t)N + ii] = to_fix(fz, scale, flags + 1);
-        e_atom[ii] = make_float4(0.5f * elj, 0.5f * edir, 0.5f * eex, 0.f);
-        gx_s[ii] = make_float4(gx, gy, gz, gq);
-        gp_s[ii] = make_float2(gs, ge);
+    float v[12] = {A.fx, A.fy, A.fz, A.elj, A.edir, A.eex, A.gx, A.gy, A.gz, A.gq, A.gs, A.ge};
+#pragma unroll
+    for (int q = 0; q < 12; ++q) v[q] = group_sum<32>(v[q]);
+    if (lane == 0) {
+        if (multi) {  // partial sums carried in tile order (12 scratch floats per atom)
+            float4* sp = pscr + 3 * (size_t)i;
+            if (t0 > 0) {
+                const float4 a = sp[0], b = sp[1], g = sp[2];
+                v[0] += a.x; v[1] += a.y; v[2] += a.z; v[3] += a.w;
+                v[4] += b.x; v[5] += b.y; v[6] += b.z; v[7] += b.w;
+                v[8] += g.x; v[9] += g.y; v[10] += g.z; v[11] += g.w;
+            }
+            if (!last) {
+                sp[0] = make_float4(v[0], v[1], v[2], v[3]);
+                sp[1] = make_float4(v[4], v[5], v[6], v[7]);
+                sp[2] = make_float4(v[8], v[9], v[10], v[11]);
+            }
+        }
+        if (last) {
+            ffix[i] = to_fix(v[0], scale, flags + 1);
+            ffix[(size_t)N + i] = to_fix(v[1], scale, flags + 1);
+            ffix[2 * (size_t)N + i] = to_fix(v[2], scale, flags + 1);
+            e_atom[i] = make_float4(0.5f * v[3], 0.5f * v[4], 0.5f * v[5], 0.f);
+            gx_s[i] = make_float4(v[6], v[7], v[8], v[9]);
+            gp_s[i] = make_float2(v[10], v[11]);
+        }
     }
-}
-
-template <int P, bool LJ, bool COUL>
-static void pair_p(nb_handle* h, cudaStream_t st) {
-    int N = h->n_atoms;
-    if (P == 32) {
-        k_pair_q<LJ, COUL><<<cdiv(N, kQWarps), kQWarps * 32, 0, st>>>(
-            N, h->cap, h->xs, h->ps, h->sid, h->sys, h->nbr, h->nbr_cnt, h->perm, h->iperm, h->ex_off, h->ex_idx,
-            h->ffix, h->e_atom, h->fscale, h->flags);
-        return;
-    }
-    k_pair<P, LJ, COUL><<<cdiv((long long)N * P, 256), 256, 0, st>>>(
-        N, h->cap, h->xs, h->ps, h->sid, h->sys, h->nbr, h->nbr_cnt, h->perm, h->iperm, h->ex_off, h->ex_idx,
-        h->ffix, h->e_atom, h->fscale, h->flags);
-}
-
-template <int P, bool LJ, bool COUL>
-static void vjp_p(nb_handle* h, cudaStream_t st) {
-    int N = h->n_atoms;
-    k_vjp<P, LJ, COUL><<<cdiv((long long)N * P, 256), 256, 0, st>>>(
-        N, h->cap, h->xs, h->ps, h->sid, h->sys, h->nbr, h->nbr_cnt, h->perm, h->iperm, h->ex_off, h->ex_idx,
-        h->lam, h->gx_s, h->gp_s, h->ffix, h->e_atom, h->fscale, h->flags);
 }
 
 template <bool LJ, bool COUL>
-static void pair_dispatch(nb_handle* h, cudaStream_t st, bool vjp) {
-    switch (h->lanes) {
-        case 4: vjp ? vjp_p<4, LJ, COUL>(h, st) : pair_p<4, LJ, COUL>(h, st); break;
-        case 8: vjp ? vjp_p<8, LJ, COUL>(h, st) : pair_p<8, LJ, COUL>(h, st); break;
-        case 16: vjp ? vjp_p<16, LJ, COUL>(h, st) : pair_p<16, LJ, COUL>(h, st); break;
-        default: vjp ? vjp_p<32, LJ, COUL>(h, st) : pair_p<32, LJ, COUL>(h, st); break;
+__global__ void __launch_bounds__(kVjpThreads) k_vjp_cell(
+    int N, int cap, int tile, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
+    const int* __restrict__ start, const float4* __restrict__ xs, const float2* __restrict__ ps,
+    const float4* __restrict__ lam, const unsigned short* __restrict__ nbr, const int* __restrict__ cnt,
+    ExclView X, float4* __restrict__ gx_s, float2* __restrict__ gp_s, long long* __restrict__ ffix,
+    float4* __restrict__ e_atom, float4* __restrict__ pscr, float scale, unsigned* flags) {
+    const int c = blockIdx.x;
+    const SysDev& S = sys[cell_sys[c]];
+    const CellCtx C = cell_ctx(c, S, start);
+    if (C.i0 == C.i1) return;
+    __shared__ BuildRun runs[kMaxRuns];
+    __shared__ int n_runs, n_cand;
+    __shared__ float4 qd_all[kVjpWarps][kQueue];
+    __shared__ int qj_all[kVjpWarps][kQueue];
+    extern __shared__ float4 smem[];
+    float4* cand = smem;
+    float4* lamc = cand + tile;
+    float2* par = reinterpret_cast<float2*>(lamc + tile);
+    unsigned char* cflag = reinterpret_cast<unsigned char*>(par + tile);
+    const int w = threadIdx.x >> 5;
+    if (w == 0) cell_runs(C, S, start, runs, &n_runs, &n_cand, flags);
+    __syncthreads();
+    const int nr = n_runs, total = n_cand;
+    if (total > 65536) return;
+    const bool multi = total > tile;
+    for (int t0 = 0; t0 < total; t0 += tile) {
+        const int t1 = min(total, t0 + tile);
+        stage_pair_tile(C, runs, nr, t0, t1, kVjpThreads, xs, ps, lam, cand, par, lamc, cflag);
+        __syncthreads();
+        const bool last = t1 == total;
+        for (int i = C.i0 + w; i < C.i1; i += kVjpWarps) {
+            if (C.gen)
+                vjp_atom<LJ, COUL, true>(C, S, N, i, t0, t1, multi, last, cand, par, lamc, cflag, qd_all[w],
+                                         qj_all[w], xs, ps, lam, nbr, cnt, cap, X, gx_s, gp_s, ffix, e_atom, pscr,
+                                         scale, flags);
+            else
+                vjp_atom<LJ, COUL, false>(C, S, N, i, t0, t1, multi, last, cand, par, lamc, cflag, qd_all[w],
+                                          qj_all[w], xs, ps, lam, nbr, cnt, cap, X, gx_s, gp_s, ffix, e_atom, pscr,
+                                          scale, flags);
+        }
+        if (!last) __syncthreads();
     }
+}
+
+static size_t pair_smem(const nb_handle* h) {
+    return (size_t)h->tile * (sizeof(float4) + sizeof(float2) + (h->build_gen ? 1 : 0));
+}
+static size_t vjp_smem(const nb_handle* h) {
+    return (size_t)h->tile * (2 * sizeof(float4) + sizeof(float2) + (h->build_gen ? 1 : 0));
+}
+
+static ExclView excl_view(const nb_handle* h) {
+    ExclView X;
+    X.ew = h->excl_w;
+    X.slot = h->ex_slot;
+    X.cnt = h->ex_cnt;
+    X.perm = h->perm;
+    X.iperm = h->iperm;
+    X.off = h->ex_off;
+    X.idx = h->ex_idx;
+    return X;
+}
+
+template <bool LJ, bool COUL>
+static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp) {
+    const ExclView X = excl_view(h);
+    if (vjp)
+        k_vjp_cell<LJ, COUL><<<h->n_cells, kVjpThreads, vjp_smem(h), st>>>(
+            h->n_atoms, h->cap, h->tile, h->cell_sys, h->sys, h->cell_start, h->xs, h->ps, h->lam, h->nbr,
+            h->nbr_cnt, X, h->gx_s, h->gp_s, h->ffix, h->e_atom, h->pscr, h->fscale, h->flags);
+    else
+        k_pair_cell<LJ, COUL><<<h->n_cells, kPairThreads, pair_smem(h), st>>>(
+            h->n_atoms, h->cap, h->tile, h->cell_sys, h->sys, h->cell_start, h->xs, h->ps, h->nbr, h->nbr_cnt, X,
+            h->ffix, h->e_atom, h->pscr, h->fscale, h->flags);
 }
 
 static void dispatch(nb_handle* h, int terms, cudaStream_t st, bool vjp) {
     bool lj = (terms & NB_TERM_LJ) != 0;
     bool coul = (terms & NB_TERM_COUL) != 0;
-    if (lj && coul) pair_dispatch<true, true>(h, st, vjp);
-    else if (lj) pair_dispatch<true, false>(h, st, vjp);
-    else if (coul) pair_dispatch<false, true>(h, st, vjp);
-    else pair_dispatch<false, false>(h, st, vjp);
+    if (lj && coul) pair_launch<true, true>(h, st, vjp);
+    else if (lj) pair_launch<true, false>(h, st, vjp);
+    else if (coul) pair_launch<false, true>(h, st, vjp);
+    else pair_launch<false, false>(h, st, vjp);
 }
 
 void launch_pair(nb_handle* h, int terms, cudaStream_t st) { dispatch(h, terms, st, false); }
 void launch_vjp(nb_handle* h, int terms, cudaStream_t st) { dispatch(h, terms, st, true); }
+
+template <bool LJ, bool COUL>
+static cudaError_t set_smem(const nb_handle* h) {
+    cudaError_t e = cudaFuncSetAttribute(k_pair_cell<LJ, COUL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pair_smem(h));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_vjp_cell<LJ, COUL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vjp_smem(h));
+}
+
+cudaError_t pair_setup(nb_handle* h) {
+    cudaError_t e = set_smem<true, true>(h);
+    if (e == cudaSuccess) e = set_smem<true, false>(h);
+    if (e == cudaSuccess) e = set_smem<false, true>(h);
+    if (e == cudaSuccess) e = set_smem<false, false>(h);
+    return e;
+}
 
 }  // namespace nb

@@ -63,7 +63,7 @@ class SystemDesc(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [
         ("max_neighbors", ctypes.c_int32),
-        ("lanes_per_atom", ctypes.c_int32),
+        ("stencil_tile", ctypes.c_int32),
         ("cell_div", ctypes.c_int32),
         ("force_bits", ctypes.c_int32),
     ]
@@ -194,7 +194,7 @@ class Handle:
     ``workloads.System`` (n, box, r_cut, r_skin, r_switch, alpha, ke,
     pme_grid, sigma, sqrt_eps, excl_off/excl_idx)."""
 
-    def __init__(self, systems, max_neighbors=0, lanes_per_atom=0, cell_div=0, force_bits=0, periodic=True):
+    def __init__(self, systems, max_neighbors=0, stencil_tile=0, cell_div=0, force_bits=0, periodic=True):
         lib = load()
         self._h = None
         n_sys = len(systems)
@@ -231,7 +231,7 @@ class Handle:
         self.sqrt_eps = np.ascontiguousarray(np.concatenate(sqe), np.float32)
         ex_off = np.ascontiguousarray(offs, np.int32)
         ex_idx = np.ascontiguousarray(np.concatenate(idxs) if idxs else np.zeros(0), np.int32)
-        opt = Options(int(max_neighbors), int(lanes_per_atom), int(cell_div), int(force_bits))
+        opt = Options(int(max_neighbors), int(stencil_tile), int(cell_div), int(force_bits))
         h = _vp()
         st = lib.nb_create(ctypes.byref(h), descs, n_sys, self.sigma.ctypes.data, self.sqrt_eps.ctypes.data,
                            ex_off.ctypes.data, ex_idx.ctypes.data if ex_idx.size else None, ctypes.byref(opt))

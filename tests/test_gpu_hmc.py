@@ -124,12 +124,16 @@ def test_hmc_backward_matches_finite_differences():
         hstep = 1e-5 * d64[r]
         fd = (_replica_loss(s, xi[r], wr, d64[r] + hstep) - _replica_loss(s, xi[r], wr, d64[r] - hstep)) / (2 * hstep)
         assert gdt[r] == pytest.approx(fd, rel=2e-3, abs=1e-9), (r, gdt[r], fd, st[r])
-        # directional derivative along a per-type change of this replica's inverse masses
+        # directional derivative along a per-type change of this replica's inverse masses;
+        # the mixed-sign direction makes g.v cancel (by ~35x here), so the FP32 error of
+        # the components is bounded against sum |g_i v_i| rather than against g.v
         dirv = np.where(s.types == 0, 1.0, -0.7) * wr
         eps = 1e-5
         fdw = (_replica_loss(s, xi[r], wr + eps * dirv, d64[r]) - _replica_loss(s, xi[r], wr - eps * dirv, d64[r])) / (
             2 * eps)
-        assert float(np.dot(gw[r * n:(r + 1) * n], dirv)) == pytest.approx(fdw, rel=2e-3, abs=1e-9), (r, fdw)
+        g = gw[r * n:(r + 1) * n]
+        tol = 2e-3 * abs(fdw) + 1e-4 * float(np.abs(g * dirv).sum())
+        assert abs(float(np.dot(g, dirv)) - fdw) <= tol, (r, float(np.dot(g, dirv)), fdw, tol)
     assert checked >= 2
 
 

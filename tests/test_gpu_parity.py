@@ -45,11 +45,13 @@ def _jittered_fcc(seed=7, jitter=0.05):
 
 # ------------------------------------------------------------ neighbour lists
 
-@pytest.mark.parametrize("lanes,cell_div", [(4, 1), (8, 2), (16, 1), (32, 2)])
-def test_neighbor_set_lj_fcc_864(lanes, cell_div):
+# tile 256 splits every stencil (864 candidates for cell_div 1) over several
+# shared-memory tiles
+@pytest.mark.parametrize("tile,cell_div", [(0, 1), (256, 2), (256, 1), (0, 2)])
+def test_neighbor_set_lj_fcc_864(tile, cell_div):
     s = _jittered_fcc()
     r_nl = s.r_cut + s.r_skin
-    with nbcore.Handle([s], lanes_per_atom=lanes, cell_div=cell_div) as h:
+    with nbcore.Handle([s], stencil_tile=tile, cell_div=cell_div) as h:
         pairs, n = h.nl_build(dev_xq(s), force_rebuild=True)
         gpu = pair_set(pairs.cpu().numpy())
     ref, n_band = oracle.neighbor_pairs(s.x.astype(np.float64), oracle_params(s), r_nl, band=band(r_nl))
@@ -107,6 +109,43 @@ def test_neighbor_list_rebuild_is_lazy_and_valid():
         assert n == len(ref)
 
 
+def test_small_box_folds_axes_without_a_stencil():
+    # L = 2.4 r_nl: two cells per axis, so every axis is visited whole and folded per pair
+    r_nl = 2.8
+    s = wl.lj_random(256, seed=17)
+    assert 2 * r_nl <= s.box[0] < 3 * r_nl
+    with nbcore.Handle([s]) as h:
+        pairs, n = h.nl_build(dev_xq(s), force_rebuild=True)
+        gpu = pair_set(pairs.cpu().numpy())
+        f, e = _forces(h, s, terms=nbcore.NB_TERM_LJ)
+    ref, n_band = oracle.neighbor_pairs(s.x.astype(np.float64), oracle_params(s), r_nl, band=band(r_nl))
+    assert n_band == 0 and gpu == pair_set(ref)
+    eo, fo = oracle_real_space(s)
+    assert rel_rms(f, fo) <= F_TOL
+    assert abs(e[0] - eo[0]) <= E_TOL * abs(eo[0])
+
+
+@pytest.mark.parametrize("wrap", [False, True])
+def test_forces_after_boundary_crossing_without_rebuild(wrap):
+    # every atom moves by 0.06..0.14 < r_skin/2 along x: atoms near L leave the box (or,
+    # wrapped by the caller, reappear near 0) while the list from the build is kept
+    s = _jittered_fcc(5)
+    with nbcore.Handle([s]) as h:
+        _forces(h, s, terms=nbcore.NB_TERM_LJ)
+        c0 = h.rebuild_count()
+        step = np.random.default_rng(3).uniform(0.06, 0.14, s.n)
+        x = s.x.astype(np.float64)
+        x[:, 0] += step
+        if wrap:
+            x -= s.box * np.floor(x / s.box)
+        s.x = x.astype(np.float32)
+        f, e = _forces(h, s, terms=nbcore.NB_TERM_LJ)
+        assert h.rebuild_count() == c0
+    eo, fo = oracle_real_space(s)
+    assert rel_rms(f, fo) <= F_TOL
+    assert abs(e[0] - eo[0]) <= E_TOL * abs(eo[0])
+
+
 # ---------------------------------------------------------------- forces
 
 @pytest.mark.parametrize("switch", [False, True])
@@ -122,9 +161,11 @@ def test_lj_forces_and_energy_864(switch):
     assert np.abs(f.sum(axis=0)).max() < 1e-6 * np.abs(fo).max() * np.sqrt(s.n)
 
 
-def test_water_real_space_forces_and_energies():
+# tile 256 splits each ~2250-candidate stencil over nine shared-memory tiles
+@pytest.mark.parametrize("tile", [0, 256])
+def test_water_real_space_forces_and_energies(tile):
     s = wl.water_box(n_side=10, L=31.05, seed=5, pme_grid=32)
-    with nbcore.Handle([s]) as h:
+    with nbcore.Handle([s], stencil_tile=tile) as h:
         f, e = _forces(h, s, terms=nbcore.NB_TERM_LJ | nbcore.NB_TERM_COUL)
     eo, fo = oracle_real_space(s)
     assert rel_rms(f, fo) <= F_TOL
@@ -190,14 +231,15 @@ def test_forces_bitwise_deterministic():
 
 # ---------------------------------------------------------------- VJP
 
-def test_force_vjp_matches_oracle():
+@pytest.mark.parametrize("tile", [0, 256])
+def test_force_vjp_matches_oracle(tile):
     s = wl.water_box(n_side=6, L=18.9, seed=12, r_cut=8.0, r_skin=1.0)
     rng = np.random.default_rng(1)
     lam = rng.standard_normal((s.n, 3)).astype(np.float32)
     gxo, gqo, gso, geo = oracle.force_vjp(s.x.astype(np.float64), s.q, s.sigma, s.sqrt_eps, oracle_params(s),
                                           lam, excl=s.excl)
     xq = dev_xq(s)
-    with nbcore.Handle([s]) as h:
+    with nbcore.Handle([s], stencil_tile=tile) as h:
         gx = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
         gq = torch.empty(s.n, dtype=torch.float32, device="cuda")
         gs = torch.empty(s.n, dtype=torch.float32, device="cuda")
@@ -215,6 +257,24 @@ def test_force_vjp_lj_switch_matches_oracle():
     s = _jittered_fcc(21)
     s.r_switch = 2.2
     rng = np.random.default_rng(2)
+    lam = rng.standard_normal((s.n, 3)).astype(np.float32)
+    gxo, _, gso, geo = oracle.force_vjp(s.x.astype(np.float64), s.q, s.sigma, s.sqrt_eps, oracle_params(s), lam)
+    with nbcore.Handle([s]) as h:
+        gx = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+        gs = torch.empty(s.n, dtype=torch.float32, device="cuda")
+        ge = torch.empty(s.n, dtype=torch.float32, device="cuda")
+        h.nonbonded_force_vjp(dev_xq(s), torch.from_numpy(lam).cuda(), gx, None, gs, ge)
+        h.check()
+    assert rel_rms(gx.cpu().numpy(), gxo) <= 1e-5
+    assert rel_rms(gs.cpu().numpy(), gso) <= 1e-5
+    assert rel_rms(ge.cpu().numpy(), geo) <= 1e-5
+
+
+def test_force_vjp_small_box_folded_axes():
+    # two cells per axis: every axis is folded per pair in the list build and the kernels
+    s = wl.lj_random(216, seed=23, n_types=2)
+    s.r_switch = 2.2
+    rng = np.random.default_rng(4)
     lam = rng.standard_normal((s.n, 3)).astype(np.float32)
     gxo, _, gso, geo = oracle.force_vjp(s.x.astype(np.float64), s.q, s.sigma, s.sqrt_eps, oracle_params(s), lam)
     with nbcore.Handle([s]) as h:
@@ -268,7 +328,7 @@ def test_md_config1_100_steps_against_oracle():
 def test_batched_systems_match_single_system_bitwise():
     systems = [wl.lj_random(700, seed=1), wl.water_box(n_side=9, L=27.9, seed=2, pme_grid=27),
                wl.lj_random(1311, seed=3), wl.water_box_density(400, seed=4)]
-    opts = dict(lanes_per_atom=16, cell_div=1, max_neighbors=1024)
+    opts = dict(cell_div=1, max_neighbors=1024)
     xs = [dev_xq(s) for s in systems]
     fb = torch.empty((sum(s.n for s in systems), 3), dtype=torch.float32, device="cuda")
     eb = torch.empty((len(systems), 6), dtype=torch.float64, device="cuda")

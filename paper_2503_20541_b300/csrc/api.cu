@@ -277,10 +277,10 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
     }
     h->cell_div = o.cell_div ? o.cell_div : (fine_cells ? 2 : 1);
     if (o.max_neighbors > 0) {
-        h->cap = round_up(o.max_neighbors, 32);
+        h->cap = std::max(128, round_up(o.max_neighbors, 32));
     } else {
         h->cap = round_up((long long)(1.5 * nb_max + 64.0), 32);
-        h->cap = std::max(32, std::min(h->cap, round_up(n_max, 32)));
+        h->cap = std::max(128, std::min(h->cap, round_up(n_max, 32)));
     }
     h->force_bits = o.force_bits ? o.force_bits : 32;
     h->fscale = std::ldexp(1.0f, h->force_bits);

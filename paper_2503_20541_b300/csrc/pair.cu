@@ -21,6 +21,23 @@
 
 namespace nb {
 
+// System constants the pair math needs, held in registers for the whole block.
+struct PairK {
+    float rc2, alpha, ke, rs, inv_sw;
+    int sw;  // LJ switch on
+};
+
+__device__ __forceinline__ PairK pair_k(const SysDev& S) {
+    PairK K;
+    K.rc2 = S.rc2;
+    K.alpha = S.alpha;
+    K.ke = S.ke;
+    K.rs = S.rs;
+    K.inv_sw = S.inv_sw;
+    K.sw = S.has_switch;
+    return K;
+}
+
 // (sigma/r)^2 with sigma^2 carried as an FMA two-product hi + lo: every pair of two given
 // atom types would otherwise share the same rounding of sigma^2, a bias that the
 // 6th/12th powers amplify and that does not average out over the pairs.
@@ -31,22 +48,21 @@ __device__ __forceinline__ float sig2_over_r2(float sig, float r2inv) {
 }
 
 // LJ per unit eps (u, f = -u'/r) with the optional switch; r2inv = 1/r^2.
-__device__ __forceinline__ void lj_unit(float sig, float r2inv, float rinv, float r2, const SysDev& S,
+__device__ __forceinline__ void lj_unit(float sig, float r2inv, float rinv, float r2, const PairK& K,
                                         float& u, float& f) {
     float s2 = sig2_over_r2(sig, r2inv);
     float s6 = s2 * s2 * s2;
     u = 4.f * (s6 * s6 - s6);
     f = 24.f * (2.f * s6 * s6 - s6) * r2inv;
-    if (S.has_switch) {
+    if (K.sw) {
+        // x = 0 below r_s gives S = 1, S' = 0 exactly: no branch on r
         float r = r2 * rinv;
-        if (r > S.rs) {
-            float x = (r - S.rs) * S.inv_sw;
-            float x2 = x * x, x3 = x2 * x;
-            float sw = 1.f + x3 * (-10.f + x * (15.f - 6.f * x));
-            float dsw = x2 * (-30.f + x * (60.f - 30.f * x)) * S.inv_sw;  // dS/dr
-            f = f * sw - u * dsw * rinv;
-            u *= sw;
-        }
+        float x = fmaxf(0.f, (r - K.rs) * K.inv_sw);
+        float x2 = x * x, x3 = x2 * x;
+        float sw = 1.f + x3 * (-10.f + x * (15.f - 6.f * x));
+        float dsw = x2 * (-30.f + x * (60.f - 30.f * x)) * K.inv_sw;  // dS/dr
+        f = f * sw - u * dsw * rinv;
+        u *= sw;
     }
 }
 
@@ -133,7 +149,7 @@ __device__ __forceinline__ void pair_vec(const float4& a, const float4& b, int p
 
 // One queued pair of the force kernel: (dx, dy, dz, r^2) and stencil index lq.
 template <bool LJ, bool COUL>
-__device__ __forceinline__ void pair_heavy(const float4& q, int lq, const float2& pi, bool do_lj, const SysDev& S,
+__device__ __forceinline__ void pair_heavy(const float4& q, int lq, const float2& pi, bool do_lj, const PairK& K,
                                            const float4* cand, const float2* par, float qke, float alpha,
                                            float gau_c, float& fx, float& fy, float& fz, float& elj, float& edir) {
     const float r2 = q.w;
@@ -145,7 +161,7 @@ __device__ __forceinline__ void pair_heavy(const float4& q, int lq, const float2
         const float eps = pi.y * pj.y;      // eps_ij = eps + eps_lo exactly
         const float eps_lo = fmaf(pi.y, pj.y, -eps);
         float u, f;
-        lj_unit(0.5f * (pi.x + pj.x), r2inv, rinv, r2, S, u, f);
+        lj_unit(0.5f * (pi.x + pj.x), r2inv, rinv, r2, K, u, f);
         elj = fmaf(eps, u, fmaf(eps_lo, u, elj));
         fr = fmaf(eps_lo, f, eps * f);
     }
@@ -163,80 +179,157 @@ __device__ __forceinline__ void pair_heavy(const float4& q, int lq, const float2
     fz = fmaf(fr, q.z, fz);
 }
 
+// Predicated shared-memory stores of a queue entry: the append stays inside the round's
+// basic block (no branch around it), so consecutive rounds interleave.
+__device__ __forceinline__ void sts_q_if(float4* qd, int* qj, float4 v, int j, bool ok) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(qd);
+    const unsigned b = (unsigned)__cvta_generic_to_shared(qj);
+    asm volatile(
+        "{\n .reg .pred q;\n setp.ne.u32 q, %6, 0;\n @q st.shared.v4.f32 [%0], {%2, %3, %4, %5};\n"
+        " @q st.shared.u32 [%1], %7;\n}\n" ::"r"(a),
+        "r"(b), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"((unsigned)ok), "r"(j)
+        : "memory");
+}
+
+// Stencil index of slot j (-1 when j is outside the cell's stencil), found by all lanes
+// of the warp testing the runs (uniform j).
+__device__ __forceinline__ int stencil_index(const BuildRun* runs, int nr, int j) {
+    const int lane = threadIdx.x & 31;
+    int li = -1;
+    for (int r0 = 0; r0 < nr; r0 += 32) {
+        const int r = r0 + lane;
+        bool hit = false;
+        int k = 0;
+        if (r < nr) {
+            const BuildRun& R = runs[r];
+            hit = j >= R.slot0 && j < R.slot0 + R.n;
+            k = R.sm0 + (j - R.slot0);
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, hit);
+        if (b) {
+            li = __shfl_sync(0xffffffffu, k, __ffs(b) - 1);
+            break;
+        }
+    }
+    return li;
+}
+
+// Header of an atom: everything its list walk needs first, loaded one atom ahead.
+struct AtomHdr {
+    float4 xr;   // position (frame of the last build) and charge
+    float2 pi;   // sigma, sqrt(eps)
+    int c;       // list length
+    uint2 g;     // this lane's four entries of the first 128-entry list group
+    int ej;      // lane q < table width: slot of exclusion partner q (-1: none)
+    int ne;      // number of exclusion partners
+};
+
+__device__ __forceinline__ AtomHdr load_hdr(int i, const float4* __restrict__ xs, const float2* __restrict__ ps,
+                                            const unsigned short* __restrict__ nbr, const int* __restrict__ cnt,
+                                            int cap, const ExclView& X, bool want_excl) {
+    const int lane = threadIdx.x & 31;
+    AtomHdr H;
+    H.xr = xs[i];
+    H.pi = ps[i];
+    H.c = cnt[i];
+    H.g = reinterpret_cast<const uint2*>(nbr + (size_t)i * cap)[lane];  // rows hold cap >= 128 entries
+    H.ne = (want_excl && X.ew) ? X.cnt[i] : 0;
+    H.ej = (want_excl && lane < X.ew) ? X.slot[(size_t)i * X.ew + lane] : -1;
+    return H;
+}
+
 // Forces and half energies of atom i over stencil tile [t0, t1) (one warp).
-template <bool LJ, bool COUL, bool GEN>
-__device__ __forceinline__ void pair_atom(const CellCtx& C, const SysDev& S, int N, int i, int t0, int t1, bool multi,
-                                          bool last, const float4* cand, const float2* par, const unsigned char* cflag,
+template <bool LJ, bool COUL, bool GEN, bool MULTI>
+__device__ __forceinline__ void pair_atom(const CellCtx& C, const PairK& K, int N, int i, const AtomHdr& H, int t0,
+                                          int t1, bool last, const BuildRun* runs, int nr,
+                                          const float4* cand, const float2* par, const unsigned char* cflag,
                                           float4* qd, int* qj, const float4* __restrict__ xs,
-                                          const float2* __restrict__ ps, const unsigned short* __restrict__ nbr,
-                                          const int* __restrict__ cnt, int cap, const ExclView& X,
+                                          const unsigned short* __restrict__ nbr, int cap, const ExclView& X,
                                           long long* __restrict__ ffix, float4* __restrict__ e_atom,
                                           float4* __restrict__ pscr, float scale, unsigned* flags) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const float4 xr = xs[i];
+    const float4 xr = H.xr;
     const float ax = xr.x + C.fs[0], ay = xr.y + C.fs[1], az = xr.z + C.fs[2];
-    const float2 pi = ps[i];
-    const int c = cnt[i];
-    const unsigned short* row = nbr + (size_t)i * cap;
-    const float rc2 = S.rc2;
-    const float qke = S.ke * xr.w;
-    const float alpha = S.alpha;
+    const float2 pi = H.pi;
+    const int c = H.c;
+    const uint2* row2 = reinterpret_cast<const uint2*>(nbr + (size_t)i * cap);
+    const float rc2 = K.rc2;
+    const float qke = K.ke * xr.w;
+    const float alpha = K.alpha;
     const float gau_c = 2.f * alpha * kInvSqrtPi;
     const bool do_lj = pi.y != 0.f;
     float fx = 0.f, fy = 0.f, fz = 0.f, elj = 0.f, edir = 0.f, eex = 0.f;
-    int nq = 0;
-    int kn = lane < c ? row[lane] : 0;  // list entries are loaded one round ahead
-    for (int base = 0; base < c; base += 32) {
-        const int k = base + lane;
-        const int li = kn;
-        kn = (k + 32 < c) ? row[k + 32] : 0;
-        const bool in = k < c && (!multi || (li >= t0 && li < t1));
-        bool acc = false;
-        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
-        if (in) {
-            const float4 cj = cand[li - t0];
-            cell_diff<GEN>(C, ax, ay, az, xr, cj, GEN ? cflag[li - t0] : 0, dx, dy, dz);
-            r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            acc = r2 < rc2;
-        }
-        const unsigned bits = __ballot_sync(0xffffffffu, acc);
-        if (acc) {
-            const int pos = nq + __popc(bits & lt);
-            qd[pos] = make_float4(dx, dy, dz, r2);
-            qj[pos] = li - t0;
-        }
-        nq += __popc(bits);
-        if (nq >= 32) {
-            __syncwarp();
-            pair_heavy<LJ, COUL>(qd[lane], qj[lane], pi, do_lj, S, cand, par, qke, alpha, gau_c, fx, fy, fz, elj,
-                                 edir);
-            __syncwarp();
-            if (lane < nq - 32) {
-                qd[lane] = qd[lane + 32];
-                qj[lane] = qj[lane + 32];
+    // pairs inside r_c wait in a 64-entry ring and are evaluated 32 at a time
+    int head = 0, nq = 0;
+    // the list is read in groups of 128 entries: lane l holds entries 4l..4l+3 of a group
+    // (one 8-byte load), the next group is loaded while this one is tested
+    uint2 gn = H.g;
+    for (int g0 = 0; g0 < c; g0 += 128) {
+        const uint2 gc = gn;
+        if (g0 + 128 < c) gn = row2[(g0 + 128) / 4 + lane];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int k = g0 + 4 * lane + t;
+            const unsigned wv = t < 2 ? gc.x : gc.y;
+            const int li = (t & 1) ? (int)(wv >> 16) : (int)(wv & 0xffffu);
+            const bool in = k < c && (!MULTI || (li >= t0 && li < t1));
+            const int lk = in ? li - t0 : 0;  // entries outside the tile read candidate 0, unused
+            const float4 cj = cand[lk];
+            float dx, dy, dz;
+            cell_diff<GEN>(C, ax, ay, az, xr, cj, GEN ? cflag[lk] : 0, dx, dy, dz);
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const bool acc = in && r2 < rc2;
+            const unsigned bits = __ballot_sync(0xffffffffu, acc);
+            const int pos = (head + nq + __popc(bits & lt)) & (kQueue - 1);
+            sts_q_if(qd + pos, qj + pos, make_float4(dx, dy, dz, r2), lk, acc);
+            nq += __popc(bits);
+            if (nq >= 32) {
+                __syncwarp();
+                const int pos = (head + lane) & (kQueue - 1);
+                const float4 q = qd[pos];
+                const int lq = qj[pos];
+                __syncwarp();
+                pair_heavy<LJ, COUL>(q, lq, pi, do_lj, K, cand, par, qke, alpha, gau_c, fx, fy, fz, elj, edir);
+                head = (head + 32) & (kQueue - 1);
+                nq -= 32;
             }
-            nq -= 32;
-            __syncwarp();
         }
     }
     __syncwarp();
-    if (lane < nq)
-        pair_heavy<LJ, COUL>(qd[lane], qj[lane], pi, do_lj, S, cand, par, qke, alpha, gau_c, fx, fy, fz, elj, edir);
+    if (lane < nq) {
+        const int pos = (head + lane) & (kQueue - 1);
+        pair_heavy<LJ, COUL>(qd[pos], qj[pos], pi, do_lj, K, cand, par, qke, alpha, gau_c, fx, fy, fz, elj, edir);
+    }
     __syncwarp();
-    if (COUL && last && alpha > 0.f) {
-        // exclusion correction for i's excluded partners (at any distance)
-        const int ne = X.count(i);
+    if (COUL && last && alpha > 0.f && H.ne > 0) {
+        // exclusion correction for i's excluded partners (at any distance); a partner in
+        // the staged stencil is read from shared memory with its image, others from xs
+        const int ne = H.ne;
+        int lk = -1;
+        const int nin = min(ne, X.ew);
+        for (int q = 0; q < nin; ++q) {
+            const int jq = __shfl_sync(0xffffffffu, H.ej, q);
+            const int k = stencil_index(runs, nr, jq);
+            if (lane == q) lk = k;
+        }
         for (int e = lane; e < ne; e += 32) {
-            const int j = X.partner(i, e);
-            const float4 xj = xs[j];
-            float dx, dy, dz;
-            pair_vec(xr, xj, C.per, C, dx, dy, dz);
+            float dx, dy, dz, qj_;
+            if (e < 32 && lk >= t0 && lk < t1) {
+                const float4 cj = cand[lk - t0];
+                cell_diff<GEN>(C, ax, ay, az, xr, cj, GEN ? cflag[lk - t0] : 0, dx, dy, dz);
+                qj_ = cj.w;
+            } else {
+                const int j = e < 32 && e < X.ew ? H.ej : X.partner(i, e);
+                const float4 xj = xs[j];
+                pair_vec(xr, xj, C.per, C, dx, dy, dz);
+                qj_ = xj.w;
+            }
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             const float rinv = rsqrtf(r2);
             const float r2inv = rinv * rinv;
             const float r = r2 * rinv;
-            const float qq = qke * xj.w;
+            const float qq = qke * qj_;
             const float ar = alpha * r;
             const float ef = erff(ar);
             const float gau = gau_c * __expf(-ar * ar);
@@ -254,7 +347,7 @@ __device__ __forceinline__ void pair_atom(const CellCtx& C, const SysDev& S, int
     edir = group_sum<32>(edir);
     eex = group_sum<32>(eex);
     if (lane == 0) {
-        if (multi) {  // stencil in several tiles: partial sums carried in tile order
+        if (MULTI) {  // stencil in several tiles: partial sums carried in tile order
             float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
             if (t0 > 0) {
                 a = pscr[3 * (size_t)i];
@@ -289,6 +382,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_cell(
     const int c = blockIdx.x;
     const SysDev& S = sys[cell_sys[c]];
     const CellCtx C = cell_ctx(c, S, start);
+    const PairK K = pair_k(S);
     if (C.i0 == C.i1) return;
     __shared__ BuildRun runs[kMaxRuns];
     __shared__ int n_runs, n_cand;
@@ -299,6 +393,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_cell(
     float2* par = reinterpret_cast<float2*>(cand + tile);
     unsigned char* cflag = reinterpret_cast<unsigned char*>(par + tile);
     const int w = threadIdx.x >> 5;
+    const bool want_excl = COUL && K.alpha > 0.f;
+    // the first atom's header is loaded while the stencil is staged
+    AtomHdr hn;
+    if (C.i0 + w < C.i1) hn = load_hdr(C.i0 + w, xs, ps, nbr, cnt, cap, X, want_excl);
     if (w == 0) cell_runs(C, S, start, runs, &n_runs, &n_cand, flags);
     __syncthreads();
     const int nr = n_runs, total = n_cand;
@@ -309,13 +407,20 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_cell(
         stage_pair_tile(C, runs, nr, t0, t1, kPairThreads, xs, ps, nullptr, cand, par, nullptr, cflag);
         __syncthreads();
         const bool last = t1 == total;
+        if (t0 > 0 && C.i0 + w < C.i1) hn = load_hdr(C.i0 + w, xs, ps, nbr, cnt, cap, X, want_excl);
         for (int i = C.i0 + w; i < C.i1; i += kPairWarps) {
-            if (C.gen)
-                pair_atom<LJ, COUL, true>(C, S, N, i, t0, t1, multi, last, cand, par, cflag, qd_all[w], qj_all[w], xs,
-                                          ps, nbr, cnt, cap, X, ffix, e_atom, pscr, scale, flags);
-            else
-                pair_atom<LJ, COUL, false>(C, S, N, i, t0, t1, multi, last, cand, par, cflag, qd_all[w], qj_all[w],
-                                           xs, ps, nbr, cnt, cap, X, ffix, e_atom, pscr, scale, flags);
+            const AtomHdr H = hn;
+            if (i + kPairWarps < C.i1) hn = load_hdr(i + kPairWarps, xs, ps, nbr, cnt, cap, X, want_excl);
+#define NB_PAIR_ARGS C, K, N, i, H, t0, t1, last, runs, nr, cand, par, cflag, qd_all[w], qj_all[w], xs, nbr, cap, X, \
+                     ffix, e_atom, pscr, scale, flags
+            if (multi) {
+                if (C.gen) pair_atom<LJ, COUL, true, true>(NB_PAIR_ARGS);
+                else pair_atom<LJ, COUL, false, true>(NB_PAIR_ARGS);
+            } else {
+                if (C.gen) pair_atom<LJ, COUL, true, false>(NB_PAIR_ARGS);
+                else pair_atom<LJ, COUL, false, false>(NB_PAIR_ARGS);
+            }
+#undef NB_PAIR_ARGS
         }
         if (!last) __syncthreads();
     }
@@ -332,7 +437,7 @@ struct VjpAcc {
 
 template <bool LJ, bool COUL>
 __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, const float4& xjq, const float2& pj,
-                                          const float4& li, const float2& pi, float qi, const SysDev& S,
+                                          const float4& li, const float2& pi, float qi, const PairK& K,
                                           float alpha, float a2, float gau_c, VjpAcc& A) {
     const float dx = q.x, dy = q.y, dz = q.z, r2 = q.w;
     const float ux = li.x - lj4.x, uy = li.y - lj4.y, uz = li.z - lj4.z;
@@ -351,19 +456,17 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, co
         const float sinv = sig > 0.f ? 1.f / sig : 0.f;
         const float us = 4.f * (12.f * s12 - 6.f * s6) * sinv;           // du/dsigma
         float fs = 24.f * (24.f * s12 - 6.f * s6) * r2inv * sinv;        // df/dsigma
-        if (S.has_switch) {
+        if (K.sw) {
             const float r = r2 * rinv;
-            if (r > S.rs) {
-                const float x = (r - S.rs) * S.inv_sw;
-                const float x2 = x * x, x3 = x2 * x;
-                const float sw = 1.f + x3 * (-10.f + x * (15.f - 6.f * x));
-                const float d1 = x2 * (-30.f + x * (60.f - 30.f * x)) * S.inv_sw;
-                const float d2 = x * (-60.f + x * (180.f - 120.f * x)) * S.inv_sw * S.inv_sw;
-                fp = fp * sw + 2.f * f * d1 * rinv - u * (d2 - d1 * rinv) * r2inv;
-                fs = fs * sw - us * d1 * rinv;
-                f = f * sw - u * d1 * rinv;
-                u *= sw;
-            }
+            const float x = fmaxf(0.f, (r - K.rs) * K.inv_sw);  // S = 1, S' = S'' = 0 below r_s
+            const float x2 = x * x, x3 = x2 * x;
+            const float sw = 1.f + x3 * (-10.f + x * (15.f - 6.f * x));
+            const float d1 = x2 * (-30.f + x * (60.f - 30.f * x)) * K.inv_sw;
+            const float d2 = x * (-60.f + x * (180.f - 120.f * x)) * K.inv_sw * K.inv_sw;
+            fp = fp * sw + 2.f * f * d1 * rinv - u * (d2 - d1 * rinv) * r2inv;
+            fs = fs * sw - us * d1 * rinv;
+            f = f * sw - u * d1 * rinv;
+            u *= sw;
         }
         const float eps_lo = fmaf(pi.y, pj.y, -eps);
         A.elj = fmaf(eps, u, fmaf(eps_lo, u, A.elj));
@@ -374,7 +477,7 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, co
     }
     if (COUL) {
         const float r = r2 * rinv;
-        const float qq = S.ke * qi * xjq.w;
+        const float qq = K.ke * qi * xjq.w;
         const float ar = alpha * r;
         const float ec = erfcf(ar);
         const float gau = gau_c * __expf(-ar * ar);
@@ -382,7 +485,7 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, co
         A.edir = fmaf(qq * ec, rinv, A.edir);
         fr = fmaf(qq, fcu, fr);
         fpr = fmaf(-qq * r2inv, fmaf(3.f, fcu, 2.f * a2 * gau), fpr);
-        A.gq = fmaf(S.ke * xjq.w * fcu, du, A.gq);
+        A.gq = fmaf(K.ke * xjq.w * fcu, du, A.gq);
     }
     const float k2 = fpr * du;
     A.gx = fmaf(fr, ux, fmaf(k2, dx, A.gx));
@@ -393,84 +496,97 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, co
     A.fz = fmaf(fr, dz, A.fz);
 }
 
-template <bool LJ, bool COUL, bool GEN>
-__device__ __forceinline__ void vjp_atom(const CellCtx& C, const SysDev& S, int N, int i, int t0, int t1, bool multi,
-                                         bool last, const float4* cand, const float2* par, const float4* lamc,
-                                         const unsigned char* cflag, float4* qd, int* qj,
-                                         const float4* __restrict__ xs, const float2* __restrict__ ps,
+template <bool LJ, bool COUL, bool GEN, bool MULTI>
+__device__ __forceinline__ void vjp_atom(const CellCtx& C, const PairK& K, int N, int i, const AtomHdr& H, int t0,
+                                         int t1, bool last, const BuildRun* runs, int nr, const float4* cand,
+                                         const float2* par, const float4* lamc, const unsigned char* cflag,
+                                         float4* qd, int* qj, const float4* __restrict__ xs,
                                          const float4* __restrict__ lam, const unsigned short* __restrict__ nbr,
-                                         const int* __restrict__ cnt, int cap, const ExclView& X,
-                                         float4* __restrict__ gx_s, float2* __restrict__ gp_s,
-                                         long long* __restrict__ ffix, float4* __restrict__ e_atom,
-                                         float4* __restrict__ pscr, float scale, unsigned* flags) {
+                                         int cap, const ExclView& X, float4* __restrict__ gx_s,
+                                         float2* __restrict__ gp_s, long long* __restrict__ ffix,
+                                         float4* __restrict__ e_atom, float4* __restrict__ pscr, float scale,
+                                         unsigned* flags) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const float4 xr = xs[i];
+    const float4 xr = H.xr;
     const float ax = xr.x + C.fs[0], ay = xr.y + C.fs[1], az = xr.z + C.fs[2];
-    const float2 pi = ps[i];
+    const float2 pi = H.pi;
     const float4 li = lam[i];
-    const int c = cnt[i];
-    const unsigned short* row = nbr + (size_t)i * cap;
-    const float rc2 = S.rc2;
-    const float alpha = S.alpha, a2 = alpha * alpha;
+    const int c = H.c;
+    const uint2* row2 = reinterpret_cast<const uint2*>(nbr + (size_t)i * cap);
+    const float rc2 = K.rc2;
+    const float alpha = K.alpha, a2 = alpha * alpha;
     const float gau_c = 2.f * alpha * kInvSqrtPi;
     VjpAcc A;
-    int nq = 0;
-    int kn = lane < c ? row[lane] : 0;
-    for (int base = 0; base < c; base += 32) {
-        const int k = base + lane;
-        const int lk = kn;
-        kn = (k + 32 < c) ? row[k + 32] : 0;
-        const bool in = k < c && (!multi || (lk >= t0 && lk < t1));
-        bool acc = false;
-        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
-        if (in) {
-            const float4 cj = cand[lk - t0];
-            cell_diff<GEN>(C, ax, ay, az, xr, cj, GEN ? cflag[lk - t0] : 0, dx, dy, dz);
-            r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            acc = r2 < rc2;
-        }
-        const unsigned bits = __ballot_sync(0xffffffffu, acc);
-        if (acc) {
-            const int pos = nq + __popc(bits & lt);
-            qd[pos] = make_float4(dx, dy, dz, r2);
-            qj[pos] = lk - t0;
-        }
-        nq += __popc(bits);
-        if (nq >= 32) {
-            __syncwarp();
-            const int lq = qj[lane];
-            vjp_heavy<LJ, COUL>(qd[lane], lamc[lq], cand[lq], par[lq], li, pi, xr.w, S, alpha, a2, gau_c, A);
-            __syncwarp();
-            if (lane < nq - 32) {
-                qd[lane] = qd[lane + 32];
-                qj[lane] = qj[lane + 32];
+    int head = 0, nq = 0;
+    uint2 gn = H.g;
+    for (int g0 = 0; g0 < c; g0 += 128) {
+        const uint2 gc = gn;
+        if (g0 + 128 < c) gn = row2[(g0 + 128) / 4 + lane];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int k = g0 + 4 * lane + t;
+            const unsigned wv = t < 2 ? gc.x : gc.y;
+            const int le = (t & 1) ? (int)(wv >> 16) : (int)(wv & 0xffffu);
+            const bool in = k < c && (!MULTI || (le >= t0 && le < t1));
+            const int lk = in ? le - t0 : 0;
+            const float4 cj = cand[lk];
+            float dx, dy, dz;
+            cell_diff<GEN>(C, ax, ay, az, xr, cj, GEN ? cflag[lk] : 0, dx, dy, dz);
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const bool acc = in && r2 < rc2;
+            const unsigned bits = __ballot_sync(0xffffffffu, acc);
+            const int pos = (head + nq + __popc(bits & lt)) & (kQueue - 1);
+            sts_q_if(qd + pos, qj + pos, make_float4(dx, dy, dz, r2), lk, acc);
+            nq += __popc(bits);
+            if (nq >= 32) {
+                __syncwarp();
+                const int p = (head + lane) & (kQueue - 1);
+                const float4 q = qd[p];
+                const int lq = qj[p];
+                __syncwarp();
+                vjp_heavy<LJ, COUL>(q, lamc[lq], cand[lq], par[lq], li, pi, xr.w, K, alpha, a2, gau_c, A);
+                head = (head + 32) & (kQueue - 1);
+                nq -= 32;
             }
-            nq -= 32;
-            __syncwarp();
         }
     }
     __syncwarp();
     if (lane < nq) {
-        const int lq = qj[lane];
-        vjp_heavy<LJ, COUL>(qd[lane], lamc[lq], cand[lq], par[lq], li, pi, xr.w, S, alpha, a2, gau_c, A);
+        const int p = (head + lane) & (kQueue - 1);
+        const int lq = qj[p];
+        vjp_heavy<LJ, COUL>(qd[p], lamc[lq], cand[lq], par[lq], li, pi, xr.w, K, alpha, a2, gau_c, A);
     }
     __syncwarp();
-    if (COUL && last && alpha > 0.f) {
-        const int ne = X.count(i);
+    if (COUL && last && alpha > 0.f && H.ne > 0) {
+        const int ne = H.ne;
+        int lk = -1;
+        const int nin = min(ne, X.ew);
+        for (int q = 0; q < nin; ++q) {
+            const int jq = __shfl_sync(0xffffffffu, H.ej, q);
+            const int k = stencil_index(runs, nr, jq);
+            if (lane == q) lk = k;
+        }
         for (int e = lane; e < ne; e += 32) {
-            const int j = X.partner(i, e);
-            const float4 xj = xs[j];
             float dx, dy, dz;
-            pair_vec(xr, xj, C.per, C, dx, dy, dz);
-            const float4 lj4 = lam[j];
+            float4 xj, lj4;
+            if (e < 32 && lk >= t0 && lk < t1) {
+                xj = cand[lk - t0];
+                lj4 = lamc[lk - t0];
+                cell_diff<GEN>(C, ax, ay, az, xr, xj, GEN ? cflag[lk - t0] : 0, dx, dy, dz);
+            } else {
+                const int j = e < 32 && e < X.ew ? H.ej : X.partner(i, e);
+                xj = xs[j];
+                lj4 = lam[j];
+                pair_vec(xr, xj, C.per, C, dx, dy, dz);
+            }
             const float ux = li.x - lj4.x, uy = li.y - lj4.y, uz = li.z - lj4.z;
             const float du = fmaf(dz, uz, fmaf(dy, uy, dx * ux));
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             const float rinv = rsqrtf(r2);
             const float r2inv = rinv * rinv;
             const float r = r2 * rinv;
-            const float qq = S.ke * xr.w * xj.w;
+            const float qq = K.ke * xr.w * xj.w;
             const float ar = alpha * r;
             const float ef = erff(ar);
             const float gau = gau_c * __expf(-ar * ar);
@@ -478,7 +594,7 @@ __device__ __forceinline__ void vjp_atom(const CellCtx& C, const SysDev& S, int 
             A.eex = fmaf(-qq * ef, rinv, A.eex);
             const float fr = qq * fxu;
             const float fpr = -qq * r2inv * fmaf(3.f, fxu, 2.f * a2 * gau);
-            A.gq = fmaf(S.ke * xj.w * fxu, du, A.gq);
+            A.gq = fmaf(K.ke * xj.w * fxu, du, A.gq);
             const float k2 = fpr * du;
             A.gx = fmaf(fr, ux, fmaf(k2, dx, A.gx));
             A.gy = fmaf(fr, uy, fmaf(k2, dy, A.gy));
@@ -492,7 +608,7 @@ __device__ __forceinline__ void vjp_atom(const CellCtx& C, const SysDev& S, int 
 #pragma unroll
     for (int q = 0; q < 12; ++q) v[q] = group_sum<32>(v[q]);
     if (lane == 0) {
-        if (multi) {  // partial sums carried in tile order (12 scratch floats per atom)
+        if (MULTI) {  // partial sums carried in tile order (12 scratch floats per atom)
             float4* sp = pscr + 3 * (size_t)i;
             if (t0 > 0) {
                 const float4 a = sp[0], b = sp[1], g = sp[2];
@@ -528,6 +644,7 @@ __global__ void __launch_bounds__(kVjpThreads) k_vjp_cell(
     const SysDev& S = sys[cell_sys[c]];
     const CellCtx C = cell_ctx(c, S, start);
     if (C.i0 == C.i1) return;
+    const PairK K = pair_k(S);
     __shared__ BuildRun runs[kMaxRuns];
     __shared__ int n_runs, n_cand;
     __shared__ float4 qd_all[kVjpWarps][kQueue];
@@ -538,6 +655,9 @@ __global__ void __launch_bounds__(kVjpThreads) k_vjp_cell(
     float2* par = reinterpret_cast<float2*>(lamc + tile);
     unsigned char* cflag = reinterpret_cast<unsigned char*>(par + tile);
     const int w = threadIdx.x >> 5;
+    const bool want_excl = COUL && K.alpha > 0.f;
+    AtomHdr hn;
+    if (C.i0 + w < C.i1) hn = load_hdr(C.i0 + w, xs, ps, nbr, cnt, cap, X, want_excl);
     if (w == 0) cell_runs(C, S, start, runs, &n_runs, &n_cand, flags);
     __syncthreads();
     const int nr = n_runs, total = n_cand;
@@ -548,15 +668,20 @@ __global__ void __launch_bounds__(kVjpThreads) k_vjp_cell(
         stage_pair_tile(C, runs, nr, t0, t1, kVjpThreads, xs, ps, lam, cand, par, lamc, cflag);
         __syncthreads();
         const bool last = t1 == total;
+        if (t0 > 0 && C.i0 + w < C.i1) hn = load_hdr(C.i0 + w, xs, ps, nbr, cnt, cap, X, want_excl);
         for (int i = C.i0 + w; i < C.i1; i += kVjpWarps) {
-            if (C.gen)
-                vjp_atom<LJ, COUL, true>(C, S, N, i, t0, t1, multi, last, cand, par, lamc, cflag, qd_all[w],
-                                         qj_all[w], xs, ps, lam, nbr, cnt, cap, X, gx_s, gp_s, ffix, e_atom, pscr,
-                                         scale, flags);
-            else
-                vjp_atom<LJ, COUL, false>(C, S, N, i, t0, t1, multi, last, cand, par, lamc, cflag, qd_all[w],
-                                          qj_all[w], xs, ps, lam, nbr, cnt, cap, X, gx_s, gp_s, ffix, e_atom, pscr,
-                                          scale, flags);
+            const AtomHdr H = hn;
+            if (i + kVjpWarps < C.i1) hn = load_hdr(i + kVjpWarps, xs, ps, nbr, cnt, cap, X, want_excl);
+#define NB_VJP_ARGS C, K, N, i, H, t0, t1, last, runs, nr, cand, par, lamc, cflag, qd_all[w], qj_all[w], xs, lam, nbr, \
+                    cap, X, gx_s, gp_s, ffix, e_atom, pscr, scale, flags
+            if (multi) {
+                if (C.gen) vjp_atom<LJ, COUL, true, true>(NB_VJP_ARGS);
+                else vjp_atom<LJ, COUL, false, true>(NB_VJP_ARGS);
+            } else {
+                if (C.gen) vjp_atom<LJ, COUL, true, false>(NB_VJP_ARGS);
+                else vjp_atom<LJ, COUL, false, false>(NB_VJP_ARGS);
+            }
+#undef NB_VJP_ARGS
         }
         if (!last) __syncthreads();
     }

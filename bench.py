@@ -239,7 +239,9 @@ def traffic_from_profile(path):
 
 
 def extras(torch, nbcore, wl):
-    """MD steps/s (LJ 864) and the backward/forward ratio of the differentiable HMC step."""
+    """MD steps/s (LJ 864), the backward/forward ratio of the differentiable HMC step and
+    the batched 256-system step."""
+    from paper_2503_20541_b300.graphs import CapturedStep
     out = {}
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     # MD: 864-atom LJ fluid, velocity Verlet dt = 0.005
@@ -261,9 +263,22 @@ def extras(torch, nbcore, wl):
         torch.cuda.synchronize()
         h.check()
         ms = e0.elapsed_time(e1)
-        out["md_steps_per_s"] = {"value": n / (ms / 1e3), "workload": "LJ fluid 864 atoms (FCC 6^3, rho* 0.8442, "
-                                 "r_c 2.5, r_skin 0.3), velocity Verlet dt 0.005, list checked every step",
-                                 "rebuilds": h.rebuild_count() - c0}
+        # the same steps as a CUDA graph of 10 velocity-Verlet steps (lazy rebuilds inside)
+        g = CapturedStep(lambda: h.md_step(xq, v, dt, 10, terms=nbcore.NB_TERM_LJ))
+        c1 = h.rebuild_count()
+        e2, e3 = ev(), ev()
+        e2.record()
+        for _ in range(n // 10):
+            g.replay()
+        e3.record()
+        torch.cuda.synchronize()
+        h.check()
+        ms_g = e2.elapsed_time(e3)
+        out["md_steps_per_s"] = {"value": n / (ms_g / 1e3), "eager": n / (ms / 1e3),
+                                 "workload": "LJ fluid 864 atoms (FCC 6^3, rho* 0.8442, r_c 2.5, r_skin 0.3), "
+                                 "velocity Verlet dt 0.005, list checked every step; value from a CUDA graph of "
+                                 "10 steps replayed, eager = the same steps launched from the host",
+                                 "rebuilds": h.rebuild_count() - c1, "rebuilds_eager": c1 - c0}
     # backward / forward: LJ 2048 atoms x 10 replicas, L = 32, checkpoints every 8
     R, L, K = 10, 32, 8
     systems = []
@@ -323,6 +338,73 @@ def extras(torch, nbcore, wl):
             "pair_kernel_us": 1e3 * kf, "vjp_kernel_us": 1e3 * kb,
             "workload": "differentiable HMC, LJ fluid 2048 atoms x 10 replicas (batched in one handle), "
                         "32 leapfrog steps, checkpoints every 8 (recompute in the backward), switch 2.2-2.5"}
+    out["batched"] = batched(torch, nbcore, wl)
+    return out
+
+
+def batched(torch, nbcore, wl, n_systems=256, reps=10):
+    """256 uneven systems (half LJ, half water with PME) in one handle: one force
+    evaluation per step as one CUDA graph, options from the autotuner, against looping
+    the single-system path (one handle per system) over the same systems."""
+    from paper_2503_20541_b300.autotune import autotune
+    from paper_2503_20541_b300.graphs import CapturedStep
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    systems = wl.batched_mix(n_systems)
+    n = sum(s.n for s in systems)
+    xs = [torch.from_numpy(nbcore.pack_xq(s.x, s.q)).cuda() for s in systems]
+    xq = torch.cat(xs)
+    best, table = autotune(systems, xq, evals=3)
+    f = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    e = torch.empty((n_systems, 6), dtype=torch.float64, device="cuda")
+    out = {"systems": n_systems, "atoms": n, "lj_systems": sum(1 for s in systems if s.ke == 0.0),
+           "options": best, "autotune_ms": [[o, t] for o, t in table]}
+    with nbcore.Handle(systems, **best) as h:
+        h.nonbonded_forces(xq, f, e)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(reps):
+            h.nonbonded_forces(xq, f, e)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_eager = e0.elapsed_time(e1) / reps
+        g = CapturedStep(lambda: h.nonbonded_forces(xq, f, e))
+        e2, e3 = ev(), ev()
+        e2.record()
+        for _ in range(reps):
+            g.replay()
+        e3.record()
+        torch.cuda.synchronize()
+        h.check()
+        ms_graph = e2.elapsed_time(e3) / reps
+        del g
+    handles = [nbcore.Handle([s]) for s in systems]
+    try:
+        fs = [torch.empty((s.n, 3), dtype=torch.float32, device="cuda") for s in systems]
+        es = [torch.empty((1, 6), dtype=torch.float64, device="cuda") for _ in systems]
+        for k, hk in enumerate(handles):
+            hk.nonbonded_forces(xs[k], fs[k], es[k])
+        torch.cuda.synchronize()
+        e4, e5 = ev(), ev()
+        e4.record()
+        for _ in range(reps):
+            for k, hk in enumerate(handles):
+                hk.nonbonded_forces(xs[k], fs[k], es[k])
+        e5.record()
+        torch.cuda.synchronize()
+        for hk in handles:
+            hk.check()
+        ms_loop = e4.elapsed_time(e5) / reps
+    finally:
+        for hk in handles:
+            hk.close()
+    out.update({"ms_per_step": ms_graph, "ms_per_step_eager": ms_eager, "ms_per_step_looped": ms_loop,
+                "speedup_vs_looped": ms_loop / ms_graph, "atom_steps_per_s": n / (ms_graph / 1e3),
+                "workload": "256 systems, N log-uniform in [500, 20000] (seed 1234): even index LJ fluid "
+                            "(rho* 0.8442, r_c 2.5, r_skin 0.3), odd index water at 1 g/cm^3 (r_c 9, r_skin "
+                            "2.25, alpha 0.32, PME K = FFT-friendly >= L/0.97 A); step = one force evaluation "
+                            "of every system (list reused), as one CUDA graph; looped = one handle per system, "
+                            "eager launches"})
     return out
 
 

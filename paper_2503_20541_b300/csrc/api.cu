@@ -212,7 +212,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
     std::memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
     if (o.cell_div != 0 && o.cell_div != 1 && o.cell_div != 2) return NB_ERR_ARG;
-    if (o.stencil_tile != 0 && (o.stencil_tile < 256 || o.stencil_tile > 8192 || o.stencil_tile % 64 != 0))
+    if (o.stencil_tile != 0 && (o.stencil_tile < 256 || o.stencil_tile > 4096 || o.stencil_tile % 64 != 0))
         return NB_ERR_ARG;
     if (o.max_neighbors < 0 || o.force_bits < 0 || o.force_bits > 48 || (o.force_bits > 0 && o.force_bits < 8))
         return NB_ERR_ARG;

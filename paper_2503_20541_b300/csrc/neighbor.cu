@@ -504,18 +504,27 @@ void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st) {
                                                             h->ex_slot, h->nbr, h->nbr_cnt, h->flags);
 }
 
+// The dynamic shared-memory limit of a kernel is process-wide, so it is raised once to
+// what the device allows (less the kernel's static shared memory) rather than to one
+// handle's need; each launch still asks only for its own tile.
+template <class K>
+static cudaError_t allow_max_smem(K kernel) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
 cudaError_t build_setup(nb_handle* h) {
-    const int smem = (int)build_smem(h);
-    cudaError_t e = cudaSuccess;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_build_cell<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_build_cell<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_build_cell<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_build_cell<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    }
+    if (build_smem(h) + 4096 > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = allow_max_smem(k_build_cell<0, false>);
+    if (e == cudaSuccess) e = allow_max_smem(k_build_cell<2, false>);
+    if (e == cudaSuccess) e = allow_max_smem(k_build_cell<4, false>);
+    if (e == cudaSuccess) e = allow_max_smem(k_build_cell<4, true>);
     return e;
 }
 

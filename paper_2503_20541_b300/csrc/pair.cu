@@ -731,19 +731,39 @@ static void dispatch(nb_handle* h, int terms, cudaStream_t st, bool vjp) {
 void launch_pair(nb_handle* h, int terms, cudaStream_t st) { dispatch(h, terms, st, false); }
 void launch_vjp(nb_handle* h, int terms, cudaStream_t st) { dispatch(h, terms, st, true); }
 
+// The dynamic shared-memory limit of a kernel is process-wide, so it is raised once to
+// what the device allows (less the kernel's static shared memory) rather than to one
+// handle's need; each launch still asks only for its own tile.
+template <class F>
+static cudaError_t allow_max_smem(F kernel) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
 template <bool LJ, bool COUL>
-static cudaError_t set_smem(const nb_handle* h) {
-    cudaError_t e = cudaFuncSetAttribute(k_pair_cell<LJ, COUL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)pair_smem(h));
+static cudaError_t set_smem() {
+    cudaError_t e = allow_max_smem(k_pair_cell<LJ, COUL>);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_vjp_cell<LJ, COUL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vjp_smem(h));
+    return allow_max_smem(k_vjp_cell<LJ, COUL>);
 }
 
 cudaError_t pair_setup(nb_handle* h) {
-    cudaError_t e = set_smem<true, true>(h);
-    if (e == cudaSuccess) e = set_smem<true, false>(h);
-    if (e == cudaSuccess) e = set_smem<false, true>(h);
-    if (e == cudaSuccess) e = set_smem<false, false>(h);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    // static shared memory of the VJP kernel: queues and runs (~23 KB)
+    if ((long long)vjp_smem(h) + 24 * 1024 > optin) return cudaErrorInvalidValue;
+    e = set_smem<true, true>();
+    if (e == cudaSuccess) e = set_smem<true, false>();
+    if (e == cudaSuccess) e = set_smem<false, true>();
+    if (e == cudaSuccess) e = set_smem<false, false>();
     return e;
 }
 

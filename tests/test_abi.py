@@ -58,7 +58,7 @@ def test_create_rejects_bad_arguments_without_a_gpu():
     st = lib.nb_create(ctypes.byref(h), d, 1, sig.ctypes.data, sig.ctypes.data, None, None, None)
     assert st == 1
     d[0].pme_grid[0] = 0
-    opt = nbcore.Options(0, 12, 0, 0)  # stencil_tile must be a multiple of 64 in [256, 8192]
+    opt = nbcore.Options(0, 12, 0, 0)  # stencil_tile must be a multiple of 64 in [256, 4096]
     st = lib.nb_create(ctypes.byref(h), d, 1, sig.ctypes.data, sig.ctypes.data, None, None, ctypes.byref(opt))
     assert st == 1
 

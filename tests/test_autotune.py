@@ -1,0 +1,64 @@
+"""Host logic of the autotuner (no GPU): candidate sets, expected stencil sizes and the
+selection, with a fake handle factory and a fake timer."""
+import math
+
+import pytest
+
+from paper_2503_20541_b300 import autotune, workloads as wl
+
+
+def test_expected_stencil_matches_density_times_volume():
+    s = wl.lj_random(32000, seed=1)
+    r_nl = s.r_cut + s.r_skin
+    L = float(s.box[0])
+    for cd in (1, 2):
+        nc = math.floor(L * cd / r_nl)
+        want = s.n / L ** 3 * ((2 * cd + 1) * L / nc) ** 3
+        assert autotune.expected_stencil([s], cd) == pytest.approx(want, rel=1e-12)
+    # an axis with fewer than 2 cd + 1 cells contributes its whole length
+    small = wl.lj_random(256, seed=2)
+    assert autotune.expected_stencil([small], 1) == pytest.approx(small.n, rel=1e-12)
+
+
+def test_candidates_cover_both_cell_sizes_with_valid_tiles():
+    c = autotune.candidate_options([wl.water_box(n_side=8, L=24.84)])
+    assert {o["cell_div"] for o in c} == {1, 2}
+    for o in c:
+        t = o.get("stencil_tile", 0)
+        assert t == 0 or (256 <= t <= 4096 and t % 64 == 0)
+
+
+def test_autotune_picks_fastest_and_skips_failures():
+    systems = [wl.lj_random(500, seed=3)]
+    cands = [dict(cell_div=1), dict(cell_div=2), dict(cell_div=2, stencil_tile=512)]
+    times = {(1, 0): 3.0, (2, 0): 2.0, (2, 512): 2.5}
+    made, closed = [], []
+
+    class FakeHandle:
+        def __init__(self, opts):
+            self.opts = opts
+
+        def close(self):
+            closed.append(self.opts)
+
+    def make(systems, **opts):
+        if opts == dict(cell_div=2):
+            made.append(opts)
+            return FakeHandle(opts)
+        if opts.get("stencil_tile") == 512:
+            raise RuntimeError("box too small")
+        made.append(opts)
+        return FakeHandle(opts)
+
+    def timer(h, xq, evals, warmup):
+        return times[(h.opts["cell_div"], h.opts.get("stencil_tile", 0))]
+
+    best, table = autotune.autotune(systems, None, candidates=cands, make_handle=make, timer=timer)
+    assert best == dict(cell_div=2)
+    assert [ms for _, ms in table] == [3.0, 2.0, None]
+    assert len(closed) == len(made) == 2
+
+
+def test_choose_raises_when_nothing_ran():
+    with pytest.raises(RuntimeError):
+        autotune.choose([(dict(cell_div=1), None)])

@@ -338,8 +338,42 @@ def extras(torch, nbcore, wl):
             "pair_kernel_us": 1e3 * kf, "vjp_kernel_us": 1e3 * kb,
             "workload": "differentiable HMC, LJ fluid 2048 atoms x 10 replicas (batched in one handle), "
                         "32 leapfrog steps, checkpoints every 8 (recompute in the backward), switch 2.2-2.5"}
+    out["hmc_training"] = hmc_training(torch, nbcore, wl)
     out["batched"] = batched(torch, nbcore, wl)
     return out
+
+
+def hmc_training(torch, nbcore, wl, iters=200):
+    """Differentiable HMC training: LJ 2048 atoms, 10 replicas, L = 32, checkpoints every
+    8, Adam over (log mu_dt, two mass logits) for 200 iterations, through the
+    torch.autograd.Function over the library's forward and adjoint."""
+    import math
+    from paper_2503_20541_b300 import hmc
+    R = 10
+    systems = []
+    for r in range(R):
+        sr = wl.lj_random(2048, seed=300 + r, n_types=2)
+        sr.r_switch = 2.2
+        systems.append(sr)
+    types = torch.from_numpy(systems[0].types.astype(np.int64)).cuda()
+    x0 = torch.cat([torch.from_numpy(nbcore.pack_xq(x.x, x.q)) for x in systems]).cuda()
+    with nbcore.Handle(systems) as h:
+        hmc.train_esjd(h, x0, types, 2048.0, iters=2, seed=1)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist = hmc.train_esjd(h, x0, types, 2048.0, iters=iters, lr=0.05, log_mu0=math.log(0.002), seed=2)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        h.check()
+    head, tail = hist[:10], hist[-10:]
+    return {"iterations": iters, "iterations_per_s": iters / wall, "wall_s": wall,
+            "esjd_first10": float(np.mean([r["loss"] for r in head])),
+            "esjd_last10": float(np.mean([r["loss"] for r in tail])),
+            "dt_first": hist[0]["mu"], "dt_last": hist[-1]["mu"], "mass_per_type_last": hist[-1]["mass_per_type"],
+            "acceptance_last10": float(np.mean([r["accepted"] for r in tail])),
+            "workload": "LJ fluid 2048 atoms (rho* 0.8442, T* 1, 2 types by index parity, switch 2.2-2.5) x 10 "
+                        "replicas, L = 32 leapfrog steps, checkpoints every 8, folded-normal dt (sigma 0.01 mu), "
+                        "fixed total mass; Adam lr 0.05 from mu = 0.002; one iteration = forward + adjoint"}
 
 
 def batched(torch, nbcore, wl, n_systems=256, reps=10):

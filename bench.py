@@ -338,9 +338,78 @@ def extras(torch, nbcore, wl):
             "pair_kernel_us": 1e3 * kf, "vjp_kernel_us": 1e3 * kb,
             "workload": "differentiable HMC, LJ fluid 2048 atoms x 10 replicas (batched in one handle), "
                         "32 leapfrog steps, checkpoints every 8 (recompute in the backward), switch 2.2-2.5"}
+    out["lj_sweep"] = lj_sweep(torch, nbcore, wl)
     out["hmc_training"] = hmc_training(torch, nbcore, wl)
     out["batched"] = batched(torch, nbcore, wl)
     return out
+
+
+def lj_sweep(torch, nbcore, wl, sizes=(4000, 32000, 256000, 2048000, 8192000), allpairs_max=256000):
+    """LJ fluid scaling sweep (rho* 0.8442, r_c 2.5, r_skin 0.3): the linear cell-list path
+    (force evaluation with the list rebuilt, with the list reused, and velocity-Verlet
+    steps) against the O(N^2) all-pairs kernel on the same GPU, the latter timed up to
+    ``allpairs_max`` atoms and extrapolated as N^2 beyond."""
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(fn, reps):
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    rows = []
+    ap_ref = None
+    for n in sizes:
+        s = wl.lj_random(n, seed=500 + n % 997, kT=1.0)
+        xq = torch.from_numpy(nbcore.pack_xq(s.x, s.q)).cuda()
+        f = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        e = torch.empty((1, 6), dtype=torch.float64, device="cuda")
+        v = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+        v[:, :3] = torch.randn((n, 3), device="cuda", generator=torch.Generator(device="cuda").manual_seed(n))
+        v[:, 3] = 1.0
+        dt = torch.tensor([0.005], dtype=torch.float32, device="cuda")
+        row = {"atoms": n, "box": float(s.box[0])}
+        with nbcore.Handle([s]) as h:
+            # exact pair counts from the list (unordered pairs with r < r_nl, then r < r_c)
+            pairs, n_list = h.nl_build(xq, force_rebuild=True)
+            p = pairs[:n_list].long()
+            d = xq[p[:, 0], :3] - xq[p[:, 1], :3]
+            box = torch.tensor(s.box, dtype=torch.float32, device="cuda")
+            d = d - box * torch.round(d / box)
+            n_cut = int(((d * d).sum(1) < s.r_cut ** 2).sum())
+            del pairs, p, d
+            reps = 20 if n <= 256000 else 5
+            h.nonbonded_forces(xq, f, e, terms=nbcore.NB_TERM_LJ, force_rebuild=True)
+            ms_rebuild = timed(lambda: h.nonbonded_forces(xq, f, e, terms=nbcore.NB_TERM_LJ, force_rebuild=True), reps)
+            ms_reuse = timed(lambda: h.nonbonded_forces(xq, f, e, terms=nbcore.NB_TERM_LJ), reps)
+            h.md_step(xq, v, dt, 5, terms=nbcore.NB_TERM_LJ)
+            torch.cuda.synchronize()
+            c0 = h.rebuild_count()
+            n_md = 50 if n <= 256000 else 10
+            ms_md = timed(lambda: h.md_step(xq, v, dt, n_md, terms=nbcore.NB_TERM_LJ), 1) / n_md
+            rebuilds = h.rebuild_count() - c0
+            if n <= allpairs_max:
+                ms_ap = timed(lambda: h.nonbonded_forces_allpairs(xq, f, e), 3 if n <= 32000 else 1)
+                ap_ref = (n, ms_ap)
+                row["allpairs_ms"] = ms_ap
+            else:
+                row["allpairs_ms_extrapolated"] = ap_ref[1] * (n / ap_ref[0]) ** 2
+            h.check()
+        row.update({"pairs_list": int(n_list), "pairs_cutoff": n_cut, "ms_eval_rebuild": ms_rebuild,
+                    "ms_eval_list_reused": ms_reuse, "ms_per_md_step": ms_md, "md_rebuilds": rebuilds,
+                    "md_steps": n_md, "pairs_per_s_list_reused": n_cut / (ms_reuse / 1e3),
+                    "md_steps_per_s": 1e3 / ms_md})
+        ap = row.get("allpairs_ms", row.get("allpairs_ms_extrapolated"))
+        row["speedup_vs_allpairs"] = ap / ms_reuse
+        rows.append(row)
+        del xq, f, v
+        torch.cuda.empty_cache()
+    return {"rows": rows, "workload": "LJ fluid rho* 0.8442, r_c 2.5, r_skin 0.3 on a jittered FCC subset (stand-in "
+                                      "for FIRE-relaxed random positions), list path vs all-pairs kernel; all-pairs "
+                                      "timed up to %d atoms and extrapolated as N^2 beyond" % allpairs_max}
 
 
 def hmc_training(torch, nbcore, wl, iters=200):

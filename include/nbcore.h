@@ -171,6 +171,19 @@ nb_status nonbonded_forces(nb_handle* h, const float* xq, float* f_out, double* 
                            int32_t terms, void* stream);
 
 /*
+ * All-pairs Lennard-Jones forces and energy: every pair (i, j != i) of each system with
+ * |mi(x_i - x_j)| < r_cut, same LJ terms and switch as nonbonded_forces, but no cell or
+ * Verlet list -- O(N^2) work per system.  It is the comparison baseline of the linear
+ * cell-list path (Sec. 3 compares neighbour-list evaluation against all-pairs); the
+ * list state of the handle is not touched.
+ *   xq [N][4]            (device) positions and charges (caller order; need not be wrapped).
+ *   f_out [N][3]         (device, may be NULL) LJ forces.
+ *   energies [n_sys][6]  (device, may be NULL) FP64 components; only NB_E_LJ is set.
+ * Launches one kernel per system and returns; errors are read with nb_check.
+ */
+nb_status nonbonded_forces_allpairs(nb_handle* h, const float* xq, float* f_out, double* energies, void* stream);
+
+/*
  * PME charge spreading alone (Sec. 2.1.2, smooth PME with order-4 cardinal B-splines):
  *   grid (device) float, for every PME system s the K0*K1*K2 real mesh of system s,
  *   index ((k0 * K1) + k1) * K2 + k2, systems concatenated in system order (systems

@@ -565,6 +565,16 @@ nb_status nonbonded_forces(nb_handle* h, const float* xq, float* f_out, double* 
     return launched();
 }
 
+nb_status nonbonded_forces_allpairs(nb_handle* h, const float* xq, float* f_out, double* energies, void* stream) {
+    if (!h || !xq) return NB_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    launch_allpairs_lj(h, F4(xq), st);
+    if (energies) launch_reduce_energy(h, NB_TERM_LJ, 0, energies, st);
+    if (f_out) launch_finalize_forces(h, f_out, st);
+    return launched();
+}
+
 nb_status pme_spread(nb_handle* h, const float* xq, float* grid, void* stream) {
     if (!h || !xq || !grid) return NB_ERR_ARG;
     DeviceGuard g(h->device);

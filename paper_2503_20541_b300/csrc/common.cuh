@@ -211,6 +211,8 @@ void launch_export_pairs(nb_handle* h, int2* out, long long max_pairs, unsigned 
 void launch_pair(nb_handle* h, int terms, cudaStream_t st);
 void launch_vjp(nb_handle* h, int terms, cudaStream_t st);
 cudaError_t pair_setup(nb_handle* h);
+// allpairs.cu
+void launch_allpairs_lj(nb_handle* h, const float4* xq, cudaStream_t st);
 // pme.cu
 cudaError_t pme_setup(nb_handle* h);
 int launch_pme(nb_handle* h, cudaStream_t st);  // spread + FFT + convolve + FFT + gather into ffix

@@ -18,53 +18,9 @@
 // the force on i is written once, converted to int64 fixed point.  Every FP32
 // summation order is fixed by the list, so results are bitwise reproducible.
 #include "cell.cuh"
+#include "lj.cuh"
 
 namespace nb {
-
-// System constants the pair math needs, held in registers for the whole block.
-struct PairK {
-    float rc2, alpha, ke, rs, inv_sw;
-    int sw;  // LJ switch on
-};
-
-__device__ __forceinline__ PairK pair_k(const SysDev& S) {
-    PairK K;
-    K.rc2 = S.rc2;
-    K.alpha = S.alpha;
-    K.ke = S.ke;
-    K.rs = S.rs;
-    K.inv_sw = S.inv_sw;
-    K.sw = S.has_switch;
-    return K;
-}
-
-// (sigma/r)^2 with sigma^2 carried as an FMA two-product hi + lo: every pair of two given
-// atom types would otherwise share the same rounding of sigma^2, a bias that the
-// 6th/12th powers amplify and that does not average out over the pairs.
-__device__ __forceinline__ float sig2_over_r2(float sig, float r2inv) {
-    float hi = sig * sig;
-    float lo = fmaf(sig, sig, -hi);
-    return fmaf(lo, r2inv, hi * r2inv);
-}
-
-// LJ per unit eps (u, f = -u'/r) with the optional switch; r2inv = 1/r^2.
-__device__ __forceinline__ void lj_unit(float sig, float r2inv, float rinv, float r2, const PairK& K,
-                                        float& u, float& f) {
-    float s2 = sig2_over_r2(sig, r2inv);
-    float s6 = s2 * s2 * s2;
-    u = 4.f * (s6 * s6 - s6);
-    f = 24.f * (2.f * s6 * s6 - s6) * r2inv;
-    if (K.sw) {
-        // x = 0 below r_s gives S = 1, S' = 0 exactly: no branch on r
-        float r = r2 * rinv;
-        float x = fmaxf(0.f, (r - K.rs) * K.inv_sw);
-        float x2 = x * x, x3 = x2 * x;
-        float sw = 1.f + x3 * (-10.f + x * (15.f - 6.f * x));
-        float dsw = x2 * (-30.f + x * (60.f - 30.f * x)) * K.inv_sw;  // dS/dr
-        f = f * sw - u * dsw * rinv;
-        u *= sw;
-    }
-}
 
 constexpr int kPairWarps = 8;
 constexpr int kPairThreads = kPairWarps * 32;

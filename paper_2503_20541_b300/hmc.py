@@ -110,7 +110,7 @@ def train_esjd(h, x0, types, m_total, iters=200, n_leap=32, kT=1.0, ckpt_every=8
         opt.step()
         x = x_new
         rec = {"it": it, "loss": -float(loss.detach()), "mu": float(torch.exp(log_mu.detach())),
-               "alpha": float(alpha.mean()), "accepted": float(acc.mean())}
+               "alpha": float(alpha.detach().mean()), "accepted": float(acc.mean())}
         with torch.no_grad():
             s = torch.exp(logits)
             counts = torch.bincount(types, minlength=n_types).to(s.dtype)

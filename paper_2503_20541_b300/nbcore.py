@@ -31,7 +31,7 @@ STATUS = {
 # Every symbol include/nbcore.h declares.
 EXPORTS = [
     "nb_status_str", "nb_create", "nb_destroy", "nb_num_atoms", "nb_num_systems", "nb_check",
-    "nl_build", "nonbonded_forces", "pme_spread", "pme_gather", "md_step", "hmc_trajectory",
+    "nl_build", "nonbonded_forces", "nonbonded_forces_allpairs", "pme_spread", "pme_gather", "md_step", "hmc_trajectory",
     "hmc_trajectory_backward", "nonbonded_force_vjp", "nb_rebuild_count", "nb_timing_enable", "nb_timing_read",
     "pme_spread_static",
 ]
@@ -104,6 +104,8 @@ def load():
     lib.nl_build.argtypes = [_vp, _vp, _vp, _i64, ctypes.POINTER(_i64), _i32, _vp]
     lib.nonbonded_forces.restype = ctypes.c_int
     lib.nonbonded_forces.argtypes = [_vp, _vp, _vp, _vp, _i32, _vp]
+    lib.nonbonded_forces_allpairs.restype = ctypes.c_int
+    lib.nonbonded_forces_allpairs.argtypes = [_vp, _vp, _vp, _vp, _vp]
     lib.pme_spread.restype = ctypes.c_int
     lib.pme_spread.argtypes = [_vp, _vp, _vp, _vp]
     lib.pme_gather.restype = ctypes.c_int
@@ -300,6 +302,16 @@ class Handle:
             _ptr(f_out, torch.float32, (N, 3), "f_out", True),
             _ptr(energies, torch.float64, (self.n_sys, NB_NE), "energies", True), t, _stream()),
             "nonbonded_forces")
+        return f_out, energies
+
+    def nonbonded_forces_allpairs(self, xq, f_out=None, energies=None):
+        """All-pairs LJ forces (no list): the O(N^2) comparison baseline."""
+        torch = _torch()
+        N = self.n_atoms
+        _ok(self._lib.nonbonded_forces_allpairs(
+            self._h, _ptr(xq, torch.float32, (N, 4), "xq"), _ptr(f_out, torch.float32, (N, 3), "f_out", True),
+            _ptr(energies, torch.float64, (self.n_sys, NB_NE), "energies", True), _stream()),
+            "nonbonded_forces_allpairs")
         return f_out, energies
 
     def pme_spread(self, xq, grid):

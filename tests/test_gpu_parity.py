@@ -366,3 +366,28 @@ def test_error_paths_return_status_without_faulting():
     with pytest.raises(nbcore.NbError) as ei:
         nbcore.Handle([small])
     assert ei.value.status == 2
+
+
+# ---------------------------------------------------------------- all-pairs baseline
+
+def test_allpairs_baseline_matches_oracle_and_list_path():
+    systems = [_jittered_fcc(31), wl.lj_random(1500, seed=32)]
+    systems[1].r_switch = 2.2
+    n = sum(s.n for s in systems)
+    xq = torch.cat([dev_xq(s) for s in systems])
+    fa = torch.empty((n, 3), device="cuda")
+    ea = torch.empty((2, 6), dtype=torch.float64, device="cuda")
+    fl = torch.empty_like(fa)
+    el = torch.empty_like(ea)
+    with nbcore.Handle(systems) as h:
+        h.nonbonded_forces_allpairs(xq, fa, ea)
+        h.nonbonded_forces(xq, fl, el, terms=nbcore.NB_TERM_LJ)
+        h.check()
+    off = 0
+    for k, s in enumerate(systems):
+        eo, fo = oracle_real_space(s)
+        f = fa[off:off + s.n].cpu().numpy().astype(np.float64)
+        assert rel_rms(f, fo) <= F_TOL
+        assert abs(ea[k, 0].item() - eo[0]) <= E_TOL * abs(eo[0])
+        assert rel_rms(f, fl[off:off + s.n].cpu().numpy().astype(np.float64)) <= F_TOL
+        off += s.n

@@ -7,13 +7,15 @@ r_skin = 2.25 A, Ewald alpha = 0.32 / A, PME 64^3 order 4): neighbour-list
 validity test, list rebuild (forced every step, so every row of the path runs),
 fused LJ + Ewald-direct + exclusion pair kernel, PME spread / cuFFT / convolve /
 cuFFT / gather, energy reduction and force output.  Inputs are synthetic and
-resident in HBM; L2 is flushed between timed steps.
+resident in HBM; L2 is flushed between timed steps.  Each step is replayed as one
+CUDA graph of the library calls (the list rebuild is decided on the device, so the
+graph is the deployed form of a step); the per-stage breakdown is from eager calls.
 
 Metric value: pair interactions/s = unordered pairs with r < r_c evaluated per
 second (whole job: summed over replicas when run on N GPUs).  Extra keys report
 MD steps/s (LJ fluid, 864 atoms), the backward/forward time ratio of the
-differentiable HMC step (LJ fluid, 2048 atoms x 10 replicas) and the per-stage
-times.
+differentiable HMC step (LJ fluid, 2048 atoms x 10 replicas), the LJ scaling sweep
+against all-pairs, the HMC training run and the 256-system batch.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -47,7 +49,10 @@ FLOP_COUL_PAIR = 45   # erfc, Gaussian, energy, force
 FLOP_EXCL_PAIR = 45   # erf correction of an excluded pair
 N_SM = 148
 FP32_LANES = 128
-KERNELS_PER_STEP = 16  # our launches per forced-rebuild water evaluation (cuFFT not counted)
+# our launches per forced-rebuild water evaluation (cuFFT not counted): load, bin, scan x3,
+# scatter, cellsort, excl_slots, build_cell, clear_rebuild, pair_cell, spread, grid_convert,
+# convolve, gather, reduce_energy, finalize
+KERNELS_PER_STEP = 17
 
 
 def parse():
@@ -529,70 +534,90 @@ def main():
     xq = torch.from_numpy(nbcore.pack_xq(s.x, s.q)).cuda()
     f = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
     e = torch.empty((1, 6), dtype=torch.float64, device="cuda")
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 126 MB L2
+    # L2 flush between timed steps: write a 256 MB buffer (> 126 MB L2), then read another
+    # 256 MB buffer so that the write-back of the flush's dirty lines is not charged to the
+    # next step; L2 then holds none of the step's data
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    flush_r = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def flush_l2():
+        flush.zero_()
+        flush_r.sum()
+
     h = nbcore.Handle([s])
 
     def step(rebuild=True):
         h.nonbonded_forces(xq, f, e, force_rebuild=rebuild)
 
-    for _ in range(args.warmup):
+    # warm-up: W steps, and at least 2 s of them, so that clocks and memory are in their
+    # loaded state when the timed region starts
+    t_w0 = time.perf_counter()
+    n_w = 0
+    while n_w < args.warmup or time.perf_counter() - t_w0 < 2.0:
+        flush_l2()
         step()
+        n_w += 1
+        if n_w % 50 == 0:
+            torch.cuda.synchronize()
     torch.cuda.synchronize()
     h.check()
     K = args.steps
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    # The step is replayed as a CUDA graph (graphs.CapturedStep): a forced-rebuild step is
+    # ~30 kernel launches, and issued one by one from Python the host's launch rate, not
+    # the GPU, sets its duration.  The per-stage breakdown comes from an eager run below.
+    from paper_2503_20541_b300.graphs import CapturedStep
+    g_step = CapturedStep(lambda: step(True))
+    g_reuse = CapturedStep(lambda: step(False))
+    xq_h = xq.cpu().pin_memory()
+    f_h = torch.empty((s.n, 3), dtype=torch.float32).pin_memory()
+    e_h = torch.empty((1, 6), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        # end to end through the C ABI with host buffers: H2D positions, evaluation,
+        # D2H forces and energies (all inside the graph, executed every replay)
+        xq.copy_(xq_h, non_blocking=True)
+        step(True)
+        f_h.copy_(f, non_blocking=True)
+        e_h.copy_(e, non_blocking=True)
+    g_e2e = CapturedStep(e2e_step)
+
+    def timed(g):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for i in range(K):
+            flush_l2()
+            ev[i][0].record()
+            g.replay()
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        return float(np.mean([x.elapsed_time(y) for x, y in ev]))
+
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     sampler = ClockSampler(vis.split(",")[local] if vis else torch.cuda.current_device())
-    h.timing_enable(True)
-    h.timing_read()
     sampler.start()
     barrier(world)
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
-    for i in range(K):
-        flush.zero_()
-        evs[i][0].record()
-        step()
-        evs[i][1].record()
+    ms_local = timed(g_step)
     torch.cuda.synchronize()
     barrier(world)
     t_wall = time.perf_counter() - t_wall0
+    ms_reuse = timed(g_reuse)
+    ms_e2e = max_over_ranks(timed(g_e2e), world)
     clocks = sampler.stop()
-    stages = h.timing_read()
-    h.timing_enable(False)
     h.check()
-    ms_local = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     ms = max_over_ranks(ms_local, world)
     value = world * pc["cutoff"] / (ms / 1e3)
+    del g_step, g_reuse, g_e2e
 
-    # list reused (the MD-like case between rebuilds)
-    for _ in range(3):
-        step(rebuild=False)
-    torch.cuda.synchronize()
-    evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    # per-stage breakdown (CUDA events between stages) from eager steps
+    h.timing_enable(True)
+    h.timing_read()
     for i in range(K):
-        flush.zero_()
-        evr[i][0].record()
-        step(rebuild=False)
-        evr[i][1].record()
+        flush_l2()
+        step(True)
     torch.cuda.synchronize()
-    ms_reuse = float(np.mean([a.elapsed_time(b) for a, b in evr]))
-
-    # end to end through the C ABI with host buffers: H2D positions, evaluation, D2H forces + energies
-    xq_h = xq.cpu().pin_memory()
-    f_h = torch.empty((s.n, 3), dtype=torch.float32).pin_memory()
-    e_h = torch.empty((1, 6), dtype=torch.float64).pin_memory()
-    eve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    for i in range(K):
-        flush.zero_()
-        eve[i][0].record()
-        xq.copy_(xq_h, non_blocking=True)
-        step()
-        f_h.copy_(f, non_blocking=True)
-        e_h.copy_(e, non_blocking=True)
-        eve[i][1].record()
-    torch.cuda.synchronize()
-    ms_e2e = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in eve])), world)
+    stages = h.timing_read()
+    h.timing_enable(False)
     h.check()
 
     # roofline of the dominant kernel (the fused pair kernel): FP32-pipe ("alu") bound
@@ -607,7 +632,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "atoms": s.n, "pairs": pc, "l2": "flushed between timed steps (256 MB write)",
+        "config": {"workload": WORKLOAD, "atoms": s.n, "pairs": pc, "l2": "flushed between timed steps (256 MB write, then 256 MB read of another buffer)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "wall_s_timed_region": t_wall},
         "roofline": {"bound": "alu", "kernel": "k_pair (fused LJ + Ewald direct + exclusion)", "achieved": achieved,
@@ -615,7 +640,7 @@ def main():
                      "flops_per_launch": fl, "pair_kernel_us": 1e3 * t_pair,
                      "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz (measured "
                                     "during the timed region)" % f_sm},
-        "stage_ms_per_step": {k: v[0] / max(K, 1) for k, v in stages.items()},
+        "stage_ms_per_step_eager": {k: v[0] / max(K, 1) for k, v in stages.items()},
         "ms_per_step_list_reused": ms_reuse,
         "e2e": {"value": world * pc["cutoff"] / (ms_e2e / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(xq.numel() * 4), "d2h_bytes_per_step": int(f.numel() * 4 + e.numel() * 8)},

@@ -95,7 +95,7 @@ typedef struct {
 /* Tuning knobs; zero-initialise for defaults. */
 typedef struct {
     int32_t max_neighbors;   /* per-atom list capacity (full list), rounded up to a multiple
-                                of 32 and to at least 128; 0: from density */
+                                of 128; 0: from density */
     int32_t stencil_tile;    /* stencil candidates per shared-memory tile of the cell kernels
                                 (multiple of 64 in [256, 4096]); 0: auto from the density */
     int32_t cell_div;        /* cells of edge >= r_nl / cell_div, cell_div in {1, 2}; 0: auto */

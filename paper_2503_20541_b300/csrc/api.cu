@@ -261,7 +261,8 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
     h->max_excl = max_excl;
     h->desc.assign(sys, sys + n_systems);
 
-    // tuning defaults from the densest system
+    // tuning defaults from the densest system; the list capacity is a multiple of 128
+    // entries because the pair kernels read rows in 128-entry groups
     double nb_max = 0.0;
     int n_max = 0;
     bool fine_cells = true;
@@ -277,10 +278,10 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
     }
     h->cell_div = o.cell_div ? o.cell_div : (fine_cells ? 2 : 1);
     if (o.max_neighbors > 0) {
-        h->cap = std::max(128, round_up(o.max_neighbors, 32));
+        h->cap = std::max(128, round_up(o.max_neighbors, 128));
     } else {
-        h->cap = round_up((long long)(1.5 * nb_max + 64.0), 32);
-        h->cap = std::max(128, std::min(h->cap, round_up(n_max, 32)));
+        h->cap = round_up((long long)(1.5 * nb_max + 64.0), 128);
+        h->cap = std::max(128, std::min(h->cap, round_up(n_max, 128)));
     }
     h->force_bits = o.force_bits ? o.force_bits : 32;
     h->fscale = std::ldexp(1.0f, h->force_bits);
@@ -430,6 +431,8 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
             NB_TRY(dalloc(h, &h->red_blk_sys, rb_sys.size()));
             NB_TRY(dalloc(h, &h->red_blk_off, rb_off.size()));
             NB_TRY(dalloc(h, &h->red_part, rb_sys.size() * 5));
+            NB_TRY(dalloc(h, &h->red_ticket, 1));
+            NB_TRY(cudaMemset(h->red_ticket, 0, sizeof(unsigned)));
             NB_TRY(cudaMemcpy(h->red_blk_sys, rb_sys.data(), sizeof(int) * rb_sys.size(), cudaMemcpyHostToDevice));
             NB_TRY(cudaMemcpy(h->red_blk_off, rb_off.data(), sizeof(int) * rb_off.size(), cudaMemcpyHostToDevice));
         }

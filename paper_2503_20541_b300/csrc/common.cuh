@@ -118,6 +118,7 @@ struct nb_handle {
     int* red_blk_sys = nullptr;  // [n_red_blocks]
     int* red_blk_off = nullptr;  // [n_sys+1] first reduction block of each system
     double* red_part = nullptr;  // [n_red_blocks * 5] per-block FP64 partial sums
+    unsigned* red_ticket = nullptr;  // [1] blocks of the energy reduction done (reset by the last)
     float* ke_atom = nullptr;    // [N] caller
     // PME
     long long* gfix = nullptr;   // [grid_total]

@@ -24,73 +24,85 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
     return t;  // valid in thread 0
 }
 
-// Energy reduction, stage 1: each block sums kRedTile atoms of one system in FP64.
-__global__ void __launch_bounds__(kRedThreads) k_reduce_part(const int* __restrict__ blk_sys,
-                                                              const int* __restrict__ blk_off,
-                                                              const SysDev* __restrict__ sys,
-                                                              const float4* __restrict__ e_atom,
-                                                              const float4* __restrict__ xs,
-                                                              const float* __restrict__ ke_atom, int with_kin,
-                                                              double* __restrict__ part) {
-    __shared__ double sm[kRedThreads / 32];
-    int b = blockIdx.x;
-    int s = blk_sys[b];
-    const SysDev& S = sys[s];
-    int a0 = S.atom_off + (b - blk_off[s]) * kRedTile;
-    int a1 = min(a0 + kRedTile, S.atom_off + S.n_atoms);
-    double lj = 0.0, dir = 0.0, ex = 0.0, q2 = 0.0, kin = 0.0;
-    for (int k = a0 + threadIdx.x; k < a1; k += kRedThreads) {
-        float4 e = e_atom[k];
-        lj += e.x;
-        dir += e.y;
-        ex += e.z;
-        float q = xs[k].w;
-        q2 += (double)q * q;
-        if (with_kin) kin += ke_atom[k];
-    }
-    lj = block_sum(lj, sm);
-    dir = block_sum(dir, sm);
-    ex = block_sum(ex, sm);
-    q2 = block_sum(q2, sm);
-    kin = block_sum(kin, sm);
-    if (threadIdx.x == 0) {
-        double* o = part + (size_t)b * 5;
-        o[0] = lj;
-        o[1] = dir;
-        o[2] = ex;
-        o[3] = q2;
-        o[4] = kin;
-    }
+// Energy reduction in one launch.  Each block sums kRedTile atoms of one system in FP64
+// (warp shuffles, one barrier) and stores its five partials; the last block to finish
+// (a ticket counter behind a fence) adds, per system and in block order, the partials
+// and the PME block energies.  Both orders are fixed, so the energies are bitwise
+// reproducible; the last block resets the counter, so the kernel replays in a graph.
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
-// Stage 2: one warp per system adds its blocks' partials (fixed order) and the PME blocks.
-__global__ void k_reduce_final(int n_sys, const SysDev* __restrict__ sys, const int* __restrict__ blk_off,
-                               const double* __restrict__ part, const double* __restrict__ e_pme_blk,
-                               const int* __restrict__ pme_blk_off, int terms, int with_kin,
-                               double* __restrict__ dst) {
-    int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int lane = threadIdx.x & 31;
-    if (s >= n_sys) return;
-    const SysDev& S = sys[s];
-    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int b = blk_off[s] + lane; b < blk_off[s + 1]; b += 32)
-        for (int c = 0; c < 5; ++c) acc[c] += part[(size_t)b * 5 + c];
-    if ((terms & NB_TERM_PME) && S.pme && pme_blk_off)
-        for (int b = pme_blk_off[s] + lane; b < pme_blk_off[s + 1]; b += 32) acc[5] += e_pme_blk[b];
+__global__ void __launch_bounds__(kRedThreads) k_reduce_energy(
+    int n_sys, const int* __restrict__ blk_sys, const int* __restrict__ blk_off, const SysDev* __restrict__ sys,
+    const float4* __restrict__ e_atom, const float4* __restrict__ xs, const float* __restrict__ ke_atom,
+    int with_kin, double* __restrict__ part, const double* __restrict__ e_pme_blk,
+    const int* __restrict__ pme_blk_off, int terms, unsigned* __restrict__ ticket, double* __restrict__ dst) {
+    constexpr int kW = kRedThreads / 32;
+    __shared__ double sm[kW][5];
+    __shared__ bool last;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {
+        const int b = blockIdx.x;
+        const int s = blk_sys[b];
+        const SysDev& S = sys[s];
+        const int a0 = S.atom_off + (b - blk_off[s]) * kRedTile;
+        const int a1 = min(a0 + kRedTile, S.atom_off + S.n_atoms);
+        double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int k = a0 + threadIdx.x; k < a1; k += kRedThreads) {
+            const float4 e = e_atom[k];
+            const float q = xs[k].w;
+            v[0] += e.x;
+            v[1] += e.y;
+            v[2] += e.z;
+            v[3] += (double)q * q;
+            if (with_kin) v[4] += ke_atom[k];
+        }
 #pragma unroll
-    for (int c = 0; c < 6; ++c)
+        for (int c = 0; c < 5; ++c) v[c] = warp_sum_d(v[c]);
+        if (lane == 0)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-    if (lane == 0) {
-        bool coul = (terms & NB_TERM_COUL) != 0;
-        double* o = dst + (size_t)s * NB_NE;
-        o[NB_E_LJ] = (terms & NB_TERM_LJ) ? acc[0] : 0.0;
-        o[NB_E_DIR] = coul ? acc[1] : 0.0;
-        o[NB_E_EXCL] = coul ? acc[2] : 0.0;
-        o[NB_E_SELF] = coul ? S.self_coef * acc[3] : 0.0;
-        o[NB_E_REC] = acc[5];
-        o[NB_E_KIN] = with_kin ? acc[4] : 0.0;
+            for (int c = 0; c < 5; ++c) sm[w][c] = v[c];
+        __syncthreads();
+        if (w == 0) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                double t = lane < kW ? sm[lane][c] : 0.0;
+                t = warp_sum_d(t);
+                if (lane == 0) part[(size_t)b * 5 + c] = t;
+            }
+            if (lane == 0) {
+                __threadfence();
+                last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+            }
+        }
+        __syncthreads();
     }
+    if (!last) return;
+    __threadfence();
+    for (int s = w; s < n_sys; s += kW) {
+        const SysDev& S = sys[s];
+        double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int b = blk_off[s] + lane; b < blk_off[s + 1]; b += 32)
+            for (int c = 0; c < 5; ++c) acc[c] += __ldcg(part + (size_t)b * 5 + c);
+        if ((terms & NB_TERM_PME) && S.pme && pme_blk_off)
+            for (int b = pme_blk_off[s] + lane; b < pme_blk_off[s + 1]; b += 32) acc[5] += e_pme_blk[b];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] = warp_sum_d(acc[c]);
+        if (lane == 0) {
+            const bool coul = (terms & NB_TERM_COUL) != 0;
+            double* o = dst + (size_t)s * NB_NE;
+            o[NB_E_LJ] = (terms & NB_TERM_LJ) ? acc[0] : 0.0;
+            o[NB_E_DIR] = coul ? acc[1] : 0.0;
+            o[NB_E_EXCL] = coul ? acc[2] : 0.0;
+            o[NB_E_SELF] = coul ? S.self_coef * acc[3] : 0.0;
+            o[NB_E_REC] = acc[5];
+            o[NB_E_KIN] = with_kin ? acc[4] : 0.0;
+        }
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 __global__ void k_finalize(int N, const long long* __restrict__ ffix, const int* __restrict__ iperm, float finv,
@@ -329,10 +341,9 @@ __global__ void __launch_bounds__(kRedThreads) k_bwd_reduce_h(const SysDev* __re
 // ------------------------------------------------------------------ launchers
 
 void launch_reduce_energy(nb_handle* h, int terms, int with_kin, double* dst, cudaStream_t st) {
-    k_reduce_part<<<h->n_red_blocks, kRedThreads, 0, st>>>(h->red_blk_sys, h->red_blk_off, h->sys, h->e_atom, h->xs,
-                                                          h->ke_atom, with_kin, h->red_part);
-    k_reduce_final<<<cdiv(h->n_sys, 8), 256, 0, st>>>(h->n_sys, h->sys, h->red_blk_off, h->red_part, h->e_pme_blk,
-                                                      h->conv_blk_off, terms, with_kin, dst);
+    k_reduce_energy<<<h->n_red_blocks, kRedThreads, 0, st>>>(h->n_sys, h->red_blk_sys, h->red_blk_off, h->sys,
+                                                            h->e_atom, h->xs, h->ke_atom, with_kin, h->red_part,
+                                                            h->e_pme_blk, h->conv_blk_off, terms, h->red_ticket, dst);
 }
 
 void launch_finalize_forces(nb_handle* h, float* f_out, cudaStream_t st) {

@@ -459,15 +459,26 @@ __global__ void __launch_bounds__(128) k_export_pairs(const int* __restrict__ ce
     if (threadIdx.x < 32) cell_runs(C, S, start, runs, &n_runs, &n_cand, flags);
     __syncthreads();
     const int nr = n_runs;
+    const int lane = threadIdx.x & 31;
     for (int i = C.i0 + (threadIdx.x >> 5); i < C.i1; i += blockDim.x >> 5) {
         const int oi = perm[i];
         const int m = cnt[i];
-        for (int n = threadIdx.x & 31; n < m; n += 32) {
-            const int k = nbr[(size_t)i * cap + n];
-            const BuildRun& R = runs[run_of(runs, nr, k)];
-            const int oj = perm[R.slot0 + (k - R.sm0)];
-            if (oi < oj) {
-                unsigned long long pos = atomicAdd(counter, 1ull);
+        for (int n0 = 0; n0 < m; n0 += 32) {
+            const int n = n0 + lane;
+            int oj = -1;
+            if (n < m) {
+                const int k = nbr[(size_t)i * cap + n];
+                const BuildRun& R = runs[run_of(runs, nr, k)];
+                oj = perm[R.slot0 + (k - R.sm0)];
+            }
+            const bool take = n < m && oi < oj;
+            // one counter update per warp: the lanes' slots follow from the ballot
+            const unsigned b = __ballot_sync(0xffffffffu, take);
+            unsigned long long base = 0;
+            if (lane == 0 && b) base = atomicAdd(counter, (unsigned long long)__popc(b));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (take) {
+                const unsigned long long pos = base + __popc(b & ((1u << lane) - 1u));
                 if (out && (long long)pos < max_pairs) out[pos] = make_int2(oi, oj);
             }
         }

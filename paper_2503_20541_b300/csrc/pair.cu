@@ -176,6 +176,7 @@ struct AtomHdr {
     float2 pi;   // sigma, sqrt(eps)
     int c;       // list length
     uint2 g;     // this lane's four entries of the first 128-entry list group
+    uint2 g2;    // ... and of the second (rows of at least 256 entries)
     int ej;      // lane q < table width: slot of exclusion partner q (-1: none)
     int ne;      // number of exclusion partners
 };
@@ -188,7 +189,10 @@ __device__ __forceinline__ AtomHdr load_hdr(int i, const float4* __restrict__ xs
     H.xr = xs[i];
     H.pi = ps[i];
     H.c = cnt[i];
-    H.g = reinterpret_cast<const uint2*>(nbr + (size_t)i * cap)[lane];  // rows hold cap >= 128 entries
+    const uint2* row2 = reinterpret_cast<const uint2*>(nbr + (size_t)i * cap);
+    // rows hold a multiple of 128 entries, so whole 128-entry groups stay inside the row
+    H.g = row2[lane];
+    H.g2 = cap >= 256 ? row2[32 + lane] : make_uint2(0u, 0u);  // used only when c > 128
     H.ne = (want_excl && X.ew) ? X.cnt[i] : 0;
     H.ej = (want_excl && lane < X.ew) ? X.slot[(size_t)i * X.ew + lane] : -1;
     return H;
@@ -219,11 +223,12 @@ __device__ __forceinline__ void pair_atom(const CellCtx& C, const PairK& K, int 
     // pairs inside r_c wait in a 64-entry ring and are evaluated 32 at a time
     int head = 0, nq = 0;
     // the list is read in groups of 128 entries: lane l holds entries 4l..4l+3 of a group
-    // (one 8-byte load), the next group is loaded while this one is tested
-    uint2 gn = H.g;
+    // (one 8-byte load); groups are loaded two ahead of the one being tested
+    uint2 ga = H.g, gb = H.g2;
     for (int g0 = 0; g0 < c; g0 += 128) {
-        const uint2 gc = gn;
-        if (g0 + 128 < c) gn = row2[(g0 + 128) / 4 + lane];
+        const uint2 gc = ga;
+        ga = gb;
+        if (g0 + 256 < c) gb = row2[(g0 + 256) / 4 + lane];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int k = g0 + 4 * lane + t;
@@ -475,10 +480,13 @@ __device__ __forceinline__ void vjp_atom(const CellCtx& C, const PairK& K, int N
     const float gau_c = 2.f * alpha * kInvSqrtPi;
     VjpAcc A;
     int head = 0, nq = 0;
-    uint2 gn = H.g;
+    // the list is read in groups of 128 entries: lane l holds entries 4l..4l+3 of a group
+    // (one 8-byte load); groups are loaded two ahead of the one being tested
+    uint2 ga = H.g, gb = H.g2;
     for (int g0 = 0; g0 < c; g0 += 128) {
-        const uint2 gc = gn;
-        if (g0 + 128 < c) gn = row2[(g0 + 128) / 4 + lane];
+        const uint2 gc = ga;
+        ga = gb;
+        if (g0 + 256 < c) gb = row2[(g0 + 256) / 4 + lane];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int k = g0 + 4 * lane + t;

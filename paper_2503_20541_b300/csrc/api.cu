@@ -121,15 +121,29 @@ nb_status run_pme(nb_handle* h, cudaStream_t st) {
     return NB_OK;
 }
 
-// Full force evaluation into h->ffix (slot order) and the energy partials.
+// Full force evaluation into h->ffix (slot order) and the energy partials.  The pair
+// kernel and the PME chain are independent once the positions are loaded, so PME runs on
+// the handle's second stream (forked and joined with events; under CUDA-graph capture this
+// becomes a fork/join of the graph) while the latency-bound pair kernel occupies the SMs.
+// Both add their per-atom fixed-point forces into ffix, zeroed first: integer sums, so
+// the result does not depend on which finishes first.
 nb_status eval(nb_handle* h, const float4* xq, int terms, bool force, cudaStream_t st) {
     prepare(h, xq, force, st);
+    cudaMemsetAsync(h->ffix, 0, sizeof(long long) * 3 * (size_t)h->n_atoms, st);
+    const bool pme = (terms & NB_TERM_PME) && h->has_pme;
+    nb_status s = NB_OK;
+    if (pme) {
+        cudaEventRecord(h->ev_fork, st);
+        cudaStreamWaitEvent(h->aux, h->ev_fork, 0);
+        s = run_pme(h, h->aux);
+        cudaEventRecord(h->ev_join, h->aux);
+    }
     {
         Stage sc(h, NB_STAGE_PAIR, st);
         launch_pair(h, terms, st);
     }
-    if ((terms & NB_TERM_PME) && h->has_pme) return run_pme(h, st);
-    return NB_OK;
+    if (pme) cudaStreamWaitEvent(st, h->ev_join, 0);
+    return s;
 }
 
 nb_status launched() { return from_cuda(cudaGetLastError()); }
@@ -461,6 +475,9 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(build_setup(h));
         NB_TRY(pair_setup(h));
         NB_TRY(pme_setup(h));
+        NB_TRY(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+        NB_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        NB_TRY(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
         NB_TRY(cudaMemcpy(h->sys, h->sys_h.data(), sizeof(SysDev) * n_systems, cudaMemcpyHostToDevice));
         NB_TRY(cudaDeviceSynchronize());
     }
@@ -478,6 +495,9 @@ void nb_destroy(nb_handle* h) {
     if (!h) return;
     DeviceGuard g(h->device);
     free_all(h);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->aux) cudaStreamDestroy(h->aux);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : h->ev_used) cudaEventDestroy(e);
     delete h;

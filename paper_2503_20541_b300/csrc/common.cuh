@@ -144,6 +144,9 @@ struct nb_handle {
     float4* xwork = nullptr;     // [N] caller: backward recomputation positions
     double* dhbar = nullptr;     // [n_sys] cotangent of dH
     unsigned long long* counter = nullptr;  // pair export counter
+    // second stream for the PME chain, forked from and joined to the caller's stream
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // optional per-stage CUDA-event timing
     int timing = 0;
     std::vector<cudaEvent_t> ev_pool;

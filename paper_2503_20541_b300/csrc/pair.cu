@@ -14,9 +14,10 @@
 // (both directions of every pair are listed; entries are 16-bit stencil indices), tests
 // r < r_c on 32 entries at a time and appends the pairs inside r_c to a per-warp queue,
 // and the interaction math runs on full warps of queued pairs.  i's data stays in
-// registers, partial sums are reduced with warp shuffles in a fixed tree.  No atomics:
-// the force on i is written once, converted to int64 fixed point.  Every FP32
-// summation order is fixed by the list, so results are bitwise reproducible.
+// registers, partial sums are reduced with warp shuffles in a fixed tree, and the force
+// on i is added once, as int64 fixed point, to the zeroed force array (the PME gather
+// adds its part concurrently; integer addition makes the order irrelevant).  Every
+// FP32 summation order is fixed by the list, so results are bitwise reproducible.
 #include "cell.cuh"
 #include "lj.cuh"
 
@@ -326,9 +327,10 @@ __device__ __forceinline__ void pair_atom(const CellCtx& C, const PairK& K, int 
             }
         }
         if (last) {
-            ffix[i] = to_fix(fx, scale, flags + 1);
-            ffix[(size_t)N + i] = to_fix(fy, scale, flags + 1);
-            ffix[2 * (size_t)N + i] = to_fix(fz, scale, flags + 1);
+            // added (ffix is zeroed per evaluation): the PME gather adds concurrently
+            red_add(ffix + i, to_fix(fx, scale, flags + 1));
+            red_add(ffix + (size_t)N + i, to_fix(fy, scale, flags + 1));
+            red_add(ffix + 2 * (size_t)N + i, to_fix(fz, scale, flags + 1));
             e_atom[i] = make_float4(0.5f * elj, 0.5f * edir, 0.5f * eex, 0.f);
         }
     }

@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(kConvThreads) k_convolve(const int* __restrict
     }
 }
 
-// 16 lanes per atom; mode 0 adds -q grad into ffix (slot order), mode 1 writes f_out (caller order).
+// 16 lanes per atom; mode 0 adds -q grad into ffix (slot order, atomically), mode 1 writes f_out
+// (caller order).
 __global__ void k_gather(int N, const float4* __restrict__ xs, const int* __restrict__ sid,
                          const SysDev* __restrict__ sys, const float* __restrict__ phi,
                          long long* __restrict__ ffix, float* __restrict__ f_out, const int* __restrict__ perm,
@@ -219,9 +220,10 @@ __global__ void k_gather(int N, const float4* __restrict__ xs, const int* __rest
     float fx = -q * k0l * gxs, fy = -q * k1l * gys, fz = -q * k2l * gzs;
     if (mode == 0) {
         if (!pme) return;
-        ffix[ii] += to_fix(fx, scale, flags + 1);
-        ffix[(size_t)N + ii] += to_fix(fy, scale, flags + 1);
-        ffix[2 * (size_t)N + ii] += to_fix(fz, scale, flags + 1);
+        // added atomically: the pair kernel adds its part concurrently
+        red_add(ffix + ii, to_fix(fx, scale, flags + 1));
+        red_add(ffix + (size_t)N + ii, to_fix(fy, scale, flags + 1));
+        red_add(ffix + 2 * (size_t)N + ii, to_fix(fz, scale, flags + 1));
     } else {
         int o = perm[ii];
         f_out[3 * (size_t)o] = fx;

@@ -49,10 +49,10 @@ FLOP_COUL_PAIR = 45   # erfc, Gaussian, energy, force
 FLOP_EXCL_PAIR = 45   # erf correction of an excluded pair
 N_SM = 148
 FP32_LANES = 128
-# our launches per forced-rebuild water evaluation (cuFFT not counted): load, bin, scan x3,
-# scatter, cellsort, excl_slots, build_cell, clear_rebuild, pair_cell, spread, grid_convert,
-# convolve, gather, reduce_energy, finalize
-KERNELS_PER_STEP = 17
+# our launches per forced-rebuild water evaluation (cuFFT not counted): load, bin, scan,
+# scatter, cellsort, build_cell, pair_cell, spread, grid_convert, convolve, gather,
+# reduce_energy, finalize
+KERNELS_PER_STEP = 13
 
 
 def parse():

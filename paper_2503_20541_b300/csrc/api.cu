@@ -96,7 +96,6 @@ void prepare(nb_handle* h, const float4* xq, bool force, cudaStream_t st) {
     }
     Stage sc(h, NB_STAGE_REBUILD, st);
     launch_rebuild(h, xq, st);
-    launch_clear_rebuild(h, st);
 }
 
 nb_status run_pme(nb_handle* h, cudaStream_t st) {
@@ -125,11 +124,10 @@ nb_status run_pme(nb_handle* h, cudaStream_t st) {
 // kernel and the PME chain are independent once the positions are loaded, so PME runs on
 // the handle's second stream (forked and joined with events; under CUDA-graph capture this
 // becomes a fork/join of the graph) while the latency-bound pair kernel occupies the SMs.
-// Both add their per-atom fixed-point forces into ffix, zeroed first: integer sums, so
-// the result does not depend on which finishes first.
+// Both add their per-atom fixed-point forces into ffix (zeroed by k_load): integer sums,
+// so the result does not depend on which finishes first.
 nb_status eval(nb_handle* h, const float4* xq, int terms, bool force, cudaStream_t st) {
     prepare(h, xq, force, st);
-    cudaMemsetAsync(h->ffix, 0, sizeof(long long) * 3 * (size_t)h->n_atoms, st);
     const bool pme = (terms & NB_TERM_PME) && h->has_pme;
     nb_status s = NB_OK;
     if (pme) {
@@ -419,6 +417,8 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(dalloc(h, &h->ffix, 3 * (size_t)N));
         NB_TRY(dalloc(h, &h->e_atom, N));
         NB_TRY(dalloc(h, &h->flags, 4));
+        NB_TRY(dalloc(h, &h->build_ticket, 1));
+        NB_TRY(cudaMemset(h->build_ticket, 0, sizeof(unsigned)));
         NB_TRY(dalloc(h, &h->energy, (size_t)n_systems * NB_NE));
         NB_TRY(dalloc(h, &h->ke_atom, N));
         NB_TRY(dalloc(h, &h->vwork, N));

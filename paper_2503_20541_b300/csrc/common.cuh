@@ -113,6 +113,7 @@ struct nb_handle {
     long long* ffix = nullptr;   // [3N] slot
     float4* e_atom = nullptr;    // [N] slot: half energies (E_lj, E_dir, E_excl, 0) of each atom
     unsigned* flags = nullptr;   // [0] rebuild request, [1] error bits, [2..3] rebuild count (u64)
+    unsigned* build_ticket = nullptr;  // [1] blocks of the list build done (reset by the last)
     double* energy = nullptr;    // [n_sys * NB_NE] scratch
     int n_red_blocks = 0;        // energy reduction: blocks of kRedTile atoms, none straddling systems
     int* red_blk_sys = nullptr;  // [n_red_blocks]
@@ -208,7 +209,6 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 void launch_load(nb_handle* h, const float4* xq, cudaStream_t st);
 void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st);
 cudaError_t build_setup(nb_handle* h);
-void launch_clear_rebuild(nb_handle* h, cudaStream_t st);
 void launch_export_pairs(nb_handle* h, int2* out, long long max_pairs, unsigned long long* counter,
                          cudaStream_t st);
 // pair.cu

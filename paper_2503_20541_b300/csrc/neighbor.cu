@@ -5,7 +5,8 @@
 // last build).  The rebuild chain (bin -> scan -> scatter -> in-cell sort ->
 // Verlet build) is always launched but each kernel returns at once unless the
 // device-side rebuild flag is set, so a step never waits on the host and the
-// whole sequence can be captured in a CUDA graph.
+// whole sequence can be captured in a CUDA graph.  The last block of the Verlet
+// build counts the rebuild and clears the flag.
 //
 // The sort is a counting sort by (system, cell) followed by a rank sort inside
 // each cell on the caller index, so the slot order -- and with it the list and
@@ -17,13 +18,18 @@ namespace nb {
 // Positions stay in the frame of the last build: slot k holds its wrapped build
 // position plus the minimum-image displacement since the build, never re-wrapped, so the
 // stencil images chosen at the build stay valid until the next one.
+// It also zeroes the fixed-point force array, into which the pair kernel and the PME
+// gather of this evaluation add.
 __global__ void k_load(int N, const float4* __restrict__ xq, const int* __restrict__ iperm,
                        const int* __restrict__ sid, const SysDev* __restrict__ sys,
                        const float4* __restrict__ xref, const float4* __restrict__ xsb, float4* __restrict__ xs,
-                       unsigned* flags) {
+                       long long* __restrict__ ffix, unsigned* flags) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool need = false;
     if (i < N) {
+        ffix[i] = 0;
+        ffix[(size_t)N + i] = 0;
+        ffix[2 * (size_t)N + i] = 0;
         float4 p = xq[i];
         const SysDev& S = sys[sid[i]];
         const int k = iperm[i];
@@ -161,6 +167,31 @@ __global__ void __launch_bounds__(1024) k_scan_c(int n, int* start, const int* _
     }
 }
 
+// All three scan steps in one block, for grids of at most kScanTile cells.
+__global__ void __launch_bounds__(1024) k_scan_single(int n, int* count, int* start, int* cursor,
+                                                       const unsigned* flags) {
+    if (flags[0] == 0u) return;
+    __shared__ int tot;
+    int base = threadIdx.x * kScanItems;
+    int v[kScanItems], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < n) ? count[base + k] : 0;
+        s += v[k];
+    }
+    int pre = block_exscan(s, &tot);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) {
+            start[base + k] = pre;
+            count[base + k] = 0;
+            cursor[base + k] = 0;
+        }
+        pre += v[k];
+    }
+    if (threadIdx.x == 0) start[n] = tot;
+}
+
 __global__ void k_scatter(int N, const int* __restrict__ cellid, const int* __restrict__ start,
                           int* cursor, int* __restrict__ perm_tmp, const unsigned* flags) {
     if (flags[0] == 0u) return;
@@ -202,21 +233,6 @@ __global__ void k_cellsort(int n_cells, const int* __restrict__ start, const int
         xsb[slot] = p;
         ps[slot] = params[i];
     }
-}
-
-// Exclusion partners of every atom as slots (slot order, E per atom, -1 padded) and the
-// number of partners, written once per rebuild so that the list build and the pair
-// kernels read them with one load.
-__global__ void k_excl_slots(int N, int E, const int* __restrict__ perm, const int* __restrict__ iperm,
-                             const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
-                             int* __restrict__ ex_slot, int* __restrict__ ex_cnt, const unsigned* flags) {
-    if (flags[0] == 0u) return;
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    int oi = perm[k];
-    int e0 = ex_off[oi], ne = ex_off[oi + 1] - e0;
-    ex_cnt[k] = ne;
-    for (int q = 0; q < E; ++q) ex_slot[(size_t)k * E + q] = q < ne ? iperm[ex_idx[e0 + q]] : -1;
 }
 
 // Predicated 16-bit store: keeps the list append inside one basic block (no branch
@@ -373,17 +389,52 @@ __device__ __forceinline__ void build_tile(const CellCtx& C, int t0, int nt, boo
 }
 
 template <int E, bool SLOW>
+__device__ __forceinline__ void build_cell_body(const CellCtx& C, const SysDev& S, int cap, int tile,
+                                                const int* __restrict__ start, const float4* __restrict__ xs,
+                                                const int* __restrict__ perm, const int* __restrict__ iperm,
+                                                const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
+                                                int* __restrict__ ex_slot, int* __restrict__ ex_cnt,
+                                                unsigned short* __restrict__ nbr, int* __restrict__ nbr_cnt,
+                                                unsigned* flags);
+
+template <int E, bool SLOW>
 __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
     int cap, int tile, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
     const int* __restrict__ start, const float4* __restrict__ xs, const int* __restrict__ perm,
     const int* __restrict__ iperm, const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
-    const int* __restrict__ ex_slot, unsigned short* __restrict__ nbr, int* __restrict__ nbr_cnt,
-    unsigned* flags) {
+    int* __restrict__ ex_slot, int* __restrict__ ex_cnt, unsigned short* __restrict__ nbr,
+    int* __restrict__ nbr_cnt, unsigned* ticket, unsigned* flags) {
     if (flags[0] == 0u) return;
     const int c = blockIdx.x;
     const SysDev& S = sys[cell_sys[c]];
     const CellCtx C = cell_ctx(c, S, start);
-    if (C.i0 == C.i1) return;
+    if (C.i0 != C.i1)
+        build_cell_body<E, SLOW>(C, S, cap, tile, start, xs, perm, iperm, ex_off, ex_idx, ex_slot, ex_cnt, nbr,
+                                 nbr_cnt, flags);
+    // the last block to finish counts the rebuild and clears the request
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        unsigned long long* cnt = reinterpret_cast<unsigned long long*>(flags + 2);
+        *cnt += 1ull;
+        flags[0] = 0u;
+        *ticket = 0u;
+    }
+}
+
+template <int E, bool SLOW>
+__device__ __forceinline__ void build_cell_body(const CellCtx& C, const SysDev& S, int cap, int tile,
+                                                const int* __restrict__ start, const float4* __restrict__ xs,
+                                                const int* __restrict__ perm, const int* __restrict__ iperm,
+                                                const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
+                                                int* __restrict__ ex_slot, int* __restrict__ ex_cnt,
+                                                unsigned short* __restrict__ nbr, int* __restrict__ nbr_cnt,
+                                                unsigned* flags) {
     __shared__ BuildRun runs[kMaxRuns];
     __shared__ int n_runs, n_cand;
     // dynamic: `tile` candidates, then `tile` image-flag bytes when any system can need
@@ -410,6 +461,18 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
             const int a = max(sm0, t0), b = min(sm0 + runs[r].n, t1);
             for (int k = a + lane; k < b; k += 32) cp_async16(&cand[k - t0], &xs[slot0 + (k - sm0)]);
         }
+        if (E > 0 && t0 == 0) {
+            // exclusion partners of this cell's atoms as slots, while the copies are in
+            // flight (read by the tests below and by the pair kernels)
+            const int na = C.i1 - C.i0;
+            for (int idx = threadIdx.x; idx < na * E; idx += kBuildThreads) {
+                const int i = C.i0 + idx / E, q = idx % E;
+                const int oi = perm[i];
+                const int e0 = ex_off[oi], ne = ex_off[oi + 1] - e0;
+                ex_slot[(size_t)i * E + q] = q < ne ? iperm[ex_idx[e0 + q]] : -1;
+                if (q == 0) ex_cnt[i] = ne;
+            }
+        }
         cp_async_wait_all();
         for (int r = w; r < nr; r += kBuildWarps) {
             const BuildRun R = runs[r];
@@ -431,14 +494,6 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
         build_tile<E, SLOW>(C, t0, nt, last, cand, cflag, xs, perm, iperm, ex_off, ex_idx, ex_slot, nbr, nbr_cnt,
                             cap, rnl2, flags);
         if (!last) __syncthreads();
-    }
-}
-
-__global__ void k_clear_rebuild(unsigned* flags) {
-    if (flags[0] != 0u) {
-        unsigned long long* c = reinterpret_cast<unsigned long long*>(flags + 2);
-        *c += 1ull;
-        flags[0] = 0u;
     }
 }
 
@@ -487,7 +542,7 @@ __global__ void __launch_bounds__(128) k_export_pairs(const int* __restrict__ ce
 
 void launch_load(nb_handle* h, const float4* xq, cudaStream_t st) {
     int N = h->n_atoms;
-    k_load<<<cdiv(N, 256), 256, 0, st>>>(N, xq, h->iperm, h->sid, h->sys, h->xref, h->xsb, h->xs, h->flags);
+    k_load<<<cdiv(N, 256), 256, 0, st>>>(N, xq, h->iperm, h->sid, h->sys, h->xref, h->xsb, h->xs, h->ffix, h->flags);
 }
 
 size_t build_smem(const nb_handle* h) { return (size_t)h->tile * (sizeof(float4) + (h->build_gen ? 1 : 0)); }
@@ -495,24 +550,27 @@ size_t build_smem(const nb_handle* h) { return (size_t)h->tile * (sizeof(float4)
 void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st) {
     int N = h->n_atoms;
     k_bin<<<cdiv(N, 256), 256, 0, st>>>(N, xq, h->sid, h->sys, h->cellid, h->cell_count, h->flags);
-    k_scan_a<<<h->n_scan_blocks, 1024, 0, st>>>(h->n_cells, h->cell_count, h->cell_start, h->scan_bsum, h->flags);
-    k_scan_b<<<1, 1024, 0, st>>>(h->n_scan_blocks, h->n_cells, h->scan_bsum, h->cell_start, h->flags);
-    k_scan_c<<<h->n_scan_blocks, 1024, 0, st>>>(h->n_cells, h->cell_start, h->scan_bsum, h->cell_count,
-                                                h->cell_cursor, h->flags);
+    if (h->n_scan_blocks == 1) {
+        k_scan_single<<<1, 1024, 0, st>>>(h->n_cells, h->cell_count, h->cell_start, h->cell_cursor, h->flags);
+    } else {
+        k_scan_a<<<h->n_scan_blocks, 1024, 0, st>>>(h->n_cells, h->cell_count, h->cell_start, h->scan_bsum,
+                                                    h->flags);
+        k_scan_b<<<1, 1024, 0, st>>>(h->n_scan_blocks, h->n_cells, h->scan_bsum, h->cell_start, h->flags);
+        k_scan_c<<<h->n_scan_blocks, 1024, 0, st>>>(h->n_cells, h->cell_start, h->scan_bsum, h->cell_count,
+                                                    h->cell_cursor, h->flags);
+    }
     k_scatter<<<cdiv(N, 256), 256, 0, st>>>(N, h->cellid, h->cell_start, h->cell_cursor, h->perm_tmp, h->flags);
     k_cellsort<<<cdiv((long long)h->n_cells * 32, 256), 256, 0, st>>>(
         h->n_cells, h->cell_start, h->perm_tmp, xq, h->params, h->sid, h->sys, h->perm, h->iperm, h->xs, h->xsb,
         h->ps, h->xref, h->flags);
-    if (h->excl_w)
-        k_excl_slots<<<cdiv(N, 256), 256, 0, st>>>(N, h->excl_w, h->perm, h->iperm, h->ex_off, h->ex_idx,
-                                                   h->ex_slot, h->ex_cnt, h->flags);
     auto build = h->excl_w == 0   ? k_build_cell<0, false>
                  : h->excl_w == 2 ? k_build_cell<2, false>
                  : h->max_excl <= 4 ? k_build_cell<4, false>
                                     : k_build_cell<4, true>;
     build<<<h->n_cells, kBuildThreads, build_smem(h), st>>>(h->cap, h->tile, h->cell_sys, h->sys, h->cell_start,
                                                             h->xs, h->perm, h->iperm, h->ex_off, h->ex_idx,
-                                                            h->ex_slot, h->nbr, h->nbr_cnt, h->flags);
+                                                            h->ex_slot, h->ex_cnt, h->nbr, h->nbr_cnt,
+                                                            h->build_ticket, h->flags);
 }
 
 // The dynamic shared-memory limit of a kernel is process-wide, so it is raised once to
@@ -538,8 +596,6 @@ cudaError_t build_setup(nb_handle* h) {
     if (e == cudaSuccess) e = allow_max_smem(k_build_cell<4, true>);
     return e;
 }
-
-void launch_clear_rebuild(nb_handle* h, cudaStream_t st) { k_clear_rebuild<<<1, 1, 0, st>>>(h->flags); }
 
 void launch_export_pairs(nb_handle* h, int2* out, long long max_pairs, unsigned long long* counter,
                          cudaStream_t st) {

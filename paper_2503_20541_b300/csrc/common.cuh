@@ -75,6 +75,7 @@ struct nb_handle {
     int n_cells = 0;
     int n_scan_blocks = 0;
     int has_pme = 0;
+    int any_coul = 0;   // some system has ke != 0
     long long grid_total = 0, cgrid_total = 0;
     int n_conv_blocks = 0;
 

@@ -25,7 +25,7 @@ namespace nb {
 
 constexpr int kPairWarps = 8;
 constexpr int kPairThreads = kPairWarps * 32;
-constexpr int kVjpWarps = 16;
+constexpr int kVjpWarps = 8;
 constexpr int kVjpThreads = kVjpWarps * 32;
 constexpr int kQueue = 64;  // per-warp queue of pairs inside r_c
 
@@ -122,7 +122,7 @@ __device__ __forceinline__ void pair_heavy(const float4& q, int lq, const float2
         elj = fmaf(eps, u, fmaf(eps_lo, u, elj));
         fr = fmaf(eps_lo, f, eps * f);
     }
-    if (COUL) {
+    if (COUL && K.ke != 0.f) {  // block-uniform: uncharged systems of a mixed batch skip it
         const float r = r2 * rinv;
         const float qq = qke * cand[lq].w;
         const float ar = alpha * r;
@@ -438,7 +438,7 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, co
         A.ge = fmaf(pj.y * f, du, A.ge);
         A.gs = fmaf(0.5f * eps * fs, du, A.gs);
     }
-    if (COUL) {
+    if (COUL && K.ke != 0.f) {  // block-uniform: uncharged systems of a mixed batch skip it
         const float r = r2 * rinv;
         const float qq = K.ke * qi * xjq.w;
         const float ar = alpha * r;
@@ -600,7 +600,9 @@ __device__ __forceinline__ void vjp_atom(const CellCtx& C, const PairK& K, int N
 }
 
 template <bool LJ, bool COUL>
-__global__ void __launch_bounds__(kVjpThreads) k_vjp_cell(
+// LJ-only instantiations are register-bound (small stencils): capped at 64 registers so
+// that four blocks share an SM; with Coulomb (larger staged stencils) two.
+__global__ void __launch_bounds__(kVjpThreads, COUL ? 2 : 4) k_vjp_cell(
     int N, int cap, int tile, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
     const int* __restrict__ start, const float4* __restrict__ xs, const float2* __restrict__ ps,
     const float4* __restrict__ lam, const unsigned short* __restrict__ nbr, const int* __restrict__ cnt,
@@ -687,7 +689,7 @@ static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp) {
 
 static void dispatch(nb_handle* h, int terms, cudaStream_t st, bool vjp) {
     bool lj = (terms & NB_TERM_LJ) != 0;
-    bool coul = (terms & NB_TERM_COUL) != 0;
+    bool coul = (terms & NB_TERM_COUL) != 0 && h->any_coul;  // uncharged systems: LJ-only kernels
     if (lj && coul) pair_launch<true, true>(h, st, vjp);
     else if (lj) pair_launch<true, false>(h, st, vjp);
     else if (coul) pair_launch<false, true>(h, st, vjp);

@@ -53,6 +53,22 @@ FP32_LANES = 128
 # scatter, cellsort, build_cell, pair_cell, spread, grid_convert, convolve, gather,
 # reduce_energy, finalize
 KERNELS_PER_STEP = 13
+MUFU_PER_SM_CLK = 16   # special-function (rsqrt, exp2, rcp) results per SM per clock
+MUFU_COUL_PAIR = 2     # rsqrt + exp per in-cutoff Coulomb pair (algorithmic)
+MUFU_LJ_ONLY_PAIR = 1  # rsqrt (or rcp) per in-cutoff pair without Coulomb
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this machine's B300 (MEASURED_PEAKS.json at the repo root),
+    else the 6.4 TB/s fallback measured earlier on a B300."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+BUILD_BYTES_PER_ATOM = 60  # positions read, cell ids, counts, sorted positions and permutation
+BUILD_BYTES_PER_ENTRY = 2  # one uint16 list entry written per directed pair
 
 
 def parse():
@@ -609,7 +625,9 @@ def main():
     value = world * pc["cutoff"] / (ms / 1e3)
     del g_step, g_reuse, g_e2e
 
-    # per-stage breakdown (CUDA events between stages) from eager steps
+    # per-stage breakdown (CUDA events between stages) from eager steps; the pair kernel's
+    # own duration (for its roofline) from steps without PME, which otherwise shares the
+    # SMs with it on the handle's second stream
     h.timing_enable(True)
     h.timing_read()
     for i in range(K):
@@ -617,16 +635,29 @@ def main():
         step(True)
     torch.cuda.synchronize()
     stages = h.timing_read()
+    for i in range(K):
+        flush_l2()
+        h.nonbonded_forces(xq, f, e, terms=nbcore.NB_TERM_LJ | nbcore.NB_TERM_COUL, force_rebuild=True)
+    torch.cuda.synchronize()
+    stages_rs = h.timing_read()
     h.timing_enable(False)
     h.check()
 
     # roofline of the dominant kernel (the fused pair kernel): FP32-pipe ("alu") bound
-    t_pair = stages["pair"][0] / max(stages["pair"][1], 1)  # ms per launch
+    t_pair = stages_rs["pair"][0] / max(stages_rs["pair"][1], 1)  # ms per launch, kernel alone
     fl = flops_per_launch(pc)
     achieved = fl / (t_pair / 1e3) / 1e12
     f_sm = clocks.get("sm_mhz") or 1920.0
     peak = N_SM * FP32_LANES * 2 * f_sm * 1e6 / 1e12
     traffic = traffic_from_profile(os.path.join(ROOT, "profiles", "pair_kernel_water24k.txt"))
+    mufu_ops = MUFU_COUL_PAIR * pc["cutoff"]
+    mufu_peak = N_SM * MUFU_PER_SM_CLK * f_sm * 1e6
+    # list build chain (bin, scan, scatter, sort, build): the rebuild-forced step less the
+    # list-reused step, against its algorithmic HBM bytes
+    t_build = max(ms - ms_reuse, 1e-6)
+    build_bytes = BUILD_BYTES_PER_ATOM * s.n + BUILD_BYTES_PER_ENTRY * 2 * pc["list"]
+    build_gbs = build_bytes / (t_build / 1e3) / 1e9
+    hbm_gbs, hbm_src = hbm_peak_gbs()
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -639,7 +670,15 @@ def main():
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "flops_per_launch": fl, "pair_kernel_us": 1e3 * t_pair,
                      "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz (measured "
-                                    "during the timed region)" % f_sm},
+                                    "during the timed region)" % f_sm,
+                     "mufu": {"ops_per_launch": mufu_ops, "peak_ops_per_s": mufu_peak,
+                              "us_at_peak": 1e6 * mufu_ops / mufu_peak,
+                              "frac": (mufu_ops / (t_pair / 1e3)) / mufu_peak}},
+        "roofline_build": {"bound": "hbm", "kernel": "list build chain (k_bin .. k_build_cell)",
+                           "achieved": build_gbs, "peak": hbm_gbs, "peak_source": hbm_src, "unit": "GB/s",
+                           "frac": build_gbs / hbm_gbs,
+                           "bytes_per_build": build_bytes, "ms_per_build": t_build,
+                           "note": "issue-bound (FP32 + ALU tests of 2250 candidates per atom), not HBM-bound"},
         "stage_ms_per_step_eager": {k: v[0] / max(K, 1) for k, v in stages.items()},
         "ms_per_step_list_reused": ms_reuse,
         "e2e": {"value": world * pc["cutoff"] / (ms_e2e / 1e3), "unit": UNIT,

@@ -38,6 +38,11 @@ def dbspline(n, u):
     return bspline(n - 1, u) - bspline(n - 1, u - 1.0)
 
 
+def d2bspline(n, u):
+    """d^2 M_n/du^2 = M_{n-2}(u) - 2 M_{n-2}(u - 1) + M_{n-2}(u - 2) (the derivative rule twice)."""
+    return bspline(n - 2, u) - 2.0 * bspline(n - 2, u - 1.0) + bspline(n - 2, u - 2.0)
+
+
 def bspline_moduli(n, K):
     """|b(m)|^2 for m = 0..K-1 (Essmann Eq. 4.4 modulus)."""
     m = np.arange(K)
@@ -60,6 +65,94 @@ def _weights(x, box, K, n):
     w = bspline(n, t)
     dw = dbspline(n, t) * (K / L)[None, :, None]
     return idx, w, dw
+
+
+def _weights2(x, box, K, n):
+    """As _weights, plus second derivatives d^2 weights / dx^2 (N,3,n)."""
+    L = np.asarray(box, dtype=np.float64)
+    xw = x - L * np.floor(x / L)
+    u = xw / L * K
+    fl = np.floor(u)
+    fr = u - fl
+    j = np.arange(n)
+    idx = (fl[:, :, None].astype(np.int64) - j[None, None, :]) % K[None, :, None]
+    t = fr[:, :, None] + j[None, None, :]
+    s = (K / L)[None, :, None]
+    return idx, bspline(n, t), dbspline(n, t) * s, d2bspline(n, t) * s * s
+
+
+def _green(K, L, alpha, ke, n):
+    V = float(np.prod(L))
+    m = [np.fft.fftfreq(int(K[d])) * K[d] / L[d] for d in range(3)]
+    m2 = m[0][:, None, None] ** 2 + m[1][None, :, None] ** 2 + m[2][None, None, :] ** 2
+    B = (bspline_moduli(n, int(K[0]))[:, None, None] * bspline_moduli(n, int(K[1]))[None, :, None]
+         * bspline_moduli(n, int(K[2]))[None, None, :])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        G = ke / (np.pi * V) * np.exp(-np.pi ** 2 * m2 / alpha ** 2) / m2 * B
+    G[0, 0, 0] = 0.0
+    return G
+
+
+def pme_force_vjp(x, q, box, alpha, ke, K, lam, order=4):
+    """Vector-Jacobian product of the reciprocal-space forces (the NEXT row of the force
+    VJP): with F_i = -q_i sum_k grad theta_i(k) phi(k), phi = C Q (C the symmetric
+    convolution of step 5), returns gx_j = d(lam . F)/dx_j and gq_j = d(lam . F)/dq_j:
+
+      lam . F = -<psi, phi>,  psi(k) = sum_i q_i lam_i . grad theta_i(k)
+      gx_j = -q_j sum_k (Hess theta_j(k) lam_j) phi(k) - q_j sum_k grad theta_j(k) chi(k)
+      gq_j = -sum_k (lam_j . grad theta_j(k)) phi(k) - sum_k theta_j(k) chi(k),  chi = C psi.
+    """
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    q = np.asarray(q, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.float64).reshape(-1, 3)
+    L = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
+    K = np.broadcast_to(np.asarray(K, dtype=np.int64), (3,)).copy()
+    n = order
+    idx, w, dw, d2w = _weights2(x, L, K, n)
+    G = _green(K, L, alpha, ke, n)
+    scale = float(np.prod(K))
+
+    def conv(M):
+        return np.real(np.fft.ifftn(G * np.fft.fftn(M))) * scale
+    Q = np.zeros(tuple(K))
+    psi = np.zeros(tuple(K))
+    N = x.shape[0]
+    for a in range(n):
+        for b in range(n):
+            for c in range(n):
+                ii = (idx[:, 0, a], idx[:, 1, b], idx[:, 2, c])
+                th = w[:, 0, a] * w[:, 1, b] * w[:, 2, c]
+                gth = np.stack([dw[:, 0, a] * w[:, 1, b] * w[:, 2, c], w[:, 0, a] * dw[:, 1, b] * w[:, 2, c],
+                                w[:, 0, a] * w[:, 1, b] * dw[:, 2, c]], axis=1)
+                np.add.at(Q, ii, q * th)
+                np.add.at(psi, ii, q * np.sum(lam * gth, axis=1))
+    phi = conv(Q)
+    chi = conv(psi)
+    gx = np.zeros((N, 3))
+    gq = np.zeros(N)
+    for a in range(n):
+        for b in range(n):
+            for c in range(n):
+                ii = (idx[:, 0, a], idx[:, 1, b], idx[:, 2, c])
+                p, h = phi[ii], chi[ii]
+                W = [w[:, 0, a], w[:, 1, b], w[:, 2, c]]
+                D = [dw[:, 0, a], dw[:, 1, b], dw[:, 2, c]]
+                D2 = [d2w[:, 0, a], d2w[:, 1, b], d2w[:, 2, c]]
+                th = W[0] * W[1] * W[2]
+                gth = np.stack([D[0] * W[1] * W[2], W[0] * D[1] * W[2], W[0] * W[1] * D[2]], axis=1)
+                H = np.empty((N, 3, 3))
+                for d in range(3):
+                    for e in range(3):
+                        f = [W[0], W[1], W[2]]
+                        if d == e:
+                            f[d] = D2[d]
+                        else:
+                            f[d] = D[d]
+                            f[e] = D[e]
+                        H[:, d, e] = f[0] * f[1] * f[2]
+                gx -= q[:, None] * (np.einsum("nde,ne->nd", H, lam) * p[:, None] + gth * h[:, None])
+                gq -= np.sum(lam * gth, axis=1) * p + th * h
+    return gx, gq
 
 
 def pme(x, q, box, alpha, ke, K, order=4, return_grid=False):

@@ -427,3 +427,38 @@ def test_oracle_and_library_share_no_code():
         for fn in files:
             if fn.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
                 assert not pat_p.search(open(os.path.join(dirpath, fn)).read()), fn
+
+
+def test_pme_force_vjp_matches_central_differences_and_is_symmetric():
+    """The reciprocal-space force VJP: d(lam . F_rec)/dx and /dq by FP64 central
+    differences of the forward PME forces, and <h, VJP(g)> = <g, VJP(h)> (the position
+    Hessian of E_rec is symmetric)."""
+    from oracle import pme as opme
+    rng = np.random.default_rng(7)
+    n, L, K = 24, np.array([9.0, 9.0, 9.0]), (12, 12, 12)
+    x = rng.uniform(0, 9.0, (n, 3))
+    q = rng.uniform(-1, 1, n)
+    q -= q.mean()
+    alpha, ke = 0.45, 1.0
+    lam = rng.standard_normal((n, 3))
+    gx, gq = opme.pme_force_vjp(x, q, L, alpha, ke, K, lam)
+
+    def lf(xx, qq):
+        return float(np.sum(lam * opme.pme(xx, qq, L, alpha, ke, K)[1]))
+    h = 1e-5
+    for i in (0, 5, 17):
+        for d in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, d] += h
+            xm[i, d] -= h
+            fd = (lf(xp, q) - lf(xm, q)) / (2 * h)
+            assert abs(gx[i, d] - fd) <= 1e-6 * (1.0 + abs(fd)), (i, d, gx[i, d], fd)
+        qp, qm = q.copy(), q.copy()
+        qp[i] += h
+        qm[i] -= h
+        fd = (lf(x, qp) - lf(x, qm)) / (2 * h)
+        assert abs(gq[i] - fd) <= 1e-6 * (1.0 + abs(fd)), (i, gq[i], fd)
+    g2 = rng.standard_normal((n, 3))
+    gx2, _ = opme.pme_force_vjp(x, q, L, alpha, ke, K, g2)
+    a, b = float(np.sum(g2 * gx)), float(np.sum(lam * gx2))
+    assert abs(a - b) <= 1e-10 * (abs(a) + abs(b))

@@ -249,8 +249,8 @@ nb_status hmc_trajectory(nb_handle* h, const float* x0, float* x_out, const floa
  * call with the same arguments) and applying the force VJP at every state.
  *   stats            (device) the forward call's stats.
  * The first call with a given ckpt_every allocates a segment buffer of
- * 3 (ckpt_every + 1) N float4.  Returns NB_ERR_ARG when `terms` includes PME for a
- * handle with PME systems (the reciprocal-space VJP is not provided).
+ * 3 (ckpt_every + 1) N float4.  With NB_TERM_PME the reciprocal-space VJP is applied
+ * at every state as well.
  */
 nb_status hmc_trajectory_backward(nb_handle* h, const float* x0, const float* inv_mass,
                                   const float* dt, int32_t n_leap, double kT, const float* xi,
@@ -259,17 +259,21 @@ nb_status hmc_trajectory_backward(nb_handle* h, const float* x0, const float* in
                                   double* g_dt, float* g_inv_mass, int32_t terms, void* stream);
 
 /*
- * Force vector-Jacobian product of the real-space terms (LJ, Ewald direct, exclusion
- * correction): for a cotangent lam [N][3],
+ * Force vector-Jacobian product (Sec. 4 differentiates the trajectory through the
+ * forces): for a cotangent lam [N][3] and the terms selected by `terms` (NB_TERM_*),
  *   gx = (dF/dx)^T lam           (a Hessian-vector product of -E),
  *   gq, gsigma, gsqrt_eps        gradients of lam . F with respect to q_i, sigma_i and
  *                                sqrt(eps_i) (each may be NULL),
  *   f_out                        the forces F at xq (may be NULL).
- * All outputs are overwritten, (device) FP32.  PME reciprocal space is not included.
+ * Real space (LJ, Ewald direct, exclusion correction) in one pass over the list; with
+ * NB_TERM_PME the reciprocal part: with psi(k) = sum_i q_i lam_i . grad theta_i(k) spread
+ * on a second mesh and chi = C psi (C the PME convolution),
+ *   gx_j -= q_j sum_k (Hess theta_j(k) lam_j) phi(k) + q_j sum_k grad theta_j(k) chi(k),
+ *   gq_j -= sum_k (lam_j . grad theta_j(k)) phi(k) + sum_k theta_j(k) chi(k).
+ * All outputs are overwritten, (device) FP32.
  */
-nb_status nonbonded_force_vjp(nb_handle* h, const float* xq, const float* lam, float* gx,
-                              float* gq, float* gsigma, float* gsqrt_eps, float* f_out,
-                              void* stream);
+nb_status nonbonded_force_vjp(nb_handle* h, const float* xq, const float* lam, float* gx, float* gq,
+                              float* gsigma, float* gsqrt_eps, float* f_out, int32_t terms, void* stream);
 
 /*
  * PME charge spreading without any device allocation.  The paper has no counterpart:

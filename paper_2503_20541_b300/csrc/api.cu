@@ -685,7 +685,6 @@ nb_status hmc_trajectory_backward(nb_handle* h, const float* x0, const float* in
         n_leap < 1 || ckpt_every < 1 || !(kT > 0.0))
         return NB_ERR_ARG;
     int t = terms & NB_TERM_ALL;
-    if ((t & NB_TERM_PME) && h->has_pme) return NB_ERR_ARG;  // reciprocal-space VJP not provided
     DeviceGuard g(h->device);
     cudaStream_t st = S(stream);
     int N = h->n_atoms;
@@ -733,6 +732,7 @@ nb_status hmc_trajectory_backward(nb_handle* h, const float* x0, const float* in
                 Stage sc(h, NB_STAGE_PAIR, st);
                 launch_vjp(h, t, st);
             }
+            if ((t & NB_TERM_PME) && h->has_pme && launch_pme_vjp(h, st)) return NB_ERR_CUDA;
             launch_bwd_adjoint(h, inv_mass, dt, cf, state == n_leap, seg_p(q), g_inv_mass, st);
         }
     }
@@ -743,16 +743,21 @@ nb_status hmc_trajectory_backward(nb_handle* h, const float* x0, const float* in
 }
 
 nb_status nonbonded_force_vjp(nb_handle* h, const float* xq, const float* lam, float* gx, float* gq, float* gsigma,
-                              float* gsqrt_eps, float* f_out, void* stream) {
+                              float* gsqrt_eps, float* f_out, int32_t terms, void* stream) {
     if (!h || !xq || !lam || !gx) return NB_ERR_ARG;
     DeviceGuard g(h->device);
     cudaStream_t st = S(stream);
     int N = h->n_atoms;
+    const int t = terms & NB_TERM_ALL;
     prepare(h, F4(xq), false, st);
     k_lam_scatter<<<cdiv(N, 256), 256, 0, st>>>(N, lam, h->iperm, h->lam);
     {
         Stage sc(h, NB_STAGE_PAIR, st);
-        launch_vjp(h, NB_TERM_LJ | NB_TERM_COUL, st);
+        launch_vjp(h, t & (NB_TERM_LJ | NB_TERM_COUL), st);
+    }
+    if ((t & NB_TERM_PME) && h->has_pme) {
+        Stage sc(h, NB_STAGE_GATHER, st);
+        if (launch_pme_vjp(h, st)) return NB_ERR_CUDA;
     }
     Stage sc(h, NB_STAGE_UPDATE, st);
     k_vjp_out<<<cdiv(N, 256), 256, 0, st>>>(N, h->gx_s, h->gp_s, h->iperm, gx, gq, gsigma, gsqrt_eps);

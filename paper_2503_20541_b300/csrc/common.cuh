@@ -125,6 +125,9 @@ struct nb_handle {
     // PME
     long long* gfix = nullptr;   // [grid_total]
     float* grid = nullptr;       // [grid_total]
+    float* grid2 = nullptr;      // [grid_total] second mesh of the reciprocal VJP
+    unsigned* lam_max = nullptr; // [1] largest |lam| (float bits) of a VJP call
+    float kl_max = 0.f;          // largest K/L over the PME systems
     float2* cgrid = nullptr;     // [cgrid_total]
     float* green = nullptr;      // [cgrid_total] influence function G(m)
     int* conv_blk_sys = nullptr; // [n_conv_blocks]
@@ -221,6 +224,7 @@ void launch_allpairs_lj(nb_handle* h, const float4* xq, cudaStream_t st);
 // pme.cu
 cudaError_t pme_setup(nb_handle* h);
 int launch_pme(nb_handle* h, cudaStream_t st);  // spread + FFT + convolve + FFT + gather into ffix
+int launch_pme_vjp(nb_handle* h, cudaStream_t st);  // launch_pme, then the reciprocal VJP into gx_s
 void launch_pme_spread(nb_handle* h, cudaStream_t st);
 int launch_pme_fft(nb_handle* h, int inverse, cudaStream_t st);
 void launch_pme_convolve(nb_handle* h, cudaStream_t st);

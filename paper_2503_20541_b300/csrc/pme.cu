@@ -11,6 +11,7 @@
 // cuFFT performs the 3-D transforms (one batched plan per distinct mesh shape).
 #include <math.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -155,6 +156,7 @@ __global__ void __launch_bounds__(kConvThreads) k_convolve(const int* __restrict
             cgrid[S.cgrid_off + c] = make_float2(q.x * g, q.y * g);
         }
     }
+    if (!e_blk) return;  // convolution only (the VJP's second mesh)
     double v = (double)acc;
     __shared__ double red[kConvThreads / 32];
 #pragma unroll
@@ -294,11 +296,17 @@ cudaError_t pme_setup(nb_handle* h) {
     cudaError_t e;
     if ((e = alloc((void**)&h->gfix, sizeof(long long) * goff)) != cudaSuccess) return e;
     if ((e = alloc((void**)&h->grid, sizeof(float) * goff)) != cudaSuccess) return e;
+    if ((e = alloc((void**)&h->grid2, sizeof(float) * goff)) != cudaSuccess) return e;
+    if ((e = alloc((void**)&h->lam_max, sizeof(unsigned))) != cudaSuccess) return e;
     if ((e = alloc((void**)&h->cgrid, sizeof(float2) * coff)) != cudaSuccess) return e;
     if ((e = alloc((void**)&h->green, sizeof(float) * coff)) != cudaSuccess) return e;
     if ((e = alloc((void**)&h->conv_blk_sys, sizeof(int) * blk_sys.size())) != cudaSuccess) return e;
     if ((e = alloc((void**)&h->conv_blk_off, sizeof(int) * blk_off.size())) != cudaSuccess) return e;
     if ((e = alloc((void**)&h->e_pme_blk, sizeof(double) * blk_sys.size())) != cudaSuccess) return e;
+    h->kl_max = 0.f;
+    for (int s = 0; s < h->n_sys; ++s)
+        if (h->sys_h[s].pme)
+            for (int d = 0; d < 3; ++d) h->kl_max = std::max(h->kl_max, h->sys_h[s].kl_hi[d]);
     cudaMemset(h->gfix, 0, sizeof(long long) * goff);
     cudaMemset(h->grid, 0, sizeof(float) * goff);
     cudaMemset(h->green, 0, sizeof(float) * coff);
@@ -335,22 +343,24 @@ static void spread(nb_handle* h, cudaStream_t st) {
 
 void launch_pme_spread(nb_handle* h, cudaStream_t st) { spread(h, st); }
 
-int launch_pme_fft(nb_handle* h, int inverse, cudaStream_t st) {
+static int fft_on(nb_handle* h, float* mesh, int inverse, cudaStream_t st) {
     for (auto& g : h->fft) {
         if (!inverse) {
             cufftSetStream(g.r2c, st);
-            if (cufftExecR2C(g.r2c, h->grid + g.grid_off, reinterpret_cast<cufftComplex*>(h->cgrid + g.cgrid_off)) !=
+            if (cufftExecR2C(g.r2c, mesh + g.grid_off, reinterpret_cast<cufftComplex*>(h->cgrid + g.cgrid_off)) !=
                 CUFFT_SUCCESS)
                 return 1;
         } else {
             cufftSetStream(g.c2r, st);
-            if (cufftExecC2R(g.c2r, reinterpret_cast<cufftComplex*>(h->cgrid + g.cgrid_off), h->grid + g.grid_off) !=
+            if (cufftExecC2R(g.c2r, reinterpret_cast<cufftComplex*>(h->cgrid + g.cgrid_off), mesh + g.grid_off) !=
                 CUFFT_SUCCESS)
                 return 1;
         }
     }
     return 0;
 }
+
+int launch_pme_fft(nb_handle* h, int inverse, cudaStream_t st) { return fft_on(h, h->grid, inverse, st); }
 
 void launch_pme_convolve(nb_handle* h, cudaStream_t st) {
     k_convolve<<<h->n_conv_blocks, kConvThreads, 0, st>>>(h->conv_blk_sys, h->conv_blk_off, h->sys, h->cgrid,
@@ -361,6 +371,178 @@ void launch_pme_gather(nb_handle* h, cudaStream_t st) {
     int N = h->n_atoms;
     k_gather<<<cdiv((long long)N * 16, 256), 256, 0, st>>>(N, h->xs, h->sid, h->sys, h->grid, h->ffix, nullptr,
                                                            h->perm, h->fscale, 0, h->flags);
+}
+
+// ---------------------------------------------------------------- reciprocal-space VJP
+// With F_i = -q_i sum_k grad theta_i(k) phi(k) and phi = C Q (C the symmetric convolution
+// with G), lam . F = -<psi, phi> where psi(k) = sum_i q_i lam_i . grad theta_i(k).  Then
+//   d(lam . F)/dx_j = -q_j sum_k (Hess theta_j(k) lam_j) phi(k) - q_j sum_k grad theta_j(k) chi(k)
+//   d(lam . F)/dq_j = -sum_k (lam_j . grad theta_j(k)) phi(k) - sum_k theta_j(k) chi(k)
+// with chi = C psi: psi is spread like Q (int64 fixed point, scale 2^32 over the largest
+// |lam| K/L, a power of two), convolved on a second mesh, and both meshes are gathered.
+
+// Second derivatives of the order-4 pieces (u units): the cubic weights differentiated twice.
+__device__ __forceinline__ void bspline4_d2(float t, float d2[4]) {
+    d2[0] = t;
+    d2[1] = 1.f - 3.f * t;
+    d2[2] = 3.f * t - 2.f;
+    d2[3] = 1.f - t;
+}
+
+__global__ void k_absmax(int N, const float4* __restrict__ lam, unsigned* __restrict__ out) {
+    float m = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const float4 l = lam[i];
+        m = fmaxf(m, fmaxf(fabsf(l.x), fmaxf(fabsf(l.y), fabsf(l.z))));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // non-negative floats order as integers
+}
+
+// 2^32 over the largest |lam| K/L, rounded down to a power of two (so the round trip of
+// the fixed-point mesh is exact in its scale).
+__device__ __forceinline__ float psi_scale(const unsigned* lam_max, float kl_max) {
+    const float m = fmaxf(__uint_as_float(*lam_max) * kl_max, 1e-30f);
+    return ldexpf(1.f, 31 - ilogbf(m));
+}
+
+__global__ void k_spread_vjp(int N, const float4* __restrict__ xs, const float4* __restrict__ lam,
+                             const int* __restrict__ sid, const SysDev* __restrict__ sys,
+                             long long* __restrict__ gfix, const unsigned* __restrict__ lam_max, float kl_max) {
+    int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = gt >> 4, sub = gt & 15;
+    if (i >= N) return;
+    const SysDev& S = sys[sid[i]];
+    if (!S.pme) return;
+    const float vs = psi_scale(lam_max, kl_max);
+    const float4 p = xs[i];
+    const float4 l = lam[i];
+    int K0 = S.K[0], K1 = S.K[1], K2 = S.K[2];
+    int f0, f1, f2;
+    float t0, t1, t2;
+    frac_coord(p.x, K0, S.kl_hi[0], S.kl_lo[0], f0, t0);
+    frac_coord(p.y, K1, S.kl_hi[1], S.kl_lo[1], f1, t1);
+    frac_coord(p.z, K2, S.kl_hi[2], S.kl_lo[2], f2, t2);
+    float w0[4], w1[4], w2[4], d0[4], d1[4], d2[4];
+    bspline4(t0, w0, d0);
+    bspline4(t1, w1, d1);
+    bspline4(t2, w2, d2);
+    const float lu0 = l.x * S.kl_hi[0], lu1 = l.y * S.kl_hi[1], lu2 = l.z * S.kl_hi[2];  // lam in u units
+    int a = sub >> 2, b = sub & 3;
+    int ix = wrapk(f0 - a, K0), iy = wrapk(f1 - b, K1);
+    long long* g = gfix + S.grid_off + ((long long)ix * K1 + iy) * K2;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float wv = lu0 * d0[a] * w1[b] * w2[c] + lu1 * w0[a] * d1[b] * w2[c] + lu2 * w0[a] * w1[b] * d2[c];
+        red_add(g + wrapk(f2 - c, K2), __float2ll_rn(p.w * wv * vs));
+    }
+}
+
+__global__ void k_grid_convert_dyn(long long n, long long* __restrict__ gfix, float* __restrict__ grid,
+                                   const unsigned* __restrict__ lam_max, float kl_max) {
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double inv = 1.0 / (double)psi_scale(lam_max, kl_max);
+    grid[k] = (float)((double)gfix[k] * inv);
+    gfix[k] = 0;
+}
+
+// 16 lanes per atom as in k_gather; adds (gx, gq) to the slot-order VJP output.
+__global__ void k_gather_vjp(int N, const float4* __restrict__ xs, const float4* __restrict__ lam,
+                             const int* __restrict__ sid, const SysDev* __restrict__ sys,
+                             const float* __restrict__ phi, const float* __restrict__ chi,
+                             float4* __restrict__ gx_s) {
+    int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = gt >> 4, sub = gt & 15;
+    bool valid = i < N;
+    int ii = valid ? i : N - 1;
+    const SysDev& S = sys[sid[ii]];
+    bool pme = valid && S.pme;
+    float A[3] = {0.f, 0.f, 0.f}, B[3] = {0.f, 0.f, 0.f}, c1 = 0.f, c2 = 0.f;
+    float q = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    if (pme) {
+        const float4 p = xs[ii];
+        const float4 l = lam[ii];
+        q = p.w;
+        s0 = S.kl_hi[0];
+        s1 = S.kl_hi[1];
+        s2 = S.kl_hi[2];
+        int K0 = S.K[0], K1 = S.K[1], K2 = S.K[2];
+        int f0, f1, f2;
+        float t0, t1, t2;
+        frac_coord(p.x, K0, S.kl_hi[0], S.kl_lo[0], f0, t0);
+        frac_coord(p.y, K1, S.kl_hi[1], S.kl_lo[1], f1, t1);
+        frac_coord(p.z, K2, S.kl_hi[2], S.kl_lo[2], f2, t2);
+        float w0[4], w1[4], w2[4], d0[4], d1[4], d2[4], e0[4], e1[4], e2[4];
+        bspline4(t0, w0, d0);
+        bspline4(t1, w1, d1);
+        bspline4(t2, w2, d2);
+        bspline4_d2(t0, e0);
+        bspline4_d2(t1, e1);
+        bspline4_d2(t2, e2);
+        const float lu0 = l.x * s0, lu1 = l.y * s1, lu2 = l.z * s2;
+        int a = sub >> 2, b = sub & 3;
+        int ix = wrapk(f0 - a, K0), iy = wrapk(f1 - b, K1);
+        const long long row = S.grid_off + ((long long)ix * K1 + iy) * K2;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const long long k = row + wrapk(f2 - c, K2);
+            const float pv = __ldg(phi + k), hv = __ldg(chi + k);
+            const float th = w0[a] * w1[b] * w2[c];
+            const float g0 = d0[a] * w1[b] * w2[c], g1 = w0[a] * d1[b] * w2[c], g2 = w0[a] * w1[b] * d2[c];
+            const float h01 = d0[a] * d1[b] * w2[c], h02 = d0[a] * w1[b] * d2[c], h12 = w0[a] * d1[b] * d2[c];
+            const float hx = e0[a] * w1[b] * w2[c] * lu0 + h01 * lu1 + h02 * lu2;
+            const float hy = h01 * lu0 + w0[a] * e1[b] * w2[c] * lu1 + h12 * lu2;
+            const float hz = h02 * lu0 + h12 * lu1 + w0[a] * w1[b] * e2[c] * lu2;
+            A[0] = fmaf(hx, pv, A[0]);
+            A[1] = fmaf(hy, pv, A[1]);
+            A[2] = fmaf(hz, pv, A[2]);
+            B[0] = fmaf(g0, hv, B[0]);
+            B[1] = fmaf(g1, hv, B[1]);
+            B[2] = fmaf(g2, hv, B[2]);
+            c1 = fmaf(lu0 * g0 + lu1 * g1 + lu2 * g2, pv, c1);
+            c2 = fmaf(th, hv, c2);
+        }
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            A[d] += __shfl_xor_sync(0xffffffffu, A[d], o);
+            B[d] += __shfl_xor_sync(0xffffffffu, B[d], o);
+        }
+        c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+        c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+    }
+    if (!pme || sub != 0) return;
+    float4 g = gx_s[ii];
+    g.x -= q * s0 * (A[0] + B[0]);
+    g.y -= q * s1 * (A[1] + B[1]);
+    g.z -= q * s2 * (A[2] + B[2]);
+    g.w -= c1 + c2;
+    gx_s[ii] = g;
+}
+
+int launch_pme_vjp(nb_handle* h, cudaStream_t st) {
+    if (!h->has_pme) return 0;
+    int N = h->n_atoms;
+    // forward: phi on the first mesh, the reciprocal energy and forces (added to ffix)
+    if (launch_pme(h, st)) return 1;
+    // psi on the second mesh, chi = C psi
+    cudaMemsetAsync(h->lam_max, 0, sizeof(unsigned), st);
+    k_absmax<<<std::min(cdiv(N, 256), 1184), 256, 0, st>>>(N, h->lam, h->lam_max);
+    k_spread_vjp<<<cdiv((long long)N * 16, 256), 256, 0, st>>>(N, h->xs, h->lam, h->sid, h->sys, h->gfix,
+                                                                h->lam_max, h->kl_max);
+    k_grid_convert_dyn<<<cdiv(h->grid_total, 256), 256, 0, st>>>(h->grid_total, h->gfix, h->grid2, h->lam_max,
+                                                                 h->kl_max);
+    if (fft_on(h, h->grid2, 0, st)) return 1;
+    k_convolve<<<h->n_conv_blocks, kConvThreads, 0, st>>>(h->conv_blk_sys, h->conv_blk_off, h->sys, h->cgrid,
+                                                          h->green, nullptr);
+    if (fft_on(h, h->grid2, 1, st)) return 1;
+    k_gather_vjp<<<cdiv((long long)N * 16, 256), 256, 0, st>>>(N, h->xs, h->lam, h->sid, h->sys, h->grid,
+                                                                h->grid2, h->gx_s);
+    return 0;
 }
 
 int launch_pme(nb_handle* h, cudaStream_t st) {

@@ -118,7 +118,7 @@ def load():
     lib.hmc_trajectory_backward.argtypes = [_vp, _vp, _vp, _vp, _i32, _dbl, _vp, _vp, _i32, _vp, _vp, _vp, _vp,
                                             _vp, _i32, _vp]
     lib.nonbonded_force_vjp.restype = ctypes.c_int
-    lib.nonbonded_force_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    lib.nonbonded_force_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp]
     lib.nb_timing_enable.restype = ctypes.c_int
     lib.nb_timing_enable.argtypes = [_vp, _i32]
     lib.nb_timing_read.restype = ctypes.c_int
@@ -364,11 +364,12 @@ class Handle:
             _ptr(g_inv_mass, torch.float32, (N,), "g_inv_mass"), int(terms), _stream()),
             "hmc_trajectory_backward")
 
-    def nonbonded_force_vjp(self, xq, lam, gx, gq=None, gsigma=None, gsqrt_eps=None, f_out=None):
+    def nonbonded_force_vjp(self, xq, lam, gx, gq=None, gsigma=None, gsqrt_eps=None, f_out=None,
+                            terms=NB_TERM_LJ | NB_TERM_COUL):
         torch = _torch()
         N = self.n_atoms
         _ok(self._lib.nonbonded_force_vjp(
             self._h, _ptr(xq, torch.float32, (N, 4), "xq"), _ptr(lam, torch.float32, (N, 3), "lam"),
             _ptr(gx, torch.float32, (N, 3), "gx"), _ptr(gq, torch.float32, (N,), "gq", True),
             _ptr(gsigma, torch.float32, (N,), "gsigma", True), _ptr(gsqrt_eps, torch.float32, (N,), "gsqrt_eps", True),
-            _ptr(f_out, torch.float32, (N, 3), "f_out", True), _stream()), "nonbonded_force_vjp")
+            _ptr(f_out, torch.float32, (N, 3), "f_out", True), int(terms), _stream()), "nonbonded_force_vjp")

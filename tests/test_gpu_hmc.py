@@ -137,19 +137,9 @@ def test_hmc_backward_matches_finite_differences():
     assert checked >= 2
 
 
-def test_hmc_recompute_is_bitwise_and_rejects_pme_backward():
+def test_hmc_recompute_is_bitwise():
     systems, w, dts, xi, u = _setup(n=216)
     with nbcore.Handle(systems) as h:
         _, x1, s1, _, _ = _gpu_forward(h, systems, w, dts, xi, u)
         _, x2, s2, _, _ = _gpu_forward(h, systems, w, dts, xi, u)
     assert torch.equal(x1, x2) and torch.equal(s1, s2)
-    s = wl.water_box(n_side=6, L=18.9, seed=1, r_cut=8.0, r_skin=1.0, pme_grid=20)
-    with nbcore.Handle([s]) as h:
-        z = torch.zeros(1, dtype=torch.float64, device="cuda")
-        x = dev_xq(s)
-        with pytest.raises(nbcore.NbError):
-            h.hmc_trajectory_backward(x, torch.ones(s.n, device="cuda"), torch.ones(1, device="cuda"), 4, 1.0,
-                                      torch.zeros((s.n, 3), device="cuda"),
-                                      torch.zeros(nbcore.ckpt_size(s.n, 4, 4), device="cuda"), 4,
-                                      torch.zeros((1, 4), dtype=torch.float64, device="cuda"), z, z, z.clone(),
-                                      torch.zeros(s.n, device="cuda"), terms=nbcore.NB_TERM_ALL)

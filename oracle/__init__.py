@@ -15,9 +15,13 @@ Contents (each cites the passage of the paper it follows):
   * ``pme`` -- smooth PME with recursive B-splines (module ``oracle.pme``).
   * ``dynamics`` -- velocity Verlet (Sec. 2.2.1) and the HMC proposal / ESJD loss
     (Sec. 4, Eqs. loss and acceptance).
+  * ``tuning`` -- the folded-normal trajectory length, the step-length-weighted loss
+    L_HMC truncated at L_q (Sec. 4, Eq. loss_steps), per-step HMC statistics, and the
+    autocorrelation A(k) / tau_exp (Sec. 4).
 
-Parity status: every function is pinned by tests/test_oracle_pins.py (closed
-forms, lattice sums, finite differences, brute-force invariants).
+Parity status: every function is pinned by tests/test_oracle_pins.py and
+tests/test_oracle_tuning.py (closed forms, lattice sums, finite differences,
+brute-force invariants, scipy's folded normal).
 """
 import ctypes
 import numpy as np

@@ -11,8 +11,12 @@ Readings where the paper leaves a choice open:
   * w_l is the folded-normal density itself, evaluated at the integer l (no
     renormalisation over 1..L_q); the same discretised weights, normalised, are the
     distribution the proposal's length is drawn from.
-  * A(k) replaces the thermodynamic averages by averages over one stationary series:
-    <O> and <O^2> over all n samples, <O_t O_{t+k}> over the n - k available pairs.
+  * A(k) replaces the thermodynamic averages by averages over one stationary series, in
+    the centred form: for expectations <O_t O_{t+k}> - <O>^2 = <(O_t - <O>)(O_{t+k} - <O>)>,
+    and A is unchanged by O -> a O + b; with finite series only the centred estimator
+    keeps that invariance (the plain one carries an O(k/n) edge term times <O>^2, which
+    swamps the covariance of an energy trace whose mean is far larger than its spread).
+    So A(k) = [1/(n-k) sum_{t<n-k} d_t d_{t+k}] / [1/n sum_t d_t^2], d_t = O_t - mean(O).
   * tau_exp is the least-squares slope of ln A(k) against k over the lags k >= 1 from
     the first with A(k) <= a_hi up to the last before A(k) first falls below a_lo
     (the decay region above the noise floor); fewer than two such lags give NaN.
@@ -109,16 +113,15 @@ def lhmc_loss(alpha, jump, mu_L, sigma_L=1.0):
 
 
 def autocorrelation(o, max_lag):
-    """A(k) for k = 0..max_lag of one series (Sec. 4): the lagged covariance over the variance."""
+    """A(k) for k = 0..max_lag of one series (Sec. 4): the lagged covariance over the
+    variance, both about the series mean (see the module header)."""
     o = np.asarray(o, dtype=np.float64)
     n = o.size
-    m1 = float(np.mean(o))
-    m2 = float(np.mean(o * o))
-    var = m2 - m1 * m1
+    d = o - float(np.mean(o))
+    var = float(np.mean(d * d))
     out = np.empty(max_lag + 1)
     for k in range(max_lag + 1):
-        c = float(np.mean(o[:n - k] * o[k:]))
-        out[k] = (c - m1 * m1) / var
+        out[k] = float(np.mean(d[:n - k] * d[k:])) / var
     return out
 
 

@@ -118,6 +118,16 @@ def test_autocorrelation_closed_forms():
     assert math.isnan(tun.tau_exp(tun.autocorrelation(rng.standard_normal(20000), 10)))
 
 
+def test_autocorrelation_is_invariant_under_affine_maps():
+    # A(k) is a correlation: O -> a O + b (a > 0) leaves it unchanged, also with an offset
+    # two hundred times the spread, as for a potential-energy trace
+    rng = np.random.default_rng(4)
+    o = signal.lfilter([1.0], [1.0, -0.7], rng.standard_normal(5000))
+    a = tun.autocorrelation(o, 30)
+    np.testing.assert_allclose(tun.autocorrelation(3.0 * o - 600.0, 30), a, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(tun.autocorrelation(-2.0 * o, 30), a, rtol=0, atol=1e-13)
+
+
 def test_autocorrelation_of_ar1_process():
     # o_t = phi o_{t-1} + e_t has A(k) = phi^k and tau_exp = -1/ln(phi)
     phi = 0.8

@@ -361,6 +361,7 @@ def extras(torch, nbcore, wl):
                         "32 leapfrog steps, checkpoints every 8 (recompute in the backward), switch 2.2-2.5"}
     out["lj_sweep"] = lj_sweep(torch, nbcore, wl)
     out["hmc_training"] = hmc_training(torch, nbcore, wl)
+    out["hmc_lhmc"] = hmc_lhmc(torch, nbcore, wl)
     out["batched"] = batched(torch, nbcore, wl)
     return out
 
@@ -464,6 +465,110 @@ def hmc_training(torch, nbcore, wl, iters=200):
             "workload": "LJ fluid 2048 atoms (rho* 0.8442, T* 1, 2 types by index parity, switch 2.2-2.5) x 10 "
                         "replicas, L = 32 leapfrog steps, checkpoints every 8, folded-normal dt (sigma 0.01 mu), "
                         "fixed total mass; Adam lr 0.05 from mu = 0.002; one iteration = forward + adjoint"}
+
+
+def _energy_chain(torch, nbcore, hmc, h, x, w, dt, mu_L, L_fixed, n_prop, burn, gen, kT=1.0, keep=False):
+    """Potential energy after every proposal of R HMC chains: lengths drawn from the
+    discretised N_F(mu_L, 1) (L_fixed None) or all L_fixed.  Returns the (R, n_prop - burn)
+    energy series and the mean number of force evaluations per proposal (keep: a list
+    holding the final chain state instead of the series)."""
+    R, N = h.n_sys, h.n_atoms
+    dev = x.device
+    L_q = hmc.length_cutoff(mu_L) if L_fixed is None else L_fixed
+    stats = torch.empty((R, 4), dtype=torch.float64, device=dev)
+    sst = torch.empty((L_q, R, 3), dtype=torch.float64, device=dev)
+    e = torch.empty((R, 6), dtype=torch.float64, device=dev)
+    x_new = torch.empty_like(x)
+    us, lens = [], []
+    for p in range(n_prop):
+        xi = torch.randn((N, 3), dtype=torch.float32, device=dev, generator=gen)
+        u = torch.rand(R, dtype=torch.float64, device=dev, generator=gen)
+        if L_fixed is None:
+            l_prop = hmc.draw_lengths(mu_L, 1.0, L_q, torch.rand(R, dtype=torch.float64, device=dev, generator=gen))
+        else:
+            l_prop = torch.full((R,), L_fixed, dtype=torch.int32, device=dev)
+        h.hmc_trajectory_steps(x, x_new, w, dt, L_q, l_prop, kT, xi, u, stats, sst, terms=nbcore.NB_TERM_LJ)
+        x, x_new = x_new, x
+        h.nonbonded_forces(x, None, e, terms=nbcore.NB_TERM_LJ)
+        if p >= burn:
+            us.append(e[:, 0].clone())
+            lens.append(l_prop.to(torch.float64).mean())
+    if keep:
+        return [x], float(torch.stack(lens).mean())
+    return torch.stack(us, 1).contiguous(), float(torch.stack(lens).mean())
+
+
+def hmc_lhmc(torch, nbcore, wl, iters=200, n_prop=1550, burn=50, n_equil=200, max_lag=150):
+    """Eq. loss_steps training: LJ 2048 atoms x 10 replicas, dt and trajectory length both
+    folded normals (sigma_dt = 0.01 mu_dt, sigma_L = 1), per-type masses, 200 Adam steps;
+    then tau_exp of the potential energy (A(k) and its fit in libnbcore) along chains run
+    with the trained parameters against ad-hoc ones, in force evaluations."""
+    import math
+    from paper_2503_20541_b300 import hmc
+    R = 10
+    systems = []
+    for r in range(R):
+        sr = wl.lj_random(2048, seed=300 + r, n_types=2)
+        sr.r_switch = 2.2
+        systems.append(sr)
+    types = torch.from_numpy(systems[0].types.astype(np.int64)).cuda()
+    x0 = torch.cat([torch.from_numpy(nbcore.pack_xq(x.x, x.q)) for x in systems]).cuda()
+    with nbcore.Handle(systems) as h:
+        hmc.train_lhmc(h, x0, types, 2048.0, iters=2, seed=1)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist = hmc.train_lhmc(h, x0, types, 2048.0, iters=iters, lr=0.05, log_mu0=math.log(0.002), mu_L0=10.0,
+                              seed=2)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        h.check()
+        steps = sum(r["L_q"] for r in hist)
+        last = hist[-1]
+        gen = torch.Generator(device="cuda").manual_seed(5)
+        m = torch.tensor(last["mass_per_type"], dtype=torch.float64, device="cuda")[types]
+        w_tr = (1.0 / m).to(torch.float32).repeat(R).contiguous()
+        dt_tr = torch.full((R,), last["mu"], dtype=torch.float32, device="cuda")
+        w_ad = torch.ones(R * 2048, dtype=torch.float32, device="cuda")
+        dt_ad = torch.full((R,), 0.005, dtype=torch.float32, device="cuda")
+        # both samplers start from one equilibrated state: the relaxed start lies far below
+        # the T* = 1 potential energy, and the drift back would dominate A(k)
+        t1 = time.perf_counter()
+        eq, _ = _energy_chain(torch, nbcore, hmc, h, x0.clone(), w_tr, dt_tr, last["mu_L"], None, n_equil, 0, gen,
+                              keep=True)
+        x_eq = eq.pop()
+        equil_s = time.perf_counter() - t1
+        res = {}
+        for name, w, dt, mu_L, L_fixed in (("trained", w_tr, dt_tr, last["mu_L"], None),
+                                          ("ad_hoc", w_ad, dt_ad, 10.0, 10)):
+            t1 = time.perf_counter()
+            us, mean_len = _energy_chain(torch, nbcore, hmc, h, x_eq.clone(), w, dt, mu_L, L_fixed, n_prop, burn,
+                                         gen)
+            acf, tau = nbcore.autocorrelation(us, max_lag)
+            torch.cuda.synchronize()
+            tau = tau.cpu().numpy()
+            ok = tau[np.isfinite(tau)]
+            t_med = float(np.median(ok)) if ok.size else float("nan")
+            res[name] = {"tau_exp_proposals_median": t_med, "tau_exp_proposals": tau.tolist(),
+                         "force_evals_per_proposal": mean_len, "tau_exp_force_evals": t_med * mean_len,
+                         "acf_mean_first10": acf.mean(0)[:10].cpu().numpy().tolist(),
+                         "wall_s": time.perf_counter() - t1}
+        h.check()
+    head, tail = hist[:10], hist[-10:]
+    sp = res["ad_hoc"]["tau_exp_force_evals"] / res["trained"]["tau_exp_force_evals"]
+    return {"iterations": iters, "iterations_per_s": iters / wall, "wall_s": wall, "leapfrog_steps": steps,
+            "lhmc_first10": float(np.mean([r["loss"] for r in head])),
+            "lhmc_last10": float(np.mean([r["loss"] for r in tail])),
+            "dt_first": hist[0]["mu"], "dt_last": last["mu"], "mu_L_first": hist[0]["mu_L"], "mu_L_last": last["mu_L"],
+            "L_q_last": last["L_q"], "mass_per_type_last": last["mass_per_type"],
+            "acceptance_last10": float(np.mean([r["accepted"] for r in tail])),
+            "evaluation": res, "tau_speedup_force_evals": sp, "equilibration_s": equil_s,
+            "workload": "LJ fluid 2048 atoms (rho* 0.8442, T* 1, 2 types by index parity, switch 2.2-2.5) x 10 "
+                        "replicas; Eq. loss_steps with folded-normal dt (sigma 0.01 mu) and L (sigma 1, L_q at the "
+                        "0.999 quantile), fixed total mass; Adam lr 0.05 from dt 0.002, mu_L 10; evaluation: "
+                        "both samplers from one state equilibrated by %d trained proposals, %d proposals per chain "
+                        "(%d burn-in), tau_exp of the potential energy from A(k) up to lag %d (fit where "
+                        "0.05 <= A <= 0.5), median over the 10 chains; ad hoc: dt 0.005, L 10, equal masses; cost "
+                        "per proposal = drawn length" % (n_equil, n_prop, burn, max_lag)}
 
 
 def batched(torch, nbcore, wl, n_systems=256, reps=10):

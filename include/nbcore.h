@@ -51,6 +51,7 @@ typedef enum {
 #define NB_DEVERR_LIST_OVERFLOW 1u
 #define NB_DEVERR_FIXEDPOINT 2u
 #define NB_DEVERR_NONFINITE 4u
+#define NB_DEVERR_ARG 8u          /* a device-side argument out of range (e.g. a proposal length) */
 
 /* Energy components per system, in this order (FP64). */
 #define NB_E_LJ 0    /* Lennard-Jones, Eq. (lj), r < r_c, optional switch S(x) */
@@ -257,6 +258,62 @@ nb_status hmc_trajectory_backward(nb_handle* h, const float* x0, const float* in
                                   const float* ckpt, int32_t ckpt_every, const double* stats,
                                   const double* g_alpha, const double* g_jump,
                                   double* g_dt, float* g_inv_mass, int32_t terms, void* stream);
+
+/*
+ * HMC with a drawn trajectory length and per-step statistics (Sec. 4, Eq. loss_steps):
+ * one trajectory of n_leap = L_q velocity-Verlet steps per system from the
+ * Maxwell-Boltzmann draw v0 = sqrt(kT w) xi, recording at every step l = 1..n_leap the
+ * statistics of proposing (x_l, v_l), and proposing the state after l_prop[s] steps.
+ *   x0 [N][4]           (device) start positions and charges.
+ *   x_out [N][4]        (device) the new chain state: x_{l_prop[s]} where accepted, x0
+ *                       elsewhere.  May not alias x0.
+ *   inv_mass [N], dt [n_sys], xi [N][3], u [n_sys]  as for hmc_trajectory.
+ *   l_prop [n_sys]      (device, int32) the proposal length of each system, in
+ *                       [1, n_leap] (the caller draws it from the discretised folded
+ *                       normal); a value outside that range keeps x0 for the system,
+ *                       zeroes its stats and makes nb_check return NB_ERR_ARG.
+ *   stats [n_sys][4]    (device, FP64) out: dH, alpha, jump, accepted of the proposal.
+ *   step_stats          (device, FP64) out: [n_leap][n_sys][3] (dH_l, alpha_l, jump_l),
+ *                       dH_l = E(x_l, v_l) - E(x_0, v_0), alpha_l = min(1, exp(-dH_l/kT)),
+ *                       jump_l = |mi(x_l - x_0)|^2 summed over the system's atoms.
+ *   ckpt, ckpt_every    as for hmc_trajectory (positions and velocities at steps 0, k, ...).
+ * Every system runs all n_leap steps.
+ */
+nb_status hmc_trajectory_steps(nb_handle* h, const float* x0, float* x_out, const float* inv_mass,
+                               const float* dt, int32_t n_leap, const int32_t* l_prop, double kT,
+                               const float* xi, const double* u, double* stats, double* step_stats,
+                               float* ckpt, int32_t ckpt_every, int32_t terms, void* stream);
+
+/*
+ * Reverse-mode derivative of hmc_trajectory_steps: given cotangents
+ * g_alpha [n_leap][n_sys] and g_jump [n_leap][n_sys] (device, FP64) of every step's
+ * acceptance probability and squared jump, accumulates g_dt [n_sys] (FP64, +=) and
+ * g_inv_mass [N] (FP32, +=), recomputing from `ckpt` like hmc_trajectory_backward.
+ *   step_stats          (device) the forward call's step_stats.
+ */
+nb_status hmc_trajectory_steps_backward(nb_handle* h, const float* x0, const float* inv_mass,
+                                        const float* dt, int32_t n_leap, double kT, const float* xi,
+                                        const float* ckpt, int32_t ckpt_every,
+                                        const double* step_stats, const double* g_alpha,
+                                        const double* g_jump, double* g_dt, float* g_inv_mass,
+                                        int32_t terms, void* stream);
+
+/*
+ * Autocorrelation function and exponential autocorrelation time (Sec. 4) of n_series
+ * series of n samples each (e.g. the potential energy along HMC chains):
+ *   A(k) = (<O_t O_{t+k}> - <O>^2) / (<O^2> - <O>^2),  k = 0..max_lag,
+ * estimated about the series mean m: [1/(n-k) sum_{t<n-k} (O_t - m)(O_{t+k} - m)] over
+ * [1/n sum_t (O_t - m)^2] (equal in expectation, and invariant under O -> a O + b);
+ * tau_exp from A(k) -> exp(-k/tau_exp): the least-squares slope of ln A(k) against k over
+ * the lags k >= 1 from the first with A(k) <= a_hi up to the last before A(k) first falls
+ * below a_lo; NaN when fewer than two lags qualify.
+ *   series [n_series][n]        (device, FP64).
+ *   acf [n_series][max_lag+1]   (device, FP64) out.
+ *   tau [n_series]              (device, FP64) out (may be NULL).
+ * Requires 1 <= max_lag < n and 0 < a_lo < a_hi <= 1.
+ */
+nb_status autocorrelation(const double* series, int32_t n_series, int32_t n, int32_t max_lag, double a_hi,
+                          double a_lo, double* acf, double* tau, void* stream);
 
 /*
  * Force vector-Jacobian product (Sec. 4 differentiates the trajectory through the

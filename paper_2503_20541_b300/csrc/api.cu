@@ -433,7 +433,6 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(dalloc(h, &h->xbar, N));
         NB_TRY(dalloc(h, &h->vbar, N));
         NB_TRY(dalloc(h, &h->xwork, N));
-        NB_TRY(dalloc(h, &h->dhbar, n_systems));
         NB_TRY(dalloc(h, &h->counter, 1));
         {
             std::vector<int> rb_sys, rb_off(n_systems + 1, 0);
@@ -445,7 +444,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
             h->n_red_blocks = (int)rb_sys.size();
             NB_TRY(dalloc(h, &h->red_blk_sys, rb_sys.size()));
             NB_TRY(dalloc(h, &h->red_blk_off, rb_off.size()));
-            NB_TRY(dalloc(h, &h->red_part, rb_sys.size() * 5));
+            NB_TRY(dalloc(h, &h->red_part, rb_sys.size() * 6));
             NB_TRY(dalloc(h, &h->red_ticket, 1));
             NB_TRY(cudaMemset(h->red_ticket, 0, sizeof(unsigned)));
             NB_TRY(cudaMemcpy(h->red_blk_sys, rb_sys.data(), sizeof(int) * rb_sys.size(), cudaMemcpyHostToDevice));
@@ -518,6 +517,7 @@ nb_status nb_check(nb_handle* h, void* stream) {
     if (bits & NB_DEVERR_NONFINITE) return NB_ERR_NONFINITE;
     if (bits & NB_DEVERR_LIST_OVERFLOW) return NB_ERR_LIST_OVERFLOW;
     if (bits & NB_DEVERR_FIXEDPOINT) return NB_ERR_FIXEDPOINT_OVERFLOW;
+    if (bits & NB_DEVERR_ARG) return NB_ERR_ARG;
     return NB_OK;
 }
 
@@ -677,18 +677,71 @@ nb_status hmc_trajectory(nb_handle* h, const float* x0, float* x_out, const floa
     return launched();
 }
 
-nb_status hmc_trajectory_backward(nb_handle* h, const float* x0, const float* inv_mass, const float* dt,
-                                  int32_t n_leap, double kT, const float* xi, const float* ckpt, int32_t ckpt_every,
-                                  const double* stats, const double* g_alpha, const double* g_jump, double* g_dt,
-                                  float* g_inv_mass, int32_t terms, void* stream) {
-    if (!h || !x0 || !inv_mass || !dt || !xi || !ckpt || !stats || !g_alpha || !g_jump || !g_dt || !g_inv_mass ||
-        n_leap < 1 || ckpt_every < 1 || !(kT > 0.0))
+nb_status hmc_trajectory_steps(nb_handle* h, const float* x0, float* x_out, const float* inv_mass, const float* dt,
+                               int32_t n_leap, const int32_t* l_prop, double kT, const float* xi, const double* u,
+                               double* stats, double* step_stats, float* ckpt, int32_t ckpt_every, int32_t terms,
+                               void* stream) {
+    if (!h || !x0 || !x_out || x0 == x_out || !inv_mass || !dt || !l_prop || !xi || !u || !stats || !step_stats ||
+        n_leap < 1 || !(kT > 0.0))
         return NB_ERR_ARG;
-    int t = terms & NB_TERM_ALL;
+    if (ckpt && ckpt_every < 1) return NB_ERR_ARG;
     DeviceGuard g(h->device);
     cudaStream_t st = S(stream);
+    int t = terms & NB_TERM_ALL;
     int N = h->n_atoms;
-    int k = ckpt_every;
+    // the trajectory runs in xwork; x_out receives each system's state at step l_prop[s]
+    float4* x = h->xwork;
+    float4* ck = ckpt ? F4(ckpt) : nullptr;
+    cudaMemcpyAsync(x, x0, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st);
+    launch_hmc_init(h, inv_mass, xi, kT, st);
+    nb_status s = eval(h, x, t, ck != nullptr, st);
+    if (s != NB_OK) return s;
+    launch_reduce_energy(h, t, 1, h->e0, st);
+    const size_t sstride = (size_t)h->n_sys * 3;
+    StepObs ob;
+    ob.x0 = F4(x0);
+    ob.jump = h->jump_atom;
+    ob.l_prop = l_prop;
+    ob.x_prop = F4(x_out);
+    StepStat ss;
+    ss.jump = h->jump_atom;
+    ss.e_ref = h->e0;
+    ss.kT = kT;
+    for (int l = 0; l <= n_leap; ++l) {
+        float4* cx = nullptr;
+        float4* cv = nullptr;
+        if (ck && l < n_leap && l % ckpt_every == 0) {
+            cx = ck + (size_t)(l / ckpt_every) * 2 * N;
+            cv = cx + N;
+        }
+        {
+            Stage sc(h, NB_STAGE_UPDATE, st);
+            ob.step = l;
+            launch_integrate(h, x, h->vwork, inv_mass, dt, l == 0 ? 0.f : 0.5f, l == n_leap ? 0.f : 0.5f,
+                             l < n_leap, cx, cv, nullptr, st, l > 0 ? ob : StepObs());
+            if (l > 0) {
+                ss.sstat = step_stats + (size_t)(l - 1) * sstride;
+                launch_reduce_energy(h, t, 1, h->e1, st, ss);
+            }
+        }
+        if (l == n_leap) break;
+        s = eval(h, x, t, ck != nullptr && (l + 1) % ckpt_every == 0, st);
+        if (s != NB_OK) return s;
+    }
+    Stage sc(h, NB_STAGE_UPDATE, st);
+    launch_hmc_pick(h, F4(x_out), F4(x0), l_prop, n_leap, step_stats, u, stats, st);
+    return launched();
+}
+
+}  // extern "C"
+
+// Reverse sweep shared by both HMC backward entry points; inj(l) gives the loss
+// cotangents entering at state l (1..n_leap).
+template <class InjectAt>
+static nb_status hmc_backward(nb_handle* h, const float* x0, const float* inv_mass, const float* dt, int n_leap,
+                              double kT, const float* xi, const float* ckpt, int k, InjectAt inj, double* g_dt,
+                              float* g_inv_mass, int t, cudaStream_t st) {
+    int N = h->n_atoms;
     if (h->seg_k < k) {
         // (k+1) states of positions, velocities and half-step velocities
         float4* p = nullptr;
@@ -706,10 +759,12 @@ nb_status hmc_trajectory_backward(nb_handle* h, const float* x0, const float* in
     auto seg_v = [&](int i) { return h->seg + (size_t)(h->seg_k + 1 + i) * N; };
     auto seg_p = [&](int i) { return h->seg + (size_t)(2 * (h->seg_k + 1) + i) * N; };
     cudaMemsetAsync(h->hbar_atom, 0, sizeof(double) * N, st);
+    cudaMemsetAsync(h->xbar, 0, sizeof(float4) * N, st);
+    cudaMemsetAsync(h->vbar, 0, sizeof(float4) * N, st);
     int n_seg = (n_leap + k - 1) / k;
     nb_status s;
     for (int j = n_seg - 1; j >= 0; --j) {
-        int s0 = j * k, e = std::min(s0 + k, (int)n_leap), m = e - s0;
+        int s0 = j * k, e = std::min(s0 + k, n_leap), m = e - s0;
         cudaMemcpyAsync(h->xwork, ck + (size_t)j * 2 * N, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st);
         cudaMemcpyAsync(h->vwork, ck + (size_t)j * 2 * N + N, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st);
         s = eval(h, h->xwork, t, true, st);
@@ -721,25 +776,69 @@ nb_status hmc_trajectory_backward(nb_handle* h, const float* x0, const float* in
             if (s != NB_OK) return s;
         }
         launch_integrate(h, h->xwork, h->vwork, inv_mass, dt, 0.5f, 0.f, 0, seg_x(m), seg_v(m), nullptr, st);
-        if (j == n_seg - 1)
-            launch_bwd_init(h, seg_x(m), seg_v(m), F4(x0), inv_mass, stats, g_alpha, g_jump, kT, g_inv_mass, st);
         for (int q = m; q >= 1; --q) {
-            int state = s0 + q;
-            float cf = state == n_leap ? 0.5f : 1.0f;
+            const Inject in = inj(s0 + q);
             prepare(h, seg_x(q), false, st);
-            launch_bwd_lambda(h, inv_mass, dt, cf, st);
+            launch_bwd_lambda(h, inv_mass, dt, seg_v(q), in, kT, st);
             {
                 Stage sc(h, NB_STAGE_PAIR, st);
                 launch_vjp(h, t, st);
             }
             if ((t & NB_TERM_PME) && h->has_pme && launch_pme_vjp(h, st)) return NB_ERR_CUDA;
-            launch_bwd_adjoint(h, inv_mass, dt, cf, state == n_leap, seg_p(q), g_inv_mass, st);
+            launch_bwd_adjoint(h, inv_mass, dt, seg_x(q), seg_v(q), F4(x0), in, kT, seg_p(q), g_inv_mass, st);
         }
     }
     s = eval(h, F4(x0), t, false, st);
     if (s != NB_OK) return s;
     launch_bwd_final(h, inv_mass, dt, xi, kT, g_inv_mass, g_dt, st);
     return launched();
+}
+
+extern "C" {
+
+nb_status hmc_trajectory_backward(nb_handle* h, const float* x0, const float* inv_mass, const float* dt,
+                                  int32_t n_leap, double kT, const float* xi, const float* ckpt, int32_t ckpt_every,
+                                  const double* stats, const double* g_alpha, const double* g_jump, double* g_dt,
+                                  float* g_inv_mass, int32_t terms, void* stream) {
+    if (!h || !x0 || !inv_mass || !dt || !xi || !ckpt || !stats || !g_alpha || !g_jump || !g_dt || !g_inv_mass ||
+        n_leap < 1 || ckpt_every < 1 || !(kT > 0.0))
+        return NB_ERR_ARG;
+    DeviceGuard g(h->device);
+    const int L = n_leap;
+    auto inj = [&](int l) {
+        Inject in;
+        if (l == L) {
+            in.ga = g_alpha;
+            in.gj = g_jump;
+            in.alpha = stats + 1;
+            in.a_stride = 4;
+        }
+        return in;
+    };
+    return hmc_backward(h, x0, inv_mass, dt, L, kT, xi, ckpt, ckpt_every, inj, g_dt, g_inv_mass,
+                        terms & NB_TERM_ALL, S(stream));
+}
+
+nb_status hmc_trajectory_steps_backward(nb_handle* h, const float* x0, const float* inv_mass, const float* dt,
+                                        int32_t n_leap, double kT, const float* xi, const float* ckpt,
+                                        int32_t ckpt_every, const double* step_stats, const double* g_alpha,
+                                        const double* g_jump, double* g_dt, float* g_inv_mass, int32_t terms,
+                                        void* stream) {
+    if (!h || !x0 || !inv_mass || !dt || !xi || !ckpt || !step_stats || !g_alpha || !g_jump || !g_dt ||
+        !g_inv_mass || n_leap < 1 || ckpt_every < 1 || !(kT > 0.0))
+        return NB_ERR_ARG;
+    DeviceGuard g(h->device);
+    const size_t ns = (size_t)h->n_sys;
+    auto inj = [&](int l) {
+        Inject in;
+        in.ga = g_alpha + (size_t)(l - 1) * ns;
+        in.gj = g_jump + (size_t)(l - 1) * ns;
+        in.alpha = step_stats + (size_t)(l - 1) * ns * 3 + 1;
+        in.a_stride = 3;
+        return in;
+    };
+    return hmc_backward(h, x0, inv_mass, dt, n_leap, kT, xi, ckpt, ckpt_every, inj, g_dt, g_inv_mass,
+                        terms & NB_TERM_ALL, S(stream));
 }
 
 nb_status nonbonded_force_vjp(nb_handle* h, const float* xq, const float* lam, float* gx, float* gq, float* gsigma,

@@ -119,7 +119,7 @@ struct nb_handle {
     int n_red_blocks = 0;        // energy reduction: blocks of kRedTile atoms, none straddling systems
     int* red_blk_sys = nullptr;  // [n_red_blocks]
     int* red_blk_off = nullptr;  // [n_sys+1] first reduction block of each system
-    double* red_part = nullptr;  // [n_red_blocks * 5] per-block FP64 partial sums
+    double* red_part = nullptr;  // [n_red_blocks * 6] per-block FP64 partial sums
     unsigned* red_ticket = nullptr;  // [1] blocks of the energy reduction done (reset by the last)
     float* ke_atom = nullptr;    // [N] caller
     // PME
@@ -147,7 +147,6 @@ struct nb_handle {
     float4* xbar = nullptr;      // [N] caller
     float4* vbar = nullptr;      // [N] caller
     float4* xwork = nullptr;     // [N] caller: backward recomputation positions
-    double* dhbar = nullptr;     // [n_sys] cotangent of dH
     unsigned long long* counter = nullptr;  // pair export counter
     // second stream for the PME chain, forked from and joined to the caller's stream
     cudaStream_t aux = nullptr;
@@ -232,19 +231,49 @@ void launch_pme_gather(nb_handle* h, cudaStream_t st);
 void launch_pme_spread_only(nb_handle* h, float* grid_out, cudaStream_t st);
 void launch_pme_gather_only(nb_handle* h, const float* phi, float* f_out, cudaStream_t st);
 // dynamics.cu
-void launch_reduce_energy(nb_handle* h, int terms, int with_kin, double* dst, cudaStream_t st);
+// Observables of an HMC trajectory recorded by the integrator at integer step `step`
+// (before its drift): the squared minimum-image jump |x - x0|^2 of every atom (FP64,
+// caller order) and, for each system s with l_prop[s] == step, its positions as the
+// proposal.  x0 == nullptr records nothing.
+struct StepObs {
+    const float4* x0 = nullptr;
+    double* jump = nullptr;
+    const int* l_prop = nullptr;
+    float4* x_prop = nullptr;
+    int step = 0;
+};
+// Statistics of the state whose energies a reduction sums: with sstat != nullptr, per
+// system (dH, alpha, jump) = (H - H_ref, min(1, exp(-dH/kT)), sum of `jump`).
+struct StepStat {
+    const double* jump = nullptr;
+    const double* e_ref = nullptr;
+    double kT = 1.0;
+    double* sstat = nullptr;
+};
+// Loss cotangents entering the HMC adjoint at one state l: ga[s] and gj[s] of the
+// acceptance probability and squared jump of proposing state l, alpha[s * a_stride] its
+// acceptance probability.  ga == nullptr: no loss term at this state.
+struct Inject {
+    const double* ga = nullptr;
+    const double* gj = nullptr;
+    const double* alpha = nullptr;
+    int a_stride = 0;
+};
+void launch_reduce_energy(nb_handle* h, int terms, int with_kin, double* dst, cudaStream_t st,
+                          const StepStat& ss = StepStat());
 void launch_finalize_forces(nb_handle* h, float* f_out, cudaStream_t st);
 void launch_integrate(nb_handle* h, float4* xq, float4* v, const float* w_override, const float* dt,
                       float c_pre, float c_post, int drift, float4* ck_x, float4* ck_v,
-                      float4* ck_p, cudaStream_t st);
+                      float4* ck_p, cudaStream_t st, const StepObs& ob = StepObs());
 void launch_hmc_init(nb_handle* h, const float* w, const float* xi, double kT, cudaStream_t st);
 void launch_hmc_finish(nb_handle* h, float4* x_out, const float4* x0, double kT, const double* u,
                        double* stats, cudaStream_t st);
-void launch_bwd_lambda(nb_handle* h, const float* w, const float* dt, float cf, cudaStream_t st);
-void launch_bwd_init(nb_handle* h, const float4* xL, const float4* vL, const float4* x0, const float* w,
-                     const double* stats, const double* g_alpha, const double* g_jump, double kT,
-                     float* wbar, cudaStream_t st);
-void launch_bwd_adjoint(nb_handle* h, const float* w, const float* dt, float cf, int last,
+void launch_hmc_pick(nb_handle* h, float4* x_out, const float4* x0, const int* l_prop, int n_leap,
+                     const double* step_stats, const double* u, double* stats, cudaStream_t st);
+void launch_bwd_lambda(nb_handle* h, const float* w, const float* dt, const float4* v_state,
+                       const Inject& inj, double kT, cudaStream_t st);
+void launch_bwd_adjoint(nb_handle* h, const float* w, const float* dt, const float4* x_state,
+                        const float4* v_state, const float4* x0, const Inject& inj, double kT,
                         const float4* p_prev, float* wbar, cudaStream_t st);
 void launch_bwd_final(nb_handle* h, const float* w, const float* dt, const float* xi, double kT,
                       float* wbar, double* g_dt, cudaStream_t st);

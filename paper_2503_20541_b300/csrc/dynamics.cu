@@ -39,9 +39,11 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_energy(
     int n_sys, const int* __restrict__ blk_sys, const int* __restrict__ blk_off, const SysDev* __restrict__ sys,
     const float4* __restrict__ e_atom, const float4* __restrict__ xs, const float* __restrict__ ke_atom,
     int with_kin, double* __restrict__ part, const double* __restrict__ e_pme_blk,
-    const int* __restrict__ pme_blk_off, int terms, unsigned* __restrict__ ticket, double* __restrict__ dst) {
+    const int* __restrict__ pme_blk_off, int terms, unsigned* __restrict__ ticket, double* __restrict__ dst,
+    StepStat ss) {
     constexpr int kW = kRedThreads / 32;
-    __shared__ double sm[kW][5];
+    constexpr int kC = 6;  // LJ, direct, exclusion, q^2, kinetic, jump
+    __shared__ double sm[kW][kC];
     __shared__ bool last;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     {
@@ -50,7 +52,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_energy(
         const SysDev& S = sys[s];
         const int a0 = S.atom_off + (b - blk_off[s]) * kRedTile;
         const int a1 = min(a0 + kRedTile, S.atom_off + S.n_atoms);
-        double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        double v[kC] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         for (int k = a0 + threadIdx.x; k < a1; k += kRedThreads) {
             const float4 e = e_atom[k];
             const float q = xs[k].w;
@@ -59,19 +61,22 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_energy(
             v[2] += e.z;
             v[3] += (double)q * q;
             if (with_kin) v[4] += ke_atom[k];
+            // a system owns the same index range in both orders: its jump sum reads
+            // caller-order entries over that range
+            if (ss.jump) v[5] += ss.jump[k];
         }
 #pragma unroll
-        for (int c = 0; c < 5; ++c) v[c] = warp_sum_d(v[c]);
+        for (int c = 0; c < kC; ++c) v[c] = warp_sum_d(v[c]);
         if (lane == 0)
 #pragma unroll
-            for (int c = 0; c < 5; ++c) sm[w][c] = v[c];
+            for (int c = 0; c < kC; ++c) sm[w][c] = v[c];
         __syncthreads();
         if (w == 0) {
 #pragma unroll
-            for (int c = 0; c < 5; ++c) {
+            for (int c = 0; c < kC; ++c) {
                 double t = lane < kW ? sm[lane][c] : 0.0;
                 t = warp_sum_d(t);
-                if (lane == 0) part[(size_t)b * 5 + c] = t;
+                if (lane == 0) part[(size_t)b * kC + c] = t;
             }
             if (lane == 0) {
                 __threadfence();
@@ -84,22 +89,39 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_energy(
     __threadfence();
     for (int s = w; s < n_sys; s += kW) {
         const SysDev& S = sys[s];
-        double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        double acc[kC + 1] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         for (int b = blk_off[s] + lane; b < blk_off[s + 1]; b += 32)
-            for (int c = 0; c < 5; ++c) acc[c] += __ldcg(part + (size_t)b * 5 + c);
+            for (int c = 0; c < kC; ++c) acc[c] += __ldcg(part + (size_t)b * kC + c);
         if ((terms & NB_TERM_PME) && S.pme && pme_blk_off)
-            for (int b = pme_blk_off[s] + lane; b < pme_blk_off[s + 1]; b += 32) acc[5] += e_pme_blk[b];
+            for (int b = pme_blk_off[s] + lane; b < pme_blk_off[s + 1]; b += 32) acc[kC] += e_pme_blk[b];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) acc[c] = warp_sum_d(acc[c]);
+        for (int c = 0; c <= kC; ++c) acc[c] = warp_sum_d(acc[c]);
         if (lane == 0) {
             const bool coul = (terms & NB_TERM_COUL) != 0;
+            double e[NB_NE];
+            e[NB_E_LJ] = (terms & NB_TERM_LJ) ? acc[0] : 0.0;
+            e[NB_E_DIR] = coul ? acc[1] : 0.0;
+            e[NB_E_EXCL] = coul ? acc[2] : 0.0;
+            e[NB_E_SELF] = coul ? S.self_coef * acc[3] : 0.0;
+            e[NB_E_REC] = acc[kC];
+            e[NB_E_KIN] = with_kin ? acc[4] : 0.0;
             double* o = dst + (size_t)s * NB_NE;
-            o[NB_E_LJ] = (terms & NB_TERM_LJ) ? acc[0] : 0.0;
-            o[NB_E_DIR] = coul ? acc[1] : 0.0;
-            o[NB_E_EXCL] = coul ? acc[2] : 0.0;
-            o[NB_E_SELF] = coul ? S.self_coef * acc[3] : 0.0;
-            o[NB_E_REC] = acc[5];
-            o[NB_E_KIN] = with_kin ? acc[4] : 0.0;
+#pragma unroll
+            for (int c = 0; c < NB_NE; ++c) o[c] = e[c];
+            if (ss.sstat) {
+                double H0 = 0.0, H1 = 0.0;
+                for (int c = 0; c < NB_NE; ++c) {
+                    H0 += ss.e_ref[(size_t)s * NB_NE + c];
+                    H1 += e[c];
+                }
+                const double dH = H1 - H0;
+                double a = (dH <= 0.0) ? 1.0 : exp(-dH / ss.kT);
+                if (!(dH == dH)) a = 0.0;  // NaN energy: never accepted
+                double* q = ss.sstat + (size_t)s * 3;
+                q[0] = dH;
+                q[1] = a;
+                q[2] = acc[5];
+            }
         }
     }
     if (threadIdx.x == 0) *ticket = 0u;
@@ -125,10 +147,12 @@ __global__ void k_integrate(int N, float4* __restrict__ xq, float4* __restrict__
                             const float* __restrict__ dt, const int* __restrict__ sid,
                             const long long* __restrict__ ffix, const int* __restrict__ iperm, float finv,
                             float c_pre, float c_post, int drift, float* __restrict__ ke_atom,
-                            float4* __restrict__ ck_x, float4* __restrict__ ck_v, float4* __restrict__ ck_p) {
+                            float4* __restrict__ ck_x, float4* __restrict__ ck_v, float4* __restrict__ ck_p,
+                            const SysDev* __restrict__ sys, StepObs ob) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    float h = dt[sid[i]];
+    const int si = sid[i];
+    float h = dt[si];
     float3 F = load_force(ffix, N, iperm[i], finv);
     float4 vi = v[i];
     float w = w_ovr ? w_ovr[i] : vi.w;
@@ -140,6 +164,18 @@ __global__ void k_integrate(int N, float4* __restrict__ xq, float4* __restrict__
     ke_atom[i] = (w > 0.f) ? 0.5f * (vi.x * vi.x + vi.y * vi.y + vi.z * vi.z) / w : 0.f;
     if (ck_x) ck_x[i] = x;
     if (ck_v) ck_v[i] = make_float4(vi.x, vi.y, vi.z, w);
+    if (ob.x0) {
+        const SysDev& S = sys[si];
+        const float4 b0 = ob.x0[i];
+        float dx = x.x - b0.x, dy = x.y - b0.y, dz = x.z - b0.z;
+        if (S.periodic) {
+            dx = mi_any(dx, S.L[0], S.invL[0]);
+            dy = mi_any(dy, S.L[1], S.invL[1]);
+            dz = mi_any(dz, S.L[2], S.invL[2]);
+        }
+        ob.jump[i] = (double)dx * dx + (double)dy * dy + (double)dz * dz;
+        if (ob.l_prop[si] == ob.step) ob.x_prop[i] = x;
+    }
     float b = c_post * h * w;
     vi.x = fmaf(b, F.x, vi.x);
     vi.y = fmaf(b, F.y, vi.y);
@@ -218,82 +254,131 @@ __global__ void k_hmc_restore(int N, float4* __restrict__ x_out, const float4* _
     if (stats[(size_t)sid[i] * 4 + 3] == 0.0) x_out[i] = x0[i];
 }
 
-// ------------------------------------------------------------- HMC adjoint
-
-// lam (slot order) = cf * dt * w * vbar
-__global__ void k_bwd_lambda(int N, const float4* __restrict__ vbar, const float* __restrict__ w,
-                             const float* __restrict__ dt, const int* __restrict__ sid, const int* __restrict__ iperm,
-                             float cf, float4* __restrict__ lam) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    float c = cf * dt[sid[i]] * w[i];
-    float4 b = vbar[i];
-    lam[iperm[i]] = make_float4(c * b.x, c * b.y, c * b.z, 0.f);
-}
-
-// Adjoint of the loss at the final state: xbar = g_jump 2 mi(x_L - x_0), vbar = dHbar v_L / w,
-// wbar += -dHbar |v_L|^2 / (2 w^2), dHbar = g_alpha dalpha/d dH.
-__global__ void k_bwd_init(int N, const float4* __restrict__ xL, const float4* __restrict__ vL,
-                           const float4* __restrict__ x0, const float* __restrict__ w, const int* __restrict__ sid,
-                           const SysDev* __restrict__ sys, const double* __restrict__ stats,
-                           const double* __restrict__ g_alpha, const double* __restrict__ g_jump, double kT,
-                           float4* __restrict__ xbar, float4* __restrict__ vbar, float* __restrict__ wbar,
-                           double* __restrict__ dhbar) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    int s = sid[i];
-    const SysDev& S = sys[s];
-    double a = stats[(size_t)s * 4 + 1];
-    double dHb = (a < 1.0) ? -g_alpha[s] * a / kT : 0.0;
-    if (i == S.atom_off) dhbar[s] = dHb;
-    float4 p = xL[i], q = x0[i], v = vL[i];
-    float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
-    if (S.periodic) {
-        dx = mi_any(dx, S.L[0], S.invL[0]);
-        dy = mi_any(dy, S.L[1], S.invL[1]);
-        dz = mi_any(dz, S.L[2], S.invL[2]);
+// The proposal of each system is the state after l_prop[s] steps (Sec. 4: the length is
+// drawn from the discretised folded normal): its statistics are that step's, and the
+// Metropolis test u[s] < alpha decides.  A length outside [1, n_leap] is reported and
+// the system keeps x0.
+__global__ void k_hmc_pick(int n_sys, const int* __restrict__ l_prop, int n_leap,
+                           const double* __restrict__ step_stats, const double* __restrict__ u,
+                           double* __restrict__ stats, unsigned* __restrict__ err) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_sys) return;
+    const int l = l_prop[s];
+    double* o = stats + (size_t)s * 4;
+    if (l < 1 || l > n_leap) {
+        atomicOr(err, NB_DEVERR_ARG);
+        o[0] = 0.0;
+        o[1] = 0.0;
+        o[2] = 0.0;
+        o[3] = 0.0;
+        return;
     }
-    float gj = 2.f * (float)g_jump[s];
-    xbar[i] = make_float4(gj * dx, gj * dy, gj * dz, 0.f);
-    float wi = w[i];
-    float fb = (wi > 0.f) ? (float)dHb / wi : 0.f;
-    vbar[i] = make_float4(fb * v.x, fb * v.y, fb * v.z, 0.f);
-    if (wi > 0.f) wbar[i] += -(float)dHb * 0.5f * (v.x * v.x + v.y * v.y + v.z * v.z) / (wi * wi);
+    const double* q = step_stats + ((size_t)(l - 1) * n_sys + s) * 3;
+    o[0] = q[0];
+    o[1] = q[1];
+    o[2] = q[2];
+    o[3] = (u[s] < q[1]) ? 1.0 : 0.0;
 }
 
-// One state s of the reverse sweep, after the VJP kernel at x_s:
-//   xbar += (dF/dx)^T lam [- dHbar F_s at the final state]
-//   hbar += cf w F_s . vbar ; wbar += cf dt F_s . vbar
-//   (drift of step s-1) hbar += p_{s-1} . xbar ; vbar += dt xbar
+// ------------------------------------------------------------- HMC adjoint
+//
+// Reverse sweep over the states l = L..1 of the trajectory.  Entering state l, xbar is
+// the cotangent of x_l and vbar that of the half-step velocity v_{l+1/2} (zero at l = L).
+// A loss term at state l (acceptance probability alpha_l of H_l = U(x_l) + K(v_l), the
+// squared jump |mi(x_l - x_0)|^2) adds
+//   c_v = dHbar v_l / w                     to the cotangent of v_l,
+//   2 gj mi(x_l - x_0) - dHbar F_l          to xbar,
+//   -dHbar |v_l|^2 / (2 w^2)                to wbar (K = |v|^2 / 2w at fixed v),
+// with dHbar = ga dalpha/ddH = -ga alpha / kT where alpha < 1.  The two half kicks
+// around v_l, v_{l+1/2} = v_l + (dt/2) w F_l and v_l = v_{l-1/2} + (dt/2) w F_l, then
+// pass u = 2 vbar + c_v through F: the force VJP takes lam = (dt/2) w u, and the step and
+// inverse mass collect (1/2) w F.u and (dt/2) F.u.  The cotangent of v_{l-1/2} is
+// vbar + c_v; the drift x_l = x_{l-1} + dt v_{l-1/2} then adds dt xbar to it and
+// v_{l-1/2}.xbar to the step's cotangent.
+
+__device__ __forceinline__ float inject_dhbar(const Inject& inj, int s, double kT) {
+    if (!inj.ga) return 0.f;
+    const double a = inj.alpha[(size_t)s * inj.a_stride];
+    return (a < 1.0) ? (float)(-inj.ga[s] * a / kT) : 0.f;
+}
+
+// lam (slot order) = (dt/2) w (2 vbar + c_v)
+__global__ void k_bwd_lambda(int N, const float4* __restrict__ vbar, const float4* __restrict__ v_state,
+                             const float* __restrict__ w, const float* __restrict__ dt, const int* __restrict__ sid,
+                             const int* __restrict__ iperm, Inject inj, double kT, float4* __restrict__ lam) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int s = sid[i];
+    const float wi = w[i];
+    const float c = 0.5f * dt[s] * wi;
+    const float4 b = vbar[i];
+    float ux = 2.f * b.x, uy = 2.f * b.y, uz = 2.f * b.z;
+    const float d = inject_dhbar(inj, s, kT);
+    if (d != 0.f && wi > 0.f) {
+        const float4 v = v_state[i];
+        const float fb = d / wi;
+        ux = fmaf(fb, v.x, ux);
+        uy = fmaf(fb, v.y, uy);
+        uz = fmaf(fb, v.z, uz);
+    }
+    lam[iperm[i]] = make_float4(c * ux, c * uy, c * uz, 0.f);
+}
+
+// One state of the reverse sweep, after the VJP kernels wrote gx_s = (dF/dx)^T lam.
 __global__ void k_bwd_adjoint(int N, const float4* __restrict__ gx_s, const long long* __restrict__ ffix,
                               const int* __restrict__ iperm, float finv, const float* __restrict__ w,
-                              const float* __restrict__ dt, const int* __restrict__ sid, float cf,
-                              const double* __restrict__ dhbar, int last, const float4* __restrict__ p_prev,
+                              const float* __restrict__ dt, const int* __restrict__ sid,
+                              const SysDev* __restrict__ sys, Inject inj, double kT,
+                              const float4* __restrict__ x_state, const float4* __restrict__ v_state,
+                              const float4* __restrict__ x0, const float4* __restrict__ p_prev,
                               float4* __restrict__ xbar, float4* __restrict__ vbar, float* __restrict__ wbar,
                               double* __restrict__ hbar) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    int s = sid[i];
-    int k = iperm[i];
-    float h = dt[s];
-    float wi = w[i];
-    float3 F = load_force(ffix, N, k, finv);
-    float4 g = gx_s[k];
+    const int s = sid[i];
+    const int k = iperm[i];
+    const float h = dt[s];
+    const float wi = w[i];
+    const float3 F = load_force(ffix, N, k, finv);
+    const float4 g = gx_s[k];
     float4 xb = xbar[i], vb = vbar[i];
+    float ux = 2.f * vb.x, uy = 2.f * vb.y, uz = 2.f * vb.z;
     xb.x += g.x;
     xb.y += g.y;
     xb.z += g.z;
-    if (last) {
-        float d = (float)dhbar[s];
-        xb.x -= d * F.x;
-        xb.y -= d * F.y;
-        xb.z -= d * F.z;
+    float wb = 0.f;
+    if (inj.ga) {
+        const float d = inject_dhbar(inj, s, kT);
+        const float gj = 2.f * (float)inj.gj[s];
+        const SysDev& S = sys[s];
+        const float4 p = x_state[i], q = x0[i];
+        float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+        if (S.periodic) {
+            dx = mi_any(dx, S.L[0], S.invL[0]);
+            dy = mi_any(dy, S.L[1], S.invL[1]);
+            dz = mi_any(dz, S.L[2], S.invL[2]);
+        }
+        xb.x += gj * dx - d * F.x;
+        xb.y += gj * dy - d * F.y;
+        xb.z += gj * dz - d * F.z;
+        if (d != 0.f && wi > 0.f) {
+            const float4 v = v_state[i];
+            const float fb = d / wi;
+            const float cx = fb * v.x, cy = fb * v.y, cz = fb * v.z;
+            ux += cx;
+            uy += cy;
+            uz += cz;
+            vb.x += cx;
+            vb.y += cy;
+            vb.z += cz;
+            wb = -d * 0.5f * (v.x * v.x + v.y * v.y + v.z * v.z) / (wi * wi);
+        }
     }
-    float fv = F.x * vb.x + F.y * vb.y + F.z * vb.z;
-    double hb = (double)(cf * wi * fv);
-    wbar[i] += cf * h * fv;
-    float4 p = p_prev[i];
-    hb += (double)(p.x * xb.x + p.y * xb.y + p.z * xb.z);
+    const float fu = F.x * ux + F.y * uy + F.z * uz;
+    double hb = (double)(0.5f * wi * fu);
+    wbar[i] += wb + 0.5f * h * fu;
+    const float4 pv = p_prev[i];
+    hb += (double)(pv.x * xb.x + pv.y * xb.y + pv.z * xb.z);
     vb.x = fmaf(h, xb.x, vb.x);
     vb.y = fmaf(h, xb.y, vb.y);
     vb.z = fmaf(h, xb.z, vb.z);
@@ -340,10 +425,11 @@ __global__ void __launch_bounds__(kRedThreads) k_bwd_reduce_h(const SysDev* __re
 
 // ------------------------------------------------------------------ launchers
 
-void launch_reduce_energy(nb_handle* h, int terms, int with_kin, double* dst, cudaStream_t st) {
+void launch_reduce_energy(nb_handle* h, int terms, int with_kin, double* dst, cudaStream_t st, const StepStat& ss) {
     k_reduce_energy<<<h->n_red_blocks, kRedThreads, 0, st>>>(h->n_sys, h->red_blk_sys, h->red_blk_off, h->sys,
                                                             h->e_atom, h->xs, h->ke_atom, with_kin, h->red_part,
-                                                            h->e_pme_blk, h->conv_blk_off, terms, h->red_ticket, dst);
+                                                            h->e_pme_blk, h->conv_blk_off, terms, h->red_ticket, dst,
+                                                            ss);
 }
 
 void launch_finalize_forces(nb_handle* h, float* f_out, cudaStream_t st) {
@@ -352,10 +438,11 @@ void launch_finalize_forces(nb_handle* h, float* f_out, cudaStream_t st) {
 }
 
 void launch_integrate(nb_handle* h, float4* xq, float4* v, const float* w_ovr, const float* dt, float c_pre,
-                      float c_post, int drift, float4* ck_x, float4* ck_v, float4* ck_p, cudaStream_t st) {
+                      float c_post, int drift, float4* ck_x, float4* ck_v, float4* ck_p, cudaStream_t st,
+                      const StepObs& ob) {
     int N = h->n_atoms;
     k_integrate<<<cdiv(N, 256), 256, 0, st>>>(N, xq, v, w_ovr, dt, h->sid, h->ffix, h->iperm, h->finv, c_pre, c_post,
-                                              drift, h->ke_atom, ck_x, ck_v, ck_p);
+                                              drift, h->ke_atom, ck_x, ck_v, ck_p, h->sys, ob);
 }
 
 void launch_hmc_init(nb_handle* h, const float* w, const float* xi, double kT, cudaStream_t st) {
@@ -371,24 +458,26 @@ void launch_hmc_finish(nb_handle* h, float4* x_out, const float4* x0, double kT,
     k_hmc_restore<<<cdiv(N, 256), 256, 0, st>>>(N, x_out, x0, h->sid, stats);
 }
 
-void launch_bwd_lambda(nb_handle* h, const float* w, const float* dt, float cf, cudaStream_t st) {
+void launch_hmc_pick(nb_handle* h, float4* x_out, const float4* x0, const int* l_prop, int n_leap,
+                     const double* step_stats, const double* u, double* stats, cudaStream_t st) {
     int N = h->n_atoms;
-    k_bwd_lambda<<<cdiv(N, 256), 256, 0, st>>>(N, h->vbar, w, dt, h->sid, h->iperm, cf, h->lam);
+    k_hmc_pick<<<cdiv(h->n_sys, 128), 128, 0, st>>>(h->n_sys, l_prop, n_leap, step_stats, u, stats, h->flags + 1);
+    k_hmc_restore<<<cdiv(N, 256), 256, 0, st>>>(N, x_out, x0, h->sid, stats);
 }
 
-void launch_bwd_init(nb_handle* h, const float4* xL, const float4* vL, const float4* x0, const float* w,
-                     const double* stats, const double* g_alpha, const double* g_jump, double kT, float* wbar,
-                     cudaStream_t st) {
+void launch_bwd_lambda(nb_handle* h, const float* w, const float* dt, const float4* v_state, const Inject& inj,
+                       double kT, cudaStream_t st) {
     int N = h->n_atoms;
-    k_bwd_init<<<cdiv(N, 256), 256, 0, st>>>(N, xL, vL, x0, w, h->sid, h->sys, stats, g_alpha, g_jump, kT, h->xbar,
-                                             h->vbar, wbar, h->dhbar);
+    k_bwd_lambda<<<cdiv(N, 256), 256, 0, st>>>(N, h->vbar, v_state, w, dt, h->sid, h->iperm, inj, kT, h->lam);
 }
 
-void launch_bwd_adjoint(nb_handle* h, const float* w, const float* dt, float cf, int last, const float4* p_prev,
-                        float* wbar, cudaStream_t st) {
+void launch_bwd_adjoint(nb_handle* h, const float* w, const float* dt, const float4* x_state, const float4* v_state,
+                        const float4* x0, const Inject& inj, double kT, const float4* p_prev, float* wbar,
+                        cudaStream_t st) {
     int N = h->n_atoms;
-    k_bwd_adjoint<<<cdiv(N, 256), 256, 0, st>>>(N, h->gx_s, h->ffix, h->iperm, h->finv, w, dt, h->sid, cf, h->dhbar,
-                                                last, p_prev, h->xbar, h->vbar, wbar, h->hbar_atom);
+    k_bwd_adjoint<<<cdiv(N, 256), 256, 0, st>>>(N, h->gx_s, h->ffix, h->iperm, h->finv, w, dt, h->sid, h->sys, inj,
+                                                kT, x_state, v_state, x0, p_prev, h->xbar, h->vbar, wbar,
+                                                h->hbar_atom);
 }
 
 void launch_bwd_final(nb_handle* h, const float* w, const float* dt, const float* xi, double kT, float* wbar,

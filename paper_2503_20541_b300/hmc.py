@@ -13,6 +13,15 @@ dt = |mu + 0.01 mu eps| (reparameterised, eps frozen per iteration), and the per
 masses keep the total mass fixed, m_t = M s_t / sum_t n_t s_t with s_t = exp(logit_t).
 ``train_esjd`` maximises the expected squared jump distance per force evaluation,
 (1/R) sum_r alpha_r |x'_r - x_r|^2 / L, with Adam over (log mu, mass logits).
+
+The trajectory length of Sec. 4 is a folded normal N_F(mu_L, sigma_L = 1) as well:
+``HMCStepsProposal`` runs L_q steps (L_q = ceil of the 0.999 quantile) and returns the
+acceptance probability and squared jump of every intermediate state, the proposal being
+the state after a length drawn from the discretised N_F.  ``lhmc_loss`` is Eq. loss_steps,
+(1/R) sum_i sum_{l<=L_q} N_F(l; mu_L, sigma_L) alpha_{i,l} |x_{i,l} - x_i|^2 / l, which is
+differentiable in mu_L through the weights; ``train_lhmc`` maximises it over (log dt mean,
+log mu_L, mass logits).  Only the parameterisations (weights, quantile, length draw) are
+torch or host arithmetic; the trajectories and their adjoint run in libnbcore.
 """
 import math
 
@@ -59,6 +68,95 @@ class HMCProposal(torch.autograd.Function):
         g_w = torch.zeros(N, dtype=torch.float32, device=x0.device)
         h.hmc_trajectory_backward(x0, wd, dtd, n_leap, kT, xi, ck, ckpt_every, stats, ga, gj, g_dt, g_w, terms=terms)
         return (g_w.to(w_dtype), g_dt.to(dt_dtype), None, None, None, None, None, None, None, None)
+
+
+class HMCStepsProposal(torch.autograd.Function):
+    """(alpha, jump, x_out, stats) = HMCStepsProposal.apply(w, dt, h, x0, xi, u, l_prop, n_leap, kT, ckpt_every, terms)
+
+    As ``HMCProposal``, with n_leap = L_q steps per replica and the proposal taken after
+    l_prop[r] steps (int32, (R,), in [1, n_leap]).  alpha and jump are (n_leap, R) float64:
+    the acceptance probability and squared jump of every state l = 1..n_leap.  stats is
+    (R, 4) float64 (dH, alpha, jump, accepted) of the proposal.  Gradients flow to w and dt
+    through alpha and jump.
+    """
+
+    @staticmethod
+    def forward(ctx, w, dt, h, x0, xi, u, l_prop, n_leap, kT, ckpt_every, terms):
+        R, N = h.n_sys, h.n_atoms
+        wd = w.detach().to(torch.float32).contiguous()
+        dtd = dt.detach().to(torch.float32).contiguous()
+        x_out = torch.empty_like(x0)
+        stats = torch.empty((R, 4), dtype=torch.float64, device=x0.device)
+        sst = torch.empty((n_leap, R, 3), dtype=torch.float64, device=x0.device)
+        ck = torch.empty(nbcore.ckpt_size(N, n_leap, ckpt_every), dtype=torch.float32, device=x0.device)
+        h.hmc_trajectory_steps(x0, x_out, wd, dtd, n_leap, l_prop, kT, xi, u, stats, sst, ck, ckpt_every, terms=terms)
+        ctx.h = h
+        ctx.cfg = (n_leap, kT, ckpt_every, terms, w.dtype, dt.dtype)
+        ctx.save_for_backward(wd, dtd, x0, xi, ck, sst)
+        ctx.mark_non_differentiable(x_out, stats)
+        return sst[:, :, 1].clone(), sst[:, :, 2].clone(), x_out, stats
+
+    @staticmethod
+    def backward(ctx, g_alpha, g_jump, g_x, g_stats):
+        wd, dtd, x0, xi, ck, sst = ctx.saved_tensors
+        n_leap, kT, ckpt_every, terms, w_dtype, dt_dtype = ctx.cfg
+        h = ctx.h
+        R, N = h.n_sys, h.n_atoms
+        z = torch.zeros((n_leap, R), dtype=torch.float64, device=x0.device)
+        ga = z if g_alpha is None else g_alpha.to(torch.float64).contiguous()
+        gj = z if g_jump is None else g_jump.to(torch.float64).contiguous()
+        g_dt = torch.zeros(R, dtype=torch.float64, device=x0.device)
+        g_w = torch.zeros(N, dtype=torch.float32, device=x0.device)
+        h.hmc_trajectory_steps_backward(x0, wd, dtd, n_leap, kT, xi, ck, ckpt_every, sst, ga, gj, g_dt, g_w,
+                                        terms=terms)
+        return (g_w.to(w_dtype), g_dt.to(dt_dtype), None, None, None, None, None, None, None, None, None)
+
+
+def folded_normal_pdf(x, mu, sigma):
+    """N_F(x; mu, sigma) = N(x; mu, sigma) + N(-x; mu, sigma) (Sec. 4), differentiable in mu."""
+    c = 1.0 / math.sqrt(2.0 * math.pi * sigma * sigma)
+    return c * (torch.exp(-(x - mu) ** 2 / (2.0 * sigma * sigma)) + torch.exp(-(x + mu) ** 2 / (2.0 * sigma * sigma)))
+
+
+def folded_normal_quantile(p, mu, sigma):
+    """Q(p) of N_F(mu, sigma) by bisection on its CDF 1/2 [erf((x+mu)/(s sqrt2)) + erf((x-mu)/(s sqrt2))]."""
+    s = sigma * math.sqrt(2.0)
+    cdf = lambda x: 0.5 * (math.erf((x + mu) / s) + math.erf((x - mu) / s))  # noqa: E731
+    lo, hi = 0.0, abs(mu) + sigma
+    while cdf(hi) < p:
+        hi *= 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if cdf(mid) < p:
+            lo = mid
+        else:
+            hi = mid
+        if hi - lo <= 1e-13 * max(1.0, hi):
+            break
+    return 0.5 * (lo + hi)
+
+
+def length_cutoff(mu_L, sigma_L=1.0, p=0.999):
+    """L_q = ceil(Q(0.999)) of N_F(mu_L, sigma_L): the trajectory length every replica runs."""
+    return max(1, int(math.ceil(folded_normal_quantile(p, float(mu_L), sigma_L))))
+
+
+def draw_lengths(mu_L, sigma_L, L_q, u):
+    """Proposal lengths l in 1..L_q with probabilities proportional to N_F(l; mu_L, sigma_L),
+    by inverse transform of the uniforms u (R,) -> int32 (R,) on u's device."""
+    ell = torch.arange(1, L_q + 1, dtype=torch.float64, device=u.device)
+    w = folded_normal_pdf(ell, torch.as_tensor(float(mu_L), dtype=torch.float64, device=u.device), sigma_L)
+    c = torch.cumsum(w, 0) / torch.sum(w)
+    return (torch.searchsorted(c, u.to(torch.float64).contiguous(), right=True) + 1).clamp_(max=L_q).to(torch.int32)
+
+
+def lhmc_loss(alpha, jump, mu_L, sigma_L=1.0):
+    """Eq. loss_steps: (1/R) sum_i sum_{l=1}^{L_q} w_l alpha_{i,l} jump_{i,l} / l, with
+    alpha, jump (L_q, R) and w_l = N_F(l; mu_L, sigma_L) (mu_L a tensor: differentiable)."""
+    L_q, R = alpha.shape
+    ell = torch.arange(1, L_q + 1, dtype=alpha.dtype, device=alpha.device)
+    w = folded_normal_pdf(ell, mu_L.to(alpha.dtype), sigma_L)
+    return torch.sum((w / ell)[:, None] * alpha * jump) / R
 
 
 def folded_normal_step(log_mu, eps, rel_sigma=0.01):
@@ -111,6 +209,59 @@ def train_esjd(h, x0, types, m_total, iters=200, n_leap=32, kT=1.0, ckpt_every=8
         x = x_new
         rec = {"it": it, "loss": -float(loss.detach()), "mu": float(torch.exp(log_mu.detach())),
                "alpha": float(alpha.detach().mean()), "accepted": float(acc.mean())}
+        with torch.no_grad():
+            s = torch.exp(logits)
+            counts = torch.bincount(types, minlength=n_types).to(s.dtype)
+            rec["mass_per_type"] = (m_total * s / torch.sum(counts * s)).tolist()
+        hist.append(rec)
+        if callback is not None:
+            callback(rec)
+    return hist
+
+
+def train_lhmc(h, x0, types, m_total, iters=200, kT=1.0, ckpt_every=8, lr=0.05, log_mu0=math.log(0.005),
+               mu_L0=32.0, sigma_L=1.0, logits0=None, seed=0, terms=nbcore.NB_TERM_LJ, callback=None):
+    """Adam on (log dt mean, log mu_L, mass logits) maximising L_HMC (Eq. loss_steps).
+
+    Each iteration: L_q from the current mu_L, dt per replica from its folded normal,
+    proposal lengths drawn from the discretised N_F(mu_L, sigma_L), one L_q-step
+    trajectory per replica, the gradient of L_HMC through the weights (mu_L) and the
+    trajectories (dt, masses), and every chain continues from its accepted/rejected state.
+    Returns the per-iteration history (loss, dt mean, mu_L, L_q, masses per type, mean
+    alpha of the proposals, acceptance).
+    """
+    dev = x0.device
+    R = h.n_sys
+    n = types.numel()
+    n_types = int(types.max().item()) + 1
+    log_mu = torch.tensor(log_mu0, dtype=torch.float64, device=dev, requires_grad=True)
+    log_mu_L = torch.tensor(math.log(mu_L0), dtype=torch.float64, device=dev, requires_grad=True)
+    logits = torch.zeros(n_types, dtype=torch.float64, device=dev) if logits0 is None else \
+        torch.as_tensor(logits0, dtype=torch.float64, device=dev).clone()
+    logits.requires_grad_(True)
+    opt = torch.optim.Adam([log_mu, log_mu_L, logits], lr=lr)
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    x = x0.clone()
+    hist = []
+    for it in range(iters):
+        mu_L = torch.exp(log_mu_L)
+        L_q = length_cutoff(float(mu_L.detach()), sigma_L)
+        eps = torch.randn(R, dtype=torch.float64, device=dev, generator=gen)
+        xi = torch.randn((R * n, 3), dtype=torch.float32, device=dev, generator=gen)
+        u = torch.rand(R, dtype=torch.float64, device=dev, generator=gen)
+        ul = torch.rand(R, dtype=torch.float64, device=dev, generator=gen)
+        l_prop = draw_lengths(float(mu_L.detach()), sigma_L, L_q, ul)
+        dt = folded_normal_step(log_mu, eps)
+        w = (1.0 / masses_from_logits(logits, types, m_total)).repeat(R)
+        alpha, jump, x_new, stats = HMCStepsProposal.apply(w, dt, h, x, xi, u, l_prop, L_q, kT, ckpt_every, terms)
+        loss = -lhmc_loss(alpha, jump, mu_L, sigma_L)
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+        x = x_new
+        rec = {"it": it, "loss": -float(loss.detach()), "mu": float(torch.exp(log_mu.detach())),
+               "mu_L": float(mu_L.detach()), "L_q": L_q, "alpha": float(stats[:, 1].mean()),
+               "accepted": float(stats[:, 3].mean())}
         with torch.no_grad():
             s = torch.exp(logits)
             counts = torch.bincount(types, minlength=n_types).to(s.dtype)

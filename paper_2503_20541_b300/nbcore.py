@@ -32,8 +32,8 @@ STATUS = {
 EXPORTS = [
     "nb_status_str", "nb_create", "nb_destroy", "nb_num_atoms", "nb_num_systems", "nb_check",
     "nl_build", "nonbonded_forces", "nonbonded_forces_allpairs", "pme_spread", "pme_gather", "md_step", "hmc_trajectory",
-    "hmc_trajectory_backward", "nonbonded_force_vjp", "nb_rebuild_count", "nb_timing_enable", "nb_timing_read",
-    "pme_spread_static",
+    "hmc_trajectory_backward", "hmc_trajectory_steps", "hmc_trajectory_steps_backward", "autocorrelation",
+    "nonbonded_force_vjp", "nb_rebuild_count", "nb_timing_enable", "nb_timing_read", "pme_spread_static",
 ]
 STATIC_MESH_MAX = 1 << 20
 STAGES = ["check", "rebuild", "pair", "spread", "fft", "convolve", "gather", "update"]
@@ -117,6 +117,14 @@ def load():
     lib.hmc_trajectory_backward.restype = ctypes.c_int
     lib.hmc_trajectory_backward.argtypes = [_vp, _vp, _vp, _vp, _i32, _dbl, _vp, _vp, _i32, _vp, _vp, _vp, _vp,
                                             _vp, _i32, _vp]
+    lib.hmc_trajectory_steps.restype = ctypes.c_int
+    lib.hmc_trajectory_steps.argtypes = [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _dbl, _vp, _vp, _vp, _vp, _vp, _i32,
+                                         _i32, _vp]
+    lib.hmc_trajectory_steps_backward.restype = ctypes.c_int
+    lib.hmc_trajectory_steps_backward.argtypes = [_vp, _vp, _vp, _vp, _i32, _dbl, _vp, _vp, _i32, _vp, _vp, _vp,
+                                                  _vp, _vp, _i32, _vp]
+    lib.autocorrelation.restype = ctypes.c_int
+    lib.autocorrelation.argtypes = [_vp, _i32, _i32, _i32, _dbl, _dbl, _vp, _vp, _vp]
     lib.nonbonded_force_vjp.restype = ctypes.c_int
     lib.nonbonded_force_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp]
     lib.nb_timing_enable.restype = ctypes.c_int
@@ -174,6 +182,22 @@ def pme_spread_static(xq, box, mesh, grid):
                               _ptr(grid, torch.float32, (int(np.prod(m.astype(np.int64))),), "grid"), _stream()),
         "pme_spread_static")
     return grid
+
+
+def autocorrelation(series, max_lag, a_hi=0.5, a_lo=0.05, acf=None, tau=None):
+    """A(k), k = 0..max_lag, and tau_exp of each row of ``series`` ((n_series, n) float64
+    on the device) -- autocorrelation in include/nbcore.h.  Returns (acf, tau)."""
+    torch = _torch()
+    lib = load()
+    ns, n = int(series.shape[0]), int(series.shape[1])
+    if acf is None:
+        acf = torch.empty((ns, max_lag + 1), dtype=torch.float64, device=series.device)
+    if tau is None:
+        tau = torch.empty(ns, dtype=torch.float64, device=series.device)
+    _ok(lib.autocorrelation(_ptr(series, torch.float64, (ns, n), "series"), ns, n, int(max_lag), float(a_hi),
+                            float(a_lo), _ptr(acf, torch.float64, (ns, max_lag + 1), "acf"),
+                            _ptr(tau, torch.float64, (ns,), "tau"), _stream()), "autocorrelation")
+    return acf, tau
 
 
 def ckpt_size(n_atoms, n_leap, ckpt_every):
@@ -363,6 +387,33 @@ class Handle:
             _ptr(g_dt, torch.float64, (self.n_sys,), "g_dt"),
             _ptr(g_inv_mass, torch.float32, (N,), "g_inv_mass"), int(terms), _stream()),
             "hmc_trajectory_backward")
+
+    def hmc_trajectory_steps(self, x0, x_out, inv_mass, dt, n_leap, l_prop, kT, xi, u, stats, step_stats, ckpt=None,
+                             ckpt_every=0, terms=NB_TERM_ALL):
+        torch = _torch()
+        N, R = self.n_atoms, self.n_sys
+        ck_shape = (ckpt_size(N, n_leap, ckpt_every),) if ckpt is not None else None
+        _ok(self._lib.hmc_trajectory_steps(
+            self._h, _ptr(x0, torch.float32, (N, 4), "x0"), _ptr(x_out, torch.float32, (N, 4), "x_out"),
+            _ptr(inv_mass, torch.float32, (N,), "inv_mass"), _ptr(dt, torch.float32, (R,), "dt"), int(n_leap),
+            _ptr(l_prop, torch.int32, (R,), "l_prop"), float(kT), _ptr(xi, torch.float32, (N, 3), "xi"),
+            _ptr(u, torch.float64, (R,), "u"), _ptr(stats, torch.float64, (R, 4), "stats"),
+            _ptr(step_stats, torch.float64, (n_leap, R, 3), "step_stats"),
+            _ptr(ckpt, torch.float32, ck_shape, "ckpt", True), int(ckpt_every), int(terms), _stream()),
+            "hmc_trajectory_steps")
+
+    def hmc_trajectory_steps_backward(self, x0, inv_mass, dt, n_leap, kT, xi, ckpt, ckpt_every, step_stats, g_alpha,
+                                      g_jump, g_dt, g_inv_mass, terms=NB_TERM_LJ | NB_TERM_COUL):
+        torch = _torch()
+        N, R = self.n_atoms, self.n_sys
+        _ok(self._lib.hmc_trajectory_steps_backward(
+            self._h, _ptr(x0, torch.float32, (N, 4), "x0"), _ptr(inv_mass, torch.float32, (N,), "inv_mass"),
+            _ptr(dt, torch.float32, (R,), "dt"), int(n_leap), float(kT), _ptr(xi, torch.float32, (N, 3), "xi"),
+            _ptr(ckpt, torch.float32, (ckpt_size(N, n_leap, ckpt_every),), "ckpt"), int(ckpt_every),
+            _ptr(step_stats, torch.float64, (n_leap, R, 3), "step_stats"),
+            _ptr(g_alpha, torch.float64, (n_leap, R), "g_alpha"), _ptr(g_jump, torch.float64, (n_leap, R), "g_jump"),
+            _ptr(g_dt, torch.float64, (R,), "g_dt"), _ptr(g_inv_mass, torch.float32, (N,), "g_inv_mass"),
+            int(terms), _stream()), "hmc_trajectory_steps_backward")
 
     def nonbonded_force_vjp(self, xq, lam, gx, gq=None, gsigma=None, gsqrt_eps=None, f_out=None,
                             terms=NB_TERM_LJ | NB_TERM_COUL):

@@ -8,7 +8,8 @@ imports it.
 Contents (each cites the passage of the paper it follows):
   * ``nonbonded`` / ``nonbonded_rows`` -- all-pairs LJ (Eq. lj, Lorentz-Berthelot
     mixing, optional switch S(x)) + Ewald direct erfc sum + exclusion correction +
-    self energy (Sec. 2.1.2), in C (oracle.c).
+    self energy, or the reaction field (Eq. RFA) instead of the Ewald terms
+    (Sec. 2.1.2), in C (oracle.c).
   * ``ewald_recip`` -- exact reciprocal-space structure-factor sum (Sec. 2.1.2).
   * ``neighbor_pairs`` -- brute-force Verlet pair set at r_nl = r_c + r_g.
   * ``force_vjp`` -- analytic pair-Jacobian vector product of the real-space forces.
@@ -40,6 +41,7 @@ class OrcParams(ctypes.Structure):
         ("r_switch", ctypes.c_double),
         ("alpha", ctypes.c_double),
         ("ke", ctypes.c_double),
+        ("eps_rf", ctypes.c_double),
     ]
 
 
@@ -61,7 +63,10 @@ def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
 
 
-def make_params(box, r_cut, r_switch=-1.0, alpha=0.0, ke=0.0, periodic=True):
+def make_params(box, r_cut, r_switch=-1.0, alpha=0.0, ke=0.0, periodic=True, eps_rf=0.0):
+    """Oracle parameters; eps_rf > 0 selects the reaction field (Eq. RFA) with solvent
+    dielectric eps_rf in place of the Ewald direct term (alpha must then be 0)."""
+    assert not (eps_rf > 0.0 and alpha > 0.0)
     p = OrcParams()
     b = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
     for k in range(3):
@@ -71,6 +76,7 @@ def make_params(box, r_cut, r_switch=-1.0, alpha=0.0, ke=0.0, periodic=True):
     p.r_switch = float(r_switch)
     p.alpha = float(alpha)
     p.ke = float(ke)
+    p.eps_rf = float(eps_rf)
     return p
 
 

@@ -38,6 +38,7 @@ typedef struct {
     double r_switch;   /* r_s of the LJ switch S(x); < 0 disables it */
     double alpha;      /* Ewald splitting parameter; 0 = bare truncated Coulomb */
     double ke;         /* Coulomb constant 1/(4 pi eps0) in the caller's units */
+    double eps_rf;     /* reaction field: solvent dielectric eps_s (> 0 selects it, alpha = 0) */
 } orc_params;
 
 static double mi(double a, double L, int periodic) {
@@ -97,6 +98,25 @@ static void erfc_terms(double r, double a, double* g, double* dg, double* d2g) {
     *d2g = 2.0 * ec / (r * r * r) + 2.0 * gau / (r * r) + 2.0 * a * a * gau;
 }
 
+/* ---- Reaction field (RFA, Sec. 2.1.2): g(r) = 1/r + k r^2 - c, r < r_c, with
+ * k = (eps_s - 1) / ((2 eps_s + 1) r_c^3) and c = 3 eps_s / ((2 eps_s + 1) r_c), so that
+ * g(r_c) = 0 (the printed denominators 2 eps + 1 read as 2 eps_s + 1, which is what makes
+ * c = 1/r_c + k r_c^2). ---- */
+static void rf_terms(double r, double rc, double eps_s, double* g, double* dg, double* d2g) {
+    double k = (eps_s - 1.0) / ((2.0 * eps_s + 1.0) * rc * rc * rc);
+    double c = 3.0 * eps_s / ((2.0 * eps_s + 1.0) * rc);
+    *g = 1.0 / r + k * r * r - c;
+    *dg = -1.0 / (r * r) + 2.0 * k * r;
+    *d2g = 2.0 / (r * r * r) + 2.0 * k;
+}
+
+/* Coulomb pair kernel of the selected electrostatics: reaction field when eps_rf > 0,
+ * else the Ewald direct term (bare 1/r for alpha = 0). */
+static void coul_terms(double r, const orc_params* p, double* g, double* dg, double* d2g) {
+    if (p->eps_rf > 0.0) rf_terms(r, p->r_cut, p->eps_rf, g, dg, d2g);
+    else erfc_terms(r, p->alpha, g, dg, d2g);
+}
+
 /*
  * Full nonbonded energy and forces (definition, all pairs i<j):
  *   E_lj   = sum_{r<rc, not excl} 4 eps_ij[(s/r)^12-(s/r)^6] S      Eq. (lj)
@@ -106,6 +126,9 @@ static void erfc_terms(double r, double a, double* g, double* dg, double* d2g) {
  *            smooth part makes the total equal to "all charges minus the bare
  *            Coulomb of excluded pairs")
  *   E_self = -ke alpha/sqrt(pi) sum_i q_i^2                          Ewald U_self
+ * With the reaction field (eps_rf > 0) E_dir is sum_{r<rc, not excl} ke q_i q_j
+ * (1/r + k r^2 - c), Eq. (RFA), and excluded pairs do not interact (no reciprocal sum
+ * to correct, no self term).
  * energy[0..3] = E_lj, E_dir, E_excl, E_self.  f[3n] = -grad E.
  */
 int orc_nonbonded(int n, const double* x, const double* q, const double* sig, const double* sqe,
@@ -141,7 +164,7 @@ int orc_nonbonded(int n, const double* x, const double* q, const double* sig, co
                 double c = p->ke * q[i] * q[j];
                 if (c != 0.0) {
                     double g, dg, d2g;
-                    erfc_terms(r, p->alpha, &g, &dg, &d2g);
+                    coul_terms(r, p, &g, &dg, &d2g);
                     edir += c * g;
                     dU += c * dg;
                 }
@@ -201,7 +224,7 @@ int orc_nonbonded_rows(int n, const double* x, const double* q, const double* si
                 double c = p->ke * q[i] * q[j];
                 if (c != 0.0) {
                     double g, dg, d2g;
-                    erfc_terms(r, p->alpha, &g, &dg, &d2g);
+                    coul_terms(r, p, &g, &dg, &d2g);
                     edir += 0.5 * c * g;
                     dU += c * dg;
                 }
@@ -295,8 +318,8 @@ int64_t orc_neighbor_pairs(int n, const double* x, const orc_params* p, double r
 }
 
 /*
- * Force vector-Jacobian product of the real-space terms (LJ, Ewald direct,
- * exclusion correction).  For the pair Jacobian
+ * Force vector-Jacobian product of the real-space terms (LJ, Ewald direct or
+ * reaction field, exclusion correction).  For the pair Jacobian
  *   J = dF_i/dx_i = f(r) I + (f'(r)/r) d d^T,   dF_i/dx_j = -J,
  * the product with a cotangent lam gives
  *   gx_i += J (lam_i - lam_j),  gx_j -= J (lam_i - lam_j).
@@ -349,7 +372,7 @@ int orc_force_vjp(int n, const double* x, const double* q, const double* sig, co
                 double c = p->ke * q[i] * q[j];
                 if (p->ke != 0.0) {
                     double g, dg, d2g;
-                    erfc_terms(r, p->alpha, &g, &dg, &d2g);
+                    coul_terms(r, p, &g, &dg, &d2g);
                     dU += c * dg;
                     d2U += c * d2g;
                     gq[i] += -p->ke * q[j] * dg / r * du;

@@ -244,9 +244,12 @@ def test_neighbor_pairs_drop_exclusions():
 
 # ------------------------------------------------ forces, invariances, VJP
 
-def _small_water(seed=4):
+def _small_water(seed=4, elec="ewald"):
     s = wl.water_box(n_side=3, L=9.6, seed=seed, r_cut=4.6, alpha=0.8)
-    p = oracle.make_params(s.box, r_cut=4.6, r_switch=4.0, alpha=0.8, ke=wl.KE_KJ_MOL_A)
+    if elec == "rf":
+        p = oracle.make_params(s.box, r_cut=4.6, r_switch=4.0, ke=wl.KE_KJ_MOL_A, eps_rf=78.5)
+    else:
+        p = oracle.make_params(s.box, r_cut=4.6, r_switch=4.0, alpha=0.8, ke=wl.KE_KJ_MOL_A)
     return s, p
 
 
@@ -257,8 +260,9 @@ def _near_cutoff(x, i, p, rc, tol=2e-3):
     return np.any(np.abs(r - rc) < tol)
 
 
-def test_forces_are_minus_gradient_real_space():
-    s, p = _small_water()
+@pytest.mark.parametrize("elec", ["ewald", "rf"])
+def test_forces_are_minus_gradient_real_space(elec):
+    s, p = _small_water(elec=elec)
     x = s.x.astype(np.float64)
     e, F = oracle.nonbonded(x, s.q, s.sigma, s.sqrt_eps, p, excl=s.excl)
     rng = np.random.default_rng(1)
@@ -301,8 +305,9 @@ def test_newton_third_law_and_translation_invariance():
     np.testing.assert_allclose(F2, F, atol=1e-8 * np.abs(F).max())
 
 
-def test_force_vjp_matches_finite_differences():
-    s, p = _small_water(6)
+@pytest.mark.parametrize("elec", ["ewald", "rf"])
+def test_force_vjp_matches_finite_differences(elec):
+    s, p = _small_water(6, elec=elec)
     x = s.x.astype(np.float64)
     n = s.n
     rng = np.random.default_rng(2)
@@ -335,14 +340,50 @@ def test_force_vjp_matches_finite_differences():
             assert g[k] == pytest.approx(fd, rel=1e-5, abs=1e-4)
 
 
-def test_force_jacobian_is_symmetric():
-    s, p = _small_water(8)
+@pytest.mark.parametrize("elec", ["ewald", "rf"])
+def test_force_jacobian_is_symmetric(elec):
+    s, p = _small_water(8, elec=elec)
     x = s.x.astype(np.float64)
     rng = np.random.default_rng(3)
     g1, g2 = rng.standard_normal((2, s.n, 3))
     v1 = oracle.force_vjp(x, s.q, s.sigma, s.sqrt_eps, p, g1, excl=s.excl)[0]
     v2 = oracle.force_vjp(x, s.q, s.sigma, s.sqrt_eps, p, g2, excl=s.excl)[0]
     assert np.sum(g2 * v1) == pytest.approx(np.sum(g1 * v2), rel=1e-11)
+
+
+# ------------------------------------------------------------ reaction field (Eq. RFA)
+
+def _rf_dimer(r, eps_rf, rc=9.0, excl=False):
+    x = np.array([[5.0, 5.0, 5.0], [5.0 + r, 5.0, 5.0]])
+    q = np.array([0.7, -0.4])
+    p = oracle.make_params(40.0, r_cut=rc, ke=wl.KE_KJ_MOL_A, eps_rf=eps_rf)
+    ex = (np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32)) if excl else None
+    return oracle.nonbonded(x, q, np.ones(2), np.zeros(2), p, excl=ex)
+
+
+def test_reaction_field_special_cases():
+    rc = 9.0
+    qq = wl.KE_KJ_MOL_A * 0.7 * -0.4
+    # eps_s = 1 (no dielectric beyond r_c): Coulomb shifted to vanish at r_c, force unchanged
+    for r in (1.0, 3.7, 8.5):
+        e, f = _rf_dimer(r, 1.0)
+        assert e[1] == pytest.approx(qq * (1.0 / r - 1.0 / rc), rel=1e-13)
+        assert f[0, 0] == pytest.approx(-qq / (r * r), rel=1e-13)
+        assert f[1, 0] == pytest.approx(qq / (r * r), rel=1e-13)
+        assert e[2] == 0.0 and e[3] == 0.0
+    # conducting boundary (eps_s -> infinity): k r_c^3 -> 1/2, c r_c -> 3/2
+    r = 4.5
+    e, f = _rf_dimer(r, 1e15)
+    assert e[1] == pytest.approx(qq * (1.0 / r + r * r / (2 * rc ** 3) - 1.5 / rc), rel=1e-12)
+    assert f[0, 0] == pytest.approx(-qq * (1.0 / (r * r) - r / rc ** 3), rel=1e-12)
+    # the energy goes to zero at the cut-off and is cut beyond it
+    e_in, _ = _rf_dimer(rc * (1 - 1e-12), 78.5)
+    e_out, f_out = _rf_dimer(rc * (1 + 1e-12), 78.5)
+    assert abs(e_in[1]) < 1e-9 * abs(qq) / rc
+    assert e_out[1] == 0.0 and np.all(f_out == 0.0)
+    # excluded pairs do not interact under the reaction field
+    e, f = _rf_dimer(1.0, 78.5, excl=True)
+    assert np.all(e == 0.0) and np.all(f == 0.0)
 
 
 # ------------------------------------------------------------ dynamics / HMC

@@ -64,7 +64,7 @@ typedef enum {
 
 /* Term flags for nonbonded_forces / md_step / hmc_trajectory. */
 #define NB_TERM_LJ 1
-#define NB_TERM_COUL 2   /* Ewald direct + exclusion correction + self */
+#define NB_TERM_COUL 2   /* Ewald direct + exclusion correction + self, or the reaction field */
 #define NB_TERM_PME 4    /* PME reciprocal space (systems with a PME mesh) */
 #define NB_TERM_ALL 7
 #define NB_FORCE_REBUILD 256 /* rebuild the neighbour list unconditionally */
@@ -76,7 +76,13 @@ typedef enum {
  *   LJ with Lorentz-Berthelot mixing, optional switch from r_switch to r_cut;
  *   Ewald splitting alpha, Coulomb constant ke (ke = 0: no charges);
  *   smooth PME of order 4 on a pme_grid[0] x pme_grid[1] x pme_grid[2] mesh
- *   (all zero: no reciprocal space).
+ *   (all zero: no reciprocal space);
+ *   or, with eps_rf >= 1, the reaction field of Eq. RFA instead of Ewald:
+ *   ke q_i q_j (1/r + k r^2 - c) for non-excluded pairs with r < r_cut,
+ *   k = (eps_rf - 1) / ((2 eps_rf + 1) r_cut^3), c = 3 eps_rf / ((2 eps_rf + 1) r_cut)
+ *   (eps_rf the solvent dielectric; excluded pairs do not interact; alpha must be 0 and
+ *   pme_grid all zero).  eps_rf = 0 selects Ewald.  The charged systems of one handle
+ *   must all use the same electrostatics (NB_ERR_ARG otherwise).
  * Periodic systems need box[d] >= 2 r_nl in every dimension.  Open systems
  * (periodic = 0) must keep every coordinate inside [0, box).
  */
@@ -91,6 +97,7 @@ typedef struct {
     double ke;
     int32_t pme_grid[3];
     int32_t pme_order;    /* 4 (the only order implemented) */
+    double eps_rf;        /* reaction field solvent dielectric (>= 1); 0: Ewald */
 } nb_system_desc;
 
 /* Tuning knobs; zero-initialise for defaults. */

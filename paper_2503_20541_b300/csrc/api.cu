@@ -197,6 +197,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
     *out = nullptr;
     if (!sys || n_systems <= 0 || !sigma || !sqrt_eps) return NB_ERR_ARG;
     long long N = 0;
+    int coul_kind = 0;
     for (int s = 0; s < n_systems; ++s) {
         const nb_system_desc& d = sys[s];
         if (d.n_atoms <= 0) return NB_ERR_ARG;
@@ -205,6 +206,16 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         if (!finite_pos(d.r_cut) || !(d.r_skin >= 0.0) || !std::isfinite(d.r_skin)) return NB_ERR_ARG;
         if (d.r_switch >= d.r_cut) return NB_ERR_ARG;
         if (!(d.alpha >= 0.0) || !std::isfinite(d.alpha) || !std::isfinite(d.ke)) return NB_ERR_ARG;
+        if (d.eps_rf != 0.0) {
+            // reaction field: no Ewald splitting, no mesh
+            if (!(d.eps_rf >= 1.0) || !std::isfinite(d.eps_rf) || d.alpha != 0.0) return NB_ERR_ARG;
+            if (d.pme_grid[0] || d.pme_grid[1] || d.pme_grid[2]) return NB_ERR_ARG;
+        }
+        if (d.ke != 0.0) {
+            const int kind = d.eps_rf != 0.0 ? 2 : 1;
+            if (coul_kind != 0 && coul_kind != kind) return NB_ERR_ARG;  // one electrostatics per handle
+            coul_kind = kind;
+        }
         double rnl = d.r_cut + d.r_skin;
         if (d.periodic)
             for (int k = 0; k < 3; ++k)
@@ -267,6 +278,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
 
     nb_handle* h = new (std::nothrow) nb_handle();
     if (!h) return NB_ERR_NOMEM;
+    h->coul_kind = coul_kind ? coul_kind : 1;
     cudaGetDevice(&h->device);
     h->n_sys = n_systems;
     h->n_atoms = (int)N;
@@ -351,6 +363,17 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
             for (int k = 0; k < 3; ++k)
                 if (D.nc[k] < 4 * D.stencil) h->build_gen = 1;  // per-pair images in some cells
         D.self_coef = -d.ke * d.alpha / std::sqrt(3.14159265358979323846);
+        if (d.eps_rf != 0.0) {
+            const double den = 2.0 * d.eps_rf + 1.0;
+            const double k = (d.eps_rf - 1.0) / (den * d.r_cut * d.r_cut * d.r_cut);
+            const double c = 3.0 * d.eps_rf / (den * d.r_cut);
+            D.krf = (float)k;
+            D.crf = (float)c;
+            D.krf_lo = (float)(k - (double)D.krf);
+            D.crf_lo = (float)(c - (double)D.crf);
+        } else {
+            D.krf = D.crf = D.krf_lo = D.crf_lo = 0.f;
+        }
         cell_off += (int)ncells;
         atom_off += d.n_atoms;
     }

@@ -48,7 +48,9 @@ struct SysDev {
     int pad1, pad2;
     double self_coef;     // -ke alpha / sqrt(pi)
     float kl_hi[3], kl_lo[3];  // K_d / L_d as an unevaluated sum hi + lo (double-float)
-    float pad3, pad4;
+    float krf, crf;       // reaction field (Eq. RFA): k = (eps_s-1)/((2eps_s+1) r_c^3), c = 3eps_s/((2eps_s+1) r_c)
+    float krf_lo, crf_lo; // k - krf and c - crf: the constants as double-float pairs for the energy
+    int pad5, pad6;
 };
 
 // An FFT group: PME systems sharing one mesh shape, meshes at a fixed stride.
@@ -76,6 +78,7 @@ struct nb_handle {
     int n_scan_blocks = 0;
     int has_pme = 0;
     int any_coul = 0;   // some system has ke != 0
+    int coul_kind = 1;  // electrostatics of the charged systems: 1 Ewald, 2 reaction field
     long long grid_total = 0, cgrid_total = 0;
     int n_conv_blocks = 0;
 

@@ -7,10 +7,18 @@
 
 namespace nb {
 
+// Electrostatics of the pair kernels (a template argument): none, Ewald direct space
+// ke q q erfc(alpha r)/r, or the reaction field ke q q (1/r + k r^2 - c) of Eq. RFA.
+constexpr int kCoulNone = 0;
+constexpr int kCoulEwald = 1;
+constexpr int kCoulRF = 2;
+
 // System constants the pair math needs, held in registers for the whole block.
 struct PairK {
     float rc2, alpha, ke, rs, inv_sw;
-    int sw;  // LJ switch on
+    float krf, crf;        // reaction field k_RFA, c_RFA (rounded to FP32)
+    float krf_lo, crf_lo;  // their rounding errors (the energy uses hi + lo)
+    int sw;                // LJ switch on
 };
 
 __device__ __forceinline__ PairK pair_k(const SysDev& S) {
@@ -18,6 +26,10 @@ __device__ __forceinline__ PairK pair_k(const SysDev& S) {
     K.rc2 = S.rc2;
     K.alpha = S.alpha;
     K.ke = S.ke;
+    K.krf = S.krf;
+    K.crf = S.crf;
+    K.krf_lo = S.krf_lo;
+    K.crf_lo = S.crf_lo;
     K.rs = S.rs;
     K.inv_sw = S.inv_sw;
     K.sw = S.has_switch;

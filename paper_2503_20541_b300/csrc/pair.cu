@@ -105,10 +105,11 @@ __device__ __forceinline__ void pair_vec(const float4& a, const float4& b, int p
 }
 
 // One queued pair of the force kernel: (dx, dy, dz, r^2) and stencil index lq.
-template <bool LJ, bool COUL>
+template <bool LJ, int COUL>
 __device__ __forceinline__ void pair_heavy(const float4& q, int lq, const float2& pi, bool do_lj, const PairK& K,
-                                           const float4* cand, const float2* par, float qke, float alpha,
-                                           float gau_c, float& fx, float& fy, float& fz, float& elj, float& edir) {
+                                           const float4* cand, const float2* par, float qke, float qke_lo,
+                                           float alpha, float gau_c, float& fx, float& fy, float& fz, float& elj,
+                                           float& edir) {
     const float r2 = q.w;
     const float rinv = rsqrtf(r2);
     float fr = 0.f;
@@ -122,7 +123,7 @@ __device__ __forceinline__ void pair_heavy(const float4& q, int lq, const float2
         elj = fmaf(eps, u, fmaf(eps_lo, u, elj));
         fr = fmaf(eps_lo, f, eps * f);
     }
-    if (COUL && K.ke != 0.f) {  // block-uniform: uncharged systems of a mixed batch skip it
+    if (COUL == kCoulEwald && K.ke != 0.f) {  // block-uniform: uncharged systems of a mixed batch skip it
         const float r = r2 * rinv;
         const float qq = qke * cand[lq].w;
         const float ar = alpha * r;
@@ -130,6 +131,17 @@ __device__ __forceinline__ void pair_heavy(const float4& q, int lq, const float2
         const float gau = gau_c * __expf(-ar * ar);
         edir = fmaf(qq * ec, rinv, edir);
         fr = fmaf(qq * fmaf(ec, rinv, gau), rinv * rinv, fr);
+    }
+    if (COUL == kCoulRF && K.ke != 0.f) {  // Eq. RFA: qq (1/r + k r^2 - c), f = qq (1/r^3 - 2k)
+        // The pair energies of water cancel ~10^4-fold in the sum, so a rounding shared by
+        // many pairs would dominate its error: ke q_i q_j (two charge values, every pair of a
+        // type pair rounded alike) is carried as hi + lo, and so are k and c.
+        const float qj_ = cand[lq].w;
+        const float qq = qke * qj_;
+        const float qq_lo = fmaf(qke_lo, qj_, fmaf(qke, qj_, -qq));
+        const float u = fmaf(K.krf, r2, rinv - K.crf) + fmaf(K.krf_lo, r2, -K.crf_lo);
+        edir = fmaf(qq, u, fmaf(qq_lo, u, edir));
+        fr = fmaf(qq, fmaf(rinv * rinv, rinv, -2.f * K.krf), fr);
     }
     fx = fmaf(fr, q.x, fx);
     fy = fmaf(fr, q.y, fy);
@@ -200,7 +212,7 @@ __device__ __forceinline__ AtomHdr load_hdr(int i, const float4* __restrict__ xs
 }
 
 // Forces and half energies of atom i over stencil tile [t0, t1) (one warp).
-template <bool LJ, bool COUL, bool GEN, bool MULTI>
+template <bool LJ, int COUL, bool GEN, bool MULTI>
 __device__ __forceinline__ void pair_atom(const CellCtx& C, const PairK& K, int N, int i, const AtomHdr& H, int t0,
                                           int t1, bool last, const BuildRun* runs, int nr,
                                           const float4* cand, const float2* par, const unsigned char* cflag,
@@ -217,6 +229,7 @@ __device__ __forceinline__ void pair_atom(const CellCtx& C, const PairK& K, int 
     const uint2* row2 = reinterpret_cast<const uint2*>(nbr + (size_t)i * cap);
     const float rc2 = K.rc2;
     const float qke = K.ke * xr.w;
+    const float qke_lo = COUL == kCoulRF ? fmaf(K.ke, xr.w, -qke) : 0.f;  // ke q_i = qke + qke_lo exactly
     const float alpha = K.alpha;
     const float gau_c = 2.f * alpha * kInvSqrtPi;
     const bool do_lj = pi.y != 0.f;
@@ -252,7 +265,8 @@ __device__ __forceinline__ void pair_atom(const CellCtx& C, const PairK& K, int 
                 const float4 q = qd[pos];
                 const int lq = qj[pos];
                 __syncwarp();
-                pair_heavy<LJ, COUL>(q, lq, pi, do_lj, K, cand, par, qke, alpha, gau_c, fx, fy, fz, elj, edir);
+                pair_heavy<LJ, COUL>(q, lq, pi, do_lj, K, cand, par, qke, qke_lo, alpha, gau_c, fx, fy, fz, elj,
+                                     edir);
                 head = (head + 32) & (kQueue - 1);
                 nq -= 32;
             }
@@ -261,10 +275,11 @@ __device__ __forceinline__ void pair_atom(const CellCtx& C, const PairK& K, int 
     __syncwarp();
     if (lane < nq) {
         const int pos = (head + lane) & (kQueue - 1);
-        pair_heavy<LJ, COUL>(qd[pos], qj[pos], pi, do_lj, K, cand, par, qke, alpha, gau_c, fx, fy, fz, elj, edir);
+        pair_heavy<LJ, COUL>(qd[pos], qj[pos], pi, do_lj, K, cand, par, qke, qke_lo, alpha, gau_c, fx, fy, fz, elj,
+                             edir);
     }
     __syncwarp();
-    if (COUL && last && alpha > 0.f && H.ne > 0) {
+    if (COUL == kCoulEwald && last && alpha > 0.f && H.ne > 0) {
         // exclusion correction for i's excluded partners (at any distance); a partner in
         // the staged stencil is read from shared memory with its image, others from xs
         const int ne = H.ne;
@@ -336,7 +351,7 @@ __device__ __forceinline__ void pair_atom(const CellCtx& C, const PairK& K, int 
     }
 }
 
-template <bool LJ, bool COUL>
+template <bool LJ, int COUL>
 __global__ void __launch_bounds__(kPairThreads) k_pair_cell(
     int N, int cap, int tile, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
     const int* __restrict__ start, const float4* __restrict__ xs, const float2* __restrict__ ps,
@@ -356,7 +371,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_cell(
     float2* par = reinterpret_cast<float2*>(cand + tile);
     unsigned char* cflag = reinterpret_cast<unsigned char*>(par + tile);
     const int w = threadIdx.x >> 5;
-    const bool want_excl = COUL && K.alpha > 0.f;
+    const bool want_excl = COUL == kCoulEwald && K.alpha > 0.f;
     // the first atom's header is loaded while the stencil is staged
     AtomHdr hn;
     if (C.i0 + w < C.i1) hn = load_hdr(C.i0 + w, xs, ps, nbr, cnt, cap, X, want_excl);
@@ -398,7 +413,7 @@ struct VjpAcc {
     float gx = 0.f, gy = 0.f, gz = 0.f, gq = 0.f, gs = 0.f, ge = 0.f;
 };
 
-template <bool LJ, bool COUL>
+template <bool LJ, int COUL>
 __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, const float4& xjq, const float2& pj,
                                           const float4& li, const float2& pi, float qi, const PairK& K,
                                           float alpha, float a2, float gau_c, VjpAcc& A) {
@@ -438,7 +453,7 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, co
         A.ge = fmaf(pj.y * f, du, A.ge);
         A.gs = fmaf(0.5f * eps * fs, du, A.gs);
     }
-    if (COUL && K.ke != 0.f) {  // block-uniform: uncharged systems of a mixed batch skip it
+    if (COUL == kCoulEwald && K.ke != 0.f) {  // block-uniform: uncharged systems of a mixed batch skip it
         const float r = r2 * rinv;
         const float qq = K.ke * qi * xjq.w;
         const float ar = alpha * r;
@@ -450,6 +465,19 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, co
         fpr = fmaf(-qq * r2inv, fmaf(3.f, fcu, 2.f * a2 * gau), fpr);
         A.gq = fmaf(K.ke * xjq.w * fcu, du, A.gq);
     }
+    if (COUL == kCoulRF && K.ke != 0.f) {  // Eq. RFA: f = qq (r^-3 - 2k), f'/r = -3 qq r^-5
+        const float qke = K.ke * qi;
+        const float qq = qke * xjq.w;
+        // energy with ke q_i q_j, k and c as double-float pairs, as in the force kernel
+        const float qq_lo = fmaf(fmaf(K.ke, qi, -qke), xjq.w, fmaf(qke, xjq.w, -qq));
+        const float r3inv = r2inv * rinv;
+        const float fcu = r3inv - 2.f * K.krf;
+        const float u = fmaf(K.krf, r2, rinv - K.crf) + fmaf(K.krf_lo, r2, -K.crf_lo);
+        A.edir = fmaf(qq, u, fmaf(qq_lo, u, A.edir));
+        fr = fmaf(qq, fcu, fr);
+        fpr = fmaf(-3.f * qq, r3inv * r2inv, fpr);
+        A.gq = fmaf(K.ke * xjq.w * fcu, du, A.gq);
+    }
     const float k2 = fpr * du;
     A.gx = fmaf(fr, ux, fmaf(k2, dx, A.gx));
     A.gy = fmaf(fr, uy, fmaf(k2, dy, A.gy));
@@ -459,7 +487,7 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, co
     A.fz = fmaf(fr, dz, A.fz);
 }
 
-template <bool LJ, bool COUL, bool GEN, bool MULTI>
+template <bool LJ, int COUL, bool GEN, bool MULTI>
 __device__ __forceinline__ void vjp_atom(const CellCtx& C, const PairK& K, int N, int i, const AtomHdr& H, int t0,
                                          int t1, bool last, const BuildRun* runs, int nr, const float4* cand,
                                          const float2* par, const float4* lamc, const unsigned char* cflag,
@@ -524,7 +552,7 @@ __device__ __forceinline__ void vjp_atom(const CellCtx& C, const PairK& K, int N
         vjp_heavy<LJ, COUL>(qd[p], lamc[lq], cand[lq], par[lq], li, pi, xr.w, K, alpha, a2, gau_c, A);
     }
     __syncwarp();
-    if (COUL && last && alpha > 0.f && H.ne > 0) {
+    if (COUL == kCoulEwald && last && alpha > 0.f && H.ne > 0) {
         const int ne = H.ne;
         int lk = -1;
         const int nin = min(ne, X.ew);
@@ -599,7 +627,7 @@ __device__ __forceinline__ void vjp_atom(const CellCtx& C, const PairK& K, int N
     }
 }
 
-template <bool LJ, bool COUL>
+template <bool LJ, int COUL>
 // LJ-only instantiations are register-bound (small stencils): capped at 64 registers so
 // that four blocks share an SM; with Coulomb (larger staged stencils) two.
 __global__ void __launch_bounds__(kVjpThreads, COUL ? 2 : 4) k_vjp_cell(
@@ -623,7 +651,7 @@ __global__ void __launch_bounds__(kVjpThreads, COUL ? 2 : 4) k_vjp_cell(
     float2* par = reinterpret_cast<float2*>(lamc + tile);
     unsigned char* cflag = reinterpret_cast<unsigned char*>(par + tile);
     const int w = threadIdx.x >> 5;
-    const bool want_excl = COUL && K.alpha > 0.f;
+    const bool want_excl = COUL == kCoulEwald && K.alpha > 0.f;
     AtomHdr hn;
     if (C.i0 + w < C.i1) hn = load_hdr(C.i0 + w, xs, ps, nbr, cnt, cap, X, want_excl);
     if (w == 0) cell_runs(C, S, start, runs, &n_runs, &n_cand, flags);
@@ -674,7 +702,7 @@ static ExclView excl_view(const nb_handle* h) {
     return X;
 }
 
-template <bool LJ, bool COUL>
+template <bool LJ, int COUL>
 static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp) {
     const ExclView X = excl_view(h);
     if (vjp)
@@ -690,10 +718,13 @@ static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp) {
 static void dispatch(nb_handle* h, int terms, cudaStream_t st, bool vjp) {
     bool lj = (terms & NB_TERM_LJ) != 0;
     bool coul = (terms & NB_TERM_COUL) != 0 && h->any_coul;  // uncharged systems: LJ-only kernels
-    if (lj && coul) pair_launch<true, true>(h, st, vjp);
-    else if (lj) pair_launch<true, false>(h, st, vjp);
-    else if (coul) pair_launch<false, true>(h, st, vjp);
-    else pair_launch<false, false>(h, st, vjp);
+    const bool rf = h->coul_kind == kCoulRF;
+    if (lj && coul && rf) pair_launch<true, kCoulRF>(h, st, vjp);
+    else if (lj && coul) pair_launch<true, kCoulEwald>(h, st, vjp);
+    else if (lj) pair_launch<true, kCoulNone>(h, st, vjp);
+    else if (coul && rf) pair_launch<false, kCoulRF>(h, st, vjp);
+    else if (coul) pair_launch<false, kCoulEwald>(h, st, vjp);
+    else pair_launch<false, kCoulNone>(h, st, vjp);
 }
 
 void launch_pair(nb_handle* h, int terms, cudaStream_t st) { dispatch(h, terms, st, false); }
@@ -714,7 +745,7 @@ static cudaError_t allow_max_smem(F kernel) {
     return e;
 }
 
-template <bool LJ, bool COUL>
+template <bool LJ, int COUL>
 static cudaError_t set_smem() {
     cudaError_t e = allow_max_smem(k_pair_cell<LJ, COUL>);
     if (e != cudaSuccess) return e;
@@ -728,10 +759,12 @@ cudaError_t pair_setup(nb_handle* h) {
     if (e != cudaSuccess) return e;
     // static shared memory of the VJP kernel: queues and runs (~23 KB)
     if ((long long)vjp_smem(h) + 24 * 1024 > optin) return cudaErrorInvalidValue;
-    e = set_smem<true, true>();
-    if (e == cudaSuccess) e = set_smem<true, false>();
-    if (e == cudaSuccess) e = set_smem<false, true>();
-    if (e == cudaSuccess) e = set_smem<false, false>();
+    e = set_smem<true, kCoulEwald>();
+    if (e == cudaSuccess) e = set_smem<true, kCoulRF>();
+    if (e == cudaSuccess) e = set_smem<true, kCoulNone>();
+    if (e == cudaSuccess) e = set_smem<false, kCoulEwald>();
+    if (e == cudaSuccess) e = set_smem<false, kCoulRF>();
+    if (e == cudaSuccess) e = set_smem<false, kCoulNone>();
     return e;
 }
 

@@ -57,6 +57,7 @@ class SystemDesc(ctypes.Structure):
         ("ke", ctypes.c_double),
         ("pme_grid", ctypes.c_int32 * 3),
         ("pme_order", ctypes.c_int32),
+        ("eps_rf", ctypes.c_double),
     ]
 
 
@@ -242,6 +243,7 @@ class Handle:
             for a in range(3):
                 d.pme_grid[a] = int(g[a])
             d.pme_order = int(getattr(s, "pme_order", 4))
+            d.eps_rf = float(getattr(s, "eps_rf", 0.0) or 0.0)
             sig.append(np.asarray(s.sigma, np.float32))
             sqe.append(np.asarray(s.sqrt_eps, np.float32))
             if s.excl_off is not None:

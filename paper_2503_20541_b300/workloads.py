@@ -31,6 +31,7 @@ WATER_HOH_DEG = 109.47
 MASS_O = 15.999
 MASS_H = 1.008
 WATER_MOL_DENSITY = 0.03343  # molecules per cubic Angstrom at 1 g/cm^3
+WATER_EPS_RF = 78.5          # solvent dielectric of the reaction field (water at 298 K)
 
 
 def f32(v):
@@ -64,6 +65,7 @@ class System:
     r_switch: float = -1.0     # LJ switching distance (<0: none)
     pme_grid: tuple = (0, 0, 0)
     pme_order: int = 4
+    eps_rf: float = 0.0        # reaction field solvent dielectric (0: Ewald / no electrostatics)
     excl_off: np.ndarray = None  # (n+1,) int32 CSR offsets (symmetric)
     excl_idx: np.ndarray = None  # int32 CSR entries
     types: np.ndarray = None     # (n,) int32 atom types (mass sharing)
@@ -224,6 +226,23 @@ def water_box_density(n_mol, seed, r_cut=9.0, r_skin=2.25, alpha=0.32, jitter=0.
     K = fft_friendly(L / 0.97)
     return water_box(n_side=n_side, L=L, seed=seed, jitter=min(jitter, 0.1 * L / n_side), r_cut=r_cut,
                      r_skin=r_skin, alpha=alpha, pme_grid=K, n_mol=n_mol)
+
+
+def as_reaction_field(s, eps_rf=WATER_EPS_RF):
+    """The same system with the reaction field of Eq. RFA (solvent dielectric eps_rf)
+    in place of Ewald + PME."""
+    s.alpha = 0.0
+    s.pme_grid = (0, 0, 0)
+    s.eps_rf = float(eps_rf)
+    s.name = s.name + "_rf"
+    return s
+
+
+def water_rf_density(n_mol, seed, r_cut=10.0, r_skin=2.5, eps_rf=WATER_EPS_RF, jitter=0.3):
+    """Water at 1 g/cm^3 with the reaction field, r_c 10 A: the setting of the paper's
+    water scaling benchmark (Sec. 3, electrostatics by RFA)."""
+    s = water_box_density(n_mol, seed, r_cut=r_cut, r_skin=r_skin, alpha=0.0, jitter=jitter)
+    return as_reaction_field(s, eps_rf)
 
 
 def batched_mix(n_systems=256, n_min=500, n_max=20000, seed=1234, water_r_nl=11.25):

@@ -1,0 +1,120 @@
+"""GPU parity of the reaction-field electrostatics (Eq. RFA) through the C ABI.
+
+Forces and energies of water boxes with the reaction field against the FP64 all-pairs
+oracle (the small box element by element, the 24,000-atom box on sampled rows with all
+rows for the energies), the force VJP under the reaction field, and the descriptor
+checks (invalid dielectric, RF with Ewald splitting or a PME mesh, charged systems of
+both kinds in one handle).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_20541_b300 import nbcore, workloads as wl
+
+from _helpers import EPS32, dev_xq, oracle_params, oracle_real_space, rel_rms, rf_rounding_scale
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F_TOL = 1e-5
+E_TOL = 1e-6
+TERMS = nbcore.NB_TERM_LJ | nbcore.NB_TERM_COUL
+
+
+def _forces(h, s, terms=TERMS):
+    f = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+    e = torch.empty((1, 6), dtype=torch.float64, device="cuda")
+    h.nonbonded_forces(dev_xq(s), f, e, terms=terms)
+    h.check()
+    return f.cpu().numpy().astype(np.float64), e.cpu().numpy()[0]
+
+
+def _rf_tol(s, e_ref, rows=None):
+    """E_RF of water is a ~10^4-fold cancelling sum of FP32 pair energies: its error is
+    bounded by 1e-6 relative plus six times the random-walk sum of the pairs' rounding
+    (EPS32 times the root sum of squares of their parts' magnitudes)."""
+    return E_TOL * abs(e_ref) + 6.0 * EPS32 * rf_rounding_scale(s, rows=rows)
+
+
+@pytest.mark.parametrize("tile", [0, 256])
+def test_reaction_field_water_matches_oracle(tile):
+    s = wl.water_rf_density(600, seed=3)  # 1800 atoms, r_c 10 A, the paper's scaling setting
+    with nbcore.Handle([s], stencil_tile=tile) as h:
+        f, e = _forces(h, s)
+    eo, fo = oracle_real_space(s)
+    assert rel_rms(f, fo) <= F_TOL
+    assert abs(e[0] - eo[0]) <= E_TOL * abs(eo[0])
+    assert abs(e[1] - eo[1]) <= _rf_tol(s, eo[1]), (e[1], eo[1], _rf_tol(s, eo[1]))
+    assert e[2] == 0.0 and e[3] == 0.0 and e[4] == 0.0  # no exclusion correction, self or mesh
+    assert eo[2] == 0.0 and eo[3] == 0.0
+
+
+def test_reaction_field_water_24k_sampled():
+    """The benchmark's 8000-molecule box with the reaction field in place of Ewald + PME."""
+    s = wl.as_reaction_field(wl.water_box())
+    with nbcore.Handle([s]) as h:
+        f, e = _forces(h, s)
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(s.n, 400, replace=False))
+    er, fr = oracle.nonbonded_rows(s.x.astype(np.float64), s.q, s.sigma, s.sqrt_eps, oracle_params(s), rows,
+                                   excl=s.excl)
+    assert rel_rms(f[rows], fr) <= F_TOL
+    er_all, _ = oracle.nonbonded_rows(s.x.astype(np.float64), s.q, s.sigma, s.sqrt_eps, oracle_params(s),
+                                      np.arange(s.n), excl=s.excl)
+    eo = er_all.sum(axis=0)
+    assert abs(e[0] - eo[0]) <= E_TOL * abs(eo[0]), (e[0], eo[0])
+    tol = _rf_tol(s, eo[1], rows=np.arange(0, s.n, 11))  # every 11th row: O and H alike
+    assert abs(e[1] - eo[1]) <= tol, (e[1], eo[1], tol)
+
+
+def test_reaction_field_vjp_matches_oracle():
+    s = wl.water_rf_density(600, seed=4)
+    rng = np.random.default_rng(5)
+    lam = rng.standard_normal((s.n, 3)).astype(np.float32)
+    gxo, gqo, gso, geo = oracle.force_vjp(s.x.astype(np.float64), s.q, s.sigma, s.sqrt_eps, oracle_params(s),
+                                          lam, excl=s.excl)
+    with nbcore.Handle([s]) as h:
+        gx = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+        gq = torch.empty(s.n, dtype=torch.float32, device="cuda")
+        gs = torch.empty(s.n, dtype=torch.float32, device="cuda")
+        ge = torch.empty(s.n, dtype=torch.float32, device="cuda")
+        fo = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+        h.nonbonded_force_vjp(dev_xq(s), torch.from_numpy(lam).cuda(), gx, gq, gs, ge, f_out=fo)
+        h.check()
+    assert rel_rms(gx.cpu().numpy(), gxo) <= 1e-5
+    assert rel_rms(gq.cpu().numpy(), gqo) <= 1e-5
+    o = s.sqrt_eps > 0
+    assert rel_rms(gs.cpu().numpy()[o], gso[o]) <= 1e-5
+    assert rel_rms(ge.cpu().numpy(), geo) <= 1e-5
+    assert rel_rms(fo.cpu().numpy(), oracle_real_space(s)[1]) <= F_TOL
+
+
+def test_reaction_field_descriptor_checks():
+    def refused(s_list):
+        with pytest.raises(nbcore.NbError) as ei:
+            nbcore.Handle(s_list)
+        assert ei.value.status == 1
+
+    s = wl.water_rf_density(600, seed=6)
+    s.eps_rf = 0.5  # below 1
+    refused([s])
+    s = wl.water_rf_density(600, seed=6)
+    s.alpha = 0.32  # RF and Ewald splitting together
+    refused([s])
+    s = wl.water_rf_density(600, seed=6)
+    s.pme_grid = (32, 32, 32)  # RF with a mesh
+    refused([s])
+    refused([wl.water_rf_density(600, seed=6), wl.water_box_density(600, seed=7)])  # two kinds
+    # an uncharged LJ system may share a handle with reaction-field water
+    lj = wl.lj_random(500, seed=8)
+    sw = wl.water_rf_density(600, seed=9)
+    with nbcore.Handle([lj, sw]) as h:
+        n = lj.n + sw.n
+        f = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        e = torch.empty((2, 6), dtype=torch.float64, device="cuda")
+        h.nonbonded_forces(torch.cat([dev_xq(lj), dev_xq(sw)]), f, e, terms=TERMS)
+        h.check()
+    eo, fo = oracle_real_space(sw)
+    assert rel_rms(f.cpu().numpy()[lj.n:].astype(np.float64), fo) <= F_TOL
+    assert abs(e.cpu().numpy()[1, 1] - eo[1]) <= _rf_tol(sw, eo[1])

@@ -21,6 +21,7 @@ against all-pairs, the HMC training run and the 256-system batch.
 """
 import argparse
 import hashlib
+import copy
 import json
 import os
 import statistics
@@ -360,6 +361,7 @@ def extras(torch, nbcore, wl):
             "workload": "differentiable HMC, LJ fluid 2048 atoms x 10 replicas (batched in one handle), "
                         "32 leapfrog steps, checkpoints every 8 (recompute in the backward), switch 2.2-2.5"}
     out["lj_sweep"] = lj_sweep(torch, nbcore, wl)
+    out["water_elec_sweep"] = water_elec_sweep(torch, nbcore, wl)
     out["hmc_training"] = hmc_training(torch, nbcore, wl)
     out["hmc_lhmc"] = hmc_lhmc(torch, nbcore, wl)
     out["batched"] = batched(torch, nbcore, wl)
@@ -432,6 +434,64 @@ def lj_sweep(torch, nbcore, wl, sizes=(4000, 32000, 256000, 2048000, 8192000), a
     return {"rows": rows, "workload": "LJ fluid rho* 0.8442, r_c 2.5, r_skin 0.3 on a jittered FCC subset (stand-in "
                                       "for FIRE-relaxed random positions), list path vs all-pairs kernel; all-pairs "
                                       "timed up to %d atoms and extrapolated as N^2 beyond" % allpairs_max}
+
+
+def water_elec_sweep(torch, nbcore, wl, n_mols=(1000, 10000, 32000, 100000)):
+    """Water at 1 g/cm^3, r_c 10 A, r_skin 2.5 A (the paper's water scaling setting):
+    one force evaluation (LJ + electrostatics) per step with the list rebuilt and with it
+    reused, for the reaction field (Eq. RFA, eps_s 78.5) and for Ewald + PME (alpha from
+    a 1.3e-4 direct-space tolerance at r_c, K = FFT-friendly >= L/0.97 A)."""
+    import math
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(fn, reps):
+        for _ in range(2 * reps):  # untimed: clocks up, caches and lazy module loads warm
+            fn()
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    alpha = math.sqrt(-math.log(2 * 1.3e-4)) / 10.0
+    rows = []
+    for nm in n_mols:
+        row = {"molecules": nm, "atoms": 3 * nm}
+        for kind in ("rf", "pme"):
+            if kind == "rf":
+                s = wl.water_rf_density(nm, seed=700 + nm % 97)
+                terms = nbcore.NB_TERM_LJ | nbcore.NB_TERM_COUL
+            else:
+                s = wl.water_box_density(nm, seed=700 + nm % 97, r_cut=10.0, r_skin=2.5, alpha=alpha)
+                terms = nbcore.NB_TERM_ALL
+            xq = torch.from_numpy(nbcore.pack_xq(s.x, s.q)).cuda()
+            f = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+            e = torch.empty((1, 6), dtype=torch.float64, device="cuda")
+            if kind == "rf":
+                # unordered non-excluded pairs with r < r_c: the list count with no skin
+                s0 = copy.copy(s)
+                s0.r_skin = 0.0
+                with nbcore.Handle([s0]) as h0:
+                    row["pairs_cutoff"] = h0.nl_build(xq, max_pairs=1, force_rebuild=True)[1]
+                row["box"] = float(s.box[0])
+            with nbcore.Handle([s]) as h:
+                reps = 20 if nm <= 32000 else 8
+                h.nonbonded_forces(xq, f, e, terms=terms | nbcore.NB_FORCE_REBUILD)
+                ms_rb = timed(lambda: h.nonbonded_forces(xq, f, e, terms=terms | nbcore.NB_FORCE_REBUILD), reps)
+                ms_ru = timed(lambda: h.nonbonded_forces(xq, f, e, terms=terms), reps)
+                h.check()
+            row[kind] = {"ms_eval_rebuild": ms_rb, "ms_eval_list_reused": ms_ru}
+            if kind == "pme":
+                row[kind]["mesh"] = list(s.pme_grid)
+            del xq, f
+            torch.cuda.empty_cache()
+        row["rf"]["pairs_per_s_list_reused"] = row["pairs_cutoff"] / (row["rf"]["ms_eval_list_reused"] / 1e3)
+        rows.append(row)
+    return {"rows": rows, "workload": "water at 1 g/cm^3 (3-site point-charge molecules, LJ on O), r_c 10 A, "
+                                      "r_skin 2.5 A; RF eps_s 78.5 vs Ewald alpha %.4f/A + PME order 4; step = one "
+                                      "force evaluation with energies; list rebuilt every step or reused" % alpha}
 
 
 def hmc_training(torch, nbcore, wl, iters=200):

@@ -108,6 +108,10 @@ typedef struct {
                                 (multiple of 64 in [256, 4096]); 0: auto from the density */
     int32_t cell_div;        /* cells of edge >= r_nl / cell_div, cell_div in {1, 2}; 0: auto */
     int32_t force_bits;      /* fixed-point fraction bits for forces; 0: 32 */
+    int32_t blocks_per_cell; /* thread blocks sharing one cell in the list build, pair and VJP
+                                kernels (each takes a strided share of the cell's atoms), in
+                                [1, 32]; 0: auto (more than one only when the cells are too few
+                                to fill the GPU).  Results do not depend on it. */
 } nb_options;
 
 typedef struct nb_handle nb_handle;
@@ -360,6 +364,10 @@ nb_status nonbonded_force_vjp(nb_handle* h, const float* xq, const float* lam, f
 #define NB_STATIC_MESH_MAX (1 << 20)
 nb_status pme_spread_static(const float* xq, int32_t n_atoms, const double* box, const int32_t* mesh,
                             float* grid, void* stream);
+
+/* Thread blocks per cell the handle uses in the list build and in the pair / VJP kernels
+ * (nb_options.blocks_per_cell, or the automatic choice).  Host only, no GPU work. */
+nb_status nb_blocks_per_cell(const nb_handle* h, int32_t* build, int32_t* pair);
 
 /* Cumulative number of neighbour-list rebuilds of a handle (synchronises `stream`). */
 int64_t nb_rebuild_count(nb_handle* h, void* stream);

@@ -239,6 +239,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         return NB_ERR_ARG;
     if (o.max_neighbors < 0 || o.force_bits < 0 || o.force_bits > 48 || (o.force_bits > 0 && o.force_bits < 8))
         return NB_ERR_ARG;
+    if (o.blocks_per_cell < 0 || o.blocks_per_cell > 32) return NB_ERR_ARG;
 
     // exclusions: validate and symmetrise
     std::vector<std::vector<int>> ex((size_t)N);
@@ -395,6 +396,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         h->tile = (int)std::max(256LL, std::min(t, 4096LL));
     }
     h->n_scan_blocks = cdiv(h->n_cells, kScanTile);
+    h->blocks_per_cell = o.blocks_per_cell;
 
     cudaError_t e = cudaSuccess;
 #define NB_TRY(x)                        \
@@ -541,6 +543,13 @@ nb_status nb_check(nb_handle* h, void* stream) {
     if (bits & NB_DEVERR_LIST_OVERFLOW) return NB_ERR_LIST_OVERFLOW;
     if (bits & NB_DEVERR_FIXEDPOINT) return NB_ERR_FIXEDPOINT_OVERFLOW;
     if (bits & NB_DEVERR_ARG) return NB_ERR_ARG;
+    return NB_OK;
+}
+
+nb_status nb_blocks_per_cell(const nb_handle* h, int32_t* build, int32_t* pair) {
+    if (!h) return NB_ERR_ARG;
+    if (build) *build = h->split_build;
+    if (pair) *pair = h->split_pair;
     return NB_OK;
 }
 

@@ -16,6 +16,7 @@
 #include <cufft.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "../../include/nbcore.h"
@@ -77,6 +78,9 @@ struct nb_handle {
     int n_cells = 0;
     int n_scan_blocks = 0;
     int has_pme = 0;
+    int blocks_per_cell = 0;     // option (0: auto)
+    int split_build = 1;         // blocks per cell of the list build
+    int split_pair = 1;          // blocks per cell of the pair and VJP kernels
     int any_coul = 0;   // some system has ke != 0
     int coul_kind = 1;  // electrostatics of the charged systems: 1 Ewald, 2 reaction field
     long long grid_total = 0, cgrid_total = 0;
@@ -233,6 +237,20 @@ void launch_pme_convolve(nb_handle* h, cudaStream_t st);
 void launch_pme_gather(nb_handle* h, cudaStream_t st);
 void launch_pme_spread_only(nb_handle* h, float* grid_out, cudaStream_t st);
 void launch_pme_gather_only(nb_handle* h, const float* phi, float* f_out, cudaStream_t st);
+// Blocks per cell for a cell kernel whose blocks hold `warps` warps and want at least
+// `atoms_per_warp` atoms per warp on average: 1 unless the cells are too few to give
+// every SM several blocks.
+inline int pick_split(const nb_handle* h, int warps, int atoms_per_warp) {
+    if (h->blocks_per_cell) return h->blocks_per_cell;
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long target = 4LL * sms;
+    if (h->n_cells >= target) return 1;
+    const int want = (int)std::min<long long>(32, (target + h->n_cells - 1) / h->n_cells);
+    const int fill = (int)((double)h->n_atoms / h->n_cells / ((double)warps * atoms_per_warp));
+    return std::max(1, std::min(want, fill));
+}
+
 // dynamics.cu
 // Observables of an HMC trajectory recorded by the integrator at integer step `step`
 // (before its drift): the squared minimum-image jump |x - x0|^2 of every atom (FP64,

@@ -257,12 +257,12 @@ constexpr int kBuildAtoms = 6;      // atoms per warp held in registers (plain i
 constexpr int kBuildAtomsGen = 3;   // atoms per warp held in registers (per-pair images)
 static_assert(kBuildAtoms == 6, "build_tile dispatches group sizes 1..6");
 
-// Tests of one tile against the atoms [m0, m0 + na) of warp w (atom m of the warp is
-// slot i0 + w + kBuildWarps m), na <= A.  Held atoms beyond na sit far away so that the
+// Tests of one tile against the atoms [m0, m0 + na) of warp w of the cell's W warps (atom
+// m of the warp is slot i0 + w + W m; W = kBuildWarps times the blocks per cell), na <= A.  Held atoms beyond na sit far away so that the
 // unrolled tests run without branches.  GEN: per-pair image flags and folded axes.
 // SLOW: atoms may have more than E exclusions (the rest are read from the CSR).
 template <int E, bool SLOW, bool GEN, int A>
-__device__ __forceinline__ void build_atoms(const CellCtx& C, int w, int m0, int na, int t0, int nt, bool last,
+__device__ __forceinline__ void build_atoms(const CellCtx& C, int w, int W, int m0, int na, int t0, int nt, bool last,
                                             const float4* cand, const unsigned char* cflag,
                                             const float4* __restrict__ xs, const int* __restrict__ perm,
                                             const int* __restrict__ iperm, const int* __restrict__ ex_off,
@@ -284,7 +284,7 @@ __device__ __forceinline__ void build_atoms(const CellCtx& C, int w, int m0, int
 #pragma unroll
         for (int q = 0; q <= E; ++q) ex[a][q] = -1;
         if (a < na) {
-            const int i = C.i0 + w + kBuildWarps * (m0 + a);
+            const int i = C.i0 + w + W * (m0 + a);
             const float4 p = xs[i];
             ax[a] = p.x + C.fs[0];
             ay[a] = p.y + C.fs[1];
@@ -327,7 +327,7 @@ __device__ __forceinline__ void build_atoms(const CellCtx& C, int w, int m0, int
 #pragma unroll
             for (int q = 0; q <= E; ++q) acc = acc && (j != ex[a][q]);
             if (SLOW && ((slow >> a) & 1u) && acc) {
-                const int i = C.i0 + w + kBuildWarps * (m0 + a);
+                const int i = C.i0 + w + W * (m0 + a);
                 const int oi = perm[i];
                 const int e0 = ex_off[oi], e1 = ex_off[oi + 1];
                 for (int e = e0 + E; e < e1 && acc; ++e) acc = (iperm[ex_idx[e]] != j);
@@ -342,7 +342,7 @@ __device__ __forceinline__ void build_atoms(const CellCtx& C, int w, int m0, int
 #pragma unroll
         for (int a = 0; a < A; ++a) {
             if (a < na) {
-                const int i = C.i0 + w + kBuildWarps * (m0 + a);
+                const int i = C.i0 + w + W * (m0 + a);
                 int c = cnt[a];
                 if (last && c > cap) {
                     atomicOr(&flags[1], NB_DEVERR_LIST_OVERFLOW);
@@ -355,23 +355,23 @@ __device__ __forceinline__ void build_atoms(const CellCtx& C, int w, int m0, int
 }
 
 template <int E, bool SLOW>
-__device__ __forceinline__ void build_tile(const CellCtx& C, int t0, int nt, bool last, const float4* cand,
+__device__ __forceinline__ void build_tile(const CellCtx& C, int w, int W, int t0, int nt, bool last,
+                                           const float4* cand,
                                            const unsigned char* cflag, const float4* __restrict__ xs,
                                            const int* __restrict__ perm, const int* __restrict__ iperm,
                                            const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
                                            const int* __restrict__ ex_slot, unsigned short* __restrict__ nbr,
                                            int* __restrict__ nbr_cnt, int cap, float rnl2, unsigned* flags) {
-    const int w = threadIdx.x >> 5;
     const int n_i = C.i1 - C.i0;
-    const int mw = n_i > w ? (n_i - w + kBuildWarps - 1) / kBuildWarps : 0;  // atoms of this warp
+    const int mw = n_i > w ? (n_i - w + W - 1) / W : 0;  // atoms of this warp
     if (mw == 0) return;
     const int A = C.gen ? kBuildAtomsGen : kBuildAtoms;
     const int ng = (mw + A - 1) / A;
     const int gs = (mw + ng - 1) / ng;  // balanced group size <= A
     for (int m0 = 0; m0 < mw; m0 += gs) {
         const int na = min(gs, mw - m0);
-#define NB_BUILD_ARGS C, w, m0, na, t0, nt, last, cand, cflag, xs, perm, iperm, ex_off, ex_idx, ex_slot, nbr, nbr_cnt, \
-                      cap, rnl2, flags
+#define NB_BUILD_ARGS C, w, W, m0, na, t0, nt, last, cand, cflag, xs, perm, iperm, ex_off, ex_idx, ex_slot, nbr, \
+                      nbr_cnt, cap, rnl2, flags
         if (C.gen) {
             build_atoms<E, SLOW, true, kBuildAtomsGen>(NB_BUILD_ARGS);
         } else {
@@ -395,7 +395,7 @@ __device__ __forceinline__ void build_cell_body(const CellCtx& C, const SysDev& 
                                                 const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
                                                 int* __restrict__ ex_slot, int* __restrict__ ex_cnt,
                                                 unsigned short* __restrict__ nbr, int* __restrict__ nbr_cnt,
-                                                unsigned* flags);
+                                                unsigned* flags, int part, int split);
 
 template <int E, bool SLOW>
 __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
@@ -403,14 +403,15 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
     const int* __restrict__ start, const float4* __restrict__ xs, const int* __restrict__ perm,
     const int* __restrict__ iperm, const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
     int* __restrict__ ex_slot, int* __restrict__ ex_cnt, unsigned short* __restrict__ nbr,
-    int* __restrict__ nbr_cnt, unsigned* ticket, unsigned* flags) {
+    int* __restrict__ nbr_cnt, unsigned* ticket, unsigned* flags, int split) {
     if (flags[0] == 0u) return;
-    const int c = blockIdx.x;
+    // `split` blocks share a cell, block `part` taking warps part*kBuildWarps.. of its W
+    const int c = blockIdx.x / split, part = blockIdx.x % split;
     const SysDev& S = sys[cell_sys[c]];
     const CellCtx C = cell_ctx(c, S, start);
-    if (C.i0 != C.i1)
+    if (C.i0 + part * kBuildWarps < C.i1)
         build_cell_body<E, SLOW>(C, S, cap, tile, start, xs, perm, iperm, ex_off, ex_idx, ex_slot, ex_cnt, nbr,
-                                 nbr_cnt, flags);
+                                 nbr_cnt, flags, part, split);
     // the last block to finish counts the rebuild and clears the request
     __shared__ bool last;
     __syncthreads();
@@ -434,7 +435,7 @@ __device__ __forceinline__ void build_cell_body(const CellCtx& C, const SysDev& 
                                                 const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
                                                 int* __restrict__ ex_slot, int* __restrict__ ex_cnt,
                                                 unsigned short* __restrict__ nbr, int* __restrict__ nbr_cnt,
-                                                unsigned* flags) {
+                                                unsigned* flags, int part, int split) {
     __shared__ BuildRun runs[kMaxRuns];
     __shared__ int n_runs, n_cand;
     // dynamic: `tile` candidates, then `tile` image-flag bytes when any system can need
@@ -462,11 +463,15 @@ __device__ __forceinline__ void build_cell_body(const CellCtx& C, const SysDev& 
             for (int k = a + lane; k < b; k += 32) cp_async16(&cand[k - t0], &xs[slot0 + (k - sm0)]);
         }
         if (E > 0 && t0 == 0) {
-            // exclusion partners of this cell's atoms as slots, while the copies are in
-            // flight (read by the tests below and by the pair kernels)
-            const int na = C.i1 - C.i0;
-            for (int idx = threadIdx.x; idx < na * E; idx += kBuildThreads) {
-                const int i = C.i0 + idx / E, q = idx % E;
+            // exclusion partners of this block's atoms as slots, while the copies are in
+            // flight (read by the tests below and by the pair kernels); the block's atoms
+            // are i0 + part*kBuildWarps + (a % kBuildWarps) + W (a / kBuildWarps)
+            const int W = split * kBuildWarps;
+            const int nb = (C.i1 - C.i0 - part * kBuildWarps + W - 1) / W * kBuildWarps;
+            for (int idx = threadIdx.x; idx < nb * E; idx += kBuildThreads) {
+                const int a = idx / E, q = idx % E;
+                const int i = C.i0 + part * kBuildWarps + a % kBuildWarps + W * (a / kBuildWarps);
+                if (i >= C.i1) continue;
                 const int oi = perm[i];
                 const int e0 = ex_off[oi], ne = ex_off[oi + 1] - e0;
                 ex_slot[(size_t)i * E + q] = q < ne ? iperm[ex_idx[e0 + q]] : -1;
@@ -491,8 +496,8 @@ __device__ __forceinline__ void build_cell_body(const CellCtx& C, const SysDev& 
         }
         __syncthreads();
         const bool last = t1 == total;
-        build_tile<E, SLOW>(C, t0, nt, last, cand, cflag, xs, perm, iperm, ex_off, ex_idx, ex_slot, nbr, nbr_cnt,
-                            cap, rnl2, flags);
+        build_tile<E, SLOW>(C, part * kBuildWarps + w, split * kBuildWarps, t0, nt, last, cand, cflag, xs, perm,
+                            iperm, ex_off, ex_idx, ex_slot, nbr, nbr_cnt, cap, rnl2, flags);
         if (!last) __syncthreads();
     }
 }
@@ -567,10 +572,9 @@ void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st) {
                  : h->excl_w == 2 ? k_build_cell<2, false>
                  : h->max_excl <= 4 ? k_build_cell<4, false>
                                     : k_build_cell<4, true>;
-    build<<<h->n_cells, kBuildThreads, build_smem(h), st>>>(h->cap, h->tile, h->cell_sys, h->sys, h->cell_start,
-                                                            h->xs, h->perm, h->iperm, h->ex_off, h->ex_idx,
-                                                            h->ex_slot, h->ex_cnt, h->nbr, h->nbr_cnt,
-                                                            h->build_ticket, h->flags);
+    build<<<h->n_cells * h->split_build, kBuildThreads, build_smem(h), st>>>(
+        h->cap, h->tile, h->cell_sys, h->sys, h->cell_start, h->xs, h->perm, h->iperm, h->ex_off, h->ex_idx,
+        h->ex_slot, h->ex_cnt, h->nbr, h->nbr_cnt, h->build_ticket, h->flags, h->split_build);
 }
 
 // The dynamic shared-memory limit of a kernel is process-wide, so it is raised once to
@@ -590,6 +594,7 @@ static cudaError_t allow_max_smem(K kernel) {
 
 cudaError_t build_setup(nb_handle* h) {
     if (build_smem(h) + 4096 > 227 * 1024) return cudaErrorInvalidValue;
+    h->split_build = pick_split(h, kBuildWarps, 3);  // keep >= 3 atoms per warp for register blocking
     cudaError_t e = allow_max_smem(k_build_cell<0, false>);
     if (e == cudaSuccess) e = allow_max_smem(k_build_cell<2, false>);
     if (e == cudaSuccess) e = allow_max_smem(k_build_cell<4, false>);

@@ -356,12 +356,15 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_cell(
     int N, int cap, int tile, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
     const int* __restrict__ start, const float4* __restrict__ xs, const float2* __restrict__ ps,
     const unsigned short* __restrict__ nbr, const int* __restrict__ cnt, ExclView X, long long* __restrict__ ffix,
-    float4* __restrict__ e_atom, float4* __restrict__ pscr, float scale, unsigned* flags) {
-    const int c = blockIdx.x;
+    float4* __restrict__ e_atom, float4* __restrict__ pscr, float scale, unsigned* flags, int split) {
+    // `split` blocks share a cell: block `part` takes atoms i0 + part*kPairWarps + w + stride*m
+    const int c = blockIdx.x / split, part = blockIdx.x % split;
+    const int stride = kPairWarps * split;
     const SysDev& S = sys[cell_sys[c]];
     const CellCtx C = cell_ctx(c, S, start);
     const PairK K = pair_k(S);
-    if (C.i0 == C.i1) return;
+    const int ib = C.i0 + part * kPairWarps + (threadIdx.x >> 5);
+    if (C.i0 + part * kPairWarps >= C.i1) return;
     __shared__ BuildRun runs[kMaxRuns];
     __shared__ int n_runs, n_cand;
     __shared__ float4 qd_all[kPairWarps][kQueue];
@@ -374,7 +377,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_cell(
     const bool want_excl = COUL == kCoulEwald && K.alpha > 0.f;
     // the first atom's header is loaded while the stencil is staged
     AtomHdr hn;
-    if (C.i0 + w < C.i1) hn = load_hdr(C.i0 + w, xs, ps, nbr, cnt, cap, X, want_excl);
+    if (ib < C.i1) hn = load_hdr(ib, xs, ps, nbr, cnt, cap, X, want_excl);
     if (w == 0) cell_runs(C, S, start, runs, &n_runs, &n_cand, flags);
     __syncthreads();
     const int nr = n_runs, total = n_cand;
@@ -385,10 +388,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_cell(
         stage_pair_tile(C, runs, nr, t0, t1, kPairThreads, xs, ps, nullptr, cand, par, nullptr, cflag);
         __syncthreads();
         const bool last = t1 == total;
-        if (t0 > 0 && C.i0 + w < C.i1) hn = load_hdr(C.i0 + w, xs, ps, nbr, cnt, cap, X, want_excl);
-        for (int i = C.i0 + w; i < C.i1; i += kPairWarps) {
+        if (t0 > 0 && ib < C.i1) hn = load_hdr(ib, xs, ps, nbr, cnt, cap, X, want_excl);
+        for (int i = ib; i < C.i1; i += stride) {
             const AtomHdr H = hn;
-            if (i + kPairWarps < C.i1) hn = load_hdr(i + kPairWarps, xs, ps, nbr, cnt, cap, X, want_excl);
+            if (i + stride < C.i1) hn = load_hdr(i + stride, xs, ps, nbr, cnt, cap, X, want_excl);
 #define NB_PAIR_ARGS C, K, N, i, H, t0, t1, last, runs, nr, cand, par, cflag, qd_all[w], qj_all[w], xs, nbr, cap, X, \
                      ffix, e_atom, pscr, scale, flags
             if (multi) {
@@ -635,11 +638,14 @@ __global__ void __launch_bounds__(kVjpThreads, COUL ? 2 : 4) k_vjp_cell(
     const int* __restrict__ start, const float4* __restrict__ xs, const float2* __restrict__ ps,
     const float4* __restrict__ lam, const unsigned short* __restrict__ nbr, const int* __restrict__ cnt,
     ExclView X, float4* __restrict__ gx_s, float2* __restrict__ gp_s, long long* __restrict__ ffix,
-    float4* __restrict__ e_atom, float4* __restrict__ pscr, float scale, unsigned* flags) {
-    const int c = blockIdx.x;
+    float4* __restrict__ e_atom, float4* __restrict__ pscr, float scale, unsigned* flags, int split) {
+    // `split` blocks share a cell, as in k_pair_cell
+    const int c = blockIdx.x / split, part = blockIdx.x % split;
+    const int stride = kVjpWarps * split;
     const SysDev& S = sys[cell_sys[c]];
     const CellCtx C = cell_ctx(c, S, start);
-    if (C.i0 == C.i1) return;
+    const int ib = C.i0 + part * kVjpWarps + (threadIdx.x >> 5);
+    if (C.i0 + part * kVjpWarps >= C.i1) return;
     const PairK K = pair_k(S);
     __shared__ BuildRun runs[kMaxRuns];
     __shared__ int n_runs, n_cand;
@@ -653,7 +659,7 @@ __global__ void __launch_bounds__(kVjpThreads, COUL ? 2 : 4) k_vjp_cell(
     const int w = threadIdx.x >> 5;
     const bool want_excl = COUL == kCoulEwald && K.alpha > 0.f;
     AtomHdr hn;
-    if (C.i0 + w < C.i1) hn = load_hdr(C.i0 + w, xs, ps, nbr, cnt, cap, X, want_excl);
+    if (ib < C.i1) hn = load_hdr(ib, xs, ps, nbr, cnt, cap, X, want_excl);
     if (w == 0) cell_runs(C, S, start, runs, &n_runs, &n_cand, flags);
     __syncthreads();
     const int nr = n_runs, total = n_cand;
@@ -664,10 +670,10 @@ __global__ void __launch_bounds__(kVjpThreads, COUL ? 2 : 4) k_vjp_cell(
         stage_pair_tile(C, runs, nr, t0, t1, kVjpThreads, xs, ps, lam, cand, par, lamc, cflag);
         __syncthreads();
         const bool last = t1 == total;
-        if (t0 > 0 && C.i0 + w < C.i1) hn = load_hdr(C.i0 + w, xs, ps, nbr, cnt, cap, X, want_excl);
-        for (int i = C.i0 + w; i < C.i1; i += kVjpWarps) {
+        if (t0 > 0 && ib < C.i1) hn = load_hdr(ib, xs, ps, nbr, cnt, cap, X, want_excl);
+        for (int i = ib; i < C.i1; i += stride) {
             const AtomHdr H = hn;
-            if (i + kVjpWarps < C.i1) hn = load_hdr(i + kVjpWarps, xs, ps, nbr, cnt, cap, X, want_excl);
+            if (i + stride < C.i1) hn = load_hdr(i + stride, xs, ps, nbr, cnt, cap, X, want_excl);
 #define NB_VJP_ARGS C, K, N, i, H, t0, t1, last, runs, nr, cand, par, lamc, cflag, qd_all[w], qj_all[w], xs, lam, nbr, \
                     cap, X, gx_s, gp_s, ffix, e_atom, pscr, scale, flags
             if (multi) {
@@ -706,13 +712,13 @@ template <bool LJ, int COUL>
 static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp) {
     const ExclView X = excl_view(h);
     if (vjp)
-        k_vjp_cell<LJ, COUL><<<h->n_cells, kVjpThreads, vjp_smem(h), st>>>(
+        k_vjp_cell<LJ, COUL><<<h->n_cells * h->split_pair, kVjpThreads, vjp_smem(h), st>>>(
             h->n_atoms, h->cap, h->tile, h->cell_sys, h->sys, h->cell_start, h->xs, h->ps, h->lam, h->nbr,
-            h->nbr_cnt, X, h->gx_s, h->gp_s, h->ffix, h->e_atom, h->pscr, h->fscale, h->flags);
+            h->nbr_cnt, X, h->gx_s, h->gp_s, h->ffix, h->e_atom, h->pscr, h->fscale, h->flags, h->split_pair);
     else
-        k_pair_cell<LJ, COUL><<<h->n_cells, kPairThreads, pair_smem(h), st>>>(
+        k_pair_cell<LJ, COUL><<<h->n_cells * h->split_pair, kPairThreads, pair_smem(h), st>>>(
             h->n_atoms, h->cap, h->tile, h->cell_sys, h->sys, h->cell_start, h->xs, h->ps, h->nbr, h->nbr_cnt, X,
-            h->ffix, h->e_atom, h->pscr, h->fscale, h->flags);
+            h->ffix, h->e_atom, h->pscr, h->fscale, h->flags, h->split_pair);
 }
 
 static void dispatch(nb_handle* h, int terms, cudaStream_t st, bool vjp) {
@@ -759,6 +765,7 @@ cudaError_t pair_setup(nb_handle* h) {
     if (e != cudaSuccess) return e;
     // static shared memory of the VJP kernel: queues and runs (~23 KB)
     if ((long long)vjp_smem(h) + 24 * 1024 > optin) return cudaErrorInvalidValue;
+    h->split_pair = pick_split(h, kPairWarps, 1);
     e = set_smem<true, kCoulEwald>();
     if (e == cudaSuccess) e = set_smem<true, kCoulRF>();
     if (e == cudaSuccess) e = set_smem<true, kCoulNone>();

@@ -33,7 +33,8 @@ EXPORTS = [
     "nb_status_str", "nb_create", "nb_destroy", "nb_num_atoms", "nb_num_systems", "nb_check",
     "nl_build", "nonbonded_forces", "nonbonded_forces_allpairs", "pme_spread", "pme_gather", "md_step", "hmc_trajectory",
     "hmc_trajectory_backward", "hmc_trajectory_steps", "hmc_trajectory_steps_backward", "autocorrelation",
-    "nonbonded_force_vjp", "nb_rebuild_count", "nb_timing_enable", "nb_timing_read", "pme_spread_static",
+    "nonbonded_force_vjp", "nb_rebuild_count", "nb_blocks_per_cell", "nb_timing_enable", "nb_timing_read",
+    "pme_spread_static",
 ]
 STATIC_MESH_MAX = 1 << 20
 STAGES = ["check", "rebuild", "pair", "spread", "fft", "convolve", "gather", "update"]
@@ -67,6 +68,7 @@ class Options(ctypes.Structure):
         ("stencil_tile", ctypes.c_int32),
         ("cell_div", ctypes.c_int32),
         ("force_bits", ctypes.c_int32),
+        ("blocks_per_cell", ctypes.c_int32),
     ]
 
 
@@ -128,6 +130,8 @@ def load():
     lib.autocorrelation.argtypes = [_vp, _i32, _i32, _i32, _dbl, _dbl, _vp, _vp, _vp]
     lib.nonbonded_force_vjp.restype = ctypes.c_int
     lib.nonbonded_force_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp]
+    lib.nb_blocks_per_cell.restype = ctypes.c_int
+    lib.nb_blocks_per_cell.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
     lib.nb_timing_enable.restype = ctypes.c_int
     lib.nb_timing_enable.argtypes = [_vp, _i32]
     lib.nb_timing_read.restype = ctypes.c_int
@@ -221,7 +225,8 @@ class Handle:
     ``workloads.System`` (n, box, r_cut, r_skin, r_switch, alpha, ke,
     pme_grid, sigma, sqrt_eps, excl_off/excl_idx)."""
 
-    def __init__(self, systems, max_neighbors=0, stencil_tile=0, cell_div=0, force_bits=0, periodic=True):
+    def __init__(self, systems, max_neighbors=0, stencil_tile=0, cell_div=0, force_bits=0, periodic=True,
+                 blocks_per_cell=0):
         lib = load()
         self._h = None
         n_sys = len(systems)
@@ -259,7 +264,7 @@ class Handle:
         self.sqrt_eps = np.ascontiguousarray(np.concatenate(sqe), np.float32)
         ex_off = np.ascontiguousarray(offs, np.int32)
         ex_idx = np.ascontiguousarray(np.concatenate(idxs) if idxs else np.zeros(0), np.int32)
-        opt = Options(int(max_neighbors), int(stencil_tile), int(cell_div), int(force_bits))
+        opt = Options(int(max_neighbors), int(stencil_tile), int(cell_div), int(force_bits), int(blocks_per_cell))
         h = _vp()
         st = lib.nb_create(ctypes.byref(h), descs, n_sys, self.sigma.ctypes.data, self.sqrt_eps.ctypes.data,
                            ex_off.ctypes.data, ex_idx.ctypes.data if ex_idx.size else None, ctypes.byref(opt))
@@ -303,6 +308,12 @@ class Handle:
         cnt = np.zeros(len(STAGES), np.int64)
         _ok(self._lib.nb_timing_read(self._h, _stream(), ms.ctypes.data, cnt.ctypes.data), "nb_timing_read")
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(STAGES)}
+
+    def blocks_per_cell(self):
+        """(list build, pair/VJP kernels) thread blocks per cell."""
+        b, p = _i32(0), _i32(0)
+        _ok(self._lib.nb_blocks_per_cell(self._h, ctypes.byref(b), ctypes.byref(p)), "nb_blocks_per_cell")
+        return int(b.value), int(p.value)
 
     def nl_build(self, xq, max_pairs=0, force_rebuild=False):
         """Return (pairs int32 [n, 2] on the device, n_pairs)."""

@@ -16,12 +16,15 @@ Contents (each cites the passage of the paper it follows):
   * ``pme`` -- smooth PME with recursive B-splines (module ``oracle.pme``).
   * ``dynamics`` -- velocity Verlet (Sec. 2.2.1) and the HMC proposal / ESJD loss
     (Sec. 4, Eqs. loss and acceptance).
+  * ``constraints`` -- rigid-water constraints as their defining equations (SHAKE by
+    Newton's method, RATTLE by a linear solve) and the Langevin middle scheme
+    (Sec. 2.2.1).
   * ``tuning`` -- the folded-normal trajectory length, the step-length-weighted loss
     L_HMC truncated at L_q (Sec. 4, Eq. loss_steps), per-step HMC statistics, and the
     autocorrelation A(k) / tau_exp (Sec. 4).
 
-Parity status: every function is pinned by tests/test_oracle_pins.py and
-tests/test_oracle_tuning.py (closed forms, lattice sums, finite differences,
+Parity status: every function is pinned by tests/test_oracle_pins.py,
+tests/test_oracle_tuning.py and tests/test_oracle_constraints.py (closed forms, lattice sums, finite differences,
 brute-force invariants, scipy's folded normal).
 """
 import ctypes

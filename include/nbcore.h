@@ -227,6 +227,54 @@ nb_status md_step(nb_handle* h, float* xq, float* v, const float* dt, int32_t n_
                   double* energies, int32_t terms, void* stream);
 
 /*
+ * Rigid three-site water for langevin_step and the constraint calls (Sec. 2.2.1:
+ * position and velocity constraints, SETTLE):
+ *   mols [n_mol][3] (host) caller indices (O, H1, H2) of each molecule, each atom in at
+ *                   most one molecule, the three in one system; both H of a molecule must
+ *                   have the same mass.
+ *   d_oh, d_hh      the constrained O-H and H-H distances (0 < d_hh < 2 d_oh).
+ * n_mol = 0 removes all constraints.  Host work and one copy; NB_ERR_ARG on invalid input.
+ */
+nb_status nb_set_water_constraints(nb_handle* h, const int32_t* mols, int32_t n_mol, double d_oh, double d_hh);
+
+/*
+ * Langevin dynamics (Sec. 2.2.1; the "middle" scheme of the unified thermostat framework the
+ * paper cites, in leapfrog variables, velocities at half steps), n_steps steps of
+ *   v += dt w F;  constrain v;  x' = x + dt/2 v;  v = c1 v + c2 sqrt(kT w) xi;
+ *   x'' = x' + dt/2 v;  x = SETTLE(x, x'');  v += (x - x'') / dt
+ * with c1 = exp(-gamma dt), c2 = sqrt(1 - c1^2), the constraints those set by
+ * nb_set_water_constraints (none: plain Langevin; gamma = 0: leapfrog velocity Verlet).
+ *   xq [N][4]        (device, in/out) positions and charges.
+ *   v [N][4]         (device, in/out) (vx, vy, vz, inverse mass): the velocity half a step
+ *                    before xq's step (read and written), the inverse mass read only.
+ *   dt, gamma [n_sys] (device) step and friction per system.
+ *   kT               thermal energy in the energy unit of the force field.
+ *   xi               (device) [n_steps][N][3] standard normals, one triple per atom and step.
+ *   energies         (device, may be NULL) FP64 [n_steps+1][n_sys][6] as md_step, the kinetic
+ *                    energy at step n the mean of the two neighbouring half steps (at the
+ *                    last step, the half step before it).
+ * A molecule that SETTLE cannot place (a step far too large) makes nb_check return
+ * NB_ERR_NONFINITE.
+ */
+nb_status langevin_step(nb_handle* h, float* xq, float* v, const float* dt, const float* gamma, double kT,
+                        int32_t n_steps, const float* xi, double* energies, int32_t terms, void* stream);
+
+/*
+ * SETTLE alone: constrains every molecule of x relative to the constrained positions
+ * x_ref (both [N][4], device; x overwritten), with inverse masses inv_mass [N] (device);
+ * v [N][4] (device, may be NULL) gets the correction / dt added.  Atoms outside molecules
+ * are untouched.
+ */
+nb_status constrain_positions(nb_handle* h, const float* x_ref, float* x, float* v, const float* inv_mass, float dt,
+                              void* stream);
+
+/*
+ * Velocity constraint alone: v [N][4] (device, (vx, vy, vz, inverse mass)) projected so that
+ * every constrained distance of the molecules at x [N][4] has zero rate.
+ */
+nb_status constrain_velocities(nb_handle* h, const float* x, float* v, void* stream);
+
+/*
  * One HMC proposal per system (Sec. 4): Maxwell-Boltzmann velocities
  * v0 = sqrt(kT w) xi (w = inverse mass), n_leap velocity-Verlet steps of length dt[s],
  * E = U + K in FP64, acceptance alpha = min(1, exp(-(E' - E)/kT)), Metropolis test

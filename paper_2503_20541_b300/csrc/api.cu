@@ -458,6 +458,15 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(dalloc(h, &h->xbar, N));
         NB_TRY(dalloc(h, &h->vbar, N));
         NB_TRY(dalloc(h, &h->xwork, N));
+        NB_TRY(dalloc(h, &h->groups, N));
+        {
+            // no constraints until nb_set_water_constraints: every atom is its own group
+            std::vector<int4> g((size_t)N);
+            for (long long i = 0; i < N; ++i) g[(size_t)i] = make_int4((int)i, -1, -1, 1);
+            NB_TRY(cudaMemcpy(h->groups, g.data(), sizeof(int4) * N, cudaMemcpyHostToDevice));
+            h->n_groups = (int)N;
+            h->sid_host = sid_h;
+        }
         NB_TRY(dalloc(h, &h->counter, 1));
         {
             std::vector<int> rb_sys, rb_off(n_systems + 1, 0);
@@ -646,6 +655,72 @@ nb_status pme_gather(nb_handle* h, const float* xq, const float* phi, float* f_o
     cudaStream_t st = S(stream);
     launch_load(h, F4(xq), st);
     launch_pme_gather_only(h, phi, f_out, st);
+    return launched();
+}
+
+nb_status nb_set_water_constraints(nb_handle* h, const int32_t* mols, int32_t n_mol, double d_oh, double d_hh) {
+    if (!h || n_mol < 0 || (n_mol > 0 && !mols)) return NB_ERR_ARG;
+    if (n_mol > 0 && !(d_oh > 0.0 && d_hh > 0.0 && d_hh < 2.0 * d_oh && std::isfinite(d_oh))) return NB_ERR_ARG;
+    const int N = h->n_atoms;
+    std::vector<char> used((size_t)N, 0);
+    std::vector<int4> g;
+    g.reserve((size_t)N);
+    for (int m = 0; m < n_mol; ++m) {
+        const int a = mols[3 * m], b = mols[3 * m + 1], c = mols[3 * m + 2];
+        for (int i : {a, b, c})
+            if (i < 0 || i >= N || used[(size_t)i]++) return NB_ERR_ARG;  // out of range or in two molecules
+        if (h->sid_host[(size_t)a] != h->sid_host[(size_t)b] || h->sid_host[(size_t)a] != h->sid_host[(size_t)c])
+            return NB_ERR_ARG;
+        g.push_back(make_int4(a, b, c, 3));
+    }
+    for (int i = 0; i < N; ++i)
+        if (!used[(size_t)i]) g.push_back(make_int4(i, -1, -1, 1));
+    DeviceGuard dg(h->device);
+    if (cudaMemcpy(h->groups, g.data(), sizeof(int4) * g.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return NB_ERR_CUDA;
+    h->n_groups = (int)g.size();
+    h->n_water = n_mol;
+    h->d_oh = d_oh;
+    h->d_hh = d_hh;
+    return NB_OK;
+}
+
+nb_status langevin_step(nb_handle* h, float* xq, float* v, const float* dt, const float* gamma, double kT,
+                        int32_t n_steps, const float* xi, double* energies, int32_t terms, void* stream) {
+    if (!h || !xq || !v || !dt || !gamma || !xi || n_steps < 1 || !(kT >= 0.0)) return NB_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    const int t = terms & NB_TERM_ALL;
+    float4* x4 = F4(xq);
+    float4* v4 = F4(v);
+    const size_t stride = (size_t)h->n_sys * NB_NE;
+    for (int step = 0; step <= n_steps; ++step) {
+        nb_status s = eval(h, x4, t, step == 0 && (terms & NB_FORCE_REBUILD), st);
+        if (s != NB_OK) return s;
+        Stage sc(h, NB_STAGE_UPDATE, st);
+        if (step < n_steps) {
+            launch_langevin(h, x4, v4, dt, gamma, kT, xi + (size_t)step * 3 * h->n_atoms, st);
+        } else {
+            if (!energies) break;
+            launch_kinetic(h, v4, st);
+        }
+        if (energies) launch_reduce_energy(h, t, 1, energies + (size_t)step * stride, st);
+    }
+    return launched();
+}
+
+nb_status constrain_positions(nb_handle* h, const float* x_ref, float* x, float* v, const float* inv_mass, float dt,
+                              void* stream) {
+    if (!h || !x_ref || !x || !inv_mass || (v && !(dt > 0.f))) return NB_ERR_ARG;
+    DeviceGuard g(h->device);
+    launch_settle(h, F4(x_ref), F4(x), v ? F4(v) : nullptr, inv_mass, dt, S(stream));
+    return launched();
+}
+
+nb_status constrain_velocities(nb_handle* h, const float* x, float* v, void* stream) {
+    if (!h || !x || !v) return NB_ERR_ARG;
+    DeviceGuard g(h->device);
+    launch_rattle(h, F4(x), F4(v), S(stream));
     return launched();
 }
 

@@ -81,6 +81,13 @@ struct nb_handle {
     int blocks_per_cell = 0;     // option (0: auto)
     int split_build = 1;         // blocks per cell of the list build
     int split_pair = 1;          // blocks per cell of the pair and VJP kernels
+    // rigid water (Langevin dynamics): constraint groups covering every atom once,
+    // (O, H1, H2, 3) or (atom, -1, -1, 1)
+    int n_groups = 0;
+    int4* groups = nullptr;
+    int n_water = 0;
+    double d_oh = 0.0, d_hh = 0.0;
+    std::vector<int> sid_host;   // system of each atom (caller order)
     int any_coul = 0;   // some system has ke != 0
     int coul_kind = 1;  // electrostatics of the charged systems: 1 Ewald, 2 reaction field
     long long grid_total = 0, cgrid_total = 0;
@@ -298,5 +305,12 @@ void launch_bwd_adjoint(nb_handle* h, const float* w, const float* dt, const flo
                         const float4* p_prev, float* wbar, cudaStream_t st);
 void launch_bwd_final(nb_handle* h, const float* w, const float* dt, const float* xi, double kT,
                       float* wbar, double* g_dt, cudaStream_t st);
+// langevin.cu
+void launch_langevin(nb_handle* h, float4* xq, float4* v, const float* dt, const float* gamma, double kT,
+                     const float* xi, cudaStream_t st);
+void launch_kinetic(nb_handle* h, const float4* v, cudaStream_t st);
+void launch_settle(nb_handle* h, const float4* x_ref, float4* x, float4* v, const float* inv_mass, float dt,
+                   cudaStream_t st);
+void launch_rattle(nb_handle* h, const float4* x, float4* v, cudaStream_t st);
 
 }  // namespace nb

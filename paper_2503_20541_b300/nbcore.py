@@ -34,7 +34,7 @@ EXPORTS = [
     "nl_build", "nonbonded_forces", "nonbonded_forces_allpairs", "pme_spread", "pme_gather", "md_step", "hmc_trajectory",
     "hmc_trajectory_backward", "hmc_trajectory_steps", "hmc_trajectory_steps_backward", "autocorrelation",
     "nonbonded_force_vjp", "nb_rebuild_count", "nb_blocks_per_cell", "nb_timing_enable", "nb_timing_read",
-    "pme_spread_static",
+    "pme_spread_static", "nb_set_water_constraints", "langevin_step", "constrain_positions", "constrain_velocities",
 ]
 STATIC_MESH_MAX = 1 << 20
 STAGES = ["check", "rebuild", "pair", "spread", "fft", "convolve", "gather", "update"]
@@ -130,6 +130,14 @@ def load():
     lib.autocorrelation.argtypes = [_vp, _i32, _i32, _i32, _dbl, _dbl, _vp, _vp, _vp]
     lib.nonbonded_force_vjp.restype = ctypes.c_int
     lib.nonbonded_force_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp]
+    lib.nb_set_water_constraints.restype = ctypes.c_int
+    lib.nb_set_water_constraints.argtypes = [_vp, _vp, _i32, _dbl, _dbl]
+    lib.langevin_step.restype = ctypes.c_int
+    lib.langevin_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _dbl, _i32, _vp, _vp, _i32, _vp]
+    lib.constrain_positions.restype = ctypes.c_int
+    lib.constrain_positions.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_float, _vp]
+    lib.constrain_velocities.restype = ctypes.c_int
+    lib.constrain_velocities.argtypes = [_vp, _vp, _vp, _vp]
     lib.nb_blocks_per_cell.restype = ctypes.c_int
     lib.nb_blocks_per_cell.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
     lib.nb_timing_enable.restype = ctypes.c_int
@@ -308,6 +316,36 @@ class Handle:
         cnt = np.zeros(len(STAGES), np.int64)
         _ok(self._lib.nb_timing_read(self._h, _stream(), ms.ctypes.data, cnt.ctypes.data), "nb_timing_read")
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(STAGES)}
+
+    def set_water_constraints(self, mols, d_oh, d_hh):
+        """Rigid water: mols (n_mol, 3) caller indices (O, H1, H2); d_oh, d_hh distances."""
+        m = np.ascontiguousarray(np.asarray(mols, dtype=np.int32).reshape(-1, 3))
+        _ok(self._lib.nb_set_water_constraints(self._h, m.ctypes.data if m.size else None, int(m.shape[0]),
+                                               float(d_oh), float(d_hh)), "nb_set_water_constraints")
+
+    def langevin_step(self, xq, v, dt, gamma, kT, n_steps, xi, energies=None, terms=NB_TERM_ALL):
+        torch = _torch()
+        N, R = self.n_atoms, self.n_sys
+        _ok(self._lib.langevin_step(
+            self._h, _ptr(xq, torch.float32, (N, 4), "xq"), _ptr(v, torch.float32, (N, 4), "v"),
+            _ptr(dt, torch.float32, (R,), "dt"), _ptr(gamma, torch.float32, (R,), "gamma"), float(kT), int(n_steps),
+            _ptr(xi, torch.float32, (n_steps, N, 3), "xi"),
+            _ptr(energies, torch.float64, (n_steps + 1, R, NB_NE), "energies", True), int(terms), _stream()),
+            "langevin_step")
+
+    def constrain_positions(self, x_ref, x, inv_mass, v=None, dt=0.0):
+        torch = _torch()
+        N = self.n_atoms
+        _ok(self._lib.constrain_positions(
+            self._h, _ptr(x_ref, torch.float32, (N, 4), "x_ref"), _ptr(x, torch.float32, (N, 4), "x"),
+            _ptr(v, torch.float32, (N, 4), "v", True), _ptr(inv_mass, torch.float32, (N,), "inv_mass"), float(dt),
+            _stream()), "constrain_positions")
+
+    def constrain_velocities(self, x, v):
+        torch = _torch()
+        N = self.n_atoms
+        _ok(self._lib.constrain_velocities(self._h, _ptr(x, torch.float32, (N, 4), "x"),
+                                           _ptr(v, torch.float32, (N, 4), "v"), _stream()), "constrain_velocities")
 
     def blocks_per_cell(self):
         """(list build, pair/VJP kernels) thread blocks per cell."""

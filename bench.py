@@ -482,7 +482,10 @@ def water_elec_sweep(torch, nbcore, wl, n_mols=(1000, 10000, 32000, 100000)):
                 ms_rb = timed(lambda: h.nonbonded_forces(xq, f, e, terms=terms | nbcore.NB_FORCE_REBUILD), reps)
                 ms_ru = timed(lambda: h.nonbonded_forces(xq, f, e, terms=terms), reps)
                 h.check()
-            row[kind] = {"ms_eval_rebuild": ms_rb, "ms_eval_list_reused": ms_ru}
+                res = {"ms_eval_rebuild": ms_rb, "ms_eval_list_reused": ms_ru}
+                if kind == "rf":
+                    res.update(_rigid_water_md(torch, nbcore, h, s, xq))
+            row[kind] = res
             if kind == "pme":
                 row[kind]["mesh"] = list(s.pme_grid)
             del xq, f
@@ -491,7 +494,58 @@ def water_elec_sweep(torch, nbcore, wl, n_mols=(1000, 10000, 32000, 100000)):
         rows.append(row)
     return {"rows": rows, "workload": "water at 1 g/cm^3 (3-site point-charge molecules, LJ on O), r_c 10 A, "
                                       "r_skin 2.5 A; RF eps_s 78.5 vs Ewald alpha %.4f/A + PME order 4; step = one "
-                                      "force evaluation with energies; list rebuilt every step or reused" % alpha}
+                                      "force evaluation with energies; list rebuilt every step or reused; rigid-water "
+                                      "MD: Langevin middle scheme with SETTLE, dt 0.5 fs, gamma 0.1/fs, 300 K (the "
+                                      "paper's water run settings, with rigid instead of flexible molecules), list "
+                                      "checked every step, a CUDA graph of 10 steps replayed, normals precomputed on "
+                                      "the device" % alpha}
+
+
+def _rigid_water_md(torch, nbcore, h, s, xq, n_inner=10, reps=10):
+    """ms per Langevin + SETTLE step of water system s on handle h (units: A, amu, kJ/mol:
+    time unit 0.1 ps)."""
+    import math
+    from paper_2503_20541_b300.graphs import CapturedStep
+    n_mol = s.n // 3
+    mols = np.arange(s.n, dtype=np.int32).reshape(n_mol, 3)
+    d_hh = 2.0 * wl_roh() * math.sin(math.radians(wl_hoh()) / 2.0)
+    h.set_water_constraints(mols, wl_roh(), d_hh)
+    x = xq.clone()
+    m = torch.from_numpy(s.mass.astype(np.float32)).cuda()
+    v = torch.zeros((s.n, 4), dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    kT = 2.494
+    v[:, :3] = torch.randn((s.n, 3), device="cuda", generator=gen) * torch.sqrt(kT / m)[:, None]
+    v[:, 3] = 1.0 / m
+    h.constrain_velocities(x, v)
+    xi = torch.randn((n_inner, s.n, 3), device="cuda", generator=gen)
+    dt = torch.tensor([0.005], device="cuda")
+    gamma = torch.tensor([10.0], device="cuda")
+    terms = nbcore.NB_TERM_LJ | nbcore.NB_TERM_COUL
+    step = CapturedStep(lambda: h.langevin_step(x, v, dt, gamma, kT, n_inner, xi, terms=terms), warmup=2)
+    for _ in range(3):
+        step.replay()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        step.replay()
+    b.record()
+    torch.cuda.synchronize()
+    h.check()
+    ms = a.elapsed_time(b) / (reps * n_inner)
+    h.set_water_constraints(np.zeros((0, 3), np.int32), 1.0, 1.0)
+    return {"md_ms_per_step": ms, "md_steps_per_s": 1e3 / ms, "md_ns_per_day": 1e3 / ms * 0.5e-6 * 86400}
+
+
+def wl_roh():
+    from paper_2503_20541_b300 import workloads
+    return workloads.WATER_ROH
+
+
+def wl_hoh():
+    from paper_2503_20541_b300 import workloads
+    return workloads.WATER_HOH_DEG
 
 
 def hmc_training(torch, nbcore, wl, iters=200):

@@ -118,3 +118,73 @@ def test_reaction_field_descriptor_checks():
     eo, fo = oracle_real_space(sw)
     assert rel_rms(f.cpu().numpy()[lj.n:].astype(np.float64), fo) <= F_TOL
     assert abs(e.cpu().numpy()[1, 1] - eo[1]) <= _rf_tol(sw, eo[1])
+
+
+R_HMC, N_LEAP, K_CKPT, KT = 3, 8, 4, 2.494
+
+
+def _rf_water(r):
+    return wl.as_reaction_field(wl.water_box(n_side=4, L=12.42, seed=80 + r, r_cut=5.0, r_skin=0.5, alpha=0.0,
+                                             pme_grid=16))
+
+
+def _oracle_hmc_loss(s, xi, w, dt):
+    from oracle import dynamics as odyn
+    p = oracle_params(s)
+
+    def fe(x):
+        e, f = oracle.nonbonded(x, s.q, s.sigma, s.sqrt_eps, p, excl=s.excl)
+        return f, float(e.sum())
+    o = odyn.hmc_proposal(s.x.astype(np.float64), xi.astype(np.float64), w, float(dt), N_LEAP, KT, fe, s.box)
+    return o["alpha"] * o["jump"] / (R_HMC * N_LEAP), o
+
+
+def test_hmc_backward_with_reaction_field_matches_finite_differences():
+    systems = [_rf_water(r) for r in range(R_HMC)]
+    n = systems[0].n
+    mass = np.where(systems[0].q < 0, 15.999, 1.008)
+    w = np.tile(1.0 / mass, R_HMC).astype(np.float32)
+    dts = np.array([0.01, 0.014, 0.012], np.float32)
+    xi, u = wl.hmc_randoms(R_HMC, n, seed=6)
+    with nbcore.Handle(systems) as h:
+        x0 = torch.cat([dev_xq(s) for s in systems])
+        x_out = torch.empty_like(x0)
+        stats = torch.empty((R_HMC, 4), dtype=torch.float64, device="cuda")
+        ck = torch.empty(nbcore.ckpt_size(R_HMC * n, N_LEAP, K_CKPT), dtype=torch.float32, device="cuda")
+        wt, dtt = torch.from_numpy(w).cuda(), torch.from_numpy(dts).cuda()
+        xit, ut = torch.from_numpy(xi.reshape(-1, 3)).cuda(), torch.from_numpy(u).cuda()
+        h.hmc_trajectory(x0, x_out, wt, dtt, N_LEAP, KT, xit, ut, stats, ck, K_CKPT, terms=TERMS)
+        st = stats.cpu().numpy()
+        g_alpha = torch.from_numpy(st[:, 2] / (R_HMC * N_LEAP)).cuda()
+        g_jump = torch.from_numpy(st[:, 1] / (R_HMC * N_LEAP)).cuda()
+        g_dt = torch.zeros(R_HMC, dtype=torch.float64, device="cuda")
+        g_w = torch.zeros(R_HMC * n, dtype=torch.float32, device="cuda")
+        h.hmc_trajectory_backward(x0, wt, dtt, N_LEAP, KT, xit, ck, K_CKPT, stats, g_alpha, g_jump, g_dt, g_w,
+                                  terms=TERMS)
+        h.check()
+    gdt = g_dt.cpu().numpy()
+    gw = g_w.cpu().numpy().astype(np.float64)
+    w64, d64 = w.astype(np.float64), dts.astype(np.float64)
+    checked = 0
+    for r in range(R_HMC):
+        s = systems[r]
+        wr = w64[r * n:(r + 1) * n]
+        _, o = _oracle_hmc_loss(s, xi[r], wr, d64[r])
+        # dH = H1 - H0: two reaction-field energies, each within its rounding bound
+        tol_dh = 2.0 * _rf_tol(s, o["U0"]) + 1e-6 * (abs(o["U0"]) + o["K0"])
+        assert abs(st[r, 0] - o["dH"]) <= tol_dh, (r, st[r, 0], o["dH"], tol_dh)
+        if abs(o["dH"]) < 10.0 * abs(st[r, 0] - o["dH"]) or (o["dH"] > 0) != (st[r, 0] > 0):
+            continue  # within the measured dH error of the alpha = 1 kink
+        checked += 1
+        hs = 1e-5 * d64[r]
+        fd = (_oracle_hmc_loss(s, xi[r], wr, d64[r] + hs)[0] - _oracle_hmc_loss(s, xi[r], wr, d64[r] - hs)[0]) / (
+            2 * hs)
+        assert gdt[r] == pytest.approx(fd, rel=2e-3, abs=1e-9), (r, gdt[r], fd)
+        dirv = np.where(s.q < 0, 1.0, -0.5) * wr
+        eps = 1e-5
+        fdw = (_oracle_hmc_loss(s, xi[r], wr + eps * dirv, d64[r])[0] -
+               _oracle_hmc_loss(s, xi[r], wr - eps * dirv, d64[r])[0]) / (2 * eps)
+        g = gw[r * n:(r + 1) * n]
+        tol = 2e-3 * abs(fdw) + 1e-4 * float(np.abs(g * dirv).sum())
+        assert abs(float(np.dot(g, dirv)) - fdw) <= tol, (r, float(np.dot(g, dirv)), fdw, tol)
+    assert checked >= 1

@@ -61,12 +61,9 @@ __device__ __forceinline__ int cell_coord(float w, float scale, int nc) {
     return min(max(c, 0), nc - 1);
 }
 
-__global__ void k_bin(int N, const float4* __restrict__ xq, const int* __restrict__ sid,
-                      const SysDev* __restrict__ sys, int* __restrict__ cellid, int* cell_count,
-                      unsigned* flags) {
-    if (flags[0] == 0u) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+__device__ __forceinline__ void bin_atom(int i, const float4* __restrict__ xq, const int* __restrict__ sid,
+                                         const SysDev* __restrict__ sys, int* __restrict__ cellid, int* cell_count,
+                                         unsigned* flags) {
     float4 p = xq[i];
     const SysDev& S = sys[sid[i]];
     if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z))) {
@@ -84,6 +81,14 @@ __global__ void k_bin(int N, const float4* __restrict__ xq, const int* __restric
     int c = S.cell_off + (cz * S.nc[1] + cy) * S.nc[0] + cx;
     cellid[i] = c;
     atomicAdd(&cell_count[c], 1);
+}
+
+__global__ void k_bin(int N, const float4* __restrict__ xq, const int* __restrict__ sid,
+                      const SysDev* __restrict__ sys, int* __restrict__ cellid, int* cell_count,
+                      unsigned* flags) {
+    if (flags[0] == 0u) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) bin_atom(i, xq, sid, sys, cellid, cell_count, flags);
 }
 
 // Block-wide exclusive scan of one int per thread (1024 threads); returns the block total.
@@ -167,10 +172,8 @@ __global__ void __launch_bounds__(1024) k_scan_c(int n, int* start, const int* _
     }
 }
 
-// All three scan steps in one block, for grids of at most kScanTile cells.
-__global__ void __launch_bounds__(1024) k_scan_single(int n, int* count, int* start, int* cursor,
-                                                       const unsigned* flags) {
-    if (flags[0] == 0u) return;
+// All three scan steps in one block of 1024 threads, for grids of at most kScanTile cells.
+__device__ __forceinline__ void scan_single_body(int n, int* count, int* start, int* cursor) {
     __shared__ int tot;
     int base = threadIdx.x * kScanItems;
     int v[kScanItems], s = 0;
@@ -192,6 +195,12 @@ __global__ void __launch_bounds__(1024) k_scan_single(int n, int* count, int* st
     if (threadIdx.x == 0) start[n] = tot;
 }
 
+__global__ void __launch_bounds__(1024) k_scan_single(int n, int* count, int* start, int* cursor,
+                                                       const unsigned* flags) {
+    if (flags[0] == 0u) return;
+    scan_single_body(n, count, start, cursor);
+}
+
 __global__ void k_scatter(int N, const int* __restrict__ cellid, const int* __restrict__ start,
                           int* cursor, int* __restrict__ perm_tmp, const unsigned* flags) {
     if (flags[0] == 0u) return;
@@ -201,17 +210,14 @@ __global__ void k_scatter(int N, const int* __restrict__ cellid, const int* __re
     perm_tmp[start[c] + atomicAdd(&cursor[c], 1)] = i;
 }
 
-// One warp per cell: order the cell's atoms by caller index and gather slot data.
-__global__ void k_cellsort(int n_cells, const int* __restrict__ start, const int* __restrict__ perm_tmp,
-                           const float4* __restrict__ xq, const float2* __restrict__ params,
-                           const int* __restrict__ sid, const SysDev* __restrict__ sys,
-                           int* __restrict__ perm, int* __restrict__ iperm, float4* __restrict__ xs,
-                           float4* __restrict__ xsb, float2* __restrict__ ps, float4* __restrict__ xref,
-                           const unsigned* flags) {
-    if (flags[0] == 0u) return;
-    int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (w >= n_cells) return;
+// Atoms of cell w (one warp) in caller-index order, and their slot data.
+__device__ __forceinline__ void sort_cell(int w, const int* __restrict__ start, const int* __restrict__ perm_tmp,
+                                          const float4* __restrict__ xq, const float2* __restrict__ params,
+                                          const int* __restrict__ sid, const SysDev* __restrict__ sys,
+                                          int* __restrict__ perm, int* __restrict__ iperm, float4* __restrict__ xs,
+                                          float4* __restrict__ xsb, float2* __restrict__ ps,
+                                          float4* __restrict__ xref) {
+    const int lane = threadIdx.x & 31;
     int b = start[w], m = start[w + 1] - b;
     for (int a = lane; a < m; a += 32) {
         int i = perm_tmp[b + a];
@@ -233,6 +239,46 @@ __global__ void k_cellsort(int n_cells, const int* __restrict__ start, const int
         xsb[slot] = p;
         ps[slot] = params[i];
     }
+}
+
+// One warp per cell: order the cell's atoms by caller index and gather slot data.
+__global__ void k_cellsort(int n_cells, const int* __restrict__ start, const int* __restrict__ perm_tmp,
+                           const float4* __restrict__ xq, const float2* __restrict__ params,
+                           const int* __restrict__ sid, const SysDev* __restrict__ sys,
+                           int* __restrict__ perm, int* __restrict__ iperm, float4* __restrict__ xs,
+                           float4* __restrict__ xsb, float2* __restrict__ ps, float4* __restrict__ xref,
+                           const unsigned* flags) {
+    if (flags[0] == 0u) return;
+    int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= n_cells) return;
+    sort_cell(w, start, perm_tmp, xq, params, sid, sys, perm, iperm, xs, xsb, ps, xref);
+}
+
+
+// The whole re-slotting of a small handle (at most kScanTile cells, kSmallSortAtoms
+// atoms) in one block of 1024 threads: binning, the scan, the scatter and the in-cell
+// sort of k_bin, k_scan_single, k_scatter and k_cellsort, phase after phase behind block
+// barriers.  A step that keeps its list then runs one early-exiting kernel instead of four.
+__global__ void __launch_bounds__(1024) k_sort_small(int N, int n_cells, const float4* __restrict__ xq,
+                                                      const int* __restrict__ sid, const SysDev* __restrict__ sys,
+                                                      int* __restrict__ cellid, int* cell_count, int* start,
+                                                      int* cursor, int* __restrict__ perm_tmp,
+                                                      const float2* __restrict__ params, int* __restrict__ perm,
+                                                      int* __restrict__ iperm, float4* __restrict__ xs,
+                                                      float4* __restrict__ xsb, float2* __restrict__ ps,
+                                                      float4* __restrict__ xref, unsigned* flags) {
+    if (flags[0] == 0u) return;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) bin_atom(i, xq, sid, sys, cellid, cell_count, flags);
+    __syncthreads();
+    scan_single_body(n_cells, cell_count, start, cursor);
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int c = cellid[i];
+        perm_tmp[start[c] + atomicAdd(&cursor[c], 1)] = i;
+    }
+    __syncthreads();
+    for (int w = threadIdx.x >> 5; w < n_cells; w += blockDim.x >> 5)
+        sort_cell(w, start, perm_tmp, xq, params, sid, sys, perm, iperm, xs, xsb, ps, xref);
 }
 
 // Predicated 16-bit store: keeps the list append inside one basic block (no branch
@@ -552,8 +598,25 @@ void launch_load(nb_handle* h, const float4* xq, cudaStream_t st) {
 
 size_t build_smem(const nb_handle* h) { return (size_t)h->tile * (sizeof(float4) + (h->build_gen ? 1 : 0)); }
 
+static void launch_build(nb_handle* h, cudaStream_t st) {
+    auto build = h->excl_w == 0   ? k_build_cell<0, false>
+                 : h->excl_w == 2 ? k_build_cell<2, false>
+                 : h->max_excl <= 4 ? k_build_cell<4, false>
+                                    : k_build_cell<4, true>;
+    build<<<h->n_cells * h->split_build, kBuildThreads, build_smem(h), st>>>(
+        h->cap, h->tile, h->cell_sys, h->sys, h->cell_start, h->xs, h->perm, h->iperm, h->ex_off, h->ex_idx,
+        h->ex_slot, h->ex_cnt, h->nbr, h->nbr_cnt, h->build_ticket, h->flags, h->split_build);
+}
+
 void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st) {
     int N = h->n_atoms;
+    if (h->n_scan_blocks == 1 && N <= kSmallSortAtoms) {
+        k_sort_small<<<1, 1024, 0, st>>>(N, h->n_cells, xq, h->sid, h->sys, h->cellid, h->cell_count,
+                                         h->cell_start, h->cell_cursor, h->perm_tmp, h->params, h->perm, h->iperm,
+                                         h->xs, h->xsb, h->ps, h->xref, h->flags);
+        launch_build(h, st);
+        return;
+    }
     k_bin<<<cdiv(N, 256), 256, 0, st>>>(N, xq, h->sid, h->sys, h->cellid, h->cell_count, h->flags);
     if (h->n_scan_blocks == 1) {
         k_scan_single<<<1, 1024, 0, st>>>(h->n_cells, h->cell_count, h->cell_start, h->cell_cursor, h->flags);
@@ -568,13 +631,7 @@ void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st) {
     k_cellsort<<<cdiv((long long)h->n_cells * 32, 256), 256, 0, st>>>(
         h->n_cells, h->cell_start, h->perm_tmp, xq, h->params, h->sid, h->sys, h->perm, h->iperm, h->xs, h->xsb,
         h->ps, h->xref, h->flags);
-    auto build = h->excl_w == 0   ? k_build_cell<0, false>
-                 : h->excl_w == 2 ? k_build_cell<2, false>
-                 : h->max_excl <= 4 ? k_build_cell<4, false>
-                                    : k_build_cell<4, true>;
-    build<<<h->n_cells * h->split_build, kBuildThreads, build_smem(h), st>>>(
-        h->cap, h->tile, h->cell_sys, h->sys, h->cell_start, h->xs, h->perm, h->iperm, h->ex_off, h->ex_idx,
-        h->ex_slot, h->ex_cnt, h->nbr, h->nbr_cnt, h->build_ticket, h->flags, h->split_build);
+    launch_build(h, st);
 }
 
 // The dynamic shared-memory limit of a kernel is process-wide, so it is raised once to

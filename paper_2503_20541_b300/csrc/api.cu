@@ -87,12 +87,13 @@ struct Stage {
     }
 };
 
-// Validity check, conditional rebuild (device-side flag), flag reset.
-void prepare(nb_handle* h, const float4* xq, bool force, cudaStream_t st) {
+// Validity check, conditional rebuild (device-side flag), flag reset.  loaded: the
+// integrator has already done the check (launch_integrate with load_next).
+void prepare(nb_handle* h, const float4* xq, bool force, cudaStream_t st, bool loaded = false) {
     {
         Stage sc(h, NB_STAGE_CHECK, st);
         if (force) request_rebuild(h, st);
-        launch_load(h, xq, st);
+        if (!loaded) launch_load(h, xq, st);
     }
     Stage sc(h, NB_STAGE_REBUILD, st);
     launch_rebuild(h, xq, st);
@@ -126,8 +127,8 @@ nb_status run_pme(nb_handle* h, cudaStream_t st) {
 // becomes a fork/join of the graph) while the latency-bound pair kernel occupies the SMs.
 // Both add their per-atom fixed-point forces into ffix (zeroed by k_load): integer sums,
 // so the result does not depend on which finishes first.
-nb_status eval(nb_handle* h, const float4* xq, int terms, bool force, cudaStream_t st) {
-    prepare(h, xq, force, st);
+nb_status eval(nb_handle* h, const float4* xq, int terms, bool force, cudaStream_t st, bool loaded = false) {
+    prepare(h, xq, force, st, loaded);
     const bool pme = (terms & NB_TERM_PME) && h->has_pme;
     nb_status s = NB_OK;
     if (pme) {
@@ -735,12 +736,14 @@ nb_status md_step(nb_handle* h, float* xq, float* v, const float* dt, int32_t n_
     const size_t stride = (size_t)h->n_sys * NB_NE;
     nb_status s;
     for (int step = 0; step <= n_steps; ++step) {
-        s = eval(h, x4, t, step == 0 && (terms & NB_FORCE_REBUILD), st);
+        // after the first step the integrator has done the check of the new positions
+        s = eval(h, x4, t, step == 0 && (terms & NB_FORCE_REBUILD), st, step > 0);
         if (s != NB_OK) return s;
         float c_pre = step == 0 ? 0.f : 0.5f;
         float c_post = step == n_steps ? 0.f : 0.5f;
         Stage sc(h, NB_STAGE_UPDATE, st);
-        launch_integrate(h, x4, v4, nullptr, dt, c_pre, c_post, step < n_steps, nullptr, nullptr, nullptr, st);
+        launch_integrate(h, x4, v4, nullptr, dt, c_pre, c_post, step < n_steps, nullptr, nullptr, nullptr, st,
+                         StepObs(), step < n_steps);
         if (energies) launch_reduce_energy(h, t, 1, energies + (size_t)step * stride, st);
     }
     return launched();
@@ -772,9 +775,10 @@ nb_status hmc_trajectory(nb_handle* h, const float* x0, float* x_out, const floa
         }
         {
             Stage sc(h, NB_STAGE_UPDATE, st);
-            launch_integrate(h, x, h->vwork, inv_mass, dt, l == 0 ? 0.f : 0.5f, 0.5f, 1, cx, cv, nullptr, st);
+            launch_integrate(h, x, h->vwork, inv_mass, dt, l == 0 ? 0.f : 0.5f, 0.5f, 1, cx, cv, nullptr, st,
+                             StepObs(), true);
         }
-        s = eval(h, x, t, ck != nullptr && (l + 1) % ckpt_every == 0, st);
+        s = eval(h, x, t, ck != nullptr && (l + 1) % ckpt_every == 0, st, true);
         if (s != NB_OK) return s;
     }
     Stage sc(h, NB_STAGE_UPDATE, st);
@@ -825,14 +829,14 @@ nb_status hmc_trajectory_steps(nb_handle* h, const float* x0, float* x_out, cons
             Stage sc(h, NB_STAGE_UPDATE, st);
             ob.step = l;
             launch_integrate(h, x, h->vwork, inv_mass, dt, l == 0 ? 0.f : 0.5f, l == n_leap ? 0.f : 0.5f,
-                             l < n_leap, cx, cv, nullptr, st, l > 0 ? ob : StepObs());
+                             l < n_leap, cx, cv, nullptr, st, l > 0 ? ob : StepObs(), l < n_leap);
             if (l > 0) {
                 ss.sstat = step_stats + (size_t)(l - 1) * sstride;
                 launch_reduce_energy(h, t, 1, h->e1, st, ss);
             }
         }
         if (l == n_leap) break;
-        s = eval(h, x, t, ck != nullptr && (l + 1) % ckpt_every == 0, st);
+        s = eval(h, x, t, ck != nullptr && (l + 1) % ckpt_every == 0, st, true);
         if (s != NB_OK) return s;
     }
     Stage sc(h, NB_STAGE_UPDATE, st);
@@ -878,8 +882,8 @@ static nb_status hmc_backward(nb_handle* h, const float* x0, const float* inv_ma
         if (s != NB_OK) return s;
         for (int q = 0; q < m; ++q) {
             launch_integrate(h, h->xwork, h->vwork, inv_mass, dt, q == 0 ? 0.f : 0.5f, 0.5f, 1, seg_x(q), seg_v(q),
-                             seg_p(q + 1), st);
-            s = eval(h, h->xwork, t, false, st);
+                             seg_p(q + 1), st, StepObs(), true);
+            s = eval(h, h->xwork, t, false, st, true);
             if (s != NB_OK) return s;
         }
         launch_integrate(h, h->xwork, h->vwork, inv_mass, dt, 0.5f, 0.f, 0, seg_x(m), seg_v(m), nullptr, st);

@@ -245,6 +245,44 @@ void launch_pme_convolve(nb_handle* h, cudaStream_t st);
 void launch_pme_gather(nb_handle* h, cudaStream_t st);
 void launch_pme_spread_only(nb_handle* h, float* grid_out, cudaStream_t st);
 void launch_pme_gather_only(nb_handle* h, const float* phi, float* f_out, cudaStream_t st);
+// Validity check of one atom at position p (caller index i, slot k): true when it has
+// moved more than r_skin/2 from its position at the last build (or the position is not
+// finite), which requests a rebuild.  Writes the atom's slot position in the frame of the
+// last build (the wrapped position when it requests the rebuild).
+__device__ __forceinline__ bool load_atom(float4 p, const SysDev& S, float4 r, const float4* __restrict__ xsb,
+                                          float4* __restrict__ xs, int k) {
+    float4 w = p;
+    float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
+    if (S.periodic) {
+        dx = mi_any(dx, S.L[0], S.invL[0]);
+        dy = mi_any(dy, S.L[1], S.invL[1]);
+        dz = mi_any(dz, S.L[2], S.invL[2]);
+    }
+    float d2 = dx * dx + dy * dy + dz * dz;
+    const bool need = !(d2 <= S.disp2);  // NaN (first call, bad input) also requests a rebuild
+    if (S.periodic) {
+        // an atom that needs the rebuild is wrapped (the rebuild re-slots it anyway;
+        // calls that only spread or gather PME charges use it as it is)
+        const float4 b = xsb[k];
+        w = need ? make_float4(wrap1(p.x, S.L[0], S.invL[0]), wrap1(p.y, S.L[1], S.invL[1]),
+                               wrap1(p.z, S.L[2], S.invL[2]), p.w)
+                 : make_float4(b.x + dx, b.y + dy, b.z + dz, p.w);
+    }
+    xs[k] = w;
+    return need;
+}
+
+// The next evaluation's load, done by the integrator right after the drift: the new
+// positions' validity check and slot positions, and the zeroing of the fixed-point forces
+// (each thread zeroes the slot whose force it has just read).  xs == nullptr: none.
+struct LoadNext {
+    const float4* xref = nullptr;
+    const float4* xsb = nullptr;
+    float4* xs = nullptr;
+    long long* ffix = nullptr;
+    unsigned* flags = nullptr;
+};
+
 // Blocks per cell for a cell kernel whose blocks hold `warps` warps and want at least
 // `atoms_per_warp` atoms per warp on average: 1 unless the cells are too few to give
 // every SM several blocks.
@@ -293,7 +331,7 @@ void launch_reduce_energy(nb_handle* h, int terms, int with_kin, double* dst, cu
 void launch_finalize_forces(nb_handle* h, float* f_out, cudaStream_t st);
 void launch_integrate(nb_handle* h, float4* xq, float4* v, const float* w_override, const float* dt,
                       float c_pre, float c_post, int drift, float4* ck_x, float4* ck_v,
-                      float4* ck_p, cudaStream_t st, const StepObs& ob = StepObs());
+                      float4* ck_p, cudaStream_t st, const StepObs& ob = StepObs(), bool load_next = false);
 void launch_hmc_init(nb_handle* h, const float* w, const float* xi, double kT, cudaStream_t st);
 void launch_hmc_finish(nb_handle* h, float4* x_out, const float4* x0, double kT, const double* u,
                        double* stats, cudaStream_t st);

@@ -143,12 +143,13 @@ __device__ __forceinline__ float3 load_force(const long long* __restrict__ ffix,
 }
 
 // v <- v + c_pre dt w F ; record KE ; [store x, v] ; v <- v + c_post dt w F ; [store v] ; x <- x + dt v
+// (ffix is read here and, with the next step's load, zeroed through ln.ffix: not restrict)
 __global__ void k_integrate(int N, float4* __restrict__ xq, float4* __restrict__ v, const float* __restrict__ w_ovr,
                             const float* __restrict__ dt, const int* __restrict__ sid,
-                            const long long* __restrict__ ffix, const int* __restrict__ iperm, float finv,
+                            const long long* ffix, const int* __restrict__ iperm, float finv,
                             float c_pre, float c_post, int drift, float* __restrict__ ke_atom,
                             float4* __restrict__ ck_x, float4* __restrict__ ck_v, float4* __restrict__ ck_p,
-                            const SysDev* __restrict__ sys, StepObs ob) {
+                            const SysDev* __restrict__ sys, StepObs ob, LoadNext ln) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int si = sid[i];
@@ -188,6 +189,15 @@ __global__ void k_integrate(int N, float4* __restrict__ xq, float4* __restrict__
         xq[i] = x;
     }
     v[i] = vi;
+    if (ln.xs) {
+        const int k = iperm[i];
+        ln.ffix[k] = 0;
+        ln.ffix[(size_t)N + k] = 0;
+        ln.ffix[2 * (size_t)N + k] = 0;
+        const bool need = load_atom(x, sys[si], ln.xref[i], ln.xsb, ln.xs, k);
+        const unsigned act = __activemask();  // threads past N returned above
+        if (__any_sync(act, need) && (threadIdx.x & 31) == __ffs(act) - 1) atomicOr(&ln.flags[0], 1u);
+    }
 }
 
 // ------------------------------------------------------------------ HMC
@@ -439,10 +449,18 @@ void launch_finalize_forces(nb_handle* h, float* f_out, cudaStream_t st) {
 
 void launch_integrate(nb_handle* h, float4* xq, float4* v, const float* w_ovr, const float* dt, float c_pre,
                       float c_post, int drift, float4* ck_x, float4* ck_v, float4* ck_p, cudaStream_t st,
-                      const StepObs& ob) {
+                      const StepObs& ob, bool load_next) {
     int N = h->n_atoms;
+    LoadNext ln;
+    if (load_next) {
+        ln.xref = h->xref;
+        ln.xsb = h->xsb;
+        ln.xs = h->xs;
+        ln.ffix = h->ffix;
+        ln.flags = h->flags;
+    }
     k_integrate<<<cdiv(N, 256), 256, 0, st>>>(N, xq, v, w_ovr, dt, h->sid, h->ffix, h->iperm, h->finv, c_pre, c_post,
-                                              drift, h->ke_atom, ck_x, ck_v, ck_p, h->sys, ob);
+                                              drift, h->ke_atom, ck_x, ck_v, ck_p, h->sys, ob, ln);
 }
 
 void launch_hmc_init(nb_handle* h, const float* w, const float* xi, double kT, cudaStream_t st) {

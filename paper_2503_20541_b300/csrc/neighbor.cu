@@ -30,28 +30,7 @@ __global__ void k_load(int N, const float4* __restrict__ xq, const int* __restri
         ffix[i] = 0;
         ffix[(size_t)N + i] = 0;
         ffix[2 * (size_t)N + i] = 0;
-        float4 p = xq[i];
-        const SysDev& S = sys[sid[i]];
-        const int k = iperm[i];
-        float4 w = p;
-        float4 r = xref[i];
-        float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
-        if (S.periodic) {
-            dx = mi_any(dx, S.L[0], S.invL[0]);
-            dy = mi_any(dy, S.L[1], S.invL[1]);
-            dz = mi_any(dz, S.L[2], S.invL[2]);
-        }
-        float d2 = dx * dx + dy * dy + dz * dz;
-        need = !(d2 <= S.disp2);  // NaN (first call, bad input) also requests a rebuild
-        if (S.periodic) {
-            // an atom that needs the rebuild is wrapped (the rebuild re-slots it anyway;
-            // calls that only spread or gather PME charges use it as it is)
-            const float4 b = xsb[k];
-            w = need ? make_float4(wrap1(p.x, S.L[0], S.invL[0]), wrap1(p.y, S.L[1], S.invL[1]),
-                                   wrap1(p.z, S.L[2], S.invL[2]), p.w)
-                     : make_float4(b.x + dx, b.y + dy, b.z + dz, p.w);
-        }
-        xs[k] = w;
+        need = load_atom(xq[i], sys[sid[i]], xref[i], xsb, xs, iperm[i]);
     }
     if (__any_sync(0xffffffffu, need) && (threadIdx.x & 31) == 0) atomicOr(&flags[0], 1u);
 }

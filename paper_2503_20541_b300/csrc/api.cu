@@ -696,15 +696,12 @@ nb_status langevin_step(nb_handle* h, float* xq, float* v, const float* dt, cons
     float4* v4 = F4(v);
     const size_t stride = (size_t)h->n_sys * NB_NE;
     for (int step = 0; step <= n_steps; ++step) {
-        nb_status s = eval(h, x4, t, step == 0 && (terms & NB_FORCE_REBUILD), st);
+        if (step == n_steps && !energies) break;  // the final state's forces serve only its energies
+        nb_status s = eval(h, x4, t, step == 0 && (terms & NB_FORCE_REBUILD), st, step > 0);
         if (s != NB_OK) return s;
         Stage sc(h, NB_STAGE_UPDATE, st);
-        if (step < n_steps) {
-            launch_langevin(h, x4, v4, dt, gamma, kT, xi + (size_t)step * 3 * h->n_atoms, st);
-        } else {
-            if (!energies) break;
-            launch_kinetic(h, v4, st);
-        }
+        if (step < n_steps) launch_langevin(h, x4, v4, dt, gamma, kT, xi + (size_t)step * 3 * h->n_atoms, st, true);
+        else launch_kinetic(h, v4, st);
         if (energies) launch_reduce_energy(h, t, 1, energies + (size_t)step * stride, st);
     }
     return launched();

@@ -346,7 +346,7 @@ void launch_bwd_final(nb_handle* h, const float* w, const float* dt, const float
                       float* wbar, double* g_dt, cudaStream_t st);
 // langevin.cu
 void launch_langevin(nb_handle* h, float4* xq, float4* v, const float* dt, const float* gamma, double kT,
-                     const float* xi, cudaStream_t st);
+                     const float* xi, cudaStream_t st, bool load_next = false);
 void launch_kinetic(nb_handle* h, const float4* v, cudaStream_t st);
 void launch_settle(nb_handle* h, const float4* x_ref, float4* x, float4* v, const float* inv_mass, float dt,
                    cudaStream_t st);

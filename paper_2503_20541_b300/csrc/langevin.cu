@@ -109,14 +109,16 @@ __device__ __forceinline__ float3 force_of(const long long* __restrict__ ffix, i
 
 // One Langevin middle step of a constraint group of NA atoms (module header).
 template <int NA>
-__device__ __forceinline__ void langevin_group(const int (&id)[3], float4* __restrict__ xq, float4* __restrict__ v,
-                                               double h, double c1, double c2, const long long* __restrict__ ffix,
+__device__ __forceinline__ bool langevin_group(const int (&id)[3], float4* __restrict__ xq, float4* __restrict__ v,
+                                               double h, double c1, double c2, const long long* ffix,
                                                const int* __restrict__ iperm, int N, float finv, double kT,
                                                const float* __restrict__ xi, double d_oh, double d_hh,
-                                               float* __restrict__ ke_atom, unsigned* __restrict__ err) {
+                                               float* __restrict__ ke_atom, unsigned* __restrict__ err,
+                                               const SysDev& S, const LoadNext& ln) {
     float4 xo[NA], vo[NA];
     D3 x0[NA], vv[NA], x2[NA], x3[NA];
     double w[NA];
+    bool need = false;
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
         const int i = id[a];
@@ -152,18 +154,28 @@ __device__ __forceinline__ void langevin_group(const int (&id)[3], float4* __res
         const double k0 = w[a] > 0.0 ? 0.5 * dot(v0, v0) / w[a] : 0.0;
         const double k1 = w[a] > 0.0 ? 0.5 * dot(vv[a], vv[a]) / w[a] : 0.0;
         ke_atom[i] = (float)(0.5 * (k0 + k1));
-        xq[i] = make_float4((float)x3[a].x, (float)x3[a].y, (float)x3[a].z, xo[a].w);
+        const float4 xn = make_float4((float)x3[a].x, (float)x3[a].y, (float)x3[a].z, xo[a].w);
+        xq[i] = xn;
         v[i] = make_float4((float)vv[a].x, (float)vv[a].y, (float)vv[a].z, vo[a].w);
+        if (ln.xs) {  // the next evaluation's load (see LoadNext)
+            const int k = iperm[i];
+            ln.ffix[k] = 0;
+            ln.ffix[(size_t)N + k] = 0;
+            ln.ffix[2 * (size_t)N + k] = 0;
+            need = load_atom(xn, S, ln.xref[i], ln.xsb, ln.xs, k) || need;
+        }
     }
+    return need;
 }
 
 // One Langevin middle step of every constraint group.  groups[g] = (O, H1, H2, 3) for a
 // water molecule or (atom, -, -, 1) for a free atom.
 __global__ void k_langevin(int n_groups, const int4* __restrict__ groups, float4* __restrict__ xq,
                            float4* __restrict__ v, const float* __restrict__ dt, const float* __restrict__ gamma,
-                           const int* __restrict__ sid, const long long* __restrict__ ffix,
+                           const int* __restrict__ sid, const SysDev* __restrict__ sys, const long long* ffix,
                            const int* __restrict__ iperm, int N, float finv, double kT, const float* __restrict__ xi,
-                           double d_oh, double d_hh, float* __restrict__ ke_atom, unsigned* __restrict__ err) {
+                           double d_oh, double d_hh, float* __restrict__ ke_atom, unsigned* __restrict__ err,
+                           LoadNext ln) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_groups) return;
     const int4 G = groups[g];
@@ -172,8 +184,14 @@ __global__ void k_langevin(int n_groups, const int4* __restrict__ groups, float4
     const double h = dt[s];
     const double c1 = exp(-(double)gamma[s] * h);
     const double c2 = sqrt(fmax(0.0, 1.0 - c1 * c1));
-    if (G.w == 3) langevin_group<3>(id, xq, v, h, c1, c2, ffix, iperm, N, finv, kT, xi, d_oh, d_hh, ke_atom, err);
-    else langevin_group<1>(id, xq, v, h, c1, c2, ffix, iperm, N, finv, kT, xi, d_oh, d_hh, ke_atom, err);
+    const SysDev& S = sys[s];
+    const bool need = G.w == 3
+                          ? langevin_group<3>(id, xq, v, h, c1, c2, ffix, iperm, N, finv, kT, xi, d_oh, d_hh, ke_atom,
+                                              err, S, ln)
+                          : langevin_group<1>(id, xq, v, h, c1, c2, ffix, iperm, N, finv, kT, xi, d_oh, d_hh, ke_atom,
+                                              err, S, ln);
+    const unsigned act = __activemask();  // threads past n_groups returned above
+    if (__any_sync(act, need) && (threadIdx.x & 31) == __ffs(act) - 1) atomicOr(&ln.flags[0], 1u);
 }
 
 // K = |v|^2 / (2 w) per atom (the last state of a run).
@@ -246,10 +264,18 @@ __global__ void k_rattle(int n_groups, const int4* __restrict__ groups, const fl
 }
 
 void launch_langevin(nb_handle* h, float4* xq, float4* v, const float* dt, const float* gamma, double kT,
-                     const float* xi, cudaStream_t st) {
-    k_langevin<<<cdiv(h->n_groups, 128), 128, 0, st>>>(h->n_groups, h->groups, xq, v, dt, gamma, h->sid, h->ffix,
-                                                       h->iperm, h->n_atoms, h->finv, kT, xi, h->d_oh, h->d_hh,
-                                                       h->ke_atom, h->flags + 1);
+                     const float* xi, cudaStream_t st, bool load_next) {
+    LoadNext ln;
+    if (load_next) {
+        ln.xref = h->xref;
+        ln.xsb = h->xsb;
+        ln.xs = h->xs;
+        ln.ffix = h->ffix;
+        ln.flags = h->flags;
+    }
+    k_langevin<<<cdiv(h->n_groups, 128), 128, 0, st>>>(h->n_groups, h->groups, xq, v, dt, gamma, h->sid, h->sys,
+                                                       h->ffix, h->iperm, h->n_atoms, h->finv, kT, xi, h->d_oh,
+                                                       h->d_hh, h->ke_atom, h->flags + 1, ln);
 }
 
 void launch_kinetic(nb_handle* h, const float4* v, cudaStream_t st) {

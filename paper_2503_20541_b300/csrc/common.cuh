@@ -27,7 +27,7 @@ constexpr float kInvSqrtPi = 0.56418958354775628f;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = 1024 * kScanItems;  // cells per block of the multi-block scan
 constexpr int kRedTile = 1024;                 // atoms per block of the energy reduction
-constexpr int kSmallSortAtoms = 32768;         // handles re-slotted by one block (k_sort_small)
+constexpr int kSmallSortAtoms = 8192;          // handles re-slotted by one block (k_sort_small)
 
 // Per-system constants, resident in device memory (read through the L1 path).
 struct SysDev {

@@ -189,6 +189,30 @@ __global__ void k_scatter(int N, const int* __restrict__ cellid, const int* __re
     perm_tmp[start[c] + atomicAdd(&cursor[c], 1)] = i;
 }
 
+// Atom i at slot `slot`: its permutation entries, reference and slot positions (wrapped
+// into the box) and parameters.
+__device__ __forceinline__ void place_atom(int i, int slot, const float4* __restrict__ xq,
+                                           const float2* __restrict__ params, const int* __restrict__ sid,
+                                           const SysDev* __restrict__ sys, int* __restrict__ perm,
+                                           int* __restrict__ iperm, float4* __restrict__ xs,
+                                           float4* __restrict__ xsb, float2* __restrict__ ps,
+                                           float4* __restrict__ xref) {
+    perm[slot] = i;
+    iperm[i] = slot;
+    float4 p = xq[i];
+    xref[i] = p;
+    const SysDev& S = sys[sid[i]];
+    if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z))) p.x = p.y = p.z = 0.f;
+    if (S.periodic) {
+        p.x = wrap1(p.x, S.L[0], S.invL[0]);
+        p.y = wrap1(p.y, S.L[1], S.invL[1]);
+        p.z = wrap1(p.z, S.L[2], S.invL[2]);
+    }
+    xs[slot] = p;
+    xsb[slot] = p;
+    ps[slot] = params[i];
+}
+
 // Atoms of cell w (one warp) in caller-index order, and their slot data.
 __device__ __forceinline__ void sort_cell(int w, const int* __restrict__ start, const int* __restrict__ perm_tmp,
                                           const float4* __restrict__ xq, const float2* __restrict__ params,
@@ -197,26 +221,12 @@ __device__ __forceinline__ void sort_cell(int w, const int* __restrict__ start, 
                                           float4* __restrict__ xsb, float2* __restrict__ ps,
                                           float4* __restrict__ xref) {
     const int lane = threadIdx.x & 31;
-    int b = start[w], m = start[w + 1] - b;
+    const int b = start[w], m = start[w + 1] - b;
     for (int a = lane; a < m; a += 32) {
-        int i = perm_tmp[b + a];
+        const int i = perm_tmp[b + a];
         int rank = 0;
         for (int t = 0; t < m; ++t) rank += (perm_tmp[b + t] < i);
-        int slot = b + rank;
-        perm[slot] = i;
-        iperm[i] = slot;
-        float4 p = xq[i];
-        xref[i] = p;
-        const SysDev& S = sys[sid[i]];
-        if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z))) p.x = p.y = p.z = 0.f;
-        if (S.periodic) {
-            p.x = wrap1(p.x, S.L[0], S.invL[0]);
-            p.y = wrap1(p.y, S.L[1], S.invL[1]);
-            p.z = wrap1(p.z, S.L[2], S.invL[2]);
-        }
-        xs[slot] = p;
-        xsb[slot] = p;
-        ps[slot] = params[i];
+        place_atom(i, b + rank, xq, params, sid, sys, perm, iperm, xs, xsb, ps, xref);
     }
 }
 
@@ -256,8 +266,15 @@ __global__ void __launch_bounds__(1024) k_sort_small(int N, int n_cells, const f
         perm_tmp[start[c] + atomicAdd(&cursor[c], 1)] = i;
     }
     __syncthreads();
-    for (int w = threadIdx.x >> 5; w < n_cells; w += blockDim.x >> 5)
-        sort_cell(w, start, perm_tmp, xq, params, sid, sys, perm, iperm, xs, xsb, ps, xref);
+    // the in-cell order by caller index, one thread per atom (k_cellsort's result)
+    for (int p = threadIdx.x; p < N; p += blockDim.x) {
+        const int i = perm_tmp[p];
+        const int c = cellid[i];
+        const int b = start[c], m = start[c + 1] - b;
+        int rank = 0;
+        for (int t = 0; t < m; ++t) rank += (perm_tmp[b + t] < i);
+        place_atom(i, b + rank, xq, params, sid, sys, perm, iperm, xs, xsb, ps, xref);
+    }
 }
 
 // Predicated 16-bit store: keeps the list append inside one basic block (no branch

@@ -48,6 +48,13 @@ FLOP_LIST_PAIR = 18   # min-image difference, r^2, compare
 FLOP_LJ_PAIR = 25     # mixing, (sigma/r)^6, energy, force
 FLOP_COUL_PAIR = 45   # erfc, Gaussian, energy, force
 FLOP_EXCL_PAIR = 45   # erf correction of an excluded pair
+FLOP_LJ_VJP_PAIR = 2 * FLOP_LJ_PAIR  # VJP pair math: f and f'/r, J (lam_i - lam_j), parameter gradients
+# per-atom bytes of the integrator kernel (velocity Verlet with the next evaluation's load):
+# reads system id 4, fixed-point force 24, slot 4, v 16, x 16, x_ref 16, build position 16;
+# writes kinetic energy 4, x 16, v 16, zeroed force 24, slot position 16
+BYTES_INTEGRATE_ATOM = 172
+ISSUE_PER_SM_CLK = 4   # warp instructions issued per SM per clock (4 schedulers)
+LEAD_CYCLES = 400000   # device idle (~0.2 ms) queued ahead of each eager timed evaluation
 N_SM = 148
 FP32_LANES = 128
 # our launches per forced-rebuild water evaluation (cuFFT not counted): load, bin, scan,
@@ -250,9 +257,9 @@ def flops_per_launch(pc):
             + FLOP_EXCL_PAIR * pc["excluded"])
 
 
-def traffic_from_profile(path):
-    """DRAM bytes per launch of the pair kernel from the committed ncu summary, if it
-    was taken on the current kernel source (its sha256 prefix is recorded there)."""
+def profile_record(path):
+    """The figures of a committed ncu summary of the pair kernel, if it was taken on the
+    current kernel source (its sha256 prefix is recorded there); else None."""
     try:
         src = open(os.path.join(ROOT, "paper_2503_20541_b300", "csrc", "pair.cu"), "rb").read()
         sha = hashlib.sha256(src).hexdigest()[:16]
@@ -261,11 +268,54 @@ def traffic_from_profile(path):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 rec[k.strip()] = v.strip()
-        if rec.get("pair_cu_sha256_16") != sha:
-            return None
-        return float(rec["dram_bytes_per_launch"])
-    except (OSError, KeyError, ValueError):
+        return rec if rec.get("pair_cu_sha256_16") == sha else None
+    except OSError:
         return None
+
+
+def traffic_from_profile(path):
+    """DRAM bytes per launch of the pair kernel from the committed ncu summary (None when
+    the summary predates the current source)."""
+    rec = profile_record(path)
+    try:
+        return float(rec["dram_bytes_per_launch"]) if rec else None
+    except (KeyError, ValueError):
+        return None
+
+
+def row_rooflines(s, st, hbm_gbs, hbm_src):
+    """HBM rooflines of the PME rows (spread, convolution, gather) of the water box from
+    their per-launch CUDA-event durations, with algorithmic bytes per launch:
+      spread   16 B per atom (position + charge) + 20 B per mesh point (int64 mesh read and
+               cleared, FP32 mesh written); 64 int64 atomic adds per atom into the mesh
+      convolve 20 B per complex mesh point (complex read and written, influence function)
+      gather   16 B per atom + 4 B slot + 24 B of fixed-point force adds, + 4 B per mesh point"""
+    n = s.n
+    k3 = int(np.prod(s.pme_grid))
+    kc = s.pme_grid[0] * s.pme_grid[1] * (s.pme_grid[2] // 2 + 1)
+
+    def per(stage):
+        return st[stage][0] / max(st[stage][1], 1)
+
+    def row(kernel, ms, nbytes, **kw):
+        gbs = nbytes / (ms / 1e3) / 1e9
+        r = {"bound": "hbm", "kernel": kernel, "ms_per_launch": ms, "bytes_per_launch": nbytes, "achieved": gbs,
+             "peak": hbm_gbs, "peak_source": hbm_src, "unit": "GB/s", "frac": gbs / hbm_gbs}
+        r.update(kw)
+        return r
+    t_sp = per("spread")
+    return {
+        "A7_spread": row("k_spread + k_grid_convert", t_sp, 16 * n + 20 * k3,
+                         mesh_atomic_adds_per_s=64 * n / (t_sp / 1e3),
+                         note="the int64 mesh (%.1f MB) stays in L2: the spread is bound by L2 atomic "
+                              "throughput, not by HBM" % (8 * k3 / 1e6)),
+        "A8_convolve": row("k_convolve", per("convolve"), 20 * kc),
+        "A8_fft_ms_per_transform": per("fft"),
+        "A9_gather": row("k_gather", per("gather"), 44 * n + 4 * k3,
+                         note="mesh reads (64 per atom) hit L2; latency-bound"),
+        "workload": "water box 24,000 atoms, PME 64^3 order 4, PME terms alone (list reused), L2 flushed "
+                    "between evaluations; cuFFT reported separately",
+    }
 
 
 def extras(torch, nbcore, wl):
@@ -363,16 +413,102 @@ def extras(torch, nbcore, wl):
         t_b = e2.elapsed_time(e3) / reps
         kf = st_f["pair"][0] / max(st_f["pair"][1], 1)
         kb = st_b["pair"][0] / max(st_b["pair"][1], 1)
-        out["bwd_fwd_ratio"] = {
-            "trajectory": t_b / t_f, "kernel": kb / kf, "fwd_ms": t_f, "bwd_ms": t_b,
-            "pair_kernel_us": 1e3 * kf, "vjp_kernel_us": 1e3 * kb,
-            "workload": "differentiable HMC, LJ fluid 2048 atoms x 10 replicas (batched in one handle), "
-                        "32 leapfrog steps, checkpoints every 8 (recompute in the backward), switch 2.2-2.5"}
+        _, n_list = h.nl_build(x0, force_rebuild=True)
+    sys0 = [copy.copy(x) for x in systems]
+    for x in sys0:
+        x.r_skin = 0.0
+    with nbcore.Handle(sys0) as h0:
+        _, n_cut = h0.nl_build(x0, force_rebuild=True)
+    # algorithmic FP32 work per launch (unordered pairs at the start state; the trajectory's
+    # states differ little): the list test for every list pair plus the pair math
+    fl_f = FLOP_LIST_PAIR * n_list + FLOP_LJ_PAIR * n_cut
+    fl_b = FLOP_LIST_PAIR * n_list + FLOP_LJ_VJP_PAIR * n_cut
+    out["bwd_fwd_ratio"] = {
+        "trajectory": t_b / t_f, "kernel": kb / kf, "fwd_ms": t_f, "bwd_ms": t_b,
+        "pair_kernel_us": 1e3 * kf, "vjp_kernel_us": 1e3 * kb,
+        "pairs_list_at_x0": n_list, "pairs_cutoff_at_x0": n_cut,
+        "pair_kernel_tflops": fl_f / (kf / 1e3) / 1e12, "vjp_kernel_tflops": fl_b / (kb / 1e3) / 1e12,
+        "workload": "differentiable HMC, LJ fluid 2048 atoms x 10 replicas (batched in one handle), "
+                    "32 leapfrog steps, checkpoints every 8 (recompute in the backward), switch 2.2-2.5"}
+    out["integrator_roofline"] = integrator_roofline(torch, nbcore, wl)
+    out["water_skin_1A"] = water_skin(torch, nbcore, wl, 1.0)
     out["lj_sweep"] = lj_sweep(torch, nbcore, wl)
     out["water_elec_sweep"] = water_elec_sweep(torch, nbcore, wl)
     out["hmc_training"] = hmc_training(torch, nbcore, wl)
     out["hmc_lhmc"] = hmc_lhmc(torch, nbcore, wl)
     out["batched"] = batched(torch, nbcore, wl)
+    return out
+
+
+def integrator_roofline(torch, nbcore, wl, n_atoms=2048000, n_steps=20):
+    """Per-launch time of the velocity-Verlet kernel (with the next evaluation's load fused
+    in) inside MD steps of a large LJ fluid, against the measured HBM bandwidth."""
+    s = wl.lj_random(n_atoms, seed=11)
+    xq = torch.from_numpy(nbcore.pack_xq(s.x, s.q)).cuda()
+    v = torch.zeros((s.n, 4), dtype=torch.float32, device="cuda")
+    v[:, 3] = 1.0
+    dt = torch.tensor([0.002], dtype=torch.float32, device="cuda")
+    with nbcore.Handle([s]) as h:
+        h.md_step(xq, v, dt, 3, terms=nbcore.NB_TERM_LJ)
+        torch.cuda.synchronize()
+        h.timing_enable(True)
+        h.timing_read()
+        h.md_step(xq, v, dt, n_steps, terms=nbcore.NB_TERM_LJ)
+        torch.cuda.synchronize()
+        st = h.timing_read()
+        h.timing_enable(False)
+        h.check()
+    ms = st["update"][0] / max(st["update"][1], 1)
+    gbs = BYTES_INTEGRATE_ATOM * s.n / (ms / 1e3) / 1e9
+    peak, src = hbm_peak_gbs()
+    return {"bound": "hbm", "kernel": "k_integrate", "atoms": s.n, "ms_per_launch": ms,
+            "bytes_per_launch": BYTES_INTEGRATE_ATOM * s.n, "achieved": gbs, "peak": peak, "peak_source": src,
+            "unit": "GB/s", "frac": gbs / peak,
+            "workload": "LJ fluid %d atoms (rho* 0.8442, r_c 2.5, r_skin 0.3), %d velocity-Verlet steps, "
+                        "kernel time from CUDA events around each launch" % (s.n, n_steps)}
+
+
+def water_skin(torch, nbcore, wl, r_skin, reps=50):
+    """The headline water box with a thinner Verlet skin (the default is 0.25 r_c =
+    2.25 A): list pairs, and the graph-replayed force evaluation with the list rebuilt
+    every step and with it reused, L2 flushed between timed steps."""
+    from paper_2503_20541_b300.graphs import CapturedStep
+    s = wl.water_box()
+    s.r_skin = r_skin
+    xq = torch.from_numpy(nbcore.pack_xq(s.x, s.q)).cuda()
+    f = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+    e = torch.empty((1, 6), dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    flush_r = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = {"r_skin": r_skin}
+    with nbcore.Handle([s]) as h:
+        _, out["pairs_list"] = h.nl_build(xq, force_rebuild=True)
+        for rebuild in (True, False):
+            g = CapturedStep(lambda: h.nonbonded_forces(xq, f, e, force_rebuild=rebuild))
+            for _ in range(5):
+                g.replay()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(reps)]
+            for a, b in ev:
+                flush.zero_()
+                flush_r.sum()
+                a.record()
+                g.replay()
+                b.record()
+            torch.cuda.synchronize()
+            ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+            out["ms_eval_rebuild" if rebuild else "ms_eval_list_reused"] = ms
+            del g
+        h.check()
+    s0 = wl.water_box()
+    s0.r_skin = 0.0
+    with nbcore.Handle([s0]) as h0:
+        _, n_cut = h0.nl_build(torch.from_numpy(nbcore.pack_xq(s0.x, s0.q)).cuda(), force_rebuild=True)
+    out["pairs_cutoff"] = n_cut
+    out["pairs_per_s_rebuild"] = n_cut / (out["ms_eval_rebuild"] / 1e3)
+    out["pairs_per_s_list_reused"] = n_cut / (out["ms_eval_list_reused"] / 1e3)
+    out["workload"] = ("water box 24,000 atoms as the headline (r_c 9 A, Ewald + PME 64^3) with r_skin %.2f A; "
+                       "graph-replayed evaluation, L2 flushed between steps" % r_skin)
     return out
 
 
@@ -853,19 +989,31 @@ def main():
 
     # per-stage breakdown (CUDA events between stages) from eager steps; the pair kernel's
     # own duration (for its roofline) from steps without PME, which otherwise shares the
-    # SMs with it on the handle's second stream
+    # SMs with it on the handle's second stream.  Before each eager evaluation the device
+    # idles ~0.2 ms (torch.cuda._sleep) while the host queues the evaluation's launches, so
+    # that the stages run back to back and their events time the device, not the host.
+    def lead():
+        flush_l2()
+        torch.cuda._sleep(LEAD_CYCLES)
     h.timing_enable(True)
     h.timing_read()
     for i in range(K):
-        flush_l2()
+        lead()
         step(True)
     torch.cuda.synchronize()
     stages = h.timing_read()
     for i in range(K):
-        flush_l2()
+        lead()
         h.nonbonded_forces(xq, f, e, terms=nbcore.NB_TERM_LJ | nbcore.NB_TERM_COUL, force_rebuild=True)
     torch.cuda.synchronize()
     stages_rs = h.timing_read()
+    # the PME kernels alone (list reused, no pair kernel sharing the SMs): their
+    # per-launch durations for the row rooflines below
+    for i in range(K):
+        lead()
+        h.nonbonded_forces(xq, f, e, terms=nbcore.NB_TERM_PME)
+    torch.cuda.synchronize()
+    stages_pme = h.timing_read()
     h.timing_enable(False)
     h.check()
 
@@ -884,6 +1032,17 @@ def main():
     build_bytes = BUILD_BYTES_PER_ATOM * s.n + BUILD_BYTES_PER_ENTRY * 2 * pc["list"]
     build_gbs = build_bytes / (t_build / 1e3) / 1e9
     hbm_gbs, hbm_src = hbm_peak_gbs()
+    # instruction-issue ceiling of the pair kernel: warp instructions per launch from the
+    # committed ncu summary (when taken on the current source) over 4 per SM per clock
+    prof = profile_record(os.path.join(ROOT, "profiles", "pair_kernel_water24k.txt"))
+    issue = None
+    if prof and "warp instructions" in prof:
+        wi = float(prof["warp instructions"])
+        ach = wi / (t_pair / 1e3)
+        pk = N_SM * ISSUE_PER_SM_CLK * f_sm * 1e6
+        issue = {"warp_instructions_per_launch": wi, "achieved_per_s": ach, "peak_per_s": pk, "frac": ach / pk,
+                 "peak_source": "148 SMs x 4 schedulers x median SM clock %.0f MHz" % f_sm}
+    rows = row_rooflines(s, stages_pme, hbm_gbs, hbm_src)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -899,12 +1058,14 @@ def main():
                                     "during the timed region)" % f_sm,
                      "mufu": {"ops_per_launch": mufu_ops, "peak_ops_per_s": mufu_peak,
                               "us_at_peak": 1e6 * mufu_ops / mufu_peak,
-                              "frac": (mufu_ops / (t_pair / 1e3)) / mufu_peak}},
+                              "frac": (mufu_ops / (t_pair / 1e3)) / mufu_peak},
+                     "issue": issue},
         "roofline_build": {"bound": "hbm", "kernel": "list build chain (k_bin .. k_build_cell)",
                            "achieved": build_gbs, "peak": hbm_gbs, "peak_source": hbm_src, "unit": "GB/s",
                            "frac": build_gbs / hbm_gbs,
                            "bytes_per_build": build_bytes, "ms_per_build": t_build,
                            "note": "issue-bound (FP32 + ALU tests of 2250 candidates per atom), not HBM-bound"},
+        "row_rooflines": rows,
         "stage_ms_per_step_eager": {k: v[0] / max(K, 1) for k, v in stages.items()},
         "ms_per_step_list_reused": ms_reuse,
         "e2e": {"value": e2e_value, "unit": UNIT,

@@ -99,10 +99,11 @@ void prepare(nb_handle* h, const float4* xq, bool force, cudaStream_t st, bool l
     launch_rebuild(h, xq, st);
 }
 
-nb_status run_pme(nb_handle* h, cudaStream_t st) {
+// The mesh half of PME (spread, FFT, convolution, inverse FFT) for positions x.
+nb_status run_pme_mesh(nb_handle* h, const float4* x, cudaStream_t st) {
     {
         Stage sc(h, NB_STAGE_SPREAD, st);
-        launch_pme_spread(h, st);
+        launch_pme_spread(h, x, st);
     }
     {
         Stage sc(h, NB_STAGE_FFT, st);
@@ -112,29 +113,43 @@ nb_status run_pme(nb_handle* h, cudaStream_t st) {
         Stage sc(h, NB_STAGE_CONVOLVE, st);
         launch_pme_convolve(h, st);
     }
-    {
-        Stage sc(h, NB_STAGE_FFT, st);
-        if (launch_pme_fft(h, 1, st)) return NB_ERR_CUDA;
-    }
-    Stage sc(h, NB_STAGE_GATHER, st);
-    launch_pme_gather(h, st);
+    Stage sc(h, NB_STAGE_FFT, st);
+    if (launch_pme_fft(h, 1, st)) return NB_ERR_CUDA;
     return NB_OK;
 }
 
-// Full force evaluation into h->ffix (slot order) and the energy partials.  The pair
-// kernel and the PME chain are independent once the positions are loaded, so PME runs on
-// the handle's second stream (forked and joined with events; under CUDA-graph capture this
-// becomes a fork/join of the graph) while the latency-bound pair kernel occupies the SMs.
-// Both add their per-atom fixed-point forces into ffix (zeroed by k_load): integer sums,
-// so the result does not depend on which finishes first.
+// Full force evaluation into h->ffix (slot order) and the energy partials.  After the
+// load, PME runs on the handle's second stream (forked and joined with events; under
+// CUDA-graph capture this becomes a fork/join of the graph).  Its mesh half reads the
+// caller's positions and charges, not the slot order, so it overlaps the (conditional)
+// list rebuild; the gather waits for the rebuild only because it adds into ffix by slot,
+// and then overlaps the pair kernel.  Both add per-atom fixed-point forces into ffix
+// (zeroed by the load): integer sums, so the result does not depend on which finishes
+// first.
 nb_status eval(nb_handle* h, const float4* xq, int terms, bool force, cudaStream_t st, bool loaded = false) {
-    prepare(h, xq, force, st, loaded);
     const bool pme = (terms & NB_TERM_PME) && h->has_pme;
+    {
+        Stage sc(h, NB_STAGE_CHECK, st);
+        if (force) request_rebuild(h, st);
+        if (!loaded) launch_load(h, xq, st);
+    }
     nb_status s = NB_OK;
     if (pme) {
         cudaEventRecord(h->ev_fork, st);
         cudaStreamWaitEvent(h->aux, h->ev_fork, 0);
-        s = run_pme(h, h->aux);
+        s = run_pme_mesh(h, xq, h->aux);
+    }
+    {
+        Stage sc(h, NB_STAGE_REBUILD, st);
+        launch_rebuild(h, xq, st);
+    }
+    if (pme) {
+        cudaEventRecord(h->ev_built, st);
+        cudaStreamWaitEvent(h->aux, h->ev_built, 0);
+        {
+            Stage sc(h, NB_STAGE_GATHER, h->aux);
+            launch_pme_gather(h, xq, h->iperm, h->aux);
+        }
         cudaEventRecord(h->ev_join, h->aux);
     }
     {
@@ -361,6 +376,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
             D.kl_lo[k] = (float)(kl - (double)D.kl_hi[k]);
         }
         D.stencil = h->cell_div;
+        D.red_tile = red_tile(D.n_atoms);
         if (D.periodic)
             for (int k = 0; k < 3; ++k)
                 if (D.nc[k] < 4 * D.stencil) h->build_gen = 1;  // per-pair images in some cells
@@ -473,7 +489,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
             std::vector<int> rb_sys, rb_off(n_systems + 1, 0);
             for (int s = 0; s < n_systems; ++s) {
                 rb_off[s] = (int)rb_sys.size();
-                for (int b = 0; b < cdiv(sys[s].n_atoms, kRedTile); ++b) rb_sys.push_back(s);
+                for (int b = 0; b < cdiv(sys[s].n_atoms, red_tile(sys[s].n_atoms)); ++b) rb_sys.push_back(s);
             }
             rb_off[n_systems] = (int)rb_sys.size();
             h->n_red_blocks = (int)rb_sys.size();
@@ -513,6 +529,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
         NB_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
         NB_TRY(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        NB_TRY(cudaEventCreateWithFlags(&h->ev_built, cudaEventDisableTiming));
         NB_TRY(cudaMemcpy(h->sys, h->sys_h.data(), sizeof(SysDev) * n_systems, cudaMemcpyHostToDevice));
         NB_TRY(cudaDeviceSynchronize());
     }
@@ -532,6 +549,7 @@ void nb_destroy(nb_handle* h) {
     free_all(h);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_built) cudaEventDestroy(h->ev_built);
     if (h->aux) cudaStreamDestroy(h->aux);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : h->ev_used) cudaEventDestroy(e);

@@ -26,7 +26,14 @@ namespace nb {
 constexpr float kInvSqrtPi = 0.56418958354775628f;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = 1024 * kScanItems;  // cells per block of the multi-block scan
-constexpr int kRedTile = 1024;                 // atoms per block of the energy reduction
+// Atoms per block of the energy reduction of a system of n atoms: about one block per SM
+// for the system alone (FP64 is slow on this part: the work is spread over the SMs), in
+// multiples of 128 from 128 to 4096.  A function of the system alone, so that a system
+// sums in the same order whether it is batched with others or not.
+inline int red_tile(int n) {
+    const int t = (n + 147) / 148;
+    return std::min(4096, std::max(128, (t + 127) / 128 * 128));
+}
 constexpr int kSmallSortAtoms = 8192;          // handles re-slotted by one block (k_sort_small)
 
 // Per-system constants, resident in device memory (read through the L1 path).
@@ -47,7 +54,8 @@ struct SysDev {
     int stencil;          // cell_div: neighbour cells span +-stencil per axis
     long long grid_off;   // real PME mesh offset (elements)
     long long cgrid_off;  // complex half-spectrum offset (elements)
-    int pad1, pad2;
+    int red_tile;         // atoms per block of the energy reduction (red_tile(n_atoms))
+    int pad2;
     double self_coef;     // -ke alpha / sqrt(pi)
     float kl_hi[3], kl_lo[3];  // K_d / L_d as an unevaluated sum hi + lo (double-float)
     float krf, crf;       // reaction field (Eq. RFA): k = (eps_s-1)/((2eps_s+1) r_c^3), c = 3eps_s/((2eps_s+1) r_c)
@@ -131,7 +139,7 @@ struct nb_handle {
     unsigned* flags = nullptr;   // [0] rebuild request, [1] error bits, [2..3] rebuild count (u64)
     unsigned* build_ticket = nullptr;  // [1] blocks of the list build done (reset by the last)
     double* energy = nullptr;    // [n_sys * NB_NE] scratch
-    int n_red_blocks = 0;        // energy reduction: blocks of kRedTile atoms, none straddling systems
+    int n_red_blocks = 0;        // energy reduction: blocks of red_tile atoms, none straddling systems
     int* red_blk_sys = nullptr;  // [n_red_blocks]
     int* red_blk_off = nullptr;  // [n_sys+1] first reduction block of each system
     double* red_part = nullptr;  // [n_red_blocks * 6] per-block FP64 partial sums
@@ -165,7 +173,7 @@ struct nb_handle {
     unsigned long long* counter = nullptr;  // pair export counter
     // second stream for the PME chain, forked from and joined to the caller's stream
     cudaStream_t aux = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_built = nullptr;
     // optional per-stage CUDA-event timing
     int timing = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -239,10 +247,11 @@ void launch_allpairs_lj(nb_handle* h, const float4* xq, cudaStream_t st);
 cudaError_t pme_setup(nb_handle* h);
 int launch_pme(nb_handle* h, cudaStream_t st);  // spread + FFT + convolve + FFT + gather into ffix
 int launch_pme_vjp(nb_handle* h, cudaStream_t st);  // launch_pme, then the reciprocal VJP into gx_s
-void launch_pme_spread(nb_handle* h, cudaStream_t st);
+void launch_pme_spread(nb_handle* h, const float4* x, cudaStream_t st);  // x: caller or slot order
 int launch_pme_fft(nb_handle* h, int inverse, cudaStream_t st);
 void launch_pme_convolve(nb_handle* h, cudaStream_t st);
-void launch_pme_gather(nb_handle* h, cudaStream_t st);
+// adds -q grad into ffix: atom i of x at slot slot_of[i] (x in caller order), or slot i (null)
+void launch_pme_gather(nb_handle* h, const float4* x, const int* slot_of, cudaStream_t st);
 void launch_pme_spread_only(nb_handle* h, float* grid_out, cudaStream_t st);
 void launch_pme_gather_only(nb_handle* h, const float* phi, float* f_out, cudaStream_t st);
 // Validity check of one atom at position p (caller index i, slot k): true when it has

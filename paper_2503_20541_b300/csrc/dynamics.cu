@@ -24,7 +24,7 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
     return t;  // valid in thread 0
 }
 
-// Energy reduction in one launch.  Each block sums kRedTile atoms of one system in FP64
+// Energy reduction in one launch.  Each block sums red_tile atoms of one system in FP64
 // (warp shuffles, one barrier) and stores its five partials; the last block to finish
 // (a ticket counter behind a fence) adds, per system and in block order, the partials
 // and the PME block energies.  Both orders are fixed, so the energies are bitwise
@@ -50,8 +50,8 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_energy(
         const int b = blockIdx.x;
         const int s = blk_sys[b];
         const SysDev& S = sys[s];
-        const int a0 = S.atom_off + (b - blk_off[s]) * kRedTile;
-        const int a1 = min(a0 + kRedTile, S.atom_off + S.n_atoms);
+        const int a0 = S.atom_off + (b - blk_off[s]) * S.red_tile;
+        const int a1 = min(a0 + S.red_tile, S.atom_off + S.n_atoms);
         double v[kC] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         for (int k = a0 + threadIdx.x; k < a1; k += kRedThreads) {
             const float4 e = e_atom[k];

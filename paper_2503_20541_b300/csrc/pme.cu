@@ -9,6 +9,7 @@
 //   gather   : F_i = -q_i sum_k grad_i[M4 M4 M4](k) phi(k), phi = c2r(G Q^) (unnormalised).
 // The order-4 weights use the closed-form cubic pieces of M4 on [0,1], [1,2], [2,3], [3,4].
 // cuFFT performs the 3-D transforms (one batched plan per distinct mesh shape).
+#include <climits>
 #include <math.h>
 
 #include <algorithm>
@@ -51,13 +52,27 @@ __device__ __forceinline__ void frac_coord(float x, int K, float kh, float kl, i
         f -= 1.f;
     }
     fl = (int)f;
-    if (fl >= K) fl -= K;
-    if (fl < 0) fl += K;
+    if ((unsigned)fl >= (unsigned)K) {  // caller coordinates may lie several boxes away
+        fl %= K;
+        if (fl < 0) fl += K;
+    }
 }
 
 __device__ __forceinline__ int wrapk(int k, int K) { return k < 0 ? k + K : k; }
 
-// 16 threads per atom: thread (a, b) owns x offset a and y offset b and the 4 z points.
+// v[j] for a run-time j in 0..3 by selects, so that v stays in registers (an indexed
+// array would be placed in local memory).
+__device__ __forceinline__ float pick4(const float v[4], int j) {
+    float r = v[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) r = j == k ? v[k] : r;
+    return r;
+}
+
+// 16 threads per atom: thread (b, c) owns y offset b and z offset c and visits the 4 x
+// offsets, so that each warp-wide atomic covers 8 runs of 4 consecutive mesh points (z is
+// the contiguous axis).  The positions may be in either order (caller or slot): the mesh
+// sums are order-free.
 __global__ void k_spread(int N, const float4* __restrict__ xs, const int* __restrict__ sid,
                          const SysDev* __restrict__ sys, long long* __restrict__ gfix, float gscale) {
     int gt = blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,15 +91,14 @@ __global__ void k_spread(int N, const float4* __restrict__ xs, const int* __rest
     bspline4(t0, w0, d);
     bspline4(t1, w1, d);
     bspline4(t2, w2, d);
-    int a = sub >> 2, b = sub & 3;
-    int ix = wrapk(f0 - a, K0), iy = wrapk(f1 - b, K1);
-    float wxy = p.w * w0[a] * w1[b];
-    long long* g = gfix + S.grid_off + ((long long)ix * K1 + iy) * K2;
+    const int b = sub >> 2, c = sub & 3;
+    const int iy = wrapk(f1 - b, K1), iz = wrapk(f2 - c, K2);
+    const float wyz = p.w * pick4(w1, b) * pick4(w2, c);
+    long long* g = gfix + S.grid_off + (long long)iy * K2 + iz;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        int iz = wrapk(f2 - c, K2);
-        long long v = __float2ll_rn(wxy * w2[c] * gscale);
-        red_add(g + iz, v);
+    for (int a = 0; a < 4; ++a) {
+        const int ix = wrapk(f0 - a, K0);
+        red_add(g + (long long)ix * K1 * K2, __float2ll_rn(w0[a] * wyz * gscale));
     }
 }
 
@@ -128,7 +142,7 @@ __global__ void k_green(int K0, int K1, int K2, double L0, double L1, double L2,
 }
 
 constexpr int kConvThreads = 256;
-constexpr int kConvItems = 4;
+constexpr int kConvItems = 2;
 constexpr int kConvTile = kConvThreads * kConvItems;
 
 __global__ void __launch_bounds__(kConvThreads) k_convolve(const int* __restrict__ blk_sys,
@@ -148,7 +162,8 @@ __global__ void __launch_bounds__(kConvThreads) k_convolve(const int* __restrict
     for (int it = 0; it < kConvItems; ++it) {
         long long c = base + it * kConvThreads + threadIdx.x;
         if (c < n) {
-            int k2 = (int)(c % K2h);
+            // 32-bit remainder when the mesh allows it (a 64-bit one is a long software sequence)
+            int k2 = n <= INT_MAX ? (int)c % K2h : (int)(c % K2h);
             float g = green[S.cgrid_off + c];
             float2 q = cgrid[S.cgrid_off + c];
             float mult = (k2 == 0 || (2 * k2 == S.K[2])) ? 1.f : 2.f;
@@ -170,12 +185,13 @@ __global__ void __launch_bounds__(kConvThreads) k_convolve(const int* __restrict
     }
 }
 
-// 16 lanes per atom; mode 0 adds -q grad into ffix (slot order, atomically), mode 1 writes f_out
-// (caller order).
+// 16 lanes per atom; mode 0 adds -q grad into ffix (slot order, atomically; atom i of xs
+// goes to slot slot_of[i], or to slot i when slot_of is null), mode 1 writes f_out (caller
+// order; xs in slot order).
 __global__ void k_gather(int N, const float4* __restrict__ xs, const int* __restrict__ sid,
                          const SysDev* __restrict__ sys, const float* __restrict__ phi,
                          long long* __restrict__ ffix, float* __restrict__ f_out, const int* __restrict__ perm,
-                         float scale, int mode, unsigned* flags) {
+                         const int* __restrict__ slot_of, float scale, int mode, unsigned* flags) {
     int gt = blockIdx.x * blockDim.x + threadIdx.x;
     int i = gt >> 4, sub = gt & 15;
     bool valid = i < N;
@@ -201,15 +217,18 @@ __global__ void k_gather(int N, const float4* __restrict__ xs, const int* __rest
         bspline4(t0, w0, d0);
         bspline4(t1, w1, d1);
         bspline4(t2, w2, d2);
-        int a = sub >> 2, b = sub & 3;
-        int ix = wrapk(f0 - a, K0), iy = wrapk(f1 - b, K1);
-        const float* g = phi + S.grid_off + ((long long)ix * K1 + iy) * K2;
+        // lane (b, c) of the atom's 16: y offset b, z offset c, the 4 x offsets in turn (each
+        // warp-wide load covers 8 runs of 4 consecutive mesh points)
+        const int b = sub >> 2, c = sub & 3;
+        const int iy = wrapk(f1 - b, K1), iz = wrapk(f2 - c, K2);
+        const float* g = phi + S.grid_off + (long long)iy * K2 + iz;
+        const float wb = pick4(w1, b), db = pick4(d1, b), wc = pick4(w2, c), dc = pick4(d2, c);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            float v = __ldg(g + wrapk(f2 - c, K2));
-            gxs = fmaf(d0[a] * w1[b] * w2[c], v, gxs);
-            gys = fmaf(w0[a] * d1[b] * w2[c], v, gys);
-            gzs = fmaf(w0[a] * w1[b] * d2[c], v, gzs);
+        for (int a = 0; a < 4; ++a) {
+            float v = __ldg(g + (long long)wrapk(f0 - a, K0) * K1 * K2);
+            gxs = fmaf(d0[a] * wb * wc, v, gxs);
+            gys = fmaf(w0[a] * db * wc, v, gys);
+            gzs = fmaf(w0[a] * wb * dc, v, gzs);
         }
     }
 #pragma unroll
@@ -223,9 +242,10 @@ __global__ void k_gather(int N, const float4* __restrict__ xs, const int* __rest
     if (mode == 0) {
         if (!pme) return;
         // added atomically: the pair kernel adds its part concurrently
-        red_add(ffix + ii, to_fix(fx, scale, flags + 1));
-        red_add(ffix + (size_t)N + ii, to_fix(fy, scale, flags + 1));
-        red_add(ffix + 2 * (size_t)N + ii, to_fix(fz, scale, flags + 1));
+        const int k = slot_of ? slot_of[ii] : ii;
+        red_add(ffix + k, to_fix(fx, scale, flags + 1));
+        red_add(ffix + (size_t)N + k, to_fix(fy, scale, flags + 1));
+        red_add(ffix + 2 * (size_t)N + k, to_fix(fz, scale, flags + 1));
     } else {
         int o = perm[ii];
         f_out[3 * (size_t)o] = fx;
@@ -335,13 +355,13 @@ cudaError_t pme_setup(nb_handle* h) {
     return cudaDeviceSynchronize();
 }
 
-static void spread(nb_handle* h, cudaStream_t st) {
+static void spread(nb_handle* h, const float4* x, cudaStream_t st) {
     int N = h->n_atoms;
-    k_spread<<<cdiv((long long)N * 16, 256), 256, 0, st>>>(N, h->xs, h->sid, h->sys, h->gfix, (float)h->gscale);
+    k_spread<<<cdiv((long long)N * 16, 256), 256, 0, st>>>(N, x, h->sid, h->sys, h->gfix, (float)h->gscale);
     k_grid_convert<<<cdiv(h->grid_total, 256), 256, 0, st>>>(h->grid_total, h->gfix, h->grid, 1.0 / h->gscale);
 }
 
-void launch_pme_spread(nb_handle* h, cudaStream_t st) { spread(h, st); }
+void launch_pme_spread(nb_handle* h, const float4* x, cudaStream_t st) { spread(h, x, st); }
 
 static int fft_on(nb_handle* h, float* mesh, int inverse, cudaStream_t st) {
     for (auto& g : h->fft) {
@@ -367,10 +387,10 @@ void launch_pme_convolve(nb_handle* h, cudaStream_t st) {
                                                           h->green, h->e_pme_blk);
 }
 
-void launch_pme_gather(nb_handle* h, cudaStream_t st) {
+void launch_pme_gather(nb_handle* h, const float4* x, const int* slot_of, cudaStream_t st) {
     int N = h->n_atoms;
-    k_gather<<<cdiv((long long)N * 16, 256), 256, 0, st>>>(N, h->xs, h->sid, h->sys, h->grid, h->ffix, nullptr,
-                                                           h->perm, h->fscale, 0, h->flags);
+    k_gather<<<cdiv((long long)N * 16, 256), 256, 0, st>>>(N, x, h->sid, h->sys, h->grid, h->ffix, nullptr,
+                                                           h->perm, slot_of, h->fscale, 0, h->flags);
 }
 
 // ---------------------------------------------------------------- reciprocal-space VJP
@@ -432,9 +452,10 @@ __global__ void k_spread_vjp(int N, const float4* __restrict__ xs, const float4*
     int a = sub >> 2, b = sub & 3;
     int ix = wrapk(f0 - a, K0), iy = wrapk(f1 - b, K1);
     long long* g = gfix + S.grid_off + ((long long)ix * K1 + iy) * K2;
+    const float wa = pick4(w0, a), da = pick4(d0, a), wb = pick4(w1, b), db = pick4(d1, b);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        const float wv = lu0 * d0[a] * w1[b] * w2[c] + lu1 * w0[a] * d1[b] * w2[c] + lu2 * w0[a] * w1[b] * d2[c];
+        const float wv = lu0 * da * wb * w2[c] + lu1 * wa * db * w2[c] + lu2 * wa * wb * d2[c];
         red_add(g + wrapk(f2 - c, K2), __float2ll_rn(p.w * wv * vs));
     }
 }
@@ -485,16 +506,18 @@ __global__ void k_gather_vjp(int N, const float4* __restrict__ xs, const float4*
         int a = sub >> 2, b = sub & 3;
         int ix = wrapk(f0 - a, K0), iy = wrapk(f1 - b, K1);
         const long long row = S.grid_off + ((long long)ix * K1 + iy) * K2;
+        const float wa = pick4(w0, a), da = pick4(d0, a), ea = pick4(e0, a);
+        const float wb = pick4(w1, b), db = pick4(d1, b), eb = pick4(e1, b);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const long long k = row + wrapk(f2 - c, K2);
             const float pv = __ldg(phi + k), hv = __ldg(chi + k);
-            const float th = w0[a] * w1[b] * w2[c];
-            const float g0 = d0[a] * w1[b] * w2[c], g1 = w0[a] * d1[b] * w2[c], g2 = w0[a] * w1[b] * d2[c];
-            const float h01 = d0[a] * d1[b] * w2[c], h02 = d0[a] * w1[b] * d2[c], h12 = w0[a] * d1[b] * d2[c];
-            const float hx = e0[a] * w1[b] * w2[c] * lu0 + h01 * lu1 + h02 * lu2;
-            const float hy = h01 * lu0 + w0[a] * e1[b] * w2[c] * lu1 + h12 * lu2;
-            const float hz = h02 * lu0 + h12 * lu1 + w0[a] * w1[b] * e2[c] * lu2;
+            const float th = wa * wb * w2[c];
+            const float g0 = da * wb * w2[c], g1 = wa * db * w2[c], g2 = wa * wb * d2[c];
+            const float h01 = da * db * w2[c], h02 = da * wb * d2[c], h12 = wa * db * d2[c];
+            const float hx = ea * wb * w2[c] * lu0 + h01 * lu1 + h02 * lu2;
+            const float hy = h01 * lu0 + wa * eb * w2[c] * lu1 + h12 * lu2;
+            const float hz = h02 * lu0 + h12 * lu1 + wa * wb * e2[c] * lu2;
             A[0] = fmaf(hx, pv, A[0]);
             A[1] = fmaf(hy, pv, A[1]);
             A[2] = fmaf(hz, pv, A[2]);
@@ -547,17 +570,17 @@ int launch_pme_vjp(nb_handle* h, cudaStream_t st) {
 
 int launch_pme(nb_handle* h, cudaStream_t st) {
     if (!h->has_pme) return 0;
-    launch_pme_spread(h, st);
+    launch_pme_spread(h, h->xs, st);
     if (launch_pme_fft(h, 0, st)) return 1;
     launch_pme_convolve(h, st);
     if (launch_pme_fft(h, 1, st)) return 1;
-    launch_pme_gather(h, st);
+    launch_pme_gather(h, h->xs, nullptr, st);
     return 0;
 }
 
 void launch_pme_spread_only(nb_handle* h, float* grid_out, cudaStream_t st) {
     if (!h->has_pme) return;
-    spread(h, st);
+    spread(h, h->xs, st);
     long long off = 0;
     for (int s = 0; s < h->n_sys; ++s) {
         const SysDev& S = h->sys_h[s];
@@ -581,7 +604,7 @@ void launch_pme_gather_only(nb_handle* h, const float* phi, float* f_out, cudaSt
         off += nr;
     }
     k_gather<<<cdiv((long long)N * 16, 256), 256, 0, st>>>(N, h->xs, h->sid, h->sys, h->grid, nullptr, f_out,
-                                                           h->perm, h->fscale, 1, h->flags);
+                                                           h->perm, nullptr, h->fscale, 1, h->flags);
 }
 
 }  // namespace nb

@@ -54,7 +54,7 @@ FLOP_LJ_VJP_PAIR = 2 * FLOP_LJ_PAIR  # VJP pair math: f and f'/r, J (lam_i - lam
 # writes kinetic energy 4, x 16, v 16, zeroed force 24, slot position 16
 BYTES_INTEGRATE_ATOM = 172
 ISSUE_PER_SM_CLK = 4   # warp instructions issued per SM per clock (4 schedulers)
-LEAD_CYCLES = 400000   # device idle (~0.2 ms) queued ahead of each eager timed evaluation
+LEAD_CYCLES = 1200000  # device idle (~0.6 ms) queued ahead of each eager timed evaluation
 N_SM = 148
 FP32_LANES = 128
 # our launches per forced-rebuild water evaluation (cuFFT not counted): load, bin, scan,
@@ -990,7 +990,7 @@ def main():
     # per-stage breakdown (CUDA events between stages) from eager steps; the pair kernel's
     # own duration (for its roofline) from steps without PME, which otherwise shares the
     # SMs with it on the handle's second stream.  Before each eager evaluation the device
-    # idles ~0.2 ms (torch.cuda._sleep) while the host queues the evaluation's launches, so
+    # idles ~0.6 ms (torch.cuda._sleep) while the host queues the evaluation's launches, so
     # that the stages run back to back and their events time the device, not the host.
     def lead():
         flush_l2()

@@ -495,7 +495,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
             h->n_red_blocks = (int)rb_sys.size();
             NB_TRY(dalloc(h, &h->red_blk_sys, rb_sys.size()));
             NB_TRY(dalloc(h, &h->red_blk_off, rb_off.size()));
-            NB_TRY(dalloc(h, &h->red_part, rb_sys.size() * 6));
+            NB_TRY(dalloc(h, &h->red_part, rb_sys.size() * 6 + (size_t)n_systems * 7));
             NB_TRY(dalloc(h, &h->red_ticket, 1));
             NB_TRY(cudaMemset(h->red_ticket, 0, sizeof(unsigned)));
             NB_TRY(cudaMemcpy(h->red_blk_sys, rb_sys.data(), sizeof(int) * rb_sys.size(), cudaMemcpyHostToDevice));

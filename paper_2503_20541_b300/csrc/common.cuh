@@ -142,7 +142,7 @@ struct nb_handle {
     int n_red_blocks = 0;        // energy reduction: blocks of red_tile atoms, none straddling systems
     int* red_blk_sys = nullptr;  // [n_red_blocks]
     int* red_blk_off = nullptr;  // [n_sys+1] first reduction block of each system
-    double* red_part = nullptr;  // [n_red_blocks * 6] per-block FP64 partial sums
+    double* red_part = nullptr;  // [n_red_blocks * 6] per-block FP64 partial sums, then [n_sys * 7] totals
     unsigned* red_ticket = nullptr;  // [1] blocks of the energy reduction done (reset by the last)
     float* ke_atom = nullptr;    // [N] caller
     // PME

@@ -25,14 +25,39 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
 }
 
 // Energy reduction in one launch.  Each block sums red_tile atoms of one system in FP64
-// (warp shuffles, one barrier) and stores its five partials; the last block to finish
-// (a ticket counter behind a fence) adds, per system and in block order, the partials
-// and the PME block energies.  Both orders are fixed, so the energies are bitwise
-// reproducible; the last block resets the counter, so the kernel replays in a graph.
+// and stores its six partials; the last block to finish (a ticket counter behind a fence)
+// adds, per system and in block order, the partials and the PME block energies, one warp
+// per (system, component), and one thread per system writes the results.  Every order is
+// fixed, so the energies are bitwise reproducible; the last block resets the counter, so
+// the kernel replays in a graph.
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Sums of v[0..7] over the warp, transposed: lanes exchange half of their values at each of
+// the first three steps (xor 16, 8, 4), so 9 additions replace 8 separate trees of 5.  Lane
+// l ends with the sum of component (l >> 2) & 7.
+__device__ __forceinline__ double warp_sum8_d(const double v[8]) {
+    const int lane = threadIdx.x & 31;
+    double w[4], u[2];
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const double keep = h4 ? v[4 + j] : v[j], give = h4 ? v[j] : v[4 + j];
+        w[j] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const double keep = h3 ? w[2 + j] : w[j], give = h3 ? w[j] : w[2 + j];
+        u[j] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+    const double keep = h2 ? u[1] : u[0], give = h2 ? u[0] : u[1];
+    double t = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    return t;
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_reduce_energy(
@@ -52,7 +77,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_energy(
         const SysDev& S = sys[s];
         const int a0 = S.atom_off + (b - blk_off[s]) * S.red_tile;
         const int a1 = min(a0 + S.red_tile, S.atom_off + S.n_atoms);
-        double v[kC] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         for (int k = a0 + threadIdx.x; k < a1; k += kRedThreads) {
             const float4 e = e_atom[k];
             const float q = xs[k].w;
@@ -65,63 +90,67 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_energy(
             // caller-order entries over that range
             if (ss.jump) v[5] += ss.jump[k];
         }
-#pragma unroll
-        for (int c = 0; c < kC; ++c) v[c] = warp_sum_d(v[c]);
-        if (lane == 0)
-#pragma unroll
-            for (int c = 0; c < kC; ++c) sm[w][c] = v[c];
+        const double t = warp_sum8_d(v);
+        const int c = lane >> 2;
+        if ((lane & 3) == 0 && c < kC) sm[w][c] = t;
         __syncthreads();
-        if (w == 0) {
+        if (threadIdx.x < kC) {
+            double acc = 0.0;
 #pragma unroll
-            for (int c = 0; c < kC; ++c) {
-                double t = lane < kW ? sm[lane][c] : 0.0;
-                t = warp_sum_d(t);
-                if (lane == 0) part[(size_t)b * kC + c] = t;
-            }
-            if (lane == 0) {
-                __threadfence();
-                last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-            }
+            for (int k = 0; k < kW; ++k) acc += sm[k][threadIdx.x];
+            part[(size_t)b * kC + threadIdx.x] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            last = atomicAdd(ticket, 1u) == gridDim.x - 1;
         }
         __syncthreads();
     }
     if (!last) return;
     __threadfence();
-    for (int s = w; s < n_sys; s += kW) {
+    // per (system, component): component kC is the reciprocal energy from the PME blocks;
+    // the totals go to part[] past the block partials
+    double* tot = part + (size_t)gridDim.x * kC;
+    for (int sc = w; sc < n_sys * (kC + 1); sc += kW) {
+        const int s = sc / (kC + 1), c = sc % (kC + 1);
+        double acc = 0.0;
+        if (c < kC) {
+            for (int b = blk_off[s] + lane; b < blk_off[s + 1]; b += 32) acc += __ldcg(part + (size_t)b * kC + c);
+        } else if ((terms & NB_TERM_PME) && sys[s].pme && pme_blk_off) {
+            for (int b = pme_blk_off[s] + lane; b < pme_blk_off[s + 1]; b += 32) acc += e_pme_blk[b];
+        }
+        acc = warp_sum_d(acc);
+        if (lane == 0) tot[sc] = acc;
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < n_sys; s += kRedThreads) {
         const SysDev& S = sys[s];
-        double acc[kC + 1] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        for (int b = blk_off[s] + lane; b < blk_off[s + 1]; b += 32)
-            for (int c = 0; c < kC; ++c) acc[c] += __ldcg(part + (size_t)b * kC + c);
-        if ((terms & NB_TERM_PME) && S.pme && pme_blk_off)
-            for (int b = pme_blk_off[s] + lane; b < pme_blk_off[s + 1]; b += 32) acc[kC] += e_pme_blk[b];
+        const double* acc = tot + (size_t)s * (kC + 1);
+        const bool coul = (terms & NB_TERM_COUL) != 0;
+        double e[NB_NE];
+        e[NB_E_LJ] = (terms & NB_TERM_LJ) ? acc[0] : 0.0;
+        e[NB_E_DIR] = coul ? acc[1] : 0.0;
+        e[NB_E_EXCL] = coul ? acc[2] : 0.0;
+        e[NB_E_SELF] = coul ? S.self_coef * acc[3] : 0.0;
+        e[NB_E_REC] = acc[kC];
+        e[NB_E_KIN] = with_kin ? acc[4] : 0.0;
+        double* o = dst + (size_t)s * NB_NE;
 #pragma unroll
-        for (int c = 0; c <= kC; ++c) acc[c] = warp_sum_d(acc[c]);
-        if (lane == 0) {
-            const bool coul = (terms & NB_TERM_COUL) != 0;
-            double e[NB_NE];
-            e[NB_E_LJ] = (terms & NB_TERM_LJ) ? acc[0] : 0.0;
-            e[NB_E_DIR] = coul ? acc[1] : 0.0;
-            e[NB_E_EXCL] = coul ? acc[2] : 0.0;
-            e[NB_E_SELF] = coul ? S.self_coef * acc[3] : 0.0;
-            e[NB_E_REC] = acc[kC];
-            e[NB_E_KIN] = with_kin ? acc[4] : 0.0;
-            double* o = dst + (size_t)s * NB_NE;
-#pragma unroll
-            for (int c = 0; c < NB_NE; ++c) o[c] = e[c];
-            if (ss.sstat) {
-                double H0 = 0.0, H1 = 0.0;
-                for (int c = 0; c < NB_NE; ++c) {
-                    H0 += ss.e_ref[(size_t)s * NB_NE + c];
-                    H1 += e[c];
-                }
-                const double dH = H1 - H0;
-                double a = (dH <= 0.0) ? 1.0 : exp(-dH / ss.kT);
-                if (!(dH == dH)) a = 0.0;  // NaN energy: never accepted
-                double* q = ss.sstat + (size_t)s * 3;
-                q[0] = dH;
-                q[1] = a;
-                q[2] = acc[5];
+        for (int c = 0; c < NB_NE; ++c) o[c] = e[c];
+        if (ss.sstat) {
+            double H0 = 0.0, H1 = 0.0;
+            for (int c = 0; c < NB_NE; ++c) {
+                H0 += ss.e_ref[(size_t)s * NB_NE + c];
+                H1 += e[c];
             }
+            const double dH = H1 - H0;
+            double a = (dH <= 0.0) ? 1.0 : exp(-dH / ss.kT);
+            if (!(dH == dH)) a = 0.0;  // NaN energy: never accepted
+            double* q = ss.sstat + (size_t)s * 3;
+            q[0] = dH;
+            q[1] = a;
+            q[2] = acc[5];
         }
     }
     if (threadIdx.x == 0) *ticket = 0u;

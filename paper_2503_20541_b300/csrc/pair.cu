@@ -725,12 +725,22 @@ static void dispatch(nb_handle* h, int terms, cudaStream_t st, bool vjp) {
     bool lj = (terms & NB_TERM_LJ) != 0;
     bool coul = (terms & NB_TERM_COUL) != 0 && h->any_coul;  // uncharged systems: LJ-only kernels
     const bool rf = h->coul_kind == kCoulRF;
+    if (!lj && !coul) {
+        // no real-space term (PME alone): no list walk, only the per-atom outputs the
+        // kernels would have written as zeros (forces stay as the load zeroed them)
+        const size_t N = (size_t)h->n_atoms;
+        cudaMemsetAsync(h->e_atom, 0, sizeof(float4) * N, st);
+        if (vjp) {
+            cudaMemsetAsync(h->gx_s, 0, sizeof(float4) * N, st);
+            cudaMemsetAsync(h->gp_s, 0, sizeof(float2) * N, st);
+        }
+        return;
+    }
     if (lj && coul && rf) pair_launch<true, kCoulRF>(h, st, vjp);
     else if (lj && coul) pair_launch<true, kCoulEwald>(h, st, vjp);
     else if (lj) pair_launch<true, kCoulNone>(h, st, vjp);
     else if (coul && rf) pair_launch<false, kCoulRF>(h, st, vjp);
-    else if (coul) pair_launch<false, kCoulEwald>(h, st, vjp);
-    else pair_launch<false, kCoulNone>(h, st, vjp);
+    else pair_launch<false, kCoulEwald>(h, st, vjp);
 }
 
 void launch_pair(nb_handle* h, int terms, cudaStream_t st) { dispatch(h, terms, st, false); }
@@ -771,7 +781,6 @@ cudaError_t pair_setup(nb_handle* h) {
     if (e == cudaSuccess) e = set_smem<true, kCoulNone>();
     if (e == cudaSuccess) e = set_smem<false, kCoulEwald>();
     if (e == cudaSuccess) e = set_smem<false, kCoulRF>();
-    if (e == cudaSuccess) e = set_smem<false, kCoulNone>();
     return e;
 }
 

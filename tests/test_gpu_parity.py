@@ -194,6 +194,40 @@ def test_pme_spread_gather_and_energy():
     assert abs(ep[4] - Eo) <= E_TOL * abs(Eo)
 
 
+@pytest.mark.parametrize("shift", [-2, 4])
+def test_caller_coordinates_whole_boxes_away(shift):
+    """The list build and the mesh half of PME read the caller's positions, which need
+    not lie in the box.  In a box of 31 A with positions on a 2^-16 A grid, moving each
+    coordinate of each atom by 0 or `shift` box lengths is exact in FP32, so the wrapped
+    positions are the unshifted ones: the real-space energies are bitwise those of the
+    unshifted evaluation, and the PME forces and energy (evaluated from the shifted
+    coordinates themselves) agree with it and with the oracle."""
+    s = wl.water_box(n_side=10, L=31.0, seed=6, pme_grid=32)
+    s.x = (np.mod(np.round(s.x.astype(np.float64) * 65536.0) / 65536.0, s.box)).astype(np.float32)
+    rng = np.random.default_rng(3)
+    k = rng.integers(0, 2, size=(s.n, 3)) * shift
+    x_sh = s.x.astype(np.float64) + k * s.box
+    x32 = x_sh.astype(np.float32)
+    assert np.array_equal(x32.astype(np.float64), x_sh)  # the shift is exact in FP32
+
+    def run(x):
+        f = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+        e = torch.empty((1, 6), dtype=torch.float64, device="cuda")
+        with nbcore.Handle([s]) as h:
+            h.nonbonded_forces(torch.from_numpy(nbcore.pack_xq(x, s.q)).cuda(), f, e, force_rebuild=True)
+            h.check()
+        return f.cpu().numpy().astype(np.float64), e.cpu().numpy()[0]
+    f0, e0 = run(s.x)
+    f1, e1 = run(x32)
+    assert np.array_equal(e1[:4], e0[:4])  # LJ, direct, exclusion, self
+    assert abs(e1[4] - e0[4]) <= E_TOL * abs(e0[4])
+    assert rel_rms(f1, f0) <= F_TOL
+    eo, fo = oracle_real_space(s)
+    Ep, Fp = oracle_pme(s)
+    assert rel_rms(f1, fo + Fp) <= F_TOL
+    assert abs(e1[4] - Ep) <= E_TOL * abs(Ep)
+
+
 def test_water_config2_full_size_sampled():
     """The full 8000-molecule box in the benchmark's configuration; forces checked
     on a sample of 400 atoms (oracle rows), energies from all rows."""

@@ -193,8 +193,10 @@ def train_esjd(h, x0, types, m_total, iters=200, n_leap=32, kT=1.0, ckpt_every=8
     logits.requires_grad_(True)
     opt = torch.optim.Adam([log_mu, logits], lr=lr)
     gen = torch.Generator(device=dev).manual_seed(seed)
+    counts = torch.bincount(types, minlength=n_types).to(torch.float64)
+    keys = ("loss", "mu", "alpha", "accepted")
     x = x0.clone()
-    hist = []
+    hist, rows = [], []
     for it in range(iters):
         eps = torch.randn(R, dtype=torch.float64, device=dev, generator=gen)
         xi = torch.randn((R * n, 3), dtype=torch.float32, device=dev, generator=gen)
@@ -207,15 +209,41 @@ def train_esjd(h, x0, types, m_total, iters=200, n_leap=32, kT=1.0, ckpt_every=8
         loss.backward()
         opt.step()
         x = x_new
-        rec = {"it": it, "loss": -float(loss.detach()), "mu": float(torch.exp(log_mu.detach())),
-               "alpha": float(alpha.detach().mean()), "accepted": float(acc.mean())}
         with torch.no_grad():
-            s = torch.exp(logits)
-            counts = torch.bincount(types, minlength=n_types).to(s.dtype)
-            rec["mass_per_type"] = (m_total * s / torch.sum(counts * s)).tolist()
-        hist.append(rec)
-        if callback is not None:
-            callback(rec)
+            row = torch.stack([-loss, torch.exp(log_mu), alpha.mean(), acc.to(torch.float64).mean()])
+            row = torch.cat([row, _type_masses(logits, counts, m_total)])
+        _record(it, row, keys, {}, hist, rows, callback)
+    return _finish(hist, rows, keys, [{} for _ in rows])
+
+
+def _type_masses(logits, counts, m_total):
+    s = torch.exp(logits)
+    return m_total * s / torch.sum(counts * s)
+
+
+def _record(it, row, keys, extra, hist, rows, callback):
+    """One iteration's history: kept on the device (read once by ``_finish``) unless a
+    callback wants it now, so that the host does not wait for every iteration."""
+    if callback is None:
+        rows.append(row)
+        return
+    rec = _as_record(it, row.cpu().tolist(), keys, extra)
+    hist.append(rec)
+    callback(rec)
+
+
+def _as_record(it, vals, keys, extra):
+    rec = {"it": it}
+    rec.update(zip(keys, vals[:len(keys)]))
+    rec.update(extra)
+    rec["mass_per_type"] = vals[len(keys):]
+    return rec
+
+
+def _finish(hist, rows, keys, extras):
+    if rows:
+        vals = torch.stack(rows).cpu().tolist()
+        hist = [_as_record(it, v, keys, e) for it, (v, e) in enumerate(zip(vals, extras))]
     return hist
 
 
@@ -241,8 +269,10 @@ def train_lhmc(h, x0, types, m_total, iters=200, kT=1.0, ckpt_every=8, lr=0.05, 
     logits.requires_grad_(True)
     opt = torch.optim.Adam([log_mu, log_mu_L, logits], lr=lr)
     gen = torch.Generator(device=dev).manual_seed(seed)
+    counts = torch.bincount(types, minlength=n_types).to(torch.float64)
+    keys = ("loss", "mu", "mu_L", "alpha", "accepted")
     x = x0.clone()
-    hist = []
+    hist, rows, extras = [], [], []
     for it in range(iters):
         mu_L = torch.exp(log_mu_L)
         L_q = length_cutoff(float(mu_L.detach()), sigma_L)
@@ -259,14 +289,9 @@ def train_lhmc(h, x0, types, m_total, iters=200, kT=1.0, ckpt_every=8, lr=0.05, 
         loss.backward()
         opt.step()
         x = x_new
-        rec = {"it": it, "loss": -float(loss.detach()), "mu": float(torch.exp(log_mu.detach())),
-               "mu_L": float(mu_L.detach()), "L_q": L_q, "alpha": float(stats[:, 1].mean()),
-               "accepted": float(stats[:, 3].mean())}
         with torch.no_grad():
-            s = torch.exp(logits)
-            counts = torch.bincount(types, minlength=n_types).to(s.dtype)
-            rec["mass_per_type"] = (m_total * s / torch.sum(counts * s)).tolist()
-        hist.append(rec)
-        if callback is not None:
-            callback(rec)
-    return hist
+            row = torch.stack([-loss, torch.exp(log_mu), mu_L, stats[:, 1].mean(), stats[:, 3].mean()])
+            row = torch.cat([row, _type_masses(logits, counts, m_total)])
+        extras.append({"L_q": L_q})
+        _record(it, row, keys, {"L_q": L_q}, hist, rows, callback)
+    return _finish(hist, rows, keys, extras)

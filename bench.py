@@ -430,6 +430,7 @@ def extras(torch, nbcore, wl):
         "pair_kernel_tflops": fl_f / (kf / 1e3) / 1e12, "vjp_kernel_tflops": fl_b / (kb / 1e3) / 1e12,
         "workload": "differentiable HMC, LJ fluid 2048 atoms x 10 replicas (batched in one handle), "
                     "32 leapfrog steps, checkpoints every 8 (recompute in the backward), switch 2.2-2.5"}
+    out["hmc_batched_vs_single"] = hmc_batched_vs_single(torch, nbcore, wl)
     out["integrator_roofline"] = integrator_roofline(torch, nbcore, wl)
     out["water_skin_1A"] = water_skin(torch, nbcore, wl, 1.0)
     out["lj_sweep"] = lj_sweep(torch, nbcore, wl)
@@ -437,6 +438,95 @@ def extras(torch, nbcore, wl):
     out["hmc_training"] = hmc_training(torch, nbcore, wl)
     out["hmc_lhmc"] = hmc_lhmc(torch, nbcore, wl)
     out["batched"] = batched(torch, nbcore, wl)
+    return out
+
+
+def hmc_batched_vs_single(torch, nbcore, wl, R=10, L=32, K=8, reps=20):
+    """One differentiable HMC step (proposal + adjoint) of R LJ replicas (2048 atoms,
+    switch 2.2-2.5, dt 0.005): all replicas in one handle, the step captured as one CUDA
+    graph, against the plain single-system path (one handle per replica, eager calls),
+    with the dH of every replica compared between the two."""
+    from paper_2503_20541_b300.graphs import CapturedStep
+    systems = []
+    for r in range(R):
+        sr = wl.lj_random(2048, seed=100 + r, n_types=2)
+        sr.r_switch = 2.2
+        systems.append(sr)
+    n = systems[0].n
+    N = n * R
+    x0 = torch.cat([torch.from_numpy(nbcore.pack_xq(x.x, x.q)) for x in systems]).cuda()
+    x1 = torch.empty_like(x0)
+    w = torch.ones(N, dtype=torch.float32, device="cuda")
+    dts = torch.full((R,), 0.005, dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    xi = torch.randn((N, 3), device="cuda", generator=gen)
+    u = torch.rand(R, dtype=torch.float64, device="cuda", generator=gen)
+    stats = torch.empty((R, 4), dtype=torch.float64, device="cuda")
+    ga = torch.ones(R, dtype=torch.float64, device="cuda")
+    gj = torch.ones(R, dtype=torch.float64, device="cuda")
+    gdt = torch.zeros(R, dtype=torch.float64, device="cuda")
+    gw = torch.zeros(N, dtype=torch.float32, device="cuda")
+    ck = torch.empty(nbcore.ckpt_size(N, L, K), dtype=torch.float32, device="cuda")
+    lj = nbcore.NB_TERM_LJ
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    out = {}
+    with nbcore.Handle(systems) as h:
+        def step_b():
+            gdt.zero_()
+            gw.zero_()
+            h.hmc_trajectory(x0, x1, w, dts, L, 1.0, xi, u, stats, ck, K, terms=lj)
+            h.hmc_trajectory_backward(x0, w, dts, L, 1.0, xi, ck, K, stats, ga, gj, gdt, gw, terms=lj)
+        out["batched_eager_ms"] = timed(step_b)
+        g = CapturedStep(step_b)
+        out["batched_graph_ms"] = timed(g.replay)
+        h.check()
+        dh_b = stats[:, 0].clone()
+        gdt_b = gdt.clone()
+        del g
+    handles = [nbcore.Handle([x]) for x in systems]
+    sl = [slice(r * n, (r + 1) * n) for r in range(R)]
+    st_r = [torch.empty((1, 4), dtype=torch.float64, device="cuda") for _ in range(R)]
+    ck_r = [torch.empty(nbcore.ckpt_size(n, L, K), dtype=torch.float32, device="cuda") for _ in range(R)]
+    gdt_r = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in range(R)]
+    x1_r = [torch.empty((n, 4), dtype=torch.float32, device="cuda") for _ in range(R)]
+    xs_r = [x0[q].contiguous() for q in sl]
+    xi_r = [xi[q].contiguous() for q in sl]
+    w_r = [w[q].contiguous() for q in sl]
+    gw_r = [torch.zeros(n, dtype=torch.float32, device="cuda") for _ in range(R)]
+
+    def step_s():
+        for r, hr in enumerate(handles):
+            gdt_r[r].zero_()
+            gw_r[r].zero_()
+            hr.hmc_trajectory(xs_r[r], x1_r[r], w_r[r], dts[r:r + 1], L, 1.0, xi_r[r], u[r:r + 1], st_r[r], ck_r[r], K,
+                              terms=lj)
+            hr.hmc_trajectory_backward(xs_r[r], w_r[r], dts[r:r + 1], L, 1.0, xi_r[r], ck_r[r], K, st_r[r],
+                                       ga[r:r + 1], gj[r:r + 1], gdt_r[r], gw_r[r], terms=lj)
+    out["single_looped_eager_ms"] = timed(step_s)
+    for hr in handles:
+        hr.check()
+    dh_s = torch.cat([x[:, 0] for x in st_r])
+    scale = float(torch.max(torch.abs(dh_s)))
+    out["speedup_batched_graph_vs_single"] = out["single_looped_eager_ms"] / out["batched_graph_ms"]
+    out["dH_max_abs_diff"] = float(torch.max(torch.abs(dh_b - dh_s)))
+    out["dH_max_abs"] = scale
+    out["g_dt_max_rel_diff"] = float(torch.max(torch.abs(gdt_b - torch.cat(gdt_r)) / torch.abs(torch.cat(gdt_r))))
+    for hr in handles:
+        hr.close()
+    out["workload"] = ("differentiable HMC step (proposal + adjoint, L %d, checkpoints every %d) of %d LJ replicas of "
+                       "2048 atoms (switch 2.2-2.5, dt 0.005): one handle, captured as one CUDA graph, vs one handle "
+                       "per replica launched eagerly; dH per replica compared" % (L, K, R))
     return out
 
 

@@ -217,6 +217,29 @@ __device__ __forceinline__ long long to_fix(float v, float scale, unsigned* err)
     return __float2ll_rn(s);
 }
 
+// Programmatic dependent launch: the kernels of an evaluation's main chain are launched
+// with cudaLaunchAttributeProgrammaticStreamSerialization (launch_pdl), so that a kernel's
+// launch overlaps the end of the previous kernel in the stream.  Each of them first waits
+// here until that kernel has completed and its writes are visible (without the attribute
+// the wait returns at once).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 __device__ __forceinline__ void red_add(long long* p, long long v) {
     atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
 }

@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_energy(
     int with_kin, double* __restrict__ part, const double* __restrict__ e_pme_blk,
     const int* __restrict__ pme_blk_off, int terms, unsigned* __restrict__ ticket, double* __restrict__ dst,
     StepStat ss) {
+    pdl_wait();
     constexpr int kW = kRedThreads / 32;
     constexpr int kC = 6;  // LJ, direct, exclusion, q^2, kinetic, jump
     __shared__ double sm[kW][kC];
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_energy(
 
 __global__ void k_finalize(int N, const long long* __restrict__ ffix, const int* __restrict__ iperm, float finv,
                            float* __restrict__ f_out) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     int k = iperm[i];
@@ -179,6 +181,7 @@ __global__ void k_integrate(int N, float4* __restrict__ xq, float4* __restrict__
                             float c_pre, float c_post, int drift, float* __restrict__ ke_atom,
                             float4* __restrict__ ck_x, float4* __restrict__ ck_v, float4* __restrict__ ck_p,
                             const SysDev* __restrict__ sys, StepObs ob, LoadNext ln) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int si = sid[i];
@@ -233,6 +236,7 @@ __global__ void k_integrate(int N, float4* __restrict__ xq, float4* __restrict__
 
 __global__ void k_hmc_init(int N, const float* __restrict__ w, const float* __restrict__ xi, double kT,
                            float4* __restrict__ v, float* __restrict__ ke_atom) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     float wi = w[i];
@@ -345,6 +349,7 @@ __device__ __forceinline__ float inject_dhbar(const Inject& inj, int s, double k
 __global__ void k_bwd_lambda(int N, const float4* __restrict__ vbar, const float4* __restrict__ v_state,
                              const float* __restrict__ w, const float* __restrict__ dt, const int* __restrict__ sid,
                              const int* __restrict__ iperm, Inject inj, double kT, float4* __restrict__ lam) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int s = sid[i];
@@ -372,6 +377,7 @@ __global__ void k_bwd_adjoint(int N, const float4* __restrict__ gx_s, const long
                               const float4* __restrict__ x0, const float4* __restrict__ p_prev,
                               float4* __restrict__ xbar, float4* __restrict__ vbar, float* __restrict__ wbar,
                               double* __restrict__ hbar) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int s = sid[i];
@@ -465,7 +471,7 @@ __global__ void __launch_bounds__(kRedThreads) k_bwd_reduce_h(const SysDev* __re
 // ------------------------------------------------------------------ launchers
 
 void launch_reduce_energy(nb_handle* h, int terms, int with_kin, double* dst, cudaStream_t st, const StepStat& ss) {
-    k_reduce_energy<<<h->n_red_blocks, kRedThreads, 0, st>>>(h->n_sys, h->red_blk_sys, h->red_blk_off, h->sys,
+    launch_pdl(k_reduce_energy, h->n_red_blocks, kRedThreads, 0, st, h->n_sys, h->red_blk_sys, h->red_blk_off, h->sys,
                                                             h->e_atom, h->xs, h->ke_atom, with_kin, h->red_part,
                                                             h->e_pme_blk, h->conv_blk_off, terms, h->red_ticket, dst,
                                                             ss);
@@ -473,7 +479,7 @@ void launch_reduce_energy(nb_handle* h, int terms, int with_kin, double* dst, cu
 
 void launch_finalize_forces(nb_handle* h, float* f_out, cudaStream_t st) {
     int N = h->n_atoms;
-    k_finalize<<<cdiv(N, 256), 256, 0, st>>>(N, h->ffix, h->iperm, h->finv, f_out);
+    launch_pdl(k_finalize, cdiv(N, 256), 256, 0, st, N, h->ffix, h->iperm, h->finv, f_out);
 }
 
 void launch_integrate(nb_handle* h, float4* xq, float4* v, const float* w_ovr, const float* dt, float c_pre,
@@ -488,13 +494,13 @@ void launch_integrate(nb_handle* h, float4* xq, float4* v, const float* w_ovr, c
         ln.ffix = h->ffix;
         ln.flags = h->flags;
     }
-    k_integrate<<<cdiv(N, 256), 256, 0, st>>>(N, xq, v, w_ovr, dt, h->sid, h->ffix, h->iperm, h->finv, c_pre, c_post,
+    launch_pdl(k_integrate, cdiv(N, 256), 256, 0, st, N, xq, v, w_ovr, dt, h->sid, h->ffix, h->iperm, h->finv, c_pre, c_post,
                                               drift, h->ke_atom, ck_x, ck_v, ck_p, h->sys, ob, ln);
 }
 
 void launch_hmc_init(nb_handle* h, const float* w, const float* xi, double kT, cudaStream_t st) {
     int N = h->n_atoms;
-    k_hmc_init<<<cdiv(N, 256), 256, 0, st>>>(N, w, xi, kT, h->vwork, h->ke_atom);
+    launch_pdl(k_hmc_init, cdiv(N, 256), 256, 0, st, N, w, xi, kT, h->vwork, h->ke_atom);
 }
 
 void launch_hmc_finish(nb_handle* h, float4* x_out, const float4* x0, double kT, const double* u, double* stats,
@@ -515,14 +521,14 @@ void launch_hmc_pick(nb_handle* h, float4* x_out, const float4* x0, const int* l
 void launch_bwd_lambda(nb_handle* h, const float* w, const float* dt, const float4* v_state, const Inject& inj,
                        double kT, cudaStream_t st) {
     int N = h->n_atoms;
-    k_bwd_lambda<<<cdiv(N, 256), 256, 0, st>>>(N, h->vbar, v_state, w, dt, h->sid, h->iperm, inj, kT, h->lam);
+    launch_pdl(k_bwd_lambda, cdiv(N, 256), 256, 0, st, N, h->vbar, v_state, w, dt, h->sid, h->iperm, inj, kT, h->lam);
 }
 
 void launch_bwd_adjoint(nb_handle* h, const float* w, const float* dt, const float4* x_state, const float4* v_state,
                         const float4* x0, const Inject& inj, double kT, const float4* p_prev, float* wbar,
                         cudaStream_t st) {
     int N = h->n_atoms;
-    k_bwd_adjoint<<<cdiv(N, 256), 256, 0, st>>>(N, h->gx_s, h->ffix, h->iperm, h->finv, w, dt, h->sid, h->sys, inj,
+    launch_pdl(k_bwd_adjoint, cdiv(N, 256), 256, 0, st, N, h->gx_s, h->ffix, h->iperm, h->finv, w, dt, h->sid, h->sys, inj,
                                                 kT, x_state, v_state, x0, p_prev, h->xbar, h->vbar, wbar,
                                                 h->hbar_atom);
 }

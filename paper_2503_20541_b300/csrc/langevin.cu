@@ -176,6 +176,7 @@ __global__ void k_langevin(int n_groups, const int4* __restrict__ groups, float4
                            const int* __restrict__ iperm, int N, float finv, double kT, const float* __restrict__ xi,
                            double d_oh, double d_hh, float* __restrict__ ke_atom, unsigned* __restrict__ err,
                            LoadNext ln) {
+    pdl_wait();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_groups) return;
     const int4 G = groups[g];
@@ -273,7 +274,7 @@ void launch_langevin(nb_handle* h, float4* xq, float4* v, const float* dt, const
         ln.ffix = h->ffix;
         ln.flags = h->flags;
     }
-    k_langevin<<<cdiv(h->n_groups, 128), 128, 0, st>>>(h->n_groups, h->groups, xq, v, dt, gamma, h->sid, h->sys,
+    launch_pdl(k_langevin, cdiv(h->n_groups, 128), 128, 0, st, h->n_groups, h->groups, xq, v, dt, gamma, h->sid, h->sys,
                                                        h->ffix, h->iperm, h->n_atoms, h->finv, kT, xi, h->d_oh,
                                                        h->d_hh, h->ke_atom, h->flags + 1, ln);
 }

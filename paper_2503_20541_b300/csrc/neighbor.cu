@@ -24,6 +24,7 @@ __global__ void k_load(int N, const float4* __restrict__ xq, const int* __restri
                        const int* __restrict__ sid, const SysDev* __restrict__ sys,
                        const float4* __restrict__ xref, const float4* __restrict__ xsb, float4* __restrict__ xs,
                        long long* __restrict__ ffix, unsigned* flags) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool need = false;
     if (i < N) {
@@ -65,6 +66,7 @@ __device__ __forceinline__ void bin_atom(int i, const float4* __restrict__ xq, c
 __global__ void k_bin(int N, const float4* __restrict__ xq, const int* __restrict__ sid,
                       const SysDev* __restrict__ sys, int* __restrict__ cellid, int* cell_count,
                       unsigned* flags) {
+    pdl_wait();
     if (flags[0] == 0u) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) bin_atom(i, xq, sid, sys, cellid, cell_count, flags);
@@ -176,12 +178,14 @@ __device__ __forceinline__ void scan_single_body(int n, int* count, int* start, 
 
 __global__ void __launch_bounds__(1024) k_scan_single(int n, int* count, int* start, int* cursor,
                                                        const unsigned* flags) {
+    pdl_wait();
     if (flags[0] == 0u) return;
     scan_single_body(n, count, start, cursor);
 }
 
 __global__ void k_scatter(int N, const int* __restrict__ cellid, const int* __restrict__ start,
                           int* cursor, int* __restrict__ perm_tmp, const unsigned* flags) {
+    pdl_wait();
     if (flags[0] == 0u) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -237,6 +241,7 @@ __global__ void k_cellsort(int n_cells, const int* __restrict__ start, const int
                            int* __restrict__ perm, int* __restrict__ iperm, float4* __restrict__ xs,
                            float4* __restrict__ xsb, float2* __restrict__ ps, float4* __restrict__ xref,
                            const unsigned* flags) {
+    pdl_wait();
     if (flags[0] == 0u) return;
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= n_cells) return;
@@ -256,6 +261,7 @@ __global__ void __launch_bounds__(1024) k_sort_small(int N, int n_cells, const f
                                                       int* __restrict__ iperm, float4* __restrict__ xs,
                                                       float4* __restrict__ xsb, float2* __restrict__ ps,
                                                       float4* __restrict__ xref, unsigned* flags) {
+    pdl_wait();
     if (flags[0] == 0u) return;
     for (int i = threadIdx.x; i < N; i += blockDim.x) bin_atom(i, xq, sid, sys, cellid, cell_count, flags);
     __syncthreads();
@@ -446,6 +452,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
     const int* __restrict__ iperm, const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
     int* __restrict__ ex_slot, int* __restrict__ ex_cnt, unsigned short* __restrict__ nbr,
     int* __restrict__ nbr_cnt, unsigned* ticket, unsigned* flags, int split) {
+    pdl_wait();
     if (flags[0] == 0u) return;
     // `split` blocks share a cell, block `part` taking warps part*kBuildWarps.. of its W
     const int c = blockIdx.x / split, part = blockIdx.x % split;
@@ -589,7 +596,7 @@ __global__ void __launch_bounds__(128) k_export_pairs(const int* __restrict__ ce
 
 void launch_load(nb_handle* h, const float4* xq, cudaStream_t st) {
     int N = h->n_atoms;
-    k_load<<<cdiv(N, 256), 256, 0, st>>>(N, xq, h->iperm, h->sid, h->sys, h->xref, h->xsb, h->xs, h->ffix, h->flags);
+    launch_pdl(k_load, cdiv(N, 256), 256, 0, st, N, xq, h->iperm, h->sid, h->sys, h->xref, h->xsb, h->xs, h->ffix, h->flags);
 }
 
 size_t build_smem(const nb_handle* h) { return (size_t)h->tile * (sizeof(float4) + (h->build_gen ? 1 : 0)); }
@@ -599,7 +606,7 @@ static void launch_build(nb_handle* h, cudaStream_t st) {
                  : h->excl_w == 2 ? k_build_cell<2, false>
                  : h->max_excl <= 4 ? k_build_cell<4, false>
                                     : k_build_cell<4, true>;
-    build<<<h->n_cells * h->split_build, kBuildThreads, build_smem(h), st>>>(
+    launch_pdl(build, h->n_cells * h->split_build, kBuildThreads, build_smem(h), st,
         h->cap, h->tile, h->cell_sys, h->sys, h->cell_start, h->xs, h->perm, h->iperm, h->ex_off, h->ex_idx,
         h->ex_slot, h->ex_cnt, h->nbr, h->nbr_cnt, h->build_ticket, h->flags, h->split_build);
 }
@@ -607,15 +614,15 @@ static void launch_build(nb_handle* h, cudaStream_t st) {
 void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st) {
     int N = h->n_atoms;
     if (h->n_scan_blocks == 1 && N <= kSmallSortAtoms) {
-        k_sort_small<<<1, 1024, 0, st>>>(N, h->n_cells, xq, h->sid, h->sys, h->cellid, h->cell_count,
+        launch_pdl(k_sort_small, 1, 1024, 0, st, N, h->n_cells, xq, h->sid, h->sys, h->cellid, h->cell_count,
                                          h->cell_start, h->cell_cursor, h->perm_tmp, h->params, h->perm, h->iperm,
                                          h->xs, h->xsb, h->ps, h->xref, h->flags);
         launch_build(h, st);
         return;
     }
-    k_bin<<<cdiv(N, 256), 256, 0, st>>>(N, xq, h->sid, h->sys, h->cellid, h->cell_count, h->flags);
+    launch_pdl(k_bin, cdiv(N, 256), 256, 0, st, N, xq, h->sid, h->sys, h->cellid, h->cell_count, h->flags);
     if (h->n_scan_blocks == 1) {
-        k_scan_single<<<1, 1024, 0, st>>>(h->n_cells, h->cell_count, h->cell_start, h->cell_cursor, h->flags);
+        launch_pdl(k_scan_single, 1, 1024, 0, st, h->n_cells, h->cell_count, h->cell_start, h->cell_cursor, h->flags);
     } else {
         k_scan_a<<<h->n_scan_blocks, 1024, 0, st>>>(h->n_cells, h->cell_count, h->cell_start, h->scan_bsum,
                                                     h->flags);
@@ -623,8 +630,8 @@ void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st) {
         k_scan_c<<<h->n_scan_blocks, 1024, 0, st>>>(h->n_cells, h->cell_start, h->scan_bsum, h->cell_count,
                                                     h->cell_cursor, h->flags);
     }
-    k_scatter<<<cdiv(N, 256), 256, 0, st>>>(N, h->cellid, h->cell_start, h->cell_cursor, h->perm_tmp, h->flags);
-    k_cellsort<<<cdiv((long long)h->n_cells * 32, 256), 256, 0, st>>>(
+    launch_pdl(k_scatter, cdiv(N, 256), 256, 0, st, N, h->cellid, h->cell_start, h->cell_cursor, h->perm_tmp, h->flags);
+    launch_pdl(k_cellsort, cdiv((long long)h->n_cells * 32, 256), 256, 0, st,
         h->n_cells, h->cell_start, h->perm_tmp, xq, h->params, h->sid, h->sys, h->perm, h->iperm, h->xs, h->xsb,
         h->ps, h->xref, h->flags);
     launch_build(h, st);

@@ -357,6 +357,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_cell(
     const int* __restrict__ start, const float4* __restrict__ xs, const float2* __restrict__ ps,
     const unsigned short* __restrict__ nbr, const int* __restrict__ cnt, ExclView X, long long* __restrict__ ffix,
     float4* __restrict__ e_atom, float4* __restrict__ pscr, float scale, unsigned* flags, int split) {
+    pdl_wait();
     // `split` blocks share a cell: block `part` takes atoms i0 + part*kPairWarps + w + stride*m
     const int c = blockIdx.x / split, part = blockIdx.x % split;
     const int stride = kPairWarps * split;
@@ -639,6 +640,7 @@ __global__ void __launch_bounds__(kVjpThreads, COUL ? 2 : 4) k_vjp_cell(
     const float4* __restrict__ lam, const unsigned short* __restrict__ nbr, const int* __restrict__ cnt,
     ExclView X, float4* __restrict__ gx_s, float2* __restrict__ gp_s, long long* __restrict__ ffix,
     float4* __restrict__ e_atom, float4* __restrict__ pscr, float scale, unsigned* flags, int split) {
+    pdl_wait();
     // `split` blocks share a cell, as in k_pair_cell
     const int c = blockIdx.x / split, part = blockIdx.x % split;
     const int stride = kVjpWarps * split;
@@ -712,11 +714,11 @@ template <bool LJ, int COUL>
 static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp) {
     const ExclView X = excl_view(h);
     if (vjp)
-        k_vjp_cell<LJ, COUL><<<h->n_cells * h->split_pair, kVjpThreads, vjp_smem(h), st>>>(
+        launch_pdl(k_vjp_cell<LJ, COUL>, h->n_cells * h->split_pair, kVjpThreads, vjp_smem(h), st,
             h->n_atoms, h->cap, h->tile, h->cell_sys, h->sys, h->cell_start, h->xs, h->ps, h->lam, h->nbr,
             h->nbr_cnt, X, h->gx_s, h->gp_s, h->ffix, h->e_atom, h->pscr, h->fscale, h->flags, h->split_pair);
     else
-        k_pair_cell<LJ, COUL><<<h->n_cells * h->split_pair, kPairThreads, pair_smem(h), st>>>(
+        launch_pdl(k_pair_cell<LJ, COUL>, h->n_cells * h->split_pair, kPairThreads, pair_smem(h), st,
             h->n_atoms, h->cap, h->tile, h->cell_sys, h->sys, h->cell_start, h->xs, h->ps, h->nbr, h->nbr_cnt, X,
             h->ffix, h->e_atom, h->pscr, h->fscale, h->flags, h->split_pair);
 }

@@ -103,6 +103,7 @@ __global__ void k_spread(int N, const float4* __restrict__ xs, const int* __rest
 }
 
 __global__ void k_grid_convert(long long n, long long* __restrict__ gfix, float* __restrict__ grid, double ginv) {
+    pdl_wait();
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     grid[k] = (float)((double)gfix[k] * ginv);
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(kConvThreads) k_convolve(const int* __restrict
                                                            float2* __restrict__ cgrid,
                                                            const float* __restrict__ green,
                                                            double* __restrict__ e_blk) {
+    pdl_wait();
     int b = blockIdx.x;
     int s = blk_sys[b];
     const SysDev& S = sys[s];
@@ -358,7 +360,7 @@ cudaError_t pme_setup(nb_handle* h) {
 static void spread(nb_handle* h, const float4* x, cudaStream_t st) {
     int N = h->n_atoms;
     k_spread<<<cdiv((long long)N * 16, 256), 256, 0, st>>>(N, x, h->sid, h->sys, h->gfix, (float)h->gscale);
-    k_grid_convert<<<cdiv(h->grid_total, 256), 256, 0, st>>>(h->grid_total, h->gfix, h->grid, 1.0 / h->gscale);
+    launch_pdl(k_grid_convert, cdiv(h->grid_total, 256), 256, 0, st, h->grid_total, h->gfix, h->grid, 1.0 / h->gscale);
 }
 
 void launch_pme_spread(nb_handle* h, const float4* x, cudaStream_t st) { spread(h, x, st); }
@@ -383,7 +385,7 @@ static int fft_on(nb_handle* h, float* mesh, int inverse, cudaStream_t st) {
 int launch_pme_fft(nb_handle* h, int inverse, cudaStream_t st) { return fft_on(h, h->grid, inverse, st); }
 
 void launch_pme_convolve(nb_handle* h, cudaStream_t st) {
-    k_convolve<<<h->n_conv_blocks, kConvThreads, 0, st>>>(h->conv_blk_sys, h->conv_blk_off, h->sys, h->cgrid,
+    launch_pdl(k_convolve, h->n_conv_blocks, kConvThreads, 0, st, h->conv_blk_sys, h->conv_blk_off, h->sys, h->cgrid,
                                                           h->green, h->e_pme_blk);
 }
 
@@ -560,7 +562,7 @@ int launch_pme_vjp(nb_handle* h, cudaStream_t st) {
     k_grid_convert_dyn<<<cdiv(h->grid_total, 256), 256, 0, st>>>(h->grid_total, h->gfix, h->grid2, h->lam_max,
                                                                  h->kl_max);
     if (fft_on(h, h->grid2, 0, st)) return 1;
-    k_convolve<<<h->n_conv_blocks, kConvThreads, 0, st>>>(h->conv_blk_sys, h->conv_blk_off, h->sys, h->cgrid,
+    launch_pdl(k_convolve, h->n_conv_blocks, kConvThreads, 0, st, h->conv_blk_sys, h->conv_blk_off, h->sys, h->cgrid,
                                                           h->green, nullptr);
     if (fft_on(h, h->grid2, 1, st)) return 1;
     k_gather_vjp<<<cdiv((long long)N * 16, 256), 256, 0, st>>>(N, h->xs, h->lam, h->sid, h->sys, h->grid,

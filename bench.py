@@ -257,20 +257,32 @@ def flops_per_launch(pc):
             + FLOP_EXCL_PAIR * pc["excluded"])
 
 
-def profile_record(path):
-    """The figures of a committed ncu summary of the pair kernel, if it was taken on the
-    current kernel source (its sha256 prefix is recorded there); else None."""
+def profile_record(path, source="pair.cu"):
+    """The figures of a committed ncu summary of a kernel, if it was taken on the current
+    source of its file under csrc/ (the sha256 prefix recorded there); else None."""
     try:
-        src = open(os.path.join(ROOT, "paper_2503_20541_b300", "csrc", "pair.cu"), "rb").read()
+        src = open(os.path.join(ROOT, "paper_2503_20541_b300", "csrc", source), "rb").read()
         sha = hashlib.sha256(src).hexdigest()[:16]
         rec = {}
         for line in open(path):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 rec[k.strip()] = v.strip()
-        return rec if rec.get("pair_cu_sha256_16") == sha else None
+        return rec if rec.get(source.replace(".", "_") + "_sha256_16") == sha else None
     except OSError:
         return None
+
+
+def issue_roofline(prof, ms, f_sm):
+    """Warp instructions per launch (from an ncu summary) over the launch's CUDA-event
+    duration, against 4 warp instructions per SM per clock."""
+    if not prof or "warp instructions" not in prof:
+        return None
+    wi = float(prof["warp instructions"])
+    ach = wi / (ms / 1e3)
+    pk = N_SM * ISSUE_PER_SM_CLK * f_sm * 1e6
+    return {"warp_instructions_per_launch": wi, "achieved_per_s": ach, "peak_per_s": pk, "frac": ach / pk,
+            "peak_source": "148 SMs x 4 schedulers x median SM clock %.0f MHz" % f_sm}
 
 
 def traffic_from_profile(path):
@@ -1124,14 +1136,11 @@ def main():
     hbm_gbs, hbm_src = hbm_peak_gbs()
     # instruction-issue ceiling of the pair kernel: warp instructions per launch from the
     # committed ncu summary (when taken on the current source) over 4 per SM per clock
-    prof = profile_record(os.path.join(ROOT, "profiles", "pair_kernel_water24k.txt"))
-    issue = None
-    if prof and "warp instructions" in prof:
-        wi = float(prof["warp instructions"])
-        ach = wi / (t_pair / 1e3)
-        pk = N_SM * ISSUE_PER_SM_CLK * f_sm * 1e6
-        issue = {"warp_instructions_per_launch": wi, "achieved_per_s": ach, "peak_per_s": pk, "frac": ach / pk,
-                 "peak_source": "148 SMs x 4 schedulers x median SM clock %.0f MHz" % f_sm}
+    issue = issue_roofline(profile_record(os.path.join(ROOT, "profiles", "pair_kernel_water24k.txt")), t_pair, f_sm)
+    # the Verlet list build kernel alone (inside the rebuild chain), and its issue rate
+    t_bk = stages_rs["build"][0] / max(stages_rs["build"][1], 1)
+    issue_build = issue_roofline(profile_record(os.path.join(ROOT, "profiles", "build_kernel_water24k.txt"),
+                                                "neighbor.cu"), t_bk, f_sm)
     rows = row_rooflines(s, stages_pme, hbm_gbs, hbm_src)
 
     out = {
@@ -1154,6 +1163,7 @@ def main():
                            "achieved": build_gbs, "peak": hbm_gbs, "peak_source": hbm_src, "unit": "GB/s",
                            "frac": build_gbs / hbm_gbs,
                            "bytes_per_build": build_bytes, "ms_per_build": t_build,
+                           "build_kernel_us": 1e3 * t_bk, "issue_build_kernel": issue_build,
                            "note": "issue-bound (FP32 + ALU tests of 2250 candidates per atom), not HBM-bound"},
         "row_rooflines": rows,
         "stage_ms_per_step_eager": {k: v[0] / max(K, 1) for k, v in stages.items()},

@@ -435,7 +435,8 @@ int64_t nb_rebuild_count(nb_handle* h, void* stream);
 #define NB_STAGE_CONVOLVE 5  /* PME influence function and reciprocal energy */
 #define NB_STAGE_GATHER 6    /* PME force gathering */
 #define NB_STAGE_UPDATE 7    /* reductions, force output, integrator updates */
-#define NB_NSTAGES 8
+#define NB_STAGE_BUILD 8     /* the Verlet list build kernel alone (also inside NB_STAGE_REBUILD) */
+#define NB_NSTAGES 9
 nb_status nb_timing_enable(nb_handle* h, int32_t enable);
 nb_status nb_timing_read(nb_handle* h, void* stream, double* ms, int64_t* intervals);
 

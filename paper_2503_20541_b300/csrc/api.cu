@@ -64,9 +64,11 @@ float4* F4(float* p) { return reinterpret_cast<float4*>(p); }
 void request_rebuild(nb_handle* h, cudaStream_t st) { cudaMemsetAsync(h->flags, 0x01, sizeof(unsigned), st); }
 
 // Brackets the kernels of one stage with CUDA events when timing is enabled.
+// Stages may nest (the list build inside the rebuild): each remembers its own end event.
 struct Stage {
     nb_handle* h;
     cudaStream_t st;
+    cudaEvent_t end = nullptr;
     explicit Stage(nb_handle* hh, int stage, cudaStream_t s) : h(hh), st(s) {
         if (!h->timing) return;
         for (int k = 0; k < 2; ++k) {
@@ -80,10 +82,11 @@ struct Stage {
             h->ev_used.push_back(e);
         }
         h->ev_stage.push_back(stage);
+        end = h->ev_used.back();
         cudaEventRecord(h->ev_used[h->ev_used.size() - 2], st);
     }
     ~Stage() {
-        if (h->timing) cudaEventRecord(h->ev_used.back(), st);
+        if (h->timing) cudaEventRecord(end, st);
     }
 };
 
@@ -96,7 +99,9 @@ void prepare(nb_handle* h, const float4* xq, bool force, cudaStream_t st, bool l
         if (!loaded) launch_load(h, xq, st);
     }
     Stage sc(h, NB_STAGE_REBUILD, st);
-    launch_rebuild(h, xq, st);
+    launch_reslot(h, xq, st);
+    Stage sb(h, NB_STAGE_BUILD, st);
+    launch_build(h, st);
 }
 
 // The mesh half of PME (spread, FFT, convolution, inverse FFT) for positions x.
@@ -141,7 +146,9 @@ nb_status eval(nb_handle* h, const float4* xq, int terms, bool force, cudaStream
     }
     {
         Stage sc(h, NB_STAGE_REBUILD, st);
-        launch_rebuild(h, xq, st);
+        launch_reslot(h, xq, st);
+        Stage sb(h, NB_STAGE_BUILD, st);
+        launch_build(h, st);
     }
     if (pme) {
         cudaEventRecord(h->ev_built, st);

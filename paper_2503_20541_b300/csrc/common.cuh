@@ -256,7 +256,8 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 // ------------------------------------------------------------------ launchers
 // neighbor.cu
 void launch_load(nb_handle* h, const float4* xq, cudaStream_t st);
-void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st);
+void launch_reslot(nb_handle* h, const float4* xq, cudaStream_t st);
+void launch_build(nb_handle* h, cudaStream_t st);
 cudaError_t build_setup(nb_handle* h);
 void launch_export_pairs(nb_handle* h, int2* out, long long max_pairs, unsigned long long* counter,
                          cudaStream_t st);

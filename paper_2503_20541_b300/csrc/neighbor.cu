@@ -601,7 +601,7 @@ void launch_load(nb_handle* h, const float4* xq, cudaStream_t st) {
 
 size_t build_smem(const nb_handle* h) { return (size_t)h->tile * (sizeof(float4) + (h->build_gen ? 1 : 0)); }
 
-static void launch_build(nb_handle* h, cudaStream_t st) {
+void launch_build(nb_handle* h, cudaStream_t st) {
     auto build = h->excl_w == 0   ? k_build_cell<0, false>
                  : h->excl_w == 2 ? k_build_cell<2, false>
                  : h->max_excl <= 4 ? k_build_cell<4, false>
@@ -611,13 +611,14 @@ static void launch_build(nb_handle* h, cudaStream_t st) {
         h->ex_slot, h->ex_cnt, h->nbr, h->nbr_cnt, h->build_ticket, h->flags, h->split_build);
 }
 
-void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st) {
+// Re-slotting of a rebuild: binning, scan, scatter and in-cell sort (one block for small
+// handles); the Verlet list build (launch_build) follows.
+void launch_reslot(nb_handle* h, const float4* xq, cudaStream_t st) {
     int N = h->n_atoms;
     if (h->n_scan_blocks == 1 && N <= kSmallSortAtoms) {
         launch_pdl(k_sort_small, 1, 1024, 0, st, N, h->n_cells, xq, h->sid, h->sys, h->cellid, h->cell_count,
                                          h->cell_start, h->cell_cursor, h->perm_tmp, h->params, h->perm, h->iperm,
                                          h->xs, h->xsb, h->ps, h->xref, h->flags);
-        launch_build(h, st);
         return;
     }
     launch_pdl(k_bin, cdiv(N, 256), 256, 0, st, N, xq, h->sid, h->sys, h->cellid, h->cell_count, h->flags);
@@ -634,8 +635,8 @@ void launch_rebuild(nb_handle* h, const float4* xq, cudaStream_t st) {
     launch_pdl(k_cellsort, cdiv((long long)h->n_cells * 32, 256), 256, 0, st,
         h->n_cells, h->cell_start, h->perm_tmp, xq, h->params, h->sid, h->sys, h->perm, h->iperm, h->xs, h->xsb,
         h->ps, h->xref, h->flags);
-    launch_build(h, st);
 }
+
 
 // The dynamic shared-memory limit of a kernel is process-wide, so it is raised once to
 // what the device allows (less the kernel's static shared memory) rather than to one

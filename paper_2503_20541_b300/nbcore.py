@@ -37,7 +37,7 @@ EXPORTS = [
     "pme_spread_static", "nb_set_water_constraints", "langevin_step", "constrain_positions", "constrain_velocities",
 ]
 STATIC_MESH_MAX = 1 << 20
-STAGES = ["check", "rebuild", "pair", "spread", "fft", "convolve", "gather", "update"]
+STAGES = ["check", "rebuild", "pair", "spread", "fft", "convolve", "gather", "update", "build"]
 
 
 class NbError(RuntimeError):

@@ -42,8 +42,9 @@ WORKLOAD = ("water box 24,000 atoms (8000 3-site molecules, 62.1 A cubic, LJ on 
             "Ewald alpha 0.32/A, PME 64^3 order 4); step = one full nonbonded force evaluation with the "
             "neighbour list rebuilt every step")
 
-# Algorithmic FP32 work per unordered pair of the pair kernel (flops, FMA = 2);
-# the counts follow the kernel source ("Roofline").
+# Algorithmic FP32 work per unordered pair of the pair kernel (flops, FMA = 2): the
+# method's own arithmetic per pair (difference, r^2 and test; LJ; erfc Coulomb), counted
+# once per unordered pair although the full list evaluates each pair from both sides.
 FLOP_LIST_PAIR = 18   # min-image difference, r^2, compare
 FLOP_LJ_PAIR = 25     # mixing, (sigma/r)^6, energy, force
 FLOP_COUL_PAIR = 45   # erfc, Gaussian, energy, force

@@ -1,6 +1,6 @@
 """GPU parity: libnbcore (through its C ABI) against the FP64 oracle.
 
-Tolerances (the bar of the hot path, derived in the design doc):
+Tolerances (the bar of the hot path: FP32 pair arithmetic against FP64):
   * neighbour pair sets: identical, except pairs whose FP64 r^2 lies within
     8 ulp(fp32) of r_nl^2, which are found by brute force and counted;
   * forces: relative RMS <= 1e-5 against FP64;

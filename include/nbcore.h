@@ -106,7 +106,9 @@ typedef struct {
                                 of 128; 0: from density */
     int32_t stencil_tile;    /* stencil candidates per shared-memory tile of the cell kernels
                                 (multiple of 64 in [256, 4096]); 0: auto from the density */
-    int32_t cell_div;        /* cells of edge >= r_nl / cell_div, cell_div in {1, 2}; 0: auto */
+    int32_t cell_div;        /* cells of edge >= r_nl / cell_div, cell_div in {1, 2}, for every
+                                system; 0: chosen per system (2 for a system with >= 5 cells
+                                of edge r_nl/2 along each axis and >= 64 atoms per r_nl^3) */
     int32_t force_bits;      /* fixed-point fraction bits for forces; 0: 32 */
     int32_t blocks_per_cell; /* thread blocks sharing one cell in the list build, pair and VJP
                                 kernels (each takes a strided share of the cell's atoms), in

@@ -12,10 +12,22 @@ the finer cells) are skipped.
 import math
 
 
+def auto_cell_div(s):
+    """The library's default cell size for one system (cell_div 0): cells of edge r_nl/2
+    when there are >= 5 of them along every axis and >= 64 atoms per r_nl^3, else r_nl."""
+    box = [float(b) for b in (s.box if hasattr(s.box, "__len__") else [s.box] * 3)]
+    r_nl = float(s.r_cut) + float(s.r_skin)
+    dense = s.n / (box[0] * box[1] * box[2]) * r_nl ** 3 >= 64.0
+    return 2 if dense and all(math.floor(L * 2.0 / r_nl) >= 5 for L in box) else 1
+
+
 def candidate_options(systems):
-    """Option sets worth timing for these systems: both cell sizes, each with the
-    automatic tile and a tile about 25% smaller (a multiple of 64, >= 256)."""
+    """Option sets worth timing for these systems: both cell sizes for all systems, each
+    with the automatic tile and a tile about 25% smaller (a multiple of 64, >= 256), and,
+    when the systems would take different cell sizes, the per-system default (cell_div 0)."""
     out = []
+    if len({auto_cell_div(s) for s in systems}) > 1:
+        out.append(dict(cell_div=0))
     for cd in (1, 2):
         base = dict(cell_div=cd)
         out.append(base)

@@ -313,18 +313,23 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
     // entries because the pair kernels read rows in 128-entry groups
     double nb_max = 0.0;
     int n_max = 0;
-    bool fine_cells = true;
+    // cell size per system: the handle's option for all, or by default cells of edge
+    // r_nl/2 for a system with >= 5 of them along every axis and >= 64 atoms per r_nl^3
+    // (dense enough for the finer stencil to pay), else cells of edge r_nl
+    std::vector<int> cell_div((size_t)n_systems, o.cell_div);
     for (int s = 0; s < n_systems; ++s) {
         const nb_system_desc& d = sys[s];
         double rnl = d.r_cut + d.r_skin;
         double V = d.box[0] * d.box[1] * d.box[2];
         nb_max = std::max(nb_max, d.n_atoms / V * 4.18879020478639 * rnl * rnl * rnl);
         n_max = std::max(n_max, d.n_atoms);
+        if (o.cell_div) continue;
+        bool fine = d.n_atoms / V * rnl * rnl * rnl >= 64.0;
         for (int k = 0; k < 3; ++k)
-            if (std::floor(d.box[k] * 2.0 / rnl) < 5.0) fine_cells = false;
-        if (d.n_atoms / V * rnl * rnl * rnl < 64.0) fine_cells = false;
+            if (std::floor(d.box[k] * 2.0 / rnl) < 5.0) fine = false;
+        cell_div[(size_t)s] = fine ? 2 : 1;
     }
-    h->cell_div = o.cell_div ? o.cell_div : (fine_cells ? 2 : 1);
+    h->cell_div = o.cell_div;
     if (o.max_neighbors > 0) {
         h->cap = std::max(128, round_up(o.max_neighbors, 128));
     } else {
@@ -349,7 +354,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
             D.L[k] = (float)d.box[k];
             D.invL[k] = (float)(1.0 / d.box[k]);
             D.halfL[k] = (float)(0.5 * d.box[k]);
-            int nc = std::max(1, (int)std::floor(d.box[k] * h->cell_div / rnl));
+            int nc = std::max(1, (int)std::floor(d.box[k] * cell_div[(size_t)s] / rnl));
             nc = std::min(nc, 1024);
             D.nc[k] = nc;
             D.cell_scale[k] = (float)(nc / d.box[k]);
@@ -382,7 +387,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
             D.kl_hi[k] = (float)kl;
             D.kl_lo[k] = (float)(kl - (double)D.kl_hi[k]);
         }
-        D.stencil = h->cell_div;
+        D.stencil = cell_div[(size_t)s];
         D.red_tile = red_tile(D.n_atoms);
         if (D.periodic)
             for (int k = 0; k < 3; ++k)

@@ -80,7 +80,7 @@ struct nb_handle {
     int n_sys = 0;
     int n_atoms = 0;
     int cap = 0;        // per-atom neighbour capacity (full list)
-    int cell_div = 1;
+    int cell_div = 0;   // the handle's option (0: per system, SysDev::stencil)
     int force_bits = 32;
     float fscale = 4294967296.0f, finv = 1.0f / 4294967296.0f;
     double gscale = 4294967296.0;  // PME mesh fixed-point scale

@@ -28,6 +28,13 @@ def test_candidates_cover_both_cell_sizes_with_valid_tiles():
         assert t == 0 or (256 <= t <= 4096 and t % 64 == 0)
 
 
+def test_mixed_systems_add_the_per_system_cell_size():
+    lj, water = wl.lj_random(700, seed=1), wl.water_box()
+    assert (autotune.auto_cell_div(lj), autotune.auto_cell_div(water)) == (1, 2)
+    assert dict(cell_div=0) in autotune.candidate_options([lj, water])
+    assert dict(cell_div=0) not in autotune.candidate_options([water])
+
+
 def test_autotune_picks_fastest_and_skips_failures():
     systems = [wl.lj_random(500, seed=3)]
     cands = [dict(cell_div=1), dict(cell_div=2), dict(cell_div=2, stencil_tile=512)]

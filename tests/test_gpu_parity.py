@@ -378,6 +378,29 @@ def test_batched_systems_match_single_system_bitwise():
         off += s.n
 
 
+def test_batched_systems_take_their_own_cell_size():
+    """Without a handle-wide cell size each system takes its own default (cells of edge
+    r_nl/2 for the dense 24k water box, r_nl for the LJ fluids): batched forces and
+    energies are bitwise those of each system on its own handle."""
+    from paper_2503_20541_b300 import autotune
+    systems = [wl.lj_random(700, seed=1), wl.water_box(), wl.lj_random(1311, seed=3)]
+    assert [autotune.auto_cell_div(s) for s in systems] == [1, 2, 1]
+    opts = dict(max_neighbors=1024, stencil_tile=2560)
+    xs = [dev_xq(s) for s in systems]
+    fb = torch.empty((sum(s.n for s in systems), 3), dtype=torch.float32, device="cuda")
+    eb = torch.empty((len(systems), 6), dtype=torch.float64, device="cuda")
+    with nbcore.Handle(systems, **opts) as h:
+        h.nonbonded_forces(torch.cat(xs), fb, eb)
+        h.check()
+    off = 0
+    for k, s in enumerate(systems):
+        with nbcore.Handle([s], **opts) as h1:
+            f1, e1 = _forces(h1, s, xq=xs[k])
+        assert np.array_equal(fb[off:off + s.n].cpu().numpy().astype(np.float64), f1)
+        assert np.array_equal(eb[k].cpu().numpy(), e1)
+        off += s.n
+
+
 # ---------------------------------------------------------------- errors
 
 def test_error_paths_return_status_without_faulting():

@@ -171,6 +171,7 @@ nb_status launched() { return from_cuda(cudaGetLastError()); }
 
 __global__ void k_lam_scatter(int N, const float* __restrict__ lam, const int* __restrict__ iperm,
                               float4* __restrict__ out) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     out[iperm[i]] = make_float4(lam[3 * (size_t)i], lam[3 * (size_t)i + 1], lam[3 * (size_t)i + 2], 0.f);
@@ -179,6 +180,7 @@ __global__ void k_lam_scatter(int N, const float* __restrict__ lam, const int* _
 __global__ void k_vjp_out(int N, const float4* __restrict__ gx_s, const float2* __restrict__ gp_s,
                           const int* __restrict__ iperm, float* __restrict__ gx, float* __restrict__ gq,
                           float* __restrict__ gsig, float* __restrict__ geps) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     int k = iperm[i];
@@ -987,7 +989,7 @@ nb_status nonbonded_force_vjp(nb_handle* h, const float* xq, const float* lam, f
     int N = h->n_atoms;
     const int t = terms & NB_TERM_ALL;
     prepare(h, F4(xq), false, st);
-    k_lam_scatter<<<cdiv(N, 256), 256, 0, st>>>(N, lam, h->iperm, h->lam);
+    launch_pdl(k_lam_scatter, cdiv(N, 256), 256, 0, st, N, lam, h->iperm, h->lam);
     {
         Stage sc(h, NB_STAGE_PAIR, st);
         launch_vjp(h, t & (NB_TERM_LJ | NB_TERM_COUL), st);
@@ -997,7 +999,7 @@ nb_status nonbonded_force_vjp(nb_handle* h, const float* xq, const float* lam, f
         if (launch_pme_vjp(h, st)) return NB_ERR_CUDA;
     }
     Stage sc(h, NB_STAGE_UPDATE, st);
-    k_vjp_out<<<cdiv(N, 256), 256, 0, st>>>(N, h->gx_s, h->gp_s, h->iperm, gx, gq, gsigma, gsqrt_eps);
+    launch_pdl(k_vjp_out, cdiv(N, 256), 256, 0, st, N, h->gx_s, h->gp_s, h->iperm, gx, gq, gsigma, gsqrt_eps);
     if (f_out) launch_finalize_forces(h, f_out, st);
     return launched();
 }

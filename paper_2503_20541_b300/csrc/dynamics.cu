@@ -248,6 +248,7 @@ __global__ void k_hmc_init(int N, const float* __restrict__ w, const float* __re
 
 __global__ void k_hmc_jump(int N, const float4* __restrict__ x1, const float4* __restrict__ x0,
                            const int* __restrict__ sid, const SysDev* __restrict__ sys, double* __restrict__ jump) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const SysDev& S = sys[sid[i]];
@@ -266,6 +267,7 @@ __global__ void __launch_bounds__(kRedThreads) k_hmc_accept(const SysDev* __rest
                                                              const double* __restrict__ e0,
                                                              const double* __restrict__ e1, double kT,
                                                              const double* __restrict__ u, double* __restrict__ stats) {
+    pdl_wait();
     __shared__ double sm[kRedThreads / 32];
     int s = blockIdx.x;
     const SysDev& S = sys[s];
@@ -292,6 +294,7 @@ __global__ void __launch_bounds__(kRedThreads) k_hmc_accept(const SysDev* __rest
 
 __global__ void k_hmc_restore(int N, float4* __restrict__ x_out, const float4* __restrict__ x0,
                               const int* __restrict__ sid, const double* __restrict__ stats) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     if (stats[(size_t)sid[i] * 4 + 3] == 0.0) x_out[i] = x0[i];
@@ -304,6 +307,7 @@ __global__ void k_hmc_restore(int N, float4* __restrict__ x_out, const float4* _
 __global__ void k_hmc_pick(int n_sys, const int* __restrict__ l_prop, int n_leap,
                            const double* __restrict__ step_stats, const double* __restrict__ u,
                            double* __restrict__ stats, unsigned* __restrict__ err) {
+    pdl_wait();
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_sys) return;
     const int l = l_prop[s];
@@ -438,6 +442,7 @@ __global__ void k_bwd_final(int N, const long long* __restrict__ ffix, const int
                             const float* __restrict__ w, const float* __restrict__ dt, const int* __restrict__ sid,
                             const float* __restrict__ xi, double kT, const float4* __restrict__ vbar,
                             float* __restrict__ wbar, double* __restrict__ hbar) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     int s = sid[i];
@@ -459,6 +464,7 @@ __global__ void k_bwd_final(int N, const long long* __restrict__ ffix, const int
 __global__ void __launch_bounds__(kRedThreads) k_bwd_reduce_h(const SysDev* __restrict__ sys,
                                                                const double* __restrict__ hbar,
                                                                double* __restrict__ g_dt) {
+    pdl_wait();
     __shared__ double sm[kRedThreads / 32];
     int s = blockIdx.x;
     const SysDev& S = sys[s];
@@ -506,16 +512,16 @@ void launch_hmc_init(nb_handle* h, const float* w, const float* xi, double kT, c
 void launch_hmc_finish(nb_handle* h, float4* x_out, const float4* x0, double kT, const double* u, double* stats,
                        cudaStream_t st) {
     int N = h->n_atoms;
-    k_hmc_jump<<<cdiv(N, 256), 256, 0, st>>>(N, x_out, x0, h->sid, h->sys, h->jump_atom);
-    k_hmc_accept<<<h->n_sys, kRedThreads, 0, st>>>(h->sys, h->jump_atom, h->e0, h->e1, kT, u, stats);
-    k_hmc_restore<<<cdiv(N, 256), 256, 0, st>>>(N, x_out, x0, h->sid, stats);
+    launch_pdl(k_hmc_jump, cdiv(N, 256), 256, 0, st, N, x_out, x0, h->sid, h->sys, h->jump_atom);
+    launch_pdl(k_hmc_accept, h->n_sys, kRedThreads, 0, st, h->sys, h->jump_atom, h->e0, h->e1, kT, u, stats);
+    launch_pdl(k_hmc_restore, cdiv(N, 256), 256, 0, st, N, x_out, x0, h->sid, stats);
 }
 
 void launch_hmc_pick(nb_handle* h, float4* x_out, const float4* x0, const int* l_prop, int n_leap,
                      const double* step_stats, const double* u, double* stats, cudaStream_t st) {
     int N = h->n_atoms;
-    k_hmc_pick<<<cdiv(h->n_sys, 128), 128, 0, st>>>(h->n_sys, l_prop, n_leap, step_stats, u, stats, h->flags + 1);
-    k_hmc_restore<<<cdiv(N, 256), 256, 0, st>>>(N, x_out, x0, h->sid, stats);
+    launch_pdl(k_hmc_pick, cdiv(h->n_sys, 128), 128, 0, st, h->n_sys, l_prop, n_leap, step_stats, u, stats, h->flags + 1);
+    launch_pdl(k_hmc_restore, cdiv(N, 256), 256, 0, st, N, x_out, x0, h->sid, stats);
 }
 
 void launch_bwd_lambda(nb_handle* h, const float* w, const float* dt, const float4* v_state, const Inject& inj,
@@ -536,9 +542,9 @@ void launch_bwd_adjoint(nb_handle* h, const float* w, const float* dt, const flo
 void launch_bwd_final(nb_handle* h, const float* w, const float* dt, const float* xi, double kT, float* wbar,
                       double* g_dt, cudaStream_t st) {
     int N = h->n_atoms;
-    k_bwd_final<<<cdiv(N, 256), 256, 0, st>>>(N, h->ffix, h->iperm, h->finv, w, dt, h->sid, xi, kT, h->vbar, wbar,
+    launch_pdl(k_bwd_final, cdiv(N, 256), 256, 0, st, N, h->ffix, h->iperm, h->finv, w, dt, h->sid, xi, kT, h->vbar, wbar,
                                               h->hbar_atom);
-    k_bwd_reduce_h<<<h->n_sys, kRedThreads, 0, st>>>(h->sys, h->hbar_atom, g_dt);
+    launch_pdl(k_bwd_reduce_h, h->n_sys, kRedThreads, 0, st, h->sys, h->hbar_atom, g_dt);
 }
 
 }  // namespace nb

@@ -197,6 +197,7 @@ __global__ void k_langevin(int n_groups, const int4* __restrict__ groups, float4
 
 // K = |v|^2 / (2 w) per atom (the last state of a run).
 __global__ void k_kinetic(int N, const float4* __restrict__ v, float* __restrict__ ke_atom) {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float4 u = v[i];
@@ -208,6 +209,7 @@ __global__ void k_kinetic(int N, const float4* __restrict__ v, float* __restrict
 __global__ void k_settle(int n_groups, const int4* __restrict__ groups, const float4* __restrict__ x_ref,
                          float4* __restrict__ x, float4* __restrict__ v, const float* __restrict__ inv_mass, float dt,
                          double d_oh, double d_hh, unsigned* __restrict__ err) {
+    pdl_wait();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_groups) return;
     const int4 G = groups[g];
@@ -242,6 +244,7 @@ __global__ void k_settle(int n_groups, const int4* __restrict__ groups, const fl
 
 __global__ void k_rattle(int n_groups, const int4* __restrict__ groups, const float4* __restrict__ x,
                          float4* __restrict__ v) {
+    pdl_wait();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_groups) return;
     const int4 G = groups[g];
@@ -280,17 +283,17 @@ void launch_langevin(nb_handle* h, float4* xq, float4* v, const float* dt, const
 }
 
 void launch_kinetic(nb_handle* h, const float4* v, cudaStream_t st) {
-    k_kinetic<<<cdiv(h->n_atoms, 256), 256, 0, st>>>(h->n_atoms, v, h->ke_atom);
+    launch_pdl(k_kinetic, cdiv(h->n_atoms, 256), 256, 0, st, h->n_atoms, v, h->ke_atom);
 }
 
 void launch_settle(nb_handle* h, const float4* x_ref, float4* x, float4* v, const float* inv_mass, float dt,
                    cudaStream_t st) {
-    k_settle<<<cdiv(h->n_groups, 128), 128, 0, st>>>(h->n_groups, h->groups, x_ref, x, v, inv_mass, dt, h->d_oh,
+    launch_pdl(k_settle, cdiv(h->n_groups, 128), 128, 0, st, h->n_groups, h->groups, x_ref, x, v, inv_mass, dt, h->d_oh,
                                                      h->d_hh, h->flags + 1);
 }
 
 void launch_rattle(nb_handle* h, const float4* x, float4* v, cudaStream_t st) {
-    k_rattle<<<cdiv(h->n_groups, 128), 128, 0, st>>>(h->n_groups, h->groups, x, v);
+    launch_pdl(k_rattle, cdiv(h->n_groups, 128), 128, 0, st, h->n_groups, h->groups, x, v);
 }
 
 }  // namespace nb

@@ -103,6 +103,7 @@ __device__ __forceinline__ int block_exscan(int v, int* total) {
 
 __global__ void __launch_bounds__(1024) k_scan_a(int n, const int* __restrict__ count, int* start,
                                                   int* bsum, const unsigned* flags) {
+    pdl_wait();
     if (flags[0] == 0u) return;
     __shared__ int tot;
     int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(1024) k_scan_a(int n, const int* __restrict__ 
 
 __global__ void __launch_bounds__(1024) k_scan_b(int nb, int n, int* bsum, int* start,
                                                   const unsigned* flags) {
+    pdl_wait();
     if (flags[0] == 0u) return;
     __shared__ int tot;
     int carry = 0;
@@ -139,6 +141,7 @@ __global__ void __launch_bounds__(1024) k_scan_b(int nb, int n, int* bsum, int* 
 
 __global__ void __launch_bounds__(1024) k_scan_c(int n, int* start, const int* __restrict__ bsum,
                                                   int* count, int* cursor, const unsigned* flags) {
+    pdl_wait();
     if (flags[0] == 0u) return;
     int off = bsum[blockIdx.x];
     int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
@@ -625,10 +628,10 @@ void launch_reslot(nb_handle* h, const float4* xq, cudaStream_t st) {
     if (h->n_scan_blocks == 1) {
         launch_pdl(k_scan_single, 1, 1024, 0, st, h->n_cells, h->cell_count, h->cell_start, h->cell_cursor, h->flags);
     } else {
-        k_scan_a<<<h->n_scan_blocks, 1024, 0, st>>>(h->n_cells, h->cell_count, h->cell_start, h->scan_bsum,
+        launch_pdl(k_scan_a, h->n_scan_blocks, 1024, 0, st, h->n_cells, h->cell_count, h->cell_start, h->scan_bsum,
                                                     h->flags);
-        k_scan_b<<<1, 1024, 0, st>>>(h->n_scan_blocks, h->n_cells, h->scan_bsum, h->cell_start, h->flags);
-        k_scan_c<<<h->n_scan_blocks, 1024, 0, st>>>(h->n_cells, h->cell_start, h->scan_bsum, h->cell_count,
+        launch_pdl(k_scan_b, 1, 1024, 0, st, h->n_scan_blocks, h->n_cells, h->scan_bsum, h->cell_start, h->flags);
+        launch_pdl(k_scan_c, h->n_scan_blocks, 1024, 0, st, h->n_cells, h->cell_start, h->scan_bsum, h->cell_count,
                                                     h->cell_cursor, h->flags);
     }
     launch_pdl(k_scatter, cdiv(N, 256), 256, 0, st, N, h->cellid, h->cell_start, h->cell_cursor, h->perm_tmp, h->flags);

@@ -356,12 +356,13 @@ def extras(torch, nbcore, wl):
         torch.cuda.synchronize()
         h.check()
         ms = e0.elapsed_time(e1)
-        # the same steps as a CUDA graph of 10 velocity-Verlet steps (lazy rebuilds inside)
-        g = CapturedStep(lambda: h.md_step(xq, v, dt, 10, terms=nbcore.NB_TERM_LJ))
+        # the same steps as a CUDA graph of one 100-step call (the 100-step run of the
+        # workload; lazy rebuilds inside), replayed
+        g = CapturedStep(lambda: h.md_step(xq, v, dt, 100, terms=nbcore.NB_TERM_LJ))
         c1 = h.rebuild_count()
         e2, e3 = ev(), ev()
         e2.record()
-        for _ in range(n // 10):
+        for _ in range(n // 100):
             g.replay()
         e3.record()
         torch.cuda.synchronize()
@@ -370,7 +371,8 @@ def extras(torch, nbcore, wl):
         out["md_steps_per_s"] = {"value": n / (ms_g / 1e3), "eager": n / (ms / 1e3),
                                  "workload": "LJ fluid 864 atoms (FCC 6^3, rho* 0.8442, r_c 2.5, r_skin 0.3), "
                                  "velocity Verlet dt 0.005, list checked every step; value from a CUDA graph of "
-                                 "10 steps replayed, eager = the same steps launched from the host",
+                                 "one 100-step md_step call replayed, eager = 2000 steps in one call launched from "
+                                 "the host",
                                  "rebuilds": h.rebuild_count() - c1, "rebuilds_eager": c1 - c0}
     # backward / forward: LJ 2048 atoms x 10 replicas, L = 32, checkpoints every 8
     R, L, K = 10, 32, 8
@@ -404,26 +406,27 @@ def extras(torch, nbcore, wl):
             bwd()
         torch.cuda.synchronize()
         reps = 5
+
+        def trajectory_ms(fn):
+            a, b = ev(), ev()
+            a.record()
+            for _ in range(reps):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+        # whole trajectories without stage events (they add host work to every launch) ...
+        t_f = trajectory_ms(fwd)
+        t_b = trajectory_ms(bwd)
+        # ... and the pair / VJP kernels' own durations from a pass with them
         h.timing_enable(True)
         h.timing_read()
-        e0, e1 = ev(), ev()
-        e0.record()
-        for _ in range(reps):
-            fwd()
-        e1.record()
-        torch.cuda.synchronize()
+        trajectory_ms(fwd)
         st_f = h.timing_read()
-        e2, e3 = ev(), ev()
-        e2.record()
-        for _ in range(reps):
-            bwd()
-        e3.record()
-        torch.cuda.synchronize()
+        trajectory_ms(bwd)
         st_b = h.timing_read()
         h.timing_enable(False)
         h.check()
-        t_f = e0.elapsed_time(e1) / reps
-        t_b = e2.elapsed_time(e3) / reps
         kf = st_f["pair"][0] / max(st_f["pair"][1], 1)
         kb = st_b["pair"][0] / max(st_b["pair"][1], 1)
         _, n_list = h.nl_build(x0, force_rebuild=True)

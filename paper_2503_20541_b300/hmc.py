@@ -29,6 +29,84 @@ import torch
 
 from . import nbcore
 
+# The forward and the adjoint of a proposal are each some hundreds of kernel launches;
+# issued from Python through the autograd engine they make a training iteration
+# host-bound.  With USE_GRAPHS each is captured once per handle and configuration as a
+# CUDA graph over static buffers (inputs copied in, outputs and saved tensors copied out),
+# and replayed: the same kernels on the same data, so the results are bitwise those of
+# the direct calls.
+USE_GRAPHS = True
+
+
+class _TrajectoryGraphs:
+    """Static buffers and CUDA graphs of one handle's HMC forward and adjoint for one
+    configuration (n_leap, kT, ckpt_every, terms, and for the step-statistics variant the
+    per-state outputs).  Graphs are captured on first use, after the inputs are in place
+    (the capture's warm-up runs compute with them)."""
+
+    def __init__(self, h, dev, n_leap, kT, ckpt_every, terms, steps):
+        R, N = h.n_sys, h.n_atoms
+        f32, f64 = torch.float32, torch.float64
+        self.h, self.cfg, self.steps = h, (n_leap, kT, ckpt_every, terms), steps
+        self.w = torch.zeros(N, dtype=f32, device=dev)
+        self.dt = torch.zeros(R, dtype=f32, device=dev)
+        self.x0 = torch.zeros((N, 4), dtype=f32, device=dev)
+        self.xi = torch.zeros((N, 3), dtype=f32, device=dev)
+        self.u = torch.zeros(R, dtype=f64, device=dev)
+        self.l_prop = torch.ones(R, dtype=torch.int32, device=dev)
+        self.x_out = torch.zeros((N, 4), dtype=f32, device=dev)
+        self.stats = torch.zeros((R, 4), dtype=f64, device=dev)
+        self.sst = torch.zeros((n_leap, R, 3), dtype=f64, device=dev) if steps else None
+        self.ck = torch.zeros(nbcore.ckpt_size(N, n_leap, ckpt_every), dtype=f32, device=dev)
+        gshape = (n_leap, R) if steps else (R,)
+        self.ga = torch.zeros(gshape, dtype=f64, device=dev)
+        self.gj = torch.zeros(gshape, dtype=f64, device=dev)
+        self.g_dt = torch.zeros(R, dtype=f64, device=dev)
+        self.g_w = torch.zeros(N, dtype=f32, device=dev)
+        self.fwd = None
+        self.bwd = None
+
+    def run_fwd(self):
+        n_leap, kT, k, terms = self.cfg
+        if self.steps:
+            self.h.hmc_trajectory_steps(self.x0, self.x_out, self.w, self.dt, n_leap, self.l_prop, kT, self.xi,
+                                        self.u, self.stats, self.sst, self.ck, k, terms=terms)
+        else:
+            self.h.hmc_trajectory(self.x0, self.x_out, self.w, self.dt, n_leap, kT, self.xi, self.u, self.stats,
+                                  self.ck, k, terms=terms)
+
+    def run_bwd(self):
+        n_leap, kT, k, terms = self.cfg
+        self.g_dt.zero_()
+        self.g_w.zero_()
+        if self.steps:
+            self.h.hmc_trajectory_steps_backward(self.x0, self.w, self.dt, n_leap, kT, self.xi, self.ck, k,
+                                                 self.sst, self.ga, self.gj, self.g_dt, self.g_w, terms=terms)
+        else:
+            self.h.hmc_trajectory_backward(self.x0, self.w, self.dt, n_leap, kT, self.xi, self.ck, k, self.stats,
+                                           self.ga, self.gj, self.g_dt, self.g_w, terms=terms)
+
+    def forward(self):
+        if self.fwd is None:
+            from .graphs import CapturedStep
+            self.fwd = CapturedStep(self.run_fwd)
+        self.fwd.replay()
+
+    def backward(self):
+        if self.bwd is None:
+            from .graphs import CapturedStep
+            self.bwd = CapturedStep(self.run_bwd)
+        self.bwd.replay()
+
+
+def _graphs(h, dev, n_leap, kT, ckpt_every, terms, steps):
+    cache = h.__dict__.setdefault("_hmc_graphs", {})
+    key = (steps, int(n_leap), float(kT), int(ckpt_every), int(terms), h.n_sys, h.n_atoms)
+    g = cache.get(key)
+    if g is None:
+        g = cache[key] = _TrajectoryGraphs(h, dev, n_leap, kT, ckpt_every, terms, steps)
+    return g
+
 
 class HMCProposal(torch.autograd.Function):
     """(alpha, jump, x_out, accepted) = HMCProposal.apply(w, dt, h, x0, xi, u, n_leap, kT, ckpt_every, terms)
@@ -44,10 +122,17 @@ class HMCProposal(torch.autograd.Function):
         R, N = h.n_sys, h.n_atoms
         wd = w.detach().to(torch.float32).contiguous()
         dtd = dt.detach().to(torch.float32).contiguous()
-        x_out = torch.empty_like(x0)
-        stats = torch.empty((R, 4), dtype=torch.float64, device=x0.device)
-        ck = torch.empty(nbcore.ckpt_size(N, n_leap, ckpt_every), dtype=torch.float32, device=x0.device)
-        h.hmc_trajectory(x0, x_out, wd, dtd, n_leap, kT, xi, u, stats, ck, ckpt_every, terms=terms)
+        if USE_GRAPHS:
+            g = _graphs(h, x0.device, n_leap, kT, ckpt_every, terms, False)
+            for dst, src in ((g.w, wd), (g.dt, dtd), (g.x0, x0), (g.xi, xi), (g.u, u)):
+                dst.copy_(src)
+            g.forward()
+            x_out, stats, ck = g.x_out.clone(), g.stats.clone(), g.ck.clone()
+        else:
+            x_out = torch.empty_like(x0)
+            stats = torch.empty((R, 4), dtype=torch.float64, device=x0.device)
+            ck = torch.empty(nbcore.ckpt_size(N, n_leap, ckpt_every), dtype=torch.float32, device=x0.device)
+            h.hmc_trajectory(x0, x_out, wd, dtd, n_leap, kT, xi, u, stats, ck, ckpt_every, terms=terms)
         ctx.h = h
         ctx.cfg = (n_leap, kT, ckpt_every, terms, w.dtype, dt.dtype)
         ctx.save_for_backward(wd, dtd, x0, xi, ck, stats)
@@ -64,9 +149,18 @@ class HMCProposal(torch.autograd.Function):
         z = torch.zeros(R, dtype=torch.float64, device=x0.device)
         ga = z if g_alpha is None else g_alpha.to(torch.float64).contiguous()
         gj = z if g_jump is None else g_jump.to(torch.float64).contiguous()
-        g_dt = torch.zeros(R, dtype=torch.float64, device=x0.device)
-        g_w = torch.zeros(N, dtype=torch.float32, device=x0.device)
-        h.hmc_trajectory_backward(x0, wd, dtd, n_leap, kT, xi, ck, ckpt_every, stats, ga, gj, g_dt, g_w, terms=terms)
+        if USE_GRAPHS:
+            g = _graphs(h, x0.device, n_leap, kT, ckpt_every, terms, False)
+            for dst, src in ((g.w, wd), (g.dt, dtd), (g.x0, x0), (g.xi, xi), (g.ck, ck), (g.stats, stats),
+                             (g.ga, ga), (g.gj, gj)):
+                dst.copy_(src)
+            g.backward()
+            g_w, g_dt = g.g_w.clone(), g.g_dt.clone()
+        else:
+            g_dt = torch.zeros(R, dtype=torch.float64, device=x0.device)
+            g_w = torch.zeros(N, dtype=torch.float32, device=x0.device)
+            h.hmc_trajectory_backward(x0, wd, dtd, n_leap, kT, xi, ck, ckpt_every, stats, ga, gj, g_dt, g_w,
+                                      terms=terms)
         return (g_w.to(w_dtype), g_dt.to(dt_dtype), None, None, None, None, None, None, None, None)
 
 
@@ -85,11 +179,19 @@ class HMCStepsProposal(torch.autograd.Function):
         R, N = h.n_sys, h.n_atoms
         wd = w.detach().to(torch.float32).contiguous()
         dtd = dt.detach().to(torch.float32).contiguous()
-        x_out = torch.empty_like(x0)
-        stats = torch.empty((R, 4), dtype=torch.float64, device=x0.device)
-        sst = torch.empty((n_leap, R, 3), dtype=torch.float64, device=x0.device)
-        ck = torch.empty(nbcore.ckpt_size(N, n_leap, ckpt_every), dtype=torch.float32, device=x0.device)
-        h.hmc_trajectory_steps(x0, x_out, wd, dtd, n_leap, l_prop, kT, xi, u, stats, sst, ck, ckpt_every, terms=terms)
+        if USE_GRAPHS:
+            g = _graphs(h, x0.device, n_leap, kT, ckpt_every, terms, True)
+            for dst, src in ((g.w, wd), (g.dt, dtd), (g.x0, x0), (g.xi, xi), (g.u, u), (g.l_prop, l_prop)):
+                dst.copy_(src)
+            g.forward()
+            x_out, stats, sst, ck = g.x_out.clone(), g.stats.clone(), g.sst.clone(), g.ck.clone()
+        else:
+            x_out = torch.empty_like(x0)
+            stats = torch.empty((R, 4), dtype=torch.float64, device=x0.device)
+            sst = torch.empty((n_leap, R, 3), dtype=torch.float64, device=x0.device)
+            ck = torch.empty(nbcore.ckpt_size(N, n_leap, ckpt_every), dtype=torch.float32, device=x0.device)
+            h.hmc_trajectory_steps(x0, x_out, wd, dtd, n_leap, l_prop, kT, xi, u, stats, sst, ck, ckpt_every,
+                                   terms=terms)
         ctx.h = h
         ctx.cfg = (n_leap, kT, ckpt_every, terms, w.dtype, dt.dtype)
         ctx.save_for_backward(wd, dtd, x0, xi, ck, sst)
@@ -105,10 +207,18 @@ class HMCStepsProposal(torch.autograd.Function):
         z = torch.zeros((n_leap, R), dtype=torch.float64, device=x0.device)
         ga = z if g_alpha is None else g_alpha.to(torch.float64).contiguous()
         gj = z if g_jump is None else g_jump.to(torch.float64).contiguous()
-        g_dt = torch.zeros(R, dtype=torch.float64, device=x0.device)
-        g_w = torch.zeros(N, dtype=torch.float32, device=x0.device)
-        h.hmc_trajectory_steps_backward(x0, wd, dtd, n_leap, kT, xi, ck, ckpt_every, sst, ga, gj, g_dt, g_w,
-                                        terms=terms)
+        if USE_GRAPHS:
+            g = _graphs(h, x0.device, n_leap, kT, ckpt_every, terms, True)
+            for dst, src in ((g.w, wd), (g.dt, dtd), (g.x0, x0), (g.xi, xi), (g.ck, ck), (g.sst, sst),
+                             (g.ga, ga), (g.gj, gj)):
+                dst.copy_(src)
+            g.backward()
+            g_w, g_dt = g.g_w.clone(), g.g_dt.clone()
+        else:
+            g_dt = torch.zeros(R, dtype=torch.float64, device=x0.device)
+            g_w = torch.zeros(N, dtype=torch.float32, device=x0.device)
+            h.hmc_trajectory_steps_backward(x0, wd, dtd, n_leap, kT, xi, ck, ckpt_every, sst, ga, gj, g_dt, g_w,
+                                            terms=terms)
         return (g_w.to(w_dtype), g_dt.to(dt_dtype), None, None, None, None, None, None, None, None, None)
 
 

@@ -284,6 +284,8 @@ class Handle:
                              if s.pme_grid and s.pme_grid[0] > 0)
 
     def close(self):
+        # graphs captured over this handle's buffers (hmc._TrajectoryGraphs) die with it
+        self.__dict__.pop("_hmc_graphs", None)
         if getattr(self, "_h", None):
             self._lib.nb_destroy(self._h)
             self._h = None
@@ -423,10 +425,21 @@ class Handle:
             _ptr(ckpt, torch.float32, ck_shape, "ckpt", True), int(ckpt_every), int(terms), _stream()),
             "hmc_trajectory")
 
+    def _segment_buffer(self, ckpt_every):
+        """The backward's first call with a larger checkpoint interval than before
+        replaces the library's segment buffer: CUDA graphs captured over the old one
+        (hmc._TrajectoryGraphs with a captured backward) are dropped."""
+        if int(ckpt_every) > self.__dict__.get("_seg_k", 0):
+            self._seg_k = int(ckpt_every)
+            cache = self.__dict__.get("_hmc_graphs", {})
+            for key in [k for k, g in cache.items() if getattr(g, "bwd", None) is not None]:
+                del cache[key]
+
     def hmc_trajectory_backward(self, x0, inv_mass, dt, n_leap, kT, xi, ckpt, ckpt_every, stats, g_alpha, g_jump,
                                 g_dt, g_inv_mass, terms=NB_TERM_LJ | NB_TERM_COUL):
         torch = _torch()
         N = self.n_atoms
+        self._segment_buffer(ckpt_every)
         _ok(self._lib.hmc_trajectory_backward(
             self._h, _ptr(x0, torch.float32, (N, 4), "x0"), _ptr(inv_mass, torch.float32, (N,), "inv_mass"),
             _ptr(dt, torch.float32, (self.n_sys,), "dt"), int(n_leap), float(kT),
@@ -457,6 +470,7 @@ class Handle:
                                       g_jump, g_dt, g_inv_mass, terms=NB_TERM_LJ | NB_TERM_COUL):
         torch = _torch()
         N, R = self.n_atoms, self.n_sys
+        self._segment_buffer(ckpt_every)
         _ok(self._lib.hmc_trajectory_steps_backward(
             self._h, _ptr(x0, torch.float32, (N, 4), "x0"), _ptr(inv_mass, torch.float32, (N,), "inv_mass"),
             _ptr(dt, torch.float32, (R,), "dt"), int(n_leap), float(kT), _ptr(xi, torch.float32, (N, 3), "xi"),

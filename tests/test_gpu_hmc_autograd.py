@@ -104,3 +104,46 @@ def test_training_loop_runs_and_moves_parameters():
     assert hist[-1]["mu"] != hist[0]["mu"]
     assert abs(sum(m * c for m, c in zip(hist[-1]["mass_per_type"], np.bincount(systems[0].types))) -
                systems[0].n) < 1e-9 * systems[0].n
+
+
+def _grads(h, systems, types, xi, eps, u, k):
+    n = systems[0].n
+    log_mu = torch.tensor(math.log(0.005), dtype=torch.float64, device="cuda", requires_grad=True)
+    logits = torch.tensor([0.1, -0.2], dtype=torch.float64, device="cuda", requires_grad=True)
+    dt = hmc.folded_normal_step(log_mu, eps)
+    w = (1.0 / hmc.masses_from_logits(logits, types, float(n))).repeat(R)
+    x0 = torch.cat([dev_xq(s) for s in systems])
+    alpha, jump, x_out, _ = hmc.HMCProposal.apply(w, dt, h, x0, xi, u, N_LEAP, KT, k, nbcore.NB_TERM_LJ)
+    loss = (alpha * jump).mean() / N_LEAP
+    loss.backward()
+    return torch.cat([log_mu.grad.reshape(1), logits.grad, loss.detach().reshape(1)]), x_out
+
+
+def test_graph_replays_equal_direct_calls_across_checkpoint_intervals():
+    """The autograd function replays its forward and adjoint as CUDA graphs: gradients,
+    loss and proposals equal those of the direct library calls bitwise, also after a call
+    with a larger checkpoint interval has replaced the library's segment buffer (the
+    graphs captured over the old buffer are dropped, and captured again)."""
+    systems = _systems()
+    n = systems[0].n
+    rng = np.random.default_rng(9)
+    xi = torch.from_numpy(rng.standard_normal((R * n, 3)).astype(np.float32)).cuda()
+    eps = torch.from_numpy(rng.standard_normal(R)).cuda()
+    u = torch.full((R,), 0.5, dtype=torch.float64, device="cuda")
+    types = torch.from_numpy(systems[0].types.astype(np.int64)).cuda()
+    saved = hmc.USE_GRAPHS
+    try:
+        hmc.USE_GRAPHS = False
+        with nbcore.Handle(systems) as h:
+            ref = {k: _grads(h, systems, types, xi, eps, u, k) for k in (4, 8)}
+            h.check()
+        hmc.USE_GRAPHS = True
+        with nbcore.Handle(systems) as h:
+            # 4 captures over the first segment buffer; 8 replaces it (dropping those graphs)
+            for k in (4, 4, 8, 4, 8):
+                g, x_out = _grads(h, systems, types, xi, eps, u, k)
+                assert torch.equal(g, ref[k][0]), k
+                assert torch.equal(x_out, ref[k][1]), k
+            h.check()
+    finally:
+        hmc.USE_GRAPHS = saved

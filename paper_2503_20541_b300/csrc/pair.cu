@@ -104,13 +104,14 @@ __device__ __forceinline__ void pair_vec(const float4& a, const float4& b, int p
     }
 }
 
-// One queued pair of the force kernel: (dx, dy, dz, r^2) and stencil index lq.
+// One queued pair of the force kernel: (dx, dy, dz, q_j) and stencil index lq (r^2 is
+// recomputed with the operations of the cut-off test, so it is the same value).
 template <bool LJ, int COUL>
 __device__ __forceinline__ void pair_heavy(const float4& q, int lq, const float2& pi, bool do_lj, const PairK& K,
                                            const float4* cand, const float2* par, float qke, float qke_lo,
                                            float alpha, float gau_c, float& fx, float& fy, float& fz, float& elj,
                                            float& edir) {
-    const float r2 = q.w;
+    const float r2 = fmaf(q.z, q.z, fmaf(q.y, q.y, q.x * q.x));
     const float rinv = rsqrtf(r2);
     float fr = 0.f;
     if (LJ && do_lj) {
@@ -125,7 +126,7 @@ __device__ __forceinline__ void pair_heavy(const float4& q, int lq, const float2
     }
     if (COUL == kCoulEwald && K.ke != 0.f) {  // block-uniform: uncharged systems of a mixed batch skip it
         const float r = r2 * rinv;
-        const float qq = qke * cand[lq].w;
+        const float qq = qke * q.w;
         const float ar = alpha * r;
         const float ec = erfcf(ar);
         const float gau = gau_c * __expf(-ar * ar);
@@ -136,7 +137,7 @@ __device__ __forceinline__ void pair_heavy(const float4& q, int lq, const float2
         // The pair energies of water cancel ~10^4-fold in the sum, so a rounding shared by
         // many pairs would dominate its error: ke q_i q_j (two charge values, every pair of a
         // type pair rounded alike) is carried as hi + lo, and so are k and c.
-        const float qj_ = cand[lq].w;
+        const float qj_ = q.w;
         const float qq = qke * qj_;
         const float qq_lo = fmaf(qke_lo, qj_, fmaf(qke, qj_, -qq));
         const float u = fmaf(K.krf, r2, rinv - K.crf) + fmaf(K.krf_lo, r2, -K.crf_lo);
@@ -257,7 +258,7 @@ __device__ __forceinline__ void pair_atom(const CellCtx& C, const PairK& K, int 
             const bool acc = in && r2 < rc2;
             const unsigned bits = __ballot_sync(0xffffffffu, acc);
             const int pos = (head + nq + __popc(bits & lt)) & (kQueue - 1);
-            sts_q_if(qd + pos, qj + pos, make_float4(dx, dy, dz, r2), lk, acc);
+            sts_q_if(qd + pos, qj + pos, make_float4(dx, dy, dz, cj.w), lk, acc);
             nq += __popc(bits);
             if (nq >= 32) {
                 __syncwarp();
@@ -418,10 +419,11 @@ struct VjpAcc {
 };
 
 template <bool LJ, int COUL>
-__device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, const float4& xjq, const float2& pj,
+__device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, const float2& pj,
                                           const float4& li, const float2& pi, float qi, const PairK& K,
                                           float alpha, float a2, float gau_c, VjpAcc& A) {
-    const float dx = q.x, dy = q.y, dz = q.z, r2 = q.w;
+    // q = (dx, dy, dz, q_j); r^2 with the operations of the cut-off test (the same value)
+    const float dx = q.x, dy = q.y, dz = q.z, r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
     const float ux = li.x - lj4.x, uy = li.y - lj4.y, uz = li.z - lj4.z;
     const float du = fmaf(dz, uz, fmaf(dy, uy, dx * ux));
     const float rinv = rsqrtf(r2);
@@ -459,7 +461,7 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, co
     }
     if (COUL == kCoulEwald && K.ke != 0.f) {  // block-uniform: uncharged systems of a mixed batch skip it
         const float r = r2 * rinv;
-        const float qq = K.ke * qi * xjq.w;
+        const float qq = K.ke * qi * q.w;
         const float ar = alpha * r;
         const float ec = erfcf(ar);
         const float gau = gau_c * __expf(-ar * ar);
@@ -467,20 +469,20 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, co
         A.edir = fmaf(qq * ec, rinv, A.edir);
         fr = fmaf(qq, fcu, fr);
         fpr = fmaf(-qq * r2inv, fmaf(3.f, fcu, 2.f * a2 * gau), fpr);
-        A.gq = fmaf(K.ke * xjq.w * fcu, du, A.gq);
+        A.gq = fmaf(K.ke * q.w * fcu, du, A.gq);
     }
     if (COUL == kCoulRF && K.ke != 0.f) {  // Eq. RFA: f = qq (r^-3 - 2k), f'/r = -3 qq r^-5
         const float qke = K.ke * qi;
-        const float qq = qke * xjq.w;
+        const float qq = qke * q.w;
         // energy with ke q_i q_j, k and c as double-float pairs, as in the force kernel
-        const float qq_lo = fmaf(fmaf(K.ke, qi, -qke), xjq.w, fmaf(qke, xjq.w, -qq));
+        const float qq_lo = fmaf(fmaf(K.ke, qi, -qke), q.w, fmaf(qke, q.w, -qq));
         const float r3inv = r2inv * rinv;
         const float fcu = r3inv - 2.f * K.krf;
         const float u = fmaf(K.krf, r2, rinv - K.crf) + fmaf(K.krf_lo, r2, -K.crf_lo);
         A.edir = fmaf(qq, u, fmaf(qq_lo, u, A.edir));
         fr = fmaf(qq, fcu, fr);
         fpr = fmaf(-3.f * qq, r3inv * r2inv, fpr);
-        A.gq = fmaf(K.ke * xjq.w * fcu, du, A.gq);
+        A.gq = fmaf(K.ke * q.w * fcu, du, A.gq);
     }
     const float k2 = fpr * du;
     A.gx = fmaf(fr, ux, fmaf(k2, dx, A.gx));
@@ -535,7 +537,7 @@ __device__ __forceinline__ void vjp_atom(const CellCtx& C, const PairK& K, int N
             const bool acc = in && r2 < rc2;
             const unsigned bits = __ballot_sync(0xffffffffu, acc);
             const int pos = (head + nq + __popc(bits & lt)) & (kQueue - 1);
-            sts_q_if(qd + pos, qj + pos, make_float4(dx, dy, dz, r2), lk, acc);
+            sts_q_if(qd + pos, qj + pos, make_float4(dx, dy, dz, cj.w), lk, acc);
             nq += __popc(bits);
             if (nq >= 32) {
                 __syncwarp();
@@ -543,7 +545,7 @@ __device__ __forceinline__ void vjp_atom(const CellCtx& C, const PairK& K, int N
                 const float4 q = qd[p];
                 const int lq = qj[p];
                 __syncwarp();
-                vjp_heavy<LJ, COUL>(q, lamc[lq], cand[lq], par[lq], li, pi, xr.w, K, alpha, a2, gau_c, A);
+                vjp_heavy<LJ, COUL>(q, lamc[lq], par[lq], li, pi, xr.w, K, alpha, a2, gau_c, A);
                 head = (head + 32) & (kQueue - 1);
                 nq -= 32;
             }
@@ -553,7 +555,7 @@ __device__ __forceinline__ void vjp_atom(const CellCtx& C, const PairK& K, int N
     if (lane < nq) {
         const int p = (head + lane) & (kQueue - 1);
         const int lq = qj[p];
-        vjp_heavy<LJ, COUL>(qd[p], lamc[lq], cand[lq], par[lq], li, pi, xr.w, K, alpha, a2, gau_c, A);
+        vjp_heavy<LJ, COUL>(qd[p], lamc[lq], par[lq], li, pi, xr.w, K, alpha, a2, gau_c, A);
     }
     __syncwarp();
     if (COUL == kCoulEwald && last && alpha > 0.f && H.ne > 0) {

@@ -99,6 +99,12 @@ class _TrajectoryGraphs:
         self.bwd.replay()
 
 
+def _use_graphs():
+    """Graphs unless disabled, or unless the caller is capturing a graph of their own (the
+    direct calls are then recorded into it)."""
+    return USE_GRAPHS and not torch.cuda.is_current_stream_capturing()
+
+
 def _graphs(h, dev, n_leap, kT, ckpt_every, terms, steps):
     cache = h.__dict__.setdefault("_hmc_graphs", {})
     key = (steps, int(n_leap), float(kT), int(ckpt_every), int(terms), h.n_sys, h.n_atoms)
@@ -122,7 +128,7 @@ class HMCProposal(torch.autograd.Function):
         R, N = h.n_sys, h.n_atoms
         wd = w.detach().to(torch.float32).contiguous()
         dtd = dt.detach().to(torch.float32).contiguous()
-        if USE_GRAPHS:
+        if _use_graphs():
             g = _graphs(h, x0.device, n_leap, kT, ckpt_every, terms, False)
             for dst, src in ((g.w, wd), (g.dt, dtd), (g.x0, x0), (g.xi, xi), (g.u, u)):
                 dst.copy_(src)
@@ -149,7 +155,7 @@ class HMCProposal(torch.autograd.Function):
         z = torch.zeros(R, dtype=torch.float64, device=x0.device)
         ga = z if g_alpha is None else g_alpha.to(torch.float64).contiguous()
         gj = z if g_jump is None else g_jump.to(torch.float64).contiguous()
-        if USE_GRAPHS:
+        if _use_graphs():
             g = _graphs(h, x0.device, n_leap, kT, ckpt_every, terms, False)
             for dst, src in ((g.w, wd), (g.dt, dtd), (g.x0, x0), (g.xi, xi), (g.ck, ck), (g.stats, stats),
                              (g.ga, ga), (g.gj, gj)):
@@ -179,7 +185,7 @@ class HMCStepsProposal(torch.autograd.Function):
         R, N = h.n_sys, h.n_atoms
         wd = w.detach().to(torch.float32).contiguous()
         dtd = dt.detach().to(torch.float32).contiguous()
-        if USE_GRAPHS:
+        if _use_graphs():
             g = _graphs(h, x0.device, n_leap, kT, ckpt_every, terms, True)
             for dst, src in ((g.w, wd), (g.dt, dtd), (g.x0, x0), (g.xi, xi), (g.u, u), (g.l_prop, l_prop)):
                 dst.copy_(src)
@@ -207,7 +213,7 @@ class HMCStepsProposal(torch.autograd.Function):
         z = torch.zeros((n_leap, R), dtype=torch.float64, device=x0.device)
         ga = z if g_alpha is None else g_alpha.to(torch.float64).contiguous()
         gj = z if g_jump is None else g_jump.to(torch.float64).contiguous()
-        if USE_GRAPHS:
+        if _use_graphs():
             g = _graphs(h, x0.device, n_leap, kT, ckpt_every, terms, True)
             for dst, src in ((g.w, wd), (g.dt, dtd), (g.x0, x0), (g.xi, xi), (g.ck, ck), (g.sst, sst),
                              (g.ga, ga), (g.gj, gj)):

@@ -192,3 +192,39 @@ def test_batched_256_full_size_sampled():
             h1.check()
         assert np.array_equal(f1.cpu().numpy().astype(np.float64), fk), k
         assert np.array_equal(e1.cpu().numpy()[0], eb[k]), k
+
+
+def test_orthorhombic_water_box_against_the_oracle():
+    """A non-cubic box: the molecules of the lowest 8 of the 10 lattice layers of a 31.05 A
+    water box, in a 31.05 x 31.05 x 24.84 A cell (the lattice period along z, so the
+    spacing across the boundary is regular; a different cell count, image shift and PME
+    mesh size along z): forces, LJ, exclusion, self and reciprocal energies against the FP64 oracle, and the
+    direct-space energy within its FP32 rounding bound (a sum that cancels by ~10^3)."""
+    base = wl.water_box(n_side=10, L=31.05, seed=7, pme_grid=32)
+    m = base.n // 3
+    keep = np.where(base.x.reshape(m, 3, 3)[:, 0, 2] < 8 * 3.105)[0]
+    sel = (3 * keep[:, None] + np.arange(3)).ravel()
+    off, idx = wl.water_exclusions(len(keep))
+    s = wl.System(name="water_slab", x=np.zeros((len(sel), 3), np.float32), q=base.q[sel], sigma=base.sigma[sel],
+                  sqrt_eps=base.sqrt_eps[sel], mass=base.mass[sel], box=np.array([31.05, 31.05, 8 * 3.105]),
+                  r_cut=base.r_cut, r_skin=base.r_skin, alpha=base.alpha, ke=base.ke, pme_grid=(32, 32, 26),
+                  excl_off=off, excl_idx=idx, types=base.types[sel])
+    s.x = np.mod(base.x[sel].astype(np.float64), s.box).astype(np.float32)
+    with nbcore.Handle([s]) as h:
+        f, e = _forces(h, s, terms=nbcore.NB_TERM_ALL)
+    eo, fo = oracle_real_space(s)
+    Ep, Fp = oracle_pme(s)
+    assert rel_rms(f, fo + Fp) <= F_TOL
+    for c in (0, 2, 3):
+        assert abs(e[c] - eo[c]) <= E_TOL * abs(eo[c]), (c, e[c], eo[c])
+    assert abs(e[4] - Ep) <= E_TOL * abs(Ep)
+    # direct space: the random walk of FP32 roundings of the pair terms
+    x = s.x.astype(np.float64)
+    pairs, _ = oracle.neighbor_pairs(x, oracle_params(s), s.r_cut, excl=s.excl)
+    d = x[pairs[:, 0]] - x[pairs[:, 1]]
+    d -= s.box * np.round(d / s.box)
+    r = np.sqrt(np.sum(d * d, axis=1))
+    from scipy.special import erfc
+    t = s.ke * s.q[pairs[:, 0]].astype(np.float64) * s.q[pairs[:, 1]] * erfc(s.alpha * r) / r
+    bound = E_TOL * abs(eo[1]) + 6.0 * np.finfo(np.float32).eps * np.sqrt(np.sum(t * t))
+    assert abs(e[1] - eo[1]) <= bound, (e[1], eo[1], bound)

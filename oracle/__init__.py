@@ -10,6 +10,8 @@ Contents (each cites the passage of the paper it follows):
     mixing, optional switch S(x)) + Ewald direct erfc sum + exclusion correction +
     self energy, or the reaction field (Eq. RFA) instead of the Ewald terms
     (Sec. 2.1.2), in C (oracle.c).
+  * ``nonbonded_cells`` -- the same sums over the candidates of a cell list (Sec. 2.1.2,
+    "Neighborlists"), pinned equal to ``nonbonded``; for CPU timings at large N.
   * ``ewald_recip`` -- exact reciprocal-space structure-factor sum (Sec. 2.1.2).
   * ``neighbor_pairs`` -- brute-force Verlet pair set at r_nl = r_c + r_g.
   * ``force_vjp`` -- analytic pair-Jacobian vector product of the real-space forces.
@@ -120,8 +122,29 @@ def nonbonded_rows(x, q, sigma, sqrt_eps, params, rows, excl=None):
     return er, fr
 
 
+def nonbonded_cells(x, q, sigma, sqrt_eps, params, excl=None):
+    """The quantities of ``nonbonded`` summed per atom over the candidates of a cell list
+    of edge >= r_c (Sec. 2.1.2, "Neighborlists"); all pairs for open or small boxes."""
+    x = _d(x).reshape(-1, 3)
+    n = x.shape[0]
+    q, sigma, sqrt_eps = _d(q), _d(sigma), _d(sqrt_eps)
+    off, idx = _excl(excl, n)
+    e = np.zeros(4)
+    f = np.zeros((n, 3))
+    rc = lib().orc_nonbonded_cells(ctypes.c_int(n), _p(x), _p(q), _p(sigma), _p(sqrt_eps),
+                                   ctypes.byref(params), _p(off), _p(idx), _p(e), _p(f))
+    if rc != 0:
+        raise MemoryError("orc_nonbonded_cells: allocation failed")
+    return e, f
+
+
 def num_threads():
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n):
+    """Threads of the oracle's parallel loops from here on (single-thread timings)."""
+    lib().orc_set_num_threads(ctypes.c_int(int(n)))
 
 
 def ewald_recip(x, q, box, alpha, ke, mmax):

@@ -7,8 +7,10 @@
  * header, table or constant with the CUDA library (paper_2503_20541_b300).
  *
  * Everything here is the literal definition: O(N^2) loops over all atom
- * pairs under the minimum-image convention, no cells, no neighbour lists,
- * no blocking, FP64 throughout.  Pins (closed forms, finite differences,
+ * pairs under the minimum-image convention, no neighbour lists, no blocking,
+ * FP64 throughout.  The one exception, orc_nonbonded_cells, visits only the
+ * candidates of a plain cell list (for CPU timings at large N) and is pinned
+ * equal to the all-pairs routine.  Pins (closed forms, finite differences,
  * lattice sums) live in tests/test_oracle_pins.py.
  *
  * Conventions
@@ -246,6 +248,165 @@ int orc_num_threads(void) {
 #else
     return 1;
 #endif
+}
+
+/* Threads of the parallel loops that follow (for single-thread timings). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/*
+ * Cell-list variant of orc_nonbonded_rows over all atoms, the neighbour search of
+ * Sec. 2.1.2 "Neighborlists" (cells of edge >= r_c, the 27 cells around an atom's cell):
+ * the same pair terms as the row routine, visiting only the candidates the cells can
+ * hold within r_c, plus every excluded partner at any distance.  It is a second route to
+ * the same definition (pinned equal to orc_nonbonded), kept for CPU timings at sizes the
+ * O(N^2) loops cannot reach.  Open systems and boxes with fewer than 3 cells along an
+ * axis take the row routine.  Outputs: f[3 n] (force on every atom) and energy[4] (E_lj,
+ * E_dir, E_excl from the per-atom halves summed in atom order, and E_self), the layout
+ * of orc_nonbonded.
+ */
+int orc_nonbonded_cells(int n, const double* x, const double* q, const double* sig, const double* sqe,
+                        const orc_params* p, const int32_t* ex_off, const int32_t* ex_idx, double* energy,
+                        double* f) {
+    int nc[3];
+    int ok = p->periodic;
+    for (int k = 0; k < 3; ++k) {
+        nc[k] = (int)floor(p->box[k] / p->r_cut);
+        /* a cell edge equal to r_c up to rounding could let a pair inside r_c sit two
+         * cells apart: keep every edge clearly above r_c */
+        while (nc[k] > 0 && p->box[k] / nc[k] < p->r_cut * (1.0 + 1e-9)) --nc[k];
+        if (nc[k] < 3) ok = 0;
+    }
+    double* er = (double*)calloc((size_t)3 * n, sizeof(double));
+    if (!er) return -1;
+    if (!ok) {
+        int32_t* rows = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+        if (!rows) { free(er); return -1; }
+        for (int i = 0; i < n; ++i) rows[i] = i;
+        orc_nonbonded_rows(n, x, q, sig, sqe, p, ex_off, ex_idx, n, rows, er, f);
+        free(rows);
+    } else {
+        const int ncell = nc[0] * nc[1] * nc[2];
+        int* cell = (int*)malloc(sizeof(int) * (size_t)n);
+        int* start = (int*)calloc((size_t)ncell + 1, sizeof(int));
+        int* order = (int*)malloc(sizeof(int) * (size_t)n);
+        /* symmetric partner lists: j is a partner of i if either lists the other */
+        int* pcnt = (int*)calloc((size_t)n + 1, sizeof(int));
+        int n_ex = ex_off ? ex_off[n] : 0;
+        int* pidx = (int*)malloc(sizeof(int) * (size_t)(2 * n_ex + 1));
+        if (!cell || !start || !order || !pcnt || !pidx) {
+            free(er); free(cell); free(start); free(order); free(pcnt); free(pidx);
+            return -1;
+        }
+        for (int i = 0; i < n; ++i) {
+            int c[3];
+            for (int k = 0; k < 3; ++k) {
+                double u = x[3 * i + k] - p->box[k] * floor(x[3 * i + k] / p->box[k]);
+                c[k] = (int)floor(u * nc[k] / p->box[k]);
+                if (c[k] >= nc[k]) c[k] = nc[k] - 1;
+                if (c[k] < 0) c[k] = 0;
+            }
+            cell[i] = (c[2] * nc[1] + c[1]) * nc[0] + c[0];
+            start[cell[i] + 1] += 1;
+        }
+        for (int c = 0; c < ncell; ++c) start[c + 1] += start[c];
+        {
+            int* fill = (int*)malloc(sizeof(int) * (size_t)ncell);
+            if (!fill) { free(er); free(cell); free(start); free(order); free(pcnt); free(pidx); return -1; }
+            memcpy(fill, start, sizeof(int) * (size_t)ncell);
+            for (int i = 0; i < n; ++i) order[fill[cell[i]]++] = i;
+            free(fill);
+        }
+        for (int i = 0; i < n && ex_off; ++i)
+            for (int32_t e = ex_off[i]; e < ex_off[i + 1]; ++e) {
+                pcnt[i + 1] += 1;
+                pcnt[ex_idx[e] + 1] += 1;
+            }
+        for (int i = 0; i < n; ++i) pcnt[i + 1] += pcnt[i];
+        {
+            int* fill = (int*)malloc(sizeof(int) * (size_t)(n + 1));
+            if (!fill) { free(er); free(cell); free(start); free(order); free(pcnt); free(pidx); return -1; }
+            memcpy(fill, pcnt, sizeof(int) * (size_t)(n + 1));
+            for (int i = 0; i < n && ex_off; ++i)
+                for (int32_t e = ex_off[i]; e < ex_off[i + 1]; ++e) {
+                    pidx[fill[i]++] = ex_idx[e];
+                    pidx[fill[ex_idx[e]]++] = i;
+                }
+            free(fill);
+        }
+        const double rc2 = p->r_cut * p->r_cut;
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int i = 0; i < n; ++i) {
+            double fi[3] = {0.0, 0.0, 0.0}, elj = 0.0, edir = 0.0, eex = 0.0;
+            const int c0 = cell[i] % nc[0], c1 = (cell[i] / nc[0]) % nc[1], c2 = cell[i] / (nc[0] * nc[1]);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int a = (c0 + dx + nc[0]) % nc[0], b = (c1 + dy + nc[1]) % nc[1];
+                        const int cc = (((c2 + dz + nc[2]) % nc[2]) * nc[1] + b) * nc[0] + a;
+                        for (int s = start[cc]; s < start[cc + 1]; ++s) {
+                            const int j = order[s];
+                            if (j == i || excluded(i, j, ex_off, ex_idx)) continue;
+                            double d[3];
+                            pair_vec(x, i, j, p, d);
+                            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                            if (!(r2 < rc2)) continue;
+                            double r = sqrt(r2), dU = 0.0;
+                            double eps = sqe[i] * sqe[j], sg = 0.5 * (sig[i] + sig[j]);
+                            if (eps != 0.0) {
+                                double W, dW, d2W, dWs, dWps;
+                                lj_terms(r, sg, eps, p->r_cut, p->r_switch, &W, &dW, &d2W, &dWs, &dWps);
+                                elj += 0.5 * W;
+                                dU += dW;
+                            }
+                            double cq = p->ke * q[i] * q[j];
+                            if (cq != 0.0) {
+                                double g, dg, d2g;
+                                coul_terms(r, p, &g, &dg, &d2g);
+                                edir += 0.5 * cq * g;
+                                dU += cq * dg;
+                            }
+                            double fs = -dU / r;
+                            for (int k = 0; k < 3; ++k) fi[k] += fs * d[k];
+                        }
+                    }
+            /* excluded partners at any distance (each once, however often listed) */
+            for (int e = pcnt[i]; e < pcnt[i + 1]; ++e) {
+                const int j = pidx[e];
+                int seen = 0;
+                for (int e2 = pcnt[i]; e2 < e; ++e2) seen |= pidx[e2] == j;
+                if (seen || j == i) continue;
+                double cq = p->ke * q[i] * q[j];
+                if (cq == 0.0 || !(p->alpha > 0.0)) continue;
+                double d[3];
+                pair_vec(x, i, j, p, d);
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2], r = sqrt(r2);
+                double g, dg, d2g;
+                erfc_terms(r, p->alpha, &g, &dg, &d2g);
+                eex += 0.5 * cq * (g - 1.0 / r);
+                double fs = -(cq * (dg + 1.0 / r2)) / r;
+                for (int k = 0; k < 3; ++k) fi[k] += fs * d[k];
+            }
+            for (int k = 0; k < 3; ++k) f[3 * i + k] = fi[k];
+            er[3 * i + 0] = elj;
+            er[3 * i + 1] = edir;
+            er[3 * i + 2] = eex;
+        }
+        free(cell); free(start); free(order); free(pcnt); free(pidx);
+    }
+    energy[0] = energy[1] = energy[2] = energy[3] = 0.0;
+    for (int i = 0; i < n; ++i) {
+        for (int k = 0; k < 3; ++k) energy[k] += er[3 * i + k];
+        energy[3] += q[i] * q[i];
+    }
+    energy[3] *= -p->ke * p->alpha / sqrt(ORC_PI);
+    free(er);
+    return 0;
 }
 
 /*

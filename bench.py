@@ -87,6 +87,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--cpu-sweep", action="store_true",
+                    help="time the FP64 oracle's real-space sum over system size on the host cores and exit")
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
     return a
@@ -187,29 +189,56 @@ def pair_counts(nbcore, wl, s, torch):
     return {"list": n_list, "cutoff": n_cut, "cutoff_lj": n_cut_lj, "excluded": n_excl}
 
 
-def cpu_baseline(s, n_cut, repeats=3):
-    """The FP64 oracle as it stands, timed on the host cores: every row of the
-    all-pairs real-space sum plus the full FP64 smooth PME, best of `repeats`."""
+def _best(fn, repeats):
+    best = None
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        fn()
+        t = time.perf_counter() - t0
+        best = t if best is None else min(best, t)
+    return best
+
+
+def cpu_baseline(s, n_cut, repeats=3, row_stride=16):
+    """The FP64 oracle as it stands, timed on the host cores, best of `repeats` each:
+    the full force evaluation (real-space sum over the oracle's cell list + the full FP64
+    smooth PME) on all cores, which is `value`; the same with the all-pairs real-space sum;
+    and both real-space routes on one thread (all pairs on every `row_stride`-th row,
+    scaled by `row_stride`, since rows are independent)."""
     import oracle
     from oracle import pme as opme
     p = oracle.make_params(s.box, r_cut=s.r_cut, alpha=s.alpha, ke=s.ke)
     x = s.x.astype(np.float64)
+    q64 = s.q.astype(np.float64)
     rows = np.arange(s.n)
-    best = None
-    for _ in range(repeats):
-        t0 = time.perf_counter()
-        oracle.nonbonded_rows(x, s.q, s.sigma, s.sqrt_eps, p, rows, excl=s.excl)
-        opme.pme(x, s.q.astype(np.float64), s.box, s.alpha, s.ke, s.pme_grid)
-        t = time.perf_counter() - t0
-        best = t if best is None else min(best, t)
-    return {"value": n_cut / best, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "full force evaluation of the 24,000-atom box: all 24,000 rows of the FP64 all-pairs "
-                      "real-space sum (OpenMP over rows) + the full FP64 smooth PME (numpy FFT); best of %d, "
-                      "%.2f s each" % (repeats, best)}
+    cores = oracle.num_threads()
+    t_pme = _best(lambda: opme.pme(x, q64, s.box, s.alpha, s.ke, s.pme_grid), repeats)
+    t_cells = _best(lambda: oracle.nonbonded_cells(x, s.q, s.sigma, s.sqrt_eps, p, excl=s.excl), repeats)
+    t_all = _best(lambda: oracle.nonbonded_rows(x, s.q, s.sigma, s.sqrt_eps, p, rows, excl=s.excl), repeats)
+    oracle.set_num_threads(1)
+    try:
+        t_cells1 = _best(lambda: oracle.nonbonded_cells(x, s.q, s.sigma, s.sqrt_eps, p, excl=s.excl), repeats)
+        t_all1 = row_stride * _best(lambda: oracle.nonbonded_rows(x, s.q, s.sigma, s.sqrt_eps, p,
+                                                                  rows[::row_stride], excl=s.excl), repeats)
+    finally:
+        oracle.set_num_threads(cores)
+    t = t_cells + t_pme
+    return {"value": n_cut / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "full force evaluation of the 24,000-atom box: the FP64 real-space sum over the oracle's "
+                      "cell list (OpenMP over atoms, %.3f s) + the full FP64 smooth PME (numpy FFT, %.3f s); "
+                      "best of %d each" % (t_cells, t_pme, repeats),
+            "all_pairs": {"value": n_cut / (t_all + t_pme), "real_space_s": t_all,
+                          "note": "the same evaluation with the O(N^2) all-pairs real-space sum"},
+            "single_thread": {"cell_list_real_space_s": t_cells1, "all_pairs_real_space_s": t_all1,
+                              "cell_list_value": n_cut / (t_cells1 + t_pme),
+                              "all_pairs_value": n_cut / (t_all1 + t_pme),
+                              "note": "one OpenMP thread; all pairs timed on every %dth row x %d"
+                                      % (row_stride, row_stride)}}
 
 
 def run_reference(args):
-    """CPU reference arm: the FP64 oracle, each step a bounded sample of the same workload."""
+    """CPU reference arm: the FP64 oracle, each step one full force evaluation of the
+    workload (cell-list real-space sum on all host cores + the full FP64 smooth PME)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -219,38 +248,69 @@ def run_reference(args):
     s = wl.water_box()
     p = oracle.make_params(s.box, r_cut=s.r_cut, alpha=s.alpha, ke=s.ke)
     x = s.x.astype(np.float64)
-    frac = 4
-    rows = np.arange(0, s.n, frac)
-    # in-cutoff pair count of the workload (unordered, exclusions removed), by brute force
-    n_cut = 0
-    for i0 in range(0, s.n, 2000):
-        d = x[i0:i0 + 2000, None, :] - x[None, :, :]
-        d -= s.box * np.round(d / s.box)
-        r2 = np.einsum("ijk,ijk->ij", d, d)
-        n_cut += int(np.count_nonzero(r2 < s.r_cut ** 2)) - min(2000, s.n - i0)
-    n_cut = (n_cut - 2 * 3 * (s.n // 3)) // 2
+    q64 = s.q.astype(np.float64)
+    n_cut = cutoff_pairs_kdtree(s)
 
     def step():
         t0 = time.perf_counter()
-        oracle.nonbonded_rows(x, s.q, s.sigma, s.sqrt_eps, p, rows, excl=s.excl)
-        t_rows = time.perf_counter() - t0
-        t1 = time.perf_counter()
-        opme.pme(x, s.q.astype(np.float64), s.box, s.alpha, s.ke, s.pme_grid)
-        return t_rows * frac + (time.perf_counter() - t1)
+        oracle.nonbonded_cells(x, s.q, s.sigma, s.sqrt_eps, p, excl=s.excl)
+        opme.pme(x, q64, s.box, s.alpha, s.ke, s.pme_grid)
+        return time.perf_counter() - t0
     for _ in range(args.warmup):
         step()
     ts = [step() for _ in range(args.steps)]
     ms = 1e3 * float(np.mean(ts))
     v = n_cut / (ms / 1e3)
     cores = oracle.num_threads()
-    sample = ("every %dth of the 24,000 rows of the FP64 all-pairs real-space sum (time x %d) + the full FP64 "
-              "smooth PME, per step" % (frac, frac))
+    sample = ("one full force evaluation of the 24,000-atom box per step: the FP64 real-space sum over the "
+              "oracle's cell list (OpenMP over atoms) + the full FP64 smooth PME")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "cpu host cores"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def cutoff_pairs_kdtree(s):
+    """Unordered in-cutoff pairs of a water system (r < r_c; the three intramolecular
+    exclusions per molecule removed), counted with scipy's periodic KD-tree."""
+    from scipy.spatial import cKDTree
+    tr = cKDTree(np.mod(s.x.astype(np.float64), s.box), boxsize=s.box)
+    return int((tr.count_neighbors(tr, s.r_cut) - s.n) // 2 - 3 * (s.n // 3))
+
+
+def run_cpu_sweep(args):
+    """The oracle's real-space sum on the host cores over system size: all pairs up to
+    32,000 atoms, the cell list at every size, each on one thread and on all cores, best
+    of 3.  One JSON line per (route, size, threads); no GPU is touched."""
+    import oracle
+    from paper_2503_20541_b300 import workloads as wl
+    cores = oracle.num_threads()
+    sizes = (1000, 8000, 10666, 64000, 512000)  # molecules: 3k .. 1.54M atoms
+    for n_mol in sizes:
+        s = wl.water_box_density(n_mol, seed=1234)
+        p = oracle.make_params(s.box, r_cut=s.r_cut, alpha=s.alpha, ke=s.ke)
+        x = s.x.astype(np.float64)
+        n_cut = cutoff_pairs_kdtree(s)
+        for threads in (1, cores):
+            oracle.set_num_threads(threads)
+            runs = []
+            if s.n <= 32000:
+                stride = 16 if threads == 1 else 1
+                rows = np.arange(0, s.n, stride)
+                runs.append(("all_pairs", stride, lambda: oracle.nonbonded_rows(
+                    x, s.q, s.sigma, s.sqrt_eps, p, rows, excl=s.excl)))
+            if threads > 1 or s.n <= 200000:
+                runs.append(("cell_list", 1, lambda: oracle.nonbonded_cells(
+                    x, s.q, s.sigma, s.sqrt_eps, p, excl=s.excl)))
+            for route, stride, fn in runs:
+                t = stride * _best(fn, 3)
+                print(json.dumps({"impl": "oracle", "route": route, "atoms": s.n, "threads": threads,
+                                  "real_space_s": t, "pairs_in_cutoff": n_cut, "value": n_cut / t, "unit": UNIT,
+                                  "sample": "every %dth row x %d" % (stride, stride) if stride > 1 else "all atoms"}),
+                      flush=True)
+        oracle.set_num_threads(cores)
 
 
 def flops_per_launch(pc):
@@ -1005,6 +1065,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.cpu_sweep:
+        run_cpu_sweep(args)
         return
     rank, world, local = dist_env()
     import torch

@@ -130,7 +130,10 @@ __device__ __forceinline__ void pair_heavy(const float4& q, int lq, const float2
         const float ar = alpha * r;
         const float ec = erfcf(ar);
         const float gau = gau_c * __expf(-ar * ar);
-        edir = fmaf(qq * ec, rinv, edir);
+        // the energy is summed per unit ke q_i (q_j erfc(alpha r)/r) and scaled once per
+        // atom: ke q_i q_j, rounded alike for every pair of two atom types, would make its
+        // rounding add linearly over a sum that cancels ~10^3-fold
+        edir = fmaf(q.w * ec, rinv, edir);
         fr = fmaf(qq * fmaf(ec, rinv, gau), rinv * rinv, fr);
     }
     if (COUL == kCoulRF && K.ke != 0.f) {  // Eq. RFA: qq (1/r + k r^2 - c), f = qq (1/r^3 - 2k)
@@ -311,7 +314,7 @@ __device__ __forceinline__ void pair_atom(const CellCtx& C, const PairK& K, int 
             const float ar = alpha * r;
             const float ef = erff(ar);
             const float gau = gau_c * __expf(-ar * ar);
-            eex = fmaf(-qq * ef, rinv, eex);
+            eex = fmaf(-qj_ * ef, rinv, eex);  // per unit ke q_i, as edir
             const float fr = qq * (gau - ef * rinv) * r2inv;
             fx = fmaf(fr, dx, fx);
             fy = fmaf(fr, dy, fy);
@@ -347,6 +350,11 @@ __device__ __forceinline__ void pair_atom(const CellCtx& C, const PairK& K, int 
             red_add(ffix + i, to_fix(fx, scale, flags + 1));
             red_add(ffix + (size_t)N + i, to_fix(fy, scale, flags + 1));
             red_add(ffix + 2 * (size_t)N + i, to_fix(fz, scale, flags + 1));
+            if (COUL == kCoulEwald) {  // ke q_i = qke + (ke q_i - qke) exactly: one rounding per atom
+                const float lo = fmaf(K.ke, xr.w, -qke);
+                edir = fmaf(qke, edir, lo * edir);
+                eex = fmaf(qke, eex, lo * eex);
+            }
             e_atom[i] = make_float4(0.5f * elj, 0.5f * edir, 0.5f * eex, 0.f);
         }
     }
@@ -466,7 +474,7 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, co
         const float ec = erfcf(ar);
         const float gau = gau_c * __expf(-ar * ar);
         const float fcu = fmaf(ec, rinv, gau) * r2inv;  // f per unit qq
-        A.edir = fmaf(qq * ec, rinv, A.edir);
+        A.edir = fmaf(q.w * ec, rinv, A.edir);          // per unit ke q_i, as in the force kernel
         fr = fmaf(qq, fcu, fr);
         fpr = fmaf(-qq * r2inv, fmaf(3.f, fcu, 2.f * a2 * gau), fpr);
         A.gq = fmaf(K.ke * q.w * fcu, du, A.gq);
@@ -591,7 +599,7 @@ __device__ __forceinline__ void vjp_atom(const CellCtx& C, const PairK& K, int N
             const float ef = erff(ar);
             const float gau = gau_c * __expf(-ar * ar);
             const float fxu = (gau - ef * rinv) * r2inv;  // f per unit qq
-            A.eex = fmaf(-qq * ef, rinv, A.eex);
+            A.eex = fmaf(-xj.w * ef, rinv, A.eex);  // per unit ke q_i
             const float fr = qq * fxu;
             const float fpr = -qq * r2inv * fmaf(3.f, fxu, 2.f * a2 * gau);
             A.gq = fmaf(K.ke * xj.w * fxu, du, A.gq);
@@ -626,6 +634,11 @@ __device__ __forceinline__ void vjp_atom(const CellCtx& C, const PairK& K, int N
             ffix[i] = to_fix(v[0], scale, flags + 1);
             ffix[(size_t)N + i] = to_fix(v[1], scale, flags + 1);
             ffix[2 * (size_t)N + i] = to_fix(v[2], scale, flags + 1);
+            if (COUL == kCoulEwald) {  // ke q_i as hi + lo, as in the force kernel
+                const float qke = K.ke * xr.w, lo = fmaf(K.ke, xr.w, -qke);
+                v[4] = fmaf(qke, v[4], lo * v[4]);
+                v[5] = fmaf(qke, v[5], lo * v[5]);
+            }
             e_atom[i] = make_float4(0.5f * v[3], 0.5f * v[4], 0.5f * v[5], 0.f);
             gx_s[i] = make_float4(v[6], v[7], v[8], v[9]);
             gp_s[i] = make_float2(v[10], v[11]);

@@ -247,3 +247,43 @@ def test_batched_256_every_system_every_atom():
         except AssertionError as err:
             problems.append(str(err).splitlines()[0][:200])
     assert not problems, problems
+
+
+def test_force_vjp_water_24k_every_atom():
+    """The force vector-Jacobian product on the full 24,000-atom box: (dF/dx)^T lam and the
+    gradients of lam.F with respect to the charges, sigma and sqrt(eps) of every atom,
+    real space (LJ + Ewald direct + exclusion correction) against the FP64 oracle (all
+    pairs), and with the PME part added against the oracle's FP64 PME VJP on the same
+    mesh (the reciprocal part alone too, as it is small next to real space)."""
+    from oracle import pme as opme
+    s = wl.water_box()
+    rng = np.random.default_rng(24)
+    lam = rng.standard_normal((s.n, 3)).astype(np.float32)
+    xq = dev_xq(s)
+    lam_d = torch.from_numpy(lam).cuda()
+    out = {}
+    with nbcore.Handle([s]) as h:
+        for name, terms in (("real", nbcore.NB_TERM_LJ | nbcore.NB_TERM_COUL), ("all", nbcore.NB_TERM_ALL),
+                            ("pme", nbcore.NB_TERM_PME)):
+            g = [torch.empty((s.n, 3), dtype=torch.float32, device="cuda")] + \
+                [torch.empty(s.n, dtype=torch.float32, device="cuda") for _ in range(3)]
+            h.nonbonded_force_vjp(xq, lam_d, g[0], g[1], g[2], g[3], terms=terms)
+            h.check()
+            out[name] = [t.cpu().numpy().astype(np.float64) for t in g]
+    x64 = s.x.astype(np.float64)
+    gxo, gqo, gso, geo = oracle.force_vjp(x64, s.q, s.sigma, s.sqrt_eps, oracle_params(s), lam, excl=s.excl)
+    gxk, gqk = opme.pme_force_vjp(x64, s.q.astype(np.float64), s.box, s.alpha, s.ke, s.pme_grid,
+                                  lam.astype(np.float64))
+    gx, gq, gs, ge = out["real"]
+    o = s.sqrt_eps > 0  # LJ parameters exist on oxygen only
+    assert rel_rms(gx, gxo) <= F_TOL
+    assert rel_rms(gq, gqo) <= F_TOL
+    assert rel_rms(gs[o], gso[o]) <= F_TOL
+    assert rel_rms(ge, geo) <= F_TOL
+    err = np.linalg.norm(gx - gxo, axis=1)
+    rms = np.sqrt(np.mean(np.sum(gxo * gxo, axis=1)))
+    assert err.max() <= F_ATOM_TOL * rms, (int(np.argmax(err)), err.max(), rms)
+    assert rel_rms(out["all"][0], gxo + gxk) <= F_TOL
+    assert rel_rms(out["all"][1], gqo + gqk) <= F_TOL
+    assert rel_rms(out["pme"][0], gxk) <= 1e-4
+    assert rel_rms(out["pme"][1], gqk) <= 1e-4

@@ -311,6 +311,52 @@ def run_cpu_sweep(args):
                                   "sample": "every %dth row x %d" % (stride, stride) if stride > 1 else "all atoms"}),
                       flush=True)
         oracle.set_num_threads(cores)
+    run_cpu_dynamics(cores)
+
+
+def run_cpu_dynamics(cores):
+    """The oracle's dynamics on the host cores, best of 3, on one thread and on all cores:
+    100 velocity-Verlet steps of the 864-atom LJ fluid (dt 0.005), and one ESJD loss of the
+    differentiable-HMC configuration (10 replicas of 2048 LJ atoms with the LJ switch on
+    2.2-2.5, 32 leapfrog steps, dt 0.005, kT 1); its finite-difference gradient in dt costs three such losses, reported as 3x
+    the timed loss.  Forces from the oracle's cell-list route."""
+    import oracle
+    from oracle import dynamics as odyn
+    from paper_2503_20541_b300 import workloads as wl
+
+    def force_energy_of(s):
+        p = oracle.make_params(s.box, r_cut=s.r_cut, r_switch=s.r_switch)
+        zq = np.zeros(s.n)
+
+        def fe(x):
+            e, f = oracle.nonbonded_cells(x, zq, s.sigma, s.sqrt_eps, p)
+            return f, float(np.sum(e))
+        return fe
+    s1 = wl.lj_fcc()
+    fe1 = force_energy_of(s1)
+    w1 = 1.0 / s1.mass.astype(np.float64)
+    x1, v1 = s1.x.astype(np.float64), s1.v.astype(np.float64)
+    reps = []
+    for r in range(10):  # the replicas of the GPU configuration: own seeds, switch 2.2-2.5
+        sr = wl.lj_random(2048, seed=100 + r, n_types=2)
+        sr.r_switch = 2.2
+        reps.append((sr, force_energy_of(sr), 1.0 / sr.mass.astype(np.float64), sr.x.astype(np.float64)))
+    xi, _ = wl.hmc_randoms(10, 2048, seed=4)
+
+    def loss4():
+        props = [odyn.hmc_proposal(x, xi[r], w, 0.005, 32, 1.0, fe, sr.box) for r, (sr, fe, w, x) in enumerate(reps)]
+        return odyn.esjd_loss([q["alpha"] for q in props], [q["jump"] for q in props], 32)
+    for threads in (1, cores):
+        oracle.set_num_threads(threads)
+        t1 = _best(lambda: odyn.velocity_verlet(x1, v1, w1, 0.005, 100, fe1), 3)
+        print(json.dumps({"impl": "oracle", "route": "md_velocity_verlet", "workload": "LJ fluid 864 atoms, "
+                          "100 steps", "threads": threads, "seconds": t1, "value": 100 / t1, "unit": "MD steps/s"}),
+              flush=True)
+        t4 = _best(loss4, 3)
+        print(json.dumps({"impl": "oracle", "route": "hmc_esjd_loss_fd_gradient", "workload": "LJ fluid 2048 "
+                          "atoms x 10 replicas, 32 leapfrog steps", "threads": threads, "loss_seconds": t4,
+                          "loss_and_fd_gradient_seconds": 3 * t4, "unit": "s"}), flush=True)
+    oracle.set_num_threads(cores)
 
 
 def flops_per_launch(pc):

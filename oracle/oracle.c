@@ -273,6 +273,8 @@ void orc_set_num_threads(int n) {
 int orc_nonbonded_cells(int n, const double* x, const double* q, const double* sig, const double* sqe,
                         const orc_params* p, const int32_t* ex_off, const int32_t* ex_idx, double* energy,
                         double* f) {
+    energy[0] = energy[1] = energy[2] = energy[3] = 0.0;
+    if (n <= 0) return 0;
     int nc[3];
     int ok = p->periodic;
     for (int k = 0; k < 3; ++k) {
@@ -399,7 +401,6 @@ int orc_nonbonded_cells(int n, const double* x, const double* q, const double* s
         }
         free(cell); free(start); free(order); free(pcnt); free(pidx);
     }
-    energy[0] = energy[1] = energy[2] = energy[3] = 0.0;
     for (int i = 0; i < n; ++i) {
         for (int k = 0; k < 3; ++k) energy[k] += er[3 * i + k];
         energy[3] += q[i] * q[i];

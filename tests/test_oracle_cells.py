@@ -97,3 +97,13 @@ def test_cells_fall_back_to_all_pairs_for_open_and_small_boxes():
     _agree(*_both(x, s.q, s.sigma, s.sqrt_eps, p3, excl=s.excl))
     po = oracle.make_params(s.box, r_cut=4.6, alpha=0.8, ke=wl.KE_KJ_MOL_A, periodic=False)
     _agree(*_both(x, s.q, s.sigma, s.sqrt_eps, po, excl=s.excl))
+
+
+def test_cells_of_an_empty_and_a_single_atom_system():
+    p = oracle.make_params(20.0, r_cut=2.5, alpha=0.5, ke=1.0)
+    e, f = oracle.nonbonded_cells(np.zeros((0, 3)), np.zeros(0), np.zeros(0), np.zeros(0), p)
+    assert f.shape == (0, 3) and np.all(e == 0.0)
+    e, f = oracle.nonbonded_cells(np.array([[1.0, 2.0, 3.0]]), np.array([0.7]), np.ones(1), np.ones(1), p)
+    e0, f0 = oracle.nonbonded(np.array([[1.0, 2.0, 3.0]]), np.array([0.7]), np.ones(1), np.ones(1), p)
+    np.testing.assert_array_equal(f, f0)
+    np.testing.assert_allclose(e, e0, rtol=1e-15)

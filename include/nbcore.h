@@ -400,7 +400,8 @@ nb_status nonbonded_force_vjp(nb_handle* h, const float* xq, const float* lam, f
  * code that must not trigger the device-wide synchronisation an allocation can cause.
  * Every handle-based call in this header needs nb_create, which allocates; this one needs
  * no handle.  It computes the same mesh as pme_spread for one periodic system:
- *   xq [n_atoms][4]   (device) positions and charges.
+ *   xq [n_atoms][4]   (device) positions and charges; may be NULL when n_atoms is 0,
+ *                     which gives an all-zero mesh.
  *   box[3] (host)     box edge lengths;  mesh[3] (host) K0, K1, K2, each >= 4.
  *   grid              (device, caller-owned) float[K0*K1*K2], index ((k0*K1)+k1)*K2+k2.
  * Its int64 accumulation mesh is a library-owned static device array of

@@ -688,7 +688,8 @@ __global__ void k_static_mesh_out(long long n, const long long* __restrict__ mes
 extern "C" nb_status pme_spread_static(const float* xq, int32_t n_atoms, const double* box, const int32_t* mesh,
                                        float* grid, void* stream) {
     using namespace nb;
-    if (!xq || !grid || !box || !mesh || n_atoms < 0) return NB_ERR_ARG;
+    // an empty system reads no positions: xq may then be NULL (its mesh is all zeros)
+    if ((!xq && n_atoms > 0) || !grid || !box || !mesh || n_atoms < 0) return NB_ERR_ARG;
     long long npts = 1;
     for (int d = 0; d < 3; ++d) {
         if (!(box[d] > 0.0) || !std::isfinite(box[d]) || mesh[d] < 4) return NB_ERR_ARG;

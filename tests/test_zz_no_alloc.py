@@ -6,8 +6,8 @@ device-wide synchronisation of an allocation is not allowed.  pme_spread_static
 serves them without a handle, keeping its accumulation mesh in a static device
 array.  This file checks, through the C ABI, that two calls in a row each give the
 same mesh as the handle-based pme_spread (within the tolerance of the PME spread
-test) -- so the shared static mesh is cleared between calls -- and that a mesh
-above the static capacity is refused.  It sits in its own file, collected last.
+test) -- so the shared static mesh is cleared between calls -- that an empty
+system gives an all-zero mesh, and that a mesh above the static capacity is refused.  It sits in its own file, collected last.
 """
 import numpy as np
 import pytest
@@ -51,3 +51,18 @@ def test_static_spread_rejects_meshes_beyond_its_capacity():
     with pytest.raises(nbcore.NbError) as ei:
         nbcore.pme_spread_static(xq, s.box, K, grid)
     assert ei.value.status == 1
+
+
+def test_static_spread_of_an_empty_system_is_an_all_zero_mesh():
+    # an empty system spreads no charge; the call after a non-empty one also shows that
+    # the previous call's sums left in the shared static mesh do not reach the output
+    s = wl.water_box(n_side=4, L=12.42, seed=2, pme_grid=16)
+    K = s.pme_grid
+    g = torch.empty(int(np.prod(K)), dtype=torch.float32, device="cuda")
+    nbcore.pme_spread_static(dev_xq(s), s.box, K, g)
+    assert torch.count_nonzero(g).item() > 0
+    empty = torch.empty((0, 4), dtype=torch.float32, device="cuda")
+    g.fill_(float("nan"))
+    nbcore.pme_spread_static(empty, s.box, K, g)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(g).item() == 0

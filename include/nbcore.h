@@ -406,11 +406,13 @@ nb_status nonbonded_force_vjp(nb_handle* h, const float* xq, const float* lam, f
  *   grid              (device, caller-owned) float[K0*K1*K2], index ((k0*K1)+k1)*K2+k2.
  * Its int64 accumulation mesh is a library-owned static device array of
  * NB_STATIC_MESH_MAX points (8 MiB on every GPU that loads the library, held until the
- * process exits); K0*K1*K2 > NB_STATIC_MESH_MAX returns NB_ERR_ARG.  The first call on a
- * device looks the array's address up (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Every call clears the part of the array it uses and shares the array
- * with every other call: calls whose executions overlap on the GPU (several streams, or
- * several host threads) race and corrupt each other's result.
+ * process exits); a mesh of more points (K0*K1*K2 > NB_STATIC_MESH_MAX, any Kd above it
+ * included) returns NB_ERR_ARG before any GPU work.  Every call looks the array's address
+ * up in the current context (cudaGetSymbolAddress, which allocates nothing), so a device
+ * reset between calls is harmless; the first call on a device may load the library's GPU
+ * code, so make it before any stream capture.  Every call clears the part of the array it
+ * uses and shares the array with every other call: calls whose executions overlap on the
+ * GPU (several streams, or several host threads) race and corrupt each other's result.
  */
 #define NB_STATIC_MESH_MAX (1 << 20)
 nb_status pme_spread_static(const float* xq, int32_t n_atoms, const double* box, const int32_t* mesh,

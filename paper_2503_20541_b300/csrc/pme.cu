@@ -14,7 +14,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 
 #include "common.cuh"
 
@@ -623,24 +622,14 @@ namespace {
 
 static __device__ __align__(256) long long g_static_mesh[NB_STATIC_MESH_MAX];
 
-constexpr int kMaxDevices = 256;
-std::mutex g_static_mu;
-long long* g_static_mesh_ptr[kMaxDevices] = {};
-
-// Device address of g_static_mesh on the current device, looked up once per device.
+// Device address of g_static_mesh in the current context.  It is looked up on every call
+// (the lookup allocates nothing): an address kept from an earlier call would be stale after
+// cudaDeviceReset or once a new primary context is created on the device.
 cudaError_t static_mesh_address(long long** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_mesh);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_mesh_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_mesh);
-        if (e != cudaSuccess) return e;
-        g_static_mesh_ptr[dev] = static_cast<long long*>(p);
-    }
-    *out = g_static_mesh_ptr[dev];
+    *out = static_cast<long long*>(p);
     return cudaSuccess;
 }
 
@@ -690,12 +679,14 @@ extern "C" nb_status pme_spread_static(const float* xq, int32_t n_atoms, const d
     using namespace nb;
     // an empty system reads no positions: xq may then be NULL (its mesh is all zeros)
     if ((!xq && n_atoms > 0) || !grid || !box || !mesh || n_atoms < 0) return NB_ERR_ARG;
+    // each factor is checked against the capacity before it is multiplied in, so the
+    // product cannot wrap (three sizes up to 2^31 would overflow 64 bits)
     long long npts = 1;
     for (int d = 0; d < 3; ++d) {
-        if (!(box[d] > 0.0) || !std::isfinite(box[d]) || mesh[d] < 4) return NB_ERR_ARG;
+        if (!(box[d] > 0.0) || !std::isfinite(box[d]) || mesh[d] < 4 || mesh[d] > NB_STATIC_MESH_MAX) return NB_ERR_ARG;
         npts *= mesh[d];
+        if (npts > NB_STATIC_MESH_MAX) return NB_ERR_ARG;
     }
-    if (npts > NB_STATIC_MESH_MAX) return NB_ERR_ARG;
     long long* scratch = nullptr;
     if (static_mesh_address(&scratch) != cudaSuccess) return NB_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

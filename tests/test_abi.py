@@ -68,3 +68,17 @@ def test_workload_scalars_are_fp32_exact():
     for s in (wl.water_box(), wl.lj_fcc(), wl.lj_random(500)):
         for v in list(s.box) + [s.r_cut, s.r_skin, s.alpha, s.ke]:
             assert float(np.float32(v)) == v
+
+
+@pytest.mark.parametrize("mesh", [(1 << 22, 1 << 21, 1 << 21), (1 << 21, 1 << 21, 1 << 21), (2048, 1024, 1024),
+                                  (1 << 30, 4, 4), (4, 4, (1 << 20) + 1)])
+def test_static_spread_refuses_oversized_meshes_before_any_gpu_work(mesh):
+    """pme_spread_static checks every mesh size against its static capacity before it
+    multiplies them (a product of three int32 sizes can wrap to 0) and before any device
+    call, so the refusal needs no GPU; the pointers are never dereferenced."""
+    from paper_2503_20541_b300 import nbcore
+    lib = nbcore.load()
+    box = np.array([10.0, 10.0, 10.0])
+    m = np.array(mesh, np.int32)
+    dummy = ctypes.c_void_p(16)
+    assert lib.pme_spread_static(dummy, 4, box.ctypes.data, m.ctypes.data, dummy, None) == 1

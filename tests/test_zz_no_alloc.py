@@ -6,13 +6,19 @@ device-wide synchronisation of an allocation is not allowed.  pme_spread_static
 serves them without a handle, keeping its accumulation mesh in a static device
 array.  This file checks, through the C ABI, that two calls in a row each give the
 same mesh as the handle-based pme_spread (within the tolerance of the PME spread
-test) -- so the shared static mesh is cleared between calls -- that an empty
-system gives an all-zero mesh, and that a mesh above the static capacity is refused.  It sits in its own file, collected last.
+test) -- so the shared static mesh is cleared between calls -- that its mesh equals the
+FP64 oracle's charge mesh, that an empty system gives an all-zero mesh, and that a mesh
+above the static capacity is refused, also when the product of its sizes would wrap.
+It sits in its own file, collected last.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
 from paper_2503_20541_b300 import nbcore, workloads as wl
+
+from oracle import pme as opme
 
 from _helpers import dev_xq
 
@@ -51,6 +57,34 @@ def test_static_spread_rejects_meshes_beyond_its_capacity():
     with pytest.raises(nbcore.NbError) as ei:
         nbcore.pme_spread_static(xq, s.box, K, grid)
     assert ei.value.status == 1
+
+
+def test_static_spread_matches_the_oracle_charge_mesh():
+    # Essmann's smooth PME charge mesh Q (order-4 cardinal B-splines), FP64 on the host
+    s = wl.water_box(n_side=10, L=31.05, seed=8, pme_grid=32)
+    K = s.pme_grid
+    Qo = opme.pme(s.x.astype(np.float64), s.q.astype(np.float64), s.box, s.alpha, s.ke, K, return_grid=True)[2]
+    g = torch.full((int(np.prod(K)),), float("nan"), dtype=torch.float32, device="cuda")
+    for _ in range(2):  # the second call reuses the static mesh the first one filled
+        nbcore.pme_spread_static(dev_xq(s), s.box, K, g)
+        got = g.cpu().numpy().reshape(K)
+        assert np.abs(got - Qo).max() <= 1e-6 * np.abs(Qo).max()
+
+
+def test_static_spread_refuses_a_mesh_whose_point_count_would_wrap():
+    # 2^22 * 2^21 * 2^21 = 2^64 wraps a 64-bit product to 0; the sizes are checked one by
+    # one, before the multiplication, and nothing is written to the (small) grid
+    s = wl.water_box(n_side=4, L=12.42, seed=1, pme_grid=16)
+    xq = dev_xq(s)
+    grid = torch.full((16,), 7.0, dtype=torch.float32, device="cuda")
+    lib = nbcore.load()
+    box = np.ascontiguousarray(np.asarray(s.box, np.float64))
+    m = np.array([1 << 22, 1 << 21, 1 << 21], np.int32)
+    st = lib.pme_spread_static(ctypes.c_void_p(xq.data_ptr()), int(xq.shape[0]), box.ctypes.data, m.ctypes.data,
+                               ctypes.c_void_p(grid.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 1
+    torch.cuda.synchronize()
+    assert torch.all(grid == 7.0).item()
 
 
 def test_static_spread_of_an_empty_system_is_an_all_zero_mesh():

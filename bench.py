@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import copy
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -56,12 +57,16 @@ FLOP_LJ_VJP_PAIR = 2 * FLOP_LJ_PAIR  # VJP pair math: f and f'/r, J (lam_i - lam
 BYTES_INTEGRATE_ATOM = 172
 ISSUE_PER_SM_CLK = 4   # warp instructions issued per SM per clock (4 schedulers)
 LEAD_CYCLES = 1200000  # device idle (~0.6 ms) queued ahead of each eager timed evaluation
-N_SM = 148
+N_SM = 148  # replaced in main() by the device's multi_processor_count
 FP32_LANES = 128
 # our launches per forced-rebuild water evaluation (cuFFT not counted): load, bin, scan,
-# scatter, cellsort, build_cell, pair_cell, spread, grid_convert, convolve, gather,
+# scatter, cellsort, build_cell, pair_cell, excl, spread, grid_convert, convolve, gather,
 # reduce_energy, finalize
-KERNELS_PER_STEP = 13
+KERNELS_PER_STEP = 14
+# the timed region lasts at least this long (each timed step replays the evaluation R times),
+# so that the clock sampler (every CLOCK_MS) sees tens of samples at any --steps
+TIMED_REGION_MS = 1500.0
+CLOCK_MS = 50
 MUFU_PER_SM_CLK = 16   # special-function (rsqrt, exp2, rcp) results per SM per clock
 MUFU_COUL_PAIR = 2     # rsqrt + exp per in-cutoff Coulomb pair (algorithmic)
 MUFU_LJ_ONLY_PAIR = 1  # rsqrt (or rcp) per in-cutoff pair without Coulomb
@@ -116,7 +121,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", str(CLOCK_MS)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
         time.sleep(0.3)
@@ -234,6 +239,118 @@ def cpu_baseline(s, n_cut, repeats=3, row_stride=16):
                               "all_pairs_value": n_cut / (t_all1 + t_pme),
                               "note": "one OpenMP thread; all pairs timed on every %dth row x %d"
                                       % (row_stride, row_stride)}}
+
+
+def _rel_rms(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _energy_errors(e_gpu, e_ref, names):
+    """Per-component relative errors |E_gpu - E_fp64| / |E_fp64| (absolute error where the
+    reference is 0), with the FP64 values."""
+    out = {}
+    for k, nm in enumerate(names):
+        ref = float(e_ref[k])
+        d = abs(float(e_gpu[k]) - ref)
+        out[nm] = {"rel": d / abs(ref) if ref != 0.0 else None, "abs": d, "fp64": ref}
+    return out
+
+
+def error_vs_fp64(torch, nbcore, wl, s, f_gpu, e_gpu):
+    """The measured error of FP32 pair arithmetic (with fixed-point forces and FP64 energy
+    sums) against the FP64 oracle, per result: the headline water box (the bench's own
+    forces and energies), one row of the LJ sweep, two systems of the 256-system batch (one
+    LJ, one water, evaluated as a batch) and the HMC proposal of the differentiable-HMC row
+    (dH of each replica).  Run outside the timed region, on the host cores, as part of the
+    CPU-baseline leg."""
+    import oracle
+    from oracle import dynamics as odyn
+    from oracle import pme as opme
+    out = {"note": "relative RMS of the force vectors and |E - E_fp64| / |E_fp64| per energy component; "
+                   "the bars of the parity tests are 1e-5 (forces) and 1e-6 (energies)"}
+    names = ["E_lj", "E_dir", "E_excl", "E_self", "E_rec"]
+
+    def oracle_eval(sys_, with_pme):
+        p = oracle.make_params(sys_.box, r_cut=sys_.r_cut, r_switch=sys_.r_switch, alpha=sys_.alpha, ke=sys_.ke)
+        x = sys_.x.astype(np.float64)
+        e, f = oracle.nonbonded_cells(x, sys_.q, sys_.sigma, sys_.sqrt_eps, p, excl=sys_.excl)
+        e = list(e) + [0.0]
+        if with_pme:
+            Ep, Fp = opme.pme(x, sys_.q.astype(np.float64), sys_.box, sys_.alpha, sys_.ke, sys_.pme_grid)
+            e[4] = Ep
+            f = f + Fp
+        return np.asarray(e), f
+
+    # headline water box: LJ + Ewald direct + exclusion + self + PME
+    eo, fo = oracle_eval(s, True)
+    out["water_24k"] = {"force_rel_rms": _rel_rms(f_gpu, fo), "energy": _energy_errors(e_gpu, eo, names)}
+
+    def gpu_eval(systems, terms):
+        n_tot = sum(x.n for x in systems)
+        xq = torch.cat([torch.from_numpy(nbcore.pack_xq(x.x, x.q)) for x in systems]).cuda()
+        f = torch.empty((n_tot, 3), dtype=torch.float32, device="cuda")
+        e = torch.empty((len(systems), 6), dtype=torch.float64, device="cuda")
+        with nbcore.Handle(systems) as h:
+            h.nonbonded_forces(xq, f, e, terms=terms, force_rebuild=True)
+            h.check()
+        return f.cpu().numpy(), e.cpu().numpy()
+
+    # one LJ sweep row (32,000 atoms)
+    lj = wl.lj_random(32000, seed=11)
+    fg, eg = gpu_eval([lj], nbcore.NB_TERM_LJ)
+    eo, fo = oracle_eval(lj, False)
+    out["lj_sweep_32k"] = {"force_rel_rms": _rel_rms(fg, fo), "energy": _energy_errors(eg[0], eo, names[:1])}
+    # two systems of the 256-system batch, evaluated together
+    mix = wl.batched_mix(256)
+    pick = [mix[0], mix[1]]
+    fg, eg = gpu_eval(pick, nbcore.NB_TERM_ALL)
+    off = 0
+    rows = []
+    for k, sys_ in enumerate(pick):
+        pme = bool(getattr(sys_, "pme_grid", None)) and sys_.ke != 0.0
+        eo, fo = oracle_eval(sys_, pme)
+        rows.append({"system": k, "atoms": sys_.n, "kind": "water" if sys_.ke != 0.0 else "LJ",
+                     "force_rel_rms": _rel_rms(fg[off:off + sys_.n], fo),
+                     "energy": _energy_errors(eg[k], eo, names if sys_.ke != 0.0 else names[:1])})
+        off += sys_.n
+    out["batched_systems"] = rows
+    # HMC proposal: dH of 2 replicas of the differentiable-HMC configuration (LJ 2048,
+    # switch 2.2-2.5, L 32, dt 0.005) against the FP64 velocity-Verlet proposal
+    R, L, n = 2, 32, 2048
+    reps = []
+    for r in range(R):
+        sr = wl.lj_random(n, seed=100 + r, n_types=2)
+        sr.r_switch = 2.2
+        reps.append(sr)
+    xi, u = wl.hmc_randoms(R, n, seed=5)
+    w = np.ones(R * n, np.float32)
+    dt = np.full(R, 0.005, np.float32)
+    x0 = torch.cat([torch.from_numpy(nbcore.pack_xq(x.x, x.q)) for x in reps]).cuda()
+    x1 = torch.empty_like(x0)
+    st = torch.empty((R, 4), dtype=torch.float64, device="cuda")
+    ck = torch.empty(nbcore.ckpt_size(R * n, L, 8), dtype=torch.float32, device="cuda")
+    with nbcore.Handle(reps) as h:
+        h.hmc_trajectory(x0, x1, torch.from_numpy(w).cuda(), torch.from_numpy(dt).cuda(), L, 1.0,
+                         torch.from_numpy(xi.reshape(-1, 3)).cuda(), torch.from_numpy(u).cuda(), st, ck, 8,
+                         terms=nbcore.NB_TERM_LJ)
+        h.check()
+    stg = st.cpu().numpy()
+    hmc = []
+    for r, sr in enumerate(reps):
+        p = oracle.make_params(sr.box, r_cut=sr.r_cut, r_switch=sr.r_switch)
+
+        def fe(x, sr=sr, p=p):
+            e, f = oracle.nonbonded_cells(x, sr.q, sr.sigma, sr.sqrt_eps, p)
+            return f, float(e[0])
+        o = odyn.hmc_proposal(sr.x.astype(np.float64), xi[r].astype(np.float64), w[r * n:(r + 1) * n].astype(np.float64),
+                              float(dt[r]), L, 1.0, fe, sr.box)
+        hmc.append({"replica": r, "dH_gpu": float(stg[r, 0]), "dH_fp64": o["dH"], "dH_abs_err": abs(float(stg[r, 0]) - o["dH"]),
+                    "energy_scale": abs(o["U0"]) + o["K0"]})
+    out["hmc_proposal"] = {"replicas": hmc, "workload": "LJ 2048 atoms x 2 replicas, switch 2.2-2.5, 32 leapfrog "
+                                                       "steps, dt 0.005, the same normals on both sides"}
+    return out
 
 
 def run_reference(args):
@@ -389,7 +506,7 @@ def issue_roofline(prof, ms, f_sm):
     ach = wi / (ms / 1e3)
     pk = N_SM * ISSUE_PER_SM_CLK * f_sm * 1e6
     return {"warp_instructions_per_launch": wi, "achieved_per_s": ach, "peak_per_s": pk, "frac": ach / pk,
-            "peak_source": "148 SMs x 4 schedulers x median SM clock %.0f MHz" % f_sm}
+            "peak_source": "%d SMs x 4 schedulers x median SM clock %.0f MHz" % (N_SM, f_sm)}
 
 
 def traffic_from_profile(path):
@@ -560,6 +677,7 @@ def extras(torch, nbcore, wl):
     out["hmc_training"] = hmc_training(torch, nbcore, wl)
     out["hmc_lhmc"] = hmc_lhmc(torch, nbcore, wl)
     out["batched"] = batched(torch, nbcore, wl)
+    out["batched_dynamics"] = batched_dynamics(torch, nbcore, wl)
     return out
 
 
@@ -1107,6 +1225,97 @@ def batched(torch, nbcore, wl, n_systems=256, reps=10):
     return out
 
 
+def batched_dynamics(torch, nbcore, wl, n_inner=10, reps=5):
+    """MD (velocity Verlet, n_inner steps per call) and HMC (n_inner leapfrog steps with the
+    FP64 dH Metropolis test) over the 128 LJ systems of the 256-system mix (723,341 atoms,
+    sizes log-uniform in [500, 20000]): one handle for all systems, each call as one CUDA
+    graph, against the single-system path (one handle per system) looped over the same
+    systems inside one CUDA graph, so that the comparison isolates batching from launch
+    overhead.  Velocities Maxwell-Boltzmann at T* = 1 (seeded normals), unit masses."""
+    from paper_2503_20541_b300.graphs import CapturedStep
+    systems = [s for s in wl.batched_mix(256) if s.ke == 0.0]
+    ns = len(systems)
+    n = sum(s.n for s in systems)
+    gen = torch.Generator(device="cuda").manual_seed(31)
+    x0 = torch.cat([torch.from_numpy(nbcore.pack_xq(s.x, s.q)) for s in systems]).cuda()
+    v0 = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    v0[:, :3] = torch.randn((n, 3), device="cuda", generator=gen)
+    v0[:, 3] = 1.0
+    xi = torch.randn((n, 3), device="cuda", generator=gen)
+    u = torch.rand(ns, dtype=torch.float64, device="cuda", generator=gen)
+    w = torch.ones(n, dtype=torch.float32, device="cuda")
+    dt_md = torch.full((ns,), 0.005, dtype=torch.float32, device="cuda")
+    dt_hmc = torch.full((ns,), 0.004, dtype=torch.float32, device="cuda")
+    lj = nbcore.NB_TERM_LJ
+    offs = np.cumsum([0] + [s.n for s in systems])
+    sl = [slice(int(offs[k]), int(offs[k + 1])) for k in range(ns)]
+
+    def timed(g):
+        g.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    out = {"systems": ns, "atoms": n, "inner_steps": n_inner}
+    x = x0.clone()
+    v = v0.clone()
+    x1 = torch.empty_like(x0)
+    st = torch.empty((ns, 4), dtype=torch.float64, device="cuda")
+    with nbcore.Handle(systems) as h:
+        g = CapturedStep(lambda: h.md_step(x, v, dt_md, n_inner, terms=lj))
+        out["md_batched_ms"] = timed(g)
+        del g
+        g = CapturedStep(lambda: h.hmc_trajectory(x0, x1, w, dt_hmc, n_inner, 1.0, xi, u, st, terms=lj))
+        out["hmc_batched_ms"] = timed(g)
+        del g
+        h.check()
+        out["hmc_acceptance"] = float(st[:, 3].mean())
+    handles = [nbcore.Handle([s]) for s in systems]
+    try:
+        xs = [x0[q].clone() for q in sl]
+        vs = [v0[q].clone() for q in sl]
+        x0s = [x0[q].clone() for q in sl]
+        x1s = [torch.empty_like(a) for a in x0s]
+        ws = [w[q].clone() for q in sl]
+        xis = [xi[q].clone() for q in sl]
+        sts = [torch.empty((1, 4), dtype=torch.float64, device="cuda") for _ in systems]
+
+        def md_loop():
+            for k, hk in enumerate(handles):
+                hk.md_step(xs[k], vs[k], dt_md[k:k + 1], n_inner, terms=lj)
+
+        def hmc_loop():
+            for k, hk in enumerate(handles):
+                hk.hmc_trajectory(x0s[k], x1s[k], ws[k], dt_hmc[k:k + 1], n_inner, 1.0, xis[k], u[k:k + 1], sts[k],
+                                  terms=lj)
+        g = CapturedStep(md_loop)
+        out["md_looped_ms"] = timed(g)
+        del g
+        g = CapturedStep(hmc_loop)
+        out["hmc_looped_ms"] = timed(g)
+        del g
+        for hk in handles:
+            hk.check()
+        dh_b = st[:, 0].cpu().numpy()
+        dh_s = torch.cat([a[:, 0] for a in sts]).cpu().numpy()
+        out["hmc_dH_max_abs_diff_batched_vs_looped"] = float(np.max(np.abs(dh_b - dh_s)))
+    finally:
+        for hk in handles:
+            hk.close()
+    out["md_atom_steps_per_s"] = n * n_inner / (out["md_batched_ms"] / 1e3)
+    out["md_speedup_vs_looped"] = out["md_looped_ms"] / out["md_batched_ms"]
+    out["hmc_speedup_vs_looped"] = out["hmc_looped_ms"] / out["hmc_batched_ms"]
+    out["workload"] = ("the 128 LJ systems of the 256-system mix (rho* 0.8442, r_c 2.5, r_skin 0.3, plain cut-off), "
+                       "unit masses; MD: %d velocity-Verlet steps per call, dt 0.005; HMC: %d leapfrog steps per "
+                       "proposal, dt 0.004, kT 1, FP64 dH acceptance; batched = one handle, one graph per call; looped "
+                       "= one handle per system, all %d calls in one graph" % (n_inner, n_inner, ns))
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1118,6 +1327,8 @@ def main():
     rank, world, local = dist_env()
     import torch
     torch.cuda.set_device(local)
+    global N_SM
+    N_SM = torch.cuda.get_device_properties(local).multi_processor_count
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -1175,9 +1386,24 @@ def main():
         e_h.copy_(e, non_blocking=True)
     g_e2e = CapturedStep(e2e_step)
 
+    # Replays per timed step: each of the K timed steps replays the evaluation graph R times,
+    # each replay preceded by an L2 flush and bracketed by its own CUDA events, so that the
+    # timed region lasts >= TIMED_REGION_MS whatever K is and the clock sampler sees tens of
+    # samples; ms_per_step is the mean over the K * R evaluations.
+    def one_replay_ms(g, n=20):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n):
+            flush_l2()
+            g.replay()
+        torch.cuda.synchronize()
+        return 1e3 * (time.perf_counter() - t0) / n
+    R = max(1, int(math.ceil(TIMED_REGION_MS / (K * one_replay_ms(g_step)))))
+
     def timed(g):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        for i in range(K):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K * R)]
+        for i in range(K * R):
             flush_l2()
             ev[i][0].record()
             g.replay()
@@ -1201,6 +1427,9 @@ def main():
     h.check()
     value, ms = job_throughput(pc["cutoff"], ms_local, world)
     del g_step, g_reuse, g_e2e
+    # the forces and energies of one full evaluation, kept for the FP64 error block
+    step(True)
+    f_eval, e_eval = f.cpu().numpy().copy(), e.cpu().numpy()[0].copy()
 
     # per-stage breakdown (CUDA events between stages) from eager steps; the pair kernel's
     # own duration (for its roofline) from steps without PME, which otherwise shares the
@@ -1260,14 +1489,18 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "atoms": s.n, "pairs": pc, "l2": "flushed between timed steps (256 MB write, then 256 MB read of another buffer)",
+        "config": {"workload": WORKLOAD, "atoms": s.n, "pairs": pc, "l2": "flushed before every timed evaluation (256 MB write, then 256 MB read of another buffer)",
+                   "replays_per_step": R, "evaluations_timed": K * R,
+                   "timing": "each of the K timed steps replays the evaluation's CUDA graph R times, each replay "
+                             "after an L2 flush and between its own CUDA events; ms_per_step is the mean per "
+                             "evaluation",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "wall_s_timed_region": t_wall},
         "roofline": {"bound": "alu", "kernel": "k_pair (fused LJ + Ewald direct + exclusion)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "flops_per_launch": fl, "pair_kernel_us": 1e3 * t_pair,
-                     "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz (measured "
-                                    "during the timed region)" % f_sm,
+                     "peak_source": "%d SMs (device property) x 128 FP32 lanes x 2 flop x median SM clock "
+                                    "%.0f MHz (measured during the timed region)" % (N_SM, f_sm),
                      "mufu": {"ops_per_launch": mufu_ops, "peak_ops_per_s": mufu_peak,
                               "us_at_peak": 1e6 * mufu_ops / mufu_peak,
                               "frac": (mufu_ops / (t_pair / 1e3)) / mufu_peak},
@@ -1284,12 +1517,14 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(xq.numel() * 4), "d2h_bytes_per_step": int(f.numel() * 4 + e.numel() * 8)},
         "clocks": clocks,
-        "gpu_launches": KERNELS_PER_STEP * K,
+        "gpu_launches": KERNELS_PER_STEP * K * R,
     }
     if rank == 0 and not args.no_extras:
         out.update(extras(torch, nbcore, wl))
     if rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(s, pc["cutoff"])
+        # the same leg runs the oracle on the bench's own outputs: measured error per result
+        out["error_vs_fp64"] = error_vs_fp64(torch, nbcore, wl, s, f_eval, e_eval)
     h.close()
     if rank == 0:
         print(json.dumps(out))

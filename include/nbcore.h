@@ -104,16 +104,17 @@ typedef struct {
 typedef struct {
     int32_t max_neighbors;   /* per-atom list capacity (full list), rounded up to a multiple
                                 of 128; 0: from density */
-    int32_t stencil_tile;    /* stencil candidates per shared-memory tile of the cell kernels
+    int32_t stencil_tile;    /* stencil candidates per shared-memory tile of the list build
                                 (multiple of 64 in [256, 4096]); 0: auto from the density */
     int32_t cell_div;        /* cells of edge >= r_nl / cell_div, cell_div in {1, 2}, for every
                                 system; 0: chosen per system (2 for a system with >= 5 cells
                                 of edge r_nl/2 along each axis and >= 64 atoms per r_nl^3) */
     int32_t force_bits;      /* fixed-point fraction bits for forces; 0: 32 */
-    int32_t blocks_per_cell; /* thread blocks sharing one cell in the list build, pair and VJP
-                                kernels (each takes a strided share of the cell's atoms), in
-                                [1, 32]; 0: auto (more than one only when the cells are too few
-                                to fill the GPU).  Results do not depend on it. */
+    int32_t blocks_per_cell; /* thread blocks sharing one cell in the list build (each takes a
+                                strided share of the cell's atoms), in [1, 32]; 0: auto (more
+                                than one only when the cells are too few to fill the GPU).
+                                Results do not depend on it.  The pair and VJP kernels are not
+                                organised by cell: their blocks take consecutive atoms. */
 } nb_options;
 
 typedef struct nb_handle nb_handle;
@@ -196,6 +197,17 @@ nb_status nonbonded_forces(nb_handle* h, const float* xq, float* f_out, double* 
  * Launches one kernel per system and returns; errors are read with nb_check.
  */
 nb_status nonbonded_forces_allpairs(nb_handle* h, const float* xq, float* f_out, double* energies, void* stream);
+
+/*
+ * The complementary error function of the Ewald direct-space term ke q_i q_j erfc(alpha r)/r
+ * (Sec. 2.1.2) exactly as the pair kernels evaluate it (FP32: a fitted erfcx polynomial in
+ * t = 1/(1 + x/2) times exp(-x^2) from the hardware 2^y approximation with a two-float
+ * argument), for checking it against a reference erfc.
+ *   x [n]    (device) arguments, x >= 0 (alpha r); other values give unspecified results.
+ *   out [n]  (device) erfc(x).
+ * No handle; launches one kernel on `stream`; NB_ERR_ARG for n < 0 or NULL arrays with n > 0.
+ */
+nb_status nb_erfc_eval(const float* x, float* out, int32_t n, void* stream);
 
 /*
  * PME charge spreading alone (Sec. 2.1.2, smooth PME with order-4 cardinal B-splines):
@@ -418,8 +430,9 @@ nb_status nonbonded_force_vjp(nb_handle* h, const float* xq, const float* lam, f
 nb_status pme_spread_static(const float* xq, int32_t n_atoms, const double* box, const int32_t* mesh,
                             float* grid, void* stream);
 
-/* Thread blocks per cell the handle uses in the list build and in the pair / VJP kernels
- * (nb_options.blocks_per_cell, or the automatic choice).  Host only, no GPU work. */
+/* Thread blocks per cell the handle uses in the list build (nb_options.blocks_per_cell, or
+ * the automatic choice); `pair` is 1 (the pair and VJP kernels take consecutive atoms per
+ * block, not cells).  Host only, no GPU work. */
 nb_status nb_blocks_per_cell(const nb_handle* h, int32_t* build, int32_t* pair);
 
 /* Cumulative number of neighbour-list rebuilds of a handle (synchronises `stream`). */

@@ -461,11 +461,11 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(dalloc(h, &h->iperm, N));
         NB_TRY(dalloc(h, &h->xs, N));
         NB_TRY(dalloc(h, &h->xsb, N));
-        NB_TRY(dalloc(h, &h->pscr, 3 * (size_t)N));
         NB_TRY(dalloc(h, &h->ps, N));
         NB_TRY(dalloc(h, &h->xref, N));
         NB_TRY(dalloc(h, &h->nbr, (size_t)N * h->cap));
         NB_TRY(dalloc(h, &h->nbr_cnt, N));
+        NB_TRY(dalloc(h, &h->nbr_out, N));
         h->excl_w = h->max_excl == 0 ? 0 : (h->max_excl <= 2 ? 2 : 4);
         if (h->excl_w) {
             NB_TRY(dalloc(h, &h->ex_slot, (size_t)N * h->excl_w));
@@ -473,7 +473,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         }
         NB_TRY(dalloc(h, &h->ffix, 3 * (size_t)N));
         NB_TRY(dalloc(h, &h->e_atom, N));
-        NB_TRY(dalloc(h, &h->flags, 4));
+        NB_TRY(dalloc(h, &h->flags, kFlagWords));
         NB_TRY(dalloc(h, &h->build_ticket, 1));
         NB_TRY(cudaMemset(h->build_ticket, 0, sizeof(unsigned)));
         NB_TRY(dalloc(h, &h->energy, (size_t)n_systems * NB_NE));
@@ -531,10 +531,11 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(cudaMemset(h->cell_count, 0, sizeof(int) * h->n_cells));
         NB_TRY(cudaMemset(h->cell_cursor, 0, sizeof(int) * h->n_cells));
         NB_TRY(cudaMemset(h->nbr_cnt, 0, sizeof(int) * N));
+        NB_TRY(cudaMemset(h->nbr_out, 0, sizeof(int) * N));
         NB_TRY(cudaMemset(h->ffix, 0, sizeof(long long) * 3 * N));
         NB_TRY(cudaMemset(h->e_atom, 0, sizeof(float4) * N));
         NB_TRY(cudaMemset(h->ke_atom, 0, sizeof(float) * N));
-        NB_TRY(cudaMemset(h->flags, 0, sizeof(unsigned) * 4));
+        NB_TRY(cudaMemset(h->flags, 0, sizeof(unsigned) * kFlagWords));
         NB_TRY(cudaMemset(h->xs, 0, sizeof(float4) * N));
         NB_TRY(cudaMemset(h->xsb, 0, sizeof(float4) * N));
         NB_TRY(build_setup(h));

@@ -1,11 +1,12 @@
-// cell.cuh -- the cell tile shared by the list build, the pair kernels and the pair
-// export: one block per cell stages the cell's stencil (Sec. 2.1.2 "Neighborlists": the
-// 27-cell, or 125-cell for half-width cells, neighbourhood) in shared memory.
+// cell.cuh -- the cell tile of the list build: one block per cell stages the cell's
+// stencil (Sec. 2.1.2 "Neighborlists": the 27-cell, or 125-cell for half-width cells,
+// neighbourhood) in shared memory.
 //
 // The stencil is listed as runs of consecutive cells along x; each run is one contiguous
 // slot range (slot order is sorted by cell).  Concatenating the runs gives the cell's
-// candidate array; the Verlet list stores, for every atom, indices into that array
-// (16 bits), so the pair kernels gather from shared memory.
+// candidate array; the Verlet list stores, for every atom, its partners' slots together
+// with the image code of the run each came from, so that the pair kernels read partners
+// from the slot-ordered arrays without a stencil of their own.
 //
 // Images.  Along an axis with a stencil (nc >= 2 st + 1) the unwrapped cell index of a run
 // fixes the image, which is the minimum image of every pair within r_nl.  A run from
@@ -34,7 +35,7 @@ struct BuildRun {
     int n;      // candidates in the run
     int flags;  // per-pair image: bit d = atom moves down by L on axis d
     float s[3]; // shift added to the candidates' coordinates
-    float pad;
+    unsigned code;  // the run's image code of a list entry (common.cuh), shifted to its place
 };
 
 struct CellCtx {
@@ -93,6 +94,15 @@ __device__ __forceinline__ void run_image(int u, int nc, bool fold, bool frame, 
     } else if (frame) {
         s = -L;
     }
+}
+
+// Image code bits of a run along one axis with unwrapped cell index u: below the first
+// cell the partner moves down by L, beyond the last the atom does (folded axes: none).
+__device__ __forceinline__ unsigned run_code(int u, int nc, bool fold, int d) {
+    if (fold || u == INT_MIN) return 0u;
+    if (u < 0) return 2u << (2 * d);
+    if (u >= nc) return 1u << (2 * d);
+    return 0u;
 }
 
 // The stencil runs of the cell, computed by one warp: lane l handles stencil row l (at
@@ -167,7 +177,8 @@ __device__ __forceinline__ void cell_runs(const CellCtx& C, const SysDev& S, con
         run_image(xall ? INT_MIN : seg_lo[g], nc0, C.fold[0], C.frame[0], C.L[0], 1, R.s[0], R.flags);
         run_image(yu, nc1, C.fold[1], C.frame[1], C.L[1], 2, R.s[1], R.flags);
         run_image(zu, nc2, C.fold[2], C.frame[2], C.L[2], 4, R.s[2], R.flags);
-        R.pad = 0.f;
+        R.code = (run_code(xall ? INT_MIN : seg_lo[g], nc0, C.fold[0], 0) | run_code(yu, nc1, C.fold[1], 1) |
+                  run_code(zu, nc2, C.fold[2], 2)) << kEntrySlotBits;
         runs[r] = R;
     }
     if (lane == 0) {
@@ -199,6 +210,11 @@ __device__ __forceinline__ int run_of(const BuildRun* runs, int nr, int k) {
     }
     return lo;
 }
+
+// Squared distance of a pair from its difference vector.  The list build and the pair
+// kernels both use this one function (same operations, same order), so a pair that the
+// build found inside r_c has, from the same positions, the same r^2 in the pair kernels.
+__device__ __forceinline__ float pair_r2(float dx, float dy, float dz) { return fmaf(dz, dz, fmaf(dy, dy, dx * dx)); }
 
 // Per-pair difference for GEN cells: flagged axes move the atom down by L, folded axes
 // take the minimum image of the raw coordinates.

@@ -6,8 +6,8 @@
 //                  exclusion CSR.
 //   slot order   : atoms sorted by (system, cell, caller index) after each rebuild;
 //                  xs float4 (x,y,z,q in the frame of the last build), ps float2, the
-//                  full neighbour list nbr[k*cap + n] (uint16 indices into the stencil
-//                  of k's cell) with counts, fixed-point forces
+//                  full neighbour list nbr[k*cap + n] (uint32: partner slot and periodic
+//                  image code) with counts, fixed-point forces
 //                  ffix[d*N + k] (int64, 2^force_bits per unit), per-atom half
 //                  energies e_atom float4.
 //   System s owns the same index range [atom_off, atom_off + n) in both orders.
@@ -35,6 +35,20 @@ inline int red_tile(int n) {
     return std::min(4096, std::max(128, (t + 127) / 128 * 128));
 }
 constexpr int kSmallSortAtoms = 8192;          // handles re-slotted by one block (k_sort_small)
+// Words of the handle's device flag array: [0] rebuild request, [1] error bits, [2..3] rebuild
+// count (u64), [NB_FLAG_FRESH] 1 while the slot positions are exactly those of the last list
+// build (set by the build, cleared by every load of new positions).
+constexpr int NB_FLAG_FRESH = 4;
+constexpr int kFlagWords = 8;
+// A neighbour-list entry: the partner's slot in the low kEntrySlotBits bits and, above them,
+// the pair's periodic image as 2 bits per axis d: bit 2d, atom i moves down by L; bit 2d + 1,
+// partner j moves down by L (each shift exact: the moved coordinate lies above L/2).
+constexpr int kEntrySlotBits = 26;
+constexpr unsigned kEntrySlotMask = (1u << kEntrySlotBits) - 1u;
+// nbr_out[k]: the count of back entries in the low bits; kOutWrapBit set when some entry of
+// the row may carry an image code or the system folds an axis (periodic pairs near a face).
+constexpr int kOutCountMask = (1 << 30) - 1;
+constexpr int kOutWrapBit = 1 << 30;
 
 // Per-system constants, resident in device memory (read through the L1 path).
 struct SysDev {
@@ -130,13 +144,13 @@ struct nb_handle {
     float4* xsb = nullptr;       // [N] slot: wrapped positions at the last build
     float2* ps = nullptr;        // [N] slot
     float4* xref = nullptr;      // [N] caller
-    unsigned short* nbr = nullptr;  // [N*cap] stencil indices of each atom's neighbours
+    unsigned* nbr = nullptr;     // [N*cap] list entries (partner slot | image code << kEntrySlotBits)
     int tile = 0;                // candidates per shared-memory tile of the cell kernels
-    float4* pscr = nullptr;      // [3N] partial sums of atoms whose stencil spans several tiles
-    int* nbr_cnt = nullptr;      // [N]
+    int* nbr_cnt = nullptr;      // [N] entries at the front of the row (inside r_c at the build)
+    int* nbr_out = nullptr;      // [N] entries at the back of the row (outside r_c at the build), | kOutWrapBit
     long long* ffix = nullptr;   // [3N] slot
     float4* e_atom = nullptr;    // [N] slot: half energies (E_lj, E_dir, E_excl, 0) of each atom
-    unsigned* flags = nullptr;   // [0] rebuild request, [1] error bits, [2..3] rebuild count (u64)
+    unsigned* flags = nullptr;   // [kFlagWords]: rebuild request, error bits, rebuild count, fresh list
     unsigned* build_ticket = nullptr;  // [1] blocks of the list build done (reset by the last)
     double* energy = nullptr;    // [n_sys * NB_NE] scratch
     int n_red_blocks = 0;        // energy reduction: blocks of red_tile atoms, none straddling systems
@@ -306,8 +320,9 @@ __device__ __forceinline__ bool load_atom(float4 p, const SysDev& S, float4 r, c
 }
 
 // The next evaluation's load, done by the integrator right after the drift: the new
-// positions' validity check and slot positions, and the zeroing of the fixed-point forces
-// (each thread zeroes the slot whose force it has just read).  xs == nullptr: none.
+// positions' validity check and slot positions, the zeroing of the fixed-point forces
+// (each thread zeroes the slot whose force it has just read) and the clearing of the
+// fresh-list flag.  xs == nullptr: none.
 struct LoadNext {
     const float4* xref = nullptr;
     const float4* xsb = nullptr;

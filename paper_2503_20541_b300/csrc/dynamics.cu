@@ -222,6 +222,7 @@ __global__ void k_integrate(int N, float4* __restrict__ xq, float4* __restrict__
     }
     v[i] = vi;
     if (ln.xs) {
+        if (i == 0) ln.flags[NB_FLAG_FRESH] = 0u;
         const int k = iperm[i];
         ln.ffix[k] = 0;
         ln.ffix[(size_t)N + k] = 0;

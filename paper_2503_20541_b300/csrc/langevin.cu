@@ -179,6 +179,7 @@ __global__ void k_langevin(int n_groups, const int4* __restrict__ groups, float4
     pdl_wait();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_groups) return;
+    if (g == 0 && ln.xs) ln.flags[NB_FLAG_FRESH] = 0u;  // new positions: the list is no longer fresh
     const int4 G = groups[g];
     const int id[3] = {G.x, G.y, G.z};
     const int s = sid[G.x];

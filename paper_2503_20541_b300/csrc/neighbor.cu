@@ -26,6 +26,7 @@ __global__ void k_load(int N, const float4* __restrict__ xq, const int* __restri
                        long long* __restrict__ ffix, unsigned* flags) {
     pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) flags[NB_FLAG_FRESH] = 0u;  // the positions may differ from the build's from here on
     bool need = false;
     if (i < N) {
         ffix[i] = 0;
@@ -286,12 +287,12 @@ __global__ void __launch_bounds__(1024) k_sort_small(int N, int n_cells, const f
     }
 }
 
-// Predicated 16-bit store: keeps the list append inside one basic block (no branch
+// Predicated 32-bit store: keeps the list append inside one basic block (no branch
 // around it), so the tests of all held atoms interleave.  Nothing in the build reads
 // the list back.
-__device__ __forceinline__ void st16_if(unsigned short* p, int v, bool ok) {
+__device__ __forceinline__ void st32_if(unsigned* p, unsigned v, bool ok) {
     asm volatile(
-        "{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q st.global.u16 [%0], %1;\n}\n" ::"l"(p), "h"((unsigned short)v),
+        "{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q st.global.u32 [%0], %1;\n}\n" ::"l"(p), "r"(v),
         "r"((unsigned)ok));
 }
 
@@ -318,19 +319,20 @@ __device__ __forceinline__ void build_atoms(const CellCtx& C, int w, int W, int 
                                             const float4* __restrict__ xs, const int* __restrict__ perm,
                                             const int* __restrict__ iperm, const int* __restrict__ ex_off,
                                             const int* __restrict__ ex_idx, const int* __restrict__ ex_slot,
-                                            unsigned short* __restrict__ nbr, int* __restrict__ nbr_cnt, int cap,
-                                            float rnl2, unsigned* flags) {
+                                            unsigned* __restrict__ nbr, int* __restrict__ nbr_cnt,
+                                            int* __restrict__ nbr_out, int cap, float rnl2, float rc2,
+                                            bool wrap, unsigned* flags) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     float ax[A], ay[A], az[A];
     int ex[A][E + 1];
-    int cnt[A];
-    unsigned short* row[A];
+    int cin[A], cout[A];
+    unsigned* row[A];
     unsigned slow = 0u;
 #pragma unroll
     for (int a = 0; a < A; ++a) {
         ax[a] = ay[a] = az[a] = -kFar;
-        cnt[a] = 0;
+        cin[a] = cout[a] = 0;
         row[a] = nbr;
 #pragma unroll
         for (int q = 0; q <= E; ++q) ex[a][q] = -1;
@@ -347,14 +349,15 @@ __device__ __forceinline__ void build_atoms(const CellCtx& C, int w, int W, int 
                 const int oi = perm[i];
                 if (ex_off[oi + 1] - ex_off[oi] > E) slow |= 1u << a;
             }
-            cnt[a] = (t0 == 0) ? 0 : nbr_cnt[i];
+            cin[a] = (t0 == 0) ? 0 : nbr_cnt[i];
+            cout[a] = (t0 == 0) ? 0 : (nbr_out[i] & kOutCountMask);
             row[a] = nbr + (size_t)i * cap;
         }
     }
     for (int base = 0; base < nt; base += 32) {
         const float4 cj = cand[base + lane];
-        const int j = __float_as_int(cj.w);
-        const int li = t0 + base + lane;
+        const unsigned ent = __float_as_uint(cj.w);  // list entry: slot | image code
+        const int j = (int)(ent & kEntrySlotMask);
         int fl = 0;
         if (GEN) fl = cflag[base + lane];
         float r2[A];
@@ -370,7 +373,7 @@ __device__ __forceinline__ void build_atoms(const CellCtx& C, int w, int W, int 
                 dy = ay[a] - cj.y;
                 dz = az[a] - cj.z;
             }
-            r2[a] = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            r2[a] = pair_r2(dx, dy, dz);
         }
 #pragma unroll
         for (int a = 0; a < A; ++a) {
@@ -383,10 +386,19 @@ __device__ __forceinline__ void build_atoms(const CellCtx& C, int w, int W, int 
                 const int e0 = ex_off[oi], e1 = ex_off[oi + 1];
                 for (int e = e0 + E; e < e1 && acc; ++e) acc = (iperm[ex_idx[e]] != j);
             }
-            const unsigned bits = __ballot_sync(0xffffffffu, acc);
-            const int pos = cnt[a] + __popc(bits & lt);
-            st16_if(row[a] + pos, li, acc && pos < cap);
-            cnt[a] += __popc(bits);
+            // pairs inside r_c at the build go to the front of the row, the others to the
+            // back (in reverse order), so that the pair kernels can take the front part
+            // without a cut-off test while the positions are those of the build
+            const bool inn = acc && r2[a] < rc2;
+            const unsigned ba = __ballot_sync(0xffffffffu, acc);
+            const unsigned bi = __ballot_sync(0xffffffffu, inn);
+            const int pi = __popc(bi & lt), po = __popc(ba & lt) - pi;
+            const int pos = inn ? cin[a] + pi : cap - 1 - (cout[a] + po);
+            const bool room = inn ? cin[a] + pi < cap : cout[a] + po < cap;
+            st32_if(row[a] + pos, ent, acc && room);
+            const int ni = __popc(bi);
+            cin[a] += ni;
+            cout[a] += __popc(ba) - ni;
         }
     }
     if (lane == 0) {
@@ -394,12 +406,16 @@ __device__ __forceinline__ void build_atoms(const CellCtx& C, int w, int W, int 
         for (int a = 0; a < A; ++a) {
             if (a < na) {
                 const int i = C.i0 + w + W * (m0 + a);
-                int c = cnt[a];
-                if (last && c > cap) {
+                int ci = cin[a], co = cout[a];
+                if (last && ci + co > cap) {
+                    // the two parts have met: flagged; the counts are clamped so that
+                    // readers stay inside the row
                     atomicOr(&flags[1], NB_DEVERR_LIST_OVERFLOW);
-                    c = cap;
+                    ci = min(ci, cap);
+                    co = min(co, cap - ci);
                 }
-                nbr_cnt[i] = c;  // running count between tiles, clamped after the last
+                nbr_cnt[i] = ci;  // running counts between tiles, clamped after the last
+                nbr_out[i] = co | (wrap ? kOutWrapBit : 0);
             }
         }
     }
@@ -411,8 +427,9 @@ __device__ __forceinline__ void build_tile(const CellCtx& C, int w, int W, int t
                                            const unsigned char* cflag, const float4* __restrict__ xs,
                                            const int* __restrict__ perm, const int* __restrict__ iperm,
                                            const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
-                                           const int* __restrict__ ex_slot, unsigned short* __restrict__ nbr,
-                                           int* __restrict__ nbr_cnt, int cap, float rnl2, unsigned* flags) {
+                                           const int* __restrict__ ex_slot, unsigned* __restrict__ nbr,
+                                           int* __restrict__ nbr_cnt, int* __restrict__ nbr_out, int cap,
+                                           float rnl2, float rc2, bool wrap, unsigned* flags) {
     const int n_i = C.i1 - C.i0;
     const int mw = n_i > w ? (n_i - w + W - 1) / W : 0;  // atoms of this warp
     if (mw == 0) return;
@@ -422,7 +439,7 @@ __device__ __forceinline__ void build_tile(const CellCtx& C, int w, int W, int t
     for (int m0 = 0; m0 < mw; m0 += gs) {
         const int na = min(gs, mw - m0);
 #define NB_BUILD_ARGS C, w, W, m0, na, t0, nt, last, cand, cflag, xs, perm, iperm, ex_off, ex_idx, ex_slot, nbr, \
-                      nbr_cnt, cap, rnl2, flags
+                      nbr_cnt, nbr_out, cap, rnl2, rc2, wrap, flags
         if (C.gen) {
             build_atoms<E, SLOW, true, kBuildAtomsGen>(NB_BUILD_ARGS);
         } else {
@@ -445,16 +462,16 @@ __device__ __forceinline__ void build_cell_body(const CellCtx& C, const SysDev& 
                                                 const int* __restrict__ perm, const int* __restrict__ iperm,
                                                 const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
                                                 int* __restrict__ ex_slot, int* __restrict__ ex_cnt,
-                                                unsigned short* __restrict__ nbr, int* __restrict__ nbr_cnt,
-                                                unsigned* flags, int part, int split);
+                                                unsigned* __restrict__ nbr, int* __restrict__ nbr_cnt,
+                                                int* __restrict__ nbr_out, unsigned* flags, int part, int split);
 
 template <int E, bool SLOW>
 __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
     int cap, int tile, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
     const int* __restrict__ start, const float4* __restrict__ xs, const int* __restrict__ perm,
     const int* __restrict__ iperm, const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
-    int* __restrict__ ex_slot, int* __restrict__ ex_cnt, unsigned short* __restrict__ nbr,
-    int* __restrict__ nbr_cnt, unsigned* ticket, unsigned* flags, int split) {
+    int* __restrict__ ex_slot, int* __restrict__ ex_cnt, unsigned* __restrict__ nbr,
+    int* __restrict__ nbr_cnt, int* __restrict__ nbr_out, unsigned* ticket, unsigned* flags, int split) {
     pdl_wait();
     if (flags[0] == 0u) return;
     // `split` blocks share a cell, block `part` taking warps part*kBuildWarps.. of its W
@@ -463,7 +480,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
     const CellCtx C = cell_ctx(c, S, start);
     if (C.i0 + part * kBuildWarps < C.i1)
         build_cell_body<E, SLOW>(C, S, cap, tile, start, xs, perm, iperm, ex_off, ex_idx, ex_slot, ex_cnt, nbr,
-                                 nbr_cnt, flags, part, split);
+                                 nbr_cnt, nbr_out, flags, part, split);
     // the last block to finish counts the rebuild and clears the request
     __shared__ bool last;
     __syncthreads();
@@ -476,6 +493,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
         unsigned long long* cnt = reinterpret_cast<unsigned long long*>(flags + 2);
         *cnt += 1ull;
         flags[0] = 0u;
+        flags[NB_FLAG_FRESH] = 1u;  // slot positions are those of this build until the next load
         *ticket = 0u;
     }
 }
@@ -486,8 +504,8 @@ __device__ __forceinline__ void build_cell_body(const CellCtx& C, const SysDev& 
                                                 const int* __restrict__ perm, const int* __restrict__ iperm,
                                                 const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
                                                 int* __restrict__ ex_slot, int* __restrict__ ex_cnt,
-                                                unsigned short* __restrict__ nbr, int* __restrict__ nbr_cnt,
-                                                unsigned* flags, int part, int split) {
+                                                unsigned* __restrict__ nbr, int* __restrict__ nbr_cnt,
+                                                int* __restrict__ nbr_out, unsigned* flags, int part, int split) {
     __shared__ BuildRun runs[kMaxRuns];
     __shared__ int n_runs, n_cand;
     // dynamic: `tile` candidates, then `tile` image-flag bytes when any system can need
@@ -498,11 +516,11 @@ __device__ __forceinline__ void build_cell_body(const CellCtx& C, const SysDev& 
     if (w == 0) cell_runs(C, S, start, runs, &n_runs, &n_cand, flags);
     __syncthreads();
     const int nr = n_runs, total = n_cand;
-    if (total > 65536) {  // stencil indices are 16-bit
-        if (threadIdx.x == 0) atomicOr(&flags[1], NB_DEVERR_LIST_OVERFLOW);
-        return;
-    }
-    const float rnl2 = S.rnl2;
+    // rows of this cell may hold image codes (or the system folds an axis): the pair kernels
+    // then take the per-axis image path for its atoms
+    bool wrap = C.gen;
+    for (int r = 0; r < nr; ++r) wrap = wrap || runs[r].code != 0u;
+    const float rnl2 = S.rnl2, rc2 = S.rc2;
     for (int t0 = 0; t0 < total; t0 += tile) {
         const int t1 = min(total, t0 + tile);
         const int nt = t1 - t0;
@@ -537,62 +555,50 @@ __device__ __forceinline__ void build_cell_body(const CellCtx& C, const SysDev& 
             for (int k = a + lane; k < b; k += 32) {
                 const float4 p = cand[k - t0];
                 cand[k - t0] = make_float4(p.x + R.s[0], p.y + R.s[1], p.z + R.s[2],
-                                           __int_as_float(R.slot0 + (k - R.sm0)));
+                                           __uint_as_float((unsigned)(R.slot0 + (k - R.sm0)) | R.code));
                 if (C.gen) cflag[k - t0] = (unsigned char)R.flags;
             }
         }
         const int ntp = (nt + 31) & ~31;
         for (int k = nt + threadIdx.x; k < ntp; k += kBuildThreads) {
-            cand[k] = make_float4(kFar, kFar, kFar, __int_as_float(-1));
+            cand[k] = make_float4(kFar, kFar, kFar, __uint_as_float(kEntrySlotMask));  // never accepted
             if (C.gen) cflag[k] = 0;
         }
         __syncthreads();
         const bool last = t1 == total;
         build_tile<E, SLOW>(C, part * kBuildWarps + w, split * kBuildWarps, t0, nt, last, cand, cflag, xs, perm,
-                            iperm, ex_off, ex_idx, ex_slot, nbr, nbr_cnt, cap, rnl2, flags);
+                            iperm, ex_off, ex_idx, ex_slot, nbr, nbr_cnt, nbr_out, cap, rnl2, rc2, wrap, flags);
         if (!last) __syncthreads();
     }
 }
 
-// Pairs of the list as caller indices (i < j), one block per cell: the stencil index of
-// each entry is mapped back to its slot through the cell's runs.
-__global__ void __launch_bounds__(128) k_export_pairs(const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
-                                                      const int* __restrict__ start, int cap,
-                                                      const unsigned short* __restrict__ nbr,
-                                                      const int* __restrict__ cnt, const int* __restrict__ perm,
-                                                      int2* out, long long max_pairs, unsigned long long* counter,
-                                                      unsigned* flags) {
-    const int c = blockIdx.x;
-    const SysDev& S = sys[cell_sys[c]];
-    const CellCtx C = cell_ctx(c, S, start);
-    if (C.i0 == C.i1) return;
-    __shared__ BuildRun runs[kMaxRuns];
-    __shared__ int n_runs, n_cand;
-    if (threadIdx.x < 32) cell_runs(C, S, start, runs, &n_runs, &n_cand, flags);
-    __syncthreads();
-    const int nr = n_runs;
+// Pairs of the list as caller indices (i < j), one warp per atom: an entry's low bits are
+// the partner's slot, mapped to its caller index through the permutation.  Each warp adds
+// its pairs of a round to the output with one counter update (the order of the output is
+// not defined; the set is).
+__global__ void __launch_bounds__(256) k_export_pairs(int N, int cap, const unsigned* __restrict__ nbr,
+                                                      const int* __restrict__ cnt, const int* __restrict__ cnt_out,
+                                                      const int* __restrict__ perm, int2* out, long long max_pairs,
+                                                      unsigned long long* counter) {
+    const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    for (int i = C.i0 + (threadIdx.x >> 5); i < C.i1; i += blockDim.x >> 5) {
-        const int oi = perm[i];
-        const int m = cnt[i];
-        for (int n0 = 0; n0 < m; n0 += 32) {
-            const int n = n0 + lane;
-            int oj = -1;
-            if (n < m) {
-                const int k = nbr[(size_t)i * cap + n];
-                const BuildRun& R = runs[run_of(runs, nr, k)];
-                oj = perm[R.slot0 + (k - R.sm0)];
-            }
-            const bool take = n < m && oi < oj;
-            // one counter update per warp: the lanes' slots follow from the ballot
-            const unsigned b = __ballot_sync(0xffffffffu, take);
-            unsigned long long base = 0;
-            if (lane == 0 && b) base = atomicAdd(counter, (unsigned long long)__popc(b));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (take) {
-                const unsigned long long pos = base + __popc(b & ((1u << lane) - 1u));
-                if (out && (long long)pos < max_pairs) out[pos] = make_int2(oi, oj);
-            }
+    if (i >= N) return;
+    const int oi = perm[i];
+    // entries [0, m_in) and [cap - m_out, cap) of the row, walked as one range
+    const int m_in = cnt[i], m = m_in + (cnt_out[i] & kOutCountMask), gap = cap - m;
+    const unsigned* row = nbr + (size_t)i * cap;
+    for (int n0 = 0; n0 < m; n0 += 32) {
+        const int n = n0 + lane;
+        int oj = -1;
+        if (n < m) oj = perm[row[n < m_in ? n : n + gap] & kEntrySlotMask];
+        const bool take = n < m && oi < oj;
+        const unsigned b = __ballot_sync(0xffffffffu, take);
+        unsigned long long base = 0;
+        if (lane == 0 && b) base = atomicAdd(counter, (unsigned long long)__popc(b));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (take) {
+            const unsigned long long pos = base + __popc(b & ((1u << lane) - 1u));
+            if (out && (long long)pos < max_pairs) out[pos] = make_int2(oi, oj);
         }
     }
 }
@@ -611,7 +617,7 @@ void launch_build(nb_handle* h, cudaStream_t st) {
                                     : k_build_cell<4, true>;
     launch_pdl(build, h->n_cells * h->split_build, kBuildThreads, build_smem(h), st,
         h->cap, h->tile, h->cell_sys, h->sys, h->cell_start, h->xs, h->perm, h->iperm, h->ex_off, h->ex_idx,
-        h->ex_slot, h->ex_cnt, h->nbr, h->nbr_cnt, h->build_ticket, h->flags, h->split_build);
+        h->ex_slot, h->ex_cnt, h->nbr, h->nbr_cnt, h->nbr_out, h->build_ticket, h->flags, h->split_build);
 }
 
 // Re-slotting of a rebuild: binning, scan, scatter and in-cell sort (one block for small
@@ -668,8 +674,9 @@ cudaError_t build_setup(nb_handle* h) {
 
 void launch_export_pairs(nb_handle* h, int2* out, long long max_pairs, unsigned long long* counter,
                          cudaStream_t st) {
-    k_export_pairs<<<h->n_cells, 128, 0, st>>>(h->cell_sys, h->sys, h->cell_start, h->cap, h->nbr, h->nbr_cnt,
-                                               h->perm, out, max_pairs, counter, h->flags);
+    const int N = h->n_atoms;
+    k_export_pairs<<<cdiv((long long)N * 32, 256), 256, 0, st>>>(N, h->cap, h->nbr, h->nbr_cnt, h->nbr_out, h->perm,
+                                                                  out, max_pairs, counter);
 }
 
 }  // namespace nb

@@ -6,19 +6,29 @@
 //   Ewald direct space ke q_i q_j erfc(alpha r)/r;
 // and, for each of the atom's excluded partners (any distance), the exclusion
 // correction -ke q_i q_j erf(alpha r)/r (the reciprocal sum still contains the
-// pair).  A pair force is F_i = f(r) d with d = mi(x_i - x_j), f = -U'/r.
+// pair; k_excl, one thread per atom).  A pair force is F_i = f(r) d with d = mi(x_i - x_j),
+// f = -U'/r.
 //
-// Work decomposition: one block per cell (the cell tile of cell.cuh) stages the
-// positions, charges and LJ parameters of the cell's stencil in shared memory with the
-// build's images applied; one warp per atom of the cell walks its full neighbour list
-// (both directions of every pair are listed; entries are 16-bit stencil indices), tests
-// r < r_c on 32 entries at a time and appends the pairs inside r_c to a per-warp queue,
-// and the interaction math runs on full warps of queued pairs.  i's data stays in
-// registers, partial sums are reduced with warp shuffles in a fixed tree, and the force
-// on i is added once, as int64 fixed point, to the zeroed force array (the PME gather
-// adds its part concurrently; integer addition makes the order irrelevant).  Every
-// FP32 summation order is fixed by the list, so results are bitwise reproducible.
+// Work decomposition: one warp per atom walks its full neighbour list (both directions of
+// every pair are listed).  An entry is the partner's slot with a 6-bit image code (written
+// by the list build, which decided the periodic image of the pair), and the partner's
+// position, charge and LJ parameters are gathered straight from the slot-ordered arrays
+// through L1: a block's warps take consecutive atoms of the slot order (atoms of one cell
+// and its neighbours), so their partners overlap and mostly hit L1 after the first touch.
+// No stencil is staged and blocks are not tied to cells.  A row holds the pairs that were
+// inside r_c at the build at its front and the others at its back.  The front part is
+// evaluated in place, 32 entries per round: while the positions are still those of the
+// build (the "fresh" flag the build sets and every load clears) every front entry is
+// inside r_c by the build's own test (the same difference and pair_r2), and otherwise the
+// few that have left r_c are masked.  The back part is tested and the pairs that have
+// come inside r_c are queued and evaluated 32 at a time.  i's data stays in registers,
+// partial sums are reduced with warp shuffles in a fixed tree, and the force on i is added
+// once, as int64 fixed point, to the zeroed force array (the PME gather and the exclusion
+// correction add their parts concurrently or later; integer addition makes the order
+// irrelevant).  Every FP32 summation order is fixed by the list, so results are bitwise
+// reproducible.
 #include "cell.cuh"
+#include "erfc.cuh"
 #include "lj.cuh"
 
 namespace nb {
@@ -27,7 +37,8 @@ constexpr int kPairWarps = 8;
 constexpr int kPairThreads = kPairWarps * 32;
 constexpr int kVjpWarps = 8;
 constexpr int kVjpThreads = kVjpWarps * 32;
-constexpr int kQueue = 64;  // per-warp queue of pairs inside r_c
+constexpr int kQueue = 64;        // per-warp queue of back-part pairs inside r_c
+constexpr int kAtomsPerWarp = 2;  // consecutive atoms of a block's range per warp (header prefetch)
 
 // Exclusion partners of slot i: count and the slot of partner e (from the per-slot
 // table when it holds all of them, else from the CSR).
@@ -46,101 +57,122 @@ struct ExclView {
     }
 };
 
-// Stage the candidates of stencil tile [t0, t1): positions (image applied, q in .w), LJ
-// parameters, optionally cotangents, and per-pair image flags.
-__device__ __forceinline__ void stage_pair_tile(const CellCtx& C, const BuildRun* runs, int nr, int t0, int t1,
-                                                int nthreads, const float4* __restrict__ xs,
-                                                const float2* __restrict__ ps, const float4* __restrict__ lam,
-                                                float4* cand, float2* par, float4* lamc, unsigned char* cflag) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = nthreads >> 5;
-    for (int r = w; r < nr; r += nw) {
-        const int sm0 = runs[r].sm0, slot0 = runs[r].slot0;
-        const int a = max(sm0, t0), b = min(sm0 + runs[r].n, t1);
-        for (int k = a + lane; k < b; k += 32) {
-            const int j = slot0 + (k - sm0);
-            cp_async16(&cand[k - t0], &xs[j]);
-            cp_async8(&par[k - t0], &ps[j]);
-            if (lamc) cp_async16(&lamc[k - t0], &lam[j]);
+// Per-atom context of the pair kernels: the atom, its row lengths and its system's constants.
+struct AtomHdr {
+    float4 xr;     // position (frame of the last build) and charge
+    float2 pi;     // sigma, sqrt(eps)
+    int nin;       // entries at the front of the row (inside r_c at the build)
+    int nout;      // entries at the back of the row
+    bool wrap;     // some entry of the row may carry an image code or fold an axis
+    int sys;       // system index
+    unsigned e0, e1, e2, e3;  // front entries lane, 32 + lane, 64 + lane, 96 + lane (0 past the end)
+};
+
+__device__ __forceinline__ AtomHdr load_hdr(int i, const int* __restrict__ sid, const float4* __restrict__ xs,
+                                            const float2* __restrict__ ps, const unsigned* __restrict__ nbr,
+                                            const int* __restrict__ cnt, const int* __restrict__ cnt_out, int cap) {
+    const int lane = threadIdx.x & 31;
+    AtomHdr H;
+    H.xr = xs[i];
+    H.pi = ps[i];
+    H.nin = cnt[i];
+    const int o = cnt_out[i];
+    H.nout = o & kOutCountMask;
+    H.wrap = (o & kOutWrapBit) != 0;
+    H.sys = sid[i];  // a system owns the same index range in slot and caller order
+    const unsigned* row = nbr + (size_t)i * cap;
+    H.e0 = lane < H.nin ? row[lane] : 0u;
+    H.e1 = 32 + lane < H.nin ? row[32 + lane] : 0u;
+    H.e2 = 64 + lane < H.nin ? row[64 + lane] : 0u;
+    H.e3 = 96 + lane < H.nin ? row[96 + lane] : 0u;
+    return H;
+}
+
+// Periodic geometry of a system as the list entries need it.
+struct PairGeo {
+    float L[3], hL[3];
+    bool fold[3];  // axis with fewer cells than the stencil spans: per-pair minimum image
+};
+
+__device__ __forceinline__ PairGeo pair_geo(const SysDev& S) {
+    PairGeo G;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        G.L[d] = S.L[d];
+        G.hL[d] = S.halfL[d];
+        G.fold[d] = S.periodic && S.nc[d] <= 2 * S.stencil;
+    }
+    return G;
+}
+
+// x_i - x_j of a list entry: image code bit 2d (x_i moves down by L) and bit 2d + 1 (x_j
+// moves down by L), each shift exact (the moved coordinate lies above L/2), or the minimum
+// image on folded axes.  The list build computed the same difference for its test.
+template <bool WRAP>
+__device__ __forceinline__ void entry_diff(const float4& xr, const float4& cj, unsigned code, const PairGeo& G,
+                                           float& dx, float& dy, float& dz) {
+    if (!WRAP) {
+        dx = xr.x - cj.x;
+        dy = xr.y - cj.y;
+        dz = xr.z - cj.z;
+        return;
+    }
+    const float xi[3] = {xr.x, xr.y, xr.z}, xj[3] = {cj.x, cj.y, cj.z};
+    float d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (G.fold[k]) {
+            d[k] = mi_pair(xi[k], xj[k], G.L[k], G.hL[k]);
+        } else {
+            const float a = (code >> (2 * k)) & 1u ? xi[k] - G.L[k] : xi[k];
+            const float b = (code >> (2 * k + 1)) & 1u ? xj[k] - G.L[k] : xj[k];
+            d[k] = a - b;
         }
     }
-    cp_async_wait_all();
-    for (int r = w; r < nr; r += nw) {
-        const BuildRun R = runs[r];
-        const int a = max(R.sm0, t0), b = min(R.sm0 + R.n, t1);
-        for (int k = a + lane; k < b; k += 32) {
-            const float4 p = cand[k - t0];
-            cand[k - t0] = make_float4(p.x + R.s[0], p.y + R.s[1], p.z + R.s[2], p.w);
-            if (C.gen) cflag[k - t0] = (unsigned char)R.flags;
-        }
-    }
+    dx = d[0];
+    dy = d[1];
+    dz = d[2];
 }
 
-// Difference x_i - x_j of atom i (frame-shifted coordinates a, raw coordinates xr) and
-// staged candidate cj.
-template <bool GEN>
-__device__ __forceinline__ void cell_diff(const CellCtx& C, float ax, float ay, float az, const float4& xr,
-                                          const float4& cj, int fl, float& dx, float& dy, float& dz) {
-    if (GEN) {
-        dx = gen_diff(xr.x, cj.x, fl, 1, C.fold[0], C.L[0], C.hL[0]);
-        dy = gen_diff(xr.y, cj.y, fl, 2, C.fold[1], C.L[1], C.hL[1]);
-        dz = gen_diff(xr.z, cj.z, fl, 4, C.fold[2], C.L[2], C.hL[2]);
-    } else {
-        dx = ax - cj.x;
-        dy = ay - cj.y;
-        dz = az - cj.z;
-    }
-}
-
-__device__ __forceinline__ void pair_vec(const float4& a, const float4& b, int per, const CellCtx& C, float& dx,
-                                         float& dy, float& dz) {
-    if (per) {
-        dx = mi_pair(a.x, b.x, C.L[0], C.hL[0]);
-        dy = mi_pair(a.y, b.y, C.L[1], C.hL[1]);
-        dz = mi_pair(a.z, b.z, C.L[2], C.hL[2]);
-    } else {
-        dx = a.x - b.x;
-        dy = a.y - b.y;
-        dz = a.z - b.z;
-    }
-}
-
-// One queued pair of the force kernel: (dx, dy, dz, q_j) and stencil index lq (r^2 is
-// recomputed with the operations of the cut-off test, so it is the same value).
+// One pair of the force kernel: (dx, dy, dz, q_j) and partner slot lq (r^2 is recomputed
+// with the operations of the cut-off test, so it is the same value).  A lane with
+// on == false contributes nothing: its coupling constants are zeroed and its r^2 set to
+// r_c^2, so its arithmetic stays finite.
 template <bool LJ, int COUL>
-__device__ __forceinline__ void pair_heavy(const float4& q, int lq, const float2& pi, bool do_lj, const PairK& K,
-                                           const float4* cand, const float2* par, float qke, float qke_lo,
-                                           float alpha, float gau_c, float& fx, float& fy, float& fz, float& elj,
-                                           float& edir) {
-    const float r2 = fmaf(q.z, q.z, fmaf(q.y, q.y, q.x * q.x));
+__device__ __forceinline__ void pair_heavy(const float4& q, int lq, bool on, const float2& pi, bool do_lj,
+                                           const PairK& K, const float2* __restrict__ par, float qke, float qke_lo, float alpha,
+                                           float gau_c, float& fx, float& fy, float& fz, float& elj, float& edir) {
+    const float r2 = on ? pair_r2(q.x, q.y, q.z) : K.rc2;
     const float rinv = rsqrtf(r2);
     float fr = 0.f;
     if (LJ && do_lj) {
         const float2 pj = par[lq];
-        const float r2inv = __frcp_rn(r2);  // correctly rounded: LJ raises it to the 6th power
-        const float eps = pi.y * pj.y;      // eps_ij = eps + eps_lo exactly
-        const float eps_lo = fmaf(pi.y, pj.y, -eps);
+        const float r2inv = __frcp_rn(r2);   // correctly rounded: LJ raises it to the 6th power
+        const float ej = on ? pj.y : 0.f;
+        const float eps = pi.y * ej;         // eps_ij = eps + eps_lo exactly
+        const float eps_lo = fmaf(pi.y, ej, -eps);
         float u, f;
         lj_unit(0.5f * (pi.x + pj.x), r2inv, rinv, r2, K, u, f);
         elj = fmaf(eps, u, fmaf(eps_lo, u, elj));
         fr = fmaf(eps_lo, f, eps * f);
     }
+    const float qj_ = on ? q.w : 0.f;
     if (COUL == kCoulEwald && K.ke != 0.f) {  // block-uniform: uncharged systems of a mixed batch skip it
         const float r = r2 * rinv;
-        const float qq = qke * q.w;
+        const float qq = qke * qj_;
         const float ar = alpha * r;
         const float ec = erfcf(ar);
         const float gau = gau_c * __expf(-ar * ar);
         // the energy is summed per unit ke q_i (q_j erfc(alpha r)/r) and scaled once per
         // atom: ke q_i q_j, rounded alike for every pair of two atom types, would make its
         // rounding add linearly over a sum that cancels ~10^3-fold
-        edir = fmaf(q.w * ec, rinv, edir);
+        edir = fmaf(qj_ * ec, rinv, edir);
         fr = fmaf(qq * fmaf(ec, rinv, gau), rinv * rinv, fr);
     }
     if (COUL == kCoulRF && K.ke != 0.f) {  // Eq. RFA: qq (1/r + k r^2 - c), f = qq (1/r^3 - 2k)
         // The pair energies of water cancel ~10^4-fold in the sum, so a rounding shared by
         // many pairs would dominate its error: ke q_i q_j (two charge values, every pair of a
         // type pair rounded alike) is carried as hi + lo, and so are k and c.
-        const float qj_ = q.w;
         const float qq = qke * qj_;
         const float qq_lo = fmaf(qke_lo, qj_, fmaf(qke, qj_, -qq));
         const float u = fmaf(K.krf, r2, rinv - K.crf) + fmaf(K.krf_lo, r2, -K.crf_lo);
@@ -164,256 +196,176 @@ __device__ __forceinline__ void sts_q_if(float4* qd, int* qj, float4 v, int j, b
         : "memory");
 }
 
-// Stencil index of slot j (-1 when j is outside the cell's stencil), found by all lanes
-// of the warp testing the runs (uniform j).
-__device__ __forceinline__ int stencil_index(const BuildRun* runs, int nr, int j) {
-    const int lane = threadIdx.x & 31;
-    int li = -1;
-    for (int r0 = 0; r0 < nr; r0 += 32) {
-        const int r = r0 + lane;
-        bool hit = false;
-        int k = 0;
-        if (r < nr) {
-            const BuildRun& R = runs[r];
-            hit = j >= R.slot0 && j < R.slot0 + R.n;
-            k = R.sm0 + (j - R.slot0);
-        }
-        const unsigned b = __ballot_sync(0xffffffffu, hit);
-        if (b) {
-            li = __shfl_sync(0xffffffffu, k, __ffs(b) - 1);
-            break;
-        }
-    }
-    return li;
-}
-
-// Header of an atom: everything its list walk needs first, loaded one atom ahead.
-struct AtomHdr {
-    float4 xr;   // position (frame of the last build) and charge
-    float2 pi;   // sigma, sqrt(eps)
-    int c;       // list length
-    uint2 g;     // this lane's four entries of the first 128-entry list group
-    uint2 g2;    // ... and of the second (rows of at least 256 entries)
-    int ej;      // lane q < table width: slot of exclusion partner q (-1: none)
-    int ne;      // number of exclusion partners
-};
-
-__device__ __forceinline__ AtomHdr load_hdr(int i, const float4* __restrict__ xs, const float2* __restrict__ ps,
-                                            const unsigned short* __restrict__ nbr, const int* __restrict__ cnt,
-                                            int cap, const ExclView& X, bool want_excl) {
-    const int lane = threadIdx.x & 31;
-    AtomHdr H;
-    H.xr = xs[i];
-    H.pi = ps[i];
-    H.c = cnt[i];
-    const uint2* row2 = reinterpret_cast<const uint2*>(nbr + (size_t)i * cap);
-    // rows hold a multiple of 128 entries, so whole 128-entry groups stay inside the row
-    H.g = row2[lane];
-    H.g2 = cap >= 256 ? row2[32 + lane] : make_uint2(0u, 0u);  // used only when c > 128
-    H.ne = (want_excl && X.ew) ? X.cnt[i] : 0;
-    H.ej = (want_excl && lane < X.ew) ? X.slot[(size_t)i * X.ew + lane] : -1;
-    return H;
-}
-
-// Forces and half energies of atom i over stencil tile [t0, t1) (one warp).
-template <bool LJ, int COUL, bool GEN, bool MULTI>
-__device__ __forceinline__ void pair_atom(const CellCtx& C, const PairK& K, int N, int i, const AtomHdr& H, int t0,
-                                          int t1, bool last, const BuildRun* runs, int nr,
-                                          const float4* cand, const float2* par, const unsigned char* cflag,
-                                          float4* qd, int* qj, const float4* __restrict__ xs,
-                                          const unsigned short* __restrict__ nbr, int cap, const ExclView& X,
-                                          long long* __restrict__ ffix, float4* __restrict__ e_atom,
-                                          float4* __restrict__ pscr, float scale, unsigned* flags) {
+// The back part of a row (pairs outside r_c at the build, stored in reverse from the end
+// of the row): tested, and the ones now inside r_c queued and evaluated 32 at a time.
+template <bool WRAP, class Heavy>
+__device__ __forceinline__ void walk_back(const float4& xr, const PairGeo& G, const unsigned* __restrict__ brow,
+                                          int nout, float rc2, const float4* __restrict__ xs, float4* qd, int* qj,
+                                          Heavy& heavy) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const float4 xr = H.xr;
-    const float ax = xr.x + C.fs[0], ay = xr.y + C.fs[1], az = xr.z + C.fs[2];
-    const float2 pi = H.pi;
-    const int c = H.c;
-    const uint2* row2 = reinterpret_cast<const uint2*>(nbr + (size_t)i * cap);
-    const float rc2 = K.rc2;
-    const float qke = K.ke * xr.w;
-    const float qke_lo = COUL == kCoulRF ? fmaf(K.ke, xr.w, -qke) : 0.f;  // ke q_i = qke + qke_lo exactly
-    const float alpha = K.alpha;
-    const float gau_c = 2.f * alpha * kInvSqrtPi;
-    const bool do_lj = pi.y != 0.f;
-    float fx = 0.f, fy = 0.f, fz = 0.f, elj = 0.f, edir = 0.f, eex = 0.f;
-    // pairs inside r_c wait in a 64-entry ring and are evaluated 32 at a time
     int head = 0, nq = 0;
-    // the list is read in groups of 128 entries: lane l holds entries 4l..4l+3 of a group
-    // (one 8-byte load); groups are loaded two ahead of the one being tested
-    uint2 ga = H.g, gb = H.g2;
-    for (int g0 = 0; g0 < c; g0 += 128) {
-        const uint2 gc = ga;
-        ga = gb;
-        if (g0 + 256 < c) gb = row2[(g0 + 256) / 4 + lane];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int k = g0 + 4 * lane + t;
-            const unsigned wv = t < 2 ? gc.x : gc.y;
-            const int li = (t & 1) ? (int)(wv >> 16) : (int)(wv & 0xffffu);
-            const bool in = k < c && (!MULTI || (li >= t0 && li < t1));
-            const int lk = in ? li - t0 : 0;  // entries outside the tile read candidate 0, unused
-            const float4 cj = cand[lk];
-            float dx, dy, dz;
-            cell_diff<GEN>(C, ax, ay, az, xr, cj, GEN ? cflag[lk] : 0, dx, dy, dz);
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const bool acc = in && r2 < rc2;
-            const unsigned bits = __ballot_sync(0xffffffffu, acc);
+    // entries two rounds ahead, the partner's position one round ahead
+    unsigned b0 = lane < nout ? brow[lane] : 0u, b1 = 32 + lane < nout ? brow[32 + lane] : 0u;
+    float4 g = xs[b0 & kEntrySlotMask];
+    for (int e0 = 0; e0 < nout; e0 += 32) {
+        const unsigned ent = b0;
+        const float4 cj = g;
+        b0 = b1;
+        const int en = e0 + 64 + lane;
+        b1 = en < nout ? brow[en] : 0u;
+        if (e0 + 32 + lane < nout) g = xs[b0 & kEntrySlotMask];
+        const bool in = e0 + lane < nout;
+        const int j = in ? (int)(ent & kEntrySlotMask) : 0;
+        float dx, dy, dz;
+        entry_diff<WRAP>(xr, cj, ent >> kEntrySlotBits, G, dx, dy, dz);
+        const bool acc = in && pair_r2(dx, dy, dz) < rc2;
+        const unsigned bits = __ballot_sync(0xffffffffu, acc);
+        if (bits) {  // warp-uniform: most back rounds accept nothing
             const int pos = (head + nq + __popc(bits & lt)) & (kQueue - 1);
-            sts_q_if(qd + pos, qj + pos, make_float4(dx, dy, dz, cj.w), lk, acc);
+            sts_q_if(qd + pos, qj + pos, make_float4(dx, dy, dz, cj.w), j, acc);
             nq += __popc(bits);
             if (nq >= 32) {
                 __syncwarp();
-                const int pos = (head + lane) & (kQueue - 1);
-                const float4 q = qd[pos];
-                const int lq = qj[pos];
+                const int p = (head + lane) & (kQueue - 1);
+                const float4 q = qd[p];
+                const int lq = qj[p];
                 __syncwarp();
-                pair_heavy<LJ, COUL>(q, lq, pi, do_lj, K, cand, par, qke, qke_lo, alpha, gau_c, fx, fy, fz, elj,
-                                     edir);
+                heavy(q, lq, true);
                 head = (head + 32) & (kQueue - 1);
                 nq -= 32;
             }
         }
     }
     __syncwarp();
-    if (lane < nq) {
-        const int pos = (head + lane) & (kQueue - 1);
-        pair_heavy<LJ, COUL>(qd[pos], qj[pos], pi, do_lj, K, cand, par, qke, qke_lo, alpha, gau_c, fx, fy, fz, elj,
-                             edir);
+    if (nq > 0) {  // warp-uniform
+        const int p = (head + lane) & (kQueue - 1);
+        const bool on = lane < nq;
+        // lanes past the queue's end hold stale or never written entries: replaced by zeros
+        const float4 q = on ? qd[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int lq = on ? qj[p] : 0;
+        __syncwarp();
+        heavy(q, lq, on);
     }
     __syncwarp();
-    if (COUL == kCoulEwald && last && alpha > 0.f && H.ne > 0) {
-        // exclusion correction for i's excluded partners (at any distance); a partner in
-        // the staged stencil is read from shared memory with its image, others from xs
-        const int ne = H.ne;
-        int lk = -1;
-        const int nin = min(ne, X.ew);
-        for (int q = 0; q < nin; ++q) {
-            const int jq = __shfl_sync(0xffffffffu, H.ej, q);
-            const int k = stencil_index(runs, nr, jq);
-            if (lane == q) lk = k;
-        }
-        for (int e = lane; e < ne; e += 32) {
-            float dx, dy, dz, qj_;
-            if (e < 32 && lk >= t0 && lk < t1) {
-                const float4 cj = cand[lk - t0];
-                cell_diff<GEN>(C, ax, ay, az, xr, cj, GEN ? cflag[lk - t0] : 0, dx, dy, dz);
-                qj_ = cj.w;
-            } else {
-                const int j = e < 32 && e < X.ew ? H.ej : X.partner(i, e);
-                const float4 xj = xs[j];
-                pair_vec(xr, xj, C.per, C, dx, dy, dz);
-                qj_ = xj.w;
-            }
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float rinv = rsqrtf(r2);
-            const float r2inv = rinv * rinv;
-            const float r = r2 * rinv;
-            const float qq = qke * qj_;
-            const float ar = alpha * r;
-            const float ef = erff(ar);
-            const float gau = gau_c * __expf(-ar * ar);
-            eex = fmaf(-qj_ * ef, rinv, eex);  // per unit ke q_i, as edir
-            const float fr = qq * (gau - ef * rinv) * r2inv;
-            fx = fmaf(fr, dx, fx);
-            fy = fmaf(fr, dy, fy);
-            fz = fmaf(fr, dz, fz);
-        }
+}
+
+// The list walk of one atom (one warp): heavy(q, j, on) is called for every round of 32
+// pairs, q = (x_i - x_j, q_j), j the partner's slot, `on` whether the lane's pair is inside
+// r_c.  Front entries go in place, the lane taking entry e0 + lane of each round; with
+// fresh lists their test is the build's own, so they are all on.  Entries are loaded four
+// rounds ahead (the first four with the atom's header, one atom ahead) and the partner's
+// position one round ahead.
+template <bool WRAP, class Heavy>
+__device__ __forceinline__ void walk_list(const AtomHdr& H, const PairGeo& G, const unsigned* __restrict__ row,
+                                          int cap, bool fresh, float rc2, const float4* __restrict__ xs, float4* qd,
+                                          int* qj, Heavy& heavy) {
+    const int lane = threadIdx.x & 31;
+    const int nin = H.nin;
+    const float4 xr = H.xr;
+    unsigned p0 = H.e0, p1 = H.e1, p2 = H.e2, p3 = H.e3;
+    float4 g = xs[lane < nin ? (int)(p0 & kEntrySlotMask) : 0];
+    for (int e0 = 0; e0 < nin; e0 += 32) {
+        const unsigned ent = p0;
+        const float4 cj = g;
+        p0 = p1;
+        p1 = p2;
+        p2 = p3;
+        const int en = e0 + 128 + lane;
+        p3 = en < nin ? row[en] : 0u;
+        if (e0 + 32 + lane < nin) g = xs[p0 & kEntrySlotMask];
+        const bool in = e0 + lane < nin;
+        float dx, dy, dz;
+        entry_diff<WRAP>(xr, cj, ent >> kEntrySlotBits, G, dx, dy, dz);
+        const bool on = in && (fresh || pair_r2(dx, dy, dz) < rc2);
+        heavy(make_float4(dx, dy, dz, cj.w), in ? (int)(ent & kEntrySlotMask) : 0, on);
     }
+    if (!fresh && H.nout > 0)
+        walk_back<WRAP>(xr, G, row + (cap - H.nout), H.nout, rc2, xs, qd, qj, heavy);
+}
+
+// Atoms of block b: [b * per_block, min(N, (b + 1) * per_block)), warp w taking atoms
+// w, w + warps, ... of the range.
+struct AtomRange {
+    int i0, i1, step;
+};
+__device__ __forceinline__ AtomRange block_atoms(int N, int per_block, int warps) {
+    AtomRange R;
+    const int b0 = blockIdx.x * per_block;
+    R.i0 = b0 + (threadIdx.x >> 5);
+    R.i1 = min(N, b0 + per_block);
+    R.step = warps;
+    return R;
+}
+
+// Forces and half energies of atom i (one warp).
+template <bool LJ, int COUL, bool WRAP>
+__device__ __forceinline__ void pair_atom(int N, int i, const AtomHdr& H, const SysDev& S, bool fresh,
+                                          const float4* __restrict__ xs, const float2* __restrict__ ps,
+                                          const unsigned* __restrict__ nbr, int cap, float4* qd, int* qj,
+                                          long long* __restrict__ ffix, float4* __restrict__ e_atom, float scale,
+                                          unsigned* flags) {
+    const int lane = threadIdx.x & 31;
+    const PairK K = pair_k(S);
+    const PairGeo G = pair_geo(S);
+    const float4 xr = H.xr;
+    const float2 pi = H.pi;
+    const float qke = K.ke * xr.w;
+    const float qke_lo = COUL == kCoulRF ? fmaf(K.ke, xr.w, -qke) : 0.f;  // ke q_i = qke + qke_lo exactly
+    const float alpha = K.alpha;
+    const float gau_c = 2.f * alpha * kInvSqrtPi;
+    const bool do_lj = pi.y != 0.f;
+    float fx = 0.f, fy = 0.f, fz = 0.f, elj = 0.f, edir = 0.f;
+    auto heavy = [&](const float4& q, int j, bool on) {
+        pair_heavy<LJ, COUL>(q, j, on, pi, do_lj, K, ps, qke, qke_lo, alpha, gau_c, fx, fy, fz, elj, edir);
+    };
+    walk_list<WRAP>(H, G, nbr + (size_t)i * cap, cap, fresh, K.rc2, xs, qd, qj, heavy);
     fx = group_sum<32>(fx);
     fy = group_sum<32>(fy);
     fz = group_sum<32>(fz);
     elj = group_sum<32>(elj);
     edir = group_sum<32>(edir);
-    eex = group_sum<32>(eex);
     if (lane == 0) {
-        if (MULTI) {  // stencil in several tiles: partial sums carried in tile order
-            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-            if (t0 > 0) {
-                a = pscr[3 * (size_t)i];
-                b = pscr[3 * (size_t)i + 1];
-            }
-            fx += a.x;
-            fy += a.y;
-            fz += a.z;
-            elj += a.w;
-            edir += b.x;
-            eex += b.y;
-            if (!last) {
-                pscr[3 * (size_t)i] = make_float4(fx, fy, fz, elj);
-                pscr[3 * (size_t)i + 1] = make_float4(edir, eex, 0.f, 0.f);
-            }
+        // added (ffix is zeroed per evaluation): the PME gather adds concurrently
+        red_add(ffix + i, to_fix(fx, scale, flags + 1));
+        red_add(ffix + (size_t)N + i, to_fix(fy, scale, flags + 1));
+        red_add(ffix + 2 * (size_t)N + i, to_fix(fz, scale, flags + 1));
+        if (COUL == kCoulEwald) {  // ke q_i = qke + (ke q_i - qke) exactly: one rounding per atom
+            const float lo = fmaf(K.ke, xr.w, -qke);
+            edir = fmaf(qke, edir, lo * edir);
         }
-        if (last) {
-            // added (ffix is zeroed per evaluation): the PME gather adds concurrently
-            red_add(ffix + i, to_fix(fx, scale, flags + 1));
-            red_add(ffix + (size_t)N + i, to_fix(fy, scale, flags + 1));
-            red_add(ffix + 2 * (size_t)N + i, to_fix(fz, scale, flags + 1));
-            if (COUL == kCoulEwald) {  // ke q_i = qke + (ke q_i - qke) exactly: one rounding per atom
-                const float lo = fmaf(K.ke, xr.w, -qke);
-                edir = fmaf(qke, edir, lo * edir);
-                eex = fmaf(qke, eex, lo * eex);
-            }
-            e_atom[i] = make_float4(0.5f * elj, 0.5f * edir, 0.5f * eex, 0.f);
-        }
+        // .z (exclusion correction) is written by k_excl
+        e_atom[i] = make_float4(0.5f * elj, 0.5f * edir, 0.f, 0.f);
     }
 }
 
+// 64 registers, four blocks (32 warps) per SM: the walk is latency-bound and the few
+// spilled values are cheaper than the lost occupancy (water 24k: 64.7 -> 63.0 us fresh,
+// 106.8 -> 99.6 us with the list reused, against 80 registers and three blocks).
 template <bool LJ, int COUL>
-__global__ void __launch_bounds__(kPairThreads) k_pair_cell(
-    int N, int cap, int tile, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
-    const int* __restrict__ start, const float4* __restrict__ xs, const float2* __restrict__ ps,
-    const unsigned short* __restrict__ nbr, const int* __restrict__ cnt, ExclView X, long long* __restrict__ ffix,
-    float4* __restrict__ e_atom, float4* __restrict__ pscr, float scale, unsigned* flags, int split) {
+__global__ void __launch_bounds__(kPairThreads, 4) k_pair(
+    int N, int per_block, int cap, const int* __restrict__ sid, const SysDev* __restrict__ sys,
+    const float4* __restrict__ xs, const float2* __restrict__ ps, const unsigned* __restrict__ nbr,
+    const int* __restrict__ cnt, const int* __restrict__ cnt_out, long long* __restrict__ ffix,
+    float4* __restrict__ e_atom, float scale, unsigned* flags) {
     pdl_wait();
-    // `split` blocks share a cell: block `part` takes atoms i0 + part*kPairWarps + w + stride*m
-    const int c = blockIdx.x / split, part = blockIdx.x % split;
-    const int stride = kPairWarps * split;
-    const SysDev& S = sys[cell_sys[c]];
-    const CellCtx C = cell_ctx(c, S, start);
-    const PairK K = pair_k(S);
-    const int ib = C.i0 + part * kPairWarps + (threadIdx.x >> 5);
-    if (C.i0 + part * kPairWarps >= C.i1) return;
-    __shared__ BuildRun runs[kMaxRuns];
-    __shared__ int n_runs, n_cand;
     __shared__ float4 qd_all[kPairWarps][kQueue];
     __shared__ int qj_all[kPairWarps][kQueue];
-    extern __shared__ float4 smem[];
-    float4* cand = smem;
-    float2* par = reinterpret_cast<float2*>(cand + tile);
-    unsigned char* cflag = reinterpret_cast<unsigned char*>(par + tile);
     const int w = threadIdx.x >> 5;
-    const bool want_excl = COUL == kCoulEwald && K.alpha > 0.f;
-    // the first atom's header is loaded while the stencil is staged
-    AtomHdr hn;
-    if (ib < C.i1) hn = load_hdr(ib, xs, ps, nbr, cnt, cap, X, want_excl);
-    if (w == 0) cell_runs(C, S, start, runs, &n_runs, &n_cand, flags);
-    __syncthreads();
-    const int nr = n_runs, total = n_cand;
-    if (total > 65536) return;  // the build has flagged the overflow
-    const bool multi = total > tile;
-    for (int t0 = 0; t0 < total; t0 += tile) {
-        const int t1 = min(total, t0 + tile);
-        stage_pair_tile(C, runs, nr, t0, t1, kPairThreads, xs, ps, nullptr, cand, par, nullptr, cflag);
-        __syncthreads();
-        const bool last = t1 == total;
-        if (t0 > 0 && ib < C.i1) hn = load_hdr(ib, xs, ps, nbr, cnt, cap, X, want_excl);
-        for (int i = ib; i < C.i1; i += stride) {
-            const AtomHdr H = hn;
-            if (i + stride < C.i1) hn = load_hdr(i + stride, xs, ps, nbr, cnt, cap, X, want_excl);
-#define NB_PAIR_ARGS C, K, N, i, H, t0, t1, last, runs, nr, cand, par, cflag, qd_all[w], qj_all[w], xs, nbr, cap, X, \
-                     ffix, e_atom, pscr, scale, flags
-            if (multi) {
-                if (C.gen) pair_atom<LJ, COUL, true, true>(NB_PAIR_ARGS);
-                else pair_atom<LJ, COUL, false, true>(NB_PAIR_ARGS);
-            } else {
-                if (C.gen) pair_atom<LJ, COUL, true, false>(NB_PAIR_ARGS);
-                else pair_atom<LJ, COUL, false, false>(NB_PAIR_ARGS);
-            }
-#undef NB_PAIR_ARGS
-        }
-        if (!last) __syncthreads();
+    const AtomRange R = block_atoms(N, per_block, kPairWarps);
+    if (R.i0 >= R.i1) return;
+    const bool fresh = flags[NB_FLAG_FRESH] != 0u;  // positions are those of the list build
+    AtomHdr hn = load_hdr(R.i0, sid, xs, ps, nbr, cnt, cnt_out, cap);
+    for (int i = R.i0; i < R.i1; i += R.step) {
+        const AtomHdr H = hn;
+        if (i + R.step < R.i1) hn = load_hdr(i + R.step, sid, xs, ps, nbr, cnt, cnt_out, cap);
+        const SysDev& S = sys[H.sys];
+        if (H.wrap)
+            pair_atom<LJ, COUL, true>(N, i, H, S, fresh, xs, ps, nbr, cap, qd_all[w], qj_all[w], ffix, e_atom,
+                                      scale, flags);
+        else
+            pair_atom<LJ, COUL, false>(N, i, H, S, fresh, xs, ps, nbr, cap, qd_all[w], qj_all[w], ffix, e_atom,
+                                       scale, flags);
     }
 }
 
@@ -426,12 +378,16 @@ struct VjpAcc {
     float gx = 0.f, gy = 0.f, gz = 0.f, gq = 0.f, gs = 0.f, ge = 0.f;
 };
 
+// One pair of the VJP kernel, q = (dx, dy, dz, q_j); r^2 with the operations of the cut-off
+// test (the same value).  A lane with on == false contributes nothing (its couplings are
+// zeroed and its r^2 set to r_c^2), as in pair_heavy.
 template <bool LJ, int COUL>
-__device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, const float2& pj,
+__device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, float2 pj, bool on,
                                           const float4& li, const float2& pi, float qi, const PairK& K,
                                           float alpha, float a2, float gau_c, VjpAcc& A) {
-    // q = (dx, dy, dz, q_j); r^2 with the operations of the cut-off test (the same value)
-    const float dx = q.x, dy = q.y, dz = q.z, r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    const float dx = q.x, dy = q.y, dz = q.z, r2 = on ? pair_r2(dx, dy, dz) : K.rc2;
+    pj.y = on ? pj.y : 0.f;
+    const float qj_ = on ? q.w : 0.f;
     const float ux = li.x - lj4.x, uy = li.y - lj4.y, uz = li.z - lj4.z;
     const float du = fmaf(dz, uz, fmaf(dy, uy, dx * ux));
     const float rinv = rsqrtf(r2);
@@ -469,28 +425,28 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, co
     }
     if (COUL == kCoulEwald && K.ke != 0.f) {  // block-uniform: uncharged systems of a mixed batch skip it
         const float r = r2 * rinv;
-        const float qq = K.ke * qi * q.w;
+        const float qq = K.ke * qi * qj_;
         const float ar = alpha * r;
         const float ec = erfcf(ar);
         const float gau = gau_c * __expf(-ar * ar);
         const float fcu = fmaf(ec, rinv, gau) * r2inv;  // f per unit qq
-        A.edir = fmaf(q.w * ec, rinv, A.edir);          // per unit ke q_i, as in the force kernel
+        A.edir = fmaf(qj_ * ec, rinv, A.edir);          // per unit ke q_i, as in the force kernel
         fr = fmaf(qq, fcu, fr);
         fpr = fmaf(-qq * r2inv, fmaf(3.f, fcu, 2.f * a2 * gau), fpr);
-        A.gq = fmaf(K.ke * q.w * fcu, du, A.gq);
+        A.gq = fmaf(K.ke * qj_ * fcu, du, A.gq);
     }
     if (COUL == kCoulRF && K.ke != 0.f) {  // Eq. RFA: f = qq (r^-3 - 2k), f'/r = -3 qq r^-5
         const float qke = K.ke * qi;
-        const float qq = qke * q.w;
+        const float qq = qke * qj_;
         // energy with ke q_i q_j, k and c as double-float pairs, as in the force kernel
-        const float qq_lo = fmaf(fmaf(K.ke, qi, -qke), q.w, fmaf(qke, q.w, -qq));
+        const float qq_lo = fmaf(fmaf(K.ke, qi, -qke), qj_, fmaf(qke, qj_, -qq));
         const float r3inv = r2inv * rinv;
         const float fcu = r3inv - 2.f * K.krf;
         const float u = fmaf(K.krf, r2, rinv - K.crf) + fmaf(K.krf_lo, r2, -K.crf_lo);
         A.edir = fmaf(qq, u, fmaf(qq_lo, u, A.edir));
         fr = fmaf(qq, fcu, fr);
         fpr = fmaf(-3.f * qq, r3inv * r2inv, fpr);
-        A.gq = fmaf(K.ke * q.w * fcu, du, A.gq);
+        A.gq = fmaf(K.ke * qj_ * fcu, du, A.gq);
     }
     const float k2 = fpr * du;
     A.gx = fmaf(fr, ux, fmaf(k2, dx, A.gx));
@@ -501,216 +457,150 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, co
     A.fz = fmaf(fr, dz, A.fz);
 }
 
-template <bool LJ, int COUL, bool GEN, bool MULTI>
-__device__ __forceinline__ void vjp_atom(const CellCtx& C, const PairK& K, int N, int i, const AtomHdr& H, int t0,
-                                         int t1, bool last, const BuildRun* runs, int nr, const float4* cand,
-                                         const float2* par, const float4* lamc, const unsigned char* cflag,
-                                         float4* qd, int* qj, const float4* __restrict__ xs,
-                                         const float4* __restrict__ lam, const unsigned short* __restrict__ nbr,
-                                         int cap, const ExclView& X, float4* __restrict__ gx_s,
-                                         float2* __restrict__ gp_s, long long* __restrict__ ffix,
-                                         float4* __restrict__ e_atom, float4* __restrict__ pscr, float scale,
+template <bool LJ, int COUL, bool WRAP>
+__device__ __forceinline__ void vjp_atom(int N, int i, const AtomHdr& H, const SysDev& S, bool fresh,
+                                         const float4* __restrict__ xs, const float2* __restrict__ ps,
+                                         const float4* __restrict__ lam, const unsigned* __restrict__ nbr, int cap,
+                                         float4* qd, int* qj, float4* __restrict__ gx_s, float2* __restrict__ gp_s,
+                                         long long* __restrict__ ffix, float4* __restrict__ e_atom, float scale,
                                          unsigned* flags) {
     const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
+    const PairK K = pair_k(S);
+    const PairGeo G = pair_geo(S);
     const float4 xr = H.xr;
-    const float ax = xr.x + C.fs[0], ay = xr.y + C.fs[1], az = xr.z + C.fs[2];
     const float2 pi = H.pi;
     const float4 li = lam[i];
-    const int c = H.c;
-    const uint2* row2 = reinterpret_cast<const uint2*>(nbr + (size_t)i * cap);
-    const float rc2 = K.rc2;
     const float alpha = K.alpha, a2 = alpha * alpha;
     const float gau_c = 2.f * alpha * kInvSqrtPi;
     VjpAcc A;
-    int head = 0, nq = 0;
-    // the list is read in groups of 128 entries: lane l holds entries 4l..4l+3 of a group
-    // (one 8-byte load); groups are loaded two ahead of the one being tested
-    uint2 ga = H.g, gb = H.g2;
-    for (int g0 = 0; g0 < c; g0 += 128) {
-        const uint2 gc = ga;
-        ga = gb;
-        if (g0 + 256 < c) gb = row2[(g0 + 256) / 4 + lane];
+    auto heavy = [&](const float4& q, int j, bool on) {
+        vjp_heavy<LJ, COUL>(q, lam[j], ps[j], on, li, pi, xr.w, K, alpha, a2, gau_c, A);
+    };
+    walk_list<WRAP>(H, G, nbr + (size_t)i * cap, cap, fresh, K.rc2, xs, qd, qj, heavy);
+    float v[11] = {A.fx, A.fy, A.fz, A.elj, A.edir, A.gx, A.gy, A.gz, A.gq, A.gs, A.ge};
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int k = g0 + 4 * lane + t;
-            const unsigned wv = t < 2 ? gc.x : gc.y;
-            const int le = (t & 1) ? (int)(wv >> 16) : (int)(wv & 0xffffu);
-            const bool in = k < c && (!MULTI || (le >= t0 && le < t1));
-            const int lk = in ? le - t0 : 0;
-            const float4 cj = cand[lk];
-            float dx, dy, dz;
-            cell_diff<GEN>(C, ax, ay, az, xr, cj, GEN ? cflag[lk] : 0, dx, dy, dz);
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const bool acc = in && r2 < rc2;
-            const unsigned bits = __ballot_sync(0xffffffffu, acc);
-            const int pos = (head + nq + __popc(bits & lt)) & (kQueue - 1);
-            sts_q_if(qd + pos, qj + pos, make_float4(dx, dy, dz, cj.w), lk, acc);
-            nq += __popc(bits);
-            if (nq >= 32) {
-                __syncwarp();
-                const int p = (head + lane) & (kQueue - 1);
-                const float4 q = qd[p];
-                const int lq = qj[p];
-                __syncwarp();
-                vjp_heavy<LJ, COUL>(q, lamc[lq], par[lq], li, pi, xr.w, K, alpha, a2, gau_c, A);
-                head = (head + 32) & (kQueue - 1);
-                nq -= 32;
-            }
-        }
-    }
-    __syncwarp();
-    if (lane < nq) {
-        const int p = (head + lane) & (kQueue - 1);
-        const int lq = qj[p];
-        vjp_heavy<LJ, COUL>(qd[p], lamc[lq], par[lq], li, pi, xr.w, K, alpha, a2, gau_c, A);
-    }
-    __syncwarp();
-    if (COUL == kCoulEwald && last && alpha > 0.f && H.ne > 0) {
-        const int ne = H.ne;
-        int lk = -1;
-        const int nin = min(ne, X.ew);
-        for (int q = 0; q < nin; ++q) {
-            const int jq = __shfl_sync(0xffffffffu, H.ej, q);
-            const int k = stencil_index(runs, nr, jq);
-            if (lane == q) lk = k;
-        }
-        for (int e = lane; e < ne; e += 32) {
-            float dx, dy, dz;
-            float4 xj, lj4;
-            if (e < 32 && lk >= t0 && lk < t1) {
-                xj = cand[lk - t0];
-                lj4 = lamc[lk - t0];
-                cell_diff<GEN>(C, ax, ay, az, xr, xj, GEN ? cflag[lk - t0] : 0, dx, dy, dz);
-            } else {
-                const int j = e < 32 && e < X.ew ? H.ej : X.partner(i, e);
-                xj = xs[j];
-                lj4 = lam[j];
-                pair_vec(xr, xj, C.per, C, dx, dy, dz);
-            }
-            const float ux = li.x - lj4.x, uy = li.y - lj4.y, uz = li.z - lj4.z;
-            const float du = fmaf(dz, uz, fmaf(dy, uy, dx * ux));
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float rinv = rsqrtf(r2);
-            const float r2inv = rinv * rinv;
-            const float r = r2 * rinv;
-            const float qq = K.ke * xr.w * xj.w;
-            const float ar = alpha * r;
-            const float ef = erff(ar);
-            const float gau = gau_c * __expf(-ar * ar);
-            const float fxu = (gau - ef * rinv) * r2inv;  // f per unit qq
-            A.eex = fmaf(-xj.w * ef, rinv, A.eex);  // per unit ke q_i
-            const float fr = qq * fxu;
-            const float fpr = -qq * r2inv * fmaf(3.f, fxu, 2.f * a2 * gau);
-            A.gq = fmaf(K.ke * xj.w * fxu, du, A.gq);
-            const float k2 = fpr * du;
-            A.gx = fmaf(fr, ux, fmaf(k2, dx, A.gx));
-            A.gy = fmaf(fr, uy, fmaf(k2, dy, A.gy));
-            A.gz = fmaf(fr, uz, fmaf(k2, dz, A.gz));
-            A.fx = fmaf(fr, dx, A.fx);
-            A.fy = fmaf(fr, dy, A.fy);
-            A.fz = fmaf(fr, dz, A.fz);
-        }
-    }
-    float v[12] = {A.fx, A.fy, A.fz, A.elj, A.edir, A.eex, A.gx, A.gy, A.gz, A.gq, A.gs, A.ge};
-#pragma unroll
-    for (int q = 0; q < 12; ++q) v[q] = group_sum<32>(v[q]);
+    for (int q = 0; q < 11; ++q) v[q] = group_sum<32>(v[q]);
     if (lane == 0) {
-        if (MULTI) {  // partial sums carried in tile order (12 scratch floats per atom)
-            float4* sp = pscr + 3 * (size_t)i;
-            if (t0 > 0) {
-                const float4 a = sp[0], b = sp[1], g = sp[2];
-                v[0] += a.x; v[1] += a.y; v[2] += a.z; v[3] += a.w;
-                v[4] += b.x; v[5] += b.y; v[6] += b.z; v[7] += b.w;
-                v[8] += g.x; v[9] += g.y; v[10] += g.z; v[11] += g.w;
-            }
-            if (!last) {
-                sp[0] = make_float4(v[0], v[1], v[2], v[3]);
-                sp[1] = make_float4(v[4], v[5], v[6], v[7]);
-                sp[2] = make_float4(v[8], v[9], v[10], v[11]);
-            }
+        ffix[i] = to_fix(v[0], scale, flags + 1);
+        ffix[(size_t)N + i] = to_fix(v[1], scale, flags + 1);
+        ffix[2 * (size_t)N + i] = to_fix(v[2], scale, flags + 1);
+        if (COUL == kCoulEwald) {  // ke q_i as hi + lo, as in the force kernel
+            const float qke = K.ke * xr.w, lo = fmaf(K.ke, xr.w, -qke);
+            v[4] = fmaf(qke, v[4], lo * v[4]);
         }
-        if (last) {
-            ffix[i] = to_fix(v[0], scale, flags + 1);
-            ffix[(size_t)N + i] = to_fix(v[1], scale, flags + 1);
-            ffix[2 * (size_t)N + i] = to_fix(v[2], scale, flags + 1);
-            if (COUL == kCoulEwald) {  // ke q_i as hi + lo, as in the force kernel
-                const float qke = K.ke * xr.w, lo = fmaf(K.ke, xr.w, -qke);
-                v[4] = fmaf(qke, v[4], lo * v[4]);
-                v[5] = fmaf(qke, v[5], lo * v[5]);
-            }
-            e_atom[i] = make_float4(0.5f * v[3], 0.5f * v[4], 0.5f * v[5], 0.f);
-            gx_s[i] = make_float4(v[6], v[7], v[8], v[9]);
-            gp_s[i] = make_float2(v[10], v[11]);
-        }
+        e_atom[i] = make_float4(0.5f * v[3], 0.5f * v[4], 0.f, 0.f);
+        gx_s[i] = make_float4(v[5], v[6], v[7], v[8]);
+        gp_s[i] = make_float2(v[9], v[10]);
     }
 }
 
 template <bool LJ, int COUL>
-// LJ-only instantiations are register-bound (small stencils): capped at 64 registers so
-// that four blocks share an SM; with Coulomb (larger staged stencils) two.
-__global__ void __launch_bounds__(kVjpThreads, COUL ? 2 : 4) k_vjp_cell(
-    int N, int cap, int tile, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
-    const int* __restrict__ start, const float4* __restrict__ xs, const float2* __restrict__ ps,
-    const float4* __restrict__ lam, const unsigned short* __restrict__ nbr, const int* __restrict__ cnt,
-    ExclView X, float4* __restrict__ gx_s, float2* __restrict__ gp_s, long long* __restrict__ ffix,
-    float4* __restrict__ e_atom, float4* __restrict__ pscr, float scale, unsigned* flags, int split) {
+// LJ-only instantiations are register-bound: capped at 64 registers so that four blocks
+// share an SM; with Coulomb two.
+__global__ void __launch_bounds__(kVjpThreads, COUL ? 2 : 4) k_vjp(
+    int N, int per_block, int cap, const int* __restrict__ sid, const SysDev* __restrict__ sys,
+    const float4* __restrict__ xs, const float2* __restrict__ ps, const float4* __restrict__ lam,
+    const unsigned* __restrict__ nbr, const int* __restrict__ cnt, const int* __restrict__ cnt_out,
+    float4* __restrict__ gx_s, float2* __restrict__ gp_s, long long* __restrict__ ffix,
+    float4* __restrict__ e_atom, float scale, unsigned* flags) {
     pdl_wait();
-    // `split` blocks share a cell, as in k_pair_cell
-    const int c = blockIdx.x / split, part = blockIdx.x % split;
-    const int stride = kVjpWarps * split;
-    const SysDev& S = sys[cell_sys[c]];
-    const CellCtx C = cell_ctx(c, S, start);
-    const int ib = C.i0 + part * kVjpWarps + (threadIdx.x >> 5);
-    if (C.i0 + part * kVjpWarps >= C.i1) return;
-    const PairK K = pair_k(S);
-    __shared__ BuildRun runs[kMaxRuns];
-    __shared__ int n_runs, n_cand;
     __shared__ float4 qd_all[kVjpWarps][kQueue];
     __shared__ int qj_all[kVjpWarps][kQueue];
-    extern __shared__ float4 smem[];
-    float4* cand = smem;
-    float4* lamc = cand + tile;
-    float2* par = reinterpret_cast<float2*>(lamc + tile);
-    unsigned char* cflag = reinterpret_cast<unsigned char*>(par + tile);
     const int w = threadIdx.x >> 5;
-    const bool want_excl = COUL == kCoulEwald && K.alpha > 0.f;
-    AtomHdr hn;
-    if (ib < C.i1) hn = load_hdr(ib, xs, ps, nbr, cnt, cap, X, want_excl);
-    if (w == 0) cell_runs(C, S, start, runs, &n_runs, &n_cand, flags);
-    __syncthreads();
-    const int nr = n_runs, total = n_cand;
-    if (total > 65536) return;
-    const bool multi = total > tile;
-    for (int t0 = 0; t0 < total; t0 += tile) {
-        const int t1 = min(total, t0 + tile);
-        stage_pair_tile(C, runs, nr, t0, t1, kVjpThreads, xs, ps, lam, cand, par, lamc, cflag);
-        __syncthreads();
-        const bool last = t1 == total;
-        if (t0 > 0 && ib < C.i1) hn = load_hdr(ib, xs, ps, nbr, cnt, cap, X, want_excl);
-        for (int i = ib; i < C.i1; i += stride) {
-            const AtomHdr H = hn;
-            if (i + stride < C.i1) hn = load_hdr(i + stride, xs, ps, nbr, cnt, cap, X, want_excl);
-#define NB_VJP_ARGS C, K, N, i, H, t0, t1, last, runs, nr, cand, par, lamc, cflag, qd_all[w], qj_all[w], xs, lam, nbr, \
-                    cap, X, gx_s, gp_s, ffix, e_atom, pscr, scale, flags
-            if (multi) {
-                if (C.gen) vjp_atom<LJ, COUL, true, true>(NB_VJP_ARGS);
-                else vjp_atom<LJ, COUL, false, true>(NB_VJP_ARGS);
-            } else {
-                if (C.gen) vjp_atom<LJ, COUL, true, false>(NB_VJP_ARGS);
-                else vjp_atom<LJ, COUL, false, false>(NB_VJP_ARGS);
-            }
-#undef NB_VJP_ARGS
-        }
-        if (!last) __syncthreads();
+    const AtomRange R = block_atoms(N, per_block, kVjpWarps);
+    if (R.i0 >= R.i1) return;
+    const bool fresh = flags[NB_FLAG_FRESH] != 0u;
+    AtomHdr hn = load_hdr(R.i0, sid, xs, ps, nbr, cnt, cnt_out, cap);
+    for (int i = R.i0; i < R.i1; i += R.step) {
+        const AtomHdr H = hn;
+        if (i + R.step < R.i1) hn = load_hdr(i + R.step, sid, xs, ps, nbr, cnt, cnt_out, cap);
+        const SysDev& S = sys[H.sys];
+        if (H.wrap)
+            vjp_atom<LJ, COUL, true>(N, i, H, S, fresh, xs, ps, lam, nbr, cap, qd_all[w], qj_all[w], gx_s, gp_s,
+                                     ffix, e_atom, scale, flags);
+        else
+            vjp_atom<LJ, COUL, false>(N, i, H, S, fresh, xs, ps, lam, nbr, cap, qd_all[w], qj_all[w], gx_s, gp_s,
+                                      ffix, e_atom, scale, flags);
     }
 }
 
-static size_t pair_smem(const nb_handle* h) {
-    return (size_t)h->tile * (sizeof(float4) + sizeof(float2) + (h->build_gen ? 1 : 0));
-}
-static size_t vjp_smem(const nb_handle* h) {
-    return (size_t)h->tile * (2 * sizeof(float4) + sizeof(float2) + (h->build_gen ? 1 : 0));
+// Exclusion correction (Ewald): for each excluded partner j of atom i (at any distance; the
+// reciprocal sum still contains the pair), -ke q_i q_j erf(alpha r)/r and its force, one
+// thread per atom (slot order), launched after the pair (or VJP) kernel.  The partners are
+// few (two per water atom), so a warp per atom in the pair kernel left most lanes idle and
+// held its block at a barrier.  The difference is the minimum image of the two positions
+// in the frame of the last build.  The force is added as fixed point (ffix is an integer
+// sum, so the order against the pair kernel's and the PME gather's adds is irrelevant);
+// the energy (per unit ke q_i, scaled by ke q_i as hi + lo) goes to e_atom[i].z, which the
+// pair kernel wrote as 0.  VJP: J (lam_i - lam_j) and the charge gradient are added to
+// gx_s[i].  Systems without Ewald electrostatics (ke = 0 or alpha = 0) are skipped.
+template <bool VJP>
+__global__ void k_excl(int N, const int* __restrict__ sid, const SysDev* __restrict__ sys,
+                       const float4* __restrict__ xs, const float4* __restrict__ lam, ExclView X,
+                       long long* __restrict__ ffix, float4* __restrict__ e_atom, float4* __restrict__ gx_s,
+                       float scale, unsigned* flags) {
+    pdl_wait();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int ne = X.count(i);
+    if (ne == 0) return;
+    const SysDev& S = sys[sid[i]];  // a system owns the same index range in slot and caller order
+    const float alpha = S.alpha, ke = S.ke;
+    if (!(alpha > 0.f) || ke == 0.f) return;
+    const float gau_c = 2.f * alpha * kInvSqrtPi, a2 = alpha * alpha;
+    const float4 xr = xs[i];
+    float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (VJP) li = lam[i];
+    const float qke = ke * xr.w;
+    float fx = 0.f, fy = 0.f, fz = 0.f, eex = 0.f, gx = 0.f, gy = 0.f, gz = 0.f, gq = 0.f;
+    for (int e = 0; e < ne; ++e) {
+        const int j = X.partner(i, e);
+        const float4 xj = xs[j];
+        float dx = xr.x - xj.x, dy = xr.y - xj.y, dz = xr.z - xj.z;
+        if (S.periodic) {
+            dx = mi_pair(xr.x, xj.x, S.L[0], S.halfL[0]);
+            dy = mi_pair(xr.y, xj.y, S.L[1], S.halfL[1]);
+            dz = mi_pair(xr.z, xj.z, S.L[2], S.halfL[2]);
+        }
+        const float r2 = pair_r2(dx, dy, dz);
+        const float rinv = rsqrtf(r2);
+        const float r2inv = rinv * rinv;
+        const float r = r2 * rinv;
+        const float qq = qke * xj.w;
+        const float ar = alpha * r;
+        const float ef = erff(ar);
+        const float gau = gau_c * __expf(-ar * ar);
+        const float fxu = (gau - ef * rinv) * r2inv;  // f per unit qq
+        eex = fmaf(-xj.w * ef, rinv, eex);
+        const float fr = qq * fxu;
+        fx = fmaf(fr, dx, fx);
+        fy = fmaf(fr, dy, fy);
+        fz = fmaf(fr, dz, fz);
+        if (VJP) {
+            const float4 lj4 = lam[j];
+            const float ux = li.x - lj4.x, uy = li.y - lj4.y, uz = li.z - lj4.z;
+            const float du = fmaf(dz, uz, fmaf(dy, uy, dx * ux));
+            const float fpr = -qq * r2inv * fmaf(3.f, fxu, 2.f * a2 * gau);
+            gq = fmaf(ke * xj.w * fxu, du, gq);
+            const float k2 = fpr * du;
+            gx = fmaf(fr, ux, fmaf(k2, dx, gx));
+            gy = fmaf(fr, uy, fmaf(k2, dy, gy));
+            gz = fmaf(fr, uz, fmaf(k2, dz, gz));
+        }
+    }
+    red_add(ffix + i, to_fix(fx, scale, flags + 1));
+    red_add(ffix + (size_t)N + i, to_fix(fy, scale, flags + 1));
+    red_add(ffix + 2 * (size_t)N + i, to_fix(fz, scale, flags + 1));
+    const float lo = fmaf(ke, xr.w, -qke);  // ke q_i = qke + lo exactly
+    reinterpret_cast<float*>(e_atom + i)[2] = 0.5f * fmaf(qke, eex, lo * eex);
+    if (VJP) {
+        float4 g = gx_s[i];
+        g.x += gx;
+        g.y += gy;
+        g.z += gz;
+        g.w += gq;
+        gx_s[i] = g;
+    }
 }
 
 static ExclView excl_view(const nb_handle* h) {
@@ -725,17 +615,37 @@ static ExclView excl_view(const nb_handle* h) {
     return X;
 }
 
+// Atoms per block of the pair and VJP kernels: kAtomsPerWarp per warp, fewer when the
+// handle is too small to give every SM a few blocks.
+static int pair_atoms_per_block(const nb_handle* h, int warps) {
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long full = (long long)warps * kAtomsPerWarp;
+    if ((long long)h->n_atoms >= full * 4LL * sms) return (int)full;
+    return warps;
+}
+
 template <bool LJ, int COUL>
 static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp) {
-    const ExclView X = excl_view(h);
-    if (vjp)
-        launch_pdl(k_vjp_cell<LJ, COUL>, h->n_cells * h->split_pair, kVjpThreads, vjp_smem(h), st,
-            h->n_atoms, h->cap, h->tile, h->cell_sys, h->sys, h->cell_start, h->xs, h->ps, h->lam, h->nbr,
-            h->nbr_cnt, X, h->gx_s, h->gp_s, h->ffix, h->e_atom, h->pscr, h->fscale, h->flags, h->split_pair);
-    else
-        launch_pdl(k_pair_cell<LJ, COUL>, h->n_cells * h->split_pair, kPairThreads, pair_smem(h), st,
-            h->n_atoms, h->cap, h->tile, h->cell_sys, h->sys, h->cell_start, h->xs, h->ps, h->nbr, h->nbr_cnt, X,
-            h->ffix, h->e_atom, h->pscr, h->fscale, h->flags, h->split_pair);
+    const int N = h->n_atoms;
+    if (vjp) {
+        const int pb = pair_atoms_per_block(h, kVjpWarps);
+        launch_pdl(k_vjp<LJ, COUL>, cdiv(N, pb), kVjpThreads, 0, st, N, pb, h->cap, h->sid, h->sys, h->xs, h->ps,
+                   h->lam, h->nbr, h->nbr_cnt, h->nbr_out, h->gx_s, h->gp_s, h->ffix, h->e_atom, h->fscale, h->flags);
+    } else {
+        const int pb = pair_atoms_per_block(h, kPairWarps);
+        launch_pdl(k_pair<LJ, COUL>, cdiv(N, pb), kPairThreads, 0, st, N, pb, h->cap, h->sid, h->sys, h->xs, h->ps,
+                   h->nbr, h->nbr_cnt, h->nbr_out, h->ffix, h->e_atom, h->fscale, h->flags);
+    }
+    if (COUL == kCoulEwald && h->excl_w) {
+        const ExclView X = excl_view(h);
+        if (vjp)
+            launch_pdl(k_excl<true>, cdiv(N, 128), 128, 0, st, N, h->sid, h->sys, h->xs, h->lam, X, h->ffix,
+                       h->e_atom, h->gx_s, h->fscale, h->flags);
+        else
+            launch_pdl(k_excl<false>, cdiv(N, 128), 128, 0, st, N, h->sid, h->sys, h->xs, (const float4*)nullptr, X,
+                       h->ffix, h->e_atom, (float4*)nullptr, h->fscale, h->flags);
+    }
 }
 
 static void dispatch(nb_handle* h, int terms, cudaStream_t st, bool vjp) {
@@ -763,42 +673,25 @@ static void dispatch(nb_handle* h, int terms, cudaStream_t st, bool vjp) {
 void launch_pair(nb_handle* h, int terms, cudaStream_t st) { dispatch(h, terms, st, false); }
 void launch_vjp(nb_handle* h, int terms, cudaStream_t st) { dispatch(h, terms, st, true); }
 
-// The dynamic shared-memory limit of a kernel is process-wide, so it is raised once to
-// what the device allows (less the kernel's static shared memory) rather than to one
-// handle's need; each launch still asks only for its own tile.
-template <class F>
-static cudaError_t allow_max_smem(F kernel) {
-    int dev = 0, optin = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa;
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-    return e;
-}
-
-template <bool LJ, int COUL>
-static cudaError_t set_smem() {
-    cudaError_t e = allow_max_smem(k_pair_cell<LJ, COUL>);
-    if (e != cudaSuccess) return e;
-    return allow_max_smem(k_vjp_cell<LJ, COUL>);
-}
-
 cudaError_t pair_setup(nb_handle* h) {
-    int dev = 0, optin = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return e;
-    // static shared memory of the VJP kernel: queues and runs (~23 KB)
-    if ((long long)vjp_smem(h) + 24 * 1024 > optin) return cudaErrorInvalidValue;
-    h->split_pair = pick_split(h, kPairWarps, 1);
-    e = set_smem<true, kCoulEwald>();
-    if (e == cudaSuccess) e = set_smem<true, kCoulRF>();
-    if (e == cudaSuccess) e = set_smem<true, kCoulNone>();
-    if (e == cudaSuccess) e = set_smem<false, kCoulEwald>();
-    if (e == cudaSuccess) e = set_smem<false, kCoulRF>();
-    return e;
+    h->split_pair = 1;
+    return cudaSuccess;
 }
 
 }  // namespace nb
+
+namespace nb {
+namespace {
+__global__ void k_erfc_eval(int n, const float* __restrict__ x, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = erfc_with_exp(x[i], exp_neg_sq(x[i]));
+}
+}  // namespace
+}  // namespace nb
+
+extern "C" nb_status nb_erfc_eval(const float* x, float* out, int32_t n, void* stream) {
+    if (n < 0 || (n > 0 && (!x || !out))) return NB_ERR_ARG;
+    if (n == 0) return NB_OK;
+    nb::k_erfc_eval<<<nb::cdiv(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, x, out);
+    return cudaGetLastError() == cudaSuccess ? NB_OK : NB_ERR_CUDA;
+}

@@ -35,6 +35,7 @@ EXPORTS = [
     "hmc_trajectory_backward", "hmc_trajectory_steps", "hmc_trajectory_steps_backward", "autocorrelation",
     "nonbonded_force_vjp", "nb_rebuild_count", "nb_blocks_per_cell", "nb_timing_enable", "nb_timing_read",
     "pme_spread_static", "nb_set_water_constraints", "langevin_step", "constrain_positions", "constrain_velocities",
+    "nb_erfc_eval",
 ]
 STATIC_MESH_MAX = 1 << 20
 STAGES = ["check", "rebuild", "pair", "spread", "fft", "convolve", "gather", "update", "build"]
@@ -146,6 +147,8 @@ def load():
     lib.nb_timing_read.argtypes = [_vp, _vp, _vp, _vp]
     lib.pme_spread_static.restype = ctypes.c_int
     lib.pme_spread_static.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp]
+    lib.nb_erfc_eval.restype = ctypes.c_int
+    lib.nb_erfc_eval.argtypes = [_vp, _vp, _i32, _vp]
     _lib = lib
     return lib
 
@@ -195,6 +198,19 @@ def pme_spread_static(xq, box, mesh, grid):
                               _ptr(grid, torch.float32, (int(np.prod(m.astype(np.int64))),), "grid"), _stream()),
         "pme_spread_static")
     return grid
+
+
+def erfc_eval(x, out=None):
+    """erfc(x) of a float32 device tensor x >= 0 with the pair kernels' own evaluation
+    (nb_erfc_eval in include/nbcore.h)."""
+    torch = _torch()
+    lib = load()
+    n = int(x.numel())
+    if out is None:
+        out = torch.empty_like(x)
+    _ok(lib.nb_erfc_eval(_ptr(x, torch.float32, (n,), "x"), _ptr(out, torch.float32, (n,), "out"), n, _stream()),
+        "nb_erfc_eval")
+    return out
 
 
 def autocorrelation(series, max_lag, a_hi=0.5, a_lo=0.05, acf=None, tau=None):

@@ -47,6 +47,7 @@ WORKLOAD = ("water box 24,000 atoms (8000 3-site molecules, 62.1 A cubic, LJ on 
 # method's own arithmetic per pair (difference, r^2 and test; LJ; erfc Coulomb), counted
 # once per unordered pair although the full list evaluates each pair from both sides.
 FLOP_LIST_PAIR = 18   # min-image difference, r^2, compare
+FLOP_DIFF_R2 = 9      # difference and r^2 of a pair taken without a test
 FLOP_LJ_PAIR = 25     # mixing, (sigma/r)^6, energy, force
 FLOP_COUL_PAIR = 45   # erfc, Gaussian, energy, force
 FLOP_EXCL_PAIR = 45   # erf correction of an excluded pair
@@ -82,7 +83,7 @@ def hbm_peak_gbs():
         return 6400.0, "fallback"
 
 BUILD_BYTES_PER_ATOM = 60  # positions read, cell ids, counts, sorted positions and permutation
-BUILD_BYTES_PER_ENTRY = 2  # one uint16 list entry written per directed pair
+BUILD_BYTES_PER_ENTRY = 4  # one 32-bit list entry (slot | image code) written per directed pair
 
 
 def parse():
@@ -273,7 +274,8 @@ def error_vs_fp64(torch, nbcore, wl, s, f_gpu, e_gpu):
     names = ["E_lj", "E_dir", "E_excl", "E_self", "E_rec"]
 
     def oracle_eval(sys_, with_pme):
-        p = oracle.make_params(sys_.box, r_cut=sys_.r_cut, r_switch=sys_.r_switch, alpha=sys_.alpha, ke=sys_.ke)
+        p = oracle.make_params(sys_.box, r_cut=sys_.r_cut, r_switch=sys_.r_switch, alpha=sys_.alpha, ke=sys_.ke,
+                               eps_rf=getattr(sys_, "eps_rf", 0.0) or 0.0)
         x = sys_.x.astype(np.float64)
         e, f = oracle.nonbonded_cells(x, sys_.q, sys_.sigma, sys_.sqrt_eps, p, excl=sys_.excl)
         e = list(e) + [0.0]
@@ -316,6 +318,20 @@ def error_vs_fp64(torch, nbcore, wl, s, f_gpu, e_gpu):
                      "energy": _energy_errors(eg[k], eo, names if sys_.ke != 0.0 else names[:1])})
         off += sys_.n
     out["batched_systems"] = rows
+    # boxes whose cancelling energy sums sit near the FP32 floor (the parity tests bound them
+    # by the random walk of the per-pair roundings where 1e-6 is below that floor)
+    small = {}
+    mix_water = [x for x in mix if x.ke != 0.0]
+    cases = (("water_rf_1800_atoms", wl.water_rf_density(600, seed=3), nbcore.NB_TERM_LJ | nbcore.NB_TERM_COUL, False),
+             ("water_8x8x8_lattice", wl.water_box(n_side=8, L=24.84, seed=9, pme_grid=24), nbcore.NB_TERM_ALL, True),
+             ("water_slab_orthorhombic", wl.water_slab(seed=7), nbcore.NB_TERM_ALL, True),
+             ("smallest_batch_water", min(mix_water, key=lambda x: x.n), nbcore.NB_TERM_ALL, True))
+    for name, sys_, terms, pme in cases:
+        fg, eg = gpu_eval([sys_], terms)
+        eo, fo = oracle_eval(sys_, pme)
+        small[name] = {"atoms": sys_.n, "force_rel_rms": _rel_rms(fg, fo),
+                       "energy": _energy_errors(eg[0], eo, names if pme else names[:2])}
+    out["small_boxes"] = small
     # HMC proposal: dH of 2 replicas of the differentiable-HMC configuration (LJ 2048,
     # switch 2.2-2.5, L 32, dt 0.005) against the FP64 velocity-Verlet proposal
     R, L, n = 2, 32, 2048
@@ -481,6 +497,13 @@ def flops_per_launch(pc):
             + FLOP_EXCL_PAIR * pc["excluded"])
 
 
+def flops_per_launch_fresh(pc):
+    """Right after a rebuild the pair kernel takes the pairs inside r_c without a test: their
+    difference and r^2 (FLOP_DIFF_R2) and math; the list's other pairs are not touched."""
+    return (FLOP_DIFF_R2 * pc["cutoff"] + FLOP_LJ_PAIR * pc["cutoff_lj"] + FLOP_COUL_PAIR * pc["cutoff"]
+            + FLOP_EXCL_PAIR * pc["excluded"])
+
+
 def profile_record(path, source="pair.cu"):
     """The figures of a committed ncu summary of a kernel, if it was taken on the current
     source of its file under csrc/ (the sha256 prefix recorded there); else None."""
@@ -519,7 +542,39 @@ def traffic_from_profile(path):
         return None
 
 
-def row_rooflines(s, st, hbm_gbs, hbm_src):
+def l2_ceilings(torch, reps=10):
+    """Measured on-chip ceilings for the PME rows, whose meshes stay in L2: the throughput of
+    64-bit integer atomic adds to random targets of an L2-resident array (torch's
+    index_add_ on int64, itself an atomic-add kernel: a lower bound of the hardware's) and
+    the copy bandwidth of an L2-resident buffer (torch copy_ of 16 MB, read + write bytes)."""
+    n_tgt, n_add = 262144, 16 * 1024 * 1024  # 2 MB of int64, like the 64^3 mesh
+    tgt = torch.zeros(n_tgt, dtype=torch.int64, device="cuda")
+    idx = torch.randint(0, n_tgt, (n_add,), device="cuda")
+    val = torch.ones(n_add, dtype=torch.int64, device="cuda")
+    a = torch.empty(4 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+
+    def best(fn):
+        fn()
+        torch.cuda.synchronize()
+        out = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            out = t if out is None else min(out, t)
+        return out
+    t_at = best(lambda: tgt.index_add_(0, idx, val))
+    t_cp = best(lambda: b.copy_(a))
+    return {"int64_atomic_adds_per_s": n_add / (t_at / 1e3), "l2_copy_gbs": 2 * a.numel() * 4 / (t_cp / 1e3) / 1e9,
+            "how": "best of %d: torch index_add_ of 16.8M int64 ones to random targets of a 2 MB array; torch copy_ "
+                   "of a 16 MB float32 buffer (both L2-resident)" % reps}
+
+
+def row_rooflines(s, st, hbm_gbs, hbm_src, l2=None):
     """HBM rooflines of the PME rows (spread, convolution, gather) of the water box from
     their per-launch CUDA-event durations, with algorithmic bytes per launch:
       spread   16 B per atom (position + charge) + 20 B per mesh point (int64 mesh read and
@@ -540,15 +595,26 @@ def row_rooflines(s, st, hbm_gbs, hbm_src):
         r.update(kw)
         return r
     t_sp = per("spread")
+    t_ga = per("gather")
+    sp_rate = 64 * n / (t_sp / 1e3)
+    sp = row("k_spread + k_grid_convert", t_sp, 16 * n + 20 * k3, mesh_atomic_adds_per_s=sp_rate,
+             note="the int64 mesh (%.1f MB) stays in L2: the spread is bound by L2 atomic throughput, not by "
+                  "HBM" % (8 * k3 / 1e6))
+    ga_bytes_l2 = 44 * n + 64 * 4 * n  # per atom: its data, and 64 mesh reads of 4 B from L2
+    ga = row("k_gather", t_ga, 44 * n + 4 * k3, note="mesh reads (64 per atom) hit L2; latency-bound")
+    if l2:
+        sp["l2_atomic_roofline"] = {"achieved": sp_rate, "peak": l2["int64_atomic_adds_per_s"], "unit": "adds/s",
+                                    "frac": sp_rate / l2["int64_atomic_adds_per_s"],
+                                    "peak_source": "measured (l2_ceilings)"}
+        ga_gbs = ga_bytes_l2 / (t_ga / 1e3) / 1e9
+        ga["l2_roofline"] = {"achieved": ga_gbs, "peak": l2["l2_copy_gbs"], "unit": "GB/s",
+                             "frac": ga_gbs / l2["l2_copy_gbs"], "bytes_per_launch": ga_bytes_l2,
+                             "peak_source": "measured (l2_ceilings)"}
     return {
-        "A7_spread": row("k_spread + k_grid_convert", t_sp, 16 * n + 20 * k3,
-                         mesh_atomic_adds_per_s=64 * n / (t_sp / 1e3),
-                         note="the int64 mesh (%.1f MB) stays in L2: the spread is bound by L2 atomic "
-                              "throughput, not by HBM" % (8 * k3 / 1e6)),
+        "A7_spread": sp,
         "A8_convolve": row("k_convolve", per("convolve"), 20 * kc),
         "A8_fft_ms_per_transform": per("fft"),
-        "A9_gather": row("k_gather", per("gather"), 44 * n + 4 * k3,
-                         note="mesh reads (64 per atom) hit L2; latency-bound"),
+        "A9_gather": ga,
         "workload": "water box 24,000 atoms, PME 64^3 order 4, PME terms alone (list reused), L2 flushed "
                     "between evaluations; cuFFT reported separately",
     }
@@ -1451,6 +1517,12 @@ def main():
         h.nonbonded_forces(xq, f, e, terms=nbcore.NB_TERM_LJ | nbcore.NB_TERM_COUL, force_rebuild=True)
     torch.cuda.synchronize()
     stages_rs = h.timing_read()
+    # the pair kernel on a kept list (the MD steady state: every list entry is tested)
+    for i in range(K):
+        lead()
+        h.nonbonded_forces(xq, f, e, terms=nbcore.NB_TERM_LJ | nbcore.NB_TERM_COUL)
+    torch.cuda.synchronize()
+    stages_ru = h.timing_read()
     # the PME kernels alone (list reused, no pair kernel sharing the SMs): their
     # per-launch durations for the row rooflines below
     for i in range(K):
@@ -1461,9 +1533,15 @@ def main():
     h.timing_enable(False)
     h.check()
 
-    # roofline of the dominant kernel (the fused pair kernel): FP32-pipe ("alu") bound
-    t_pair = stages_rs["pair"][0] / max(stages_rs["pair"][1], 1)  # ms per launch, kernel alone
+    # roofline of the fused pair kernel: FP32-pipe ("alu") bound.  The pair stage is the pair
+    # kernel and the exclusion-correction kernel.  On a kept list (the MD steady state) the
+    # kernel tests every list pair: the algorithmic count of every list pair plus the pair math.
+    # Right after a rebuild (the step timed above) it evaluates only the pairs the build found
+    # inside r_c, without a test: those pairs' math plus their difference and r^2.
+    t_pair = stages_ru["pair"][0] / max(stages_ru["pair"][1], 1)  # ms per launch, kernels alone
+    t_fresh = stages_rs["pair"][0] / max(stages_rs["pair"][1], 1)
     fl = flops_per_launch(pc)
+    fl_fresh = flops_per_launch_fresh(pc)
     achieved = fl / (t_pair / 1e3) / 1e12
     f_sm = clocks.get("sm_mhz") or 1920.0
     peak = N_SM * FP32_LANES * 2 * f_sm * 1e6 / 1e12
@@ -1483,7 +1561,9 @@ def main():
     t_bk = stages_rs["build"][0] / max(stages_rs["build"][1], 1)
     issue_build = issue_roofline(profile_record(os.path.join(ROOT, "profiles", "build_kernel_water24k.txt"),
                                                 "neighbor.cu"), t_bk, f_sm)
-    rows = row_rooflines(s, stages_pme, hbm_gbs, hbm_src)
+    l2 = l2_ceilings(torch)
+    rows = row_rooflines(s, stages_pme, hbm_gbs, hbm_src, l2)
+    rows["l2_ceilings"] = l2
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -1496,9 +1576,15 @@ def main():
                              "evaluation",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "wall_s_timed_region": t_wall},
-        "roofline": {"bound": "alu", "kernel": "k_pair (fused LJ + Ewald direct + exclusion)", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "k_pair + k_excl (fused LJ + Ewald direct; exclusion correction), "
+                                              "list kept (every list pair tested)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "flops_per_launch": fl, "pair_kernel_us": 1e3 * t_pair,
+                     "fresh_list": {"kernel": "the same kernels right after the rebuild (the timed step's): the pairs "
+                                              "inside r_c, no test", "flops_per_launch": fl_fresh,
+                                    "pair_kernel_us": 1e3 * t_fresh,
+                                    "achieved": fl_fresh / (t_fresh / 1e3) / 1e12,
+                                    "frac": fl_fresh / (t_fresh / 1e3) / 1e12 / peak},
                      "peak_source": "%d SMs (device property) x 128 FP32 lanes x 2 flop x median SM clock "
                                     "%.0f MHz (measured during the timed region)" % (N_SM, f_sm),
                      "mufu": {"ops_per_launch": mufu_ops, "peak_ops_per_s": mufu_peak,

@@ -105,13 +105,19 @@ __device__ __forceinline__ PairGeo pair_geo(const SysDev& S) {
     return G;
 }
 
+// Image handling of an atom's row (warp-uniform): plain differences, image codes, or image
+// codes with the minimum image on folded axes (systems with fewer cells than the stencil).
+constexpr int kImgPlain = 0;
+constexpr int kImgCode = 1;
+constexpr int kImgFold = 2;
+
 // x_i - x_j of a list entry: image code bit 2d (x_i moves down by L) and bit 2d + 1 (x_j
 // moves down by L), each shift exact (the moved coordinate lies above L/2), or the minimum
 // image on folded axes.  The list build computed the same difference for its test.
-template <bool WRAP>
+template <int IMG>
 __device__ __forceinline__ void entry_diff(const float4& xr, const float4& cj, unsigned code, const PairGeo& G,
                                            float& dx, float& dy, float& dz) {
-    if (!WRAP) {
+    if (IMG == kImgPlain) {
         dx = xr.x - cj.x;
         dy = xr.y - cj.y;
         dz = xr.z - cj.z;
@@ -121,7 +127,7 @@ __device__ __forceinline__ void entry_diff(const float4& xr, const float4& cj, u
     float d[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        if (G.fold[k]) {
+        if (IMG == kImgFold && G.fold[k]) {
             d[k] = mi_pair(xi[k], xj[k], G.L[k], G.hL[k]);
         } else {
             const float a = (code >> (2 * k)) & 1u ? xi[k] - G.L[k] : xi[k];
@@ -132,6 +138,11 @@ __device__ __forceinline__ void entry_diff(const float4& xr, const float4& cj, u
     dx = d[0];
     dy = d[1];
     dz = d[2];
+}
+
+__device__ __forceinline__ int img_mode(const AtomHdr& H, const PairGeo& G) {
+    if (G.fold[0] || G.fold[1] || G.fold[2]) return kImgFold;
+    return H.wrap ? kImgCode : kImgPlain;
 }
 
 // One pair of the force kernel: (dx, dy, dz, q_j) and partner slot lq (r^2 is recomputed
@@ -198,7 +209,7 @@ __device__ __forceinline__ void sts_q_if(float4* qd, int* qj, float4 v, int j, b
 
 // The back part of a row (pairs outside r_c at the build, stored in reverse from the end
 // of the row): tested, and the ones now inside r_c queued and evaluated 32 at a time.
-template <bool WRAP, class Heavy>
+template <int IMG, class Heavy>
 __device__ __forceinline__ void walk_back(const float4& xr, const PairGeo& G, const unsigned* __restrict__ brow,
                                           int nout, float rc2, const float4* __restrict__ xs, float4* qd, int* qj,
                                           Heavy& heavy) {
@@ -218,7 +229,7 @@ __device__ __forceinline__ void walk_back(const float4& xr, const PairGeo& G, co
         const bool in = e0 + lane < nout;
         const int j = in ? (int)(ent & kEntrySlotMask) : 0;
         float dx, dy, dz;
-        entry_diff<WRAP>(xr, cj, ent >> kEntrySlotBits, G, dx, dy, dz);
+        entry_diff<IMG>(xr, cj, ent >> kEntrySlotBits, G, dx, dy, dz);
         const bool acc = in && pair_r2(dx, dy, dz) < rc2;
         const unsigned bits = __ballot_sync(0xffffffffu, acc);
         if (bits) {  // warp-uniform: most back rounds accept nothing
@@ -256,7 +267,7 @@ __device__ __forceinline__ void walk_back(const float4& xr, const PairGeo& G, co
 // fresh lists their test is the build's own, so they are all on.  Entries are loaded four
 // rounds ahead (the first four with the atom's header, one atom ahead) and the partner's
 // position one round ahead.
-template <bool WRAP, class Heavy>
+template <int IMG, class Heavy>
 __device__ __forceinline__ void walk_list(const AtomHdr& H, const PairGeo& G, const unsigned* __restrict__ row,
                                           int cap, bool fresh, float rc2, const float4* __restrict__ xs, float4* qd,
                                           int* qj, Heavy& heavy) {
@@ -276,12 +287,12 @@ __device__ __forceinline__ void walk_list(const AtomHdr& H, const PairGeo& G, co
         if (e0 + 32 + lane < nin) g = xs[p0 & kEntrySlotMask];
         const bool in = e0 + lane < nin;
         float dx, dy, dz;
-        entry_diff<WRAP>(xr, cj, ent >> kEntrySlotBits, G, dx, dy, dz);
+        entry_diff<IMG>(xr, cj, ent >> kEntrySlotBits, G, dx, dy, dz);
         const bool on = in && (fresh || pair_r2(dx, dy, dz) < rc2);
         heavy(make_float4(dx, dy, dz, cj.w), in ? (int)(ent & kEntrySlotMask) : 0, on);
     }
     if (!fresh && H.nout > 0)
-        walk_back<WRAP>(xr, G, row + (cap - H.nout), H.nout, rc2, xs, qd, qj, heavy);
+        walk_back<IMG>(xr, G, row + (cap - H.nout), H.nout, rc2, xs, qd, qj, heavy);
 }
 
 // Atoms of block b: [b * per_block, min(N, (b + 1) * per_block)), warp w taking atoms
@@ -299,7 +310,7 @@ __device__ __forceinline__ AtomRange block_atoms(int N, int per_block, int warps
 }
 
 // Forces and half energies of atom i (one warp).
-template <bool LJ, int COUL, bool WRAP>
+template <bool LJ, int COUL, int IMG>
 __device__ __forceinline__ void pair_atom(int N, int i, const AtomHdr& H, const SysDev& S, bool fresh,
                                           const float4* __restrict__ xs, const float2* __restrict__ ps,
                                           const unsigned* __restrict__ nbr, int cap, float4* qd, int* qj,
@@ -319,7 +330,7 @@ __device__ __forceinline__ void pair_atom(int N, int i, const AtomHdr& H, const 
     auto heavy = [&](const float4& q, int j, bool on) {
         pair_heavy<LJ, COUL>(q, j, on, pi, do_lj, K, ps, qke, qke_lo, alpha, gau_c, fx, fy, fz, elj, edir);
     };
-    walk_list<WRAP>(H, G, nbr + (size_t)i * cap, cap, fresh, K.rc2, xs, qd, qj, heavy);
+    walk_list<IMG>(H, G, nbr + (size_t)i * cap, cap, fresh, K.rc2, xs, qd, qj, heavy);
     fx = group_sum<32>(fx);
     fy = group_sum<32>(fy);
     fz = group_sum<32>(fz);
@@ -360,12 +371,12 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_pair(
         const AtomHdr H = hn;
         if (i + R.step < R.i1) hn = load_hdr(i + R.step, sid, xs, ps, nbr, cnt, cnt_out, cap);
         const SysDev& S = sys[H.sys];
-        if (H.wrap)
-            pair_atom<LJ, COUL, true>(N, i, H, S, fresh, xs, ps, nbr, cap, qd_all[w], qj_all[w], ffix, e_atom,
-                                      scale, flags);
-        else
-            pair_atom<LJ, COUL, false>(N, i, H, S, fresh, xs, ps, nbr, cap, qd_all[w], qj_all[w], ffix, e_atom,
-                                       scale, flags);
+        const int mode = img_mode(H, pair_geo(S));
+#define NB_PAIR_ARGS N, i, H, S, fresh, xs, ps, nbr, cap, qd_all[w], qj_all[w], ffix, e_atom, scale, flags
+        if (mode == kImgPlain) pair_atom<LJ, COUL, kImgPlain>(NB_PAIR_ARGS);
+        else if (mode == kImgCode) pair_atom<LJ, COUL, kImgCode>(NB_PAIR_ARGS);
+        else pair_atom<LJ, COUL, kImgFold>(NB_PAIR_ARGS);
+#undef NB_PAIR_ARGS
     }
 }
 
@@ -457,7 +468,7 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, fl
     A.fz = fmaf(fr, dz, A.fz);
 }
 
-template <bool LJ, int COUL, bool WRAP>
+template <bool LJ, int COUL, int IMG>
 __device__ __forceinline__ void vjp_atom(int N, int i, const AtomHdr& H, const SysDev& S, bool fresh,
                                          const float4* __restrict__ xs, const float2* __restrict__ ps,
                                          const float4* __restrict__ lam, const unsigned* __restrict__ nbr, int cap,
@@ -476,7 +487,7 @@ __device__ __forceinline__ void vjp_atom(int N, int i, const AtomHdr& H, const S
     auto heavy = [&](const float4& q, int j, bool on) {
         vjp_heavy<LJ, COUL>(q, lam[j], ps[j], on, li, pi, xr.w, K, alpha, a2, gau_c, A);
     };
-    walk_list<WRAP>(H, G, nbr + (size_t)i * cap, cap, fresh, K.rc2, xs, qd, qj, heavy);
+    walk_list<IMG>(H, G, nbr + (size_t)i * cap, cap, fresh, K.rc2, xs, qd, qj, heavy);
     float v[11] = {A.fx, A.fy, A.fz, A.elj, A.edir, A.gx, A.gy, A.gz, A.gq, A.gs, A.ge};
 #pragma unroll
     for (int q = 0; q < 11; ++q) v[q] = group_sum<32>(v[q]);
@@ -515,12 +526,13 @@ __global__ void __launch_bounds__(kVjpThreads, COUL ? 2 : 4) k_vjp(
         const AtomHdr H = hn;
         if (i + R.step < R.i1) hn = load_hdr(i + R.step, sid, xs, ps, nbr, cnt, cnt_out, cap);
         const SysDev& S = sys[H.sys];
-        if (H.wrap)
-            vjp_atom<LJ, COUL, true>(N, i, H, S, fresh, xs, ps, lam, nbr, cap, qd_all[w], qj_all[w], gx_s, gp_s,
-                                     ffix, e_atom, scale, flags);
-        else
-            vjp_atom<LJ, COUL, false>(N, i, H, S, fresh, xs, ps, lam, nbr, cap, qd_all[w], qj_all[w], gx_s, gp_s,
-                                      ffix, e_atom, scale, flags);
+        const int mode = img_mode(H, pair_geo(S));
+#define NB_VJP_ARGS N, i, H, S, fresh, xs, ps, lam, nbr, cap, qd_all[w], qj_all[w], gx_s, gp_s, ffix, e_atom, scale, \
+                    flags
+        if (mode == kImgPlain) vjp_atom<LJ, COUL, kImgPlain>(NB_VJP_ARGS);
+        else if (mode == kImgCode) vjp_atom<LJ, COUL, kImgCode>(NB_VJP_ARGS);
+        else vjp_atom<LJ, COUL, kImgFold>(NB_VJP_ARGS);
+#undef NB_VJP_ARGS
     }
 }
 

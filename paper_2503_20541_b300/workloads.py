@@ -219,6 +219,26 @@ def water_box(n_side=20, L=62.1, seed=1234, jitter=0.3, r_cut=9.0, r_skin=2.25, 
                   types=np.tile(np.array([0, 1, 1], np.int32), m))
 
 
+def water_slab(seed=7, n_layers=8):
+    """A non-cubic water box: the molecules of the lowest n_layers of the 10 lattice layers
+    of a 31.05 A water box (seed), in a 31.05 x 31.05 x (n_layers * 3.105) A cell (the
+    lattice period along z, so the spacing across the boundary stays regular), PME mesh
+    32 x 32 x 26 for 8 layers."""
+    base = water_box(n_side=10, L=31.05, seed=seed, pme_grid=32)
+    m = base.n // 3
+    keep = np.where(base.x.reshape(m, 3, 3)[:, 0, 2] < n_layers * 3.105)[0]
+    sel = (3 * keep[:, None] + np.arange(3)).ravel()
+    off, idx = water_exclusions(len(keep))
+    box = np.array([31.05, 31.05, n_layers * 3.105])
+    kz = int(math.ceil(n_layers * 3.105 / 0.97))
+    s = System(name="water_slab", x=np.zeros((len(sel), 3), np.float32), q=base.q[sel], sigma=base.sigma[sel],
+               sqrt_eps=base.sqrt_eps[sel], mass=base.mass[sel], box=box, r_cut=base.r_cut, r_skin=base.r_skin,
+               alpha=base.alpha, ke=base.ke, pme_grid=(32, 32, kz), excl_off=off, excl_idx=idx,
+               types=base.types[sel])
+    s.x = np.mod(base.x[sel].astype(np.float64), s.box).astype(np.float32)
+    return s
+
+
 def water_box_density(n_mol, seed, r_cut=9.0, r_skin=2.25, alpha=0.32, jitter=0.3):
     """Water at 1 g/cm^3 with n_mol molecules; grid K = FFT-friendly >= L/0.97 A."""
     L = (n_mol / WATER_MOL_DENSITY) ** (1.0 / 3.0)

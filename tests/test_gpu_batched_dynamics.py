@@ -77,7 +77,10 @@ def test_batched_md_matches_oracle_and_single_systems():
         # the FP64 velocity-Verlet trajectory
         xo, vo, Uo, Ko = odyn.velocity_verlet(s.x.astype(np.float64), vs[k].astype(np.float64), np.ones(s.n),
                                               dt, n_steps, _oracle_fe(s))
-        np.testing.assert_allclose(Eb[:, k, 0], Uo, rtol=1e-5)
+        # the potential energy of a relaxing jittered lattice crosses zero: its FP32 error is
+        # bounded against the energy scale |U| + K of the trajectory, as the dH of HMC is
+        scale = np.abs(Uo).max() + Ko.max()
+        assert np.abs(Eb[:, k, 0] - Uo).max() <= 2e-6 * scale, (k, Eb[:, k, 0], Uo)
         np.testing.assert_allclose(Eb[:, k, 5], Ko, rtol=1e-5)
         d = odyn.min_image(xb[sl, :3].astype(np.float64) - xo, s.box)
         assert np.sqrt(np.mean(d ** 2)) < 1e-4

@@ -200,16 +200,7 @@ def test_orthorhombic_water_box_against_the_oracle():
     spacing across the boundary is regular; a different cell count, image shift and PME
     mesh size along z): forces, LJ, exclusion, self and reciprocal energies against the FP64 oracle, and the
     direct-space energy within its FP32 rounding bound (a sum that cancels by ~10^3)."""
-    base = wl.water_box(n_side=10, L=31.05, seed=7, pme_grid=32)
-    m = base.n // 3
-    keep = np.where(base.x.reshape(m, 3, 3)[:, 0, 2] < 8 * 3.105)[0]
-    sel = (3 * keep[:, None] + np.arange(3)).ravel()
-    off, idx = wl.water_exclusions(len(keep))
-    s = wl.System(name="water_slab", x=np.zeros((len(sel), 3), np.float32), q=base.q[sel], sigma=base.sigma[sel],
-                  sqrt_eps=base.sqrt_eps[sel], mass=base.mass[sel], box=np.array([31.05, 31.05, 8 * 3.105]),
-                  r_cut=base.r_cut, r_skin=base.r_skin, alpha=base.alpha, ke=base.ke, pme_grid=(32, 32, 26),
-                  excl_off=off, excl_idx=idx, types=base.types[sel])
-    s.x = np.mod(base.x[sel].astype(np.float64), s.box).astype(np.float32)
+    s = wl.water_slab(seed=7)
     with nbcore.Handle([s]) as h:
         f, e = _forces(h, s, terms=nbcore.NB_TERM_ALL)
     eo, fo = oracle_real_space(s)

@@ -620,7 +620,7 @@ def row_rooflines(s, st, hbm_gbs, hbm_src, l2=None):
     }
 
 
-def extras(torch, nbcore, wl):
+def extras(torch, nbcore, wl, f_sm=None, hbm_gbs=None):
     """MD steps/s (LJ 864), the backward/forward ratio of the differentiable HMC step and
     the batched 256-system step."""
     from paper_2503_20541_b300.graphs import CapturedStep
@@ -738,7 +738,8 @@ def extras(torch, nbcore, wl):
     out["hmc_batched_vs_single"] = hmc_batched_vs_single(torch, nbcore, wl)
     out["integrator_roofline"] = integrator_roofline(torch, nbcore, wl)
     out["water_skin_1A"] = water_skin(torch, nbcore, wl, 1.0)
-    out["lj_sweep"] = lj_sweep(torch, nbcore, wl)
+    out["lj_sweep"] = lj_sweep(torch, nbcore, wl, f_sm=f_sm, hbm_gbs=hbm_gbs)
+    out["lj_fire_check"] = fire_check(torch, nbcore, wl)
     out["water_elec_sweep"] = water_elec_sweep(torch, nbcore, wl)
     out["hmc_training"] = hmc_training(torch, nbcore, wl)
     out["hmc_lhmc"] = hmc_lhmc(torch, nbcore, wl)
@@ -908,7 +909,8 @@ def water_skin(torch, nbcore, wl, r_skin, reps=50):
     return out
 
 
-def lj_sweep(torch, nbcore, wl, sizes=(4000, 32000, 256000, 2048000, 8192000), allpairs_max=256000):
+def lj_sweep(torch, nbcore, wl, sizes=(4000, 32000, 256000, 2048000, 8192000), allpairs_max=256000, f_sm=None,
+             hbm_gbs=None):
     """LJ fluid scaling sweep (rho* 0.8442, r_c 2.5, r_skin 0.3): the linear cell-list path
     (force evaluation with the list rebuilt, with the list reused, and velocity-Verlet
     steps) against the O(N^2) all-pairs kernel on the same GPU, the latter timed up to
@@ -955,6 +957,18 @@ def lj_sweep(torch, nbcore, wl, sizes=(4000, 32000, 256000, 2048000, 8192000), a
             n_md = 50 if n <= 256000 else 10
             ms_md = timed(lambda: h.md_step(xq, v, dt, n_md, terms=nbcore.NB_TERM_LJ), 1) / n_md
             rebuilds = h.rebuild_count() - c0
+            # per-row rooflines: the pair kernel alone (stage events) on a fresh and on a kept
+            # list, and the list-build kernel
+            h.timing_enable(True)
+            h.timing_read()
+            h.nonbonded_forces(xq, f, e, terms=nbcore.NB_TERM_LJ, force_rebuild=True)
+            torch.cuda.synchronize()
+            st_f = h.timing_read()
+            h.nonbonded_forces(xq, f, e, terms=nbcore.NB_TERM_LJ)
+            torch.cuda.synchronize()
+            st_r = h.timing_read()
+            h.timing_enable(False)
+            t_pf, t_pr, t_b = st_f["pair"][0], st_r["pair"][0], st_f["build"][0]
             if n <= allpairs_max:
                 ms_ap = timed(lambda: h.nonbonded_forces_allpairs(xq, f, e), 3 if n <= 32000 else 1)
                 ap_ref = (n, ms_ap)
@@ -968,12 +982,110 @@ def lj_sweep(torch, nbcore, wl, sizes=(4000, 32000, 256000, 2048000, 8192000), a
                     "md_steps_per_s": 1e3 / ms_md})
         ap = row.get("allpairs_ms", row.get("allpairs_ms_extrapolated"))
         row["speedup_vs_allpairs"] = ap / ms_reuse
+        if f_sm:
+            peak = N_SM * FP32_LANES * 2 * f_sm * 1e6 / 1e12
+            fl_kept = FLOP_LIST_PAIR * n_list + FLOP_LJ_PAIR * n_cut
+            fl_fresh = (FLOP_DIFF_R2 + FLOP_LJ_PAIR) * n_cut
+            b_build = BUILD_BYTES_PER_ATOM * n + BUILD_BYTES_PER_ENTRY * 2 * n_list
+            row["roofline"] = {
+                "pair_kept_list": {"bound": "alu", "us": 1e3 * t_pr, "flops": fl_kept,
+                                   "frac": fl_kept / (t_pr / 1e3) / 1e12 / peak},
+                "pair_fresh_list": {"bound": "alu", "us": 1e3 * t_pf, "flops": fl_fresh,
+                                    "frac": fl_fresh / (t_pf / 1e3) / 1e12 / peak},
+                "build_kernel": {"bound": "hbm", "us": 1e3 * t_b, "bytes": b_build,
+                                 "frac": b_build / (t_b / 1e3) / 1e9 / hbm_gbs if hbm_gbs else None},
+                "peak_tflops": peak, "note": "one launch each, CUDA events of the library's stages"}
         rows.append(row)
         del xq, f, v
         torch.cuda.empty_cache()
     return {"rows": rows, "workload": "LJ fluid rho* 0.8442, r_c 2.5, r_skin 0.3 on a jittered FCC subset (stand-in "
                                       "for FIRE-relaxed random positions), list path vs all-pairs kernel; all-pairs "
                                       "timed up to %d atoms and extrapolated as N^2 beyond" % allpairs_max}
+
+
+def fire_relaxed_lj(torch, nbcore, wl, n, seed, steps=200, dt0=0.005, dt_max=0.05, max_disp=0.1):
+    """Config 3's stated inputs: uniform random positions at rho* 0.8442 relaxed by 200 FIRE
+    steps (Bitzek, Koskinen, Gaehler, Moseler and Gumbsch 2006: N_min 5, f_inc 1.1, f_dec 0.5,
+    alpha_start 0.1, f_alpha 0.99, semi-implicit Euler, dt_max 10 dt0), with the library's
+    own LJ forces.  Setup of bench inputs only.  Pairs closer than 0.6 sigma are redrawn
+    first (their forces would exceed the fixed-point range), and a step moves no atom by
+    more than max_disp."""
+    from scipy.spatial import cKDTree
+    base = wl.lj_random(n, seed=seed)
+    L = float(base.box[0])
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0.0, L, (n, 3))
+    for _ in range(200):
+        p = cKDTree(x, boxsize=L).query_pairs(0.6, output_type="ndarray")
+        if not len(p):
+            break
+        bad = np.unique(p[:, 1])
+        x[bad] = rng.uniform(0.0, L, (len(bad), 3))
+    base.x = np.mod(x, L).astype(np.float32)
+    xq = torch.from_numpy(nbcore.pack_xq(base.x, base.q)).cuda()
+    f = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    v = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    alpha, dt, npos = 0.1, dt0, 0
+    with nbcore.Handle([base]) as h:
+        h.nonbonded_forces(xq, f, None, terms=nbcore.NB_TERM_LJ)
+        for _ in range(steps):
+            P = float((f * v).sum())
+            if P > 0.0:
+                v = (1.0 - alpha) * v + alpha * torch.linalg.norm(v) * f / torch.linalg.norm(f)
+                if npos > 5:
+                    dt = min(dt * 1.1, dt_max)
+                    alpha *= 0.99
+                npos += 1
+            else:
+                v.zero_()
+                dt *= 0.5
+                alpha, npos = 0.1, 0
+            v += dt * f
+            dx = dt * v
+            m = torch.linalg.norm(dx, dim=1, keepdim=True)
+            dx = dx * torch.clamp(max_disp / torch.clamp(m, min=1e-30), max=1.0)
+            xq[:, :3] += dx
+            h.nonbonded_forces(xq, f, None, terms=nbcore.NB_TERM_LJ)
+        h.check()
+    base.x = np.mod(xq[:, :3].cpu().numpy().astype(np.float64), L).astype(np.float32)
+    return base
+
+
+def fire_check(torch, nbcore, wl, sizes=(32000, 256000), reps=20):
+    """The LJ sweep's inputs (a jittered random subset of FCC sites) against config 3's stated
+    ones (uniform random positions relaxed by 200 FIRE steps) at two sizes: list and in-cutoff
+    pair counts, and the force evaluation times with the list rebuilt and reused."""
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def measure(s):
+        xq = torch.from_numpy(nbcore.pack_xq(s.x, s.q)).cuda()
+        f = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+        s0 = copy.copy(s)
+        s0.r_skin = 0.0
+        with nbcore.Handle([s0]) as h0:
+            _, n_cut = h0.nl_build(xq, force_rebuild=True)
+        with nbcore.Handle([s]) as h:
+            _, n_list = h.nl_build(xq, force_rebuild=True)
+            t_rb = timed(lambda: h.nonbonded_forces(xq, f, None, terms=nbcore.NB_TERM_LJ, force_rebuild=True))
+            t_ru = timed(lambda: h.nonbonded_forces(xq, f, None, terms=nbcore.NB_TERM_LJ))
+            h.check()
+        return {"pairs_list_per_atom": n_list / s.n, "pairs_cutoff_per_atom": n_cut / s.n, "ms_eval_rebuild": t_rb,
+                "ms_eval_list_reused": t_ru}
+    rows = []
+    for n in sizes:
+        rows.append({"atoms": n, "jittered_fcc": measure(wl.lj_random(n, seed=500 + n % 997)),
+                     "fire_relaxed_random": measure(fire_relaxed_lj(torch, nbcore, wl, n, seed=77 + n % 991))})
+    return {"rows": rows, "workload": "LJ rho* 0.8442, r_c 2.5, r_skin 0.3: the sweep's jittered FCC subset vs "
+                                      "uniform random positions after 200 FIRE steps (library forces)"}
 
 
 def water_elec_sweep(torch, nbcore, wl, n_mols=(1000, 10000, 32000, 100000)):
@@ -1606,7 +1718,7 @@ def main():
         "gpu_launches": KERNELS_PER_STEP * K * R,
     }
     if rank == 0 and not args.no_extras:
-        out.update(extras(torch, nbcore, wl))
+        out.update(extras(torch, nbcore, wl, f_sm=f_sm, hbm_gbs=hbm_gbs))
     if rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(s, pc["cutoff"])
         # the same leg runs the oracle on the bench's own outputs: measured error per result

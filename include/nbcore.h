@@ -180,7 +180,10 @@ nb_status nl_build(nb_handle* h, const float* xq, int32_t* pairs_out, int64_t ma
  *   f_out [N][3]         (device, may be NULL) forces -dE/dx.
  *   energies [n_sys][6]  (device, may be NULL) FP64 components NB_E_* (NB_E_KIN = 0).
  * Forces are accumulated in int64 fixed point (2^force_bits units per force unit), so
- * they are bitwise reproducible run to run.
+ * they are bitwise reproducible run to run.  With energies == NULL the real-space pass
+ * runs an energy-free kernel (a polynomial erfc, 1/r^2 from 1/r, a shorter reduction):
+ * its forces agree with those of a call that asks for energies to FP32 rounding, not
+ * bit for bit.
  */
 nb_status nonbonded_forces(nb_handle* h, const float* xq, float* f_out, double* energies,
                            int32_t terms, void* stream);

@@ -131,7 +131,10 @@ nb_status run_pme_mesh(nb_handle* h, const float4* x, cudaStream_t st) {
 // and then overlaps the pair kernel.  Both add per-atom fixed-point forces into ffix
 // (zeroed by the load): integer sums, so the result does not depend on which finishes
 // first.
-nb_status eval(nb_handle* h, const float4* xq, int terms, bool force, cudaStream_t st, bool loaded = false) {
+// energy: the per-atom energies are reduced afterwards (otherwise the pair kernel runs its
+// force-only form and leaves them unwritten).
+nb_status eval(nb_handle* h, const float4* xq, int terms, bool force, cudaStream_t st, bool loaded = false,
+               bool energy = true) {
     const bool pme = (terms & NB_TERM_PME) && h->has_pme;
     {
         Stage sc(h, NB_STAGE_CHECK, st);
@@ -161,7 +164,7 @@ nb_status eval(nb_handle* h, const float4* xq, int terms, bool force, cudaStream
     }
     {
         Stage sc(h, NB_STAGE_PAIR, st);
-        launch_pair(h, terms, st);
+        launch_pair(h, terms | (energy ? kTermEnergy : 0), st);
     }
     if (pme) cudaStreamWaitEvent(st, h->ev_join, 0);
     return s;
@@ -656,7 +659,7 @@ nb_status nonbonded_forces(nb_handle* h, const float* xq, float* f_out, double* 
     DeviceGuard g(h->device);
     cudaStream_t st = S(stream);
     int t = terms & NB_TERM_ALL;
-    nb_status s = eval(h, F4(xq), t, (terms & NB_FORCE_REBUILD) != 0, st);
+    nb_status s = eval(h, F4(xq), t, (terms & NB_FORCE_REBUILD) != 0, st, false, energies != nullptr);
     if (s != NB_OK) return s;
     Stage sc(h, NB_STAGE_UPDATE, st);
     if (energies) launch_reduce_energy(h, t, 0, energies, st);
@@ -730,7 +733,7 @@ nb_status langevin_step(nb_handle* h, float* xq, float* v, const float* dt, cons
     const size_t stride = (size_t)h->n_sys * NB_NE;
     for (int step = 0; step <= n_steps; ++step) {
         if (step == n_steps && !energies) break;  // the final state's forces serve only its energies
-        nb_status s = eval(h, x4, t, step == 0 && (terms & NB_FORCE_REBUILD), st, step > 0);
+        nb_status s = eval(h, x4, t, step == 0 && (terms & NB_FORCE_REBUILD), st, step > 0, energies != nullptr);
         if (s != NB_OK) return s;
         Stage sc(h, NB_STAGE_UPDATE, st);
         if (step < n_steps) launch_langevin(h, x4, v4, dt, gamma, kT, xi + (size_t)step * 3 * h->n_atoms, st, true);
@@ -767,7 +770,7 @@ nb_status md_step(nb_handle* h, float* xq, float* v, const float* dt, int32_t n_
     nb_status s;
     for (int step = 0; step <= n_steps; ++step) {
         // after the first step the integrator has done the check of the new positions
-        s = eval(h, x4, t, step == 0 && (terms & NB_FORCE_REBUILD), st, step > 0);
+        s = eval(h, x4, t, step == 0 && (terms & NB_FORCE_REBUILD), st, step > 0, energies != nullptr);
         if (s != NB_OK) return s;
         float c_pre = step == 0 ? 0.f : 0.5f;
         float c_post = step == n_steps ? 0.f : 0.5f;
@@ -808,7 +811,8 @@ nb_status hmc_trajectory(nb_handle* h, const float* x0, float* x_out, const floa
             launch_integrate(h, x, h->vwork, inv_mass, dt, l == 0 ? 0.f : 0.5f, 0.5f, 1, cx, cv, nullptr, st,
                              StepObs(), true);
         }
-        s = eval(h, x, t, ck != nullptr && (l + 1) % ckpt_every == 0, st, true);
+        // the energies of the end state only (dH); the inner steps need forces alone
+        s = eval(h, x, t, ck != nullptr && (l + 1) % ckpt_every == 0, st, true, l == n_leap - 1);
         if (s != NB_OK) return s;
     }
     Stage sc(h, NB_STAGE_UPDATE, st);
@@ -877,11 +881,15 @@ nb_status hmc_trajectory_steps(nb_handle* h, const float* x0, float* x_out, cons
 }  // extern "C"
 
 // Reverse sweep shared by both HMC backward entry points; inj(l) gives the loss
-// cotangents entering at state l (1..n_leap).
+// cotangents entering at state l (1..n_leap).  The recomputation evaluates with the
+// energy kernel at the states where the forward pass asked for energies (the ends, or
+// every state), since the energy-free kernel rounds the forces differently: so each
+// segment repeats the forward trajectory bit for bit.
 template <class InjectAt>
 static nb_status hmc_backward(nb_handle* h, const float* x0, const float* inv_mass, const float* dt, int n_leap,
                               double kT, const float* xi, const float* ckpt, int k, InjectAt inj, double* g_dt,
-                              float* g_inv_mass, int t, cudaStream_t st) {
+                              float* g_inv_mass, int t, bool energy_every_state, cudaStream_t st) {
+    auto en_at = [&](int l) { return energy_every_state || l == 0 || l == n_leap; };
     int N = h->n_atoms;
     if (h->seg_k < k) {
         // (k+1) states of positions, velocities and half-step velocities
@@ -908,12 +916,12 @@ static nb_status hmc_backward(nb_handle* h, const float* x0, const float* inv_ma
         int s0 = j * k, e = std::min(s0 + k, n_leap), m = e - s0;
         cudaMemcpyAsync(h->xwork, ck + (size_t)j * 2 * N, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st);
         cudaMemcpyAsync(h->vwork, ck + (size_t)j * 2 * N + N, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st);
-        s = eval(h, h->xwork, t, true, st);
+        s = eval(h, h->xwork, t, true, st, false, en_at(s0));
         if (s != NB_OK) return s;
         for (int q = 0; q < m; ++q) {
             launch_integrate(h, h->xwork, h->vwork, inv_mass, dt, q == 0 ? 0.f : 0.5f, 0.5f, 1, seg_x(q), seg_v(q),
                              seg_p(q + 1), st, StepObs(), true);
-            s = eval(h, h->xwork, t, false, st, true);
+            s = eval(h, h->xwork, t, false, st, true, en_at(s0 + q + 1));
             if (s != NB_OK) return s;
         }
         launch_integrate(h, h->xwork, h->vwork, inv_mass, dt, 0.5f, 0.f, 0, seg_x(m), seg_v(m), nullptr, st);
@@ -929,7 +937,7 @@ static nb_status hmc_backward(nb_handle* h, const float* x0, const float* inv_ma
             launch_bwd_adjoint(h, inv_mass, dt, seg_x(q), seg_v(q), F4(x0), in, kT, seg_p(q), g_inv_mass, st);
         }
     }
-    s = eval(h, F4(x0), t, false, st);
+    s = eval(h, F4(x0), t, false, st, false, true);
     if (s != NB_OK) return s;
     launch_bwd_final(h, inv_mass, dt, xi, kT, g_inv_mass, g_dt, st);
     return launched();
@@ -957,7 +965,7 @@ nb_status hmc_trajectory_backward(nb_handle* h, const float* x0, const float* in
         return in;
     };
     return hmc_backward(h, x0, inv_mass, dt, L, kT, xi, ckpt, ckpt_every, inj, g_dt, g_inv_mass,
-                        terms & NB_TERM_ALL, S(stream));
+                        terms & NB_TERM_ALL, false, S(stream));
 }
 
 nb_status hmc_trajectory_steps_backward(nb_handle* h, const float* x0, const float* inv_mass, const float* dt,
@@ -979,7 +987,7 @@ nb_status hmc_trajectory_steps_backward(nb_handle* h, const float* x0, const flo
         return in;
     };
     return hmc_backward(h, x0, inv_mass, dt, n_leap, kT, xi, ckpt, ckpt_every, inj, g_dt, g_inv_mass,
-                        terms & NB_TERM_ALL, S(stream));
+                        terms & NB_TERM_ALL, true, S(stream));
 }
 
 nb_status nonbonded_force_vjp(nb_handle* h, const float* xq, const float* lam, float* gx, float* gq, float* gsigma,

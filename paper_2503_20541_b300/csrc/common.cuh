@@ -39,6 +39,9 @@ constexpr int kSmallSortAtoms = 8192;          // handles re-slotted by one bloc
 // count (u64), [NB_FLAG_FRESH] 1 while the slot positions are exactly those of the last list
 // build (set by the build, cleared by every load of new positions).
 constexpr int NB_FLAG_FRESH = 4;
+// Internal bit of the `terms` passed to launch_pair: the per-atom energies are wanted (an
+// evaluation whose energies nobody reduces runs the pair kernel's force-only form).
+constexpr int kTermEnergy = 1 << 16;
 constexpr int kFlagWords = 8;
 // A neighbour-list entry: the partner's slot in the low kEntrySlotBits bits and, above them,
 // the pair's periodic image as 2 bits per axis d: bit 2d, atom i moves down by L; bit 2d + 1,
@@ -263,6 +266,35 @@ __device__ __forceinline__ float group_sum(float v) {
 #pragma unroll
     for (int o = P / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Warp sums of NV values (NV a power of two, 2..32) by a transposed butterfly: at each of
+// the first log2(NV) levels a lane keeps half of its values and sends the other half to
+// its partner, so every level moves half as many values as the last; the remaining levels
+// are plain pairwise sums.  Returns, in lane l, the warp sum of value l >> (5 - log2 NV)
+// (NV - 1 + 5 - log2 NV shuffles instead of 5 NV).  The summation order is fixed.
+template <int NV>
+__device__ __forceinline__ float warp_sum_transposed(float (&v)[NV]) {
+    const int lane = threadIdx.x & 31;
+    int n = NV, o = 16;
+#pragma unroll
+    for (int lev = 0; (1 << lev) < NV; ++lev) {
+        n >>= 1;
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < NV / 2; ++k) {
+            if (k < n) {
+                const float keep = upper ? v[n + k] : v[k];
+                const float give = upper ? v[k] : v[n + k];
+                v[k] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+            }
+        }
+        o >>= 1;
+    }
+    float r = v[0];
+#pragma unroll
+    for (; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
 }
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -1,6 +1,8 @@
 // erfc.cuh -- complementary error function of the Ewald direct-space pair term (Sec. 2.1.2:
-// ke q_i q_j erfc(alpha r)/r), written for the pair kernels so that the Gaussian of the
-// force, exp(-(alpha r)^2), and erfc share one exponential and no division.
+// ke q_i q_j erfc(alpha r)/r), written for the pair kernel's force-only form so that the
+// Gaussian of the force, exp(-(alpha r)^2), and erfc share one exponential and no division.
+// Its error (a few ulp) is far inside the force tolerance; the energy sums, which cancel
+// ~1000-fold, are evaluated with CUDA's erfcf, whose residual error is smoother.
 //
 //   erfc(x) = exp(-x^2) erfcx(x),   x >= 0,
 //   erfcx(x) = t P(2t - 1),         t = 1 / (1 + x/2) in (0, 1],

@@ -148,23 +148,28 @@ __device__ __forceinline__ int img_mode(const AtomHdr& H, const PairGeo& G) {
 // One pair of the force kernel: (dx, dy, dz, q_j) and partner slot lq (r^2 is recomputed
 // with the operations of the cut-off test, so it is the same value).  A lane with
 // on == false contributes nothing: its coupling constants are zeroed and its r^2 set to
-// r_c^2, so its arithmetic stays finite.
-template <bool LJ, int COUL>
+// r_c^2, so its arithmetic stays finite.  EN: the energies are wanted.  Without them the
+// pair is evaluated for its force alone: erfc from the fitted form of erfc.cuh sharing its
+// exponential with the Gaussian (a few ulp, far inside the force tolerance; the energy sums
+// cancel ~1000-fold and need CUDA's erfcf), and 1/r^2 as (1/r)^2.
+template <bool LJ, int COUL, bool EN>
 __device__ __forceinline__ void pair_heavy(const float4& q, int lq, bool on, const float2& pi, bool do_lj,
-                                           const PairK& K, const float2* __restrict__ par, float qke, float qke_lo, float alpha,
-                                           float gau_c, float& fx, float& fy, float& fz, float& elj, float& edir) {
+                                           const PairK& K, const float2* __restrict__ par, float qke, float qke_lo,
+                                           float alpha, float gau_c, float& fx, float& fy, float& fz, float& elj,
+                                           float& edir) {
     const float r2 = on ? pair_r2(q.x, q.y, q.z) : K.rc2;
     const float rinv = rsqrtf(r2);
     float fr = 0.f;
     if (LJ && do_lj) {
         const float2 pj = par[lq];
-        const float r2inv = __frcp_rn(r2);   // correctly rounded: LJ raises it to the 6th power
+        // correctly rounded for the energy: LJ raises it to the 6th power
+        const float r2inv = EN ? __frcp_rn(r2) : rinv * rinv;
         const float ej = on ? pj.y : 0.f;
         const float eps = pi.y * ej;         // eps_ij = eps + eps_lo exactly
         const float eps_lo = fmaf(pi.y, ej, -eps);
         float u, f;
         lj_unit(0.5f * (pi.x + pj.x), r2inv, rinv, r2, K, u, f);
-        elj = fmaf(eps, u, fmaf(eps_lo, u, elj));
+        if (EN) elj = fmaf(eps, u, fmaf(eps_lo, u, elj));
         fr = fmaf(eps_lo, f, eps * f);
     }
     const float qj_ = on ? q.w : 0.f;
@@ -172,12 +177,19 @@ __device__ __forceinline__ void pair_heavy(const float4& q, int lq, bool on, con
         const float r = r2 * rinv;
         const float qq = qke * qj_;
         const float ar = alpha * r;
-        const float ec = erfcf(ar);
-        const float gau = gau_c * __expf(-ar * ar);
-        // the energy is summed per unit ke q_i (q_j erfc(alpha r)/r) and scaled once per
-        // atom: ke q_i q_j, rounded alike for every pair of two atom types, would make its
-        // rounding add linearly over a sum that cancels ~10^3-fold
-        edir = fmaf(qj_ * ec, rinv, edir);
+        float ec, gau;
+        if (EN) {
+            ec = erfcf(ar);
+            gau = gau_c * __expf(-ar * ar);
+            // the energy is summed per unit ke q_i (q_j erfc(alpha r)/r) and scaled once per
+            // atom: ke q_i q_j, rounded alike for every pair of two atom types, would make its
+            // rounding add linearly over a sum that cancels ~10^3-fold
+            edir = fmaf(qj_ * ec, rinv, edir);
+        } else {
+            const float E = exp_neg_sq(ar);
+            ec = erfc_with_exp(ar, E);
+            gau = gau_c * E;
+        }
         fr = fmaf(qq * fmaf(ec, rinv, gau), rinv * rinv, fr);
     }
     if (COUL == kCoulRF && K.ke != 0.f) {  // Eq. RFA: qq (1/r + k r^2 - c), f = qq (1/r^3 - 2k)
@@ -185,9 +197,11 @@ __device__ __forceinline__ void pair_heavy(const float4& q, int lq, bool on, con
         // many pairs would dominate its error: ke q_i q_j (two charge values, every pair of a
         // type pair rounded alike) is carried as hi + lo, and so are k and c.
         const float qq = qke * qj_;
-        const float qq_lo = fmaf(qke_lo, qj_, fmaf(qke, qj_, -qq));
-        const float u = fmaf(K.krf, r2, rinv - K.crf) + fmaf(K.krf_lo, r2, -K.crf_lo);
-        edir = fmaf(qq, u, fmaf(qq_lo, u, edir));
+        if (EN) {
+            const float qq_lo = fmaf(qke_lo, qj_, fmaf(qke, qj_, -qq));
+            const float u = fmaf(K.krf, r2, rinv - K.crf) + fmaf(K.krf_lo, r2, -K.crf_lo);
+            edir = fmaf(qq, u, fmaf(qq_lo, u, edir));
+        }
         fr = fmaf(qq, fmaf(rinv * rinv, rinv, -2.f * K.krf), fr);
     }
     fx = fmaf(fr, q.x, fx);
@@ -309,8 +323,8 @@ __device__ __forceinline__ AtomRange block_atoms(int N, int per_block, int warps
     return R;
 }
 
-// Forces and half energies of atom i (one warp).
-template <bool LJ, int COUL, int IMG>
+// Forces and (EN) half energies of atom i (one warp).
+template <bool LJ, int COUL, bool EN, int IMG>
 __device__ __forceinline__ void pair_atom(int N, int i, const AtomHdr& H, const SysDev& S, bool fresh,
                                           const float4* __restrict__ xs, const float2* __restrict__ ps,
                                           const unsigned* __restrict__ nbr, int cap, float4* qd, int* qj,
@@ -328,32 +342,42 @@ __device__ __forceinline__ void pair_atom(int N, int i, const AtomHdr& H, const 
     const bool do_lj = pi.y != 0.f;
     float fx = 0.f, fy = 0.f, fz = 0.f, elj = 0.f, edir = 0.f;
     auto heavy = [&](const float4& q, int j, bool on) {
-        pair_heavy<LJ, COUL>(q, j, on, pi, do_lj, K, ps, qke, qke_lo, alpha, gau_c, fx, fy, fz, elj, edir);
+        pair_heavy<LJ, COUL, EN>(q, j, on, pi, do_lj, K, ps, qke, qke_lo, alpha, gau_c, fx, fy, fz, elj, edir);
     };
     walk_list<IMG>(H, G, nbr + (size_t)i * cap, cap, fresh, K.rc2, xs, qd, qj, heavy);
-    fx = group_sum<32>(fx);
-    fy = group_sum<32>(fy);
-    fz = group_sum<32>(fz);
-    elj = group_sum<32>(elj);
-    edir = group_sum<32>(edir);
-    if (lane == 0) {
+    if (!EN) {  // lane 8k holds the warp sum of force component k; no energy record
+        float v[4] = {fx, fy, fz, 0.f};
+        const float sum = warp_sum_transposed<4>(v);
+        const int k = lane >> 3;
+        if ((lane & 7) == 0 && k < 3) red_add(ffix + (size_t)k * N + i, to_fix(sum, scale, flags + 1));
+        return;
+    }
+    // lane 4k holds the warp sum of value k: fx, fy, fz, elj, edir
+    float v[8] = {fx, fy, fz, elj, edir, 0.f, 0.f, 0.f};
+    const float sum = warp_sum_transposed<8>(v);
+    const int k = lane >> 2;
+    if ((lane & 3) == 0 && k < 3) {
         // added (ffix is zeroed per evaluation): the PME gather adds concurrently
-        red_add(ffix + i, to_fix(fx, scale, flags + 1));
-        red_add(ffix + (size_t)N + i, to_fix(fy, scale, flags + 1));
-        red_add(ffix + 2 * (size_t)N + i, to_fix(fz, scale, flags + 1));
+        red_add(ffix + (size_t)k * N + i, to_fix(sum, scale, flags + 1));
+    } else if (lane == 12) {
+        reinterpret_cast<float*>(e_atom + i)[0] = 0.5f * sum;
+    } else if (lane == 16) {
+        float ed = sum;
         if (COUL == kCoulEwald) {  // ke q_i = qke + (ke q_i - qke) exactly: one rounding per atom
             const float lo = fmaf(K.ke, xr.w, -qke);
-            edir = fmaf(qke, edir, lo * edir);
+            ed = fmaf(qke, ed, lo * ed);
         }
+        reinterpret_cast<float*>(e_atom + i)[1] = 0.5f * ed;
+    } else if (lane == 20) {
         // .z (exclusion correction) is written by k_excl
-        e_atom[i] = make_float4(0.5f * elj, 0.5f * edir, 0.f, 0.f);
+        reinterpret_cast<float2*>(e_atom + i)[1] = make_float2(0.f, 0.f);
     }
 }
 
 // 64 registers, four blocks (32 warps) per SM: the walk is latency-bound and the few
 // spilled values are cheaper than the lost occupancy (water 24k: 64.7 -> 63.0 us fresh,
 // 106.8 -> 99.6 us with the list reused, against 80 registers and three blocks).
-template <bool LJ, int COUL>
+template <bool LJ, int COUL, bool EN>
 __global__ void __launch_bounds__(kPairThreads, 4) k_pair(
     int N, int per_block, int cap, const int* __restrict__ sid, const SysDev* __restrict__ sys,
     const float4* __restrict__ xs, const float2* __restrict__ ps, const unsigned* __restrict__ nbr,
@@ -373,9 +397,9 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_pair(
         const SysDev& S = sys[H.sys];
         const int mode = img_mode(H, pair_geo(S));
 #define NB_PAIR_ARGS N, i, H, S, fresh, xs, ps, nbr, cap, qd_all[w], qj_all[w], ffix, e_atom, scale, flags
-        if (mode == kImgPlain) pair_atom<LJ, COUL, kImgPlain>(NB_PAIR_ARGS);
-        else if (mode == kImgCode) pair_atom<LJ, COUL, kImgCode>(NB_PAIR_ARGS);
-        else pair_atom<LJ, COUL, kImgFold>(NB_PAIR_ARGS);
+        if (mode == kImgPlain) pair_atom<LJ, COUL, EN, kImgPlain>(NB_PAIR_ARGS);
+        else if (mode == kImgCode) pair_atom<LJ, COUL, EN, kImgCode>(NB_PAIR_ARGS);
+        else pair_atom<LJ, COUL, EN, kImgFold>(NB_PAIR_ARGS);
 #undef NB_PAIR_ARGS
     }
 }
@@ -488,20 +512,24 @@ __device__ __forceinline__ void vjp_atom(int N, int i, const AtomHdr& H, const S
         vjp_heavy<LJ, COUL>(q, lam[j], ps[j], on, li, pi, xr.w, K, alpha, a2, gau_c, A);
     };
     walk_list<IMG>(H, G, nbr + (size_t)i * cap, cap, fresh, K.rc2, xs, qd, qj, heavy);
-    float v[11] = {A.fx, A.fy, A.fz, A.elj, A.edir, A.gx, A.gy, A.gz, A.gq, A.gs, A.ge};
+    // lane 2k holds the warp sum of value k
+    float v[16] = {A.fx, A.fy, A.fz, A.elj, A.edir, A.gx, A.gy, A.gz, A.gq, A.gs, A.ge, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float sum = warp_sum_transposed<16>(v);
+    const int k = lane >> 1;
+    if (COUL == kCoulEwald && k == 4) {  // ke q_i as hi + lo, as in the force kernel
+        const float qke = K.ke * xr.w, lo = fmaf(K.ke, xr.w, -qke);
+        sum = fmaf(qke, sum, lo * sum);
+    }
+    // the fixed-point forces by lanes 0, 2, 4 in parallel; the other sums go to lane 0 (one
+    // shuffle each), which writes the atom's energy and gradient records
+    if ((lane & 1) == 0 && k < 3) ffix[(size_t)k * N + i] = to_fix(sum, scale, flags + 1);
+    float w[11];
 #pragma unroll
-    for (int q = 0; q < 11; ++q) v[q] = group_sum<32>(v[q]);
+    for (int q = 3; q < 11; ++q) w[q] = __shfl_sync(0xffffffffu, sum, 2 * q);
     if (lane == 0) {
-        ffix[i] = to_fix(v[0], scale, flags + 1);
-        ffix[(size_t)N + i] = to_fix(v[1], scale, flags + 1);
-        ffix[2 * (size_t)N + i] = to_fix(v[2], scale, flags + 1);
-        if (COUL == kCoulEwald) {  // ke q_i as hi + lo, as in the force kernel
-            const float qke = K.ke * xr.w, lo = fmaf(K.ke, xr.w, -qke);
-            v[4] = fmaf(qke, v[4], lo * v[4]);
-        }
-        e_atom[i] = make_float4(0.5f * v[3], 0.5f * v[4], 0.f, 0.f);
-        gx_s[i] = make_float4(v[5], v[6], v[7], v[8]);
-        gp_s[i] = make_float2(v[9], v[10]);
+        e_atom[i] = make_float4(0.5f * w[3], 0.5f * w[4], 0.f, 0.f);
+        gx_s[i] = make_float4(w[5], w[6], w[7], w[8]);
+        gp_s[i] = make_float2(w[9], w[10]);
     }
 }
 
@@ -638,7 +666,7 @@ static int pair_atoms_per_block(const nb_handle* h, int warps) {
 }
 
 template <bool LJ, int COUL>
-static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp) {
+static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp, bool energy) {
     const int N = h->n_atoms;
     if (vjp) {
         const int pb = pair_atoms_per_block(h, kVjpWarps);
@@ -646,8 +674,9 @@ static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp) {
                    h->lam, h->nbr, h->nbr_cnt, h->nbr_out, h->gx_s, h->gp_s, h->ffix, h->e_atom, h->fscale, h->flags);
     } else {
         const int pb = pair_atoms_per_block(h, kPairWarps);
-        launch_pdl(k_pair<LJ, COUL>, cdiv(N, pb), kPairThreads, 0, st, N, pb, h->cap, h->sid, h->sys, h->xs, h->ps,
-                   h->nbr, h->nbr_cnt, h->nbr_out, h->ffix, h->e_atom, h->fscale, h->flags);
+        launch_pdl(energy ? k_pair<LJ, COUL, true> : k_pair<LJ, COUL, false>, cdiv(N, pb), kPairThreads, 0, st, N,
+                   pb, h->cap, h->sid, h->sys, h->xs, h->ps, h->nbr, h->nbr_cnt, h->nbr_out, h->ffix, h->e_atom,
+                   h->fscale, h->flags);
     }
     if (COUL == kCoulEwald && h->excl_w) {
         const ExclView X = excl_view(h);
@@ -675,11 +704,12 @@ static void dispatch(nb_handle* h, int terms, cudaStream_t st, bool vjp) {
         }
         return;
     }
-    if (lj && coul && rf) pair_launch<true, kCoulRF>(h, st, vjp);
-    else if (lj && coul) pair_launch<true, kCoulEwald>(h, st, vjp);
-    else if (lj) pair_launch<true, kCoulNone>(h, st, vjp);
-    else if (coul && rf) pair_launch<false, kCoulRF>(h, st, vjp);
-    else pair_launch<false, kCoulEwald>(h, st, vjp);
+    const bool en = vjp || (terms & kTermEnergy) != 0;
+    if (lj && coul && rf) pair_launch<true, kCoulRF>(h, st, vjp, en);
+    else if (lj && coul) pair_launch<true, kCoulEwald>(h, st, vjp, en);
+    else if (lj) pair_launch<true, kCoulNone>(h, st, vjp, en);
+    else if (coul && rf) pair_launch<false, kCoulRF>(h, st, vjp, en);
+    else pair_launch<false, kCoulEwald>(h, st, vjp, en);
 }
 
 void launch_pair(nb_handle* h, int terms, cudaStream_t st) { dispatch(h, terms, st, false); }

@@ -2,7 +2,7 @@
 
 Forward: dH, acceptance probability and squared jump of every intermediate state of
 every replica against the FP64 oracle trajectory; the proposal after the drawn length;
-with every length at L_q, the same chain state as the fixed-length proposal.  Backward:
+with every length at L_q, the fixed-length proposal's chain state (to FP32 rounding).  Backward:
 the gradient of the step-weighted loss with respect to dt and the inverse masses against
 FP64 central differences of the oracle loss.  A(k) and tau_exp against the oracle.
 """
@@ -115,13 +115,24 @@ def test_steps_at_full_length_equal_the_fixed_length_proposal():
                          terms=nbcore.NB_TERM_LJ)
         h.check()
     # same integrator and list rebuild schedule (the checkpoints force the same
-    # rebuilds): identical states and energies; the jump sums the same per-atom terms
-    # in another order
-    assert torch.equal(ck_a, ck_b)
-    assert torch.equal(x_a, x_b)
+    # rebuilds).  The fixed-length proposal asks for energies only at its last step, so
+    # its other force evaluations take the energy-free kernel (another erfc and 1/r^2,
+    # another reduction tree): states agree to FP32 rounding, not bit for bit.
+    ca, cb = ck_a.cpu().numpy().astype(np.float64), ck_b.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(ca - cb)) <= 1e-4 * max(1.0, float(np.max(np.abs(ca))))
+    xa, xb = x_a.cpu().numpy().astype(np.float64), x_b.cpu().numpy().astype(np.float64)
+    d = xa[:, :3] - xb[:, :3]
+    d -= systems[0].box * np.round(d / systems[0].box)
+    assert np.max(np.abs(d)) <= 1e-4
+    np.testing.assert_array_equal(xa[:, 3], xb[:, 3])
     sa, sb = st_a.cpu().numpy(), st_b.cpu().numpy()
-    np.testing.assert_array_equal(sa[:, [0, 1, 3]], sb[:, [0, 1, 3]])
-    np.testing.assert_allclose(sa[:, 2], sb[:, 2], rtol=1e-13)
+    n = systems[0].n
+    for r, s in enumerate(systems):
+        scale = _energy_scale(s, xi[r], w[r * n:(r + 1) * n])
+        assert abs(sa[r, 0] - sb[r, 0]) <= 2e-6 * scale, (r, sa[r, 0], sb[r, 0])
+        assert abs(sa[r, 1] - sb[r, 1]) <= 2e-6 * scale
+        assert sa[r, 3] == sb[r, 3]  # u keeps off the FP32 band of alpha
+    np.testing.assert_allclose(sa[:, 2], sb[:, 2], rtol=1e-4)
 
 
 def _oracle_loss(s, xi, w, dt, coef):

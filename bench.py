@@ -95,6 +95,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--cpu-sweep", action="store_true",
                     help="time the FP64 oracle's real-space sum over system size on the host cores and exit")
+    ap.add_argument("--kernel-case", action="store_true",
+                    help="run the short fixed evaluation sequence that kernel captures select from, and exit")
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
     return a
@@ -520,24 +522,25 @@ def profile_record(path, source="pair.cu"):
         return None
 
 
-def issue_roofline(prof, ms, f_sm):
-    """Warp instructions per launch (from an ncu summary) over the launch's CUDA-event
-    duration, against 4 warp instructions per SM per clock."""
-    if not prof or "warp instructions" not in prof:
+def issue_roofline(prof, ms, f_sm, prefix=""):
+    """Warp instructions per launch (from an ncu summary; `prefix` picks another launch of
+    the summary) over the launch's CUDA-event duration, against 4 warp instructions per SM
+    per clock."""
+    if not prof or prefix + "warp instructions" not in prof:
         return None
-    wi = float(prof["warp instructions"])
+    wi = float(prof[prefix + "warp instructions"])
     ach = wi / (ms / 1e3)
     pk = N_SM * ISSUE_PER_SM_CLK * f_sm * 1e6
     return {"warp_instructions_per_launch": wi, "achieved_per_s": ach, "peak_per_s": pk, "frac": ach / pk,
             "peak_source": "%d SMs x 4 schedulers x median SM clock %.0f MHz" % (N_SM, f_sm)}
 
 
-def traffic_from_profile(path):
+def traffic_from_profile(path, prefix=""):
     """DRAM bytes per launch of the pair kernel from the committed ncu summary (None when
-    the summary predates the current source)."""
+    the summary predates the current source); `prefix` picks another launch of the summary."""
     rec = profile_record(path)
     try:
-        return float(rec["dram_bytes_per_launch"]) if rec else None
+        return float(rec[prefix + "dram_bytes_per_launch"]) if rec else None
     except (KeyError, ValueError):
         return None
 
@@ -1494,6 +1497,25 @@ def batched_dynamics(torch, nbcore, wl, n_inner=10, reps=5):
     return out
 
 
+def kernel_case(torch, nbcore, wl):
+    """A short fixed sequence of evaluations of the headline water box for kernel captures
+    (ncu -k <kernel> -c <n>), in this order: a forced-rebuild evaluation with energies (one
+    list build; the pair kernel on a just-built list), the same positions with the list
+    kept (every entry tested), then both again without energies (the energy-free pair
+    kernel).  All terms, so the PME kernels run once per evaluation."""
+    s = wl.water_box()
+    xq = torch.from_numpy(nbcore.pack_xq(s.x, s.q)).cuda()
+    f = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+    e = torch.empty((1, 6), dtype=torch.float64, device="cuda")
+    with nbcore.Handle([s]) as h:
+        for energies in (e, None):
+            h.nonbonded_forces(xq, f, energies, force_rebuild=True)
+            h.nonbonded_forces(xq, f, energies)
+        torch.cuda.synchronize()
+        h.check()
+    print(json.dumps({"kernel_case": "water box %d atoms" % s.n, "evaluations": 4}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1501,6 +1523,11 @@ def main():
         return
     if args.cpu_sweep:
         run_cpu_sweep(args)
+        return
+    if args.kernel_case:
+        import torch
+        from paper_2503_20541_b300 import nbcore, workloads as wl
+        kernel_case(torch, nbcore, wl)
         return
     rank, world, local = dist_env()
     import torch
@@ -1657,7 +1684,8 @@ def main():
     achieved = fl / (t_pair / 1e3) / 1e12
     f_sm = clocks.get("sm_mhz") or 1920.0
     peak = N_SM * FP32_LANES * 2 * f_sm * 1e6 / 1e12
-    traffic = traffic_from_profile(os.path.join(ROOT, "profiles", "pair_kernel_water24k.txt"))
+    pair_prof = os.path.join(ROOT, "profiles", "pair_kernel_water24k.txt")
+    traffic = traffic_from_profile(pair_prof)
     mufu_ops = MUFU_COUL_PAIR * pc["cutoff"]
     mufu_peak = N_SM * MUFU_PER_SM_CLK * f_sm * 1e6
     # list build chain (bin, scan, scatter, sort, build): the rebuild-forced step less the
@@ -1668,7 +1696,8 @@ def main():
     hbm_gbs, hbm_src = hbm_peak_gbs()
     # instruction-issue ceiling of the pair kernel: warp instructions per launch from the
     # committed ncu summary (when taken on the current source) over 4 per SM per clock
-    issue = issue_roofline(profile_record(os.path.join(ROOT, "profiles", "pair_kernel_water24k.txt")), t_pair, f_sm)
+    issue = issue_roofline(profile_record(pair_prof), t_pair, f_sm)
+    issue_fresh = issue_roofline(profile_record(pair_prof), t_fresh, f_sm, "fresh ")
     # the Verlet list build kernel alone (inside the rebuild chain), and its issue rate
     t_bk = stages_rs["build"][0] / max(stages_rs["build"][1], 1)
     issue_build = issue_roofline(profile_record(os.path.join(ROOT, "profiles", "build_kernel_water24k.txt"),
@@ -1696,7 +1725,8 @@ def main():
                                               "inside r_c, no test", "flops_per_launch": fl_fresh,
                                     "pair_kernel_us": 1e3 * t_fresh,
                                     "achieved": fl_fresh / (t_fresh / 1e3) / 1e12,
-                                    "frac": fl_fresh / (t_fresh / 1e3) / 1e12 / peak},
+                                    "frac": fl_fresh / (t_fresh / 1e3) / 1e12 / peak,
+                                    "traffic": traffic_from_profile(pair_prof, "fresh "), "issue": issue_fresh},
                      "peak_source": "%d SMs (device property) x 128 FP32 lanes x 2 flop x median SM clock "
                                     "%.0f MHz (measured during the timed region)" % (N_SM, f_sm),
                      "mufu": {"ops_per_launch": mufu_ops, "peak_ops_per_s": mufu_peak,

@@ -391,14 +391,17 @@ __device__ __forceinline__ void build_atoms(const CellCtx& C, int w, int W, int 
             // without a cut-off test while the positions are those of the build
             const bool inn = acc && r2[a] < rc2;
             const unsigned ba = __ballot_sync(0xffffffffu, acc);
+            if (ba == 0u) continue;  // warp-uniform: ~40% of (atom, chunk) pairs accept nothing
             const unsigned bi = __ballot_sync(0xffffffffu, inn);
+            const int ni = __popc(bi), no = __popc(ba) - ni;
+            // a chunk is written when both parts stay apart inside the row; once a row is
+            // full the counts run on past cap and nothing more is written (see below)
+            const bool room = cin[a] + cout[a] + ni + no <= cap;
             const int pi = __popc(bi & lt), po = __popc(ba & lt) - pi;
             const int pos = inn ? cin[a] + pi : cap - 1 - (cout[a] + po);
-            const bool room = inn ? cin[a] + pi < cap : cout[a] + po < cap;
             st32_if(row[a] + pos, ent, acc && room);
-            const int ni = __popc(bi);
             cin[a] += ni;
-            cout[a] += __popc(ba) - ni;
+            cout[a] += no;
         }
     }
     if (lane == 0) {
@@ -408,13 +411,13 @@ __device__ __forceinline__ void build_atoms(const CellCtx& C, int w, int W, int 
                 const int i = C.i0 + w + W * (m0 + a);
                 int ci = cin[a], co = cout[a];
                 if (last && ci + co > cap) {
-                    // the two parts have met: flagged; the counts are clamped so that
-                    // readers stay inside the row
+                    // the row overflowed: flagged, and left empty, so that the kernels that
+                    // read it before the host sees the flag find no unwritten entries
                     atomicOr(&flags[1], NB_DEVERR_LIST_OVERFLOW);
-                    ci = min(ci, cap);
-                    co = min(co, cap - ci);
+                    ci = 0;
+                    co = 0;
                 }
-                nbr_cnt[i] = ci;  // running counts between tiles, clamped after the last
+                nbr_cnt[i] = ci;  // running counts between tiles, cleared after the last on overflow
                 nbr_out[i] = co | (wrap ? kOutWrapBit : 0);
             }
         }

@@ -575,33 +575,76 @@ __device__ __forceinline__ void build_cell_body(const CellCtx& C, const SysDev& 
     }
 }
 
-// Pairs of the list as caller indices (i < j), one warp per atom: an entry's low bits are
-// the partner's slot, mapped to its caller index through the permutation.  Each warp adds
-// its pairs of a round to the output with one counter update (the order of the output is
-// not defined; the set is).
-__global__ void __launch_bounds__(256) k_export_pairs(int N, int cap, const unsigned* __restrict__ nbr,
-                                                      const int* __restrict__ cnt, const int* __restrict__ cnt_out,
-                                                      const int* __restrict__ perm, int2* out, long long max_pairs,
-                                                      unsigned long long* counter) {
-    const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= N) return;
+// Pairs of the list as caller indices (i < j), one warp per atom, eight atoms per block.
+// Every unordered pair is listed in both rows; the row whose slot is the smaller one emits
+// it, which an entry's slot bits decide without the permutation, and only the emitted
+// entries are mapped to caller indices (a random gather each).  The block counts its pairs
+// first, takes its output range with one counter update, and walks the rows again to
+// write them (the list is then in L2); a single counter updated per warp round serialised
+// ~450k atomic adds on one address (water 24k: 160 us; now 18 us counting, 37 us writing).
+// Each walk loads four rounds of a row at once: it is latency-bound.  The order of the
+// output is not defined; the set is.  out == nullptr: count only.
+constexpr int kExportWarps = 8;
+
+__device__ __forceinline__ int export_slot(const unsigned* row, int n, int m, int m_in, int gap) {
+    return n < m ? (int)(row[n < m_in ? n : n + gap] & kEntrySlotMask) : -1;
+}
+
+__global__ void __launch_bounds__(kExportWarps * 32) k_export_pairs(int N, int cap, const unsigned* __restrict__ nbr,
+                                                                    const int* __restrict__ cnt,
+                                                                    const int* __restrict__ cnt_out,
+                                                                    const int* __restrict__ perm, int2* out,
+                                                                    long long max_pairs, unsigned long long* counter) {
+    __shared__ unsigned wcnt[kExportWarps];
+    __shared__ unsigned long long wbase[kExportWarps];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kExportWarps + w;
+    int m_in = 0, m = 0, gap = 0;
+    const unsigned* row = nbr;
+    if (i < N) {  // no early return: the block meets at barriers
+        // entries [0, m_in) and [cap - m_out, cap) of the row, walked as one range
+        m_in = cnt[i];
+        m = m_in + (cnt_out[i] & kOutCountMask);
+        gap = cap - m;
+        row = nbr + (size_t)i * cap;
+    }
+    // four rounds of a row per step, their loads issued together (the walk is latency-bound)
+    unsigned c = 0;
+    for (int n0 = 0; n0 < m; n0 += 128) {
+        int sj[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sj[k] = export_slot(row, n0 + 32 * k + lane, m, m_in, gap);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c += __popc(__ballot_sync(0xffffffffu, sj[k] > i));
+    }
+    if (lane == 0) wcnt[w] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int k = 0; k < kExportWarps; ++k) t += wcnt[k];
+        unsigned long long b = t ? atomicAdd(counter, t) : 0ull;
+        for (int k = 0; k < kExportWarps; ++k) {
+            wbase[k] = b;
+            b += wcnt[k];
+        }
+    }
+    __syncthreads();
+    if (!out || m == 0) return;
     const int oi = perm[i];
-    // entries [0, m_in) and [cap - m_out, cap) of the row, walked as one range
-    const int m_in = cnt[i], m = m_in + (cnt_out[i] & kOutCountMask), gap = cap - m;
-    const unsigned* row = nbr + (size_t)i * cap;
-    for (int n0 = 0; n0 < m; n0 += 32) {
-        const int n = n0 + lane;
-        int oj = -1;
-        if (n < m) oj = perm[row[n < m_in ? n : n + gap] & kEntrySlotMask];
-        const bool take = n < m && oi < oj;
-        const unsigned b = __ballot_sync(0xffffffffu, take);
-        unsigned long long base = 0;
-        if (lane == 0 && b) base = atomicAdd(counter, (unsigned long long)__popc(b));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (take) {
+    unsigned long long base = wbase[w];
+    for (int n0 = 0; n0 < m; n0 += 128) {
+        int sj[4], oj[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sj[k] = export_slot(row, n0 + 32 * k + lane, m, m_in, gap);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) oj[k] = sj[k] > i ? perm[sj[k]] : 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool take = sj[k] > i;
+            const unsigned b = __ballot_sync(0xffffffffu, take);
             const unsigned long long pos = base + __popc(b & ((1u << lane) - 1u));
-            if (out && (long long)pos < max_pairs) out[pos] = make_int2(oi, oj);
+            if (take && (long long)pos < max_pairs) out[pos] = make_int2(min(oi, oj[k]), max(oi, oj[k]));
+            base += __popc(b);
         }
     }
 }
@@ -678,8 +721,8 @@ cudaError_t build_setup(nb_handle* h) {
 void launch_export_pairs(nb_handle* h, int2* out, long long max_pairs, unsigned long long* counter,
                          cudaStream_t st) {
     const int N = h->n_atoms;
-    k_export_pairs<<<cdiv((long long)N * 32, 256), 256, 0, st>>>(N, h->cap, h->nbr, h->nbr_cnt, h->nbr_out, h->perm,
-                                                                  out, max_pairs, counter);
+    k_export_pairs<<<cdiv(N, kExportWarps), kExportWarps * 32, 0, st>>>(N, h->cap, h->nbr, h->nbr_cnt, h->nbr_out,
+                                                                         h->perm, out, max_pairs, counter);
 }
 
 }  // namespace nb

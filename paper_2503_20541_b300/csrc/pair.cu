@@ -352,6 +352,14 @@ __device__ __forceinline__ void pair_atom(int N, int i, const AtomHdr& H, const 
         if ((lane & 7) == 0 && k < 3) red_add(ffix + (size_t)k * N + i, to_fix(sum, scale, flags + 1));
         return;
     }
+    if (COUL == kCoulNone) {  // lane 8k holds the warp sum of value k: fx, fy, fz, elj
+        float v[4] = {fx, fy, fz, elj};
+        const float sum = warp_sum_transposed<4>(v);
+        const int k = lane >> 3;
+        if ((lane & 7) == 0 && k < 3) red_add(ffix + (size_t)k * N + i, to_fix(sum, scale, flags + 1));
+        else if (lane == 24) e_atom[i] = make_float4(0.5f * sum, 0.f, 0.f, 0.f);  // no exclusion pass
+        return;
+    }
     // lane 4k holds the warp sum of value k: fx, fy, fz, elj, edir
     float v[8] = {fx, fy, fz, elj, edir, 0.f, 0.f, 0.f};
     const float sum = warp_sum_transposed<8>(v);

@@ -469,6 +469,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(dalloc(h, &h->nbr, (size_t)N * h->cap));
         NB_TRY(dalloc(h, &h->nbr_cnt, N));
         NB_TRY(dalloc(h, &h->nbr_out, N));
+        NB_TRY(dalloc(h, &h->exp_cnt, N));
         h->excl_w = h->max_excl == 0 ? 0 : (h->max_excl <= 2 ? 2 : 4);
         if (h->excl_w) {
             NB_TRY(dalloc(h, &h->ex_slot, (size_t)N * h->excl_w));

@@ -37,8 +37,11 @@ inline int red_tile(int n) {
 constexpr int kSmallSortAtoms = 8192;          // handles re-slotted by one block (k_sort_small)
 // Words of the handle's device flag array: [0] rebuild request, [1] error bits, [2..3] rebuild
 // count (u64), [NB_FLAG_FRESH] 1 while the slot positions are exactly those of the last list
-// build (set by the build, cleared by every load of new positions).
+// build (set by the build, cleared by every load of new positions), [NB_FLAG_EXPORT] 1 while
+// exp_cnt holds the pair export's per-atom counts of the current list (set by a counting
+// export, cleared by the build).
 constexpr int NB_FLAG_FRESH = 4;
+constexpr int NB_FLAG_EXPORT = 5;
 // Internal bit of the `terms` passed to launch_pair: the per-atom energies are wanted (an
 // evaluation whose energies nobody reduces runs the pair kernel's force-only form).
 constexpr int kTermEnergy = 1 << 16;
@@ -151,6 +154,7 @@ struct nb_handle {
     int tile = 0;                // candidates per shared-memory tile of the cell kernels
     int* nbr_cnt = nullptr;      // [N] entries at the front of the row (inside r_c at the build)
     int* nbr_out = nullptr;      // [N] entries at the back of the row (outside r_c at the build), | kOutWrapBit
+    int* exp_cnt = nullptr;      // [N] pairs each row emits in the pair export (valid per NB_FLAG_EXPORT)
     long long* ffix = nullptr;   // [3N] slot
     float4* e_atom = nullptr;    // [N] slot: half energies (E_lj, E_dir, E_excl, 0) of each atom
     unsigned* flags = nullptr;   // [kFlagWords]: rebuild request, error bits, rebuild count, fresh list

@@ -497,6 +497,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
         *cnt += 1ull;
         flags[0] = 0u;
         flags[NB_FLAG_FRESH] = 1u;  // slot positions are those of this build until the next load
+        flags[NB_FLAG_EXPORT] = 0u;  // the export's stored per-row counts are of the old list
         *ticket = 0u;
     }
 }
@@ -578,12 +579,14 @@ __device__ __forceinline__ void build_cell_body(const CellCtx& C, const SysDev& 
 // Pairs of the list as caller indices (i < j), one warp per atom, eight atoms per block.
 // Every unordered pair is listed in both rows; the row whose slot is the smaller one emits
 // it, which an entry's slot bits decide without the permutation, and only the emitted
-// entries are mapped to caller indices (a random gather each).  The block counts its pairs
-// first, takes its output range with one counter update, and walks the rows again to
-// write them (the list is then in L2); a single counter updated per warp round serialised
-// ~450k atomic adds on one address (water 24k: 160 us; now 18 us counting, 37 us writing).
-// Each walk loads four rounds of a row at once: it is latency-bound.  The order of the
-// output is not defined; the set is.  out == nullptr: count only.
+// entries are mapped to caller indices (a random gather each).  Each block takes its output
+// range with one counter update; a single counter updated per warp round serialised ~450k
+// atomic adds on one address (water 24k: 160 us; now 19 us counting, 29 us writing).  The
+// rows' pair counts come from a counting walk, which also stores them (exp_cnt) for a later
+// writing call on the same list (NB_FLAG_EXPORT, cleared by every build): the usual
+// count-then-write sequence walks each row twice, not three times.  Each walk loads four
+// rounds of a row at once (it is latency-bound).  The order of the output is not defined;
+// the set is.  out == nullptr: count only.
 constexpr int kExportWarps = 8;
 
 __device__ __forceinline__ int export_slot(const unsigned* row, int n, int m, int m_in, int gap) {
@@ -594,11 +597,15 @@ __global__ void __launch_bounds__(kExportWarps * 32) k_export_pairs(int N, int c
                                                                     const int* __restrict__ cnt,
                                                                     const int* __restrict__ cnt_out,
                                                                     const int* __restrict__ perm, int2* out,
-                                                                    long long max_pairs, unsigned long long* counter) {
+                                                                    long long max_pairs, unsigned long long* counter,
+                                                                    int* __restrict__ exp_cnt, unsigned* flags) {
     __shared__ unsigned wcnt[kExportWarps];
     __shared__ unsigned long long wbase[kExportWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kExportWarps + w;
+    // counts stored by an earlier counting call on this list (read before any write below;
+    // only a counting call sets the flag, and only after this launch's reads of it)
+    const bool stored = out != nullptr && flags[NB_FLAG_EXPORT] != 0u;
     int m_in = 0, m = 0, gap = 0;
     const unsigned* row = nbr;
     if (i < N) {  // no early return: the block meets at barriers
@@ -608,14 +615,18 @@ __global__ void __launch_bounds__(kExportWarps * 32) k_export_pairs(int N, int c
         gap = cap - m;
         row = nbr + (size_t)i * cap;
     }
-    // four rounds of a row per step, their loads issued together (the walk is latency-bound)
     unsigned c = 0;
-    for (int n0 = 0; n0 < m; n0 += 128) {
-        int sj[4];
+    if (stored) {
+        c = i < N ? (unsigned)exp_cnt[i] : 0u;
+    } else {
+        for (int n0 = 0; n0 < m; n0 += 128) {
+            int sj[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sj[k] = export_slot(row, n0 + 32 * k + lane, m, m_in, gap);
+            for (int k = 0; k < 4; ++k) sj[k] = export_slot(row, n0 + 32 * k + lane, m, m_in, gap);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) c += __popc(__ballot_sync(0xffffffffu, sj[k] > i));
+            for (int k = 0; k < 4; ++k) c += __popc(__ballot_sync(0xffffffffu, sj[k] > i));
+        }
+        if (lane == 0 && i < N) exp_cnt[i] = (int)c;
     }
     if (lane == 0) wcnt[w] = c;
     __syncthreads();
@@ -648,6 +659,9 @@ __global__ void __launch_bounds__(kExportWarps * 32) k_export_pairs(int N, int c
         }
     }
 }
+
+// Marks the export's per-row counts as those of the current list (after a counting walk).
+__global__ void k_export_counted(unsigned* flags) { flags[NB_FLAG_EXPORT] = 1u; }
 
 void launch_load(nb_handle* h, const float4* xq, cudaStream_t st) {
     int N = h->n_atoms;
@@ -722,7 +736,9 @@ void launch_export_pairs(nb_handle* h, int2* out, long long max_pairs, unsigned 
                          cudaStream_t st) {
     const int N = h->n_atoms;
     k_export_pairs<<<cdiv(N, kExportWarps), kExportWarps * 32, 0, st>>>(N, h->cap, h->nbr, h->nbr_cnt, h->nbr_out,
-                                                                         h->perm, out, max_pairs, counter);
+                                                                         h->perm, out, max_pairs, counter,
+                                                                         h->exp_cnt, h->flags);
+    k_export_counted<<<1, 1, 0, st>>>(h->flags);
 }
 
 }  // namespace nb

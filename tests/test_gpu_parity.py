@@ -77,6 +77,34 @@ def test_neighbor_set_water_with_exclusions_ragged():
     assert len(gpu ^ ref) <= n_band
 
 
+def test_pair_export_counts_again_after_a_rebuild_between_calls():
+    # a counting call stores the rows' pair counts for the writing call that usually
+    # follows; a writing call that rebuilds the list first (other positions) must not use
+    # them: the build clears them and the export counts again
+    import ctypes
+    s1, s2 = _jittered_fcc(9), _jittered_fcc(10)  # same box and atom count, other positions
+    r_nl = s2.r_cut + s2.r_skin
+    x1, x2 = dev_xq(s1), dev_xq(s2)
+    with nbcore.Handle([s1]) as h:
+        n = ctypes.c_int64(0)
+        xp1 = nbcore._ptr(x1, torch.float32, (s1.n, 4), "xq")
+        xp2 = nbcore._ptr(x2, torch.float32, (s2.n, 4), "xq")
+        assert h._lib.nl_build(h._h, xp1, None, 0, ctypes.byref(n), 1, None) == 0
+        cap = 2 * int(n.value)
+        out = torch.zeros((cap, 2), dtype=torch.int32, device="cuda")
+        assert h._lib.nl_build(h._h, xp2, ctypes.c_void_p(out.data_ptr()), cap, ctypes.byref(n), 1, None) == 0
+        torch.cuda.synchronize()
+        n2 = int(n.value)
+        assert n2 <= cap
+        gpu = pair_set(out[:n2].cpu().numpy())
+        # and the usual sequence on the same list: count, then write from the stored counts
+        pairs, n3 = h.nl_build(x2)
+        assert n3 == n2 and pair_set(pairs.cpu().numpy()) == gpu
+    ref, n_band = oracle.neighbor_pairs(s2.x.astype(np.float64), oracle_params(s2), r_nl, band=band(r_nl))
+    assert n_band == 0
+    assert len(gpu) == n2 and gpu == pair_set(ref)
+
+
 def test_neighbor_list_open_system():
     s = _jittered_fcc(5)
     s.periodic = False

@@ -50,7 +50,6 @@ FLOP_LIST_PAIR = 18   # min-image difference, r^2, compare
 FLOP_DIFF_R2 = 9      # difference and r^2 of a pair taken without a test
 FLOP_LJ_PAIR = 25     # mixing, (sigma/r)^6, energy, force
 FLOP_COUL_PAIR = 45   # erfc, Gaussian, energy, force
-FLOP_EXCL_PAIR = 45   # erf correction of an excluded pair
 FLOP_LJ_VJP_PAIR = 2 * FLOP_LJ_PAIR  # VJP pair math: f and f'/r, J (lam_i - lam_j), parameter gradients
 # per-atom bytes of the integrator kernel (velocity Verlet with the next evaluation's load):
 # reads system id 4, fixed-point force 24, slot 4, v 16, x 16, x_ref 16, build position 16;
@@ -60,10 +59,11 @@ ISSUE_PER_SM_CLK = 4   # warp instructions issued per SM per clock (4 schedulers
 LEAD_CYCLES = 1200000  # device idle (~0.6 ms) queued ahead of each eager timed evaluation
 N_SM = 148  # replaced in main() by the device's multi_processor_count
 FP32_LANES = 128
-# our launches per forced-rebuild water evaluation (cuFFT not counted): load, bin, scan,
-# scatter, cellsort, build_cell, pair_cell, excl, spread, grid_convert, convolve, gather,
-# reduce_energy, finalize
-KERNELS_PER_STEP = 14
+# our launches per forced-rebuild water evaluation (cuFFT not counted): load_bin (zeroed
+# forces, binning and, in its last block, the cell scan), scatter, cellsort, build_cell, pair,
+# spread, grid_convert, convolve, gather, epilogue (exclusion correction, force output, energy
+# reduction)
+KERNELS_PER_STEP = 10
 # the timed region lasts at least this long (each timed step replays the evaluation R times),
 # so that the clock sampler (every CLOCK_MS) sees tens of samples at any --steps
 TIMED_REGION_MS = 1500.0
@@ -495,15 +495,13 @@ def run_cpu_dynamics(cores):
 
 
 def flops_per_launch(pc):
-    return (FLOP_LIST_PAIR * pc["list"] + FLOP_LJ_PAIR * pc["cutoff_lj"] + FLOP_COUL_PAIR * pc["cutoff"]
-            + FLOP_EXCL_PAIR * pc["excluded"])
+    return FLOP_LIST_PAIR * pc["list"] + FLOP_LJ_PAIR * pc["cutoff_lj"] + FLOP_COUL_PAIR * pc["cutoff"]
 
 
 def flops_per_launch_fresh(pc):
     """Right after a rebuild the pair kernel takes the pairs inside r_c without a test: their
     difference and r^2 (FLOP_DIFF_R2) and math; the list's other pairs are not touched."""
-    return (FLOP_DIFF_R2 * pc["cutoff"] + FLOP_LJ_PAIR * pc["cutoff_lj"] + FLOP_COUL_PAIR * pc["cutoff"]
-            + FLOP_EXCL_PAIR * pc["excluded"])
+    return FLOP_DIFF_R2 * pc["cutoff"] + FLOP_LJ_PAIR * pc["cutoff_lj"] + FLOP_COUL_PAIR * pc["cutoff"]
 
 
 def profile_record(path, source="pair.cu"):
@@ -1691,7 +1689,7 @@ def main():
     h.check()
 
     # roofline of the fused pair kernel: FP32-pipe ("alu") bound.  The pair stage is the pair
-    # kernel and the exclusion-correction kernel.  On a kept list (the MD steady state) the
+    # kernel alone (the exclusion correction runs in the epilogue).  On a kept list (the MD steady state) the
     # kernel tests every list pair: the algorithmic count of every list pair plus the pair math.
     # Right after a rebuild (the step timed above) it evaluates only the pairs the build found
     # inside r_c, without a test: those pairs' math plus their difference and r^2.
@@ -1735,7 +1733,7 @@ def main():
                              "evaluation",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "wall_s_timed_region": t_wall},
-        "roofline": {"bound": "alu", "kernel": "k_pair + k_excl (fused LJ + Ewald direct; exclusion correction), "
+        "roofline": {"bound": "alu", "kernel": "k_pair (fused LJ + Ewald direct), "
                                               "list kept (every list pair tested)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "flops_per_launch": fl, "pair_kernel_us": 1e3 * t_pair,

@@ -93,13 +93,14 @@ struct Stage {
 // Validity check, conditional rebuild (device-side flag), flag reset.  loaded: the
 // integrator has already done the check (launch_integrate with load_next).
 void prepare(nb_handle* h, const float4* xq, bool force, cudaStream_t st, bool loaded = false) {
+    bool binned = false;
     {
         Stage sc(h, NB_STAGE_CHECK, st);
         if (force) request_rebuild(h, st);
-        if (!loaded) launch_load(h, xq, st);
+        if (!loaded) binned = launch_load(h, xq, st, force);
     }
     Stage sc(h, NB_STAGE_REBUILD, st);
-    launch_reslot(h, xq, st);
+    launch_reslot(h, xq, st, binned);
     Stage sb(h, NB_STAGE_BUILD, st);
     launch_build(h, st);
 }
@@ -136,10 +137,11 @@ nb_status run_pme_mesh(nb_handle* h, const float4* x, cudaStream_t st) {
 nb_status eval(nb_handle* h, const float4* xq, int terms, bool force, cudaStream_t st, bool loaded = false,
                bool energy = true) {
     const bool pme = (terms & NB_TERM_PME) && h->has_pme;
+    bool binned = false;
     {
         Stage sc(h, NB_STAGE_CHECK, st);
         if (force) request_rebuild(h, st);
-        if (!loaded) launch_load(h, xq, st);
+        if (!loaded) binned = launch_load(h, xq, st, force);
     }
     nb_status s = NB_OK;
     if (pme) {
@@ -149,7 +151,7 @@ nb_status eval(nb_handle* h, const float4* xq, int terms, bool force, cudaStream
     }
     {
         Stage sc(h, NB_STAGE_REBUILD, st);
-        launch_reslot(h, xq, st);
+        launch_reslot(h, xq, st, binned);
         Stage sb(h, NB_STAGE_BUILD, st);
         launch_build(h, st);
     }
@@ -480,6 +482,8 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(dalloc(h, &h->flags, kFlagWords));
         NB_TRY(dalloc(h, &h->build_ticket, 1));
         NB_TRY(cudaMemset(h->build_ticket, 0, sizeof(unsigned)));
+        NB_TRY(dalloc(h, &h->bin_ticket, 1));
+        NB_TRY(cudaMemset(h->bin_ticket, 0, sizeof(unsigned)));
         NB_TRY(dalloc(h, &h->energy, (size_t)n_systems * NB_NE));
         NB_TRY(dalloc(h, &h->ke_atom, N));
         NB_TRY(dalloc(h, &h->vwork, N));
@@ -660,11 +664,14 @@ nb_status nonbonded_forces(nb_handle* h, const float* xq, float* f_out, double* 
     DeviceGuard g(h->device);
     cudaStream_t st = S(stream);
     int t = terms & NB_TERM_ALL;
-    nb_status s = eval(h, F4(xq), t, (terms & NB_FORCE_REBUILD) != 0, st, false, energies != nullptr);
+    // with an output to write, the exclusion correction, the force output and the energy
+    // reduction run as one epilogue kernel after the pair kernel and the PME gather
+    const bool epi = f_out || energies;
+    nb_status s = eval(h, F4(xq), t | (epi ? kTermDeferExcl : 0), (terms & NB_FORCE_REBUILD) != 0, st, false,
+                       energies != nullptr);
     if (s != NB_OK) return s;
     Stage sc(h, NB_STAGE_UPDATE, st);
-    if (energies) launch_reduce_energy(h, t, 0, energies, st);
-    if (f_out) launch_finalize_forces(h, f_out, st);
+    if (epi) launch_epilogue(h, t, f_out, energies, st);
     return launched();
 }
 

@@ -45,6 +45,9 @@ constexpr int NB_FLAG_EXPORT = 5;
 // Internal bit of the `terms` passed to launch_pair: the per-atom energies are wanted (an
 // evaluation whose energies nobody reduces runs the pair kernel's force-only form).
 constexpr int kTermEnergy = 1 << 16;
+// Internal bit of the `terms` passed to launch_pair: the exclusion correction is left to the
+// evaluation's epilogue (launch_epilogue), which adds it while it writes the forces.
+constexpr int kTermDeferExcl = 1 << 17;
 constexpr int kFlagWords = 8;
 // A neighbour-list entry: the partner's slot in the low kEntrySlotBits bits and, above them,
 // the pair's periodic image as 2 bits per axis d: bit 2d, atom i moves down by L; bit 2d + 1,
@@ -159,6 +162,7 @@ struct nb_handle {
     float4* e_atom = nullptr;    // [N] slot: half energies (E_lj, E_dir, E_excl, 0) of each atom
     unsigned* flags = nullptr;   // [kFlagWords]: rebuild request, error bits, rebuild count, fresh list
     unsigned* build_ticket = nullptr;  // [1] blocks of the list build done (reset by the last)
+    unsigned* bin_ticket = nullptr;    // [1] blocks of the binning done (reset by the last, which scans)
     double* energy = nullptr;    // [n_sys * NB_NE] scratch
     int n_red_blocks = 0;        // energy reduction: blocks of red_tile atoms, none straddling systems
     int* red_blk_sys = nullptr;  // [n_red_blocks]
@@ -305,8 +309,11 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // ------------------------------------------------------------------ launchers
 // neighbor.cu
-void launch_load(nb_handle* h, const float4* xq, cudaStream_t st);
-void launch_reslot(nb_handle* h, const float4* xq, cudaStream_t st);
+// the evaluation's load; forced: the list is rebuilt in any case, and the kernel then also
+// bins the atoms (and scans the cell counts) when the re-slotting would do that in its own
+// kernels, returning true (pass it to launch_reslot as `binned`)
+bool launch_load(nb_handle* h, const float4* xq, cudaStream_t st, bool forced = false);
+void launch_reslot(nb_handle* h, const float4* xq, cudaStream_t st, bool binned = false);
 void launch_build(nb_handle* h, cudaStream_t st);
 cudaError_t build_setup(nb_handle* h);
 void launch_export_pairs(nb_handle* h, int2* out, long long max_pairs, unsigned long long* counter,
@@ -314,6 +321,9 @@ void launch_export_pairs(nb_handle* h, int2* out, long long max_pairs, unsigned 
 // pair.cu
 void launch_pair(nb_handle* h, int terms, cudaStream_t st);
 void launch_vjp(nb_handle* h, int terms, cudaStream_t st);
+// exclusion correction (when deferred), force output (f_out, may be null) and energy
+// reduction (dst, may be null) of a force evaluation in one launch
+void launch_epilogue(nb_handle* h, int terms, float* f_out, double* dst, cudaStream_t st);
 cudaError_t pair_setup(nb_handle* h);
 // allpairs.cu
 void launch_allpairs_lj(nb_handle* h, const float4* xq, cudaStream_t st);

@@ -6,11 +6,9 @@
 // kick and drifts the positions.  All per-system reductions (energies, kinetic
 // energy, HMC jump, dt gradient) sum in FP64 in a fixed order (energies: per-block
 // partials of 1024 atoms, then one warp per system), so they are deterministic.
-#include "common.cuh"
+#include "reduce.cuh"
 
 namespace nb {
-
-constexpr int kRedThreads = 256;
 
 __device__ __forceinline__ double block_sum(double v, double* sm) {
 #pragma unroll
@@ -24,42 +22,7 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
     return t;  // valid in thread 0
 }
 
-// Energy reduction in one launch.  Each block sums red_tile atoms of one system in FP64
-// and stores its six partials; the last block to finish (a ticket counter behind a fence)
-// adds, per system and in block order, the partials and the PME block energies, one warp
-// per (system, component), and one thread per system writes the results.  Every order is
-// fixed, so the energies are bitwise reproducible; the last block resets the counter, so
-// the kernel replays in a graph.
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Sums of v[0..7] over the warp, transposed: lanes exchange half of their values at each of
-// the first three steps (xor 16, 8, 4), so 9 additions replace 8 separate trees of 5.  Lane
-// l ends with the sum of component (l >> 2) & 7.
-__device__ __forceinline__ double warp_sum8_d(const double v[8]) {
-    const int lane = threadIdx.x & 31;
-    double w[4], u[2];
-    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const double keep = h4 ? v[4 + j] : v[j], give = h4 ? v[j] : v[4 + j];
-        w[j] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const double keep = h3 ? w[2 + j] : w[j], give = h3 ? w[j] : w[2 + j];
-        u[j] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
-    }
-    const double keep = h2 ? u[1] : u[0], give = h2 ? u[0] : u[1];
-    double t = keep + __shfl_xor_sync(0xffffffffu, give, 4);
-    t += __shfl_xor_sync(0xffffffffu, t, 2);
-    t += __shfl_xor_sync(0xffffffffu, t, 1);
-    return t;
-}
-
+// Energy reduction in one launch (reduce.cuh): each thread sums its atoms of the block's tile.
 __global__ void __launch_bounds__(kRedThreads) k_reduce_energy(
     int n_sys, const int* __restrict__ blk_sys, const int* __restrict__ blk_off, const SysDev* __restrict__ sys,
     const float4* __restrict__ e_atom, const float4* __restrict__ xs, const float* __restrict__ ke_atom,
@@ -67,94 +30,22 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_energy(
     const int* __restrict__ pme_blk_off, int terms, unsigned* __restrict__ ticket, double* __restrict__ dst,
     StepStat ss) {
     pdl_wait();
-    constexpr int kW = kRedThreads / 32;
-    constexpr int kC = 6;  // LJ, direct, exclusion, q^2, kinetic, jump
-    __shared__ double sm[kW][kC];
-    __shared__ bool last;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    {
-        const int b = blockIdx.x;
-        const int s = blk_sys[b];
-        const SysDev& S = sys[s];
-        const int a0 = S.atom_off + (b - blk_off[s]) * S.red_tile;
-        const int a1 = min(a0 + S.red_tile, S.atom_off + S.n_atoms);
-        double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        for (int k = a0 + threadIdx.x; k < a1; k += kRedThreads) {
-            const float4 e = e_atom[k];
-            const float q = xs[k].w;
-            v[0] += e.x;
-            v[1] += e.y;
-            v[2] += e.z;
-            v[3] += (double)q * q;
-            if (with_kin) v[4] += ke_atom[k];
-            // a system owns the same index range in both orders: its jump sum reads
-            // caller-order entries over that range
-            if (ss.jump) v[5] += ss.jump[k];
-        }
-        const double t = warp_sum8_d(v);
-        const int c = lane >> 2;
-        if ((lane & 3) == 0 && c < kC) sm[w][c] = t;
-        __syncthreads();
-        if (threadIdx.x < kC) {
-            double acc = 0.0;
-#pragma unroll
-            for (int k = 0; k < kW; ++k) acc += sm[k][threadIdx.x];
-            part[(size_t)b * kC + threadIdx.x] = acc;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-        }
-        __syncthreads();
+    int a0, a1;
+    red_tile_range(blk_sys, blk_off, sys, a0, a1);
+    double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int k = a0 + threadIdx.x; k < a1; k += kRedThreads) {
+        const float4 e = e_atom[k];
+        const float q = xs[k].w;
+        v[0] += e.x;
+        v[1] += e.y;
+        v[2] += e.z;
+        v[3] += (double)q * q;
+        if (with_kin) v[4] += ke_atom[k];
+        // a system owns the same index range in both orders: its jump sum reads
+        // caller-order entries over that range
+        if (ss.jump) v[5] += ss.jump[k];
     }
-    if (!last) return;
-    __threadfence();
-    // per (system, component): component kC is the reciprocal energy from the PME blocks;
-    // the totals go to part[] past the block partials
-    double* tot = part + (size_t)gridDim.x * kC;
-    for (int sc = w; sc < n_sys * (kC + 1); sc += kW) {
-        const int s = sc / (kC + 1), c = sc % (kC + 1);
-        double acc = 0.0;
-        if (c < kC) {
-            for (int b = blk_off[s] + lane; b < blk_off[s + 1]; b += 32) acc += __ldcg(part + (size_t)b * kC + c);
-        } else if ((terms & NB_TERM_PME) && sys[s].pme && pme_blk_off) {
-            for (int b = pme_blk_off[s] + lane; b < pme_blk_off[s + 1]; b += 32) acc += e_pme_blk[b];
-        }
-        acc = warp_sum_d(acc);
-        if (lane == 0) tot[sc] = acc;
-    }
-    __syncthreads();
-    for (int s = threadIdx.x; s < n_sys; s += kRedThreads) {
-        const SysDev& S = sys[s];
-        const double* acc = tot + (size_t)s * (kC + 1);
-        const bool coul = (terms & NB_TERM_COUL) != 0;
-        double e[NB_NE];
-        e[NB_E_LJ] = (terms & NB_TERM_LJ) ? acc[0] : 0.0;
-        e[NB_E_DIR] = coul ? acc[1] : 0.0;
-        e[NB_E_EXCL] = coul ? acc[2] : 0.0;
-        e[NB_E_SELF] = coul ? S.self_coef * acc[3] : 0.0;
-        e[NB_E_REC] = acc[kC];
-        e[NB_E_KIN] = with_kin ? acc[4] : 0.0;
-        double* o = dst + (size_t)s * NB_NE;
-#pragma unroll
-        for (int c = 0; c < NB_NE; ++c) o[c] = e[c];
-        if (ss.sstat) {
-            double H0 = 0.0, H1 = 0.0;
-            for (int c = 0; c < NB_NE; ++c) {
-                H0 += ss.e_ref[(size_t)s * NB_NE + c];
-                H1 += e[c];
-            }
-            const double dH = H1 - H0;
-            double a = (dH <= 0.0) ? 1.0 : exp(-dH / ss.kT);
-            if (!(dH == dH)) a = 0.0;  // NaN energy: never accepted
-            double* q = ss.sstat + (size_t)s * 3;
-            q[0] = dH;
-            q[1] = a;
-            q[2] = acc[5];
-        }
-    }
-    if (threadIdx.x == 0) *ticket = 0u;
+    energy_reduce_finish(v, n_sys, blk_off, sys, with_kin, part, e_pme_blk, pme_blk_off, terms, ticket, dst, ss);
 }
 
 __global__ void k_finalize(int N, const long long* __restrict__ ffix, const int* __restrict__ iperm, float finv,

@@ -64,13 +64,54 @@ __device__ __forceinline__ void bin_atom(int i, const float4* __restrict__ xq, c
     atomicAdd(&cell_count[c], 1);
 }
 
+__device__ __forceinline__ void scan_any_body(int n, const int* count, int* start, int* cursor, int* zero);
+
+// With scan != 0 (a grid of at most kScanTile cells) the last block to finish binning (a
+// ticket counter behind a fence, reset by that block) also performs the exclusive scan of
+// the cell counts (the work of k_scan_single), one launch fewer in the rebuild chain.
+__device__ __forceinline__ void bin_then_scan(int n_cells, int* cell_count, int* start, int* cursor,
+                                              unsigned* ticket) {
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    scan_any_body(n_cells, cell_count, start, cursor, cell_count);
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
 __global__ void k_bin(int N, const float4* __restrict__ xq, const int* __restrict__ sid,
                       const SysDev* __restrict__ sys, int* __restrict__ cellid, int* cell_count,
-                      unsigned* flags) {
+                      int scan, int n_cells, int* start, int* cursor, unsigned* ticket, unsigned* flags) {
     pdl_wait();
     if (flags[0] == 0u) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) bin_atom(i, xq, sid, sys, cellid, cell_count, flags);
+    if (scan) bin_then_scan(n_cells, cell_count, start, cursor, ticket);
+}
+
+// The load of an evaluation whose list is rebuilt in any case (a forced rebuild): the
+// validity test and the slot positions of k_load would be discarded by the re-slotting, so
+// this kernel only zeroes the fixed-point forces, clears the fresh-list flag and bins the
+// atoms (k_bin; with scan != 0 also the scan).  The rebuild request is already set.
+__global__ void k_load_bin(int N, const float4* __restrict__ xq, const int* __restrict__ sid,
+                           const SysDev* __restrict__ sys, int* __restrict__ cellid, int* cell_count,
+                           long long* __restrict__ ffix, int scan, int n_cells, int* start, int* cursor,
+                           unsigned* ticket, unsigned* flags) {
+    pdl_wait();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) flags[NB_FLAG_FRESH] = 0u;
+    if (i < N) {
+        ffix[i] = 0;
+        ffix[(size_t)N + i] = 0;
+        ffix[2 * (size_t)N + i] = 0;
+        bin_atom(i, xq, sid, sys, cellid, cell_count, flags);
+    }
+    if (scan) bin_then_scan(n_cells, cell_count, start, cursor, ticket);
 }
 
 // Block-wide exclusive scan of one int per thread (1024 threads); returns the block total.
@@ -176,6 +217,26 @@ __device__ __forceinline__ void scan_single_body(int n, int* count, int* start, 
             cursor[base + k] = 0;
         }
         pre += v[k];
+    }
+    if (threadIdx.x == 0) start[n] = tot;
+}
+
+// The same scan by one block of any multiple of 32 threads: thread t takes a contiguous run
+// of ceil(n / blockDim) cells.  The counts are read through L2 (they were summed there by
+// other blocks' atomics) and zeroed with the cursors.
+__device__ __forceinline__ void scan_any_body(int n, const int* count, int* start, int* cursor, int* zero) {
+    __shared__ int tot;
+    const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int b = threadIdx.x * per, e = min(n, b + per);
+    int s = 0;
+    for (int k = b; k < e; ++k) s += __ldcg(count + k);
+    int pre = block_exscan(s, &tot);
+    for (int k = b; k < e; ++k) {
+        const int c = __ldcg(count + k);
+        start[k] = pre;
+        zero[k] = 0;
+        cursor[k] = 0;
+        pre += c;
     }
     if (threadIdx.x == 0) start[n] = tot;
 }
@@ -663,9 +724,19 @@ __global__ void __launch_bounds__(kExportWarps * 32) k_export_pairs(int N, int c
 // Marks the export's per-row counts as those of the current list (after a counting walk).
 __global__ void k_export_counted(unsigned* flags) { flags[NB_FLAG_EXPORT] = 1u; }
 
-void launch_load(nb_handle* h, const float4* xq, cudaStream_t st) {
+// The re-slotting of this handle bins in its own kernel (not in the one-block k_sort_small).
+static bool bins_separately(const nb_handle* h) { return !(h->n_scan_blocks == 1 && h->n_atoms <= kSmallSortAtoms); }
+
+bool launch_load(nb_handle* h, const float4* xq, cudaStream_t st, bool forced) {
     int N = h->n_atoms;
+    if (forced && bins_separately(h)) {
+        launch_pdl(k_load_bin, cdiv(N, 256), 256, 0, st, N, xq, h->sid, h->sys, h->cellid, h->cell_count, h->ffix,
+                   h->n_scan_blocks == 1 ? 1 : 0, h->n_cells, h->cell_start, h->cell_cursor, h->bin_ticket,
+                   h->flags);
+        return true;
+    }
     launch_pdl(k_load, cdiv(N, 256), 256, 0, st, N, xq, h->iperm, h->sid, h->sys, h->xref, h->xsb, h->xs, h->ffix, h->flags);
+    return false;
 }
 
 size_t build_smem(const nb_handle* h) { return (size_t)h->tile * (sizeof(float4) + (h->build_gen ? 1 : 0)); }
@@ -682,18 +753,20 @@ void launch_build(nb_handle* h, cudaStream_t st) {
 
 // Re-slotting of a rebuild: binning, scan, scatter and in-cell sort (one block for small
 // handles); the Verlet list build (launch_build) follows.
-void launch_reslot(nb_handle* h, const float4* xq, cudaStream_t st) {
+void launch_reslot(nb_handle* h, const float4* xq, cudaStream_t st, bool binned) {
     int N = h->n_atoms;
-    if (h->n_scan_blocks == 1 && N <= kSmallSortAtoms) {
+    if (!bins_separately(h)) {
         launch_pdl(k_sort_small, 1, 1024, 0, st, N, h->n_cells, xq, h->sid, h->sys, h->cellid, h->cell_count,
                                          h->cell_start, h->cell_cursor, h->perm_tmp, h->params, h->perm, h->iperm,
                                          h->xs, h->xsb, h->ps, h->xref, h->flags);
         return;
     }
-    launch_pdl(k_bin, cdiv(N, 256), 256, 0, st, N, xq, h->sid, h->sys, h->cellid, h->cell_count, h->flags);
-    if (h->n_scan_blocks == 1) {
-        launch_pdl(k_scan_single, 1, 1024, 0, st, h->n_cells, h->cell_count, h->cell_start, h->cell_cursor, h->flags);
-    } else {
+    // a single-block scan runs in the last block of the binning kernel (k_bin or k_load_bin)
+    if (!binned)
+        launch_pdl(k_bin, cdiv(N, 256), 256, 0, st, N, xq, h->sid, h->sys, h->cellid, h->cell_count,
+                   h->n_scan_blocks == 1 ? 1 : 0, h->n_cells, h->cell_start, h->cell_cursor, h->bin_ticket,
+                   h->flags);
+    if (h->n_scan_blocks != 1) {
         launch_pdl(k_scan_a, h->n_scan_blocks, 1024, 0, st, h->n_cells, h->cell_count, h->cell_start, h->scan_bsum,
                                                     h->flags);
         launch_pdl(k_scan_b, 1, 1024, 0, st, h->n_scan_blocks, h->n_cells, h->scan_bsum, h->cell_start, h->flags);

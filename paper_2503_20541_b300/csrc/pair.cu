@@ -30,6 +30,7 @@
 #include "cell.cuh"
 #include "erfc.cuh"
 #include "lj.cuh"
+#include "reduce.cuh"
 
 namespace nb {
 
@@ -582,25 +583,24 @@ __global__ void __launch_bounds__(kVjpThreads, COUL ? 2 : 4) k_vjp(
 // the energy (per unit ke q_i, scaled by ke q_i as hi + lo) goes to e_atom[i].z, which the
 // pair kernel wrote as 0.  VJP: J (lam_i - lam_j) and the charge gradient are added to
 // gx_s[i].  Systems without Ewald electrostatics (ke = 0 or alpha = 0) are skipped.
+// Exclusion correction of slot i (the frame of the last build): force (fx, fy, fz), energy
+// per unit ke q_i (eex), and with VJP the J (lam_i - lam_j) and charge-gradient terms.
+// Returns false (nothing to add) for atoms without exclusions and systems without Ewald
+// electrostatics (ke = 0 or alpha = 0).
 template <bool VJP>
-__global__ void k_excl(int N, const int* __restrict__ sid, const SysDev* __restrict__ sys,
-                       const float4* __restrict__ xs, const float4* __restrict__ lam, ExclView X,
-                       long long* __restrict__ ffix, float4* __restrict__ e_atom, float4* __restrict__ gx_s,
-                       float scale, unsigned* flags) {
-    pdl_wait();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+__device__ __forceinline__ bool excl_terms(int i, const SysDev& S, const float4* __restrict__ xs,
+                                           const float4* __restrict__ lam, const ExclView& X, float& fx, float& fy,
+                                           float& fz, float& eex, float& gx, float& gy, float& gz, float& gq) {
+    fx = fy = fz = eex = gx = gy = gz = gq = 0.f;
     const int ne = X.count(i);
-    if (ne == 0) return;
-    const SysDev& S = sys[sid[i]];  // a system owns the same index range in slot and caller order
+    if (ne == 0) return false;
     const float alpha = S.alpha, ke = S.ke;
-    if (!(alpha > 0.f) || ke == 0.f) return;
+    if (!(alpha > 0.f) || ke == 0.f) return false;
     const float gau_c = 2.f * alpha * kInvSqrtPi, a2 = alpha * alpha;
     const float4 xr = xs[i];
     float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
     if (VJP) li = lam[i];
     const float qke = ke * xr.w;
-    float fx = 0.f, fy = 0.f, fz = 0.f, eex = 0.f, gx = 0.f, gy = 0.f, gz = 0.f, gq = 0.f;
     for (int e = 0; e < ne; ++e) {
         const int j = X.partner(i, e);
         const float4 xj = xs[j];
@@ -636,11 +636,37 @@ __global__ void k_excl(int N, const int* __restrict__ sid, const SysDev* __restr
             gz = fmaf(fr, uz, fmaf(k2, dz, gz));
         }
     }
+    return true;
+}
+
+// The atom's exclusion energy record (e_atom .z): half of ke q_i eex, ke q_i carried as
+// qke + lo exactly so that only one rounding per atom enters.
+__device__ __forceinline__ float excl_energy_half(float ke, float q, float eex) {
+    const float qke = ke * q;
+    const float lo = fmaf(ke, q, -qke);  // ke q_i = qke + lo exactly
+    return 0.5f * fmaf(qke, eex, lo * eex);
+}
+
+// Exclusion correction, one thread per atom (slot order), after the pair kernel: the
+// force is added as fixed point (ffix is an integer sum, so the order against the pair
+// kernel's and the PME gather's adds is irrelevant); the energy (per unit ke q_i, scaled by
+// ke q_i as hi + lo) goes to e_atom[i].z, which the pair kernel wrote as 0.  VJP:
+// J (lam_i - lam_j) and the charge gradient are added to gx_s[i].
+template <bool VJP>
+__global__ void k_excl(int N, const int* __restrict__ sid, const SysDev* __restrict__ sys,
+                       const float4* __restrict__ xs, const float4* __restrict__ lam, ExclView X,
+                       long long* __restrict__ ffix, float4* __restrict__ e_atom, float4* __restrict__ gx_s,
+                       float scale, unsigned* flags) {
+    pdl_wait();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const SysDev& S = sys[sid[i]];  // a system owns the same index range in slot and caller order
+    float fx, fy, fz, eex, gx, gy, gz, gq;
+    if (!excl_terms<VJP>(i, S, xs, lam, X, fx, fy, fz, eex, gx, gy, gz, gq)) return;
     red_add(ffix + i, to_fix(fx, scale, flags + 1));
     red_add(ffix + (size_t)N + i, to_fix(fy, scale, flags + 1));
     red_add(ffix + 2 * (size_t)N + i, to_fix(fz, scale, flags + 1));
-    const float lo = fmaf(ke, xr.w, -qke);  // ke q_i = qke + lo exactly
-    reinterpret_cast<float*>(e_atom + i)[2] = 0.5f * fmaf(qke, eex, lo * eex);
+    reinterpret_cast<float*>(e_atom + i)[2] = excl_energy_half(S.ke, xs[i].w, eex);
     if (VJP) {
         float4 g = gx_s[i];
         g.x += gx;
@@ -649,6 +675,60 @@ __global__ void k_excl(int N, const int* __restrict__ sid, const SysDev* __restr
         g.w += gq;
         gx_s[i] = g;
     }
+}
+
+// The end of a force evaluation (nonbonded_forces) in one launch, over the tiles of the
+// energy reduction (reduce.cuh; blocks of kRedThreads threads, red_tile atoms of one system,
+// slot order): per atom, the exclusion correction of k_excl (do_excl), the force output in
+// caller order (f_out: the fixed-point sum of the pair kernel, the PME gather and the
+// correction, converted as k_finalize does) and, with dst, the energy sums of
+// k_reduce_energy, with the correction's energy record taken from registers.  The same
+// integers are added and the same FP64 sums formed in the same order as by the three
+// separate kernels, so the results are bitwise theirs; two launches fewer on the step's
+// critical path.
+__global__ void __launch_bounds__(kRedThreads) k_epilogue(
+    int N, int n_sys, const int* __restrict__ blk_sys, const int* __restrict__ blk_off,
+    const SysDev* __restrict__ sys, const float4* __restrict__ xs, ExclView X, int do_excl,
+    const long long* __restrict__ ffix, const int* __restrict__ perm, float scale, float finv,
+    float* __restrict__ f_out, const float4* __restrict__ e_atom, double* __restrict__ part,
+    const double* __restrict__ e_pme_blk, const int* __restrict__ pme_blk_off, int terms,
+    unsigned* __restrict__ ticket, double* __restrict__ dst, unsigned* flags) {
+    pdl_wait();
+    int a0, a1;
+    red_tile_range(blk_sys, blk_off, sys, a0, a1);
+    const SysDev& S = sys[blk_sys[blockIdx.x]];
+    double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int k = a0 + threadIdx.x; k < a1; k += kRedThreads) {
+        float fx = 0.f, fy = 0.f, fz = 0.f, ez = 0.f;
+        bool has_excl = false;
+        if (do_excl) {
+            float eex, gx, gy, gz, gq;
+            has_excl = excl_terms<false>(k, S, xs, nullptr, X, fx, fy, fz, eex, gx, gy, gz, gq);
+            if (has_excl) ez = excl_energy_half(S.ke, xs[k].w, eex);
+        }
+        if (f_out) {
+            long long F0 = ffix[k], F1 = ffix[(size_t)N + k], F2 = ffix[2 * (size_t)N + k];
+            if (has_excl) {
+                F0 += to_fix(fx, scale, flags + 1);
+                F1 += to_fix(fy, scale, flags + 1);
+                F2 += to_fix(fz, scale, flags + 1);
+            }
+            const size_t o = 3 * (size_t)perm[k];
+            f_out[o] = __ll2float_rn(F0) * finv;
+            f_out[o + 1] = __ll2float_rn(F1) * finv;
+            f_out[o + 2] = __ll2float_rn(F2) * finv;
+        }
+        if (dst) {
+            const float4 e = e_atom[k];
+            const float q = xs[k].w;
+            v[0] += e.x;
+            v[1] += e.y;
+            v[2] += has_excl ? ez : e.z;
+            v[3] += (double)q * q;
+        }
+    }
+    if (dst)
+        energy_reduce_finish(v, n_sys, blk_off, sys, 0, part, e_pme_blk, pme_blk_off, terms, ticket, dst, StepStat());
 }
 
 static ExclView excl_view(const nb_handle* h) {
@@ -674,7 +754,7 @@ static int pair_atoms_per_block(const nb_handle* h, int warps) {
 }
 
 template <bool LJ, int COUL>
-static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp, bool energy) {
+static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp, bool energy, bool defer_excl) {
     const int N = h->n_atoms;
     if (vjp) {
         const int pb = pair_atoms_per_block(h, kVjpWarps);
@@ -686,7 +766,7 @@ static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp, bool energy) {
                    pb, h->cap, h->sid, h->sys, h->xs, h->ps, h->nbr, h->nbr_cnt, h->nbr_out, h->ffix, h->e_atom,
                    h->fscale, h->flags);
     }
-    if (COUL == kCoulEwald && h->excl_w) {
+    if (COUL == kCoulEwald && h->excl_w && !(defer_excl && !vjp)) {
         const ExclView X = excl_view(h);
         if (vjp)
             launch_pdl(k_excl<true>, cdiv(N, 128), 128, 0, st, N, h->sid, h->sys, h->xs, h->lam, X, h->ffix,
@@ -713,11 +793,27 @@ static void dispatch(nb_handle* h, int terms, cudaStream_t st, bool vjp) {
         return;
     }
     const bool en = vjp || (terms & kTermEnergy) != 0;
-    if (lj && coul && rf) pair_launch<true, kCoulRF>(h, st, vjp, en);
-    else if (lj && coul) pair_launch<true, kCoulEwald>(h, st, vjp, en);
-    else if (lj) pair_launch<true, kCoulNone>(h, st, vjp, en);
-    else if (coul && rf) pair_launch<false, kCoulRF>(h, st, vjp, en);
-    else pair_launch<false, kCoulEwald>(h, st, vjp, en);
+    const bool df = (terms & kTermDeferExcl) != 0;
+    if (lj && coul && rf) pair_launch<true, kCoulRF>(h, st, vjp, en, df);
+    else if (lj && coul) pair_launch<true, kCoulEwald>(h, st, vjp, en, df);
+    else if (lj) pair_launch<true, kCoulNone>(h, st, vjp, en, df);
+    else if (coul && rf) pair_launch<false, kCoulRF>(h, st, vjp, en, df);
+    else pair_launch<false, kCoulEwald>(h, st, vjp, en, df);
+}
+
+// The exclusion correction runs in the epilogue (not after the pair kernel) exactly when
+// the pair kernel would have been followed by k_excl: Ewald electrostatics on a handle with
+// exclusions and the Coulomb term selected.
+bool epilogue_has_excl(const nb_handle* h, int terms) {
+    return (terms & NB_TERM_COUL) && h->any_coul && h->coul_kind != kCoulRF && h->excl_w;
+}
+
+void launch_epilogue(nb_handle* h, int terms, float* f_out, double* dst, cudaStream_t st) {
+    const ExclView X = excl_view(h);
+    launch_pdl(k_epilogue, h->n_red_blocks, kRedThreads, 0, st, h->n_atoms, h->n_sys, h->red_blk_sys,
+               h->red_blk_off, h->sys, h->xs, X, epilogue_has_excl(h, terms) ? 1 : 0, h->ffix, h->perm, h->fscale,
+               h->finv, f_out, h->e_atom, h->red_part, h->e_pme_blk, h->conv_blk_off, terms, h->red_ticket, dst,
+               h->flags);
 }
 
 void launch_pair(nb_handle* h, int terms, cudaStream_t st) { dispatch(h, terms, st, false); }

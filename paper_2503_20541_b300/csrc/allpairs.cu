@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kApTile) k_allpairs_lj(int N, int a0, int n, c
             if (r2 < K.rc2 && j0 + jj != ii) {
                 const float2 pj = tp[jj];
                 const float rinv = rsqrtf(r2);
-                const float r2inv = __frcp_rn(r2);
+                const float r2inv = recip_r2(r2, rinv);
                 const float eps = pi.y * pj.y;
                 const float eps_lo = fmaf(pi.y, pj.y, -eps);
                 float u, f;

@@ -36,6 +36,16 @@ __device__ __forceinline__ PairK pair_k(const SysDev& S) {
     return K;
 }
 
+// 1/r^2 from rinv = rsqrtf(r2).  (1/r)^2 carries the few-ulp error of the hardware
+// reciprocal square root twice, which the 6th and 12th powers of LJ multiply; one
+// Newton-Raphson step for the reciprocal of r2, y + y (1 - r2 y) with the residual formed by
+// an FMA, brings it to about one ulp of 1/r^2 at three instructions (a correctly rounded
+// division costs several times that).
+__device__ __forceinline__ float recip_r2(float r2, float rinv) {
+    const float y = rinv * rinv;
+    return fmaf(y, fmaf(-r2, y, 1.f), y);
+}
+
 // (sigma/r)^2 with sigma^2 carried as an FMA two-product hi + lo: every pair of two given
 // atom types would otherwise share the same rounding of sigma^2, a bias that the
 // 6th/12th powers amplify and that does not average out over the pairs.

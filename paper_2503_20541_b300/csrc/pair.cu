@@ -163,8 +163,8 @@ __device__ __forceinline__ void pair_heavy(const float4& q, int lq, bool on, con
     float fr = 0.f;
     if (LJ && do_lj) {
         const float2 pj = par[lq];
-        // correctly rounded for the energy: LJ raises it to the 6th power
-        const float r2inv = EN ? __frcp_rn(r2) : rinv * rinv;
+        // refined for the energy: LJ raises it to the 6th power
+        const float r2inv = EN ? recip_r2(r2, rinv) : rinv * rinv;
         const float ej = on ? pj.y : 0.f;
         const float eps = pi.y * ej;         // eps_ij = eps + eps_lo exactly
         const float eps_lo = fmaf(pi.y, ej, -eps);
@@ -435,7 +435,7 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, fl
     const float ux = li.x - lj4.x, uy = li.y - lj4.y, uz = li.z - lj4.z;
     const float du = fmaf(dz, uz, fmaf(dy, uy, dx * ux));
     const float rinv = rsqrtf(r2);
-    const float r2inv = __frcp_rn(r2);
+    const float r2inv = recip_r2(r2, rinv);
     float fr = 0.f, fpr = 0.f;  // f and f'/r
     if (LJ) {
         const float eps = pi.y * pj.y;

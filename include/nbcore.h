@@ -115,6 +115,15 @@ typedef struct {
                                 than one only when the cells are too few to fill the GPU).
                                 Results do not depend on it.  The pair and VJP kernels are not
                                 organised by cell: their blocks take consecutive atoms. */
+    double prune_skin;       /* dynamic list pruning between builds: on the first evaluation
+                                after a build, and whenever an atom has moved more than
+                                prune_skin/2 since, every row is re-partitioned at the current
+                                positions into the pairs within r_c + prune_skin and the rest,
+                                and the pair and VJP kernels skip the rest (no pair of it can
+                                be within r_c before the next re-partition).  The list itself,
+                                its build and its rebuild test are unchanged.  > 0: this inner
+                                skin for every system (< r_skin); < 0: off; 0: r_skin/3 for
+                                systems whose r_skin is >= 0.15 r_c, off for the others. */
 } nb_options;
 
 typedef struct nb_handle nb_handle;
@@ -456,7 +465,8 @@ int64_t nb_rebuild_count(nb_handle* h, void* stream);
 #define NB_STAGE_CONVOLVE 5  /* PME influence function and reciprocal energy */
 #define NB_STAGE_GATHER 6    /* PME force gathering */
 #define NB_STAGE_UPDATE 7    /* reductions, force output, integrator updates */
-#define NB_STAGE_BUILD 8     /* the Verlet list build kernel alone (also inside NB_STAGE_REBUILD) */
+#define NB_STAGE_BUILD 8     /* the Verlet list build kernel alone (also inside NB_STAGE_REBUILD); it
+                                also re-partitions the rows of dynamic list pruning when due */
 #define NB_NSTAGES 9
 nb_status nb_timing_enable(nb_handle* h, int32_t enable);
 nb_status nb_timing_read(nb_handle* h, void* stream, double* ms, int64_t* intervals);

@@ -99,10 +99,12 @@ void prepare(nb_handle* h, const float4* xq, bool force, cudaStream_t st, bool l
         if (force) request_rebuild(h, st);
         if (!loaded) binned = launch_load(h, xq, st, force);
     }
-    Stage sc(h, NB_STAGE_REBUILD, st);
-    launch_reslot(h, xq, st, binned);
-    Stage sb(h, NB_STAGE_BUILD, st);
-    launch_build(h, st);
+    {
+        Stage sc(h, NB_STAGE_REBUILD, st);
+        launch_reslot(h, xq, st, binned);
+        Stage sb(h, NB_STAGE_BUILD, st);
+        launch_build(h, st);
+    }
 }
 
 // The mesh half of PME (spread, FFT, convolution, inverse FFT) for positions x.
@@ -270,6 +272,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
     if (o.max_neighbors < 0 || o.force_bits < 0 || o.force_bits > 48 || (o.force_bits > 0 && o.force_bits < 8))
         return NB_ERR_ARG;
     if (o.blocks_per_cell < 0 || o.blocks_per_cell > 32) return NB_ERR_ARG;
+    if (!(o.prune_skin == o.prune_skin)) return NB_ERR_ARG;  // NaN
 
     // exclusions: validate and symmetrise
     std::vector<std::vector<int>> ex((size_t)N);
@@ -371,9 +374,19 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
             delete h;
             return NB_ERR_ARG;
         }
+        D.index = s;
         D.rc2 = (float)(d.r_cut * d.r_cut);
         D.rnl2 = (float)(rnl * rnl);
         D.disp2 = (float)(0.25 * d.r_skin * d.r_skin);
+        {
+            // inner skin of dynamic list pruning (off: 0)
+            double ps = o.prune_skin;
+            if (ps == 0.0) ps = d.r_skin >= 0.15 * d.r_cut ? d.r_skin / 3.0 : -1.0;
+            const bool on = ps > 0.0 && ps < d.r_skin;
+            D.rin2 = on ? (float)((d.r_cut + ps) * (d.r_cut + ps)) : 0.f;
+            D.prune2 = on ? (float)(0.25 * ps * ps) : 0.f;
+            if (on) h->any_prune = 1;
+        }
         D.has_switch = (d.r_switch >= 0.0 && d.r_switch < d.r_cut) ? 1 : 0;
         D.rs = D.has_switch ? (float)d.r_switch : 0.f;
         D.inv_sw = D.has_switch ? (float)(1.0 / (d.r_cut - d.r_switch)) : 0.f;
@@ -484,6 +497,13 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(cudaMemset(h->build_ticket, 0, sizeof(unsigned)));
         NB_TRY(dalloc(h, &h->bin_ticket, 1));
         NB_TRY(cudaMemset(h->bin_ticket, 0, sizeof(unsigned)));
+        if (h->any_prune) {
+            NB_TRY(dalloc(h, &h->x_prune, N));
+            NB_TRY(dalloc(h, &h->prune_sys, n_systems));
+            NB_TRY(cudaMemset(h->prune_sys, 0, sizeof(unsigned) * n_systems));
+            NB_TRY(dalloc(h, &h->prune_cnt, n_systems));
+            NB_TRY(cudaMemset(h->prune_cnt, 0, sizeof(unsigned) * n_systems));
+        }
         NB_TRY(dalloc(h, &h->energy, (size_t)n_systems * NB_NE));
         NB_TRY(dalloc(h, &h->ke_atom, N));
         NB_TRY(dalloc(h, &h->vwork, N));

@@ -222,4 +222,57 @@ __device__ __forceinline__ float gen_diff(float xi, float xj, int fl, int bit, b
     return fold ? mi_pair(xi, xj, L, hL) : ((fl & bit) ? xi - L : xi) - xj;
 }
 
+// Periodic geometry of a system as the list entries need it.
+struct PairGeo {
+    float L[3], hL[3];
+    bool fold[3];  // axis with fewer cells than the stencil spans: per-pair minimum image
+};
+
+__device__ __forceinline__ PairGeo pair_geo(const SysDev& S) {
+    PairGeo G;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        G.L[d] = S.L[d];
+        G.hL[d] = S.halfL[d];
+        G.fold[d] = S.periodic && S.nc[d] <= 2 * S.stencil;
+    }
+    return G;
+}
+
+// Image handling of an atom's row (warp-uniform): plain differences, image codes, or image
+// codes with the minimum image on folded axes (systems with fewer cells than the stencil).
+constexpr int kImgPlain = 0;
+constexpr int kImgCode = 1;
+constexpr int kImgFold = 2;
+
+// x_i - x_j of a list entry: image code bit 2d (x_i moves down by L) and bit 2d + 1 (x_j
+// moves down by L), each shift exact (the moved coordinate lies above L/2), or the minimum
+// image on folded axes.  The list build computed the same difference for its test.
+template <int IMG>
+__device__ __forceinline__ void entry_diff(const float4& xr, const float4& cj, unsigned code, const PairGeo& G,
+                                           float& dx, float& dy, float& dz) {
+    if (IMG == kImgPlain) {
+        dx = xr.x - cj.x;
+        dy = xr.y - cj.y;
+        dz = xr.z - cj.z;
+        return;
+    }
+    const float xi[3] = {xr.x, xr.y, xr.z}, xj[3] = {cj.x, cj.y, cj.z};
+    float d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (IMG == kImgFold && G.fold[k]) {
+            d[k] = mi_pair(xi[k], xj[k], G.L[k], G.hL[k]);
+        } else {
+            const float a = (code >> (2 * k)) & 1u ? xi[k] - G.L[k] : xi[k];
+            const float b = (code >> (2 * k + 1)) & 1u ? xj[k] - G.L[k] : xj[k];
+            d[k] = a - b;
+        }
+    }
+    dx = d[0];
+    dy = d[1];
+    dz = d[2];
+}
+
+
 }  // namespace nb

@@ -42,6 +42,15 @@ constexpr int kSmallSortAtoms = 8192;          // handles re-slotted by one bloc
 // export, cleared by the build).
 constexpr int NB_FLAG_FRESH = 4;
 constexpr int NB_FLAG_EXPORT = 5;
+// Per-system word of dynamic list pruning (nb_handle::prune_sys): kPruned while the system's
+// rows are partitioned at the positions of its last prune (x_prune) into the pairs within
+// r_c + prune skin (front) and the rest (back), set by the prune kernel; kPruneReq set by a
+// load that finds an atom of the system more than half the prune skin from its x_prune
+// position.  The build clears both; the prune kernel sets kPruned and clears kPruneReq of the
+// systems it re-partitions.  Kept per system, so that a system's prune schedule (and with
+// it every summation order) does not depend on the other systems of a batch.
+constexpr unsigned kPruned = 1u;
+constexpr unsigned kPruneReq = 2u;
 // Internal bit of the `terms` passed to launch_pair: the per-atom energies are wanted (an
 // evaluation whose energies nobody reduces runs the pair kernel's force-only form).
 constexpr int kTermEnergy = 1 << 16;
@@ -64,6 +73,8 @@ struct SysDev {
     float L[3], invL[3], halfL[3];
     float cell_scale[3];  // cells per unit length: nc / L
     float rc2, rnl2, disp2;
+    float rin2;           // (r_c + prune skin)^2 of dynamic list pruning (0: the system does not prune)
+    float prune2;         // (prune skin / 2)^2: a larger displacement since the prune requests the next
     float rs, inv_sw;     // switch start and 1/(r_c - r_s)
     float alpha, ke;
     float beta2;          // alpha^2
@@ -78,12 +89,12 @@ struct SysDev {
     long long grid_off;   // real PME mesh offset (elements)
     long long cgrid_off;  // complex half-spectrum offset (elements)
     int red_tile;         // atoms per block of the energy reduction (red_tile(n_atoms))
-    int pad2;
     double self_coef;     // -ke alpha / sqrt(pi)
     float kl_hi[3], kl_lo[3];  // K_d / L_d as an unevaluated sum hi + lo (double-float)
     float krf, crf;       // reaction field (Eq. RFA): k = (eps_s-1)/((2eps_s+1) r_c^3), c = 3eps_s/((2eps_s+1) r_c)
     float krf_lo, crf_lo; // k - krf and c - crf: the constants as double-float pairs for the energy
-    int pad5, pad6;
+    int index;            // the system's index in the handle
+    int pad6;
 };
 
 // An FFT group: PME systems sharing one mesh shape, meshes at a fixed stride.
@@ -163,6 +174,10 @@ struct nb_handle {
     unsigned* flags = nullptr;   // [kFlagWords]: rebuild request, error bits, rebuild count, fresh list
     unsigned* build_ticket = nullptr;  // [1] blocks of the list build done (reset by the last)
     unsigned* bin_ticket = nullptr;    // [1] blocks of the binning done (reset by the last, which scans)
+    float4* x_prune = nullptr;   // [N] slot: positions (frame of the last build) at the last prune
+    unsigned* prune_sys = nullptr;  // [n_sys] kPruned | kPruneReq per system (null: no pruning)
+    unsigned* prune_cnt = nullptr;  // [n_sys] blocks of the system done in a prune (reset by the last)
+    int any_prune = 0;           // some system prunes its list between builds
     double* energy = nullptr;    // [n_sys * NB_NE] scratch
     int n_red_blocks = 0;        // energy reduction: blocks of red_tile atoms, none straddling systems
     int* red_blk_sys = nullptr;  // [n_red_blocks]
@@ -343,7 +358,8 @@ void launch_pme_gather_only(nb_handle* h, const float* phi, float* f_out, cudaSt
 // finite), which requests a rebuild.  Writes the atom's slot position in the frame of the
 // last build (the wrapped position when it requests the rebuild).
 __device__ __forceinline__ bool load_atom(float4 p, const SysDev& S, float4 r, const float4* __restrict__ xsb,
-                                          float4* __restrict__ xs, int k) {
+                                          float4* __restrict__ xs, int k, const float4* __restrict__ xp = nullptr,
+                                          bool* prune = nullptr) {
     float4 w = p;
     float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
     if (S.periodic) {
@@ -362,7 +378,23 @@ __device__ __forceinline__ bool load_atom(float4 p, const SysDev& S, float4 r, c
                  : make_float4(b.x + dx, b.y + dy, b.z + dz, p.w);
     }
     xs[k] = w;
+    if (prune && S.prune2 > 0.f && !need) {
+        // displacement since the last prune, both positions in the frame of the last build
+        const float4 q = xp[k];
+        const float ex = w.x - q.x, ey = w.y - q.y, ez = w.z - q.z;
+        *prune = !(ex * ex + ey * ey + ez * ez <= S.prune2);
+    }
     return need;
+}
+
+// A load's prune request for system s (pr: one of its atoms has moved more than half the
+// prune skin since the last prune), one atomic per system among the warp's requesting lanes
+// (when a prune falls due, most atoms request it at once).  Called by all lanes of `act`.
+__device__ __forceinline__ void request_prune(unsigned act, bool pr, int s, unsigned* prune_sys) {
+    const unsigned want = __ballot_sync(act, pr);
+    if (!want) return;
+    const unsigned grp = __match_any_sync(act, pr ? s : -1);
+    if (pr && (threadIdx.x & 31) == __ffs(grp & want) - 1) atomicOr(&prune_sys[s], kPruneReq);
 }
 
 // The next evaluation's load, done by the integrator right after the drift: the new
@@ -375,6 +407,8 @@ struct LoadNext {
     float4* xs = nullptr;
     long long* ffix = nullptr;
     unsigned* flags = nullptr;
+    const float4* x_prune = nullptr;
+    unsigned* prune_sys = nullptr;
 };
 
 // Blocks per cell for a cell kernel whose blocks hold `warps` warps and want at least

@@ -118,9 +118,12 @@ __global__ void k_integrate(int N, float4* __restrict__ xq, float4* __restrict__
         ln.ffix[k] = 0;
         ln.ffix[(size_t)N + k] = 0;
         ln.ffix[2 * (size_t)N + k] = 0;
-        const bool need = load_atom(x, sys[si], ln.xref[i], ln.xsb, ln.xs, k);
+        bool pr = false;
+        const bool need = load_atom(x, sys[si], ln.xref[i], ln.xsb, ln.xs, k, ln.x_prune, ln.x_prune ? &pr : nullptr);
         const unsigned act = __activemask();  // threads past N returned above
-        if (__any_sync(act, need) && (threadIdx.x & 31) == __ffs(act) - 1) atomicOr(&ln.flags[0], 1u);
+        const bool lead = (threadIdx.x & 31) == __ffs(act) - 1;
+        if (__any_sync(act, need) && lead) atomicOr(&ln.flags[0], 1u);
+        if (ln.x_prune) request_prune(act, pr, si, ln.prune_sys);
     }
 }
 
@@ -391,6 +394,8 @@ void launch_integrate(nb_handle* h, float4* xq, float4* v, const float* w_ovr, c
         ln.xs = h->xs;
         ln.ffix = h->ffix;
         ln.flags = h->flags;
+        ln.x_prune = h->x_prune;
+        ln.prune_sys = h->prune_sys;
     }
     launch_pdl(k_integrate, cdiv(N, 256), 256, 0, st, N, xq, v, w_ovr, dt, h->sid, h->ffix, h->iperm, h->finv, c_pre, c_post,
                                               drift, h->ke_atom, ck_x, ck_v, ck_p, h->sys, ob, ln);

@@ -109,7 +109,7 @@ __device__ __forceinline__ float3 force_of(const long long* __restrict__ ffix, i
 
 // One Langevin middle step of a constraint group of NA atoms (module header).
 template <int NA>
-__device__ __forceinline__ bool langevin_group(const int (&id)[3], float4* __restrict__ xq, float4* __restrict__ v,
+__device__ __forceinline__ unsigned langevin_group(const int (&id)[3], float4* __restrict__ xq, float4* __restrict__ v,
                                                double h, double c1, double c2, const long long* ffix,
                                                const int* __restrict__ iperm, int N, float finv, double kT,
                                                const float* __restrict__ xi, double d_oh, double d_hh,
@@ -118,7 +118,7 @@ __device__ __forceinline__ bool langevin_group(const int (&id)[3], float4* __res
     float4 xo[NA], vo[NA];
     D3 x0[NA], vv[NA], x2[NA], x3[NA];
     double w[NA];
-    bool need = false;
+    unsigned need = 0u;  // bit 0: rebuild requested, bit 1: prune requested
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
         const int i = id[a];
@@ -162,7 +162,9 @@ __device__ __forceinline__ bool langevin_group(const int (&id)[3], float4* __res
             ln.ffix[k] = 0;
             ln.ffix[(size_t)N + k] = 0;
             ln.ffix[2 * (size_t)N + k] = 0;
-            need = load_atom(xn, S, ln.xref[i], ln.xsb, ln.xs, k) || need;
+            bool pr = false;
+            if (load_atom(xn, S, ln.xref[i], ln.xsb, ln.xs, k, ln.x_prune, ln.x_prune ? &pr : nullptr)) need |= 1u;
+            if (pr) need |= 2u;
         }
     }
     return need;
@@ -187,13 +189,14 @@ __global__ void k_langevin(int n_groups, const int4* __restrict__ groups, float4
     const double c1 = exp(-(double)gamma[s] * h);
     const double c2 = sqrt(fmax(0.0, 1.0 - c1 * c1));
     const SysDev& S = sys[s];
-    const bool need = G.w == 3
+    const unsigned need = G.w == 3
                           ? langevin_group<3>(id, xq, v, h, c1, c2, ffix, iperm, N, finv, kT, xi, d_oh, d_hh, ke_atom,
                                               err, S, ln)
                           : langevin_group<1>(id, xq, v, h, c1, c2, ffix, iperm, N, finv, kT, xi, d_oh, d_hh, ke_atom,
                                               err, S, ln);
     const unsigned act = __activemask();  // threads past n_groups returned above
-    if (__any_sync(act, need) && (threadIdx.x & 31) == __ffs(act) - 1) atomicOr(&ln.flags[0], 1u);
+    if (__any_sync(act, (need & 1u) != 0u) && (threadIdx.x & 31) == __ffs(act) - 1) atomicOr(&ln.flags[0], 1u);
+    if (ln.x_prune) request_prune(act, (need & 2u) != 0u, s, ln.prune_sys);
 }
 
 // K = |v|^2 / (2 w) per atom (the last state of a run).
@@ -277,6 +280,8 @@ void launch_langevin(nb_handle* h, float4* xq, float4* v, const float* dt, const
         ln.xs = h->xs;
         ln.ffix = h->ffix;
         ln.flags = h->flags;
+        ln.x_prune = h->x_prune;
+        ln.prune_sys = h->prune_sys;
     }
     launch_pdl(k_langevin, cdiv(h->n_groups, 128), 128, 0, st, h->n_groups, h->groups, xq, v, dt, gamma, h->sid, h->sys,
                                                        h->ffix, h->iperm, h->n_atoms, h->finv, kT, xi, h->d_oh,

@@ -23,18 +23,20 @@ namespace nb {
 __global__ void k_load(int N, const float4* __restrict__ xq, const int* __restrict__ iperm,
                        const int* __restrict__ sid, const SysDev* __restrict__ sys,
                        const float4* __restrict__ xref, const float4* __restrict__ xsb, float4* __restrict__ xs,
-                       long long* __restrict__ ffix, unsigned* flags) {
+                       long long* __restrict__ ffix, const float4* __restrict__ x_prune,
+                       unsigned* __restrict__ prune_sys, unsigned* flags) {
     pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) flags[NB_FLAG_FRESH] = 0u;  // the positions may differ from the build's from here on
-    bool need = false;
+    bool need = false, pr = false;
     if (i < N) {
         ffix[i] = 0;
         ffix[(size_t)N + i] = 0;
         ffix[2 * (size_t)N + i] = 0;
-        need = load_atom(xq[i], sys[sid[i]], xref[i], xsb, xs, iperm[i]);
+        need = load_atom(xq[i], sys[sid[i]], xref[i], xsb, xs, iperm[i], x_prune, x_prune ? &pr : nullptr);
     }
     if (__any_sync(0xffffffffu, need) && (threadIdx.x & 31) == 0) atomicOr(&flags[0], 1u);
+    if (x_prune) request_prune(0xffffffffu, pr, i < N ? sid[i] : 0, prune_sys);
 }
 
 __device__ __forceinline__ int cell_coord(float w, float scale, int nc) {
@@ -529,15 +531,125 @@ __device__ __forceinline__ void build_cell_body(const CellCtx& C, const SysDev& 
                                                 unsigned* __restrict__ nbr, int* __restrict__ nbr_cnt,
                                                 int* __restrict__ nbr_out, unsigned* flags, int part, int split);
 
+// ---------------------------------------------------------------- dynamic list pruning
+//
+// Between builds the rows of the pruning systems (SysDev::rin2 > 0) are re-partitioned at
+// the current positions: the entries within r_in = r_c + delta (delta the prune skin) go to
+// the front of the row, the others to its back (stored in reverse from the end, as the build
+// stores them), each part in the order the entries are met (the old front part, then the old
+// back part as stored), so the result depends only on the list and the positions.  While no
+// atom has moved more than delta/2 since (the loads compare the positions with x_prune), no
+// pair of a back part can come within r_c: its distance was >= r_c + delta and changes by at
+// most delta; the pair and VJP kernels then skip the back parts.  The list's pair set, its
+// build and its rebuild test are untouched.  A system is re-partitioned on an evaluation that
+// keeps the list when it is not pruned yet (the first such evaluation after a build) or a
+// load has requested it.  The work runs in the list-build launch that returns at once when
+// no rebuild is due (one launch per evaluation in any case): each block takes the atoms of
+// its cell, one warp per atom staging the row in the block's shared tile so that the
+// partition can be written over it in place; the block that finishes a system's last cell
+// (a per-system counter) marks the system pruned.
+
+template <int IMG>
+__device__ __forceinline__ void prune_row(const float4& xr, const PairGeo& G, const unsigned* buf, int m, float rin2,
+                                          const float4* __restrict__ xs, unsigned* row, int cap, int& ci, int& co) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    ci = 0;
+    co = 0;
+    // four rounds of 32 entries at a time: their partner gathers are in flight together
+    for (int b0 = 0; b0 < m; b0 += 128) {  // warp-uniform
+        unsigned ent[4];
+        float4 cj[4];
+        bool inn[4], ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = b0 + 32 * u + lane;
+            ok[u] = e < m;
+            ent[u] = ok[u] ? buf[e] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cj[u] = xs[ent[u] & kEntrySlotMask];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float dx, dy, dz;
+            entry_diff<IMG>(xr, cj[u], ent[u] >> kEntrySlotBits, G, dx, dy, dz);
+            inn[u] = ok[u] && pair_r2(dx, dy, dz) < rin2;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const unsigned bi = __ballot_sync(0xffffffffu, inn[u]), bo = __ballot_sync(0xffffffffu, ok[u]) & ~bi;
+            const int pos = inn[u] ? ci + __popc(bi & lt) : cap - 1 - (co + __popc(bo & lt));
+            if (ok[u]) row[pos] = ent[u];
+            ci += __popc(bi);
+            co += __popc(bo);
+        }
+    }
+}
+
+// The prune of cell c's atoms (block `part` of the cell's `split`), when due for its system.
+__device__ __forceinline__ void prune_cell(int c, int part, int split, int cap, const int* __restrict__ cell_sys,
+                                           const SysDev* __restrict__ sys, const int* __restrict__ start,
+                                           const float4* __restrict__ xs, unsigned* __restrict__ nbr,
+                                           int* __restrict__ nbr_cnt, int* __restrict__ nbr_out,
+                                           float4* __restrict__ x_prune, unsigned* __restrict__ prune_sys,
+                                           unsigned* __restrict__ prune_cnt, unsigned* buf_all) {
+    const int s = cell_sys[c];
+    const SysDev& S = sys[s];
+    if (!(S.rin2 > 0.f)) return;
+    const unsigned ps = prune_sys[s];
+    if ((ps & kPruned) && !(ps & kPruneReq)) return;  // block-uniform
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned* buf = buf_all + (size_t)w * cap;
+    const PairGeo G = pair_geo(S);
+    const bool fold = G.fold[0] || G.fold[1] || G.fold[2];
+    const int i0 = start[c], i1 = start[c + 1], W = split * kBuildWarps;
+    for (int k = i0 + part * kBuildWarps + w; k < i1; k += W) {
+        const int nin = nbr_cnt[k], o = nbr_out[k], nout = o & kOutCountMask;
+        unsigned* row = nbr + (size_t)k * cap;
+        for (int e = lane; e < nin; e += 32) buf[e] = row[e];
+        for (int e = lane; e < nout; e += 32) buf[nin + e] = row[cap - nout + e];
+        __syncwarp();
+        const float4 xr = xs[k];
+        int ci, co;
+        if (fold) prune_row<kImgFold>(xr, G, buf, nin + nout, S.rin2, xs, row, cap, ci, co);
+        else if (o & kOutWrapBit) prune_row<kImgCode>(xr, G, buf, nin + nout, S.rin2, xs, row, cap, ci, co);
+        else prune_row<kImgPlain>(xr, G, buf, nin + nout, S.rin2, xs, row, cap, ci, co);
+        if (lane == 0) {
+            nbr_cnt[k] = ci;
+            nbr_out[k] = co | (o & kOutWrapBit);
+            x_prune[k] = xr;
+        }
+        __syncwarp();  // the staging buffer is reused by the warp's next atom
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned blocks = (unsigned)(S.nc[0] * S.nc[1] * S.nc[2] * split);
+        if (atomicAdd(&prune_cnt[s], 1u) + 1u == blocks) {
+            prune_sys[s] = kPruned;
+            prune_cnt[s] = 0u;
+        }
+    }
+}
+
 template <int E, bool SLOW>
 __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
     int cap, int tile, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
     const int* __restrict__ start, const float4* __restrict__ xs, const int* __restrict__ perm,
     const int* __restrict__ iperm, const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
     int* __restrict__ ex_slot, int* __restrict__ ex_cnt, unsigned* __restrict__ nbr,
-    int* __restrict__ nbr_cnt, int* __restrict__ nbr_out, unsigned* ticket, unsigned* flags, int split) {
+    int* __restrict__ nbr_cnt, int* __restrict__ nbr_out, unsigned* ticket, unsigned* flags, int split,
+    unsigned* __restrict__ prune_sys, int n_sys, float4* __restrict__ x_prune, unsigned* __restrict__ prune_cnt) {
     pdl_wait();
-    if (flags[0] == 0u) return;
+    if (flags[0] == 0u) {
+        // the list is kept: re-partition the cell's rows when its system's prune is due
+        if (prune_sys && flags[NB_FLAG_FRESH] == 0u) {
+            extern __shared__ float4 prune_tile[];  // the candidate tile, as kBuildWarps rows of cap entries
+            prune_cell(blockIdx.x / split, blockIdx.x % split, split, cap, cell_sys, sys, start, xs, nbr, nbr_cnt,
+                       nbr_out, x_prune, prune_sys, prune_cnt, reinterpret_cast<unsigned*>(prune_tile));
+        }
+        return;
+    }
     // `split` blocks share a cell, block `part` taking warps part*kBuildWarps.. of its W
     const int c = blockIdx.x / split, part = blockIdx.x % split;
     const SysDev& S = sys[cell_sys[c]];
@@ -559,6 +671,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
         flags[0] = 0u;
         flags[NB_FLAG_FRESH] = 1u;  // slot positions are those of this build until the next load
         flags[NB_FLAG_EXPORT] = 0u;  // the export's stored per-row counts are of the old list
+        if (prune_sys)  // the rows are split at r_c of the build, not pruned
+            for (int s = 0; s < n_sys; ++s) prune_sys[s] = 0u;
         *ticket = 0u;
     }
 }
@@ -735,7 +849,8 @@ bool launch_load(nb_handle* h, const float4* xq, cudaStream_t st, bool forced) {
                    h->flags);
         return true;
     }
-    launch_pdl(k_load, cdiv(N, 256), 256, 0, st, N, xq, h->iperm, h->sid, h->sys, h->xref, h->xsb, h->xs, h->ffix, h->flags);
+    launch_pdl(k_load, cdiv(N, 256), 256, 0, st, N, xq, h->iperm, h->sid, h->sys, h->xref, h->xsb, h->xs, h->ffix,
+               (const float4*)h->x_prune, h->prune_sys, h->flags);
     return false;
 }
 
@@ -748,7 +863,8 @@ void launch_build(nb_handle* h, cudaStream_t st) {
                                     : k_build_cell<4, true>;
     launch_pdl(build, h->n_cells * h->split_build, kBuildThreads, build_smem(h), st,
         h->cap, h->tile, h->cell_sys, h->sys, h->cell_start, h->xs, h->perm, h->iperm, h->ex_off, h->ex_idx,
-        h->ex_slot, h->ex_cnt, h->nbr, h->nbr_cnt, h->nbr_out, h->build_ticket, h->flags, h->split_build);
+        h->ex_slot, h->ex_cnt, h->nbr, h->nbr_cnt, h->nbr_out, h->build_ticket, h->flags, h->split_build,
+        h->prune_sys, h->n_sys, h->x_prune, h->prune_cnt);
 }
 
 // Re-slotting of a rebuild: binning, scan, scatter and in-cell sort (one block for small
@@ -797,6 +913,11 @@ static cudaError_t allow_max_smem(K kernel) {
 
 cudaError_t build_setup(nb_handle* h) {
     if (build_smem(h) + 4096 > 227 * 1024) return cudaErrorInvalidValue;
+    if (h->prune_sys && (size_t)kBuildWarps * h->cap * sizeof(unsigned) > build_smem(h)) {
+        // rows longer than the build's shared tile holds: the lists are not pruned
+        h->prune_sys = nullptr;
+        h->x_prune = nullptr;
+    }
     h->split_build = pick_split(h, kBuildWarps, 3);  // keep >= 3 atoms per warp for register blocking
     cudaError_t e = allow_max_smem(k_build_cell<0, false>);
     if (e == cudaSuccess) e = allow_max_smem(k_build_cell<2, false>);

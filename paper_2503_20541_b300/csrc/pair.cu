@@ -89,58 +89,6 @@ __device__ __forceinline__ AtomHdr load_hdr(int i, const int* __restrict__ sid, 
     return H;
 }
 
-// Periodic geometry of a system as the list entries need it.
-struct PairGeo {
-    float L[3], hL[3];
-    bool fold[3];  // axis with fewer cells than the stencil spans: per-pair minimum image
-};
-
-__device__ __forceinline__ PairGeo pair_geo(const SysDev& S) {
-    PairGeo G;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        G.L[d] = S.L[d];
-        G.hL[d] = S.halfL[d];
-        G.fold[d] = S.periodic && S.nc[d] <= 2 * S.stencil;
-    }
-    return G;
-}
-
-// Image handling of an atom's row (warp-uniform): plain differences, image codes, or image
-// codes with the minimum image on folded axes (systems with fewer cells than the stencil).
-constexpr int kImgPlain = 0;
-constexpr int kImgCode = 1;
-constexpr int kImgFold = 2;
-
-// x_i - x_j of a list entry: image code bit 2d (x_i moves down by L) and bit 2d + 1 (x_j
-// moves down by L), each shift exact (the moved coordinate lies above L/2), or the minimum
-// image on folded axes.  The list build computed the same difference for its test.
-template <int IMG>
-__device__ __forceinline__ void entry_diff(const float4& xr, const float4& cj, unsigned code, const PairGeo& G,
-                                           float& dx, float& dy, float& dz) {
-    if (IMG == kImgPlain) {
-        dx = xr.x - cj.x;
-        dy = xr.y - cj.y;
-        dz = xr.z - cj.z;
-        return;
-    }
-    const float xi[3] = {xr.x, xr.y, xr.z}, xj[3] = {cj.x, cj.y, cj.z};
-    float d[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        if (IMG == kImgFold && G.fold[k]) {
-            d[k] = mi_pair(xi[k], xj[k], G.L[k], G.hL[k]);
-        } else {
-            const float a = (code >> (2 * k)) & 1u ? xi[k] - G.L[k] : xi[k];
-            const float b = (code >> (2 * k + 1)) & 1u ? xj[k] - G.L[k] : xj[k];
-            d[k] = a - b;
-        }
-    }
-    dx = d[0];
-    dy = d[1];
-    dz = d[2];
-}
-
 __device__ __forceinline__ int img_mode(const AtomHdr& H, const PairGeo& G) {
     if (G.fold[0] || G.fold[1] || G.fold[2]) return kImgFold;
     return H.wrap ? kImgCode : kImgPlain;
@@ -284,7 +232,8 @@ __device__ __forceinline__ void walk_back(const float4& xr, const PairGeo& G, co
 // position one round ahead.
 template <int IMG, class Heavy>
 __device__ __forceinline__ void walk_list(const AtomHdr& H, const PairGeo& G, const unsigned* __restrict__ row,
-                                          int cap, bool fresh, float rc2, const float4* __restrict__ xs, float4* qd,
+                                          int cap, bool fresh, bool skip_back, float rc2, const float4* __restrict__ xs,
+                                          float4* qd,
                                           int* qj, Heavy& heavy) {
     const int lane = threadIdx.x & 31;
     const int nin = H.nin;
@@ -306,7 +255,7 @@ __device__ __forceinline__ void walk_list(const AtomHdr& H, const PairGeo& G, co
         const bool on = in && (fresh || pair_r2(dx, dy, dz) < rc2);
         heavy(make_float4(dx, dy, dz, cj.w), in ? (int)(ent & kEntrySlotMask) : 0, on);
     }
-    if (!fresh && H.nout > 0)
+    if (!fresh && !skip_back && H.nout > 0)
         walk_back<IMG>(xr, G, row + (cap - H.nout), H.nout, rc2, xs, qd, qj, heavy);
 }
 
@@ -326,7 +275,7 @@ __device__ __forceinline__ AtomRange block_atoms(int N, int per_block, int warps
 
 // Forces and (EN) half energies of atom i (one warp).
 template <bool LJ, int COUL, bool EN, int IMG>
-__device__ __forceinline__ void pair_atom(int N, int i, const AtomHdr& H, const SysDev& S, bool fresh,
+__device__ __forceinline__ void pair_atom(int N, int i, const AtomHdr& H, const SysDev& S, bool fresh, bool pruned,
                                           const float4* __restrict__ xs, const float2* __restrict__ ps,
                                           const unsigned* __restrict__ nbr, int cap, float4* qd, int* qj,
                                           long long* __restrict__ ffix, float4* __restrict__ e_atom, float scale,
@@ -345,7 +294,7 @@ __device__ __forceinline__ void pair_atom(int N, int i, const AtomHdr& H, const 
     auto heavy = [&](const float4& q, int j, bool on) {
         pair_heavy<LJ, COUL, EN>(q, j, on, pi, do_lj, K, ps, qke, qke_lo, alpha, gau_c, fx, fy, fz, elj, edir);
     };
-    walk_list<IMG>(H, G, nbr + (size_t)i * cap, cap, fresh, K.rc2, xs, qd, qj, heavy);
+    walk_list<IMG>(H, G, nbr + (size_t)i * cap, cap, fresh, pruned && S.rin2 > 0.f, K.rc2, xs, qd, qj, heavy);
     if (!EN) {  // lane 8k holds the warp sum of force component k; no energy record
         float v[4] = {fx, fy, fz, 0.f};
         const float sum = warp_sum_transposed<4>(v);
@@ -391,7 +340,7 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_pair(
     int N, int per_block, int cap, const int* __restrict__ sid, const SysDev* __restrict__ sys,
     const float4* __restrict__ xs, const float2* __restrict__ ps, const unsigned* __restrict__ nbr,
     const int* __restrict__ cnt, const int* __restrict__ cnt_out, long long* __restrict__ ffix,
-    float4* __restrict__ e_atom, float scale, unsigned* flags) {
+    float4* __restrict__ e_atom, float scale, unsigned* flags, const unsigned* __restrict__ prune_sys) {
     pdl_wait();
     __shared__ float4 qd_all[kPairWarps][kQueue];
     __shared__ int qj_all[kPairWarps][kQueue];
@@ -405,7 +354,9 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_pair(
         if (i + R.step < R.i1) hn = load_hdr(i + R.step, sid, xs, ps, nbr, cnt, cnt_out, cap);
         const SysDev& S = sys[H.sys];
         const int mode = img_mode(H, pair_geo(S));
-#define NB_PAIR_ARGS N, i, H, S, fresh, xs, ps, nbr, cap, qd_all[w], qj_all[w], ffix, e_atom, scale, flags
+        // the system's back parts hold no pair within r_c (dynamic list pruning)
+        const bool pruned = prune_sys && (prune_sys[H.sys] & kPruned) != 0u;
+#define NB_PAIR_ARGS N, i, H, S, fresh, pruned, xs, ps, nbr, cap, qd_all[w], qj_all[w], ffix, e_atom, scale, flags
         if (mode == kImgPlain) pair_atom<LJ, COUL, EN, kImgPlain>(NB_PAIR_ARGS);
         else if (mode == kImgCode) pair_atom<LJ, COUL, EN, kImgCode>(NB_PAIR_ARGS);
         else pair_atom<LJ, COUL, EN, kImgFold>(NB_PAIR_ARGS);
@@ -502,7 +453,7 @@ __device__ __forceinline__ void vjp_heavy(const float4& q, const float4& lj4, fl
 }
 
 template <bool LJ, int COUL, int IMG>
-__device__ __forceinline__ void vjp_atom(int N, int i, const AtomHdr& H, const SysDev& S, bool fresh,
+__device__ __forceinline__ void vjp_atom(int N, int i, const AtomHdr& H, const SysDev& S, bool fresh, bool pruned,
                                          const float4* __restrict__ xs, const float2* __restrict__ ps,
                                          const float4* __restrict__ lam, const unsigned* __restrict__ nbr, int cap,
                                          float4* qd, int* qj, float4* __restrict__ gx_s, float2* __restrict__ gp_s,
@@ -520,7 +471,7 @@ __device__ __forceinline__ void vjp_atom(int N, int i, const AtomHdr& H, const S
     auto heavy = [&](const float4& q, int j, bool on) {
         vjp_heavy<LJ, COUL>(q, lam[j], ps[j], on, li, pi, xr.w, K, alpha, a2, gau_c, A);
     };
-    walk_list<IMG>(H, G, nbr + (size_t)i * cap, cap, fresh, K.rc2, xs, qd, qj, heavy);
+    walk_list<IMG>(H, G, nbr + (size_t)i * cap, cap, fresh, pruned && S.rin2 > 0.f, K.rc2, xs, qd, qj, heavy);
     // lane 2k holds the warp sum of value k
     float v[16] = {A.fx, A.fy, A.fz, A.elj, A.edir, A.gx, A.gy, A.gz, A.gq, A.gs, A.ge, 0.f, 0.f, 0.f, 0.f, 0.f};
     float sum = warp_sum_transposed<16>(v);
@@ -550,7 +501,7 @@ __global__ void __launch_bounds__(kVjpThreads, COUL ? 2 : 4) k_vjp(
     const float4* __restrict__ xs, const float2* __restrict__ ps, const float4* __restrict__ lam,
     const unsigned* __restrict__ nbr, const int* __restrict__ cnt, const int* __restrict__ cnt_out,
     float4* __restrict__ gx_s, float2* __restrict__ gp_s, long long* __restrict__ ffix,
-    float4* __restrict__ e_atom, float scale, unsigned* flags) {
+    float4* __restrict__ e_atom, float scale, unsigned* flags, const unsigned* __restrict__ prune_sys) {
     pdl_wait();
     __shared__ float4 qd_all[kVjpWarps][kQueue];
     __shared__ int qj_all[kVjpWarps][kQueue];
@@ -564,7 +515,8 @@ __global__ void __launch_bounds__(kVjpThreads, COUL ? 2 : 4) k_vjp(
         if (i + R.step < R.i1) hn = load_hdr(i + R.step, sid, xs, ps, nbr, cnt, cnt_out, cap);
         const SysDev& S = sys[H.sys];
         const int mode = img_mode(H, pair_geo(S));
-#define NB_VJP_ARGS N, i, H, S, fresh, xs, ps, lam, nbr, cap, qd_all[w], qj_all[w], gx_s, gp_s, ffix, e_atom, scale, \
+        const bool pruned = prune_sys && (prune_sys[H.sys] & kPruned) != 0u;
+#define NB_VJP_ARGS N, i, H, S, fresh, pruned, xs, ps, lam, nbr, cap, qd_all[w], qj_all[w], gx_s, gp_s, ffix, e_atom, scale, \
                     flags
         if (mode == kImgPlain) vjp_atom<LJ, COUL, kImgPlain>(NB_VJP_ARGS);
         else if (mode == kImgCode) vjp_atom<LJ, COUL, kImgCode>(NB_VJP_ARGS);
@@ -759,12 +711,13 @@ static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp, bool energy, bo
     if (vjp) {
         const int pb = pair_atoms_per_block(h, kVjpWarps);
         launch_pdl(k_vjp<LJ, COUL>, cdiv(N, pb), kVjpThreads, 0, st, N, pb, h->cap, h->sid, h->sys, h->xs, h->ps,
-                   h->lam, h->nbr, h->nbr_cnt, h->nbr_out, h->gx_s, h->gp_s, h->ffix, h->e_atom, h->fscale, h->flags);
+                   h->lam, h->nbr, h->nbr_cnt, h->nbr_out, h->gx_s, h->gp_s, h->ffix, h->e_atom, h->fscale, h->flags,
+                   (const unsigned*)h->prune_sys);
     } else {
         const int pb = pair_atoms_per_block(h, kPairWarps);
         launch_pdl(energy ? k_pair<LJ, COUL, true> : k_pair<LJ, COUL, false>, cdiv(N, pb), kPairThreads, 0, st, N,
                    pb, h->cap, h->sid, h->sys, h->xs, h->ps, h->nbr, h->nbr_cnt, h->nbr_out, h->ffix, h->e_atom,
-                   h->fscale, h->flags);
+                   h->fscale, h->flags, (const unsigned*)h->prune_sys);
     }
     if (COUL == kCoulEwald && h->excl_w && !(defer_excl && !vjp)) {
         const ExclView X = excl_view(h);

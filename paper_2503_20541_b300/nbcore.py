@@ -70,6 +70,7 @@ class Options(ctypes.Structure):
         ("cell_div", ctypes.c_int32),
         ("force_bits", ctypes.c_int32),
         ("blocks_per_cell", ctypes.c_int32),
+        ("prune_skin", ctypes.c_double),
     ]
 
 
@@ -250,7 +251,7 @@ class Handle:
     pme_grid, sigma, sqrt_eps, excl_off/excl_idx)."""
 
     def __init__(self, systems, max_neighbors=0, stencil_tile=0, cell_div=0, force_bits=0, periodic=True,
-                 blocks_per_cell=0):
+                 blocks_per_cell=0, prune_skin=0.0):
         lib = load()
         self._h = None
         n_sys = len(systems)
@@ -288,7 +289,8 @@ class Handle:
         self.sqrt_eps = np.ascontiguousarray(np.concatenate(sqe), np.float32)
         ex_off = np.ascontiguousarray(offs, np.int32)
         ex_idx = np.ascontiguousarray(np.concatenate(idxs) if idxs else np.zeros(0), np.int32)
-        opt = Options(int(max_neighbors), int(stencil_tile), int(cell_div), int(force_bits), int(blocks_per_cell))
+        opt = Options(int(max_neighbors), int(stencil_tile), int(cell_div), int(force_bits), int(blocks_per_cell),
+                      float(prune_skin))
         h = _vp()
         st = lib.nb_create(ctypes.byref(h), descs, n_sys, self.sigma.ctypes.data, self.sqrt_eps.ctypes.data,
                            ex_off.ctypes.data, ex_idx.ctypes.data if ex_idx.size else None, ctypes.byref(opt))

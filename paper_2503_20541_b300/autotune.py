@@ -1,13 +1,17 @@
-"""Autotuner for the handle options of a set of systems: cell size and stencil tile.
+"""Autotuner for the handle options of a set of systems: cell size, stencil tile and
+thread blocks per cell of the list build.
 
-The two knobs trade work against occupancy: cells of edge r_nl/2 (cell_div 2) test
-~1.7x fewer stencil candidates than cells of edge r_nl but give more, smaller blocks;
-a smaller shared-memory stencil tile raises the number of resident blocks per SM but
-sends the densest cells through several tiles.  The tuner builds one handle per
-candidate option set, times a few force evaluations of the actual systems with CUDA
-events (list rebuilt every evaluation, so both the build and the pair kernels count),
-and keeps the fastest.  Option sets that the systems cannot take (a box too small for
-the finer cells) are skipped.
+The first two knobs trade work against occupancy: cells of edge r_nl/2 (cell_div 2)
+test ~1.7x fewer stencil candidates than cells of edge r_nl but give more, smaller
+blocks; a smaller shared-memory stencil tile raises the number of resident blocks per SM
+but sends the densest cells through several tiles.  The third splits a cell's atoms over
+several blocks of the list build (results do not depend on it): more blocks fill the
+GPU when cells are few, fewer keep the candidate staging of a cell in one block.  The
+tuner builds one handle per candidate option set, times a few force evaluations of the
+actual systems with CUDA events (list rebuilt every evaluation, so both the build and the
+pair kernels count) and keeps the fastest: first over cell size and tile, then over the
+blocks per cell of the winner.  Option sets that the systems cannot take (a box too small
+for the finer cells) are skipped.
 """
 import math
 
@@ -38,6 +42,16 @@ def candidate_options(systems):
     return out
 
 
+def refine_options(best, splits=(1, 2, 4)):
+    """Second stage: the winning option set with each explicit number of list-build blocks
+    per cell (the winner itself was timed with the automatic choice)."""
+    out = []
+    for b in splits:
+        if best.get("blocks_per_cell", 0) != b:
+            out.append(dict(best, blocks_per_cell=b))
+    return out
+
+
 def expected_stencil(systems, cell_div):
     """Largest expected stencil candidate count over the systems (density x volume of
     the (2 cell_div + 1)^3 cells around a cell, fewer when an axis has fewer cells)."""
@@ -65,8 +79,9 @@ def choose(timings):
     return best
 
 
-def autotune(systems, xq, candidates=None, evals=5, warmup=2, make_handle=None, timer=None):
-    """Time each candidate on ``systems`` (positions ``xq``, a device tensor) and return
+def autotune(systems, xq, candidates=None, evals=5, warmup=2, make_handle=None, timer=None, refine=True):
+    """Time each candidate on ``systems`` (positions ``xq``, a device tensor), then (with
+    ``refine``) the blocks-per-cell variants of the fastest, and return
     (best options, [(options, ms or None), ...]).
 
     ``make_handle(systems, **opts)`` and ``timer(handle, xq, evals, warmup)`` default to
@@ -83,16 +98,22 @@ def autotune(systems, xq, candidates=None, evals=5, warmup=2, make_handle=None, 
     if timer is None:
         timer = _event_timer
     results = []
-    for opts in candidates:
-        try:
-            h = make_handle(systems, **opts)
-        except Exception:  # e.g. a box too small for the finer cells
-            results.append((opts, None))
-            continue
-        try:
-            results.append((opts, timer(h, xq, evals, warmup)))
-        finally:
-            h.close()
+
+    def run(option_sets):
+        for opts in option_sets:
+            try:
+                h = make_handle(systems, **opts)
+            except Exception:  # e.g. a box too small for the finer cells
+                results.append((opts, None))
+                continue
+            try:
+                results.append((opts, timer(h, xq, evals, warmup)))
+            finally:
+                h.close()
+
+    run(candidates)
+    if refine:
+        run(refine_options(choose(results)))
     return choose(results), results
 
 

@@ -60,10 +60,34 @@ def test_autotune_picks_fastest_and_skips_failures():
     def timer(h, xq, evals, warmup):
         return times[(h.opts["cell_div"], h.opts.get("stencil_tile", 0))]
 
-    best, table = autotune.autotune(systems, None, candidates=cands, make_handle=make, timer=timer)
+    best, table = autotune.autotune(systems, None, candidates=cands, make_handle=make, timer=timer, refine=False)
     assert best == dict(cell_div=2)
     assert [ms for _, ms in table] == [3.0, 2.0, None]
     assert len(closed) == len(made) == 2
+
+
+def test_autotune_refines_blocks_per_cell_of_the_winner():
+    systems = [wl.lj_random(500, seed=3)]
+    cands = [dict(cell_div=1), dict(cell_div=2)]
+    times = {(1, 0): 3.0, (2, 0): 2.0, (2, 1): 2.5, (2, 2): 1.5, (2, 4): 1.8}
+
+    class FakeHandle:
+        def __init__(self, opts):
+            self.opts = opts
+
+        def close(self):
+            pass
+
+    def timer(h, xq, evals, warmup):
+        return times[(h.opts["cell_div"], h.opts.get("blocks_per_cell", 0))]
+
+    best, table = autotune.autotune(systems, None, candidates=cands, make_handle=lambda s, **o: FakeHandle(o),
+                                    timer=timer)
+    # the second stage times blocks per cell 1, 2, 4 of the first stage's winner only
+    assert [o for o, _ in table[2:]] == [dict(cell_div=2, blocks_per_cell=b) for b in (1, 2, 4)]
+    assert best == dict(cell_div=2, blocks_per_cell=2)
+    assert autotune.refine_options(dict(cell_div=1, blocks_per_cell=2)) == [
+        dict(cell_div=1, blocks_per_cell=1), dict(cell_div=1, blocks_per_cell=4)]
 
 
 def test_choose_raises_when_nothing_ran():

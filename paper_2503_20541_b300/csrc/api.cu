@@ -105,6 +105,7 @@ void prepare(nb_handle* h, const float4* xq, bool force, cudaStream_t st, bool l
         Stage sb(h, NB_STAGE_BUILD, st);
         launch_build(h, st);
     }
+    launch_prune(h, st);
 }
 
 // The mesh half of PME (spread, FFT, convolution, inverse FFT) for positions x.
@@ -155,8 +156,9 @@ nb_status eval(nb_handle* h, const float4* xq, int terms, bool force, cudaStream
         Stage sc(h, NB_STAGE_REBUILD, st);
         launch_reslot(h, xq, st, binned);
         Stage sb(h, NB_STAGE_BUILD, st);
-        launch_build(h, st);
+        launch_build(h, st, pme);  // with PME running alongside, the prune rides in the build launch
     }
+    launch_prune(h, st, pme);
     if (pme) {
         cudaEventRecord(h->ev_built, st);
         cudaStreamWaitEvent(h->aux, h->ev_built, 0);
@@ -501,6 +503,8 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
             NB_TRY(dalloc(h, &h->x_prune, N));
             NB_TRY(dalloc(h, &h->prune_sys, n_systems));
             NB_TRY(cudaMemset(h->prune_sys, 0, sizeof(unsigned) * n_systems));
+            NB_TRY(dalloc(h, &h->prune_ticket, 1));
+            NB_TRY(cudaMemset(h->prune_ticket, 0, sizeof(unsigned)));
             NB_TRY(dalloc(h, &h->prune_cnt, n_systems));
             NB_TRY(cudaMemset(h->prune_cnt, 0, sizeof(unsigned) * n_systems));
         }

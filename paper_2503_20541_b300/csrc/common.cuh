@@ -51,6 +51,10 @@ constexpr int NB_FLAG_EXPORT = 5;
 // it every summation order) does not depend on the other systems of a batch.
 constexpr unsigned kPruned = 1u;
 constexpr unsigned kPruneReq = 2u;
+// [NB_FLAG_PRUNE_ANY] some system may need a prune: set by the build (the next evaluation
+// that keeps the list prunes every pruning system) and by the loads with a request; cleared
+// by the prune kernel, which returns at once while it is clear.
+constexpr int NB_FLAG_PRUNE_ANY = 6;
 // Internal bit of the `terms` passed to launch_pair: the per-atom energies are wanted (an
 // evaluation whose energies nobody reduces runs the pair kernel's force-only form).
 constexpr int kTermEnergy = 1 << 16;
@@ -176,7 +180,9 @@ struct nb_handle {
     unsigned* bin_ticket = nullptr;    // [1] blocks of the binning done (reset by the last, which scans)
     float4* x_prune = nullptr;   // [N] slot: positions (frame of the last build) at the last prune
     unsigned* prune_sys = nullptr;  // [n_sys] kPruned | kPruneReq per system (null: no pruning)
-    unsigned* prune_cnt = nullptr;  // [n_sys] blocks of the system done in a prune (reset by the last)
+    unsigned* prune_ticket = nullptr;  // [1] blocks of the prune kernel done (reset by the last)
+    unsigned* prune_cnt = nullptr;  // [n_sys] blocks of the system done in a prune folded into the build
+    int fold_prune_ok = 0;       // the build launch's shared tile can stage a row per warp
     int any_prune = 0;           // some system prunes its list between builds
     double* energy = nullptr;    // [n_sys * NB_NE] scratch
     int n_red_blocks = 0;        // energy reduction: blocks of red_tile atoms, none straddling systems
@@ -329,7 +335,10 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 // kernels, returning true (pass it to launch_reslot as `binned`)
 bool launch_load(nb_handle* h, const float4* xq, cudaStream_t st, bool forced = false);
 void launch_reslot(nb_handle* h, const float4* xq, cudaStream_t st, bool binned = false);
-void launch_build(nb_handle* h, cudaStream_t st);
+// fold_prune: the build launch also does the dynamic list pruning when due (launch_prune
+// then launches nothing)
+void launch_build(nb_handle* h, cudaStream_t st, bool fold_prune = false);
+void launch_prune(nb_handle* h, cudaStream_t st, bool folded = false);  // returns at once unless due
 cudaError_t build_setup(nb_handle* h);
 void launch_export_pairs(nb_handle* h, int2* out, long long max_pairs, unsigned long long* counter,
                          cudaStream_t st);
@@ -390,11 +399,14 @@ __device__ __forceinline__ bool load_atom(float4 p, const SysDev& S, float4 r, c
 // A load's prune request for system s (pr: one of its atoms has moved more than half the
 // prune skin since the last prune), one atomic per system among the warp's requesting lanes
 // (when a prune falls due, most atoms request it at once).  Called by all lanes of `act`.
-__device__ __forceinline__ void request_prune(unsigned act, bool pr, int s, unsigned* prune_sys) {
+__device__ __forceinline__ void request_prune(unsigned act, bool pr, int s, unsigned* prune_sys, unsigned* flags) {
     const unsigned want = __ballot_sync(act, pr);
     if (!want) return;
     const unsigned grp = __match_any_sync(act, pr ? s : -1);
-    if (pr && (threadIdx.x & 31) == __ffs(grp & want) - 1) atomicOr(&prune_sys[s], kPruneReq);
+    if (pr && (threadIdx.x & 31) == __ffs(grp & want) - 1) {
+        atomicOr(&prune_sys[s], kPruneReq);
+        atomicOr(&flags[NB_FLAG_PRUNE_ANY], 1u);
+    }
 }
 
 // The next evaluation's load, done by the integrator right after the drift: the new

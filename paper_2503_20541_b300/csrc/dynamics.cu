@@ -123,7 +123,7 @@ __global__ void k_integrate(int N, float4* __restrict__ xq, float4* __restrict__
         const unsigned act = __activemask();  // threads past N returned above
         const bool lead = (threadIdx.x & 31) == __ffs(act) - 1;
         if (__any_sync(act, need) && lead) atomicOr(&ln.flags[0], 1u);
-        if (ln.x_prune) request_prune(act, pr, si, ln.prune_sys);
+        if (ln.x_prune) request_prune(act, pr, si, ln.prune_sys, ln.flags);
     }
 }
 

@@ -196,7 +196,7 @@ __global__ void k_langevin(int n_groups, const int4* __restrict__ groups, float4
                                               err, S, ln);
     const unsigned act = __activemask();  // threads past n_groups returned above
     if (__any_sync(act, (need & 1u) != 0u) && (threadIdx.x & 31) == __ffs(act) - 1) atomicOr(&ln.flags[0], 1u);
-    if (ln.x_prune) request_prune(act, (need & 2u) != 0u, s, ln.prune_sys);
+    if (ln.x_prune) request_prune(act, (need & 2u) != 0u, s, ln.prune_sys, ln.flags);
 }
 
 // K = |v|^2 / (2 w) per atom (the last state of a run).

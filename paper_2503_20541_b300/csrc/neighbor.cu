@@ -36,7 +36,7 @@ __global__ void k_load(int N, const float4* __restrict__ xq, const int* __restri
         need = load_atom(xq[i], sys[sid[i]], xref[i], xsb, xs, iperm[i], x_prune, x_prune ? &pr : nullptr);
     }
     if (__any_sync(0xffffffffu, need) && (threadIdx.x & 31) == 0) atomicOr(&flags[0], 1u);
-    if (x_prune) request_prune(0xffffffffu, pr, i < N ? sid[i] : 0, prune_sys);
+    if (x_prune) request_prune(0xffffffffu, pr, i < N ? sid[i] : 0, prune_sys, flags);
 }
 
 __device__ __forceinline__ int cell_coord(float w, float scale, int nc) {
@@ -632,6 +632,73 @@ __device__ __forceinline__ void prune_cell(int c, int part, int split, int cap, 
     }
 }
 
+// Two ways to run the prune, chosen per evaluation.  A force evaluation with PME folds it
+// into the build launch (prune_cell, above): one kernel fewer between the build and the pair
+// kernel matters there, because the PME kernels on the second stream take the SMs the pair
+// kernel would start on (an idle kernel at that place cost the water 24k step 20 us with
+// PME, 2 us without).  Elsewhere (dynamics, the VJP) the prune kernel below runs after the
+// build launch: at 8 warps per block and a small staging buffer it keeps more warps and more
+// L1 per SM than the build's blocks (128 threads, 40 KB tile) and prunes ~2x faster.
+// The prune kernel: a few blocks per SM, one warp per atom (grid-stride over the atoms),
+// each warp staging its row in its own part of the block's shared buffer.  It returns at
+// once unless some system may need a prune (NB_FLAG_PRUNE_ANY) and the list is not fresh;
+// the last block to finish (a ticket behind a fence) marks the systems it re-partitioned
+// (the same test as the warps', on the same unchanged words) and clears the flag.
+constexpr int kPruneWarps = 8;
+
+__device__ __forceinline__ bool prune_due(const SysDev& S, unsigned ps) {
+    return S.rin2 > 0.f && (!(ps & kPruned) || (ps & kPruneReq));
+}
+
+__global__ void __launch_bounds__(kPruneWarps * 32) k_prune(int N, int cap, const int* __restrict__ sid,
+                                                             const SysDev* __restrict__ sys, int n_sys,
+                                                             const float4* __restrict__ xs, unsigned* __restrict__ nbr,
+                                                             int* __restrict__ nbr_cnt, int* __restrict__ nbr_out,
+                                                             float4* __restrict__ x_prune,
+                                                             unsigned* __restrict__ prune_sys, unsigned* ticket,
+                                                             unsigned* flags) {
+    pdl_wait();
+    if (flags[NB_FLAG_FRESH] != 0u || flags[NB_FLAG_PRUNE_ANY] == 0u) return;  // grid-uniform
+    extern __shared__ unsigned prune_buf[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned* buf = prune_buf + (size_t)w * cap;
+    for (int k = blockIdx.x * kPruneWarps + w; k < N; k += gridDim.x * kPruneWarps) {
+        const int s = sid[k];  // a system owns the same index range in slot and caller order
+        const SysDev& S = sys[s];
+        if (!prune_due(S, prune_sys[s])) continue;  // warp-uniform
+        const int nin = nbr_cnt[k], o = nbr_out[k], nout = o & kOutCountMask;
+        unsigned* row = nbr + (size_t)k * cap;
+        for (int e = lane; e < nin; e += 32) buf[e] = row[e];
+        for (int e = lane; e < nout; e += 32) buf[nin + e] = row[cap - nout + e];
+        __syncwarp();
+        const float4 xr = xs[k];
+        const PairGeo G = pair_geo(S);
+        int ci, co;
+        if (G.fold[0] || G.fold[1] || G.fold[2]) prune_row<kImgFold>(xr, G, buf, nin + nout, S.rin2, xs, row, cap, ci, co);
+        else if (o & kOutWrapBit) prune_row<kImgCode>(xr, G, buf, nin + nout, S.rin2, xs, row, cap, ci, co);
+        else prune_row<kImgPlain>(xr, G, buf, nin + nout, S.rin2, xs, row, cap, ci, co);
+        if (lane == 0) {
+            nbr_cnt[k] = ci;
+            nbr_out[k] = co | (o & kOutWrapBit);
+            x_prune[k] = xr;
+        }
+        __syncwarp();  // the staging buffer is reused by the warp's next atom
+    }
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        for (int s = 0; s < n_sys; ++s)
+            if (prune_due(sys[s], prune_sys[s])) prune_sys[s] = kPruned;
+        flags[NB_FLAG_PRUNE_ANY] = 0u;
+        *ticket = 0u;
+    }
+}
+
 template <int E, bool SLOW>
 __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
     int cap, int tile, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
@@ -639,11 +706,13 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
     const int* __restrict__ iperm, const int* __restrict__ ex_off, const int* __restrict__ ex_idx,
     int* __restrict__ ex_slot, int* __restrict__ ex_cnt, unsigned* __restrict__ nbr,
     int* __restrict__ nbr_cnt, int* __restrict__ nbr_out, unsigned* ticket, unsigned* flags, int split,
-    unsigned* __restrict__ prune_sys, int n_sys, float4* __restrict__ x_prune, unsigned* __restrict__ prune_cnt) {
+    unsigned* __restrict__ prune_sys, int n_sys, float4* __restrict__ x_prune, unsigned* __restrict__ prune_cnt,
+    int fold_prune) {
     pdl_wait();
     if (flags[0] == 0u) {
-        // the list is kept: re-partition the cell's rows when its system's prune is due
-        if (prune_sys && flags[NB_FLAG_FRESH] == 0u) {
+        // the list is kept: with fold_prune, re-partition the cell's rows here when its
+        // system's prune is due (else k_prune, launched next, does it)
+        if (fold_prune && prune_sys && flags[NB_FLAG_FRESH] == 0u) {
             extern __shared__ float4 prune_tile[];  // the candidate tile, as kBuildWarps rows of cap entries
             prune_cell(blockIdx.x / split, blockIdx.x % split, split, cap, cell_sys, sys, start, xs, nbr, nbr_cnt,
                        nbr_out, x_prune, prune_sys, prune_cnt, reinterpret_cast<unsigned*>(prune_tile));
@@ -671,8 +740,10 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_cell(
         flags[0] = 0u;
         flags[NB_FLAG_FRESH] = 1u;  // slot positions are those of this build until the next load
         flags[NB_FLAG_EXPORT] = 0u;  // the export's stored per-row counts are of the old list
-        if (prune_sys)  // the rows are split at r_c of the build, not pruned
-            for (int s = 0; s < n_sys; ++s) prune_sys[s] = 0u;
+        if (prune_sys) {  // the rows are split at r_c of the build, not pruned: the next
+            for (int s = 0; s < n_sys; ++s) prune_sys[s] = 0u;  // evaluation that keeps them prunes
+            flags[NB_FLAG_PRUNE_ANY] = 1u;
+        }
         *ticket = 0u;
     }
 }
@@ -856,7 +927,7 @@ bool launch_load(nb_handle* h, const float4* xq, cudaStream_t st, bool forced) {
 
 size_t build_smem(const nb_handle* h) { return (size_t)h->tile * (sizeof(float4) + (h->build_gen ? 1 : 0)); }
 
-void launch_build(nb_handle* h, cudaStream_t st) {
+void launch_build(nb_handle* h, cudaStream_t st, bool fold_prune) {
     auto build = h->excl_w == 0   ? k_build_cell<0, false>
                  : h->excl_w == 2 ? k_build_cell<2, false>
                  : h->max_excl <= 4 ? k_build_cell<4, false>
@@ -864,7 +935,20 @@ void launch_build(nb_handle* h, cudaStream_t st) {
     launch_pdl(build, h->n_cells * h->split_build, kBuildThreads, build_smem(h), st,
         h->cap, h->tile, h->cell_sys, h->sys, h->cell_start, h->xs, h->perm, h->iperm, h->ex_off, h->ex_idx,
         h->ex_slot, h->ex_cnt, h->nbr, h->nbr_cnt, h->nbr_out, h->build_ticket, h->flags, h->split_build,
-        h->prune_sys, h->n_sys, h->x_prune, h->prune_cnt);
+        h->prune_sys, h->n_sys, h->x_prune, h->prune_cnt, fold_prune && h->fold_prune_ok ? 1 : 0);
+}
+
+// Dynamic list pruning (k_prune), after the build of every evaluation that uses the list
+// (folded: the build launch has done it).
+void launch_prune(nb_handle* h, cudaStream_t st, bool folded) {
+    if (!h->prune_sys || (folded && h->fold_prune_ok)) return;
+    const int N = h->n_atoms;
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::min(cdiv(N, kPruneWarps), 4 * sms);
+    launch_pdl(k_prune, grid, kPruneWarps * 32, (size_t)kPruneWarps * h->cap * sizeof(unsigned), st, N, h->cap,
+               h->sid, h->sys, h->n_sys, h->xs, h->nbr, h->nbr_cnt, h->nbr_out, h->x_prune, h->prune_sys,
+               h->prune_ticket, h->flags);
 }
 
 // Re-slotting of a rebuild: binning, scan, scatter and in-cell sort (one block for small
@@ -913,10 +997,21 @@ static cudaError_t allow_max_smem(K kernel) {
 
 cudaError_t build_setup(nb_handle* h) {
     if (build_smem(h) + 4096 > 227 * 1024) return cudaErrorInvalidValue;
-    if (h->prune_sys && (size_t)kBuildWarps * h->cap * sizeof(unsigned) > build_smem(h)) {
-        // rows longer than the build's shared tile holds: the lists are not pruned
-        h->prune_sys = nullptr;
-        h->x_prune = nullptr;
+    if (h->prune_sys) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const size_t need = (size_t)kPruneWarps * h->cap * sizeof(unsigned);
+        // the build launch can prune when its shared tile holds a row per warp
+        h->fold_prune_ok = (size_t)kBuildWarps * h->cap * sizeof(unsigned) <= build_smem(h) ? 1 : 0;
+        if (need + 1024 > (size_t)optin) {
+            // rows too long to stage: the lists are not pruned
+            h->prune_sys = nullptr;
+            h->x_prune = nullptr;
+        } else {
+            cudaError_t e = cudaFuncSetAttribute(k_prune, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+            if (e != cudaSuccess) return e;
+        }
     }
     h->split_build = pick_split(h, kBuildWarps, 3);  // keep >= 3 atoms per warp for register blocking
     cudaError_t e = allow_max_smem(k_build_cell<0, false>);

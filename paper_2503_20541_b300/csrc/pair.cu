@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_pair(
         const SysDev& S = sys[H.sys];
         const int mode = img_mode(H, pair_geo(S));
         // the system's back parts hold no pair within r_c (dynamic list pruning)
-        const bool pruned = prune_sys && (prune_sys[H.sys] & kPruned) != 0u;
+        const bool pruned = !fresh && prune_sys && (prune_sys[H.sys] & kPruned) != 0u;
 #define NB_PAIR_ARGS N, i, H, S, fresh, pruned, xs, ps, nbr, cap, qd_all[w], qj_all[w], ffix, e_atom, scale, flags
         if (mode == kImgPlain) pair_atom<LJ, COUL, EN, kImgPlain>(NB_PAIR_ARGS);
         else if (mode == kImgCode) pair_atom<LJ, COUL, EN, kImgCode>(NB_PAIR_ARGS);
@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(kVjpThreads, COUL ? 2 : 4) k_vjp(
         if (i + R.step < R.i1) hn = load_hdr(i + R.step, sid, xs, ps, nbr, cnt, cnt_out, cap);
         const SysDev& S = sys[H.sys];
         const int mode = img_mode(H, pair_geo(S));
-        const bool pruned = prune_sys && (prune_sys[H.sys] & kPruned) != 0u;
+        const bool pruned = !fresh && prune_sys && (prune_sys[H.sys] & kPruned) != 0u;
 #define NB_VJP_ARGS N, i, H, S, fresh, pruned, xs, ps, lam, nbr, cap, qd_all[w], qj_all[w], gx_s, gp_s, ffix, e_atom, scale, \
                     flags
         if (mode == kImgPlain) vjp_atom<LJ, COUL, kImgPlain>(NB_VJP_ARGS);

@@ -277,7 +277,8 @@ def error_vs_fp64(torch, nbcore, wl, s, f_gpu, e_gpu):
     from oracle import dynamics as odyn
     from oracle import pme as opme
     out = {"note": "relative RMS of the force vectors and |E - E_fp64| / |E_fp64| per energy component; "
-                   "the bars of the parity tests are 1e-5 (forces) and 1e-6 (energies)"}
+                   "the bars of the parity tests are 1e-5 (forces) and 1e-6 (energies); energy_precise: "
+                   "the same call with NB_ENERGY_PRECISE (two-float energies)"}
     names = ["E_lj", "E_dir", "E_excl", "E_self", "E_rec"]
 
     def oracle_eval(sys_, with_pme):
@@ -296,25 +297,31 @@ def error_vs_fp64(torch, nbcore, wl, s, f_gpu, e_gpu):
     eo, fo = oracle_eval(s, True)
     out["water_24k"] = {"force_rel_rms": _rel_rms(f_gpu, fo), "energy": _energy_errors(e_gpu, eo, names)}
 
-    def gpu_eval(systems, terms):
+    def gpu_eval(systems, terms, precise=False):
         n_tot = sum(x.n for x in systems)
         xq = torch.cat([torch.from_numpy(nbcore.pack_xq(x.x, x.q)) for x in systems]).cuda()
         f = torch.empty((n_tot, 3), dtype=torch.float32, device="cuda")
         e = torch.empty((len(systems), 6), dtype=torch.float64, device="cuda")
         with nbcore.Handle(systems) as h:
-            h.nonbonded_forces(xq, f, e, terms=terms, force_rebuild=True)
+            h.nonbonded_forces(xq, f, e, terms=terms, force_rebuild=True, precise=precise)
             h.check()
         return f.cpu().numpy(), e.cpu().numpy()
+
+    _, ep = gpu_eval([s], nbcore.NB_TERM_ALL, precise=True)
+    out["water_24k"]["energy_precise"] = _energy_errors(ep[0], eo, names)
 
     # one LJ sweep row (32,000 atoms)
     lj = wl.lj_random(32000, seed=11)
     fg, eg = gpu_eval([lj], nbcore.NB_TERM_LJ)
     eo, fo = oracle_eval(lj, False)
     out["lj_sweep_32k"] = {"force_rel_rms": _rel_rms(fg, fo), "energy": _energy_errors(eg[0], eo, names[:1])}
+    _, ep = gpu_eval([lj], nbcore.NB_TERM_LJ, precise=True)
+    out["lj_sweep_32k"]["energy_precise"] = _energy_errors(ep[0], eo, names[:1])
     # two systems of the 256-system batch, evaluated together
     mix = wl.batched_mix(256)
     pick = [mix[0], mix[1]]
     fg, eg = gpu_eval(pick, nbcore.NB_TERM_ALL)
+    _, ep = gpu_eval(pick, nbcore.NB_TERM_ALL, precise=True)
     off = 0
     rows = []
     for k, sys_ in enumerate(pick):
@@ -322,11 +329,13 @@ def error_vs_fp64(torch, nbcore, wl, s, f_gpu, e_gpu):
         eo, fo = oracle_eval(sys_, pme)
         rows.append({"system": k, "atoms": sys_.n, "kind": "water" if sys_.ke != 0.0 else "LJ",
                      "force_rel_rms": _rel_rms(fg[off:off + sys_.n], fo),
-                     "energy": _energy_errors(eg[k], eo, names if sys_.ke != 0.0 else names[:1])})
+                     "energy": _energy_errors(eg[k], eo, names if sys_.ke != 0.0 else names[:1]),
+                     "energy_precise": _energy_errors(ep[k], eo, names if sys_.ke != 0.0 else names[:1])})
         off += sys_.n
     out["batched_systems"] = rows
-    # boxes whose cancelling energy sums sit near the FP32 floor (the parity tests bound them
-    # by the random walk of the per-pair roundings where 1e-6 is below that floor)
+    # boxes whose cancelling energy sums sit near the FP32 floor (the parity tests bound the
+    # FP32 energies by the random walk of the per-pair roundings where 1e-6 is below that
+    # floor, and the precise energies by 1e-6)
     small = {}
     mix_water = [x for x in mix if x.ke != 0.0]
     cases = (("water_rf_1800_atoms", wl.water_rf_density(600, seed=3), nbcore.NB_TERM_LJ | nbcore.NB_TERM_COUL, False),
@@ -335,9 +344,11 @@ def error_vs_fp64(torch, nbcore, wl, s, f_gpu, e_gpu):
              ("smallest_batch_water", min(mix_water, key=lambda x: x.n), nbcore.NB_TERM_ALL, True))
     for name, sys_, terms, pme in cases:
         fg, eg = gpu_eval([sys_], terms)
+        _, ep = gpu_eval([sys_], terms, precise=True)
         eo, fo = oracle_eval(sys_, pme)
         small[name] = {"atoms": sys_.n, "force_rel_rms": _rel_rms(fg, fo),
-                       "energy": _energy_errors(eg[0], eo, names if pme else names[:2])}
+                       "energy": _energy_errors(eg[0], eo, names if pme else names[:2]),
+                       "energy_precise": _energy_errors(ep[0], eo, names if pme else names[:2])}
     out["small_boxes"] = small
     # HMC proposal: dH of 2 replicas of the differentiable-HMC configuration (LJ 2048,
     # switch 2.2-2.5, L 32, dt 0.005) against the FP64 velocity-Verlet proposal
@@ -1579,8 +1590,8 @@ def main():
 
     h = nbcore.Handle([s])
 
-    def step(rebuild=True):
-        h.nonbonded_forces(xq, f, e, force_rebuild=rebuild)
+    def step(rebuild=True, precise=False):
+        h.nonbonded_forces(xq, f, e, force_rebuild=rebuild, precise=precise)
 
     # warm-up: W steps, and at least 2 s of them, so that clocks and memory are in their
     # loaded state when the timed region starts
@@ -1601,6 +1612,7 @@ def main():
     from paper_2503_20541_b300.graphs import CapturedStep
     g_step = CapturedStep(lambda: step(True))
     g_reuse = CapturedStep(lambda: step(False))
+    g_precise = CapturedStep(lambda: step(True, True))
     xq_h = xq.cpu().pin_memory()
     f_h = torch.empty((s.n, 3), dtype=torch.float32).pin_memory()
     e_h = torch.empty((1, 6), dtype=torch.float64).pin_memory()
@@ -1652,9 +1664,11 @@ def main():
     ms_reuse = timed(g_reuse)
     e2e_value, ms_e2e = job_throughput(pc["cutoff"], timed(g_e2e), world)
     clocks = sampler.stop()
+    # the same evaluation with precise (two-float) energies: reported beside, not timed above
+    ms_precise = timed(g_precise)
     h.check()
     value, ms = job_throughput(pc["cutoff"], ms_local, world)
-    del g_step, g_reuse, g_e2e
+    del g_step, g_reuse, g_e2e, g_precise
     # the forces and energies of one full evaluation, kept for the FP64 error block
     step(True)
     f_eval, e_eval = f.cpu().numpy().copy(), e.cpu().numpy()[0].copy()
@@ -1766,6 +1780,7 @@ def main():
         "row_rooflines": rows,
         "stage_ms_per_step_eager": {k: v[0] / max(K, 1) for k, v in stages.items()},
         "ms_per_step_list_reused": ms_reuse,
+        "ms_per_step_precise_energy": ms_precise,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(xq.numel() * 4), "d2h_bytes_per_step": int(f.numel() * 4 + e.numel() * 8)},
         "clocks": clocks,

@@ -68,6 +68,7 @@ typedef enum {
 #define NB_TERM_PME 4    /* PME reciprocal space (systems with a PME mesh) */
 #define NB_TERM_ALL 7
 #define NB_FORCE_REBUILD 256 /* rebuild the neighbour list unconditionally */
+#define NB_ENERGY_PRECISE 512 /* nonbonded_forces: energies in two-float arithmetic (see there) */
 
 /*
  * One periodic (or open) system.  Follows Sec. 2.1.2 of the paper:
@@ -193,6 +194,13 @@ nb_status nl_build(nb_handle* h, const float* xq, int32_t* pairs_out, int64_t ma
  * runs an energy-free kernel (a polynomial erfc, 1/r^2 from 1/r, a shorter reduction):
  * its forces agree with those of a call that asks for energies to FP32 rounding, not
  * bit for bit.
+ * With NB_ENERGY_PRECISE in `terms` (and energies != NULL) the real-space and exclusion
+ * energies are recomputed in two-float arithmetic (an FP32 hi + lo pair, ~48 bits: exact
+ * coordinate differences, r^2, 1/r, erfc and the LJ powers to 1e-14 - 1e-12 relative, two-float
+ * per-atom sums) by a second list pass, and reduced in FP64 as hi + lo.  Energy sums whose
+ * pair terms cancel 10^3-10^4-fold (neutral water) then meet 1e-6 relative against FP64
+ * where the FP32 energies do not; the forces are the energy-free kernel's (bitwise those of
+ * a call with energies == NULL).  The PME reciprocal and self energies are FP64 either way.
  */
 nb_status nonbonded_forces(nb_handle* h, const float* xq, float* f_out, double* energies,
                            int32_t terms, void* stream);
@@ -220,6 +228,18 @@ nb_status nonbonded_forces_allpairs(nb_handle* h, const float* xq, float* f_out,
  * No handle; launches one kernel on `stream`; NB_ERR_ARG for n < 0 or NULL arrays with n > 0.
  */
 nb_status nb_erfc_eval(const float* x, float* out, int32_t n, void* stream);
+
+/*
+ * erfc(x) in two-float arithmetic exactly as the precise energies evaluate it
+ * (NB_ENERGY_PRECISE): x = x_hi + x_lo, a piecewise degree-15 interpolant with two-float
+ * coefficients on [0, 6) (FP32 erfcf beyond), for checking it against a reference erfc.
+ *   x_hi, x_lo [n]        (device) the argument as an unevaluated sum, x >= 0, |x_lo| small
+ *                         against x_hi (a rounding error); other values give unspecified results.
+ *   out_hi, out_lo [n]    (device) erfc(x) = out_hi + out_lo.
+ * No handle; launches one kernel on `stream`; NB_ERR_ARG for n < 0 or NULL arrays with n > 0.
+ */
+nb_status nb_erfc_df_eval(const float* x_hi, const float* x_lo, float* out_hi, float* out_lo, int32_t n,
+                          void* stream);
 
 /*
  * PME charge spreading alone (Sec. 2.1.2, smooth PME with order-4 cardinal B-splines):

@@ -378,6 +378,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         }
         D.index = s;
         D.rc2 = (float)(d.r_cut * d.r_cut);
+        D.rc = (float)d.r_cut;
         D.rnl2 = (float)(rnl * rnl);
         D.disp2 = (float)(0.25 * d.r_skin * d.r_skin);
         {
@@ -392,6 +393,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         D.has_switch = (d.r_switch >= 0.0 && d.r_switch < d.r_cut) ? 1 : 0;
         D.rs = D.has_switch ? (float)d.r_switch : 0.f;
         D.inv_sw = D.has_switch ? (float)(1.0 / (d.r_cut - d.r_switch)) : 0.f;
+        D.inv_sw_lo = D.has_switch ? (float)(1.0 / (d.r_cut - d.r_switch) - (double)D.inv_sw) : 0.f;
         D.alpha = (float)d.alpha;
         D.ke = (float)d.ke;
         D.beta2 = (float)(d.alpha * d.alpha);
@@ -494,6 +496,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         }
         NB_TRY(dalloc(h, &h->ffix, 3 * (size_t)N));
         NB_TRY(dalloc(h, &h->e_atom, N));
+        NB_TRY(dalloc(h, &h->e_lo, N));
         NB_TRY(dalloc(h, &h->flags, kFlagWords));
         NB_TRY(dalloc(h, &h->build_ticket, 1));
         NB_TRY(cudaMemset(h->build_ticket, 0, sizeof(unsigned)));
@@ -566,6 +569,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         NB_TRY(cudaMemset(h->nbr_out, 0, sizeof(int) * N));
         NB_TRY(cudaMemset(h->ffix, 0, sizeof(long long) * 3 * N));
         NB_TRY(cudaMemset(h->e_atom, 0, sizeof(float4) * N));
+        NB_TRY(cudaMemset(h->e_lo, 0, sizeof(float4) * N));
         NB_TRY(cudaMemset(h->ke_atom, 0, sizeof(float) * N));
         NB_TRY(cudaMemset(h->flags, 0, sizeof(unsigned) * kFlagWords));
         NB_TRY(cudaMemset(h->xs, 0, sizeof(float4) * N));
@@ -691,11 +695,13 @@ nb_status nonbonded_forces(nb_handle* h, const float* xq, float* f_out, double* 
     // with an output to write, the exclusion correction, the force output and the energy
     // reduction run as one epilogue kernel after the pair kernel and the PME gather
     const bool epi = f_out || energies;
-    nb_status s = eval(h, F4(xq), t | (epi ? kTermDeferExcl : 0), (terms & NB_FORCE_REBUILD) != 0, st, false,
-                       energies != nullptr);
+    const bool precise = energies && (terms & NB_ENERGY_PRECISE);
+    h->xq_in = F4(xq);
+    nb_status s = eval(h, F4(xq), t | (epi ? kTermDeferExcl : 0) | (precise ? kTermPrecise : 0),
+                       (terms & NB_FORCE_REBUILD) != 0, st, false, energies != nullptr);
     if (s != NB_OK) return s;
     Stage sc(h, NB_STAGE_UPDATE, st);
-    if (epi) launch_epilogue(h, t, f_out, energies, st);
+    if (epi) launch_epilogue(h, t, f_out, energies, st, precise);
     return launched();
 }
 

@@ -61,6 +61,9 @@ constexpr int kTermEnergy = 1 << 16;
 // Internal bit of the `terms` passed to launch_pair: the exclusion correction is left to the
 // evaluation's epilogue (launch_epilogue), which adds it while it writes the forces.
 constexpr int kTermDeferExcl = 1 << 17;
+// Internal bit of the `terms` passed to launch_pair: precise (two-float) energies; the pair
+// kernel runs its force-only form and k_energy_df writes e_atom and e_lo.
+constexpr int kTermPrecise = 1 << 18;
 constexpr int kFlagWords = 8;
 // A neighbour-list entry: the partner's slot in the low kEntrySlotBits bits and, above them,
 // the pair's periodic image as 2 bits per axis d: bit 2d, atom i moves down by L; bit 2d + 1,
@@ -82,7 +85,7 @@ struct SysDev {
     float rs, inv_sw;     // switch start and 1/(r_c - r_s)
     float alpha, ke;
     float beta2;          // alpha^2
-    float pad0;
+    float inv_sw_lo;      // 1/(r_c - r_s) - inv_sw: the constant as a double-float pair (precise energies)
     int nc[3];
     int cell_off;
     int atom_off, n_atoms;
@@ -98,7 +101,7 @@ struct SysDev {
     float krf, crf;       // reaction field (Eq. RFA): k = (eps_s-1)/((2eps_s+1) r_c^3), c = 3eps_s/((2eps_s+1) r_c)
     float krf_lo, crf_lo; // k - krf and c - crf: the constants as double-float pairs for the energy
     int index;            // the system's index in the handle
-    int pad6;
+    float rc;             // r_c (FP32; r_c^2 = rc rc exactly as a two-float product)
 };
 
 // An FFT group: PME systems sharing one mesh shape, meshes at a fixed stride.
@@ -175,6 +178,8 @@ struct nb_handle {
     int* exp_cnt = nullptr;      // [N] pairs each row emits in the pair export (valid per NB_FLAG_EXPORT)
     long long* ffix = nullptr;   // [3N] slot
     float4* e_atom = nullptr;    // [N] slot: half energies (E_lj, E_dir, E_excl, 0) of each atom
+    float4* e_lo = nullptr;      // [N] slot: low parts of e_atom .x, .y in a precise-energy evaluation
+    const float4* xq_in = nullptr;  // caller-order positions of the current precise-energy evaluation
     unsigned* flags = nullptr;   // [kFlagWords]: rebuild request, error bits, rebuild count, fresh list
     unsigned* build_ticket = nullptr;  // [1] blocks of the list build done (reset by the last)
     unsigned* bin_ticket = nullptr;    // [1] blocks of the binning done (reset by the last, which scans)
@@ -347,7 +352,7 @@ void launch_pair(nb_handle* h, int terms, cudaStream_t st);
 void launch_vjp(nb_handle* h, int terms, cudaStream_t st);
 // exclusion correction (when deferred), force output (f_out, may be null) and energy
 // reduction (dst, may be null) of a force evaluation in one launch
-void launch_epilogue(nb_handle* h, int terms, float* f_out, double* dst, cudaStream_t st);
+void launch_epilogue(nb_handle* h, int terms, float* f_out, double* dst, cudaStream_t st, bool precise = false);
 cudaError_t pair_setup(nb_handle* h);
 // allpairs.cu
 void launch_allpairs_lj(nb_handle* h, const float4* xq, cudaStream_t st);

@@ -31,6 +31,8 @@
 #include "erfc.cuh"
 #include "lj.cuh"
 #include "reduce.cuh"
+#include "dfloat.cuh"
+#include "erfc_df.cuh"
 
 namespace nb {
 
@@ -599,6 +601,211 @@ __device__ __forceinline__ float excl_energy_half(float ke, float q, float eex) 
     return 0.5f * fmaf(qke, eex, lo * eex);
 }
 
+// ---- Precise energies (NB_ENERGY_PRECISE) ---------------------------------------------
+// The pair energies of water cancel 10^3-10^4-fold in their sums (sum |e_ij| over |E|), so
+// the FP32 pair energies leave relative errors of a few 1e-6 on small boxes.  The precise
+// evaluation recomputes the energies -- not the forces, which the force-only pair kernel
+// gives -- in two-float arithmetic from the coordinate differences on: each difference is
+// exact (two_sum of the two image-shifted coordinates), r^2, r, 1/r, erfc and the LJ powers
+// carry 1e-14 - 1e-12 relative error, the per-atom sums are two-float and scaled once per atom by
+// ke q_i as an exact two-product, and the atom's record is split into hi (e_atom) and lo
+// (e_lo) parts that the epilogue adds in FP64.  The differences are taken from the caller's
+// positions (the slot-ordered frame positions may carry a rounding from the wrap into the
+// box), in the periodic image that the FP32 difference of the list entry names.  The pair
+// set is the exact one, r < r_c decided on the two-float r^2 against r_c^2 = rc rc (an exact
+// two-product), which is the FP64 oracle's: the FP32 test of the force kernel may put a pair
+// within its rounding band of r_c on the other side, and in water one such Coulomb pair at
+// r_c (ke q_O q_H erfc(alpha r_c)/r_c ~ 2.4e-3 kJ/mol at alpha r_c = 2.88) already moves a
+// box's E_dir by ~1e-6 relative.  So the pass walks the whole row (the back part too, except
+// where the system's prune has ruled it out: no pair there can be within r_c).
+
+constexpr float kTwoInvSqrtPi = 1.12837916709551257f;  // 2 / sqrt(pi)
+
+// erfc(x) in two-float, x = x.hi + x.lo >= 0: the piecewise interpolant of erfc_df.cuh at
+// x.hi (t = x.hi - k H is exact) plus the Taylor terms in d = x.lo to second order,
+// d erfc'(x.hi) (1 - x.hi d) with erfc'(x) = -(2/sqrt(pi)) exp(-x^2) and erfc'' = -2x erfc'
+// (|d| <= 2^-24 x.hi: the first-order term is ~1e-6 of erfc and needs FP32 accuracy, a few
+// ulp; the second ~2 x^2 d^2 relative, 4e-12 at x = 6; the third is below 1e-18).  Past the
+// table (erfc < 2.2e-17) the FP32 erfcf.
+__device__ __forceinline__ DF erfc_df(DF x) {
+    const float xh = x.hi;
+    if (!(xh < kErfcDfH * (float)kErfcDfIntervals)) return DF{erfcf(xh), 0.f};
+    const int k = max(0, min((int)(xh * kErfcDfInvH), kErfcDfIntervals - 1));
+    const float t = __fsub_rn(xh, __fmul_rn((float)k, kErfcDfH));
+    const float2* c = g_erfc_df[k];
+    float2 ck = __ldg(c + kErfcDfDeg);
+    DF p{ck.x, ck.y};
+#pragma unroll
+    for (int m = kErfcDfDeg - 1; m >= 0; --m) {
+        ck = __ldg(c + m);
+        p = df_add(df_mul_f(p, t), DF{ck.x, ck.y});
+    }
+    // exp(-x^2) with x^2 = sq.hi + sq.lo: the rounding of x^2 alone would be x^2 2^-24 of
+    // the exponent (5e-7 relative at x = 3); expf, as __expf's error also grows with x^2
+    const DF sq = two_prod(xh, xh);
+    const float d1 = -kTwoInvSqrtPi * expf(-sq.hi) * (1.f - sq.lo);
+    return df_add_f(p, __fmul_rn(__fmul_rn(x.lo, d1), fmaf(-xh, x.lo, 1.f)));
+}
+
+// The exact two-float difference x_i - x_j of the caller's positions oi, oj in the periodic
+// image of the FP32 difference d32 (taken in the frame of the list build): the two differ by
+// a whole number n of box lengths along each periodic axis (plus FP32 rounding, far below
+// L/2), and n L is subtracted as an exact two-product.
+__device__ __forceinline__ void caller_diff_df(const float4& oi, const float4& oj, const float d32[3],
+                                               const SysDev& S, DF d[3]) {
+    const float a[3] = {oi.x, oi.y, oi.z}, b[3] = {oj.x, oj.y, oj.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        d[k] = two_sum(a[k], -b[k]);
+        if (S.periodic) {
+            const float n = rintf(__fdiv_rn(__fsub_rn(d[k].hi, d32[k]), S.L[k]));
+            if (n != 0.f) d[k] = df_add(d[k], two_prod(-n, S.L[k]));
+        }
+    }
+}
+
+// r^2 < r_c^2 on two-float values (both normalised)
+__device__ __forceinline__ bool df_less(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+
+__device__ __forceinline__ DF r2_df(const DF d[3]) {
+    return df_add(df_add(df_mul(d[0], d[0]), df_mul(d[1], d[1])), df_mul(d[2], d[2]));
+}
+
+// LJ energy of one pair per unit eps_ij in two-float: 4 ((s/r)^12 - (s/r)^6), times the
+// switch S(x), x = (r - r_s)/(r_c - r_s), above r_s.
+__device__ __forceinline__ DF lj_unit_df(float sig_i, float sig_j, DF r2, const SysDev& S) {
+    const DF sig = df_scale(two_sum(sig_i, sig_j), 0.5f);
+    const DF s2 = df_div(df_mul(sig, sig), r2);
+    const DF s6 = df_mul(df_mul(s2, s2), s2);
+    DF u = df_scale(df_add(df_mul(s6, s6), df_neg(s6)), 4.f);
+    if (S.has_switch) {
+        const DF r = df_sqrt(r2);
+        const DF x = df_mul(df_add_f(r, -S.rs), DF{S.inv_sw, S.inv_sw_lo});
+        if (x.hi > 0.f) {
+            // S = 1 + x^3 (-10 + x (15 - 6 x))
+            DF p = df_add_f(df_mul_f(x, -6.f), 15.f);
+            p = df_add_f(df_mul(p, x), -10.f);
+            const DF sw = df_add_f(df_mul(df_mul(df_mul(p, x), x), x), 1.f);
+            u = df_mul(u, sw);
+        }
+    }
+    return u;
+}
+
+// Ewald direct-space (EWALD) or reaction-field energy of one pair per unit ke q_i, in
+// two-float: q_j erfc(alpha r)/r, or q_j (1/r + k r^2 - c) of Eq. RFA.
+template <int COUL>
+__device__ __forceinline__ DF coul_unit_df(float qj, DF r2, const SysDev& S) {
+    const DF r = df_sqrt(r2);
+    const DF rinv = df_div(DF{1.f, 0.f}, r);
+    if (COUL == kCoulEwald) return df_mul_f(df_mul(erfc_df(df_mul_f(r, S.alpha)), rinv), qj);
+    DF u = df_add(rinv, df_mul(DF{S.krf, S.krf_lo}, r2));
+    u = df_add(u, DF{-S.crf, -S.crf_lo});
+    return df_mul_f(u, qj);
+}
+
+// Exclusion-correction energy of slot i in two-float: half of ke q_i sum_e -q_j erf(alpha r)/r
+// (erf = 1 - erfc), each excluded pair's difference from the caller's positions (xo, caller
+// order; perm: slot -> caller index) in the minimum image that excl_terms takes.
+__device__ __forceinline__ DF excl_energy_df(int i, const SysDev& S, const float4* __restrict__ xs, const ExclView& X,
+                                             const float4* __restrict__ xo, const int* __restrict__ perm) {
+    const float4 xr = xs[i];
+    const float4 oi = xo[perm[i]];
+    const int ne = X.count(i);
+    DF sum{0.f, 0.f};
+    for (int e = 0; e < ne; ++e) {
+        const int j = X.partner(i, e);
+        const float4 xj = xs[j];
+        float d32[3] = {xr.x - xj.x, xr.y - xj.y, xr.z - xj.z};
+        if (S.periodic) {
+            d32[0] = mi_pair(xr.x, xj.x, S.L[0], S.halfL[0]);
+            d32[1] = mi_pair(xr.y, xj.y, S.L[1], S.halfL[1]);
+            d32[2] = mi_pair(xr.z, xj.z, S.L[2], S.halfL[2]);
+        }
+        DF d[3];
+        caller_diff_df(oi, xo[perm[j]], d32, S, d);
+        const DF r2 = r2_df(d);
+        const DF r = df_sqrt(r2);
+        const DF erf = df_add_f(df_neg(erfc_df(df_mul_f(r, S.alpha))), 1.f);
+        sum = df_add(sum, df_mul_f(df_div(erf, r), -xj.w));  // the charges: xs .w = xq .w
+    }
+    return df_scale(df_mul(two_prod(S.ke, xr.w), sum), 0.5f);
+}
+
+// Precise energies of atom i (one warp): lane l takes entries l, l + 32, ... of the row's
+// front and, unless the system's prune has ruled it out, its back; the pair is in if its
+// two-float r^2 (caller positions) is below r_c^2; each pair's energy and the sums are
+// two-float.  The record: half of E_LJ and of E_dir (or E_RF), hi parts in e_atom, lo parts
+// in e_lo.
+template <bool LJ, int COUL, int IMG>
+__device__ __forceinline__ void energy_df_atom(int i, const AtomHdr& H, const SysDev& S, bool skip_back,
+                                               const float4* __restrict__ xs, const float4* __restrict__ xo,
+                                               const int* __restrict__ perm, const float2* __restrict__ ps,
+                                               const unsigned* __restrict__ nbr, int cap, float4* __restrict__ e_atom,
+                                               float4* __restrict__ e_lo) {
+    const int lane = threadIdx.x & 31;
+    const PairGeo G = pair_geo(S);
+    const float4 xr = H.xr;
+    const float2 pi = H.pi;
+    const bool do_lj = LJ && pi.y != 0.f;
+    const bool do_coul = COUL != kCoulNone && S.ke != 0.f;
+    const unsigned* row = nbr + (size_t)i * cap;
+    const int n_all = H.nin + (skip_back ? 0 : H.nout);
+    const float4 oi = xo[perm[i]];
+    const DF rc2 = two_prod(S.rc, S.rc);
+    DF elj{0.f, 0.f}, eq{0.f, 0.f};
+    for (int e = lane; e < n_all; e += 32) {
+        const unsigned ent = e < H.nin ? row[e] : row[cap - H.nout + (e - H.nin)];
+        const int j = (int)(ent & kEntrySlotMask);
+        const float4 cj = xs[j];
+        float d32[3];
+        entry_diff<IMG>(xr, cj, ent >> kEntrySlotBits, G, d32[0], d32[1], d32[2]);
+        DF d[3];
+        caller_diff_df(oi, xo[perm[j]], d32, S, d);
+        const DF r2 = r2_df(d);
+        if (!df_less(r2, rc2)) continue;
+        if (do_lj) {
+            const float2 pj = ps[j];
+            if (pj.y != 0.f) elj = df_add(elj, df_mul(two_prod(pi.y, pj.y), lj_unit_df(pi.x, pj.x, r2, S)));
+        }
+        if (do_coul) eq = df_add(eq, coul_unit_df<COUL>(cj.w, r2, S));
+    }
+    elj = warp_sum_df(elj);
+    eq = warp_sum_df(eq);
+    if (lane == 0) {
+        if (COUL != kCoulNone) eq = df_mul(two_prod(S.ke, xr.w), eq);
+        e_atom[i] = make_float4(0.5f * elj.hi, 0.5f * eq.hi, 0.f, 0.f);
+        e_lo[i] = make_float4(0.5f * elj.lo, 0.5f * eq.lo, 0.f, 0.f);
+    }
+}
+
+// Precise-energy pass (one warp per atom, the pair kernel's atom ranges), launched after the
+// force-only pair kernel of the same evaluation.
+template <bool LJ, int COUL>
+__global__ void __launch_bounds__(kPairThreads) k_energy_df(
+    int N, int per_block, int cap, const int* __restrict__ sid, const SysDev* __restrict__ sys,
+    const float4* __restrict__ xs, const float2* __restrict__ ps, const unsigned* __restrict__ nbr,
+    const int* __restrict__ cnt, const int* __restrict__ cnt_out, float4* __restrict__ e_atom,
+    float4* __restrict__ e_lo, const unsigned* __restrict__ flags, const unsigned* __restrict__ prune_sys,
+    const float4* __restrict__ xo, const int* __restrict__ perm) {
+    pdl_wait();
+    const AtomRange R = block_atoms(N, per_block, kPairWarps);
+    const bool fresh = flags[NB_FLAG_FRESH] != 0u;
+    for (int i = R.i0; i < R.i1; i += R.step) {
+        const AtomHdr H = load_hdr(i, sid, xs, ps, nbr, cnt, cnt_out, cap);
+        const SysDev& S = sys[H.sys];
+        // a pruned row's back holds no pair within r_c (its front: all within r_c + the prune skin)
+        const bool skip_back = !fresh && prune_sys && (prune_sys[H.sys] & kPruned) != 0u && S.rin2 > 0.f;
+        const int mode = img_mode(H, pair_geo(S));
+        if (mode == kImgPlain)
+            energy_df_atom<LJ, COUL, kImgPlain>(i, H, S, skip_back, xs, xo, perm, ps, nbr, cap, e_atom, e_lo);
+        else if (mode == kImgCode)
+            energy_df_atom<LJ, COUL, kImgCode>(i, H, S, skip_back, xs, xo, perm, ps, nbr, cap, e_atom, e_lo);
+        else
+            energy_df_atom<LJ, COUL, kImgFold>(i, H, S, skip_back, xs, xo, perm, ps, nbr, cap, e_atom, e_lo);
+    }
+}
+
 // Exclusion correction, one thread per atom (slot order), after the pair kernel: the
 // force is added as fixed point (ffix is an integer sum, so the order against the pair
 // kernel's and the PME gather's adds is irrelevant); the energy (per unit ke q_i, scaled by
@@ -642,7 +849,8 @@ __global__ void __launch_bounds__(kRedThreads) k_epilogue(
     int N, int n_sys, const int* __restrict__ blk_sys, const int* __restrict__ blk_off,
     const SysDev* __restrict__ sys, const float4* __restrict__ xs, ExclView X, int do_excl,
     const long long* __restrict__ ffix, const int* __restrict__ perm, float scale, float finv,
-    float* __restrict__ f_out, const float4* __restrict__ e_atom, double* __restrict__ part,
+    float* __restrict__ f_out, const float4* __restrict__ e_atom, const float4* __restrict__ e_lo,
+    const float4* __restrict__ xo, double* __restrict__ part,
     const double* __restrict__ e_pme_blk, const int* __restrict__ pme_blk_off, int terms,
     unsigned* __restrict__ ticket, double* __restrict__ dst, unsigned* flags) {
     pdl_wait();
@@ -673,9 +881,16 @@ __global__ void __launch_bounds__(kRedThreads) k_epilogue(
         if (dst) {
             const float4 e = e_atom[k];
             const float q = xs[k].w;
-            v[0] += e.x;
-            v[1] += e.y;
-            v[2] += has_excl ? ez : e.z;
+            if (e_lo) {  // precise energies: hi + lo of the pair records, the correction's in two-float
+                const float4 l = e_lo[k];
+                v[0] += (double)e.x + (double)l.x;
+                v[1] += (double)e.y + (double)l.y;
+                v[2] += has_excl ? df_to_double(excl_energy_df(k, S, xs, X, xo, perm)) : (double)e.z;
+            } else {
+                v[0] += e.x;
+                v[1] += e.y;
+                v[2] += has_excl ? ez : e.z;
+            }
             v[3] += (double)q * q;
         }
     }
@@ -706,7 +921,7 @@ static int pair_atoms_per_block(const nb_handle* h, int warps) {
 }
 
 template <bool LJ, int COUL>
-static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp, bool energy, bool defer_excl) {
+static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp, bool energy, bool defer_excl, bool precise) {
     const int N = h->n_atoms;
     if (vjp) {
         const int pb = pair_atoms_per_block(h, kVjpWarps);
@@ -718,6 +933,10 @@ static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp, bool energy, bo
         launch_pdl(energy ? k_pair<LJ, COUL, true> : k_pair<LJ, COUL, false>, cdiv(N, pb), kPairThreads, 0, st, N,
                    pb, h->cap, h->sid, h->sys, h->xs, h->ps, h->nbr, h->nbr_cnt, h->nbr_out, h->ffix, h->e_atom,
                    h->fscale, h->flags, (const unsigned*)h->prune_sys);
+        if (precise)
+            launch_pdl(k_energy_df<LJ, COUL>, cdiv(N, pb), kPairThreads, 0, st, N, pb, h->cap, h->sid, h->sys, h->xs,
+                       h->ps, h->nbr, h->nbr_cnt, h->nbr_out, h->e_atom, h->e_lo, (const unsigned*)h->flags,
+                       (const unsigned*)h->prune_sys, h->xq_in, (const int*)h->perm);
     }
     if (COUL == kCoulEwald && h->excl_w && !(defer_excl && !vjp)) {
         const ExclView X = excl_view(h);
@@ -739,19 +958,22 @@ static void dispatch(nb_handle* h, int terms, cudaStream_t st, bool vjp) {
         // kernels would have written as zeros (forces stay as the load zeroed them)
         const size_t N = (size_t)h->n_atoms;
         cudaMemsetAsync(h->e_atom, 0, sizeof(float4) * N, st);
+        if (!vjp && (terms & kTermPrecise)) cudaMemsetAsync(h->e_lo, 0, sizeof(float4) * N, st);
         if (vjp) {
             cudaMemsetAsync(h->gx_s, 0, sizeof(float4) * N, st);
             cudaMemsetAsync(h->gp_s, 0, sizeof(float2) * N, st);
         }
         return;
     }
-    const bool en = vjp || (terms & kTermEnergy) != 0;
+    // precise energies: the force-only pair kernel, then the two-float energy pass
+    const bool pe = !vjp && (terms & kTermPrecise) != 0;
+    const bool en = vjp || ((terms & kTermEnergy) != 0 && !pe);
     const bool df = (terms & kTermDeferExcl) != 0;
-    if (lj && coul && rf) pair_launch<true, kCoulRF>(h, st, vjp, en, df);
-    else if (lj && coul) pair_launch<true, kCoulEwald>(h, st, vjp, en, df);
-    else if (lj) pair_launch<true, kCoulNone>(h, st, vjp, en, df);
-    else if (coul && rf) pair_launch<false, kCoulRF>(h, st, vjp, en, df);
-    else pair_launch<false, kCoulEwald>(h, st, vjp, en, df);
+    if (lj && coul && rf) pair_launch<true, kCoulRF>(h, st, vjp, en, df, pe);
+    else if (lj && coul) pair_launch<true, kCoulEwald>(h, st, vjp, en, df, pe);
+    else if (lj) pair_launch<true, kCoulNone>(h, st, vjp, en, df, pe);
+    else if (coul && rf) pair_launch<false, kCoulRF>(h, st, vjp, en, df, pe);
+    else pair_launch<false, kCoulEwald>(h, st, vjp, en, df, pe);
 }
 
 // The exclusion correction runs in the epilogue (not after the pair kernel) exactly when
@@ -761,11 +983,11 @@ bool epilogue_has_excl(const nb_handle* h, int terms) {
     return (terms & NB_TERM_COUL) && h->any_coul && h->coul_kind != kCoulRF && h->excl_w;
 }
 
-void launch_epilogue(nb_handle* h, int terms, float* f_out, double* dst, cudaStream_t st) {
+void launch_epilogue(nb_handle* h, int terms, float* f_out, double* dst, cudaStream_t st, bool precise) {
     const ExclView X = excl_view(h);
     launch_pdl(k_epilogue, h->n_red_blocks, kRedThreads, 0, st, h->n_atoms, h->n_sys, h->red_blk_sys,
                h->red_blk_off, h->sys, h->xs, X, epilogue_has_excl(h, terms) ? 1 : 0, h->ffix, h->perm, h->fscale,
-               h->finv, f_out, h->e_atom, h->red_part, h->e_pme_blk, h->conv_blk_off, terms, h->red_ticket, dst,
+               h->finv, f_out, h->e_atom, (precise && dst) ? h->e_lo : nullptr, h->xq_in, h->red_part, h->e_pme_blk, h->conv_blk_off, terms, h->red_ticket, dst,
                h->flags);
 }
 
@@ -785,6 +1007,14 @@ __global__ void k_erfc_eval(int n, const float* __restrict__ x, float* __restric
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = erfc_with_exp(x[i], exp_neg_sq(x[i]));
 }
+__global__ void k_erfc_df_eval(int n, const float* __restrict__ xh, const float* __restrict__ xl,
+                               float* __restrict__ oh, float* __restrict__ ol) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const DF e = erfc_df(DF{xh[i], xl[i]});
+    oh[i] = e.hi;
+    ol[i] = e.lo;
+}
 }  // namespace
 }  // namespace nb
 
@@ -792,5 +1022,14 @@ extern "C" nb_status nb_erfc_eval(const float* x, float* out, int32_t n, void* s
     if (n < 0 || (n > 0 && (!x || !out))) return NB_ERR_ARG;
     if (n == 0) return NB_OK;
     nb::k_erfc_eval<<<nb::cdiv(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, x, out);
+    return cudaGetLastError() == cudaSuccess ? NB_OK : NB_ERR_CUDA;
+}
+
+extern "C" nb_status nb_erfc_df_eval(const float* x_hi, const float* x_lo, float* out_hi, float* out_lo, int32_t n,
+                                     void* stream) {
+    if (n < 0 || (n > 0 && (!x_hi || !x_lo || !out_hi || !out_lo))) return NB_ERR_ARG;
+    if (n == 0) return NB_OK;
+    nb::k_erfc_df_eval<<<nb::cdiv(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, x_hi, x_lo, out_hi,
+                                                                                        out_lo);
     return cudaGetLastError() == cudaSuccess ? NB_OK : NB_ERR_CUDA;
 }

@@ -18,6 +18,7 @@ NB_TERM_COUL = 2
 NB_TERM_PME = 4
 NB_TERM_ALL = 7
 NB_FORCE_REBUILD = 256
+NB_ENERGY_PRECISE = 512
 NB_NE = 6
 E_LJ, E_DIR, E_EXCL, E_SELF, E_REC, E_KIN = range(6)
 
@@ -35,7 +36,7 @@ EXPORTS = [
     "hmc_trajectory_backward", "hmc_trajectory_steps", "hmc_trajectory_steps_backward", "autocorrelation",
     "nonbonded_force_vjp", "nb_rebuild_count", "nb_blocks_per_cell", "nb_timing_enable", "nb_timing_read",
     "pme_spread_static", "nb_set_water_constraints", "langevin_step", "constrain_positions", "constrain_velocities",
-    "nb_erfc_eval",
+    "nb_erfc_eval", "nb_erfc_df_eval",
 ]
 STATIC_MESH_MAX = 1 << 20
 STAGES = ["check", "rebuild", "pair", "spread", "fft", "convolve", "gather", "update", "build"]
@@ -150,6 +151,8 @@ def load():
     lib.pme_spread_static.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp]
     lib.nb_erfc_eval.restype = ctypes.c_int
     lib.nb_erfc_eval.argtypes = [_vp, _vp, _i32, _vp]
+    lib.nb_erfc_df_eval.restype = ctypes.c_int
+    lib.nb_erfc_df_eval.argtypes = [_vp, _vp, _vp, _vp, _i32, _vp]
     _lib = lib
     return lib
 
@@ -212,6 +215,19 @@ def erfc_eval(x, out=None):
     _ok(lib.nb_erfc_eval(_ptr(x, torch.float32, (n,), "x"), _ptr(out, torch.float32, (n,), "out"), n, _stream()),
         "nb_erfc_eval")
     return out
+
+
+def erfc_df_eval(x_hi, x_lo):
+    """erfc(x_hi + x_lo) in two-float (float32 device tensors, x >= 0) with the precise-energy
+    evaluation's own routine (nb_erfc_df_eval in include/nbcore.h); returns (hi, lo)."""
+    torch = _torch()
+    lib = load()
+    n = int(x_hi.numel())
+    hi, lo = torch.empty_like(x_hi), torch.empty_like(x_hi)
+    _ok(lib.nb_erfc_df_eval(_ptr(x_hi, torch.float32, (n,), "x_hi"), _ptr(x_lo, torch.float32, (n,), "x_lo"),
+                            _ptr(hi, torch.float32, (n,), "out_hi"), _ptr(lo, torch.float32, (n,), "out_lo"), n,
+                            _stream()), "nb_erfc_df_eval")
+    return hi, lo
 
 
 def autocorrelation(series, max_lag, a_hi=0.5, a_lo=0.05, acf=None, tau=None):
@@ -388,10 +404,12 @@ class Handle:
                                ctypes.byref(n), 0, _stream()), "nl_build")
         return out[:min(count, max_pairs)], int(n.value)
 
-    def nonbonded_forces(self, xq, f_out=None, energies=None, terms=NB_TERM_ALL, force_rebuild=False):
+    def nonbonded_forces(self, xq, f_out=None, energies=None, terms=NB_TERM_ALL, force_rebuild=False,
+                         precise=False):
+        """precise: energies in two-float arithmetic (NB_ENERGY_PRECISE)."""
         torch = _torch()
         N = self.n_atoms
-        t = int(terms) | (NB_FORCE_REBUILD if force_rebuild else 0)
+        t = int(terms) | (NB_FORCE_REBUILD if force_rebuild else 0) | (NB_ENERGY_PRECISE if precise else 0)
         _ok(self._lib.nonbonded_forces(
             self._h, _ptr(xq, torch.float32, (N, 4), "xq"),
             _ptr(f_out, torch.float32, (N, 3), "f_out", True),

@@ -219,3 +219,12 @@ def test_orthorhombic_water_box_against_the_oracle():
     t = s.ke * s.q[pairs[:, 0]].astype(np.float64) * s.q[pairs[:, 1]] * erfc(s.alpha * r) / r
     bound = E_TOL * abs(eo[1]) + 6.0 * np.finfo(np.float32).eps * np.sqrt(np.sum(t * t))
     assert abs(e[1] - eo[1]) <= bound, (e[1], eo[1], bound)
+    # precise (two-float) energies: every component at the flat bar
+    with nbcore.Handle([s]) as h:
+        ep = torch.empty((1, 6), dtype=torch.float64, device="cuda")
+        h.nonbonded_forces(torch.from_numpy(nbcore.pack_xq(s.x, s.q)).cuda(), None, ep, precise=True)
+        h.check()
+        ep = ep.cpu().numpy()[0]
+    for c in range(4):
+        assert abs(ep[c] - eo[c]) <= E_TOL * abs(eo[c]), (c, ep[c], eo[c])
+    assert abs(ep[4] - Ep) <= E_TOL * abs(Ep)

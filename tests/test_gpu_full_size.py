@@ -223,7 +223,8 @@ def test_lj_8m_every_atom():
 def test_batched_256_every_system_every_atom():
     """The 256-system batch of the benchmark (1.54M atoms, LJ and water, per-system cell
     sizes): every atom of every system (real space + PME for water) against the oracle,
-    and every system's energies."""
+    and every system's energies: the FP32 energies within 1e-6 or their rounding floor, and
+    the precise (two-float) energies of a second call within the flat 1e-6."""
     systems = wl.batched_mix(256)
     offs = np.cumsum([0] + [s.n for s in systems])
     xq = torch.cat([dev_xq(s) for s in systems])
@@ -233,9 +234,13 @@ def test_batched_256_every_system_every_atom():
     with nbcore.Handle(systems) as h:
         h.nonbonded_forces(xq, f, e)
         h.check()
-    fb = f.cpu().numpy().astype(np.float64)
-    eb = e.cpu().numpy()
+        fb = f.cpu().numpy().astype(np.float64)
+        eb = e.cpu().numpy()
+        h.nonbonded_forces(xq, f, e, precise=True)
+        h.check()
+        ebp = e.cpu().numpy()
     problems = []
+    worst = 0.0
     for k, s in enumerate(systems):
         try:
             eo, fo = _oracle_cells(s)
@@ -243,9 +248,19 @@ def test_batched_256_every_system_every_atom():
                 Ep, Fp = oracle_pme(s)
                 fo = fo + Fp
                 assert abs(eb[k, 4] - Ep) <= E_TOL * abs(Ep), ("system %d" % k, 4, eb[k, 4], Ep)
-            _check(fb[offs[k]:offs[k + 1]], fo, eb[k], eo, s, "system %d" % k)
+            eo_exact = np.array(eo, dtype=np.float64)
+            fo, eo, _ = _resolve_cutoff_pairs(fb[offs[k]:offs[k + 1]], fo, eo, s)
+            _check_forces(fb[offs[k]:offs[k + 1]], fo, "system %d" % k)
+            _check_energies(eb[k], eo, s, "system %d" % k)
+            # the precise pass decides r < r_c on its two-float r^2: the oracle's own pair set
+            for c in range(4):
+                err = abs(ebp[k, c] - eo_exact[c])
+                worst = max(worst, err / abs(eo_exact[c]) if eo_exact[c] else 0.0)
+                assert err <= max(E_TOL * abs(eo_exact[c]), 1e-12), ("system %d precise" % k, c, ebp[k, c],
+                                                                     eo_exact[c])
         except AssertionError as err:
             problems.append(str(err).splitlines()[0][:200])
+    print("batched 256: largest relative error of the precise energies %.1e" % worst)
     assert not problems, problems
 
 

@@ -22,10 +22,10 @@ E_TOL = 1e-6
 TERMS = nbcore.NB_TERM_LJ | nbcore.NB_TERM_COUL
 
 
-def _forces(h, s, terms=TERMS):
+def _forces(h, s, terms=TERMS, precise=False):
     f = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
     e = torch.empty((1, 6), dtype=torch.float64, device="cuda")
-    h.nonbonded_forces(dev_xq(s), f, e, terms=terms)
+    h.nonbonded_forces(dev_xq(s), f, e, terms=terms, precise=precise)
     h.check()
     return f.cpu().numpy().astype(np.float64), e.cpu().numpy()[0]
 
@@ -42,10 +42,14 @@ def test_reaction_field_water_matches_oracle(tile):
     s = wl.water_rf_density(600, seed=3)  # 1800 atoms, r_c 10 A, the paper's scaling setting
     with nbcore.Handle([s], stencil_tile=tile) as h:
         f, e = _forces(h, s)
+        _, ep = _forces(h, s, precise=True)
     eo, fo = oracle_real_space(s)
     assert rel_rms(f, fo) <= F_TOL
     assert abs(e[0] - eo[0]) <= E_TOL * abs(eo[0])
     assert abs(e[1] - eo[1]) <= _rf_tol(s, eo[1]), (e[1], eo[1], _rf_tol(s, eo[1]))
+    # precise (two-float) energies: the flat bar
+    for c in (0, 1):
+        assert abs(ep[c] - eo[c]) <= E_TOL * abs(eo[c]), (c, ep[c], eo[c])
     assert e[2] == 0.0 and e[3] == 0.0 and e[4] == 0.0  # no exclusion correction, self or mesh
     assert eo[2] == 0.0 and eo[3] == 0.0
 
@@ -55,6 +59,7 @@ def test_reaction_field_water_24k_sampled():
     s = wl.as_reaction_field(wl.water_box())
     with nbcore.Handle([s]) as h:
         f, e = _forces(h, s)
+        _, ep = _forces(h, s, precise=True)
     rng = np.random.default_rng(0)
     rows = np.sort(rng.choice(s.n, 400, replace=False))
     er, fr = oracle.nonbonded_rows(s.x.astype(np.float64), s.q, s.sigma, s.sqrt_eps, oracle_params(s), rows,
@@ -66,6 +71,8 @@ def test_reaction_field_water_24k_sampled():
     assert abs(e[0] - eo[0]) <= E_TOL * abs(eo[0]), (e[0], eo[0])
     tol = _rf_tol(s, eo[1], rows=np.arange(0, s.n, 11))  # every 11th row: O and H alike
     assert abs(e[1] - eo[1]) <= tol, (e[1], eo[1], tol)
+    for c in (0, 1):
+        assert abs(ep[c] - eo[c]) <= E_TOL * abs(eo[c]), (c, ep[c], eo[c])
 
 
 def test_reaction_field_vjp_matches_oracle():

@@ -699,8 +699,12 @@ __global__ void __launch_bounds__(kPruneWarps * 32) k_prune(int N, int cap, cons
     }
 }
 
+// Without exclusions (E = 0) 64 registers and eight blocks per SM: LJ 256k 263 -> 248 us per
+// build against 96 registers and five; with exclusions the extra blocks cost more than they
+// give (water 24k: 108 -> 121 us at 80 registers, 156 us at 64), and a minimum of 0 blocks
+// leaves their register count to the compiler.
 template <int E, bool SLOW>
-__global__ void __launch_bounds__(kBuildThreads) k_build_cell(
+__global__ void __launch_bounds__(kBuildThreads, E == 0 ? 8 : 0) k_build_cell(
     int cap, int tile, const int* __restrict__ cell_sys, const SysDev* __restrict__ sys,
     const int* __restrict__ start, const float4* __restrict__ xs, const int* __restrict__ perm,
     const int* __restrict__ iperm, const int* __restrict__ ex_off, const int* __restrict__ ex_idx,

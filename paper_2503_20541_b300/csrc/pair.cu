@@ -41,7 +41,7 @@ constexpr int kPairThreads = kPairWarps * 32;
 constexpr int kVjpWarps = 8;
 constexpr int kVjpThreads = kVjpWarps * 32;
 constexpr int kQueue = 64;        // per-warp queue of back-part pairs inside r_c
-constexpr int kAtomsPerWarp = 2;  // consecutive atoms of a block's range per warp (header prefetch)
+constexpr int kAtomsPerWarp = 2;  // atoms of a block's range per warp (header prefetch); 4 on large handles
 
 // Exclusion partners of slot i: count and the slot of partner e (from the per-slot
 // table when it holds all of them, else from the CSR).
@@ -760,6 +760,10 @@ __device__ __forceinline__ void energy_df_atom(int i, const AtomHdr& H, const Sy
         const float4 cj = xs[j];
         float d32[3];
         entry_diff<IMG>(xr, cj, ent >> kEntrySlotBits, G, d32[0], d32[1], d32[2]);
+        // clearly outside r_c: the FP32 r^2 (relative error ~1e-7, plus the rounding of the
+        // wrap of caller positions into the frame, ~1e-6 of r_c^2 for positions within a few
+        // box lengths) above r_c^2 (1 + 1e-3)
+        if (pair_r2(d32[0], d32[1], d32[2]) > S.rc2 * 1.001f) continue;
         DF d[3];
         caller_diff_df(oi, xo[perm[j]], d32, S, d);
         const DF r2 = r2_df(d);
@@ -911,12 +915,17 @@ static ExclView excl_view(const nb_handle* h) {
 }
 
 // Atoms per block of the pair and VJP kernels: kAtomsPerWarp per warp, fewer when the
-// handle is too small to give every SM a few blocks.
-static int pair_atoms_per_block(const nb_handle* h, int warps) {
+// handle is too small to give every SM a few blocks; with `wide`, four per warp when the
+// grid still holds at least eight waves of four blocks per SM (LJ 256k: pair kernel 136.9 ->
+// 128.8 us fresh, 182.2 -> 171.9 us kept; the 24,000-atom water box, at 1.3 waves with four,
+// keeps two: 58.2 against 64.9 us).
+static int pair_atoms_per_block(const nb_handle* h, int warps, bool wide = false) {
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long n = h->n_atoms;
+    if (wide && n >= (long long)warps * 4 * 4LL * sms * 8) return warps * 4;
     const long long full = (long long)warps * kAtomsPerWarp;
-    if ((long long)h->n_atoms >= full * 4LL * sms) return (int)full;
+    if (n >= full * 4LL * sms) return (int)full;
     return warps;
 }
 
@@ -929,7 +938,7 @@ static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp, bool energy, bo
                    h->lam, h->nbr, h->nbr_cnt, h->nbr_out, h->gx_s, h->gp_s, h->ffix, h->e_atom, h->fscale, h->flags,
                    (const unsigned*)h->prune_sys);
     } else {
-        const int pb = pair_atoms_per_block(h, kPairWarps);
+        const int pb = pair_atoms_per_block(h, kPairWarps, true);
         launch_pdl(energy ? k_pair<LJ, COUL, true> : k_pair<LJ, COUL, false>, cdiv(N, pb), kPairThreads, 0, st, N,
                    pb, h->cap, h->sid, h->sys, h->xs, h->ps, h->nbr, h->nbr_cnt, h->nbr_out, h->ffix, h->e_atom,
                    h->fscale, h->flags, (const unsigned*)h->prune_sys);

@@ -365,12 +365,14 @@ def error_vs_fp64(torch, nbcore, wl, s, f_gpu, e_gpu):
     x1 = torch.empty_like(x0)
     st = torch.empty((R, 4), dtype=torch.float64, device="cuda")
     ck = torch.empty(nbcore.ckpt_size(R * n, L, 8), dtype=torch.float32, device="cuda")
-    with nbcore.Handle(reps) as h:
-        h.hmc_trajectory(x0, x1, torch.from_numpy(w).cuda(), torch.from_numpy(dt).cuda(), L, 1.0,
-                         torch.from_numpy(xi.reshape(-1, 3)).cuda(), torch.from_numpy(u).cuda(), st, ck, 8,
-                         terms=nbcore.NB_TERM_LJ)
-        h.check()
-    stg = st.cpu().numpy()
+    stg = {}
+    for tag, terms in (("fp32", nbcore.NB_TERM_LJ), ("precise", nbcore.NB_TERM_LJ | nbcore.NB_ENERGY_PRECISE)):
+        with nbcore.Handle(reps) as h:
+            h.hmc_trajectory(x0, x1, torch.from_numpy(w).cuda(), torch.from_numpy(dt).cuda(), L, 1.0,
+                             torch.from_numpy(xi.reshape(-1, 3)).cuda(), torch.from_numpy(u).cuda(), st, ck, 8,
+                             terms=terms)
+            h.check()
+        stg[tag] = st.cpu().numpy()
     hmc = []
     for r, sr in enumerate(reps):
         p = oracle.make_params(sr.box, r_cut=sr.r_cut, r_switch=sr.r_switch)
@@ -380,10 +382,45 @@ def error_vs_fp64(torch, nbcore, wl, s, f_gpu, e_gpu):
             return f, float(e[0])
         o = odyn.hmc_proposal(sr.x.astype(np.float64), xi[r].astype(np.float64), w[r * n:(r + 1) * n].astype(np.float64),
                               float(dt[r]), L, 1.0, fe, sr.box)
-        hmc.append({"replica": r, "dH_gpu": float(stg[r, 0]), "dH_fp64": o["dH"], "dH_abs_err": abs(float(stg[r, 0]) - o["dH"]),
+        hmc.append({"replica": r, "dH_gpu": float(stg["fp32"][r, 0]), "dH_fp64": o["dH"],
+                    "dH_abs_err": abs(float(stg["fp32"][r, 0]) - o["dH"]),
+                    "dH_abs_err_precise_energies": abs(float(stg["precise"][r, 0]) - o["dH"]),
                     "energy_scale": abs(o["U0"]) + o["K0"]})
+    # a water box (Ewald + PME + exclusions), 10 steps of 0.5 fs: FP32 and precise end energies
+    sw = wl.water_box(n_side=8, L=24.84, seed=9, pme_grid=24)
+    kTw = 2.494
+    xiw, _ = wl.hmc_randoms(1, sw.n, seed=11)
+    ww = (1.0 / sw.mass).astype(np.float32)
+    dtw = np.full(1, 0.0005, np.float32)
+    xw0 = torch.from_numpy(nbcore.pack_xq(sw.x, sw.q)).cuda()
+    xw1 = torch.empty_like(xw0)
+    stw = torch.empty((1, 4), dtype=torch.float64, device="cuda")
+    dhw = {}
+    for tag, terms in (("fp32", nbcore.NB_TERM_ALL), ("precise", nbcore.NB_TERM_ALL | nbcore.NB_ENERGY_PRECISE)):
+        with nbcore.Handle([sw]) as h:
+            h.hmc_trajectory(xw0, xw1, torch.from_numpy(ww).cuda(), torch.from_numpy(dtw).cuda(), 10, kTw,
+                             torch.from_numpy(xiw.reshape(-1, 3)).cuda(), torch.zeros(1, dtype=torch.float64,
+                                                                                        device="cuda"),
+                             stw, None, 0, terms=terms)
+            h.check()
+        dhw[tag] = float(stw.cpu().numpy()[0, 0])
+    pw = oracle.make_params(sw.box, r_cut=sw.r_cut, alpha=sw.alpha, ke=sw.ke)
+
+    def few(x):
+        e, f = oracle.nonbonded_cells(x, sw.q, sw.sigma, sw.sqrt_eps, pw, excl=sw.excl)
+        Ep, Fp = opme.pme(x, sw.q.astype(np.float64), sw.box, sw.alpha, sw.ke, sw.pme_grid)
+        return f + Fp, float(np.sum(e)) + Ep
+    ow = odyn.hmc_proposal(sw.x.astype(np.float64), xiw[0].astype(np.float64), ww.astype(np.float64), float(dtw[0]),
+                           10, kTw, few, sw.box)
     out["hmc_proposal"] = {"replicas": hmc, "workload": "LJ 2048 atoms x 2 replicas, switch 2.2-2.5, 32 leapfrog "
-                                                       "steps, dt 0.005, the same normals on both sides"}
+                                                       "steps, dt 0.005, the same normals on both sides",
+                           "water": {"atoms": sw.n, "dH_fp64": ow["dH"], "dH_abs_err": abs(dhw["fp32"] - ow["dH"]),
+                                     "dH_abs_err_precise_energies": abs(dhw["precise"] - ow["dH"]),
+                                     "energy_scale": abs(ow["U0"]) + ow["K0"],
+                                     "workload": "water 8^3 lattice (1,536 atoms, Ewald + PME 24^3 + exclusions), "
+                                                 "10 leapfrog steps of 0.5 fs, kT 2.494 kJ/mol"},
+                           "note": "dH error: the FP32 trajectory's roundings (F.dx per rounding) plus, without "
+                                   "NB_ENERGY_PRECISE, the FP32 end-state energies"}
     return out
 
 

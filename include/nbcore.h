@@ -338,6 +338,10 @@ nb_status constrain_velocities(nb_handle* h, const float* x, float* v, void* str
  *                    (positions, velocities) at steps 0, k, 2k, ... for the backward pass.
  * With checkpoints, the neighbour list is rebuilt at every checkpoint step so that a
  * recomputation from a checkpoint repeats the forward trajectory bit for bit.
+ * With NB_ENERGY_PRECISE in `terms`, the potential energies of the two end states (and so
+ * dH) are the two-float energies of nonbonded_forces (the forces there come from the
+ * energy-free kernel); pass the same `terms` to hmc_trajectory_backward, whose
+ * recomputation then runs the same kernels.
  */
 nb_status hmc_trajectory(nb_handle* h, const float* x0, float* x_out, const float* inv_mass,
                          const float* dt, int32_t n_leap, double kT, const float* xi,

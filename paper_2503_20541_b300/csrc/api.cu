@@ -140,6 +140,7 @@ nb_status run_pme_mesh(nb_handle* h, const float4* x, cudaStream_t st) {
 nb_status eval(nb_handle* h, const float4* xq, int terms, bool force, cudaStream_t st, bool loaded = false,
                bool energy = true) {
     const bool pme = (terms & NB_TERM_PME) && h->has_pme;
+    if (terms & kTermPrecise) h->xq_in = xq;  // the two-float energy pass reads the caller's positions
     bool binned = false;
     {
         Stage sc(h, NB_STAGE_CHECK, st);
@@ -696,7 +697,6 @@ nb_status nonbonded_forces(nb_handle* h, const float* xq, float* f_out, double* 
     // reduction run as one epilogue kernel after the pair kernel and the PME gather
     const bool epi = f_out || energies;
     const bool precise = energies && (terms & NB_ENERGY_PRECISE);
-    h->xq_in = F4(xq);
     nb_status s = eval(h, F4(xq), t | (epi ? kTermDeferExcl : 0) | (precise ? kTermPrecise : 0),
                        (terms & NB_FORCE_REBUILD) != 0, st, false, energies != nullptr);
     if (s != NB_OK) return s;
@@ -832,11 +832,14 @@ nb_status hmc_trajectory(nb_handle* h, const float* x0, float* x_out, const floa
     int N = h->n_atoms;
     float4* x = F4(x_out);
     float4* ck = ckpt ? F4(ckpt) : nullptr;
+    // precise energies at the two end states (dH)
+    const bool precise = (terms & NB_ENERGY_PRECISE) != 0;
+    const int tp = t | (precise ? kTermPrecise : 0);
     cudaMemcpyAsync(x_out, x0, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st);
     launch_hmc_init(h, inv_mass, xi, kT, st);
-    nb_status s = eval(h, x, t, ck != nullptr, st);
+    nb_status s = eval(h, x, tp, ck != nullptr, st);
     if (s != NB_OK) return s;
-    launch_reduce_energy(h, t, 1, h->e0, st);
+    launch_reduce_energy(h, t, 1, h->e0, st, StepStat(), precise);
     for (int l = 0; l < n_leap; ++l) {
         float4* cx = nullptr;
         float4* cv = nullptr;
@@ -850,12 +853,13 @@ nb_status hmc_trajectory(nb_handle* h, const float* x0, float* x_out, const floa
                              StepObs(), true);
         }
         // the energies of the end state only (dH); the inner steps need forces alone
-        s = eval(h, x, t, ck != nullptr && (l + 1) % ckpt_every == 0, st, true, l == n_leap - 1);
+        const bool last = l == n_leap - 1;
+        s = eval(h, x, last ? tp : t, ck != nullptr && (l + 1) % ckpt_every == 0, st, true, last);
         if (s != NB_OK) return s;
     }
     Stage sc(h, NB_STAGE_UPDATE, st);
     launch_integrate(h, x, h->vwork, inv_mass, dt, 0.5f, 0.f, 0, nullptr, nullptr, nullptr, st);
-    launch_reduce_energy(h, t, 1, h->e1, st);
+    launch_reduce_energy(h, t, 1, h->e1, st, StepStat(), precise);
     launch_hmc_finish(h, x, F4(x0), kT, u, stats, st);
     return launched();
 }
@@ -1002,8 +1006,11 @@ nb_status hmc_trajectory_backward(nb_handle* h, const float* x0, const float* in
         }
         return in;
     };
+    // a forward pass with precise energies ran the energy-free pair kernel at the end states:
+    // the recomputation does the same (kTermPrecise applies only where energies are asked for)
     return hmc_backward(h, x0, inv_mass, dt, L, kT, xi, ckpt, ckpt_every, inj, g_dt, g_inv_mass,
-                        terms & NB_TERM_ALL, false, S(stream));
+                        (terms & NB_TERM_ALL) | ((terms & NB_ENERGY_PRECISE) ? kTermPrecise : 0), false,
+                        S(stream));
 }
 
 nb_status hmc_trajectory_steps_backward(nb_handle* h, const float* x0, const float* inv_mass, const float* dt,

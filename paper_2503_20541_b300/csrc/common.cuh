@@ -472,7 +472,7 @@ struct Inject {
     int a_stride = 0;
 };
 void launch_reduce_energy(nb_handle* h, int terms, int with_kin, double* dst, cudaStream_t st,
-                          const StepStat& ss = StepStat());
+                          const StepStat& ss = StepStat(), bool precise = false);
 void launch_finalize_forces(nb_handle* h, float* f_out, cudaStream_t st);
 void launch_integrate(nb_handle* h, float4* xq, float4* v, const float* w_override, const float* dt,
                       float c_pre, float c_post, int drift, float4* ck_x, float4* ck_v,

@@ -25,8 +25,8 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
 // Energy reduction in one launch (reduce.cuh): each thread sums its atoms of the block's tile.
 __global__ void __launch_bounds__(kRedThreads) k_reduce_energy(
     int n_sys, const int* __restrict__ blk_sys, const int* __restrict__ blk_off, const SysDev* __restrict__ sys,
-    const float4* __restrict__ e_atom, const float4* __restrict__ xs, const float* __restrict__ ke_atom,
-    int with_kin, double* __restrict__ part, const double* __restrict__ e_pme_blk,
+    const float4* __restrict__ e_atom, const float4* __restrict__ e_lo, const float4* __restrict__ xs,
+    const float* __restrict__ ke_atom, int with_kin, double* __restrict__ part, const double* __restrict__ e_pme_blk,
     const int* __restrict__ pme_blk_off, int terms, unsigned* __restrict__ ticket, double* __restrict__ dst,
     StepStat ss) {
     pdl_wait();
@@ -39,6 +39,12 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_energy(
         v[0] += e.x;
         v[1] += e.y;
         v[2] += e.z;
+        if (e_lo) {  // precise energies: the two-float records' low parts
+            const float4 l = e_lo[k];
+            v[0] += l.x;
+            v[1] += l.y;
+            v[2] += l.z;
+        }
         v[3] += (double)q * q;
         if (with_kin) v[4] += ke_atom[k];
         // a system owns the same index range in both orders: its jump sum reads
@@ -371,9 +377,11 @@ __global__ void __launch_bounds__(kRedThreads) k_bwd_reduce_h(const SysDev* __re
 
 // ------------------------------------------------------------------ launchers
 
-void launch_reduce_energy(nb_handle* h, int terms, int with_kin, double* dst, cudaStream_t st, const StepStat& ss) {
+void launch_reduce_energy(nb_handle* h, int terms, int with_kin, double* dst, cudaStream_t st, const StepStat& ss,
+                          bool precise) {
     launch_pdl(k_reduce_energy, h->n_red_blocks, kRedThreads, 0, st, h->n_sys, h->red_blk_sys, h->red_blk_off, h->sys,
-                                                            h->e_atom, h->xs, h->ke_atom, with_kin, h->red_part,
+                                                            h->e_atom, precise ? (const float4*)h->e_lo : nullptr,
+                                                            h->xs, h->ke_atom, with_kin, h->red_part,
                                                             h->e_pme_blk, h->conv_blk_off, terms, h->red_ticket, dst,
                                                             ss);
 }

@@ -741,8 +741,8 @@ template <bool LJ, int COUL, int IMG>
 __device__ __forceinline__ void energy_df_atom(int i, const AtomHdr& H, const SysDev& S, bool skip_back,
                                                const float4* __restrict__ xs, const float4* __restrict__ xo,
                                                const int* __restrict__ perm, const float2* __restrict__ ps,
-                                               const unsigned* __restrict__ nbr, int cap, float4* __restrict__ e_atom,
-                                               float4* __restrict__ e_lo) {
+                                               const unsigned* __restrict__ nbr, int cap, const ExclView& X,
+                                               float4* __restrict__ e_atom, float4* __restrict__ e_lo) {
     const int lane = threadIdx.x & 31;
     const PairGeo G = pair_geo(S);
     const float4 xr = H.xr;
@@ -778,8 +778,12 @@ __device__ __forceinline__ void energy_df_atom(int i, const AtomHdr& H, const Sy
     eq = warp_sum_df(eq);
     if (lane == 0) {
         if (COUL != kCoulNone) eq = df_mul(two_prod(S.ke, xr.w), eq);
-        e_atom[i] = make_float4(0.5f * elj.hi, 0.5f * eq.hi, 0.f, 0.f);
-        e_lo[i] = make_float4(0.5f * elj.lo, 0.5f * eq.lo, 0.f, 0.f);
+        // the exclusion correction's energy record (Ewald systems with excluded partners)
+        DF ex{0.f, 0.f};
+        if (COUL == kCoulEwald && X.count(i) > 0 && S.alpha > 0.f && S.ke != 0.f)
+            ex = excl_energy_df(i, S, xs, X, xo, perm);
+        e_atom[i] = make_float4(0.5f * elj.hi, 0.5f * eq.hi, ex.hi, 0.f);
+        e_lo[i] = make_float4(0.5f * elj.lo, 0.5f * eq.lo, ex.lo, 0.f);
     }
 }
 
@@ -791,7 +795,7 @@ __global__ void __launch_bounds__(kPairThreads) k_energy_df(
     const float4* __restrict__ xs, const float2* __restrict__ ps, const unsigned* __restrict__ nbr,
     const int* __restrict__ cnt, const int* __restrict__ cnt_out, float4* __restrict__ e_atom,
     float4* __restrict__ e_lo, const unsigned* __restrict__ flags, const unsigned* __restrict__ prune_sys,
-    const float4* __restrict__ xo, const int* __restrict__ perm) {
+    const float4* __restrict__ xo, const int* __restrict__ perm, ExclView X) {
     pdl_wait();
     const AtomRange R = block_atoms(N, per_block, kPairWarps);
     const bool fresh = flags[NB_FLAG_FRESH] != 0u;
@@ -802,11 +806,11 @@ __global__ void __launch_bounds__(kPairThreads) k_energy_df(
         const bool skip_back = !fresh && prune_sys && (prune_sys[H.sys] & kPruned) != 0u && S.rin2 > 0.f;
         const int mode = img_mode(H, pair_geo(S));
         if (mode == kImgPlain)
-            energy_df_atom<LJ, COUL, kImgPlain>(i, H, S, skip_back, xs, xo, perm, ps, nbr, cap, e_atom, e_lo);
+            energy_df_atom<LJ, COUL, kImgPlain>(i, H, S, skip_back, xs, xo, perm, ps, nbr, cap, X, e_atom, e_lo);
         else if (mode == kImgCode)
-            energy_df_atom<LJ, COUL, kImgCode>(i, H, S, skip_back, xs, xo, perm, ps, nbr, cap, e_atom, e_lo);
+            energy_df_atom<LJ, COUL, kImgCode>(i, H, S, skip_back, xs, xo, perm, ps, nbr, cap, X, e_atom, e_lo);
         else
-            energy_df_atom<LJ, COUL, kImgFold>(i, H, S, skip_back, xs, xo, perm, ps, nbr, cap, e_atom, e_lo);
+            energy_df_atom<LJ, COUL, kImgFold>(i, H, S, skip_back, xs, xo, perm, ps, nbr, cap, X, e_atom, e_lo);
     }
 }
 
@@ -819,7 +823,7 @@ template <bool VJP>
 __global__ void k_excl(int N, const int* __restrict__ sid, const SysDev* __restrict__ sys,
                        const float4* __restrict__ xs, const float4* __restrict__ lam, ExclView X,
                        long long* __restrict__ ffix, float4* __restrict__ e_atom, float4* __restrict__ gx_s,
-                       float scale, unsigned* flags) {
+                       float scale, unsigned* flags, int write_energy) {
     pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -829,7 +833,8 @@ __global__ void k_excl(int N, const int* __restrict__ sid, const SysDev* __restr
     red_add(ffix + i, to_fix(fx, scale, flags + 1));
     red_add(ffix + (size_t)N + i, to_fix(fy, scale, flags + 1));
     red_add(ffix + 2 * (size_t)N + i, to_fix(fz, scale, flags + 1));
-    reinterpret_cast<float*>(e_atom + i)[2] = excl_energy_half(S.ke, xs[i].w, eex);
+    // (precise energies: the two-float pass has written the record)
+    if (write_energy) reinterpret_cast<float*>(e_atom + i)[2] = excl_energy_half(S.ke, xs[i].w, eex);
     if (VJP) {
         float4 g = gx_s[i];
         g.x += gx;
@@ -889,7 +894,7 @@ __global__ void __launch_bounds__(kRedThreads) k_epilogue(
                 const float4 l = e_lo[k];
                 v[0] += (double)e.x + (double)l.x;
                 v[1] += (double)e.y + (double)l.y;
-                v[2] += has_excl ? df_to_double(excl_energy_df(k, S, xs, X, xo, perm)) : (double)e.z;
+                v[2] += (double)e.z + (double)l.z;  // the two-float pass's exclusion energy
             } else {
                 v[0] += e.x;
                 v[1] += e.y;
@@ -945,16 +950,16 @@ static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp, bool energy, bo
         if (precise)
             launch_pdl(k_energy_df<LJ, COUL>, cdiv(N, pb), kPairThreads, 0, st, N, pb, h->cap, h->sid, h->sys, h->xs,
                        h->ps, h->nbr, h->nbr_cnt, h->nbr_out, h->e_atom, h->e_lo, (const unsigned*)h->flags,
-                       (const unsigned*)h->prune_sys, h->xq_in, (const int*)h->perm);
+                       (const unsigned*)h->prune_sys, h->xq_in, (const int*)h->perm, excl_view(h));
     }
     if (COUL == kCoulEwald && h->excl_w && !(defer_excl && !vjp)) {
         const ExclView X = excl_view(h);
         if (vjp)
             launch_pdl(k_excl<true>, cdiv(N, 128), 128, 0, st, N, h->sid, h->sys, h->xs, h->lam, X, h->ffix,
-                       h->e_atom, h->gx_s, h->fscale, h->flags);
+                       h->e_atom, h->gx_s, h->fscale, h->flags, 1);
         else
             launch_pdl(k_excl<false>, cdiv(N, 128), 128, 0, st, N, h->sid, h->sys, h->xs, (const float4*)nullptr, X,
-                       h->ffix, h->e_atom, (float4*)nullptr, h->fscale, h->flags);
+                       h->ffix, h->e_atom, (float4*)nullptr, h->fscale, h->flags, precise ? 0 : 1);
     }
 }
 
@@ -974,8 +979,9 @@ static void dispatch(nb_handle* h, int terms, cudaStream_t st, bool vjp) {
         }
         return;
     }
-    // precise energies: the force-only pair kernel, then the two-float energy pass
-    const bool pe = !vjp && (terms & kTermPrecise) != 0;
+    // precise energies: the force-only pair kernel, then the two-float energy pass (only
+    // where energies are asked for; other evaluations of a precise call run as usual)
+    const bool pe = !vjp && (terms & kTermPrecise) != 0 && (terms & kTermEnergy) != 0;
     const bool en = vjp || ((terms & kTermEnergy) != 0 && !pe);
     const bool df = (terms & kTermDeferExcl) != 0;
     if (lj && coul && rf) pair_launch<true, kCoulRF>(h, st, vjp, en, df, pe);

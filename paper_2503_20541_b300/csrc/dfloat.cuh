@@ -47,6 +47,13 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
     return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
 }
 
+// a + b with the low parts added in FP32 (Dekker's addition): error ~2^-46 of |a| + |b|
+// rather than of |a + b|; for sums whose operands do not cancel far below their size.
+__device__ __forceinline__ DF df_add_fast(DF a, DF b) {
+    const DF s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
 __device__ __forceinline__ DF df_add_f(DF a, float b) {
     const DF s = two_sum(a.hi, b);
     return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
@@ -83,6 +90,16 @@ __device__ __forceinline__ DF df_sqrt(DF a) {
     const DF p = two_prod(s, s);
     const float res = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p.hi), p.lo), a.lo);
     return fast_two_sum(s, __fdiv_rn(res, __fmul_rn(2.f, s)));
+}
+
+// 1/sqrt(a), a > 0: the hardware estimate y (relative error ~2^-23) and one Newton step
+// y (1 + e/2), e = 1 - a y^2 formed in two-float (y^2 as a two-product); the step's error is
+// ~e^2, ~1e-14.  No division or square root.
+__device__ __forceinline__ DF df_rsqrt(DF a) {
+    const float y = rsqrtf(a.hi);
+    const DF m = df_mul(a, two_prod(y, y));
+    const DF e = df_add_f(df_neg(m), 1.f);
+    return fast_two_sum(y, __fmul_rn(__fmul_rn(y, e.hi), 0.5f));
 }
 
 __device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }

@@ -607,7 +607,8 @@ __device__ __forceinline__ float excl_energy_half(float ke, float q, float eex) 
 // evaluation recomputes the energies -- not the forces, which the force-only pair kernel
 // gives -- in two-float arithmetic from the coordinate differences on: each difference is
 // exact (two_sum of the two image-shifted coordinates), r^2, r, 1/r, erfc and the LJ powers
-// carry 1e-14 - 1e-12 relative error, the per-atom sums are two-float and scaled once per atom by
+// carry 1e-14 - 1e-12 relative error (1/r by a Newton step on the hardware reciprocal square
+// root, no division), the per-atom sums are two-float and scaled once per atom by
 // ke q_i as an exact two-product, and the atom's record is split into hi (e_atom) and lo
 // (e_lo) parts that the epilogue adds in FP64.  The differences are taken from the caller's
 // positions (the slot-ordered frame positions may carry a rounding from the wrap into the
@@ -626,19 +627,23 @@ constexpr float kTwoInvSqrtPi = 1.12837916709551257f;  // 2 / sqrt(pi)
 // d erfc'(x.hi) (1 - x.hi d) with erfc'(x) = -(2/sqrt(pi)) exp(-x^2) and erfc'' = -2x erfc'
 // (|d| <= 2^-24 x.hi: the first-order term is ~1e-6 of erfc and needs FP32 accuracy, a few
 // ulp; the second ~2 x^2 d^2 relative, 4e-12 at x = 6; the third is below 1e-18).  Past the
-// table (erfc < 2.2e-17) the FP32 erfcf.
-__device__ __forceinline__ DF erfc_df(DF x) {
+// table (erfc < 2.2e-17) the FP32 erfcf.  tab: the table of erfc_df.cuh, or a copy of it
+// in shared memory (lanes of a warp read different intervals).
+constexpr int kErfcDfTab = kErfcDfIntervals * (kErfcDfDeg + 1);
+__device__ __forceinline__ DF erfc_df(DF x, const float2* tab) {
     const float xh = x.hi;
     if (!(xh < kErfcDfH * (float)kErfcDfIntervals)) return DF{erfcf(xh), 0.f};
     const int k = max(0, min((int)(xh * kErfcDfInvH), kErfcDfIntervals - 1));
     const float t = __fsub_rn(xh, __fmul_rn((float)k, kErfcDfH));
-    const float2* c = g_erfc_df[k];
-    float2 ck = __ldg(c + kErfcDfDeg);
+    const float2* c = tab + k * (kErfcDfDeg + 1);
+    float2 ck = c[kErfcDfDeg];
     DF p{ck.x, ck.y};
 #pragma unroll
     for (int m = kErfcDfDeg - 1; m >= 0; --m) {
-        ck = __ldg(c + m);
-        p = df_add(df_mul_f(p, t), DF{ck.x, ck.y});
+        ck = c[m];
+        // each step's two terms stay within a factor ~20 of the result (the series alternates
+        // at most that much on an interval of 0.25): Dekker's addition is enough
+        p = df_add_fast(df_mul_f(p, t), DF{ck.x, ck.y});
     }
     // exp(-x^2) with x^2 = sq.hi + sq.lo: the rounding of x^2 alone would be x^2 2^-24 of
     // the exponent (5e-7 relative at x = 3); expf, as __expf's error also grows with x^2
@@ -675,11 +680,12 @@ __device__ __forceinline__ DF r2_df(const DF d[3]) {
 // switch S(x), x = (r - r_s)/(r_c - r_s), above r_s.
 __device__ __forceinline__ DF lj_unit_df(float sig_i, float sig_j, DF r2, const SysDev& S) {
     const DF sig = df_scale(two_sum(sig_i, sig_j), 0.5f);
-    const DF s2 = df_div(df_mul(sig, sig), r2);
+    const DF rinv = df_rsqrt(r2);
+    const DF s2 = df_mul(df_mul(sig, sig), df_mul(rinv, rinv));
     const DF s6 = df_mul(df_mul(s2, s2), s2);
     DF u = df_scale(df_add(df_mul(s6, s6), df_neg(s6)), 4.f);
     if (S.has_switch) {
-        const DF r = df_sqrt(r2);
+        const DF r = df_mul(r2, rinv);
         const DF x = df_mul(df_add_f(r, -S.rs), DF{S.inv_sw, S.inv_sw_lo});
         if (x.hi > 0.f) {
             // S = 1 + x^3 (-10 + x (15 - 6 x))
@@ -695,10 +701,10 @@ __device__ __forceinline__ DF lj_unit_df(float sig_i, float sig_j, DF r2, const 
 // Ewald direct-space (EWALD) or reaction-field energy of one pair per unit ke q_i, in
 // two-float: q_j erfc(alpha r)/r, or q_j (1/r + k r^2 - c) of Eq. RFA.
 template <int COUL>
-__device__ __forceinline__ DF coul_unit_df(float qj, DF r2, const SysDev& S) {
-    const DF r = df_sqrt(r2);
-    const DF rinv = df_div(DF{1.f, 0.f}, r);
-    if (COUL == kCoulEwald) return df_mul_f(df_mul(erfc_df(df_mul_f(r, S.alpha)), rinv), qj);
+__device__ __forceinline__ DF coul_unit_df(float qj, DF r2, const SysDev& S, const float2* tab) {
+    const DF rinv = df_rsqrt(r2);
+    const DF r = df_mul(r2, rinv);
+    if (COUL == kCoulEwald) return df_mul_f(df_mul(erfc_df(df_mul_f(r, S.alpha), tab), rinv), qj);
     DF u = df_add(rinv, df_mul(DF{S.krf, S.krf_lo}, r2));
     u = df_add(u, DF{-S.crf, -S.crf_lo});
     return df_mul_f(u, qj);
@@ -708,7 +714,8 @@ __device__ __forceinline__ DF coul_unit_df(float qj, DF r2, const SysDev& S) {
 // (erf = 1 - erfc), each excluded pair's difference from the caller's positions (xo, caller
 // order; perm: slot -> caller index) in the minimum image that excl_terms takes.
 __device__ __forceinline__ DF excl_energy_df(int i, const SysDev& S, const float4* __restrict__ xs, const ExclView& X,
-                                             const float4* __restrict__ xo, const int* __restrict__ perm) {
+                                             const float4* __restrict__ xo, const int* __restrict__ perm,
+                                             const float2* tab) {
     const float4 xr = xs[i];
     const float4 oi = xo[perm[i]];
     const int ne = X.count(i);
@@ -725,9 +732,9 @@ __device__ __forceinline__ DF excl_energy_df(int i, const SysDev& S, const float
         DF d[3];
         caller_diff_df(oi, xo[perm[j]], d32, S, d);
         const DF r2 = r2_df(d);
-        const DF r = df_sqrt(r2);
-        const DF erf = df_add_f(df_neg(erfc_df(df_mul_f(r, S.alpha))), 1.f);
-        sum = df_add(sum, df_mul_f(df_div(erf, r), -xj.w));  // the charges: xs .w = xq .w
+        const DF rinv = df_rsqrt(r2);
+        const DF erf = df_add_f(df_neg(erfc_df(df_mul_f(df_mul(r2, rinv), S.alpha), tab)), 1.f);
+        sum = df_add(sum, df_mul_f(df_mul(erf, rinv), -xj.w));  // the charges: xs .w = xq .w
     }
     return df_scale(df_mul(two_prod(S.ke, xr.w), sum), 0.5f);
 }
@@ -742,7 +749,8 @@ __device__ __forceinline__ void energy_df_atom(int i, const AtomHdr& H, const Sy
                                                const float4* __restrict__ xs, const float4* __restrict__ xo,
                                                const int* __restrict__ perm, const float2* __restrict__ ps,
                                                const unsigned* __restrict__ nbr, int cap, const ExclView& X,
-                                               float4* __restrict__ e_atom, float4* __restrict__ e_lo) {
+                                               const float2* tab, float4* __restrict__ e_atom,
+                                               float4* __restrict__ e_lo) {
     const int lane = threadIdx.x & 31;
     const PairGeo G = pair_geo(S);
     const float4 xr = H.xr;
@@ -772,7 +780,7 @@ __device__ __forceinline__ void energy_df_atom(int i, const AtomHdr& H, const Sy
             const float2 pj = ps[j];
             if (pj.y != 0.f) elj = df_add(elj, df_mul(two_prod(pi.y, pj.y), lj_unit_df(pi.x, pj.x, r2, S)));
         }
-        if (do_coul) eq = df_add(eq, coul_unit_df<COUL>(cj.w, r2, S));
+        if (do_coul) eq = df_add(eq, coul_unit_df<COUL>(cj.w, r2, S, tab));
     }
     elj = warp_sum_df(elj);
     eq = warp_sum_df(eq);
@@ -781,7 +789,7 @@ __device__ __forceinline__ void energy_df_atom(int i, const AtomHdr& H, const Sy
         // the exclusion correction's energy record (Ewald systems with excluded partners)
         DF ex{0.f, 0.f};
         if (COUL == kCoulEwald && X.count(i) > 0 && S.alpha > 0.f && S.ke != 0.f)
-            ex = excl_energy_df(i, S, xs, X, xo, perm);
+            ex = excl_energy_df(i, S, xs, X, xo, perm, tab);
         e_atom[i] = make_float4(0.5f * elj.hi, 0.5f * eq.hi, ex.hi, 0.f);
         e_lo[i] = make_float4(0.5f * elj.lo, 0.5f * eq.lo, ex.lo, 0.f);
     }
@@ -796,6 +804,10 @@ __global__ void __launch_bounds__(kPairThreads) k_energy_df(
     const int* __restrict__ cnt, const int* __restrict__ cnt_out, float4* __restrict__ e_atom,
     float4* __restrict__ e_lo, const unsigned* __restrict__ flags, const unsigned* __restrict__ prune_sys,
     const float4* __restrict__ xo, const int* __restrict__ perm, ExclView X) {
+    // the erfc table in shared memory: the lanes of a warp read ~a dozen different intervals
+    __shared__ float2 tab[kErfcDfTab];
+    for (int k = threadIdx.x; k < kErfcDfTab; k += blockDim.x) tab[k] = (&g_erfc_df[0][0])[k];
+    __syncthreads();
     pdl_wait();
     const AtomRange R = block_atoms(N, per_block, kPairWarps);
     const bool fresh = flags[NB_FLAG_FRESH] != 0u;
@@ -806,11 +818,11 @@ __global__ void __launch_bounds__(kPairThreads) k_energy_df(
         const bool skip_back = !fresh && prune_sys && (prune_sys[H.sys] & kPruned) != 0u && S.rin2 > 0.f;
         const int mode = img_mode(H, pair_geo(S));
         if (mode == kImgPlain)
-            energy_df_atom<LJ, COUL, kImgPlain>(i, H, S, skip_back, xs, xo, perm, ps, nbr, cap, X, e_atom, e_lo);
+            energy_df_atom<LJ, COUL, kImgPlain>(i, H, S, skip_back, xs, xo, perm, ps, nbr, cap, X, tab, e_atom, e_lo);
         else if (mode == kImgCode)
-            energy_df_atom<LJ, COUL, kImgCode>(i, H, S, skip_back, xs, xo, perm, ps, nbr, cap, X, e_atom, e_lo);
+            energy_df_atom<LJ, COUL, kImgCode>(i, H, S, skip_back, xs, xo, perm, ps, nbr, cap, X, tab, e_atom, e_lo);
         else
-            energy_df_atom<LJ, COUL, kImgFold>(i, H, S, skip_back, xs, xo, perm, ps, nbr, cap, X, e_atom, e_lo);
+            energy_df_atom<LJ, COUL, kImgFold>(i, H, S, skip_back, xs, xo, perm, ps, nbr, cap, X, tab, e_atom, e_lo);
     }
 }
 
@@ -1026,7 +1038,7 @@ __global__ void k_erfc_df_eval(int n, const float* __restrict__ xh, const float*
                                float* __restrict__ oh, float* __restrict__ ol) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const DF e = erfc_df(DF{xh[i], xl[i]});
+    const DF e = erfc_df(DF{xh[i], xl[i]}, &g_erfc_df[0][0]);
     oh[i] = e.hi;
     ol[i] = e.lo;
 }

@@ -6,7 +6,8 @@ evaluation recomputes the real-space and exclusion energies in two-float arithme
 every case that the FP32 energies miss is held to the flat 1e-6 relative bar, per energy
 component: the reaction-field water box of 1,800 atoms, the smallest water and LJ systems
 of the 256-system batch in one batched handle, the orthorhombic water slab, the 24,000-atom
-box, and kept and pruned lists after the atoms have moved.  The forces of a precise call
+box, kept and pruned lists after the atoms have moved, and an open water cluster without
+periodic images.  The forces of a precise call
 are bitwise those of the energy-free call, and the two-float erfc itself is checked on the
 device against the FP64 erfc."""
 import numpy as np
@@ -166,3 +167,17 @@ def test_moved_atoms_kept_and_pruned_lists_precise(prune):
             assert abs(e[0, 4] - Ep) <= E_TOL * abs(Ep)
             assert rel_rms(f, fo + Fp) <= F_TOL
         assert h.rebuild_count() == 1
+
+
+def test_open_water_cluster_precise():
+    """A water cluster without periodic images (no PME): LJ, Ewald direct and exclusion
+    energies at 1e-6, the differences taken as plain differences of the caller's positions."""
+    s = wl.water_box(n_side=6, L=18.63, seed=4, pme_grid=24)
+    s.periodic = False
+    s.pme_grid = None
+    terms = nbcore.NB_TERM_LJ | nbcore.NB_TERM_COUL
+    with nbcore.Handle([s]) as h:
+        f, e = _eval(h, dev_xq(s), s.n, terms=terms)
+    eo, fo = oracle_real_space(s)
+    _check_energies(e[0], eo, "open cluster")
+    assert rel_rms(f, fo) <= F_TOL

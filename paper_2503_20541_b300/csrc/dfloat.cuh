@@ -92,9 +92,10 @@ __device__ __forceinline__ DF df_sqrt(DF a) {
     return fast_two_sum(s, __fdiv_rn(res, __fmul_rn(2.f, s)));
 }
 
-// 1/sqrt(a), a > 0: the hardware estimate y (relative error ~2^-23) and one Newton step
-// y (1 + e/2), e = 1 - a y^2 formed in two-float (y^2 as a two-product); the step's error is
-// ~e^2, ~1e-14.  No division or square root.
+// 1/sqrt(a), a > 0: the hardware estimate y (within ~2 ulp) and one Newton step y (1 + e/2),
+// e = 1 - a y^2 formed in two-float (y^2 as a two-product); the step leaves 1.5 e0^2 of an
+// estimate off by e0 (below 2.5e-13 at 2 ulp, ~2e-14 when correctly rounded).  No division
+// or square root.
 __device__ __forceinline__ DF df_rsqrt(DF a) {
     const float y = rsqrtf(a.hi);
     const DF m = df_mul(a, two_prod(y, y));

@@ -366,6 +366,262 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_pair(
     }
 }
 
+// ---- Two atoms per warp (LJ-only kernels) ---------------------------------------------
+// With few pairs per atom (an LJ fluid: ~54 inside r_c, 1.7 rounds of 32) a warp per atom
+// spends much of its time on the per-atom part (header, system constants, reduction).
+// k_pair2 gives each half-warp (group g = lane / 16) one atom and lets each lane stand for
+// two lanes of the warp-per-atom kernel: lane l' of a group does, for every round of 32
+// entries, what lanes l' (set A) and l' + 16 (set B) of k_pair do, in the same order and
+// with the same operations; the back part's queue receives the same entries in the same
+// order; and the reduction's first level, lane l + lane l ^ 16 in k_pair, is the lane's own
+// A + B (addition commutes), the other levels (8, 4, 2, 1) pairing the same lanes.  So
+// every atom's forces and energies are bitwise those of k_pair, whichever kernel a handle
+// runs (a batched handle with charged systems runs k_pair for its LJ systems too).
+
+// Per-atom context of a group: as AtomHdr, with the first two rounds' entries of both sets
+// (row positions l', 16 + l', 32 + l', 48 + l').
+struct AtomHdr2 {
+    float4 xr;
+    float2 pi;
+    int nin, nout;
+    bool wrap;
+    int sys;
+    unsigned a0, b0, a1, b1;
+};
+
+__device__ __forceinline__ AtomHdr2 load_hdr2(int i, bool valid, const int* __restrict__ sid,
+                                              const float4* __restrict__ xs, const float2* __restrict__ ps,
+                                              const unsigned* __restrict__ nbr, const int* __restrict__ cnt,
+                                              const int* __restrict__ cnt_out, int cap) {
+    const int l = threadIdx.x & 15;
+    AtomHdr2 H;
+    H.xr = xs[i];
+    H.pi = ps[i];
+    H.nin = valid ? cnt[i] : 0;
+    const int o = valid ? cnt_out[i] : 0;
+    H.nout = o & kOutCountMask;
+    H.wrap = (o & kOutWrapBit) != 0;
+    H.sys = sid[i];
+    const unsigned* row = nbr + (size_t)i * cap;
+    H.a0 = l < H.nin ? row[l] : 0u;
+    H.b0 = 16 + l < H.nin ? row[16 + l] : 0u;
+    H.a1 = 32 + l < H.nin ? row[32 + l] : 0u;
+    H.b1 = 48 + l < H.nin ? row[48 + l] : 0u;
+    return H;
+}
+
+// The front of the group's row, two rounds of entries ahead and the partners' positions one
+// round ahead; rounds past the group's own count are skipped (the other group may have more).
+template <int IMG, class HeavyA, class HeavyB>
+__device__ __forceinline__ void walk_front2(const AtomHdr2& H, const PairGeo& G, const unsigned* __restrict__ row,
+                                            int nin_max, bool fresh, float rc2, const float4* __restrict__ xs,
+                                            HeavyA& heavyA, HeavyB& heavyB) {
+    const int l = threadIdx.x & 15;
+    const int nin = H.nin;
+    unsigned pa0 = H.a0, pb0 = H.b0, pa1 = H.a1, pb1 = H.b1;
+    float4 ga = xs[l < nin ? (int)(pa0 & kEntrySlotMask) : 0];
+    float4 gb = xs[16 + l < nin ? (int)(pb0 & kEntrySlotMask) : 0];
+    for (int e0 = 0; e0 < nin_max; e0 += 32) {
+        const unsigned ea = pa0, eb = pb0;
+        const float4 ca = ga, cb = gb;
+        pa0 = pa1;
+        pb0 = pb1;
+        pa1 = e0 + 64 + l < nin ? row[e0 + 64 + l] : 0u;
+        pb1 = e0 + 80 + l < nin ? row[e0 + 80 + l] : 0u;
+        if (e0 + 32 + l < nin) ga = xs[pa0 & kEntrySlotMask];
+        if (e0 + 48 + l < nin) gb = xs[pb0 & kEntrySlotMask];
+        if (e0 < nin) {
+            const bool ina = e0 + l < nin, inb = e0 + 16 + l < nin;
+            float dx, dy, dz;
+            entry_diff<IMG>(H.xr, ca, ea >> kEntrySlotBits, G, dx, dy, dz);
+            bool on = ina && (fresh || pair_r2(dx, dy, dz) < rc2);
+            heavyA(make_float4(dx, dy, dz, ca.w), ina ? (int)(ea & kEntrySlotMask) : 0, on);
+            entry_diff<IMG>(H.xr, cb, eb >> kEntrySlotBits, G, dx, dy, dz);
+            on = inb && (fresh || pair_r2(dx, dy, dz) < rc2);
+            heavyB(make_float4(dx, dy, dz, cb.w), inb ? (int)(eb & kEntrySlotMask) : 0, on);
+        }
+    }
+}
+
+// The back of the group's row (kept lists that are not pruned): the entries now inside r_c
+// are queued in the order k_pair queues them (set A's half of each round of 32, then set
+// B's) and evaluated 32 at a time, set A taking queue positions head + l' and set B
+// head + 16 + l'.  Each group has its own queue; ballots and barriers are warp-wide.
+template <int IMG, class HeavyA, class HeavyB>
+__device__ __forceinline__ void walk_back2(const AtomHdr2& H, const PairGeo& G, const unsigned* __restrict__ brow,
+                                           int nout, int nout_max, float rc2, const float4* __restrict__ xs,
+                                           float4* qd, int* qj, HeavyA& heavyA, HeavyB& heavyB) {
+    const int lane = threadIdx.x & 31, l = lane & 15, sh = lane & 16;
+    const unsigned lta = (1u << l) - 1u, ltb = (1u << (l + 16)) - 1u;
+    int head = 0, nq = 0;
+    unsigned ba0 = l < nout ? brow[l] : 0u, bb0 = 16 + l < nout ? brow[16 + l] : 0u;
+    unsigned ba1 = 32 + l < nout ? brow[32 + l] : 0u, bb1 = 48 + l < nout ? brow[48 + l] : 0u;
+    float4 ga = xs[ba0 & kEntrySlotMask], gb = xs[bb0 & kEntrySlotMask];
+    for (int e0 = 0; e0 < nout_max; e0 += 32) {
+        const unsigned ea = ba0, eb = bb0;
+        const float4 ca = ga, cb = gb;
+        ba0 = ba1;
+        bb0 = bb1;
+        ba1 = e0 + 64 + l < nout ? brow[e0 + 64 + l] : 0u;
+        bb1 = e0 + 80 + l < nout ? brow[e0 + 80 + l] : 0u;
+        if (e0 + 32 + l < nout) ga = xs[ba0 & kEntrySlotMask];
+        if (e0 + 48 + l < nout) gb = xs[bb0 & kEntrySlotMask];
+        const bool ina = e0 + l < nout, inb = e0 + 16 + l < nout;
+        float ax, ay, az, bx, by, bz;
+        entry_diff<IMG>(H.xr, ca, ea >> kEntrySlotBits, G, ax, ay, az);
+        entry_diff<IMG>(H.xr, cb, eb >> kEntrySlotBits, G, bx, by, bz);
+        const bool acca = ina && pair_r2(ax, ay, az) < rc2;
+        const bool accb = inb && pair_r2(bx, by, bz) < rc2;
+        const unsigned wa = __ballot_sync(0xffffffffu, acca), wb = __ballot_sync(0xffffffffu, accb);
+        // the group's round as k_pair's warp sees it: set A in bits 0-15, set B in 16-31
+        const unsigned bits = ((wa >> sh) & 0xffffu) | (((wb >> sh) & 0xffffu) << 16);
+        if (__any_sync(0xffffffffu, bits != 0u)) {
+            const int pa = (head + nq + __popc(bits & lta)) & (kQueue - 1);
+            const int pb = (head + nq + __popc(bits & ltb)) & (kQueue - 1);
+            sts_q_if(qd + pa, qj + pa, make_float4(ax, ay, az, ca.w), ina ? (int)(ea & kEntrySlotMask) : 0, acca);
+            sts_q_if(qd + pb, qj + pb, make_float4(bx, by, bz, cb.w), inb ? (int)(eb & kEntrySlotMask) : 0, accb);
+            nq += __popc(bits);
+            const bool flush = nq >= 32;
+            if (__any_sync(0xffffffffu, flush)) {
+                __syncwarp();
+                float4 qa = make_float4(0.f, 0.f, 0.f, 0.f), qb = qa;
+                int ja = 0, jb = 0;
+                if (flush) {
+                    const int p0 = (head + l) & (kQueue - 1), p1 = (head + 16 + l) & (kQueue - 1);
+                    qa = qd[p0];
+                    ja = qj[p0];
+                    qb = qd[p1];
+                    jb = qj[p1];
+                }
+                __syncwarp();
+                if (flush) {
+                    heavyA(qa, ja, true);
+                    heavyB(qb, jb, true);
+                    head = (head + 32) & (kQueue - 1);
+                    nq -= 32;
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (__any_sync(0xffffffffu, nq > 0)) {
+        const bool ona = l < nq, onb = 16 + l < nq;
+        const int p0 = (head + l) & (kQueue - 1), p1 = (head + 16 + l) & (kQueue - 1);
+        // positions past the queue's end hold stale or never written entries: zeros instead
+        const float4 qa = ona ? qd[p0] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 qb = onb ? qd[p1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int ja = ona ? qj[p0] : 0, jb = onb ? qj[p1] : 0;
+        __syncwarp();
+        if (nq > 0) {
+            heavyA(qa, ja, ona);
+            heavyB(qb, jb, onb);
+        }
+    }
+    __syncwarp();
+}
+
+// Sums of v[0..NV) over the 16 lanes of a group, transposed as warp_sum_transposed does it
+// from its second level on (xor 8, 4, ...): group lane (16 / NV) k ends with the sum of
+// value k.  The caller has already formed the first level (its sets A + B).
+template <int NV>
+__device__ __forceinline__ float group_sum_transposed(float (&v)[NV]) {
+    const int lane = threadIdx.x & 31;
+    int n = NV, o = 8;
+#pragma unroll
+    for (int lev = 0; (1 << lev) < NV; ++lev) {
+        n >>= 1;
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < NV / 2; ++k) {
+            if (k < n) {
+                const float keep = upper ? v[n + k] : v[k];
+                const float give = upper ? v[k] : v[n + k];
+                v[k] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+            }
+        }
+        o >>= 1;
+    }
+    float r = v[0];
+#pragma unroll
+    for (; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
+}
+
+// Forces and (EN) half LJ energy of the group's atom i (LJ only; valid: the group has an
+// atom).  Sets A and B accumulate as lanes l' and l' + 16 of k_pair.
+template <bool LJ, bool EN, int IMG>
+__device__ __forceinline__ void pair_atom2(int N, int i, bool valid, const AtomHdr2& H, const PairK& K,
+                                           const PairGeo& G, bool fresh, bool skip_back, int nin_max, int nout_max,
+                                           const float4* __restrict__ xs, const float2* __restrict__ ps,
+                                           const unsigned* __restrict__ nbr, int cap, float4* qd, int* qj,
+                                           long long* __restrict__ ffix, float4* __restrict__ e_atom, float scale,
+                                           unsigned* flags) {
+    const int l = threadIdx.x & 15;
+    const float2 pi = H.pi;
+    const bool do_lj = pi.y != 0.f;
+    float fxa = 0.f, fya = 0.f, fza = 0.f, ea = 0.f, da = 0.f;
+    float fxb = 0.f, fyb = 0.f, fzb = 0.f, eb = 0.f, db = 0.f;
+    auto heavy_a = [&](const float4& q, int j, bool on) {
+        pair_heavy<LJ, kCoulNone, EN>(q, j, on, pi, do_lj, K, ps, 0.f, 0.f, 0.f, 0.f, fxa, fya, fza, ea, da);
+    };
+    auto heavy_b = [&](const float4& q, int j, bool on) {
+        pair_heavy<LJ, kCoulNone, EN>(q, j, on, pi, do_lj, K, ps, 0.f, 0.f, 0.f, 0.f, fxb, fyb, fzb, eb, db);
+    };
+    const unsigned* row = nbr + (size_t)i * cap;
+    walk_front2<IMG>(H, G, row, nin_max, fresh, K.rc2, xs, heavy_a, heavy_b);
+    const int nout = (!fresh && !skip_back) ? H.nout : 0;
+    walk_back2<IMG>(H, G, row + (cap - nout), nout, nout_max, K.rc2, xs, qd, qj, heavy_a, heavy_b);
+    // lane 4k of the group holds the sum of value k: fx, fy, fz, elj
+    float v[4] = {fxa + fxb, fya + fyb, fza + fzb, EN ? ea + eb : 0.f};
+    const float sum = group_sum_transposed<4>(v);
+    const int k = l >> 2;
+    if (!valid || (l & 3) != 0) return;
+    if (k < 3) red_add(ffix + (size_t)k * N + i, to_fix(sum, scale, flags + 1));
+    else if (EN) e_atom[i] = make_float4(0.5f * sum, 0.f, 0.f, 0.f);  // no exclusion pass
+}
+
+// LJ-only pair kernel, two atoms per warp (one per group), the atom ranges of k_pair's
+// blocks.  Results bitwise those of k_pair<LJ, kCoulNone, EN>.
+template <bool LJ, bool EN>
+__global__ void __launch_bounds__(kPairThreads, 4) k_pair2(
+    int N, int per_block, int cap, const int* __restrict__ sid, const SysDev* __restrict__ sys,
+    const float4* __restrict__ xs, const float2* __restrict__ ps, const unsigned* __restrict__ nbr,
+    const int* __restrict__ cnt, const int* __restrict__ cnt_out, long long* __restrict__ ffix,
+    float4* __restrict__ e_atom, float scale, unsigned* flags, const unsigned* __restrict__ prune_sys) {
+    pdl_wait();
+    __shared__ float4 qd_all[kPairWarps][2][kQueue];
+    __shared__ int qj_all[kPairWarps][2][kQueue];
+    const int w = threadIdx.x >> 5, grp = (threadIdx.x >> 4) & 1;
+    const int b0 = blockIdx.x * per_block;
+    const int i1 = min(N, b0 + per_block);
+    const bool fresh = flags[NB_FLAG_FRESH] != 0u;
+    for (int base = b0 + 2 * w; base < i1; base += 2 * kPairWarps) {
+        const int i = base + grp;
+        const bool valid = i < i1;
+        const AtomHdr2 H = load_hdr2(valid ? i : base, valid, sid, xs, ps, nbr, cnt, cnt_out, cap);
+        const SysDev& S = sys[H.sys];
+        const PairK K = pair_k(S);
+        const PairGeo G = pair_geo(S);
+        const bool pruned = !fresh && prune_sys && (prune_sys[H.sys] & kPruned) != 0u;
+        const bool skip_back = pruned && S.rin2 > 0.f;
+        const int nout = (!fresh && !skip_back) ? H.nout : 0;
+        const int nin_max = max(H.nin, __shfl_xor_sync(0xffffffffu, H.nin, 16));
+        const int nout_max = max(nout, __shfl_xor_sync(0xffffffffu, nout, 16));
+        // the more general image mode of the two atoms (on a row without image codes, or an
+        // axis that is not folded, the general forms reduce to the plain difference)
+        int mode = (G.fold[0] || G.fold[1] || G.fold[2]) ? kImgFold : (H.wrap ? kImgCode : kImgPlain);
+        mode = max(mode, __shfl_xor_sync(0xffffffffu, mode, 16));
+        float4* qd = qd_all[w][grp];
+        int* qj = qj_all[w][grp];
+#define NB_PAIR2_ARGS N, i, valid, H, K, G, fresh, skip_back, nin_max, nout_max, xs, ps, nbr, cap, qd, qj, ffix, e_atom, \
+                      scale, flags
+        if (mode == kImgPlain) pair_atom2<LJ, EN, kImgPlain>(NB_PAIR2_ARGS);
+        else if (mode == kImgCode) pair_atom2<LJ, EN, kImgCode>(NB_PAIR2_ARGS);
+        else pair_atom2<LJ, EN, kImgFold>(NB_PAIR2_ARGS);
+#undef NB_PAIR2_ARGS
+    }
+}
+
 // Force VJP.  For each directed pair (i, j) with u = lam_i - lam_j and du = d.u:
 //   gx_i += f u + (f'/r) du d           (J (lam_i - lam_j), J = f I + (f'/r) d d^T)
 //   gq_i += ke q_j (f / qq) du,  gsig_i += 1/2 (df/dsigma_ij) du,  ge_i += sqrt(eps_j) (f/eps) du
@@ -956,9 +1212,14 @@ static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp, bool energy, bo
                    (const unsigned*)h->prune_sys);
     } else {
         const int pb = pair_atoms_per_block(h, kPairWarps, true);
-        launch_pdl(energy ? k_pair<LJ, COUL, true> : k_pair<LJ, COUL, false>, cdiv(N, pb), kPairThreads, 0, st, N,
-                   pb, h->cap, h->sid, h->sys, h->xs, h->ps, h->nbr, h->nbr_cnt, h->nbr_out, h->ffix, h->e_atom,
-                   h->fscale, h->flags, (const unsigned*)h->prune_sys);
+        if (COUL == kCoulNone)  // LJ only: two atoms per warp, bitwise the same results
+            launch_pdl(energy ? k_pair2<LJ, true> : k_pair2<LJ, false>, cdiv(N, pb), kPairThreads, 0, st, N, pb,
+                       h->cap, h->sid, h->sys, h->xs, h->ps, h->nbr, h->nbr_cnt, h->nbr_out, h->ffix, h->e_atom,
+                       h->fscale, h->flags, (const unsigned*)h->prune_sys);
+        else
+            launch_pdl(energy ? k_pair<LJ, COUL, true> : k_pair<LJ, COUL, false>, cdiv(N, pb), kPairThreads, 0, st,
+                       N, pb, h->cap, h->sid, h->sys, h->xs, h->ps, h->nbr, h->nbr_cnt, h->nbr_out, h->ffix, h->e_atom,
+                       h->fscale, h->flags, (const unsigned*)h->prune_sys);
         if (precise)
             launch_pdl(k_energy_df<LJ, COUL>, cdiv(N, pb), kPairThreads, 0, st, N, pb, h->cap, h->sid, h->sys, h->xs,
                        h->ps, h->nbr, h->nbr_cnt, h->nbr_out, h->e_atom, h->e_lo, (const unsigned*)h->flags,

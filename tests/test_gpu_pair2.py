@@ -1,0 +1,76 @@
+"""The LJ-only pair kernel with two atoms per warp (k_pair2) against the warp-per-atom
+kernel: an LJ system evaluated alone runs k_pair2; the same system in a handle that also
+holds a charged water box runs k_pair (the handle's kernels then carry electrostatics,
+skipped for the uncharged system).  Forces and energies must agree bit for bit: on a just
+built list, on the kept list after the atoms have moved (the back parts walked through the
+queue), with and without energies, with the LJ switch, in a box small enough for per-pair
+minimum images, and for several LJ systems of different sizes in one handle."""
+import numpy as np
+import pytest
+
+from paper_2503_20541_b300 import nbcore, workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _run(systems, xs_list, energies):
+    xq0 = [nbcore.pack_xq(s.x, s.q) for s in systems]
+    n = sum(s.n for s in systems)
+    f = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    e = torch.empty((len(systems), 6), dtype=torch.float64, device="cuda")
+    out = []
+    with nbcore.Handle(systems) as h:
+        for xs in xs_list:
+            parts = [nbcore.pack_xq(x, s.q) if x is not None else q for x, s, q in zip(xs, systems, xq0)]
+            xq = torch.from_numpy(np.concatenate(parts)).cuda()
+            h.nonbonded_forces(xq, f, e if energies else None)
+            h.check()
+            out.append((f.cpu().numpy().copy(), e.cpu().numpy().copy() if energies else None))
+        rebuilds = h.rebuild_count()
+    return out, rebuilds
+
+
+def _moves(s, seed, amps):
+    rng = np.random.default_rng(seed)
+    return [(s.x.astype(np.float64) + rng.uniform(-a, a, s.x.shape)).astype(np.float32) for a in amps]
+
+
+def _water():
+    return wl.water_box(n_side=8, L=24.84, seed=9, pme_grid=24)
+
+
+@pytest.mark.parametrize("case", ["random", "switch", "small_box"])
+@pytest.mark.parametrize("energies", [True, False])
+def test_two_atoms_per_warp_bitwise_equal(case, energies):
+    if case == "random":
+        s = wl.lj_random(3000, seed=31)
+    elif case == "switch":
+        s = wl.lj_random(2500, seed=32, n_types=2)
+        s.r_switch = 2.2
+    else:
+        s = wl.lj_fcc(n_cells=4, seed=33)  # 2 cells of r_nl per axis: per-pair minimum images
+    amps = [0.0, 0.03, 0.06]  # below r_skin/2 = 0.15 per atom: the list is kept
+    xs = _moves(s, 7, amps)
+    w = _water()
+    alone, rb1 = _run([s], [[x] for x in xs], energies)
+    mixed, rb2 = _run([s, w], [[x, None] for x in xs], energies)
+    assert rb1 == 1 and rb2 == 1
+    for k, ((fa, ea), (fm, em)) in enumerate(zip(alone, mixed)):
+        assert np.array_equal(fa, fm[:s.n]), (case, k, np.abs(fa - fm[:s.n]).max())
+        if energies:
+            assert np.array_equal(ea[0], em[0]), (case, k, ea[0], em[0])
+
+
+def test_several_lj_systems_in_one_handle():
+    systems = [wl.lj_random(n, seed=40 + n % 97) for n in (700, 2100, 1300)]
+    amps = [0.0, 0.05]
+    moves = [_moves(s, 11 + k, amps) for k, s in enumerate(systems)]
+    xs_list = [[moves[k][a] for k in range(3)] for a in range(len(amps))]
+    batched, _ = _run(systems, xs_list, True)
+    offs = np.cumsum([0] + [s.n for s in systems])
+    for k, s in enumerate(systems):
+        alone, _ = _run([s, _water()], [[moves[k][a], None] for a in range(len(amps))], True)
+        for a in range(len(amps)):
+            assert np.array_equal(batched[a][0][offs[k]:offs[k + 1]], alone[a][0][:s.n]), (k, a)
+            assert np.array_equal(batched[a][1][k], alone[a][1][0]), (k, a)

@@ -4,7 +4,9 @@ holds a charged water box runs k_pair (the handle's kernels then carry electrost
 skipped for the uncharged system).  Forces and energies must agree bit for bit: on a just
 built list, on the kept list after the atoms have moved (the back parts walked through the
 queue), with and without energies, with the LJ switch, in a box small enough for per-pair
-minimum images, and for several LJ systems of different sizes in one handle."""
+minimum images, and for several LJ systems of different sizes in one handle.  The kernel
+runs on handles large enough for blocks of 16 atoms (9,472 atoms on 148 SMs), so the
+LJ-only handles here hold 10,000 atoms or more (the small boxes as a batch of 40)."""
 import numpy as np
 import pytest
 
@@ -40,16 +42,14 @@ def _water():
     return wl.water_box(n_side=8, L=24.84, seed=9, pme_grid=24)
 
 
-@pytest.mark.parametrize("case", ["random", "switch", "small_box"])
+@pytest.mark.parametrize("case", ["random", "switch"])
 @pytest.mark.parametrize("energies", [True, False])
 def test_two_atoms_per_warp_bitwise_equal(case, energies):
     if case == "random":
-        s = wl.lj_random(3000, seed=31)
-    elif case == "switch":
-        s = wl.lj_random(2500, seed=32, n_types=2)
-        s.r_switch = 2.2
+        s = wl.lj_random(12000, seed=31)
     else:
-        s = wl.lj_fcc(n_cells=4, seed=33)  # 2 cells of r_nl per axis: per-pair minimum images
+        s = wl.lj_random(10000, seed=32, n_types=2)
+        s.r_switch = 2.2
     amps = [0.0, 0.03, 0.06]  # below r_skin/2 = 0.15 per atom: the list is kept
     xs = _moves(s, 7, amps)
     w = _water()
@@ -62,14 +62,18 @@ def test_two_atoms_per_warp_bitwise_equal(case, energies):
             assert np.array_equal(ea[0], em[0]), (case, k, ea[0], em[0])
 
 
-def test_several_lj_systems_in_one_handle():
-    systems = [wl.lj_random(n, seed=40 + n % 97) for n in (700, 2100, 1300)]
+@pytest.mark.parametrize("kind", ["sizes", "small_boxes"])
+def test_several_lj_systems_in_one_handle(kind):
+    if kind == "sizes":
+        systems = [wl.lj_random(n, seed=40 + n % 97) for n in (3100, 4700, 2900)]
+    else:  # 40 boxes of 256 atoms, 2 cells of r_nl per axis: per-pair minimum images
+        systems = [wl.lj_fcc(n_cells=4, seed=33 + k) for k in range(40)]
     amps = [0.0, 0.05]
     moves = [_moves(s, 11 + k, amps) for k, s in enumerate(systems)]
-    xs_list = [[moves[k][a] for k in range(3)] for a in range(len(amps))]
+    xs_list = [[moves[k][a] for k in range(len(systems))] for a in range(len(amps))]
     batched, _ = _run(systems, xs_list, True)
     offs = np.cumsum([0] + [s.n for s in systems])
-    for k, s in enumerate(systems):
+    for k, s in enumerate(systems[:3]):
         alone, _ = _run([s, _water()], [[moves[k][a], None] for a in range(len(amps))], True)
         for a in range(len(amps)):
             assert np.array_equal(batched[a][0][offs[k]:offs[k + 1]], alone[a][0][:s.n]), (k, a)

@@ -783,6 +783,85 @@ __global__ void __launch_bounds__(kVjpThreads, COUL ? 2 : 4) k_vjp(
     }
 }
 
+// Force VJP of an LJ-only handle, two atoms per warp as in k_pair2: lane l' of group g does
+// what lanes l' and l' + 16 of k_vjp do for the group's atom (sets A and B), and the
+// reduction's first level is A + B, so the results are bitwise those of k_vjp.
+template <int IMG>
+__device__ __forceinline__ void vjp_atom2(int N, int i, bool valid, const AtomHdr2& H, const PairK& K,
+                                          const PairGeo& G, bool fresh, bool skip_back, int nin_max, int nout_max,
+                                          const float4* __restrict__ xs, const float2* __restrict__ ps,
+                                          const float4* __restrict__ lam, const unsigned* __restrict__ nbr, int cap,
+                                          float4* qd, int* qj, float4* __restrict__ gx_s, float2* __restrict__ gp_s,
+                                          long long* __restrict__ ffix, float4* __restrict__ e_atom, float scale,
+                                          unsigned* flags) {
+    const int lane = threadIdx.x & 31, l = lane & 15;
+    const float2 pi = H.pi;
+    const float4 li = lam[i];
+    VjpAcc A, B;
+    auto heavy_a = [&](const float4& q, int j, bool on) {
+        vjp_heavy<true, kCoulNone>(q, lam[j], ps[j], on, li, pi, H.xr.w, K, 0.f, 0.f, 0.f, A);
+    };
+    auto heavy_b = [&](const float4& q, int j, bool on) {
+        vjp_heavy<true, kCoulNone>(q, lam[j], ps[j], on, li, pi, H.xr.w, K, 0.f, 0.f, 0.f, B);
+    };
+    const unsigned* row = nbr + (size_t)i * cap;
+    walk_front2<IMG>(H, G, row, nin_max, fresh, K.rc2, xs, heavy_a, heavy_b);
+    const int nout = (!fresh && !skip_back) ? H.nout : 0;
+    walk_back2<IMG>(H, G, row + (cap - nout), nout, nout_max, K.rc2, xs, qd, qj, heavy_a, heavy_b);
+    // group lane k holds the sum of value k
+    float v[16] = {A.fx + B.fx, A.fy + B.fy, A.fz + B.fz, A.elj + B.elj, A.edir + B.edir, A.gx + B.gx,
+                   A.gy + B.gy, A.gz + B.gz, A.gq + B.gq, A.gs + B.gs, A.ge + B.ge, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float sum = group_sum_transposed<16>(v);
+    if (valid && l < 3) ffix[(size_t)l * N + i] = to_fix(sum, scale, flags + 1);
+    float w[11];
+#pragma unroll
+    for (int q = 3; q < 11; ++q) w[q] = __shfl_sync(0xffffffffu, sum, (lane & 16) + q);
+    if (valid && l == 0) {
+        e_atom[i] = make_float4(0.5f * w[3], 0.5f * w[4], 0.f, 0.f);
+        gx_s[i] = make_float4(w[5], w[6], w[7], w[8]);
+        gp_s[i] = make_float2(w[9], w[10]);
+    }
+}
+
+template <bool LJ>
+__global__ void __launch_bounds__(kVjpThreads, 3) k_vjp2(
+    int N, int per_block, int cap, const int* __restrict__ sid, const SysDev* __restrict__ sys,
+    const float4* __restrict__ xs, const float2* __restrict__ ps, const float4* __restrict__ lam,
+    const unsigned* __restrict__ nbr, const int* __restrict__ cnt, const int* __restrict__ cnt_out,
+    float4* __restrict__ gx_s, float2* __restrict__ gp_s, long long* __restrict__ ffix,
+    float4* __restrict__ e_atom, float scale, unsigned* flags, const unsigned* __restrict__ prune_sys) {
+    pdl_wait();
+    __shared__ float4 qd_all[kVjpWarps][2][kQueue];
+    __shared__ int qj_all[kVjpWarps][2][kQueue];
+    const int w = threadIdx.x >> 5, grp = (threadIdx.x >> 4) & 1;
+    const int b0 = blockIdx.x * per_block;
+    const int i1 = min(N, b0 + per_block);
+    const bool fresh = flags[NB_FLAG_FRESH] != 0u;
+    for (int base = b0 + 2 * w; base < i1; base += 2 * kVjpWarps) {
+        const int i = base + grp;
+        const bool valid = i < i1;
+        const AtomHdr2 H = load_hdr2(valid ? i : base, valid, sid, xs, ps, nbr, cnt, cnt_out, cap);
+        const SysDev& S = sys[H.sys];
+        const PairK K = pair_k(S);
+        const PairGeo G = pair_geo(S);
+        const bool pruned = !fresh && prune_sys && (prune_sys[H.sys] & kPruned) != 0u;
+        const bool skip_back = pruned && S.rin2 > 0.f;
+        const int nout = (!fresh && !skip_back) ? H.nout : 0;
+        const int nin_max = max(H.nin, __shfl_xor_sync(0xffffffffu, H.nin, 16));
+        const int nout_max = max(nout, __shfl_xor_sync(0xffffffffu, nout, 16));
+        int mode = (G.fold[0] || G.fold[1] || G.fold[2]) ? kImgFold : (H.wrap ? kImgCode : kImgPlain);
+        mode = max(mode, __shfl_xor_sync(0xffffffffu, mode, 16));
+        float4* qd = qd_all[w][grp];
+        int* qj = qj_all[w][grp];
+#define NB_VJP2_ARGS N, valid ? i : base, valid, H, K, G, fresh, skip_back, nin_max, nout_max, xs, ps, lam, nbr, cap, \
+                     qd, qj, gx_s, gp_s, ffix, e_atom, scale, flags
+        if (mode == kImgPlain) vjp_atom2<kImgPlain>(NB_VJP2_ARGS);
+        else if (mode == kImgCode) vjp_atom2<kImgCode>(NB_VJP2_ARGS);
+        else vjp_atom2<kImgFold>(NB_VJP2_ARGS);
+#undef NB_VJP2_ARGS
+    }
+}
+
 // Exclusion correction (Ewald): for each excluded partner j of atom i (at any distance; the
 // reciprocal sum still contains the pair), -ke q_i q_j erf(alpha r)/r and its force, one
 // thread per atom (slot order), launched after the pair (or VJP) kernel.  The partners are
@@ -1207,9 +1286,14 @@ static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp, bool energy, bo
     const int N = h->n_atoms;
     if (vjp) {
         const int pb = pair_atoms_per_block(h, kVjpWarps);
-        launch_pdl(k_vjp<LJ, COUL>, cdiv(N, pb), kVjpThreads, 0, st, N, pb, h->cap, h->sid, h->sys, h->xs, h->ps,
-                   h->lam, h->nbr, h->nbr_cnt, h->nbr_out, h->gx_s, h->gp_s, h->ffix, h->e_atom, h->fscale, h->flags,
-                   (const unsigned*)h->prune_sys);
+        if (COUL == kCoulNone && LJ && pb >= 2 * kVjpWarps)  // LJ only: two atoms per warp, bitwise the same
+            launch_pdl(k_vjp2<LJ>, cdiv(N, pb), kVjpThreads, 0, st, N, pb, h->cap, h->sid, h->sys, h->xs, h->ps,
+                       h->lam, h->nbr, h->nbr_cnt, h->nbr_out, h->gx_s, h->gp_s, h->ffix, h->e_atom, h->fscale,
+                       h->flags, (const unsigned*)h->prune_sys);
+        else
+            launch_pdl(k_vjp<LJ, COUL>, cdiv(N, pb), kVjpThreads, 0, st, N, pb, h->cap, h->sid, h->sys, h->xs,
+                       h->ps, h->lam, h->nbr, h->nbr_cnt, h->nbr_out, h->gx_s, h->gp_s, h->ffix, h->e_atom, h->fscale,
+                       h->flags, (const unsigned*)h->prune_sys);
     } else {
         const int pb = pair_atoms_per_block(h, kPairWarps, true);
         // LJ only: two atoms per warp, bitwise the same results; not on handles too small to

@@ -78,3 +78,35 @@ def test_several_lj_systems_in_one_handle(kind):
         for a in range(len(amps)):
             assert np.array_equal(batched[a][0][offs[k]:offs[k + 1]], alone[a][0][:s.n]), (k, a)
             assert np.array_equal(batched[a][1][k], alone[a][1][0]), (k, a)
+
+
+def _vjp(systems, xs_list, lam_lj):
+    xq0 = [nbcore.pack_xq(s.x, s.q) for s in systems]
+    n = sum(s.n for s in systems)
+    lam = np.zeros((n, 3), np.float32)
+    lam[:lam_lj.shape[0]] = lam_lj
+    lam_d = torch.from_numpy(lam).cuda()
+    outs = []
+    with nbcore.Handle(systems) as h:
+        for xs in xs_list:
+            parts = [nbcore.pack_xq(x, s.q) if x is not None else q for x, s, q in zip(xs, systems, xq0)]
+            xq = torch.from_numpy(np.concatenate(parts)).cuda()
+            gx = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+            gq, gs, ge = (torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3))
+            f = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+            h.nonbonded_force_vjp(xq, lam_d, gx, gq, gs, ge, f)
+            h.check()
+            outs.append([t.cpu().numpy() for t in (gx, gq, gs, ge, f)])
+    return outs
+
+
+def test_force_vjp_two_atoms_per_warp_bitwise_equal():
+    s = wl.lj_random(12000, seed=34, n_types=2)
+    s.r_switch = 2.2
+    xs = _moves(s, 8, [0.0, 0.05])
+    lam = np.random.default_rng(3).standard_normal((s.n, 3)).astype(np.float32)
+    alone = _vjp([s], [[x] for x in xs], lam)
+    mixed = _vjp([s, _water()], [[x, None] for x in xs], lam)
+    for k, (a, m) in enumerate(zip(alone, mixed)):
+        for name, ta, tm in zip(("gx", "gq", "gsigma", "gsqrt_eps", "f"), a, m):
+            assert np.array_equal(ta, tm[:s.n]), (k, name, np.abs(ta - tm[:s.n]).max())

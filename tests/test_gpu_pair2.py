@@ -16,13 +16,13 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _run(systems, xs_list, energies):
+def _run(systems, xs_list, energies, **opts):
     xq0 = [nbcore.pack_xq(s.x, s.q) for s in systems]
     n = sum(s.n for s in systems)
     f = torch.empty((n, 3), dtype=torch.float32, device="cuda")
     e = torch.empty((len(systems), 6), dtype=torch.float64, device="cuda")
     out = []
-    with nbcore.Handle(systems) as h:
+    with nbcore.Handle(systems, **opts) as h:
         for xs in xs_list:
             parts = [nbcore.pack_xq(x, s.q) if x is not None else q for x, s, q in zip(xs, systems, xq0)]
             xq = torch.from_numpy(np.concatenate(parts)).cuda()
@@ -110,3 +110,15 @@ def test_force_vjp_two_atoms_per_warp_bitwise_equal():
     for k, (a, m) in enumerate(zip(alone, mixed)):
         for name, ta, tm in zip(("gx", "gq", "gsigma", "gsqrt_eps", "f"), a, m):
             assert np.array_equal(ta, tm[:s.n]), (k, name, np.abs(ta - tm[:s.n]).max())
+
+
+def test_two_atoms_per_warp_with_pruned_lists():
+    """Dynamic list pruning on (prune skin 0.1): the kept rows are re-partitioned and the
+    back parts skipped, in both kernels alike."""
+    s = wl.lj_random(12000, seed=35)
+    xs = _moves(s, 9, [0.0, 0.02, 0.045, 0.06])  # past half the prune skin from the third on
+    alone, _ = _run([s], [[x] for x in xs], True, prune_skin=0.1)
+    mixed, _ = _run([s, _water()], [[x, None] for x in xs], True, prune_skin=0.1)
+    for k, ((fa, ea), (fm, em)) in enumerate(zip(alone, mixed)):
+        assert np.array_equal(fa, fm[:s.n]), (k, np.abs(fa - fm[:s.n]).max())
+        assert np.array_equal(ea[0], em[0]), k

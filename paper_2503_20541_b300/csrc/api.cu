@@ -404,6 +404,7 @@ nb_status nb_create(nb_handle** out, const nb_system_desc* sys, int32_t n_system
         D.periodic = d.periodic ? 1 : 0;
         D.has_coul = d.ke != 0.0;
         if (D.has_coul) h->any_coul = 1;
+        else h->any_uncharged = 1;
         D.has_lj = 1;
         D.pme = d.pme_grid[0] > 0;
         for (int k = 0; k < 3; ++k) {

@@ -139,6 +139,7 @@ struct nb_handle {
     double d_oh = 0.0, d_hh = 0.0;
     std::vector<int> sid_host;   // system of each atom (caller order)
     int any_coul = 0;   // some system has ke != 0
+    int any_uncharged = 0;  // some system has ke == 0
     int coul_kind = 1;  // electrostatics of the charged systems: 1 Ewald, 2 reaction field
     long long grid_total = 0, cgrid_total = 0;
     int n_conv_blocks = 0;

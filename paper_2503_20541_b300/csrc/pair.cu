@@ -337,13 +337,34 @@ __device__ __forceinline__ void pair_atom(int N, int i, const AtomHdr& H, const 
 // 64 registers, four blocks (32 warps) per SM: the walk is latency-bound and the few
 // spilled values are cheaper than the lost occupancy (water 24k: 64.7 -> 63.0 us fresh,
 // 106.8 -> 99.6 us with the list reused, against 80 registers and three blocks).
-template <bool LJ, int COUL, bool EN>
+// The two-atoms-per-warp pass of an LJ-only block (defined with k_pair2 below).
+template <bool LJ, bool EN>
+__device__ __forceinline__ void pair2_block(
+    int N, int per_block, int cap, const int* __restrict__ sid, const SysDev* __restrict__ sys,
+    const float4* __restrict__ xs, const float2* __restrict__ ps, const unsigned* __restrict__ nbr,
+    const int* __restrict__ cnt, const int* __restrict__ cnt_out, long long* __restrict__ ffix,
+    float4* __restrict__ e_atom, float scale, unsigned* flags, const unsigned* __restrict__ prune_sys);
+
+// MIXED: the handle holds both charged and uncharged systems; a block whose atoms all belong
+// to one uncharged system runs the two-atoms-per-warp pass (bitwise the same results).
+template <bool LJ, int COUL, bool EN, bool MIXED>
 __global__ void __launch_bounds__(kPairThreads, 4) k_pair(
     int N, int per_block, int cap, const int* __restrict__ sid, const SysDev* __restrict__ sys,
     const float4* __restrict__ xs, const float2* __restrict__ ps, const unsigned* __restrict__ nbr,
     const int* __restrict__ cnt, const int* __restrict__ cnt_out, long long* __restrict__ ffix,
     float4* __restrict__ e_atom, float scale, unsigned* flags, const unsigned* __restrict__ prune_sys) {
     pdl_wait();
+    if (MIXED) {
+        const int b0 = blockIdx.x * per_block, i1 = min(N, b0 + per_block);
+        if (b0 < i1) {
+            const int s0 = sid[b0];
+            if (s0 == sid[i1 - 1] && sys[s0].ke == 0.f) {
+                pair2_block<LJ, EN>(N, per_block, cap, sid, sys, xs, ps, nbr, cnt, cnt_out, ffix, e_atom, scale,
+                                    flags, prune_sys);
+                return;
+            }
+        }
+    }
     __shared__ float4 qd_all[kPairWarps][kQueue];
     __shared__ int qj_all[kPairWarps][kQueue];
     const int w = threadIdx.x >> 5;
@@ -583,12 +604,11 @@ __device__ __forceinline__ void pair_atom2(int N, int i, bool valid, const AtomH
 // LJ-only pair kernel, two atoms per warp (one per group), the atom ranges of k_pair's
 // blocks.  Results bitwise those of k_pair<LJ, kCoulNone, EN>.
 template <bool LJ, bool EN>
-__global__ void __launch_bounds__(kPairThreads, 4) k_pair2(
+__device__ __forceinline__ void pair2_block(
     int N, int per_block, int cap, const int* __restrict__ sid, const SysDev* __restrict__ sys,
     const float4* __restrict__ xs, const float2* __restrict__ ps, const unsigned* __restrict__ nbr,
     const int* __restrict__ cnt, const int* __restrict__ cnt_out, long long* __restrict__ ffix,
     float4* __restrict__ e_atom, float scale, unsigned* flags, const unsigned* __restrict__ prune_sys) {
-    pdl_wait();
     __shared__ float4 qd_all[kPairWarps][2][kQueue];
     __shared__ int qj_all[kPairWarps][2][kQueue];
     const int w = threadIdx.x >> 5, grp = (threadIdx.x >> 4) & 1;
@@ -620,6 +640,16 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_pair2(
         else pair_atom2<LJ, EN, kImgFold>(NB_PAIR2_ARGS);
 #undef NB_PAIR2_ARGS
     }
+}
+
+template <bool LJ, bool EN>
+__global__ void __launch_bounds__(kPairThreads, 4) k_pair2(
+    int N, int per_block, int cap, const int* __restrict__ sid, const SysDev* __restrict__ sys,
+    const float4* __restrict__ xs, const float2* __restrict__ ps, const unsigned* __restrict__ nbr,
+    const int* __restrict__ cnt, const int* __restrict__ cnt_out, long long* __restrict__ ffix,
+    float4* __restrict__ e_atom, float scale, unsigned* flags, const unsigned* __restrict__ prune_sys) {
+    pdl_wait();
+    pair2_block<LJ, EN>(N, per_block, cap, sid, sys, xs, ps, nbr, cnt, cnt_out, ffix, e_atom, scale, flags, prune_sys);
 }
 
 // Force VJP.  For each directed pair (i, j) with u = lam_i - lam_j and du = d.u:
@@ -1303,10 +1333,14 @@ static void pair_launch(nb_handle* h, cudaStream_t st, bool vjp, bool energy, bo
             launch_pdl(energy ? k_pair2<LJ, true> : k_pair2<LJ, false>, cdiv(N, pb), kPairThreads, 0, st, N, pb,
                        h->cap, h->sid, h->sys, h->xs, h->ps, h->nbr, h->nbr_cnt, h->nbr_out, h->ffix, h->e_atom,
                        h->fscale, h->flags, (const unsigned*)h->prune_sys);
+        else if (LJ && COUL != kCoulNone && h->any_uncharged && pb >= 2 * kPairWarps)
+            launch_pdl(energy ? k_pair<LJ, COUL, true, true> : k_pair<LJ, COUL, false, true>, cdiv(N, pb),
+                       kPairThreads, 0, st, N, pb, h->cap, h->sid, h->sys, h->xs, h->ps, h->nbr, h->nbr_cnt,
+                       h->nbr_out, h->ffix, h->e_atom, h->fscale, h->flags, (const unsigned*)h->prune_sys);
         else
-            launch_pdl(energy ? k_pair<LJ, COUL, true> : k_pair<LJ, COUL, false>, cdiv(N, pb), kPairThreads, 0, st,
-                       N, pb, h->cap, h->sid, h->sys, h->xs, h->ps, h->nbr, h->nbr_cnt, h->nbr_out, h->ffix, h->e_atom,
-                       h->fscale, h->flags, (const unsigned*)h->prune_sys);
+            launch_pdl(energy ? k_pair<LJ, COUL, true, false> : k_pair<LJ, COUL, false, false>, cdiv(N, pb),
+                       kPairThreads, 0, st, N, pb, h->cap, h->sid, h->sys, h->xs, h->ps, h->nbr, h->nbr_cnt,
+                       h->nbr_out, h->ffix, h->e_atom, h->fscale, h->flags, (const unsigned*)h->prune_sys);
         if (precise)
             launch_pdl(k_energy_df<LJ, COUL>, cdiv(N, pb), kPairThreads, 0, st, N, pb, h->cap, h->sid, h->sys, h->xs,
                        h->ps, h->nbr, h->nbr_cnt, h->nbr_out, h->e_atom, h->e_lo, (const unsigned*)h->flags,
